@@ -1,0 +1,201 @@
+"""The oracle: a plain CPU evaluator of ALCQI(D) hypotheses by set semantics.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference arm may import this package.  It shares
+no code with the GPU library (``paper_2412_00802_gb300``) and never imports
+it.
+
+``hedl_oracle.c`` is the evaluator (byte-per-membership sets, role
+assertions as (subject, object) pairs, the paper's Section III layout);
+``fo_brute`` is a second, first-order-semantics evaluator in pure Python for
+tiny inputs, used to pin the C one.  This wrapper only marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hedl_oracle.c")
+_LIB = os.path.join(_HERE, "libhedl_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {0: "ok", -1: "bad op", -2: "bad id", -3: "stack underflow", -4: "stack overflow",
+          -5: "program does not reduce to one concept", -6: "empty program", -7: "out of memory"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (plain -O2, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _KB(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64),
+                ("n_concepts", ctypes.c_int32),
+                ("concept_member", ctypes.c_void_p),
+                ("n_roles", ctypes.c_int32),
+                ("role_off", ctypes.c_void_p),
+                ("subj", ctypes.c_void_p),
+                ("obj", ctypes.c_void_p),
+                ("n_props", ctypes.c_int32),
+                ("prop", ctypes.c_void_p)]
+
+
+def load(path: str):
+    """Load an oracle shared library from ``path`` and declare its signatures."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.oracle_validate.argtypes = [P, P, ctypes.c_int64]
+    L.oracle_validate.restype = ctypes.c_int
+    L.oracle_eval.argtypes = [P, P, ctypes.c_int64, P]
+    L.oracle_eval.restype = ctypes.c_int
+    L.oracle_score.argtypes = [ctypes.c_int64, P, P, P, P]
+    L.oracle_score.restype = None
+    L.oracle_eval_batch.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int32, P, P, P]
+    L.oracle_eval_batch.restype = ctypes.c_int64
+    return L
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load(build())
+    return _lib
+
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+@dataclass
+class OracleKB:
+    """A KB in the oracle's own layout (bytes per membership, assertion pairs)."""
+    n: int
+    member: np.ndarray        # uint8 [C][n]
+    role_off: np.ndarray      # int64 [R+1]
+    subj: np.ndarray          # uint32 [E]
+    obj: np.ndarray           # uint32 [E]
+    prop: np.ndarray          # float32 [P][n]
+    pos: np.ndarray           # uint8 [n]
+    neg: np.ndarray           # uint8 [n]
+
+    def __post_init__(self):
+        for name in ("member", "role_off", "subj", "obj", "prop", "pos", "neg"):
+            setattr(self, name, np.ascontiguousarray(getattr(self, name)))
+        self._c = _KB(self.n, self.member.shape[0], _ptr(self.member) if self.member.size else None,
+                      self.role_off.size - 1, _ptr(self.role_off), _ptr(self.subj) if self.subj.size else None,
+                      _ptr(self.obj) if self.obj.size else None, self.prop.shape[0],
+                      _ptr(self.prop) if self.prop.size else None)
+
+    @property
+    def cptr(self):
+        return ctypes.addressof(self._c)
+
+    @classmethod
+    def from_parts(cls, n: int, member: np.ndarray, edges: Sequence[Tuple[np.ndarray, np.ndarray]],
+                   prop: np.ndarray, pos: np.ndarray, neg: np.ndarray) -> "OracleKB":
+        """edges: per role (subjects, objects); each pair must appear at most once."""
+        offs = [0]
+        subj, obj = [], []
+        for s, o in edges:
+            s = np.asarray(s, dtype=np.uint32)
+            o = np.asarray(o, dtype=np.uint32)
+            if s.size:
+                key = s.astype(np.uint64) * np.uint64(max(n, 1)) + o.astype(np.uint64)
+                if np.unique(key).size != key.size:
+                    raise ValueError("role assertions must be a set (duplicate pair)")
+                if int(s.max()) >= n or int(o.max()) >= n:
+                    raise ValueError("assertion names an individual >= n")
+            subj.append(s)
+            obj.append(o)
+            offs.append(offs[-1] + s.size)
+        cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0, np.uint32)
+        return cls(n, np.asarray(member, np.uint8).reshape(-1, n) if n else np.zeros((len(member), 0), np.uint8),
+                   np.array(offs, dtype=np.int64), cat(subj), cat(obj),
+                   np.asarray(prop, np.float32).reshape(-1, n) if n else np.zeros((len(prop), 0), np.float32),
+                   np.asarray(pos, np.uint8), np.asarray(neg, np.uint8))
+
+
+def from_synth(kb) -> OracleKB:
+    """Convert a synthetic KB (bitsets + CSR) into the oracle's layout.
+
+    Only forward assertions are passed: the oracle reads an inverse role by
+    swapping subject and object, never through the inverse CSR.
+    """
+    n = kb.n
+    nbytes = (n + 7) // 8
+    member = np.zeros((kb.n_concepts, n), dtype=np.uint8)
+    for c in range(kb.n_concepts):
+        member[c] = np.unpackbits(kb.concept_bits[c].view(np.uint8)[:nbytes], bitorder="little")[:n]
+    edges = []
+    for r in range(kb.n_roles):
+        deg = np.diff(kb.row_ptr[r].astype(np.int64))
+        edges.append((np.repeat(np.arange(n, dtype=np.uint32), deg), kb.col[r]))
+    pos = np.zeros(n, dtype=np.uint8)
+    pos[kb.pos_idx] = 1
+    neg = np.zeros(n, dtype=np.uint8)
+    neg[kb.neg_idx] = 1
+    return OracleKB.from_parts(n, member, edges, kb.prop_vals, pos, neg)
+
+
+def validate(okb: OracleKB, prog, L=None) -> int:
+    p = np.ascontiguousarray(prog, dtype=np.uint64)
+    return (L or lib()).oracle_validate(okb.cptr, _ptr(p) if p.size else None, p.size)
+
+
+def eval_program(okb: OracleKB, prog, L=None) -> np.ndarray:
+    """Instance set of one program as bool[n]; raises ValueError on a bad program."""
+    p = np.ascontiguousarray(prog, dtype=np.uint64)
+    out = np.zeros(max(okb.n, 1), dtype=np.uint8)
+    e = (L or lib()).oracle_eval(okb.cptr, _ptr(p) if p.size else None, p.size, _ptr(out))
+    if e:
+        raise ValueError(ERRORS.get(e, str(e)))
+    return out[: okb.n].astype(bool)
+
+
+def score(okb: OracleKB, r: np.ndarray, L=None) -> np.ndarray:
+    """(TP, FP, FN, TN) of an instance set (Algorithm 15 plus the complements)."""
+    rr = np.ascontiguousarray(r, dtype=np.uint8)
+    c = np.zeros(4, dtype=np.int64)
+    (L or lib()).oracle_score(okb.n, _ptr(rr), _ptr(okb.pos), _ptr(okb.neg), _ptr(c))
+    return c
+
+
+def eval_batch(okb: OracleKB, progs: np.ndarray, offs: np.ndarray, threads: int = 1,
+               keep_sets: bool = False, L=None) -> Tuple[np.ndarray, Optional[np.ndarray], np.ndarray]:
+    """Evaluate and score a batch: returns counts int64[H][4], sets uint8[H][n] or None, errs."""
+    progs = np.ascontiguousarray(progs, dtype=np.uint64)
+    offs64 = np.ascontiguousarray(offs, dtype=np.int64)
+    H = offs64.size - 1
+    counts = np.zeros((H, 4), dtype=np.int64)
+    errs = np.zeros(H, dtype=np.int32)
+    sets = np.zeros((H, okb.n), dtype=np.uint8) if keep_sets else None
+    (L or lib()).oracle_eval_batch(okb.cptr, _ptr(progs) if progs.size else None, _ptr(offs64), H,
+                            _ptr(okb.pos), _ptr(okb.neg), threads, _ptr(counts),
+                            _ptr(sets) if sets is not None else None, _ptr(errs))
+    return counts, sets, errs
+
+
+def accuracy_f1(counts: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """acc = (TP+TN)/(|P|+|N|), F1 = 2TP/(2TP+FP+FN) (0 when the denominator is 0), in float64."""
+    c = np.asarray(counts, dtype=np.float64).reshape(-1, 4)
+    tp, fp, fn, tn = c[:, 0], c[:, 1], c[:, 2], c[:, 3]
+    tot = tp + fp + fn + tn
+    acc = np.where(tot > 0, (tp + tn) / np.where(tot > 0, tot, 1), 0.0)
+    den = 2 * tp + fp + fn
+    f1 = np.where(den > 0, 2 * tp / np.where(den > 0, den, 1), 0.0)
+    return acc, f1

@@ -1,0 +1,359 @@
+"""Seeded synthetic knowledge bases with the shapes of the paper's workloads.
+
+A KB here is plain host data:
+
+* concept membership bitsets, uint32 words, bit i of word w is individual
+  32*w + i (LSB first); each row padded to ``wp`` words (a multiple of 4, so a
+  row starts on a 16-byte boundary); bits >= n are zero;
+* per role a CSR (``row_ptr`` uint32[n+1], ``col`` uint32[E]) with sorted,
+  duplicate-free rows, plus the inverse CSR (the transpose), whose rows come out
+  sorted because it is built by a stable sort of the forward edges by object;
+* numeric data properties as float32[n], NaN where the value is missing;
+* positive and negative example sets (bitsets and index lists).
+
+Degree laws, value distributions and example counts follow the workload
+descriptions.  The generator draws random numbers only from the counter-based
+streams in :mod:`synth.rng`, so every array is a pure function of the seed.
+It holds none of the evaluation method's arithmetic.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+from . import rng
+
+# sub-stream ids (one per component, so components are independent)
+S_CONCEPT_P = 1
+S_DAG = 2
+S_PROP_VAL = 3
+S_PROP_MISS = 4
+S_EXAMPLES = 5
+S_CONCEPT = 1 << 16
+S_ROLE_DEG = 2 << 16
+S_ROLE_TGT = 3 << 16
+S_PROP = 4 << 16
+
+
+@dataclass(frozen=True)
+class KBConfig:
+    name: str
+    seed: int
+    n: int
+    n_concepts: int
+    p_lo: float
+    p_hi: float
+    dag: bool
+    n_roles: int
+    degree: Tuple            # ("poisson", lam) | ("zipf", a, mean, cap) | ("single",) | ("unique",)
+    n_props: int
+    prop_dist: Tuple         # ("uniform", lo, hi) | ("lognormal", mu, sigma) | ("normal", mu, sd)
+    missing: float
+    n_pos: int
+    n_neg: int
+
+    def scaled(self, n: int, **kw) -> "KBConfig":
+        """Same distributions on ``n`` individuals (example counts scaled)."""
+        f = n / self.n
+        d = dict(n=n, n_pos=max(1, int(round(self.n_pos * f))), n_neg=max(1, int(round(self.n_neg * f))))
+        d.update(kw)
+        return replace(self, **d)
+
+
+CONFIGS = {
+    # plain single-hypothesis evaluation on a small KB
+    "c1": KBConfig("c1", 1, 10_000, 50, 0.02, 0.30, True, 8, ("poisson", 3.0), 4,
+                   ("uniform", 0.0, 100.0), 0.20, 200, 200),
+    # single large hypothesis latency
+    "c2": KBConfig("c2", 2, 10_000_000, 200, 0.01, 0.50, False, 32, ("zipf", 2.1, 8.0, 10_000), 16,
+                   ("lognormal", 0.0, 1.0), 0.10, 100_000, 100_000),
+    # batched exact evaluation
+    "c3": KBConfig("c3", 3, 1_000_000, 100, 0.01, 0.50, False, 16, ("poisson", 6.0), 8,
+                   ("uniform", 0.0, 1000.0), 0.0, 10_000, 10_000),
+    # refinement search
+    "c5": KBConfig("c5", 5, 4_000_000, 300, 0.01, 0.50, False, 64, ("zipf", 2.3, 10.0, 10_000), 32,
+                   ("normal", 50.0, 15.0), 0.15, 50_000, 50_000),
+}
+CONFIGS["c4"] = replace(CONFIGS["c2"], name="c4")
+
+
+def words(n: int) -> Tuple[int, int]:
+    w = (n + 31) // 32
+    return w, (w + 3) // 4 * 4
+
+
+def pack_bits(member: np.ndarray, wp: int) -> np.ndarray:
+    """bool[n] -> uint32[wp] LSB-first, zero padded."""
+    b = np.packbits(member.astype(bool), bitorder="little")
+    out = np.zeros(wp * 4, dtype=np.uint8)
+    out[: b.size] = b
+    return out.view("<u4").copy()
+
+
+def unpack_bits(bits: np.ndarray, n: int) -> np.ndarray:
+    """uint32[>=W] -> bool[n]."""
+    b = np.ascontiguousarray(bits, dtype="<u4").view(np.uint8)
+    return np.unpackbits(b, bitorder="little")[:n].astype(bool)
+
+
+# --------------------------------------------------------------------------- degree laws
+def poisson_cdf(lam: float, kmax: int) -> np.ndarray:
+    p = np.empty(kmax + 1)
+    p[0] = math.exp(-lam)
+    for k in range(1, kmax + 1):
+        p[k] = p[k - 1] * lam / k
+    c = np.cumsum(p)
+    c[-1] = 1.0
+    return c
+
+
+def shifted_zipf_pmf(a: float, s: float, cap: int) -> np.ndarray:
+    d = np.arange(cap + 1, dtype=np.float64)
+    w = (d + s) ** (-a)
+    return w / w.sum()
+
+
+def solve_zipf_shift(a: float, mean: float, cap: int) -> float:
+    """Shift s with E[d] = mean for P(d) proportional to (d+s)^-a on {0..cap}.
+
+    The mean grows with s, so bisection on s finds it.
+    """
+    d = np.arange(cap + 1, dtype=np.float64)
+    lo, hi = 1e-6, 1e6
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        m = float((shifted_zipf_pmf(a, mid, cap) * d).sum())
+        if m < mean:
+            lo = mid
+        else:
+            hi = mid
+    return math.sqrt(lo * hi)
+
+
+def draw_degrees(cfg: KBConfig, r: int, n: int) -> Tuple[np.ndarray, dict]:
+    kind = cfg.degree[0]
+    meta = {}
+    if kind == "poisson":
+        cdf = poisson_cdf(cfg.degree[1], 200)
+        u = rng.uniform_range(cfg.seed, S_ROLE_DEG + r, n)
+        deg = np.searchsorted(cdf, u, side="right")
+    elif kind == "zipf":
+        a, mean, cap = cfg.degree[1], cfg.degree[2], int(cfg.degree[3])
+        s = solve_zipf_shift(a, mean, cap)
+        meta["zipf_shift"] = s
+        cdf = np.cumsum(shifted_zipf_pmf(a, s, cap))
+        cdf[-1] = 1.0
+        u = rng.uniform_range(cfg.seed, S_ROLE_DEG + r, n)
+        deg = np.searchsorted(cdf, u, side="right")
+    elif kind == "single":        # the paper's "single subject" set: one subject holds every edge
+        e = int(cfg.degree[1]) if len(cfg.degree) > 1 else n
+        deg = np.zeros(n, dtype=np.int64)
+        deg[int(rng.randint(cfg.seed, S_ROLE_DEG + r, np.array([0]), n)[0])] = min(e, n)
+    elif kind == "unique":        # the paper's "unique subject" set: each subject has one edge
+        deg = np.ones(n, dtype=np.int64)
+    else:
+        raise ValueError(kind)
+    return np.minimum(deg.astype(np.int64), n), meta
+
+
+def draw_targets(cfg: KBConfig, r: int, deg: np.ndarray, n: int) -> np.ndarray:
+    """Uniform targets, without replacement within a row, rows sorted ascending."""
+    e = int(deg.sum())
+    rows = np.repeat(np.arange(n, dtype=np.int64), deg)
+    if cfg.degree[0] == "unique":
+        # a permutation: subject i -> pi(i)
+        key = rng.u64(cfg.seed, S_ROLE_TGT + r, np.arange(n, dtype=np.uint64))
+        return np.argsort(key, kind="stable").astype(np.uint32)
+    tgt = rng.randint(cfg.seed, S_ROLE_TGT + r, np.arange(e, dtype=np.uint64), n)
+    attempt = 0
+    while True:
+        key = rows * n + tgt
+        order = np.argsort(key, kind="stable")
+        key = key[order]
+        tgt = tgt[order]
+        dup = np.zeros(e, dtype=bool)
+        if e > 1:
+            dup[1:] = key[1:] == key[:-1]
+        nd = int(dup.sum())
+        if nd == 0:
+            return tgt.astype(np.uint32)
+        attempt += 1
+        idx = np.nonzero(dup)[0].astype(np.uint64) + np.uint64(attempt) * np.uint64(1 << 40)
+        tgt[dup] = rng.randint(cfg.seed, S_ROLE_TGT + r, idx, n)
+        if attempt > 10_000:
+            raise RuntimeError("could not draw distinct targets")
+
+
+def transpose_csr(row_ptr: np.ndarray, col: np.ndarray, n: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Inverse CSR: a stable sort of the edges by object keeps subjects ascending per row."""
+    deg = np.diff(row_ptr.astype(np.int64))
+    subj = np.repeat(np.arange(n, dtype=np.uint32), deg)
+    order = np.argsort(col, kind="stable")
+    inv_col = subj[order].astype(np.uint32)
+    cnt = np.bincount(col.astype(np.int64), minlength=n)
+    inv_ptr = np.zeros(n + 1, dtype=np.uint32)
+    np.cumsum(cnt, out=inv_ptr[1:])
+    return inv_ptr, inv_col
+
+
+# --------------------------------------------------------------------------- the KB
+@dataclass
+class KB:
+    cfg: KBConfig
+    n: int
+    w: int
+    wp: int
+    concept_bits: np.ndarray          # uint32 [C][wp]
+    row_ptr: List[np.ndarray]         # per role uint32 [n+1]
+    col: List[np.ndarray]             # per role uint32 [E]
+    inv_row_ptr: List[np.ndarray]
+    inv_col: List[np.ndarray]
+    prop_vals: np.ndarray             # float32 [P][n]
+    pos_idx: np.ndarray
+    neg_idx: np.ndarray
+    pos_bits: np.ndarray              # uint32 [wp]
+    neg_bits: np.ndarray
+    meta: dict
+
+    @property
+    def n_concepts(self) -> int:
+        return self.concept_bits.shape[0]
+
+    @property
+    def n_roles(self) -> int:
+        return len(self.row_ptr)
+
+    @property
+    def n_props(self) -> int:
+        return self.prop_vals.shape[0]
+
+    def n_edges(self, r: int) -> int:
+        return int(self.col[r].size)
+
+    def nbytes(self) -> int:
+        t = self.concept_bits.nbytes + self.prop_vals.nbytes + 2 * self.pos_bits.nbytes
+        for r in range(self.n_roles):
+            t += 2 * self.row_ptr[r].nbytes + 2 * self.col[r].nbytes
+        return t
+
+
+def gen_concepts(cfg: KBConfig, wp: int, meta: dict) -> np.ndarray:
+    n, c = cfg.n, cfg.n_concepts
+    p = cfg.p_lo + (cfg.p_hi - cfg.p_lo) * rng.uniform_range(cfg.seed, S_CONCEPT_P, c)
+    bits = np.zeros((c, wp), dtype=np.uint32)
+    for j in range(c):
+        member = rng.uniform_range(cfg.seed, S_CONCEPT + j, n) < p[j]
+        bits[j] = pack_bits(member, wp)
+    if cfg.dag and c > 1:
+        # random subsumption forest: concept j < C has parent pj < j with prob 1/2
+        # (so the edges form a DAG); the ABox is closed downward, i.e. every
+        # member of a sub-concept is also a member of its super-concept.
+        j = np.arange(c, dtype=np.uint64)
+        has = rng.uniform(cfg.seed, S_DAG, j * np.uint64(2)) < 0.5
+        parent = np.full(c, -1, dtype=np.int64)
+        for k in range(1, c):
+            if has[k]:
+                parent[k] = int(rng.randint(cfg.seed, S_DAG, np.array([2 * k + 1], dtype=np.uint64), k)[0])
+        for k in range(c - 1, 0, -1):       # children have larger ids: finish them first
+            if parent[k] >= 0:
+                bits[parent[k]] |= bits[k]
+        meta["dag_parent"] = parent.tolist()
+    return bits
+
+
+def gen_props(cfg: KBConfig) -> np.ndarray:
+    n = cfg.n
+    out = np.empty((cfg.n_props, n), dtype=np.float32)
+    kind = cfg.prop_dist[0]
+    for p in range(cfg.n_props):
+        st = S_PROP + p
+        if kind == "uniform":
+            lo, hi = cfg.prop_dist[1], cfg.prop_dist[2]
+            v = lo + (hi - lo) * rng.uniform_range(cfg.seed, st, n)
+        elif kind == "lognormal":
+            v = np.exp(cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, st, n))
+        elif kind == "normal":
+            v = cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, st, n)
+        else:
+            raise ValueError(kind)
+        v = v.astype(np.float32)
+        if cfg.missing > 0:
+            miss = rng.uniform_range(cfg.seed, S_PROP_MISS * 1000 + p, n) < cfg.missing
+            v[miss] = np.nan
+        out[p] = v
+    return out
+
+
+def gen_examples(cfg: KBConfig, wp: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Disjoint uniform positive / negative sets (sorted index arrays)."""
+    n = cfg.n
+    if cfg.n_pos + cfg.n_neg > n:
+        raise ValueError("more examples than individuals")
+    key = rng.u64(cfg.seed, S_EXAMPLES, np.arange(n, dtype=np.uint64))
+    perm = np.argsort(key, kind="stable")
+    pos = np.sort(perm[: cfg.n_pos]).astype(np.int64)
+    neg = np.sort(perm[cfg.n_pos: cfg.n_pos + cfg.n_neg]).astype(np.int64)
+    return pos, neg
+
+
+def generate(cfg: KBConfig, roles: Optional[int] = None) -> KB:
+    n = cfg.n
+    w, wp = words(n)
+    meta = {"seed": cfg.seed, "config": cfg.name}
+    cb = gen_concepts(cfg, wp, meta)
+    rps, cols, irps, icols = [], [], [], []
+    for r in range(cfg.n_roles if roles is None else roles):
+        deg, m = draw_degrees(cfg, r, n)
+        meta.update(m)
+        tgt = draw_targets(cfg, r, deg, n)
+        rp = np.zeros(n + 1, dtype=np.uint32)
+        np.cumsum(deg, out=rp[1:])
+        rps.append(rp)
+        cols.append(tgt)
+        ip, ic = transpose_csr(rp, tgt, n)
+        irps.append(ip)
+        icols.append(ic)
+    props = gen_props(cfg)
+    pos, neg = gen_examples(cfg, wp)
+    mp = np.zeros(n, dtype=bool)
+    mp[pos] = True
+    mn = np.zeros(n, dtype=bool)
+    mn[neg] = True
+    return KB(cfg, n, w, wp, cb, rps, cols, irps, icols, props, pos, neg,
+              pack_bits(mp, wp), pack_bits(mn, wp), meta)
+
+
+def from_arrays(n: int, concepts: List[List[int]], roles: List[List[Tuple[int, int]]],
+                props: List[List[float]], pos: List[int], neg: List[int]) -> KB:
+    """Small hand-written KB (fixtures): concepts as member lists, roles as edge lists."""
+    w, wp = words(n)
+    cb = np.zeros((max(len(concepts), 0), wp), dtype=np.uint32)
+    for j, mem in enumerate(concepts):
+        m = np.zeros(n, dtype=bool)
+        m[list(mem)] = True
+        cb[j] = pack_bits(m, wp)
+    rps, cols, irps, icols = [], [], [], []
+    for edges in roles:
+        es = sorted(set((int(a), int(b)) for a, b in edges))
+        rp = np.zeros(n + 1, dtype=np.uint32)
+        for a, _ in es:
+            rp[a + 1] += 1
+        rp = np.cumsum(rp).astype(np.uint32)
+        col = np.array([b for _, b in es], dtype=np.uint32)
+        rps.append(rp)
+        cols.append(col)
+        ip, ic = transpose_csr(rp, col, n)
+        irps.append(ip)
+        icols.append(ic)
+    pv = np.array(props, dtype=np.float32).reshape(len(props), n) if props else np.zeros((0, n), np.float32)
+    mp = np.zeros(n, dtype=bool)
+    mp[list(pos)] = True
+    mn = np.zeros(n, dtype=bool)
+    mn[list(neg)] = True
+    cfg = KBConfig("fixture", 0, n, len(concepts), 0, 0, False, len(roles), ("fixture",), len(props),
+                   ("fixture",), 0.0, len(pos), len(neg))
+    return KB(cfg, n, w, wp, cb, rps, cols, irps, icols, pv, np.array(sorted(pos), dtype=np.int64),
+              np.array(sorted(neg), dtype=np.int64), pack_bits(mp, wp), pack_bits(mn, wp), {})

@@ -1,0 +1,289 @@
+"""Pins of the oracle to facts that do not come from the oracle itself.
+
+Each ``pin_*`` function takes a loaded oracle library and returns a list of
+failure messages (empty = pinned).  ``tests/test_oracle.py`` runs them on
+the real oracle and on deliberately broken copies of it (a planted mistake
+must make at least one pin fail).
+
+Sources of truth:
+* hand-worked fixtures (tests/golden/*.txt, each with its citations);
+* a first-order brute-force evaluator on tiny random KBs (oracle.fo_brute);
+* DL identities (De Morgan, double negation, excluded middle, FORALL as
+  NOT EXISTS NOT, ATLEAST 1 as EXISTS, ATMOST n as NOT ATLEAST n+1, EXACTLY
+  as ATLEAST and ATMOST, ATLEAST 0 as TOP, (r^-)^- = r) -- the oracle computes
+  each side by its own code path;
+* closed forms on the paper's two role-assertion stress shapes ("single
+  subject": one subject holds every assertion; "unique subject": each
+  subject one assertion, here a permutation) and on sorted data values;
+* the transposed assertion list: EXISTS r^- C on a KB equals EXISTS r C on
+  the KB whose role is the (numpy-built) transpose.
+"""
+from __future__ import annotations
+
+import math
+from typing import List
+
+import numpy as np
+
+import oracle
+from oracle import fo_brute
+from synth import kb as K
+from synth import programs as P
+from synth.rng import Rng
+from tests import golden_io
+
+
+def tiny_from_fixture(fx):
+    okb = oracle.OracleKB.from_parts(
+        fx.n,
+        np.array([[1 if i in c else 0 for i in range(fx.n)] for c in fx.concept_list()], dtype=np.uint8)
+        .reshape(-1, fx.n),
+        [(np.array([a for a, _ in es], np.uint32), np.array([b for _, b in es], np.uint32))
+         for es in fx.role_list()],
+        np.array(fx.prop_rows(), dtype=np.float32).reshape(-1, fx.n),
+        np.array([1 if i in fx.pos else 0 for i in range(fx.n)], np.uint8),
+        np.array([1 if i in fx.neg else 0 for i in range(fx.n)], np.uint8))
+    return okb
+
+
+def pin_golden(L) -> List[str]:
+    bad = []
+    for name in golden_io.fixtures():
+        fx = golden_io.load(name)
+        okb = tiny_from_fixture(fx)
+        for q, inst, cnt in fx.queries:
+            got = oracle.eval_program(okb, P.compile_text(q), L=L)
+            got_set = set(np.nonzero(got)[0].tolist())
+            if got_set != inst:
+                bad.append(f"{name}: {q}: {sorted(got_set)} != {sorted(inst)}")
+            c = tuple(int(x) for x in oracle.score(okb, got, L=L))
+            if c != cnt:
+                bad.append(f"{name}: {q}: counts {c} != {cnt}")
+    return bad
+
+
+def to_tiny(kb: K.KB) -> fo_brute.TinyKB:
+    n = kb.n
+    concepts = [set(np.nonzero(K.unpack_bits(kb.concept_bits[c], n))[0].tolist()) for c in range(kb.n_concepts)]
+    roles = []
+    for r in range(kb.n_roles):
+        rp, col = kb.row_ptr[r], kb.col[r]
+        roles.append({(a, int(col[k])) for a in range(n) for k in range(int(rp[a]), int(rp[a + 1]))})
+    props = [{i: float(v) for i, v in enumerate(kb.prop_vals[p]) if not math.isnan(v)} for p in range(kb.n_props)]
+    return fo_brute.TinyKB(n, concepts, roles, props)
+
+
+def random_program(r: Rng, kb: K.KB, depth: int, role_free: bool = False) -> P.Node:
+    """Random tree over every constructor, including TOP, BOT, EXACTLY and DEQ."""
+    if depth <= 1 or r.random() < 0.25:
+        k = r.randint(0, 9)
+        if k == 0:
+            return P.Node(P.TOP)
+        if k == 1:
+            return P.Node(P.BOT)
+        if k <= 3 and kb.n_props:
+            p = r.randint(0, kb.n_props - 1)
+            vals = kb.prop_vals[p]
+            t = float(vals[r.randint(0, kb.n - 1)])
+            if math.isnan(t):
+                t = float(r.randint(0, 100))
+            return P.Node((P.DGE, P.DLE, P.DEQ)[r.randint(0, 2)], p, P.f32_bits(t))
+        return P.Node(P.ATOM, r.randint(0, kb.n_concepts - 1))
+    k = r.randint(0, 2 if role_free else 8)
+    if k == 0:
+        return P.Node(P.NOT, kids=[random_program(r, kb, depth - 1, role_free)])
+    if k <= 2:
+        return P.Node((P.AND, P.OR)[k - 1], kids=[random_program(r, kb, depth - 1, role_free),
+                                                  random_program(r, kb, depth - 1, role_free)])
+    op = (P.EXISTS, P.FORALL, P.ATLEAST, P.ATMOST, P.EXACTLY, P.EXISTS)[k - 3]
+    n = r.randint(0, 4) if op in P.COUNT_OPS else 0
+    return P.Node(op, r.randint(0, kb.n_roles - 1), n, r.random() < 0.5, [random_program(r, kb, depth - 1)])
+
+
+def tiny_kbs():
+    base = K.CONFIGS["c1"]
+    out = []
+    for seed, n, deg in ((101, 20, ("poisson", 2.0)), (102, 33, ("poisson", 3.0)), (103, 40, ("poisson", 4.0)),
+                         (104, 17, ("zipf", 2.1, 3.0, 16))):
+        cfg = base.scaled(n, seed=seed, n_concepts=5, n_roles=3, degree=deg, n_props=2, n_pos=4, n_neg=4)
+        out.append(K.generate(cfg))
+    return out
+
+
+def pin_brute_force(L, programs_per_kb: int = 60) -> List[str]:
+    bad = []
+    for kb in tiny_kbs():
+        okb = oracle.from_synth(kb)
+        tiny = to_tiny(kb)
+        pos = set(kb.pos_idx.tolist())
+        neg = set(kb.neg_idx.tolist())
+        r = Rng(kb.cfg.seed, 77)
+        for i in range(programs_per_kb):
+            prog = random_program(r, kb, r.randint(1, 4)).postfix()
+            want = fo_brute.evaluate(tiny, prog)
+            got = oracle.eval_program(okb, prog, L=L)
+            got_set = set(np.nonzero(got)[0].tolist())
+            if got_set != want:
+                bad.append(f"brute force n={kb.n}: {P.to_text(P.from_postfix(prog))}")
+                continue
+            if tuple(oracle.score(okb, got, L=L)) != fo_brute.coverage(want, pos, neg):
+                bad.append(f"coverage n={kb.n}: {P.to_text(P.from_postfix(prog))}")
+    return bad
+
+
+def _identities(x: str, y: str, r: str, n: int) -> List[tuple]:
+    return [
+        (f"(not (and {x} {y}))", f"(or (not {x}) (not {y}))"),
+        (f"(not (or {x} {y}))", f"(and (not {x}) (not {y}))"),
+        (f"(not (not {x}))", x),
+        (f"(and {x} (not {x}))", "BOT"),
+        (f"(or {x} (not {x}))", "TOP"),
+        (f"(all {r} {x})", f"(not (some {r} (not {x})))"),
+        (f"(min 1 {r} {x})", f"(some {r} {x})"),
+        (f"(max {n} {r} {x})", f"(not (min {n + 1} {r} {x}))"),
+        (f"(exactly {n} {r} {x})", f"(and (min {n} {r} {x}) (max {n} {r} {x}))"),
+        (f"(min 0 {r} {x})", "TOP"),
+        (f"(max 0 {r} {x})", f"(not (some {r} {x}))"),
+        (f"(some {r}-- {x})", f"(some {r} {x})"),
+    ]
+
+
+def identity_kb(n: int = 600):
+    cfg = K.CONFIGS["c1"].scaled(n, seed=31, n_concepts=8, n_roles=3)
+    return K.generate(cfg)
+
+
+def pin_identities(L, kb=None, count: int = 6) -> List[str]:
+    kb = kb or identity_kb()
+    okb = oracle.from_synth(kb)
+    r = Rng(5, 5)
+    bad = []
+    for i in range(count):
+        x = P.to_text(random_program(r, kb, 3))
+        y = P.to_text(random_program(r, kb, 2))
+        role = f"r{r.randint(0, kb.n_roles - 1)}{'-' if r.random() < 0.5 else ''}"
+        n = r.randint(0, 3)
+        for lhs, rhs in _identities(x, y, role, n):
+            a = oracle.eval_program(okb, P.compile_text(lhs), L=L)
+            b = oracle.eval_program(okb, P.compile_text(rhs), L=L)
+            if not np.array_equal(a, b):
+                bad.append(f"identity {lhs} == {rhs}")
+        res = oracle.eval_program(okb, P.compile_text(x), L=L)
+        tp, fp, fn, tn = oracle.score(okb, res, L=L)
+        if tp + fn != kb.pos_idx.size or fp + tn != kb.neg_idx.size:
+            bad.append("TP+FN != |P| or FP+TN != |N|")
+        if tp != int(res[kb.pos_idx].sum()) or fp != int(res[kb.neg_idx].sum()):
+            bad.append("coverage differs from counting the example indices")
+    return bad
+
+
+def pin_inverse_transpose(L, kb=None) -> List[str]:
+    """EXISTS/FORALL/ATLEAST r^- C on a KB equal the forward ops on the transposed KB."""
+    kb = kb or identity_kb()
+    okb = oracle.from_synth(kb)
+    n = kb.n
+    edges_t = []
+    for r in range(kb.n_roles):
+        deg = np.diff(kb.inv_row_ptr[r].astype(np.int64))
+        edges_t.append((np.repeat(np.arange(n, dtype=np.uint32), deg), kb.inv_col[r]))
+    okb_t = oracle.OracleKB.from_parts(n, okb.member, edges_t, okb.prop, okb.pos, okb.neg)
+    bad = []
+    r = Rng(6, 6)
+    for i in range(8):
+        x = P.to_text(random_program(r, kb, 3, role_free=True))
+        role = r.randint(0, kb.n_roles - 1)
+        for form in ("(some r{}{} X)", "(all r{}{} X)", "(min 2 r{}{} X)", "(max 1 r{}{} X)"):
+            a = oracle.eval_program(okb, P.compile_text(form.format(role, "-").replace("X", x)), L=L)
+            b = oracle.eval_program(okb_t, P.compile_text(form.format(role, "").replace("X", x)), L=L)
+            if not np.array_equal(a, b):
+                bad.append(f"inverse vs transpose {form}")
+    return bad
+
+
+def pin_closed_forms(L) -> List[str]:
+    bad = []
+    base = K.CONFIGS["c1"]
+    # unique subject: role r is a permutation pi (a -> pi(a))
+    kb = K.generate(base.scaled(257, seed=41, n_concepts=4, n_roles=1, degree=("unique",)))
+    okb = oracle.from_synth(kb)
+    pi = kb.col[0].astype(np.int64)
+    for c in range(kb.n_concepts):
+        C = K.unpack_bits(kb.concept_bits[c], kb.n)
+        pre = C[pi]                                   # {a : pi(a) in C}
+        img = np.zeros(kb.n, bool)
+        img[pi[C]] = True                             # {pi(a) : a in C}
+        checks = [(f"(some r0 A{c})", pre), (f"(all r0 A{c})", pre), (f"(some r0- A{c})", img),
+                  (f"(min 2 r0 A{c})", np.zeros(kb.n, bool)), (f"(max 0 r0 A{c})", ~pre),
+                  (f"(exactly 1 r0- A{c})", img)]
+        for q, want in checks:
+            if not np.array_equal(oracle.eval_program(okb, P.compile_text(q), L=L), want):
+                bad.append(f"unique subject: {q}")
+    # single subject: subject s holds every assertion, to targets T
+    kb = K.generate(base.scaled(300, seed=42, n_concepts=4, n_roles=1, degree=("single", 120)))
+    okb = oracle.from_synth(kb)
+    s = int(np.nonzero(np.diff(kb.row_ptr[0].astype(np.int64)))[0][0])
+    T = np.zeros(kb.n, bool)
+    T[kb.col[0]] = True
+    for c in range(kb.n_concepts):
+        C = K.unpack_bits(kb.concept_bits[c], kb.n)
+        k = int((C & T).sum())
+        only_s = np.zeros(kb.n, bool)
+        only_s[s] = True
+        none = np.zeros(kb.n, bool)
+        allx = np.ones(kb.n, bool)
+        checks = [(f"(some r0 A{c})", only_s if k > 0 else none),
+                  (f"(min {k} r0 A{c})", only_s if k > 0 else allx),
+                  (f"(min {k + 1} r0 A{c})", none),
+                  (f"(exactly {k} r0 A{c})", only_s if k > 0 else allx),
+                  (f"(all r0 A{c})", allx if not (T & ~C).any() else ~only_s),
+                  (f"(some r0- A{c})", T if C[s] else none),
+                  (f"(max {max(k - 1, 0)} r0 A{c})", ~only_s if k > 0 else allx)]
+        for q, want in checks:
+            if not np.array_equal(oracle.eval_program(okb, P.compile_text(q), L=L), want):
+                bad.append(f"single subject: {q}")
+    # data ranges: counts from sorted present values (searchsorted)
+    kb = K.generate(base.scaled(5000, seed=43, n_concepts=1, n_roles=1))
+    okb = oracle.from_synth(kb)
+    for p in range(kb.n_props):
+        v = kb.prop_vals[p]
+        pres = np.sort(v[~np.isnan(v)])
+        for t in (float(pres[0]), float(pres[len(pres) // 3]), float(pres[-1]), -0.0, 0.0, 50.0,
+                  math.inf, -math.inf):
+            t32 = np.float32(t)
+            ge = len(pres) - int(np.searchsorted(pres, t32, side="left"))
+            le = int(np.searchsorted(pres, t32, side="right"))
+            eq = le - int(np.searchsorted(pres, t32, side="left"))
+            for op, want in ((P.DGE, ge), (P.DLE, le), (P.DEQ, eq)):
+                got = int(oracle.eval_program(okb, [P.insn(op, 0, p, P.f32_bits(t))], L=L).sum())
+                if got != want:
+                    bad.append(f"data closed form op={op} t={t}: {got} != {want}")
+    return bad
+
+
+def pin_validation(L) -> List[str]:
+    fx = golden_io.load("family.txt")
+    okb = tiny_from_fixture(fx)
+    A = lambda c: P.insn(P.ATOM, 0, c)
+    cases = [
+        ([], -6),
+        ([P.insn(0)], -1),
+        ([P.insn(15)], -1),
+        ([P.insn(255)], -1),
+        ([A(4)], -2),
+        ([A(0), P.insn(P.EXISTS, 0, 2)], -2),
+        ([P.insn(P.DGE, 0, 1, 0)], -2),
+        ([A(0), P.insn(P.AND)], -3),
+        ([P.insn(P.NOT)], -3),
+        ([A(0), A(1)], -5),
+        ([A(0)] * 65 + [P.insn(P.AND)] * 64, -4),
+        ([A(0)] * 64 + [P.insn(P.AND)] * 63, 0),
+    ]
+    bad = []
+    for prog, want in cases:
+        got = oracle.validate(okb, np.array(prog, dtype=np.uint64), L=L)
+        if got != want:
+            bad.append(f"validate {prog[:3]}...: {got} != {want}")
+    return bad
+
+
+ALL_PINS = (pin_golden, pin_brute_force, pin_identities, pin_inverse_transpose, pin_closed_forms, pin_validation)

@@ -1,0 +1,103 @@
+"""Seeded input generators: determinism and structural invariants (no GPU)."""
+import numpy as np
+import pytest
+
+from synth import hyps as Hy
+from synth import kb as K
+from synth import programs as P
+from synth import rng
+
+
+def test_counter_rng_is_stateless():
+    a = rng.u64(7, 3, np.arange(100, dtype=np.uint64))
+    r = rng.Rng(7, 3)
+    b = [r.next_u64() for _ in range(100)]
+    assert [int(x) for x in a] == b
+    assert np.array_equal(rng.u64(7, 3, np.arange(50, 100, dtype=np.uint64)), a[50:])
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return K.generate(K.CONFIGS["c1"])
+
+
+def test_deterministic(c1):
+    again = K.generate(K.CONFIGS["c1"])
+    assert np.array_equal(again.concept_bits, c1.concept_bits)
+    for r in range(c1.n_roles):
+        assert np.array_equal(again.col[r], c1.col[r])
+    assert np.array_equal(again.prop_vals, c1.prop_vals, equal_nan=True)
+
+
+def test_csr_and_transpose(c1):
+    n = c1.n
+    for r in range(c1.n_roles):
+        rp, col = c1.row_ptr[r].astype(np.int64), c1.col[r].astype(np.int64)
+        assert rp[0] == 0 and rp[-1] == col.size and np.all(np.diff(rp) >= 0)
+        assert col.max() < n
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        key = rows * n + col
+        assert np.all(np.diff(key) > 0), "rows sorted, no duplicate assertion"
+        ip, ic = c1.inv_row_ptr[r], c1.inv_col[r]
+        ikey = np.repeat(np.arange(n), np.diff(ip.astype(np.int64))) * n + ic.astype(np.int64)
+        assert np.all(np.diff(ikey) > 0)
+        # transpose of the transpose is the original
+        rp2, col2 = K.transpose_csr(ip, ic, n)
+        assert np.array_equal(rp2, c1.row_ptr[r]) and np.array_equal(col2, c1.col[r])
+
+
+def test_tails_zero_and_dag_closed(c1):
+    w = c1.n // 32
+    tail = c1.n % 32
+    if tail:
+        assert not (c1.concept_bits[:, w] >> np.uint32(tail)).any()
+    assert not c1.concept_bits[:, c1.w:].any()
+    parent = c1.meta["dag_parent"]
+    for j, p in enumerate(parent):
+        if p >= 0:
+            assert not (c1.concept_bits[j] & ~c1.concept_bits[p]).any(), "sub-concept members are in the parent"
+
+
+def test_degree_laws():
+    cfg = K.CONFIGS["c3"].scaled(200_000, n_roles=1)
+    deg, _ = K.draw_degrees(cfg, 0, cfg.n)
+    assert abs(deg.mean() - 6.0) < 0.05
+    cfg = K.CONFIGS["c2"].scaled(200_000, n_roles=1)
+    deg, meta = K.draw_degrees(cfg, 0, cfg.n)
+    assert abs(deg.mean() - 8.0) < 0.5 and deg.max() <= 10_000
+    s = meta["zipf_shift"]
+    pmf = K.shifted_zipf_pmf(2.1, s, 10_000)
+    assert abs((pmf * np.arange(10_001)).sum() - 8.0) < 1e-6
+
+
+def test_props_and_examples(c1):
+    v = c1.prop_vals
+    miss = np.isnan(v).mean()
+    assert 0.18 < miss < 0.22
+    assert np.nanmin(v) >= 0 and np.nanmax(v) <= 100
+    assert c1.pos_idx.size == 200 and c1.neg_idx.size == 200
+    assert not np.intersect1d(c1.pos_idx, c1.neg_idx).size
+
+
+def test_hypothesis_shapes(c1):
+    g = Hy.TreeGen(c1, 5)
+    r = rng.Rng(5, 1)
+    for _ in range(300):
+        L, D = Hy.random_shape(r, 40, 1, 8)
+        t = g._gen(r, L, D)
+        assert t.size() == L and t.height() == D
+        assert len(t.postfix()) == L
+    batch = Hy.batch_hyps(c1, 9, 0, 256)
+    assert all(1 <= len(p) <= 40 for p in batch)
+    for p in Hy.chain_hyps(c1, 4, 8):
+        assert P.from_postfix(p).height() == 6
+
+
+def test_text_roundtrip():
+    for s in ["(and A1 (not (some r2- (min 3 r0 (ge p1 2.5)))))", "(or TOP BOT)", "(exactly 2 r1 (le p0 -0.0))",
+              "(all r3 (eq p2 1e+30))"]:
+        assert P.to_text(P.parse(s)) == s
+    assert P.to_text(P.parse("(some r2-- A0)")) == "(some r2 A0)"
+    assert P.to_text(P.parse("(some r2--- A0)")) == "(some r2- A0)"
+    prog = P.compile_text("(min 3 r7- A9)")
+    assert P.fields(prog[-1]) == (P.ATLEAST, 1, 7, 3)
