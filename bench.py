@@ -1,0 +1,365 @@
+"""Benchmark: batched exact hypothesis evaluation on one GB300 (or N, one process per GPU).
+
+Workload (default): 1,000,000 individuals, 100 concepts, 16 roles with
+Poisson(6) out-degree (+ inverses), 8 data properties uniform [0, 1000],
+10,000 / 10,000 examples; every step evaluates and scores one batch of 4,096
+seeded hypotheses of postfix length uniform 1..40 and depth uniform 1..8 with
+shared sub-concepts at rate 0.3.  Inputs are synthetic (seeded generators),
+and larger than L2 (the KB alone is ~0.95 GB), so no L2 flush is needed.
+
+Prints ONE JSON line (rank 0):
+  value          hypotheses/s, device-timed, KB and plans resident in HBM
+                 (CUDA events on the launching stream around graph replays)
+  e2e            the same metric through hedl_score_batch from HOST programs
+                 (planning, plan upload, launch, D2H of the counts), wall clock
+  roofline       achieved = algorithmic bytes of a launch (the plan's byte
+                 model) / mean launch time, against the measured HBM peak
+  cpu_baseline   the oracle on the host cores on a bounded sample
+  plain          the one-launch-per-operation path on the same batches
+``--impl reference`` times the oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("batched exact evaluation: N=1,000,000 individuals, 100 concepts, 16 roles Poisson(6) + inverses, "
+            "8 props U[0,1000], 10k/10k examples; 4,096 hypotheses per step, length U[1,40], depth U[1,8], "
+            "shared sub-concepts 0.3")
+METRIC = "exact hypotheses/sec"
+UNIT = "hyp/s"
+BATCH = 4096
+
+
+def shard_batches(rank: int, world: int, warmup: int, steps: int):
+    """Batch indices this rank evaluates: warm-up ones, then timed ones; disjoint across ranks."""
+    per = warmup + steps
+    base = rank * per
+    return list(range(base, base + warmup)), list(range(base + warmup, base + per))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(workload_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel build."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        from paper_2412_00802_gb300 import build
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(workload_key)
+        if e and e.get("build_digest") == build._digest():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def make_workload(seed_kb: int = 3):
+    from synth import kb as K
+    return K.generate(K.CONFIGS["c3"])
+
+
+def make_batch(kb, idx: int, gen=None):
+    from synth import hyps
+    return hyps.batch_hyps(kb, 1003, idx, BATCH, gen=gen)
+
+
+def cpu_baseline(kb, progs, budget_s: float = 12.0):
+    """The oracle (as it stands) on all host cores over a bounded sample of the batch."""
+    import oracle
+    from synth import programs as P
+    okb = oracle.from_synth(kb)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    done, t0 = 0, time.perf_counter()
+    chunk = max(cores, 16)
+    while done < len(progs) and time.perf_counter() - t0 < budget_s:
+        sub = progs[done:done + chunk]
+        flat, offs = P.pack_batch(sub)
+        oracle.eval_batch(okb, flat, offs, threads=cores)
+        done += len(sub)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} hypotheses of a 4,096-hypothesis batch of this workload, "
+                      f"hypothesis-parallel on {cores} host threads ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    kb = make_workload()
+    from synth import hyps
+    gen = hyps.TreeGen(kb, 1003, share=0.3)
+    import oracle
+    from synth import programs as P
+    okb = oracle.from_synth(kb)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    per_step = max(cores, 16)
+    steps = []
+    for s in range(args.warmup + args.steps):
+        progs = make_batch(kb, s, gen)[:per_step]
+        flat, offs = P.pack_batch(progs)
+        t0 = time.perf_counter()
+        oracle.eval_batch(okb, flat, offs, threads=cores)
+        steps.append(time.perf_counter() - t0)
+    timed = steps[args.warmup:]
+    value = per_step * len(timed) / sum(timed)
+    sample = f"{per_step} hypotheses per step (of each 4,096-hypothesis batch), {cores} host threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(timed), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2412_00802_gb300 as H
+    from paper_2412_00802_gb300 import build
+    from synth import hyps, programs as P
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    build.build()
+    kb = make_workload()
+    dkb = H.DeviceKB.from_synth(kb, device=f"cuda:{local_rank}")
+    gen = hyps.TreeGen(kb, 1003, share=0.3)
+    warm_ids, timed_ids = shard_batches(rank, world, args.warmup, args.steps)
+    ids = warm_ids + timed_ids
+    batches = {i: P.pack_batch(make_batch(kb, i, gen)) for i in ids}
+
+    stream = torch.cuda.current_stream(dev)
+    # ---- plan every batch (host), give each its own workspace, upload once
+    plans, infos, wss = {}, {}, {}
+    plan_s = []
+    for i in ids:
+        t0 = time.perf_counter()
+        plans[i] = H.hedl_plan_batch(dkb.handle, *batches[i], args.flags)
+        plan_s.append(time.perf_counter() - t0)
+        infos[i] = H.hedl_plan_info_get(plans[i])
+        wss[i] = torch.empty(infos[i]["workspace_bytes"], dtype=torch.uint8, device=dev)
+    counts = torch.zeros((BATCH, 4), dtype=torch.int32, device=dev)
+    for i in ids:
+        H.hedl_plan_execute(dkb.handle, plans[i], counts, None, wss[i])
+    H.hedl_sync_status(dkb.handle)
+    for i in warm_ids:
+        H.hedl_plan_replay(dkb.handle, plans[i], counts, None, wss[i])
+    H.hedl_sync_status(dkb.handle)
+
+    # ---- timed region: device-resident replays, events per launch on the launching stream
+    dist = world > 1
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in timed_ids]
+    with ClockSampler(local_rank) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for (a, b), i in zip(ev, timed_ids):
+            a.record(stream)
+            H.hedl_plan_replay(dkb.handle, plans[i], counts, None, wss[i])
+            b.record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    H.hedl_sync_status(dkb.handle)
+    elapsed = t_all0.elapsed_time(t_all1) / 1000.0
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+        torch.distributed.barrier()
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    value = world * len(timed_ids) * BATCH / elapsed
+
+    # ---- roofline of the interpreter launch
+    peak, peak_kind = measured_peaks()
+    model = [infos[i]["model_bytes"] for i in timed_ids]
+    achieved = statistics.mean(m / (t / 1000.0) for m, t in zip(model, launch_ms)) / 1e9
+    traffic = traffic_for("c3_batch")
+
+    # ---- end to end through the public C ABI from host programs
+    e2e_ids = timed_ids[: min(len(timed_ids), 5)]
+    pinned = torch.empty((BATCH, 4), dtype=torch.int32, pin_memory=True)
+    e2e_ws = torch.empty(max(infos[i]["workspace_bytes"] for i in ids), dtype=torch.uint8, device=dev)
+    flat, offs = batches[e2e_ids[0]]
+    H.hedl_score_batch(dkb.handle, flat, offs, counts, e2e_ws, args.flags)   # warm the path
+    torch.cuda.synchronize()
+    h2d = []
+    t0 = time.perf_counter()
+    for i in e2e_ids:
+        flat, offs = batches[i]
+        H.hedl_score_batch(dkb.handle, flat, offs, counts, e2e_ws, args.flags)
+        pinned.copy_(counts, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d.append(infos[i]["workspace_bytes"] - infos[i]["n_slots"] * 4 * dkb.wp)
+    e2e_s = time.perf_counter() - t0
+    H.hedl_sync_status(dkb.handle)
+    e2e = {"value": len(e2e_ids) * BATCH / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(statistics.mean(h2d)), "d2h_bytes_per_step": BATCH * 16,
+           "note": "hedl_score_batch from host programs: host planning + plan upload + launch + counts to host"}
+
+    # ---- plain path (one launch per operation) on the first timed batch, and sharing off
+    plain = None
+    if not args.no_plain:
+        i = timed_ids[0]
+        pplan = H.hedl_plan_batch(dkb.handle, *batches[i], H.HEDL_PLAIN)
+        pws = torch.empty(H.hedl_plan_info_get(pplan)["workspace_bytes"], dtype=torch.uint8, device=dev)
+        pcounts = torch.zeros((BATCH, 4), dtype=torch.int32, device=dev)
+        H.hedl_plan_execute(dkb.handle, pplan, pcounts, None, pws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        H.hedl_plan_execute(dkb.handle, pplan, pcounts, None, pws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        H.hedl_sync_status(dkb.handle)
+        same = bool(torch.equal(pcounts, counts)) if i == e2e_ids[-1] else None
+        plain = {"value": BATCH / (a.elapsed_time(b) / 1000.0), "unit": UNIT}
+        # verify the batched counts of that batch against the plain path
+        H.hedl_plan_replay(dkb.handle, plans[i], counts, None, wss[i])
+        torch.cuda.synchronize()
+        plain["counts_identical"] = bool(torch.equal(pcounts, counts))
+    info0 = infos[timed_ids[0]]
+    ncse = H.hedl_plan_info_get(H.hedl_plan_batch(dkb.handle, *batches[timed_ids[0]], H.HEDL_NO_CSE))
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline(kb, make_batch(kb, timed_ids[0], gen))
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_ids),
+        "warmup": len(warm_ids), "ms_per_step": 1000.0 * elapsed / len(timed_ids), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": BATCH, "l2": "inputs larger than L2 (KB ~0.95 GB + workspaces)",
+                   "parallelism": f"replicas{world}", "flags": args.flags,
+                   "tuning": H.hedl_tuning_get(dkb.handle)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "exec_kernel (persistent segment interpreter)",
+                     "model_bytes_per_launch": statistics.mean(model),
+                     "launch_ms": statistics.mean(launch_ms)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": 2 * len(timed_ids),
+        "plain": plain,
+        "batched_vs_plain": (value / world / plain["value"]) if plain else None,
+        "plan": {"host_ms_per_batch": 1000 * statistics.mean(plan_s), "segments": info0["n_segments"],
+                 "slots": info0["n_slots"], "levels": info0["n_levels"], "items": info0["n_items"],
+                 "role_ops": info0["n_role_ops"], "role_ops_without_sharing": ncse["n_role_ops"],
+                 "model_bytes": info0["model_bytes"], "model_bytes_without_sharing": ncse["model_bytes"]},
+        "effective_frac_unshared": value / world * (ncse["model_bytes"] / BATCH) / 1e9 / peak,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--flags", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        td.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * hedl.h -- C ABI of the GB300 hypothesis-evaluation library.
+ *
+ * The library evaluates ALCQI(D) concepts ("hypotheses") over every
+ * individual of a knowledge base held in GPU memory, and scores each instance
+ * set against positive and negative example sets.  It follows the paper's
+ * statement of the problem (HT-HEDL, arXiv 2412.00802):
+ *   - the knowledge base lives on the device for the whole session and is
+ *     never copied per hypothesis (Section III-A);
+ *   - a hypothesis is one contiguous array of DL operations (Section IV);
+ *   - each hypothesis yields its covered positive and negative examples
+ *     (Section IV, Algorithm 15), copied back once per batch (Section III-A).
+ *
+ * Conventions for every call:
+ *   - Device pointers are CUDA global-memory addresses on the current device;
+ *     host pointers are ordinary process memory.  Each parameter says which.
+ *   - Device arrays passed in are BORROWED: the caller owns them, they must
+ *     stay allocated and unmodified while a handle that references them is
+ *     alive, and the library never frees them.  Handles (hedl_kb, hedl_plan)
+ *     are owned by the library and released by their *_free call.
+ *   - Work is enqueued on the given stream (NULL = the legacy default
+ *     stream) and the call returns without waiting, unless the entry point
+ *     says it synchronizes.  Programs are validated on the host before
+ *     anything is launched, so a rejected call launches nothing.
+ *   - Return value: HEDL_OK (0) or a negative hedl_status.  The calling
+ *     thread's hedl_last_error() then describes the failure.  Failures found
+ *     on the device (a bounded wait that gave up) are reported by the next
+ *     hedl_sync_status() on the handle.
+ *
+ * Bitsets: a set of individuals is uint32 words, bit i of word w standing
+ * for individual 32*w + i (least significant bit first).  A row has
+ * hedl_row_words(n) words: ceil(n/32) rounded up to a multiple of 4, so every
+ * row starts on a 16-byte boundary.  Bits of individuals >= n and padding
+ * words are zero in every input and every output.
+ */
+#ifndef HEDL_H
+#define HEDL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t. */
+typedef struct CUstream_st *hedl_stream;
+
+typedef enum {
+    HEDL_OK = 0,
+    HEDL_ERR_INVALID_ARG = -1,          /* a NULL / out-of-range argument */
+    HEDL_ERR_BAD_PROGRAM = -2,          /* a program failed validation */
+    HEDL_ERR_WORKSPACE_TOO_SMALL = -3,  /* the workspace is smaller than required */
+    HEDL_ERR_CUDA = -4,                 /* a CUDA runtime call failed */
+    HEDL_ERR_TIMEOUT = -5,              /* a bounded device wait gave up */
+    HEDL_ERR_BAD_KB = -6,               /* the knowledge base failed validation */
+    HEDL_ERR_NO_EXAMPLES = -7,          /* scoring before hedl_examples_set */
+    HEDL_ERR_OOM = -8                   /* host or device allocation failed */
+} hedl_status;
+
+/*
+ * Program format: postfix, one uint64 per instruction.
+ *   bits  0..7   op (hedl_op)
+ *   bits  8..15  flags: bit 0 = read the role inverted (r^-); other bits ignored
+ *   bits 16..31  a: concept id (ATOM), role id (role ops), property id (data ops)
+ *   bits 32..63  b: n for ATLEAST / ATMOST / EXACTLY; the IEEE float32 bit
+ *                pattern of the threshold for DGE / DLE / DEQ; ignored otherwise
+ * AND and OR pop two operands, NOT and the role restrictions one, the rest are
+ * leaves.  A valid program is non-empty, names existing ids, never pops an
+ * empty stack, never holds more than HEDL_MAX_STACK operands, and leaves
+ * exactly one.
+ *
+ * Semantics (closed world, Section III-A: what is not asserted is false):
+ *   ATOM c        members of concept c
+ *   TOP, BOT      every individual / no individual
+ *   NOT X         the individuals not in X                      (Algs 1-2)
+ *   AND, OR       intersection, union                            (Algs 1-2)
+ *   EXISTS r X    a with some r-successor in X                   (Algs 3-4)
+ *   FORALL r X    a all of whose r-successors are in X; an
+ *                 individual without successors belongs          (Algs 5-6)
+ *   ATLEAST r n X a with >= n distinct r-successors in X
+ *   ATMOST r n X  a with <= n of them (zero included)
+ *   EXACTLY r n X a with exactly n of them                       (Algs 7-8)
+ *   r^-           subject and object swapped (Section III-B), read from
+ *                 the inverse CSR
+ *   DGE/DLE/DEQ   a whose value of property p is >= / <= / == t (float32
+ *                 compares; a missing value, NaN, satisfies none) (Algs 9-10)
+ */
+typedef enum {
+    HEDL_OP_ATOM = 1, HEDL_OP_TOP = 2, HEDL_OP_BOT = 3, HEDL_OP_NOT = 4,
+    HEDL_OP_AND = 5, HEDL_OP_OR = 6,
+    HEDL_OP_EXISTS = 7, HEDL_OP_FORALL = 8, HEDL_OP_ATLEAST = 9, HEDL_OP_ATMOST = 10,
+    HEDL_OP_EXACTLY = 11,
+    HEDL_OP_DGE = 12, HEDL_OP_DLE = 13, HEDL_OP_DEQ = 14
+} hedl_op;
+
+#define HEDL_FLAG_INVERSE 1u
+#define HEDL_MAX_STACK 64
+
+/* Words per bitset row for n individuals: ceil(n/32) rounded up to 4. */
+uint32_t hedl_row_words(uint32_t n_indiv);
+
+/* ------------------------------------------------------------------ KB */
+
+/* One role's assertions as CSR (rows = subjects, Section III-A's 2-column
+ * role matrix grouped by subject). Device arrays: row_ptr uint32[n_indiv+1]
+ * with row_ptr[0] = 0 and row_ptr[n_indiv] = n_edges; col uint32[n_edges],
+ * each row strictly increasing (a set of distinct objects < n_indiv). */
+typedef struct {
+    const uint32_t *row_ptr;
+    const uint32_t *col;
+    uint32_t n_edges;          /* < 2^31 */
+} hedl_csr;
+
+typedef struct {
+    uint32_t n_indiv;                  /* individuals, >= 1 */
+    uint32_t n_concepts;
+    const uint32_t *concept_bits;      /* device, [n_concepts][hedl_row_words(n)] */
+    uint32_t n_roles;
+    const hedl_csr *roles;             /* HOST array [n_roles] of device CSRs */
+    const hedl_csr *inv_roles;         /* HOST array [n_roles]: the transposes */
+    uint32_t n_props;
+    const float *prop_vals;            /* device, [n_props][prop_stride], NaN = missing */
+    uint64_t prop_stride;              /* floats between property rows, >= n_indiv */
+} hedl_kb_desc;
+
+typedef struct hedl_kb hedl_kb;
+
+#define HEDL_KB_NO_VALIDATE 1u   /* skip the device-side structural checks */
+
+/* Register a knowledge base resident on the device (Section III-A).
+ * Borrows every device array of d (see the conventions above); copies the
+ * small host arrays roles / inv_roles.  Unless HEDL_KB_NO_VALIDATE, checks on
+ * the device that concept rows have zero tails, that each CSR is well formed
+ * (monotone row_ptr, rows strictly increasing, ids < n) and that each inverse
+ * CSR is exactly the transpose of its forward CSR; a failed check returns
+ * HEDL_ERR_BAD_KB and no handle.  SYNCHRONIZES the stream.
+ * *out receives the handle; release it with hedl_kb_free. */
+int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb **out);
+
+/* A planning-only handle: reads only the sizes in d (n_indiv, the counts and
+ * each role's n_edges; pointers may be NULL) and makes no CUDA call, so it
+ * works on a host without a GPU.  hedl_validate, hedl_plan_batch and
+ * hedl_plan_info_get accept it; every call that would launch work returns
+ * HEDL_ERR_INVALID_ARG.  Release it with hedl_kb_free. */
+int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out);
+
+/* Release a handle (waits for the device to go idle first).  NULL is fine. */
+void hedl_kb_free(hedl_kb *kb);
+
+/* Set the positive and negative examples (Section IV's examples matrix) as
+ * two borrowed device bitsets of hedl_row_words(n) words each.  Computes |P|
+ * and |N| on the device.  SYNCHRONIZES the stream.  Until it is called,
+ * scoring entry points return HEDL_ERR_NO_EXAMPLES. */
+int hedl_examples_set(hedl_kb *kb, const uint32_t *pos_bits, const uint32_t *neg_bits, hedl_stream s);
+
+/* |P| and |N| as cached by hedl_examples_set (host values). */
+int hedl_examples_counts(const hedl_kb *kb, uint32_t *n_pos, uint32_t *n_neg);
+
+/* Host-only validation of one program against the KB's ids (no GPU work).
+ * Returns HEDL_OK or HEDL_ERR_BAD_PROGRAM (reason in hedl_last_error). */
+int hedl_validate(const hedl_kb *kb, const uint64_t *prog, uint32_t len);
+
+/* ------------------------------------------------------------------ plans */
+
+/* A batch of programs compiled on the host into a device work queue: the
+ * programs' expression DAG with common sub-concepts shared across the batch
+ * (hash-consing), cut into segments at role restrictions (a role restriction
+ * needs its filler over all individuals before any tile of its result), each
+ * segment split into tiles of individuals.  The paper builds one evaluation
+ * plan per hypothesis on the CPU (Section IV; multi-threaded, Section V). */
+typedef struct hedl_plan hedl_plan;
+
+#define HEDL_NO_CSE     1u   /* no sharing of common sub-concepts */
+#define HEDL_NO_GRAPH   2u   /* launch directly instead of replaying a CUDA graph */
+#define HEDL_PLAIN      4u   /* one launch per operation per hypothesis */
+#define HEDL_LEVELS     8u   /* one launch per dependency level, no device waits */
+#define HEDL_TEST_UNSAT_DEP 0x100u  /* TEST HOOK: add a dependency nothing
+                                        satisfies, so the bounded device wait
+                                        gives up (the call then reports
+                                        HEDL_ERR_TIMEOUT) */
+
+typedef struct {
+    uint32_t n_hyps;
+    uint32_t n_nodes;        /* distinct DAG nodes after sharing */
+    uint32_t n_segments;
+    uint32_t n_slots;        /* materialized intermediate bitsets */
+    uint32_t n_levels;
+    uint32_t n_items;        /* (segment, tile) work items */
+    uint32_t tile_words;
+    uint32_t n_role_ops;     /* role restrictions evaluated (after sharing) */
+    uint32_t n_data_ops;
+    uint32_t n_atom_loads;
+    uint64_t total_insns;    /* instructions in the input programs */
+    uint64_t workspace_bytes;
+    uint64_t model_bytes;    /* algorithmic bytes of the plan (one pass) */
+} hedl_plan_info;
+
+/* Compile H programs (HOST arrays: progs uint64[offs[H]], offs uint32[H+1],
+ * program h = progs[offs[h] .. offs[h+1])).  Rejects the batch with
+ * HEDL_ERR_BAD_PROGRAM naming the first bad program.  Host-only; the plan
+ * keeps no pointer to the inputs. */
+int hedl_plan_batch(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+                    unsigned flags, hedl_plan **out);
+int hedl_plan_info_get(const hedl_plan *p, hedl_plan_info *info);
+void hedl_plan_free(hedl_plan *p);
+
+/* Execute a plan.  counts: device uint32[H][4] receiving (TP, FP, FN, TN) per
+ * program (Algorithm 15 and its complements), or NULL; out_bits: device
+ * uint32[H][hedl_row_words(n)] receiving each instance set, or NULL (not both
+ * NULL).  ws: device workspace of ws_bytes >= workspace_bytes of the plan
+ * info, 256-byte aligned, used exclusively by this call until it completes.
+ * The plan image is copied host-to-device on s.  Asynchronous. */
+int hedl_plan_execute(hedl_kb *kb, const hedl_plan *p, uint32_t *counts, uint32_t *out_bits,
+                      void *ws, size_t ws_bytes, hedl_stream s);
+
+/* Run again a plan whose image an earlier hedl_plan_execute on the same ws
+ * already put there (ws not reused since): only the plan's counters are
+ * reset, nothing is copied from the host.  Same arguments as
+ * hedl_plan_execute.  Asynchronous. */
+int hedl_plan_replay(hedl_kb *kb, const hedl_plan *p, uint32_t *counts, uint32_t *out_bits,
+                     void *ws, size_t ws_bytes, hedl_stream s);
+
+/* ------------------------------------------------------------------ one-shot calls */
+
+/* Workspace bytes hedl_score_batch / hedl_eval_concept need for these
+ * programs and flags (plans them; the plan is cached on the handle so the
+ * following call with the same programs does not plan again). */
+int hedl_workspace_size(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+                        unsigned flags, size_t *bytes);
+
+/* Evaluate and score H programs (HOST progs/offs as in hedl_plan_batch) into
+ * device counts uint32[H][4] = (TP, FP, FN, TN).  Plans (or reuses the cached
+ * plan), copies the plan image to ws and launches.  Asynchronous. */
+int hedl_score_batch(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+                     uint32_t *counts, void *ws, size_t ws_bytes, unsigned flags, hedl_stream s);
+
+/* Evaluate one program (HOST prog uint64[len]) into the device bitset
+ * out_bits (hedl_row_words(n) words).  Workspace as for hedl_score_batch with
+ * H = 1.  Asynchronous. */
+int hedl_eval_concept(hedl_kb *kb, const uint64_t *prog, uint32_t len, uint32_t *out_bits,
+                      void *ws, size_t ws_bytes, unsigned flags, hedl_stream s);
+
+/* Wait for s, then report (and clear) the first device-side failure recorded
+ * by work launched on this handle since the last call: HEDL_OK,
+ * HEDL_ERR_TIMEOUT, or HEDL_ERR_CUDA for an asynchronous CUDA error. */
+int hedl_sync_status(hedl_kb *kb, hedl_stream s);
+
+/* ------------------------------------------------------------------ tuning */
+
+typedef struct {
+    uint32_t warps_per_cta;    /* 4, 8 or 16 */
+    uint32_t words_per_lane;   /* 1 or 4: bitset words a lane holds per pass */
+    uint32_t rounds;           /* warp passes per work item (tile = warps*32*words_per_lane*rounds words) */
+    uint32_t ctas_per_sm;      /* 0 = as many as fit */
+    uint32_t wait_timeout_ms;  /* bound of every device-side dependency wait */
+} hedl_tuning;
+
+int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t);
+/* Set the launch shape used by later plans and executions on this handle;
+ * rejects unsupported values with HEDL_ERR_INVALID_ARG. */
+int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t);
+
+/* Description of the calling thread's last failure ("" if none). */
+const char *hedl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEDL_H */

@@ -1,0 +1,198 @@
+// Device building blocks shared by the batched interpreter (exec.cu) and the
+// one-operation-per-launch path (plain.cu).
+//
+// Layout: a set of individuals is a row of uint32 words, bit i of word w =
+// individual 32*w + i.  A warp works on 32*WPL consecutive words; lane l holds
+// words wb + l*WPL .. wb + l*WPL + WPL-1 (so WPL = 4 gives 128-bit loads).
+#pragma once
+
+#include <cstdint>
+
+#include "hedl_internal.h"
+
+namespace hedl {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t tail_mask(uint32_t w, uint32_t n_words, uint32_t n) {
+    if (w + 1 < n_words) return FULL;
+    if (w + 1 == n_words) {
+        uint32_t r = n & 31u;
+        return r ? ((1u << r) - 1u) : FULL;
+    }
+    return 0u;
+}
+
+// bits lo..hi-1 set (0 <= lo <= hi <= 32)
+__device__ __forceinline__ uint32_t range_mask(uint32_t lo, uint32_t hi) {
+    uint32_t up = hi >= 32 ? FULL : ((1u << hi) - 1u);
+    uint32_t dn = lo >= 32 ? FULL : ((1u << lo) - 1u);
+    return up & ~dn;
+}
+
+template <int WPL>
+__device__ __forceinline__ void load_row_ro(const uint32_t *__restrict__ row, uint32_t wb, uint32_t lane,
+                                            uint32_t wp, uint32_t (&v)[WPL]) {
+    uint32_t w0 = wb + lane * WPL;
+    if constexpr (WPL == 4) {
+        if (w0 < wp) {
+            uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + w0));
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        } else {
+            v[0] = v[1] = v[2] = v[3] = 0u;
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) v[s] = (w0 + s < wp) ? __ldg(row + w0 + s) : 0u;
+    }
+}
+
+// Rows written earlier in the same kernel (slots) are read with plain loads,
+// never through the read-only path.
+template <int WPL>
+__device__ __forceinline__ void load_row_rw(const uint32_t *row, uint32_t wb, uint32_t lane, uint32_t wp,
+                                            uint32_t (&v)[WPL]) {
+    uint32_t w0 = wb + lane * WPL;
+    if constexpr (WPL == 4) {
+        if (w0 < wp) {
+            uint4 q = *reinterpret_cast<const uint4 *>(row + w0);
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        } else {
+            v[0] = v[1] = v[2] = v[3] = 0u;
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) v[s] = (w0 + s < wp) ? row[w0 + s] : 0u;
+    }
+}
+
+template <int WPL>
+__device__ __forceinline__ void store_row(uint32_t *row, uint32_t wb, uint32_t lane, uint32_t wp,
+                                          const uint32_t (&v)[WPL]) {
+    uint32_t w0 = wb + lane * WPL;
+    if constexpr (WPL == 4) {
+        if (w0 < wp) *reinterpret_cast<uint4 *>(row + w0) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s)
+            if (w0 + s < wp) row[w0 + s] = v[s];
+    }
+}
+
+// Does count `cnt` decide the restriction?  Returns the threshold at which the
+// answer can no longer change (the walk over a row may stop there).
+__device__ __forceinline__ uint64_t decide_cap(uint32_t kind, uint32_t n) {
+    switch (kind) {
+    case HEDL_OP_EXISTS: return 1;             // one C-successor
+    case HEDL_OP_FORALL: return 1;             // one successor outside C
+    case HEDL_OP_ATLEAST: return n;
+    default: return (uint64_t)n + 1;           // ATMOST / EXACTLY: n+1 of them
+    }
+}
+
+__device__ __forceinline__ bool role_pred(uint32_t kind, uint32_t cnt, uint32_t n) {
+    switch (kind) {
+    case HEDL_OP_EXISTS: return cnt >= 1;
+    case HEDL_OP_FORALL: return cnt == 0;      // cnt counts successors NOT in C
+    case HEDL_OP_ATLEAST: return cnt >= n;
+    case HEDL_OP_ATMOST: return cnt <= n;
+    default: return cnt == n;                  // EXACTLY
+    }
+}
+
+// Role restriction over the warp's 32*WPL words (Algorithms 3-8 of the
+// paper, recast): for each word, the warp streams the CSR edge range of the
+// word's 32 individuals in coalesced chunks of 32 edges; lane e tests the
+// filler bit of edge e's object, a ballot packs the 32 tests, and lane i
+// counts the set bits that fall inside its own row.  Counts stay in registers
+// (no atomics, no counter matrix); the walk stops as soon as every lane's
+// answer is decided.  FORALL counts successors outside the filler.
+template <int WPL>
+__device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *filler, uint32_t kind, uint32_t n_arg,
+                                           uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
+                                           uint32_t (&v)[WPL]) {
+    const uint32_t neg = kind == HEDL_OP_FORALL ? 1u : 0u;
+    const uint64_t cap = decide_cap(kind, n_arg);
+    const uint32_t *__restrict__ rp = g.rp;
+    const uint32_t *__restrict__ col = g.col;
+#pragma unroll 1
+    for (int j = 0; j < 32; ++j) {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) {
+            const uint32_t w = wb + (uint32_t)j * WPL + s;
+            uint32_t word = 0;
+            if (w < n_words) {
+                const uint32_t i = w * 32u + lane;
+                const bool valid = i < n;
+                uint32_t lo = 0, hi = 0;
+                if (valid) {
+                    lo = __ldg(rp + i);
+                    hi = __ldg(rp + i + 1);
+                }
+                const uint32_t nv = min(32u, n - w * 32u);
+                const uint32_t e0 = __shfl_sync(FULL, lo, 0);
+                const uint32_t e1 = __shfl_sync(FULL, hi, nv - 1);
+                uint32_t cnt = 0;
+                if (cap > 0) {
+#pragma unroll 1
+                    for (uint32_t k0 = e0; k0 < e1; k0 += 32u) {
+                        const uint32_t k = k0 + lane;
+                        uint32_t hit = 0;
+                        if (k < e1) {
+                            const uint32_t b = __ldg(col + k);
+                            hit = ((filler[b >> 5] >> (b & 31u)) & 1u) ^ neg;
+                        }
+                        const uint32_t m = __ballot_sync(FULL, hit);
+                        const uint32_t a0 = lo > k0 ? lo - k0 : 0u;
+                        const uint32_t a1 = hi > k0 ? min(hi - k0, 32u) : 0u;
+                        if (a0 < a1) cnt += __popc(m & range_mask(a0, a1));
+                        const bool done = !valid || hi <= k0 + 32u || (uint64_t)cnt >= cap;
+                        if (__all_sync(FULL, done)) break;
+                    }
+                }
+                word = __ballot_sync(FULL, valid && role_pred(kind, cnt, n_arg));
+            }
+            if (lane == (uint32_t)j) v[s] = word;
+        }
+    }
+}
+
+// Numeric data-range restriction (Algorithms 9-10): one float compare per
+// individual, a ballot packs 32 of them into a word.  NaN (missing) compares
+// false.
+template <int WPL>
+__device__ __forceinline__ void data_words(const float *__restrict__ vals, uint32_t cmp, float t, uint32_t n,
+                                           uint32_t n_words, uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) {
+            const uint32_t w = wb + (uint32_t)j * WPL + s;
+            uint32_t word = 0;
+            if (w < n_words) {
+                const uint32_t i = w * 32u + lane;
+                bool p = false;
+                if (i < n) {
+                    const float x = __ldg(vals + i);
+                    p = cmp == HEDL_OP_DGE ? (x >= t) : cmp == HEDL_OP_DLE ? (x <= t) : (x == t);
+                }
+                word = __ballot_sync(FULL, p);
+            }
+            if (lane == (uint32_t)j) v[s] = word;
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+}  // namespace hedl

@@ -1,0 +1,298 @@
+// Batched evaluation: one persistent interpreter kernel over a work queue of
+// (segment, tile) items (see plan.cpp for how a batch becomes segments).
+//
+// Each CTA pops an item, waits (bounded) until every segment it reads is
+// complete, then its warps run the segment's program over the tile: a stack
+// machine whose values are bitset words (one register set per lane, deeper
+// stack entries in shared memory), whose leaves load concept rows / slots,
+// evaluate data ranges by ballot, or evaluate role restrictions by the
+// warp-cooperative CSR walk.  A segment's result is written to its slot, or,
+// for a hypothesis root, reduced against the example sets by popcount (the
+// paper's coverage count, Algorithm 15) with one atomic per warp.
+//
+// Waits never spin unbounded: each gives up after the plan's timeout, sets an
+// abort flag and an error bit, and every CTA then leaves the kernel.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace hedl {
+
+namespace {
+
+struct ExecArgs {
+    KBView kb;
+    uint8_t *ws;
+    uint32_t *counts;     // [H][4] or null
+    uint32_t *out_bits;   // [H][wp] or null
+    uint32_t item_begin, item_end;
+    uint32_t use_queue;   // 1: dynamic queue with dependency waits; 0: static striding, no waits
+};
+
+template <int NW, int WPL>
+struct Smem {
+    uint32_t stk[NW][STACK_MAX][WPL][32];
+    uint32_t item;
+    uint32_t ok;
+};
+
+__device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_groups, uint32_t item) {
+    uint32_t lo = 0, hi = n_groups;  // last group with item_begin <= item
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (groups[mid].item_begin <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int NW, int WPL>
+__device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg, uint32_t tile,
+                         Smem<NW, WPL> &sm, uint32_t *slots, uint32_t *acc) {
+    const KBView &kb = A.kb;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const DInsn *code = reinterpret_cast<const DInsn *>(A.ws + hd.off_code) + seg.code_off;
+    const uint32_t rounds = hd.tile_words / (NW * 32u * WPL);
+    uint32_t tp = 0, fp = 0;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t wb = tile * hd.tile_words + (r * NW + warp) * 32u * WPL;
+        if (wb >= kb.wp) break;
+        uint32_t top[WPL];
+        uint32_t sp = 0;  // values on the stack, top included
+        for (uint32_t pc = 0; pc < seg.code_len; ++pc) {
+            const DInsn d = code[pc];
+            const uint32_t op = d.op & 0xFFu;
+            if (op == D_NOT) {
+#pragma unroll
+                for (int s = 0; s < WPL; ++s)
+                    top[s] = ~top[s] & tail_mask(wb + lane * WPL + s, kb.w, kb.n);
+                continue;
+            }
+            if (op == D_AND || op == D_OR) {
+                sp -= 1;
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) {
+                    uint32_t o = sm.stk[warp][sp - 1][s][lane];
+                    top[s] = op == D_AND ? (top[s] & o) : (top[s] | o);
+                }
+                continue;
+            }
+            // a leaf: spill the current top, compute the new one
+            if (sp > 0) {
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) sm.stk[warp][sp - 1][s][lane] = top[s];
+            }
+            sp += 1;
+            switch (op) {
+            case D_ATOM:
+                load_row_ro<WPL>(kb.concepts + (uint64_t)d.a * kb.wp, wb, lane, kb.wp, top);
+                break;
+            case D_SLOT:
+                load_row_rw<WPL>(slots + (uint64_t)d.ref * kb.wp, wb, lane, kb.wp, top);
+                break;
+            case D_TOP:
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) top[s] = tail_mask(wb + lane * WPL + s, kb.w, kb.n);
+                break;
+            case D_BOT:
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) top[s] = 0u;
+                break;
+            case D_DATA:
+                data_words<WPL>(kb.props + (uint64_t)d.a * kb.prop_stride, (d.op >> 16) & 0xFFu,
+                                __uint_as_float(d.b), kb.n, kb.w, wb, lane, top);
+                break;
+            default: {  // D_ROLE
+                const uint32_t inv = (d.op >> 8) & 1u;
+                const DevCSR g = kb.csr[2u * d.a + inv];
+                const uint32_t *filler = (d.ref & REF_SLOT) ? slots + (uint64_t)(d.ref & ~REF_SLOT) * kb.wp
+                                                            : kb.concepts + (uint64_t)d.ref * kb.wp;
+                role_words<WPL>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                break;
+            }
+            }
+        }
+        if (seg.out_slot != NO_SLOT) store_row<WPL>(slots + (uint64_t)seg.out_slot * kb.wp, wb, lane, kb.wp, top);
+        if (seg.hyp != NO_HYP) {
+            if (A.out_bits) store_row<WPL>(A.out_bits + (uint64_t)seg.hyp * kb.wp, wb, lane, kb.wp, top);
+            if (A.counts) {
+                uint32_t pv[WPL], nv[WPL];
+                load_row_ro<WPL>(kb.pos, wb, lane, kb.wp, pv);
+                load_row_ro<WPL>(kb.neg, wb, lane, kb.wp, nv);
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) {
+                    tp += __popc(top[s] & pv[s]);
+                    fp += __popc(top[s] & nv[s]);
+                }
+            }
+        }
+    }
+    if (seg.hyp != NO_HYP && A.counts) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tp += __shfl_xor_sync(FULL, tp, o);
+            fp += __shfl_xor_sync(FULL, fp, o);
+        }
+        if (lane == 0) {
+            if (tp) atomicAdd(acc + 2u * seg.hyp, tp);
+            if (fp) atomicAdd(acc + 2u * seg.hyp + 1u, fp);
+        }
+    }
+}
+
+// Bounded wait for every producer segment of `seg` (thread 0 only).
+__device__ bool wait_deps(const PlanHeader &hd, const uint32_t *deps, const Seg &seg, uint32_t *done,
+                          Counters *ctr) {
+    for (uint32_t k = 0; k < seg.dep_cnt; ++k) {
+        const uint32_t *flag = done + deps[seg.dep_off + k];
+        if (ld_acquire(flag) >= hd.n_tiles) continue;
+        const uint64_t t0 = global_ns();
+        uint64_t spins = 0;
+        const uint64_t max_spins = hd.timeout_ns / 16 + 1000000ull;
+        while (ld_acquire(flag) < hd.n_tiles) {
+            if (*(volatile uint32_t *)&ctr->abort) return false;
+            if (global_ns() - t0 > hd.timeout_ns || ++spins > max_spins) {
+                atomicOr(&ctr->err, ST_TIMEOUT);
+                atomicExch(&ctr->abort, 1u);
+                return false;
+            }
+            __nanosleep(128);
+        }
+    }
+    return true;
+}
+
+template <int NW, int WPL>
+__global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
+    const PlanHeader hd = *reinterpret_cast<const PlanHeader *>(A.ws);
+    const Seg *segs = reinterpret_cast<const Seg *>(A.ws + hd.off_segs);
+    const Group *groups = reinterpret_cast<const Group *>(A.ws + hd.off_groups);
+    const uint32_t *gsegs = reinterpret_cast<const uint32_t *>(A.ws + hd.off_gsegs);
+    const uint32_t *deps = reinterpret_cast<const uint32_t *>(A.ws + hd.off_deps);
+    Counters *ctr = reinterpret_cast<Counters *>(A.ws + hd.off_ctr);
+    uint32_t *done = reinterpret_cast<uint32_t *>(ctr + 1);
+    uint32_t *acc = done + hd.n_segs + 1;
+    uint32_t *slots = reinterpret_cast<uint32_t *>(A.ws + hd.off_slots);
+
+    uint32_t stride_next = A.item_begin + blockIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t it;
+            if (A.use_queue) {
+                it = *(volatile uint32_t *)&ctr->abort ? A.item_end : A.item_begin + atomicAdd(&ctr->head, 1u);
+            } else {
+                it = stride_next;
+            }
+            sm.item = it;
+        }
+        __syncthreads();
+        const uint32_t item = sm.item;
+        stride_next += gridDim.x;
+        if (item >= A.item_end) break;
+        const uint32_t g = find_group(groups, hd.n_groups, item);
+        const Group grp = groups[g];
+        const uint32_t local = item - grp.item_begin;
+        const uint32_t tile = local / grp.n_segs;
+        const uint32_t sidx = gsegs[grp.seg_begin + local % grp.n_segs];
+        const Seg seg = segs[sidx];
+        if (A.use_queue) {
+            if (threadIdx.x == 0) sm.ok = wait_deps(hd, deps, seg, done, ctr) ? 1u : 0u;
+            __syncthreads();
+            if (!sm.ok) break;
+        }
+        run_tile<NW, WPL>(A, hd, seg, tile, sm, slots, acc);
+        __syncthreads();
+        if (threadIdx.x == 0 && A.use_queue) {
+            __threadfence();
+            atomicAdd(done + sidx, 1u);
+        }
+    }
+}
+
+// (TP, FP) accumulators -> (TP, FP, FN, TN); records a device error on the handle.
+__global__ void finalize_kernel(KBView kb, const uint8_t *ws, uint32_t *counts) {
+    const PlanHeader *hd = reinterpret_cast<const PlanHeader *>(ws);
+    const Counters *ctr = reinterpret_cast<const Counters *>(ws + hd->off_ctr);
+    const uint32_t *acc = reinterpret_cast<const uint32_t *>(ctr + 1) + hd->n_segs + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctr->err) atomicOr(kb.status, ctr->err);
+    if (!counts) return;
+    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < hd->n_hyps; h += gridDim.x * blockDim.x) {
+        const uint32_t tp = acc[2 * h], fp = acc[2 * h + 1];
+        uint4 c = make_uint4(tp, fp, kb.n_pos - tp, kb.n_neg - fp);
+        *reinterpret_cast<uint4 *>(counts + 4ull * h) = c;
+    }
+}
+
+using KernelFn = void (*)(ExecArgs);
+
+KernelFn pick(uint32_t warps, uint32_t wpl) {
+    if (wpl == 4) {
+        if (warps == 4) return exec_kernel<4, 4>;
+        if (warps == 16) return exec_kernel<16, 4>;
+        return exec_kernel<8, 4>;
+    }
+    if (warps == 4) return exec_kernel<4, 1>;
+    if (warps == 16) return exec_kernel<16, 1>;
+    return exec_kernel<8, 1>;
+}
+
+}  // namespace
+
+size_t exec_smem_bytes(const Tuning &t) {
+    return sizeof(uint32_t) * (size_t)t.warps * STACK_MAX * t.wpl * 32 + 16;
+}
+
+int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm) {
+    KernelFn fn = pick(t.warps, t.wpl);
+    size_t smem = exec_smem_bytes(t);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, (int)(t.warps * 32), smem);
+    return e;
+}
+
+int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t *out_bits, void *ws,
+                void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const Tuning &t = p->tuning;
+    KernelFn fn = pick(t.warps, t.wpl);
+    size_t smem = exec_smem_bytes(t);
+    int bps = p->bps;
+    if (bps < 1) return cudaErrorInvalidConfiguration;
+    if (t.ctas_per_sm && (int)t.ctas_per_sm < bps) bps = (int)t.ctas_per_sm;
+    ExecArgs A{};
+    A.kb = kb->view();
+    A.ws = (uint8_t *)ws;
+    A.counts = counts;
+    A.out_bits = out_bits;
+    const uint32_t n_items = p->info.n_items;
+    if (p->flags & HEDL_LEVELS) {
+        // one launch per level; items of a level are independent
+        A.use_queue = 0;
+        for (uint32_t l = 0; l < p->info.n_levels; ++l) {
+            A.item_begin = p->level_items[l];
+            A.item_end = p->level_items[l + 1];
+            uint32_t n = A.item_end - A.item_begin;
+            if (!n) continue;
+            uint32_t grid = std::min<uint32_t>(n, (uint32_t)(bps * kb->n_sms));
+            fn<<<grid, t.warps * 32, smem, s>>>(A);
+            cudaError_t le = cudaGetLastError();
+            if (le != cudaSuccess) return le;
+        }
+    } else {
+        A.use_queue = 1;
+        A.item_begin = 0;
+        A.item_end = n_items;
+        uint32_t grid = std::min<uint32_t>(std::max<uint32_t>(n_items, 1), (uint32_t)(bps * kb->n_sms));
+        fn<<<grid, t.warps * 32, smem, s>>>(A);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return le;
+    }
+    finalize_kernel<<<std::max<uint32_t>(1, std::min<uint32_t>((p->n_hyps + 255) / 256, 1024)), 256, 0, s>>>(
+        kb->view(), (const uint8_t *)ws, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace hedl

@@ -1,0 +1,189 @@
+// Library-private declarations shared by the host planner (plan.cpp), the
+// C-ABI layer (api.cu) and the device kernels (exec.cu, plain.cu, kb.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hedl.h"
+
+namespace hedl {
+
+// ------------------------------------------------------------------ device-side KB view
+struct DevCSR {
+    const uint32_t *rp;    // [n+1]
+    const uint32_t *col;   // [E]
+    uint32_t n_edges;
+    uint32_t pad;
+};
+
+// Passed by value to every kernel.
+struct KBView {
+    const uint32_t *concepts;    // [C][wp]
+    const DevCSR *csr;           // device [2*R]: role r forward at 2r, inverse at 2r+1
+    const float *props;          // [P][prop_stride]
+    uint64_t prop_stride;
+    const uint32_t *pos;         // [wp] or null
+    const uint32_t *neg;
+    uint32_t *status;            // device status word owned by the handle
+    uint32_t n, w, wp;           // individuals, valid words, row words
+    uint32_t n_pos, n_neg;
+};
+
+// status word bits (device)
+enum : uint32_t { ST_TIMEOUT = 1u, ST_DEVICE_CHECK = 2u };
+
+// ------------------------------------------------------------------ segment code
+// One 16-byte instruction of a segment program (a role-free boolean
+// expression whose leaves may be role restrictions over materialized fillers).
+enum : uint32_t {
+    D_ATOM = 1, D_TOP = 2, D_BOT = 3, D_NOT = 4, D_AND = 5, D_OR = 6,
+    D_ROLE = 7,      // aux = kind (HEDL_OP_EXISTS..EXACTLY), a = role, flags bit0 = inverse, b = n
+    D_DATA = 12,     // aux = cmp (HEDL_OP_DGE/DLE/DEQ), a = property, b = float bits
+    D_SLOT = 32      // a materialized bitset: ref = slot index
+};
+constexpr uint32_t REF_SLOT = 0x80000000u;   // filler ref: slot (low bits) vs concept id
+
+struct DInsn {
+    uint32_t op;     // D_*
+    uint32_t a;      // concept / role / property id
+    uint32_t b;      // n or threshold bits
+    uint32_t ref;    // D_ROLE: filler ref; D_SLOT: slot; bits 16..23 of op word: aux, bit 8: inverse
+};
+inline uint32_t dop(uint32_t w) { return w & 0xFF; }
+
+constexpr uint32_t NO_SLOT = 0xFFFFFFFFu;
+constexpr uint32_t NO_HYP = 0xFFFFFFFFu;
+
+struct Seg {
+    uint32_t code_off;   // index into code[]
+    uint32_t code_len;
+    uint32_t out_slot;   // NO_SLOT if none
+    uint32_t hyp;        // NO_HYP if not a hypothesis root
+    uint32_t dep_off;    // index into deps[]
+    uint32_t dep_cnt;
+    uint32_t level;
+    uint32_t stack;      // stack depth its code needs
+};
+
+struct Group {
+    uint32_t item_begin;
+    uint32_t seg_begin;  // index into gsegs[]
+    uint32_t n_segs;
+    uint32_t level;
+};
+
+// Header at the start of the workspace (plan image).
+struct PlanHeader {
+    uint32_t n_items, n_segs, n_groups, n_hyps;
+    uint32_t n_tiles, tile_words, n_slots, flags;
+    uint32_t n_levels, n_deps, pad0, pad1;
+    uint64_t off_segs, off_groups, off_gsegs, off_deps;
+    uint64_t off_code, off_level_items, off_ctr, off_slots;
+    uint64_t timeout_ns;
+};
+
+// Counters region (zeroed for every execution)
+struct Counters {
+    uint32_t head;     // next work item
+    uint32_t abort;    // set when a wait gave up
+    uint32_t err;
+    uint32_t pad;
+    // followed by done[n_segs] (tiles finished) and acc[n_hyps][2] (TP, FP)
+};
+
+constexpr int STACK_MAX = 16;
+
+// ------------------------------------------------------------------ host objects
+struct Tuning {
+    uint32_t warps = 8;
+    uint32_t wpl = 1;        // words per lane
+    uint32_t rounds = 1;
+    uint32_t ctas_per_sm = 0;
+    uint32_t timeout_ms = 2000;
+    uint32_t tile_words() const { return warps * 32u * wpl * rounds; }
+};
+
+struct PlanImpl;
+
+}  // namespace hedl
+
+struct hedl_kb {
+    uint32_t n = 0, w = 0, wp = 0;
+    uint32_t n_concepts = 0, n_roles = 0, n_props = 0;
+    const uint32_t *concepts = nullptr;
+    const float *props = nullptr;
+    uint64_t prop_stride = 0;
+    std::vector<hedl::DevCSR> csr_host;     // [2R]
+    std::vector<uint32_t> role_edges;       // [R] forward edge counts
+    hedl::DevCSR *csr_dev = nullptr;
+    uint32_t *status_dev = nullptr;         // [4]: status, |P|, |N|, scratch
+    const uint32_t *pos = nullptr, *neg = nullptr;
+    uint32_t n_pos = 0, n_neg = 0;
+    bool has_examples = false;
+    int device = 0;
+    int n_sms = 0;
+    bool plan_only = false;                 // sizes only, no device state
+    void *capture_stream = nullptr;         // private stream that CUDA graphs are captured on
+    hedl::Tuning tuning;
+    // one cached plan for the one-shot calls
+    hedl_plan *cached = nullptr;
+    uint64_t cached_hash = 0;
+    unsigned cached_flags = 0;
+    hedl::KBView view() const;
+};
+
+struct hedl_plan {
+    hedl::PlanImpl *impl = nullptr;
+};
+
+namespace hedl {
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(int cuda_err, const char *what);
+
+// plan.cpp
+struct PlanImpl {
+    unsigned flags = 0;
+    uint32_t n_hyps = 0;
+    hedl_plan_info info{};
+    std::vector<uint8_t> image;          // header + tables + zeroed counters
+    uint64_t image_bytes = 0;            // bytes to upload (aligned)
+    uint64_t ctr_off = 0, ctr_bytes = 0; // counters region inside the image
+    uint64_t slots_off = 0;              // slots region (after the image)
+    uint64_t ws_bytes = 0;
+    std::vector<uint32_t> level_items;   // [n_levels+1] item range per level
+    uint32_t max_stack = 0;
+    Tuning tuning;
+    int bps = 0;                         // resident CTAs per SM of the interpreter
+    // plain path: validated programs
+    std::vector<uint64_t> progs;
+    std::vector<uint32_t> offs;
+    uint32_t plain_depth = 0;
+    // graph cache
+    void *graph_exec = nullptr;
+    void *graph_ws = nullptr;
+    uint32_t *graph_counts = nullptr;
+    uint32_t *graph_out = nullptr;
+    ~PlanImpl();
+};
+
+int validate_program(const hedl_kb *kb, const uint64_t *prog, uint32_t len, std::string *why);
+int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+               unsigned flags, PlanImpl **out);
+uint64_t hash_programs(const uint64_t *progs, const uint32_t *offs, uint32_t H);
+
+// exec.cu / plain.cu / kb.cu launchers (return cudaError_t as int)
+int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t *out_bits, void *ws,
+                void *stream);
+int launch_plain(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t *out_bits, void *ws,
+                 void *stream);
+int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm);
+int kb_validate_device(const hedl_kb *kb, void *stream, std::string *why);
+int examples_count_device(const hedl_kb *kb, void *stream, uint32_t *np, uint32_t *nn);
+size_t exec_smem_bytes(const Tuning &t);
+
+}  // namespace hedl

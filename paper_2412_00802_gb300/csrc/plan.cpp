@@ -1,0 +1,528 @@
+// Host planner: turns a batch of postfix hypothesis programs into the device
+// work queue executed by the segment interpreter (exec.cu).
+//
+// The paper builds an evaluation plan (a query plan fixing the order of the
+// DL operations and their inputs) for each hypothesis on the CPU before it
+// runs (Section IV), multi-threaded across a batch (Section V).  Here the plan
+// of a whole batch is one DAG:
+//   1. every program is decoded and validated, and its nodes are hash-consed
+//      into one DAG shared by the batch (common sub-concepts are evaluated
+//      once; AND/OR operands are put in canonical order and NOT NOT X folds to
+//      X, which changes no instance set);
+//   2. a node is materialized as a full bitset ("slot") if it is the filler
+//      of a role restriction (a role restriction reads its filler at
+//      arbitrary individuals, so the filler must exist over all individuals
+//      first) or if it is used twice or more and its inline expansion holds a
+//      role restriction (so that work is done once);
+//   3. every materialized node and every hypothesis root becomes a segment:
+//      a role-free boolean program whose leaves are atoms, data ranges,
+//      slots and role restrictions over slots or concept rows;
+//   4. segments get levels (1 + the deepest producer of a slot they read) and
+//      are grouped by (level, first role read); each group's work items are
+//      (segment, tile) pairs in tile-major order so that segments sweeping the
+//      same role stream the same CSR rows at about the same time.
+#include <algorithm>
+#include <cstring>
+#include <unordered_map>
+
+#include "hedl_internal.h"
+
+namespace hedl {
+
+namespace {
+
+struct PNode {
+    uint8_t op;
+    uint8_t inv;
+    uint16_t pad;
+    uint32_t a;
+    uint32_t b;
+    int32_t k0, k1;
+};
+
+struct Key {
+    uint64_t x, y;
+    bool operator==(const Key &o) const { return x == o.x && y == o.y; }
+};
+struct KeyHash {
+    size_t operator()(const Key &k) const {
+        uint64_t h = k.x * 0x9E3779B97F4A7C15ull ^ (k.y + 0x632BE59BD9B4E019ull + (k.x << 6) + (k.x >> 2));
+        h ^= h >> 31;
+        h *= 0xBF58476D1CE4E5B9ull;
+        return (size_t)(h ^ (h >> 29));
+    }
+};
+
+inline bool is_role(uint32_t op) { return op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY; }
+inline bool is_data(uint32_t op) { return op >= HEDL_OP_DGE && op <= HEDL_OP_DEQ; }
+inline int arity(uint32_t op) {
+    if (op == HEDL_OP_ATOM || op == HEDL_OP_TOP || op == HEDL_OP_BOT || is_data(op)) return 0;
+    if (op == HEDL_OP_NOT || is_role(op)) return 1;
+    if (op == HEDL_OP_AND || op == HEDL_OP_OR) return 2;
+    return -1;
+}
+
+const char *op_name(uint32_t op) {
+    static const char *names[] = {"?", "ATOM", "TOP", "BOT", "NOT", "AND", "OR", "EXISTS", "FORALL",
+                                  "ATLEAST", "ATMOST", "EXACTLY", "DGE", "DLE", "DEQ"};
+    return op < 15 ? names[op] : "?";
+}
+
+}  // namespace
+
+int validate_program(const hedl_kb *kb, const uint64_t *prog, uint32_t len, std::string *why) {
+    if (len == 0) {
+        *why = "empty program";
+        return HEDL_ERR_BAD_PROGRAM;
+    }
+    int depth = 0;
+    for (uint32_t k = 0; k < len; ++k) {
+        uint64_t w = prog[k];
+        uint32_t op = (uint32_t)(w & 0xFF);
+        uint32_t a = (uint32_t)((w >> 16) & 0xFFFF);
+        int ar = arity(op);
+        char buf[160];
+        if (ar < 0) {
+            snprintf(buf, sizeof buf, "instruction %u: unknown op %u", k, op);
+            *why = buf;
+            return HEDL_ERR_BAD_PROGRAM;
+        }
+        if ((op == HEDL_OP_ATOM && a >= kb->n_concepts) || (is_role(op) && a >= kb->n_roles) ||
+            (is_data(op) && a >= kb->n_props)) {
+            snprintf(buf, sizeof buf, "instruction %u: %s names id %u, out of range", k, op_name(op), a);
+            *why = buf;
+            return HEDL_ERR_BAD_PROGRAM;
+        }
+        if (depth < ar) {
+            snprintf(buf, sizeof buf, "instruction %u: %s pops an empty stack", k, op_name(op));
+            *why = buf;
+            return HEDL_ERR_BAD_PROGRAM;
+        }
+        depth = depth - ar + 1;
+        if (depth > HEDL_MAX_STACK) {
+            snprintf(buf, sizeof buf, "instruction %u: more than %d operands on the stack", k, HEDL_MAX_STACK);
+            *why = buf;
+            return HEDL_ERR_BAD_PROGRAM;
+        }
+    }
+    if (depth != 1) {
+        *why = "program leaves " + std::to_string(depth) + " operands, not 1";
+        return HEDL_ERR_BAD_PROGRAM;
+    }
+    return HEDL_OK;
+}
+
+uint64_t hash_programs(const uint64_t *progs, const uint32_t *offs, uint32_t H) {
+    uint64_t h = 0xCBF29CE484222325ull ^ H;
+    auto mix = [&](uint64_t v) {
+        h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+        h *= 0x100000001B3ull;
+    };
+    for (uint32_t i = 0; i <= H; ++i) mix(offs[i]);
+    for (uint32_t i = 0; i < offs[H]; ++i) mix(progs[i]);
+    return h;
+}
+
+PlanImpl::~PlanImpl() = default;
+
+namespace {
+
+template <class T>
+uint64_t put(std::vector<uint8_t> &img, const std::vector<T> &v) {
+    uint64_t off = (img.size() + 255) & ~uint64_t(255);
+    img.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) memcpy(img.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+}
+
+}  // namespace
+
+int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, unsigned flags,
+               PlanImpl **out) {
+    *out = nullptr;
+    if (H == 0) return fail(HEDL_ERR_INVALID_ARG, "empty batch (H = 0)");
+    if (offs[0] != 0) return fail(HEDL_ERR_INVALID_ARG, "offs[0] must be 0");
+    for (uint32_t h = 0; h < H; ++h) {
+        if (offs[h + 1] < offs[h]) return fail(HEDL_ERR_INVALID_ARG, "offs must be non-decreasing");
+        std::string why;
+        int e = validate_program(kb, progs + offs[h], offs[h + 1] - offs[h], &why);
+        if (e) return fail(e, "program " + std::to_string(h) + ": " + why);
+    }
+    auto *p = new PlanImpl();
+    p->flags = flags;
+    p->n_hyps = H;
+    p->tuning = kb->tuning;
+    const uint64_t N = kb->n, B = 4ull * kb->wp;
+    p->info.n_hyps = H;
+    p->info.total_insns = offs[H];
+
+    if (flags & HEDL_PLAIN) {
+        // One launch per operation: keep the programs; the stack of the
+        // deepest program sizes the workspace.
+        p->progs.assign(progs, progs + offs[H]);
+        p->offs.assign(offs, offs + H + 1);
+        uint32_t maxd = 1;
+        uint64_t mb = 0;
+        for (uint32_t h = 0; h < H; ++h) {
+            int d = 0;
+            for (uint32_t k = offs[h]; k < offs[h + 1]; ++k) {
+                uint32_t op = (uint32_t)(progs[k] & 0xFF);
+                uint32_t a = (uint32_t)((progs[k] >> 16) & 0xFFFF);
+                d = d - arity(op) + 1;
+                maxd = std::max<uint32_t>(maxd, (uint32_t)d);
+                if (op == HEDL_OP_ATOM) mb += B, p->info.n_atom_loads++;
+                else if (is_data(op)) mb += 4 * N, p->info.n_data_ops++;
+                else if (is_role(op)) mb += 4 * (N + 1) + 4ull * kb->role_edges[a] + B, p->info.n_role_ops++;
+            }
+            mb += B + 2 * B + 16;  // result row, scoring
+        }
+        p->plain_depth = maxd;
+        p->info.model_bytes = mb;
+        // workspace: header page, accumulators [H][2], stack rows
+        uint64_t acc_off = 256;
+        uint64_t rows_off = (acc_off + 8ull * H + 255) & ~uint64_t(255);
+        p->ws_bytes = rows_off + (uint64_t)(maxd + 1) * B;
+        p->info.workspace_bytes = p->ws_bytes;
+        p->info.n_levels = 0;
+        *out = p;
+        return HEDL_OK;
+    }
+
+    const bool cse = !(flags & HEDL_NO_CSE);
+    std::vector<PNode> nodes;
+    nodes.reserve(offs[H] + 16);
+    std::unordered_map<Key, int32_t, KeyHash> memo;
+    memo.reserve(cse ? offs[H] * 2 + 16 : 0);
+    auto make = [&](PNode n) -> int32_t {
+        // canonical form: ignored fields zeroed, commutative operands ordered
+        if (!is_role(n.op)) n.inv = 0;
+        if (!(n.op == HEDL_OP_ATOM || is_role(n.op) || is_data(n.op))) n.a = 0;
+        if (!(n.op == HEDL_OP_ATLEAST || n.op == HEDL_OP_ATMOST || n.op == HEDL_OP_EXACTLY || is_data(n.op))) n.b = 0;
+        if (cse) {
+            if ((n.op == HEDL_OP_AND || n.op == HEDL_OP_OR) && n.k0 > n.k1) std::swap(n.k0, n.k1);
+            if (n.op == HEDL_OP_NOT && nodes[n.k0].op == HEDL_OP_NOT) return nodes[n.k0].k0;
+            Key k{(uint64_t)n.op | ((uint64_t)n.inv << 8) | ((uint64_t)n.a << 16) | ((uint64_t)n.b << 32),
+                  (uint64_t)(uint32_t)n.k0 | ((uint64_t)(uint32_t)n.k1 << 32)};
+            auto it = memo.find(k);
+            if (it != memo.end()) return it->second;
+            memo.emplace(k, (int32_t)nodes.size());
+        }
+        nodes.push_back(n);
+        return (int32_t)nodes.size() - 1;
+    };
+
+    std::vector<int32_t> roots(H);
+    std::vector<int32_t> st;
+    for (uint32_t h = 0; h < H; ++h) {
+        st.clear();
+        for (uint32_t k = offs[h]; k < offs[h + 1]; ++k) {
+            uint64_t w = progs[k];
+            PNode n{};
+            n.op = (uint8_t)(w & 0xFF);
+            n.inv = (uint8_t)((w >> 8) & 1);
+            n.a = (uint32_t)((w >> 16) & 0xFFFF);
+            n.b = (uint32_t)(w >> 32);
+            n.k0 = n.k1 = -1;
+            int ar = arity(n.op);
+            if (ar == 2) {
+                n.k1 = st.back();
+                st.pop_back();
+                n.k0 = st.back();
+                st.pop_back();
+            } else if (ar == 1) {
+                n.k0 = st.back();
+                st.pop_back();
+            }
+            st.push_back(make(n));
+        }
+        roots[h] = st.back();
+    }
+    const uint32_t NN = (uint32_t)nodes.size();
+    p->info.n_nodes = NN;
+
+    // reference counts (parents + hypothesis roots)
+    std::vector<uint32_t> refc(NN, 0);
+    for (uint32_t i = 0; i < NN; ++i) {
+        if (nodes[i].k0 >= 0) refc[nodes[i].k0]++;
+        if (nodes[i].k1 >= 0) refc[nodes[i].k1]++;
+    }
+    for (uint32_t h = 0; h < H; ++h) refc[roots[h]]++;
+
+    // materialization (children are created before parents, so index order
+    // is a topological order)
+    std::vector<uint8_t> mat(NN, 0);
+    for (uint32_t i = 0; i < NN; ++i)
+        if (is_role(nodes[i].op) && nodes[nodes[i].k0].op != HEDL_OP_ATOM) mat[nodes[i].k0] = 1;
+    std::vector<uint8_t> role_inline(NN, 0);
+    std::vector<uint32_t> need(NN, 1);
+    for (uint32_t i = 0; i < NN; ++i) {
+        const PNode &n = nodes[i];
+        auto ri = [&](int32_t c) { return c >= 0 && !mat[c] && role_inline[c]; };
+        role_inline[i] = is_role(n.op) || ri(n.k0) || ri(n.k1);
+        if (!mat[i] && refc[i] >= 2 && role_inline[i] && n.op != HEDL_OP_ATOM) mat[i] = 1;
+        // stack need (Sethi-Ullman), materialized children count as leaves
+        auto nd = [&](int32_t c) -> uint32_t { return mat[c] ? 1u : need[c]; };
+        if (n.op == HEDL_OP_NOT) need[i] = nd(n.k0);
+        else if (n.op == HEDL_OP_AND || n.op == HEDL_OP_OR) {
+            uint32_t a = nd(n.k0), b = nd(n.k1);
+            uint32_t v = a == b ? a + 1 : std::max(a, b);
+            if (v > (uint32_t)STACK_MAX - 1) {   // keep every segment within the device stack
+                mat[a >= b ? n.k0 : n.k1] = 1;
+                a = nd(n.k0);
+                b = nd(n.k1);
+                v = a == b ? a + 1 : std::max(a, b);
+            }
+            need[i] = v;
+        } else need[i] = 1;
+    }
+
+    // slots and segments
+    std::vector<uint32_t> slot_of(NN, NO_SLOT);
+    uint32_t n_slots = 0;
+    for (uint32_t i = 0; i < NN; ++i)
+        if (mat[i]) slot_of[i] = n_slots++;
+    std::vector<Seg> segs;
+    std::vector<DInsn> code;
+    std::vector<std::vector<uint32_t>> seg_slots_read;
+    std::vector<uint32_t> seg_of_slot(n_slots, 0);
+    std::vector<uint32_t> role_key;  // first role read, for grouping
+    uint64_t model = 0;
+
+    std::vector<int32_t> work;
+    auto emit_segment = [&](int32_t root, uint32_t out_slot, uint32_t hyp) {
+        Seg s{};
+        s.code_off = (uint32_t)code.size();
+        s.out_slot = out_slot;
+        s.hyp = hyp;
+        std::vector<uint32_t> reads;
+        uint32_t rk = 0xFFFFFFFFu;
+        // iterative post-order emission, larger stack need first
+        struct Frame { int32_t n; int state; };
+        std::vector<Frame> fr;
+        fr.push_back({root, 0});
+        int depth = 0, maxdepth = 0;
+        while (!fr.empty()) {
+            Frame &f = fr.back();
+            int32_t i = f.n;
+            const PNode &n = nodes[i];
+            bool leafish = (i != root && mat[i]) || arity(n.op) == 0 || is_role(n.op);
+            if (leafish) {
+                DInsn d{};
+                if (i != root && mat[i]) {
+                    d.op = D_SLOT;
+                    d.ref = slot_of[i];
+                    reads.push_back(slot_of[i]);
+                    model += B;
+                } else if (n.op == HEDL_OP_ATOM) {
+                    d.op = D_ATOM;
+                    d.a = n.a;
+                    model += B;
+                    p->info.n_atom_loads++;
+                } else if (n.op == HEDL_OP_TOP || n.op == HEDL_OP_BOT) {
+                    d.op = n.op;
+                } else if (is_data(n.op)) {
+                    d.op = D_DATA | (n.op << 16);
+                    d.a = n.a;
+                    d.b = n.b;
+                    model += 4 * N;
+                    p->info.n_data_ops++;
+                } else {  // role restriction
+                    int32_t c = n.k0;
+                    d.op = D_ROLE | ((uint32_t)n.inv << 8) | ((uint32_t)n.op << 16);
+                    d.a = n.a;
+                    d.b = n.b;
+                    if (nodes[c].op == HEDL_OP_ATOM && !mat[c]) d.ref = nodes[c].a;
+                    else {
+                        d.ref = REF_SLOT | slot_of[c];
+                        reads.push_back(slot_of[c]);
+                    }
+                    if (rk == 0xFFFFFFFFu) rk = n.a * 2 + n.inv;
+                    const DevCSR &g = kb->csr_host[2 * n.a + n.inv];
+                    model += 4 * (N + 1) + 4ull * g.n_edges + B;
+                    p->info.n_role_ops++;
+                }
+                code.push_back(d);
+                depth++;
+                maxdepth = std::max(maxdepth, depth);
+                fr.pop_back();
+                continue;
+            }
+            if (n.op == HEDL_OP_NOT) {
+                if (f.state == 0) {
+                    f.state = 1;
+                    fr.push_back({n.k0, 0});
+                } else {
+                    DInsn d{};
+                    d.op = D_NOT;
+                    code.push_back(d);
+                    fr.pop_back();
+                }
+                continue;
+            }
+            // AND / OR
+            auto nd = [&](int32_t c) -> uint32_t { return mat[c] ? 1u : need[c]; };
+            int32_t first = nd(n.k0) >= nd(n.k1) ? n.k0 : n.k1;
+            int32_t second = first == n.k0 ? n.k1 : n.k0;
+            if (f.state == 0) {
+                f.state = 1;
+                fr.push_back({first, 0});
+            } else if (f.state == 1) {
+                f.state = 2;
+                fr.push_back({second, 0});
+            } else {
+                DInsn d{};
+                d.op = n.op;
+                code.push_back(d);
+                depth--;
+                fr.pop_back();
+            }
+        }
+        s.code_len = (uint32_t)code.size() - s.code_off;
+        s.stack = (uint32_t)maxdepth;
+        p->max_stack = std::max(p->max_stack, (uint32_t)maxdepth);
+        model += B;  // output row (slot, instance set or score input)
+        if (hyp != NO_HYP) model += 2 * B + 16;
+        std::sort(reads.begin(), reads.end());
+        reads.erase(std::unique(reads.begin(), reads.end()), reads.end());
+        seg_slots_read.push_back(reads);
+        role_key.push_back(rk);
+        segs.push_back(s);
+    };
+    for (uint32_t i = 0; i < NN; ++i)
+        if (mat[i]) {
+            seg_of_slot[slot_of[i]] = (uint32_t)segs.size();
+            emit_segment((int32_t)i, slot_of[i], NO_HYP);
+        }
+    for (uint32_t h = 0; h < H; ++h) {
+        if (mat[roots[h]]) {  // the root is already a slot: the segment reads it
+            Seg s{};
+            s.code_off = (uint32_t)code.size();
+            s.code_len = 1;
+            s.out_slot = NO_SLOT;
+            s.hyp = h;
+            s.stack = 1;
+            DInsn d{};
+            d.op = D_SLOT;
+            d.ref = slot_of[roots[h]];
+            code.push_back(d);
+            model += B + B + 2 * B + 16;
+            seg_slots_read.push_back({slot_of[roots[h]]});
+            role_key.push_back(0xFFFFFFFFu);
+            segs.push_back(s);
+            p->max_stack = std::max(p->max_stack, 1u);
+        } else {
+            emit_segment(roots[h], NO_SLOT, h);
+        }
+    }
+    if (p->max_stack > (uint32_t)STACK_MAX) {
+        delete p;
+        return fail(HEDL_ERR_BAD_PROGRAM, "internal: segment stack exceeds the device limit");
+    }
+    const uint32_t NS = (uint32_t)segs.size();
+
+    // dependencies and levels
+    std::vector<uint32_t> deps;
+    uint32_t n_levels = 0;
+    for (uint32_t s = 0; s < NS; ++s) {
+        segs[s].dep_off = (uint32_t)deps.size();
+        uint32_t lvl = 0;
+        for (uint32_t sl : seg_slots_read[s]) {
+            uint32_t prod = seg_of_slot[sl];
+            deps.push_back(prod);
+            lvl = std::max(lvl, segs[prod].level + 1);
+        }
+        segs[s].dep_cnt = (uint32_t)deps.size() - segs[s].dep_off;
+        segs[s].level = lvl;
+        n_levels = std::max(n_levels, lvl + 1);
+    }
+    if (flags & HEDL_TEST_UNSAT_DEP) {
+        // the last segment additionally waits on a counter past the real
+        // ones, which nothing ever increments
+        segs[NS - 1].dep_off = (uint32_t)deps.size();
+        segs[NS - 1].dep_cnt = 1;
+        deps.push_back(NS);
+    }
+
+    // groups: (level, role key), items tile-major inside a group
+    const Tuning &t = p->tuning;
+    const uint32_t TW = t.tile_words();
+    const uint32_t n_tiles = (kb->wp + TW - 1) / TW;
+    std::vector<uint32_t> order(NS);
+    for (uint32_t s = 0; s < NS; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (segs[x].level != segs[y].level) return segs[x].level < segs[y].level;
+        return role_key[x] < role_key[y];
+    });
+    std::vector<Group> groups;
+    std::vector<uint32_t> gsegs;
+    std::vector<uint32_t> level_items(n_levels + 1, 0);
+    uint64_t items = 0;
+    for (uint32_t k = 0; k < NS;) {
+        uint32_t s0 = order[k];
+        Group g{};
+        g.item_begin = (uint32_t)items;
+        g.seg_begin = (uint32_t)gsegs.size();
+        g.level = segs[s0].level;
+        uint32_t k2 = k;
+        while (k2 < NS && segs[order[k2]].level == g.level && role_key[order[k2]] == role_key[s0]) {
+            gsegs.push_back(order[k2]);
+            ++k2;
+        }
+        g.n_segs = k2 - k;
+        items += (uint64_t)g.n_segs * n_tiles;
+        groups.push_back(g);
+        level_items[g.level + 1] = (uint32_t)items;
+        k = k2;
+    }
+    for (uint32_t l = 1; l <= n_levels; ++l) level_items[l] = std::max(level_items[l], level_items[l - 1]);
+    if (items >= 0xFFFFFFFFull) {
+        delete p;
+        return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^32 work items");
+    }
+
+    // image: header, tables, counters; then the slots
+    std::vector<uint8_t> &img = p->image;
+    img.resize(sizeof(PlanHeader));
+    PlanHeader hd{};
+    hd.n_items = (uint32_t)items;
+    hd.n_segs = NS;
+    hd.n_groups = (uint32_t)groups.size();
+    hd.n_hyps = H;
+    hd.n_tiles = n_tiles;
+    hd.tile_words = TW;
+    hd.n_slots = n_slots;
+    hd.flags = flags;
+    hd.n_levels = n_levels;
+    hd.n_deps = (uint32_t)deps.size();
+    hd.off_segs = put(img, segs);
+    hd.off_groups = put(img, groups);
+    hd.off_gsegs = put(img, gsegs);
+    hd.off_deps = put(img, deps);
+    hd.off_code = put(img, code);
+    hd.off_level_items = put(img, level_items);
+    // counters: Counters + done[NS + 1] + acc[H][2]
+    std::vector<uint32_t> zeros(4 + (NS + 1) + 2ull * H, 0);
+    hd.off_ctr = put(img, zeros);
+    p->ctr_off = hd.off_ctr;
+    p->ctr_bytes = zeros.size() * 4;
+    img.resize((img.size() + 255) & ~size_t(255));
+    hd.off_slots = img.size();
+    hd.timeout_ns = (uint64_t)t.timeout_ms * 1000000ull;
+    memcpy(img.data(), &hd, sizeof hd);
+    p->image_bytes = img.size();
+    p->slots_off = hd.off_slots;
+    p->ws_bytes = hd.off_slots + (uint64_t)n_slots * B;
+    p->level_items = level_items;
+
+    p->info.n_segments = NS;
+    p->info.n_slots = n_slots;
+    p->info.n_levels = n_levels;
+    p->info.n_items = (uint32_t)items;
+    p->info.tile_words = TW;
+    p->info.workspace_bytes = p->ws_bytes;
+    p->info.model_bytes = model;
+    *out = p;
+    return HEDL_OK;
+}
+
+}  // namespace hedl

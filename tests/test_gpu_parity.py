@@ -1,0 +1,229 @@
+"""Parity of the CUDA path with the oracle (bit-exact), through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2412_00802_gb300 as H
+from synth import hyps, kb as K, programs as P
+from synth.rng import Rng
+from tests import golden_io
+from tests import oracle_pins as pins
+from tests.gpu_util import compare_batch, device_kb
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"default": 0, "no_cse": H.HEDL_NO_CSE, "no_graph": H.HEDL_NO_GRAPH, "levels": H.HEDL_LEVELS,
+         "plain": H.HEDL_PLAIN}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2412_00802_gb300 import build
+    build.build()
+    oracle.build()
+
+
+@pytest.mark.parametrize("name", golden_io.fixtures())
+def test_hand_worked_fixtures(name):
+    """The GPU reproduces the hand-derived instance sets and counts."""
+    fx = golden_io.load(name)
+    kb = K.from_arrays(fx.n, fx.concept_list(), fx.role_list(), fx.prop_rows(), sorted(fx.pos), sorted(fx.neg))
+    dkb = device_kb(kb)
+    progs = [P.compile_text(q) for q, _, _ in fx.queries]
+    for mode in MODES.values():
+        counts, bits = dkb.score(*P.pack_batch(progs), mode, out_bits=True)
+        for h, (q, inst, cnt) in enumerate(fx.queries):
+            got = set(np.nonzero(K.unpack_bits(bits[h], fx.n))[0].tolist())
+            assert got == inst, (mode, q, sorted(got))
+            assert tuple(int(x) for x in counts[h]) == cnt, (mode, q, counts[h])
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return K.generate(K.CONFIGS["c1"])
+
+
+@pytest.fixture(scope="module")
+def c1_dev(c1):
+    return device_kb(c1)
+
+
+@pytest.fixture(scope="module")
+def c1_progs(c1):
+    return hyps.small_hyps(c1, 11, 1000)
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_c1_all_hypotheses(c1, c1_dev, c1_progs, mode):
+    """Workload 1: 1,000 hypotheses of depth <= 4, every instance set and count."""
+    compare_batch(c1, c1_dev, c1_progs, MODES[mode])
+
+
+def test_c1_batched_shapes(c1, c1_dev):
+    """Uneven lengths 1..40, depths 1..8, shared sub-concepts."""
+    progs = hyps.batch_hyps(c1, 21, 0, 512)
+    compare_batch(c1, c1_dev, progs, 0)
+    compare_batch(c1, c1_dev, progs, H.HEDL_LEVELS)
+
+
+@pytest.mark.parametrize("tuning", [dict(warps_per_cta=4, words_per_lane=4, rounds=2),
+                                    dict(warps_per_cta=16, words_per_lane=1, rounds=3),
+                                    dict(warps_per_cta=8, words_per_lane=4, rounds=1, ctas_per_sm=1)])
+def test_launch_shapes(c1, tuning):
+    dkb = device_kb(c1)
+    H.hedl_tuning_set(dkb.handle, **tuning)
+    compare_batch(c1, dkb, hyps.batch_hyps(c1, 22, 0, 300), 0)
+
+
+def test_eval_concept(c1, c1_dev):
+    okb = oracle.from_synth(c1)
+    r = Rng(9, 9)
+    for i in range(40):
+        prog = pins.random_program(r, c1, r.randint(1, 6)).postfix()
+        got = K.unpack_bits(c1_dev.eval(np.array(prog, np.uint64)), c1.n)
+        assert np.array_equal(got, oracle.eval_program(okb, prog)), P.to_text(P.from_postfix(prog))
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 63, 64, 65, 100, 127, 129, 1000, 4097])
+def test_ragged_sizes_every_constructor(n):
+    """Sizes around word and 128-bit boundaries, every constructor incl. TOP/BOT/EXACTLY/DEQ."""
+    cfg = K.CONFIGS["c1"].scaled(n, seed=1000 + n, n_concepts=6, n_roles=3, n_props=2,
+                                 degree=("poisson", min(3.0, max(n - 1, 0) / 2 + 0.5)),
+                                 n_pos=max(1, n // 4), n_neg=max(1, n // 4) if n > 1 else 0)
+    cfg = cfg if cfg.n_pos + cfg.n_neg <= n else cfg.scaled(n, n_pos=1, n_neg=0)
+    kb = K.generate(cfg)
+    dkb = device_kb(kb)
+    r = Rng(n, 3)
+    progs = [np.array(pins.random_program(r, kb, r.randint(1, 5)).postfix(), np.uint64) for _ in range(120)]
+    for mode in (0, H.HEDL_PLAIN):
+        compare_batch(kb, dkb, progs, mode)
+
+
+def test_stress_shapes_single_and_unique_subject():
+    """The paper's two assertion-set shapes: one subject holding every assertion (a 6,000-edge row)
+    and one assertion per subject (a permutation)."""
+    base = K.CONFIGS["c1"]
+    for deg in (("single", 6000), ("unique",)):
+        kb = K.generate(base.scaled(9000, seed=77, n_concepts=5, n_roles=2, degree=deg))
+        dkb = device_kb(kb)
+        r = Rng(5, 1)
+        progs = [np.array(pins.random_program(r, kb, r.randint(2, 4)).postfix(), np.uint64) for _ in range(80)]
+        progs += [P.compile_text(t) for t in ("(min 3000 r0 A1)", "(max 2999 r0 TOP)", "(exactly 6000 r0 TOP)",
+                                                "(all r0 A2)", "(some r0- A0)", "(min 1 r1- (not A3))")]
+        for mode in (0, H.HEDL_LEVELS, H.HEDL_PLAIN):
+            compare_batch(kb, dkb, progs, mode)
+
+
+def test_zipf_heavy_rows():
+    kb = K.generate(K.CONFIGS["c2"].scaled(40_000, seed=55, n_concepts=12, n_roles=3, n_props=3))
+    dkb = device_kb(kb)
+    progs = hyps.batch_hyps(kb, 5, 0, 300, lmax=30, dmax=7)
+    compare_batch(kb, dkb, progs, 0)
+
+
+def test_special_thresholds_and_counts(c1, c1_dev):
+    texts = ["(ge p0 -0.0)", "(le p0 0.0)", "(eq p0 -0.0)", "(ge p1 inf)", "(le p1 -inf)", "(ge p2 nan)",
+             "(not (le p3 nan))", "(min 0 r1 BOT)", "(max 4294967295 r2 TOP)", "(exactly 4294967295 r2 TOP)",
+             "(min 4294967295 r2 TOP)", "(exactly 0 r3- A5)", "TOP", "BOT", "(not TOP)", "A0"]
+    progs = [P.compile_text(t) for t in texts]
+    deep = np.array([P.insn(P.ATOM, 0, i % 50) for i in range(64)] + [P.insn(P.AND)] * 32 + [P.insn(P.OR)] * 31,
+                    np.uint64)
+    progs.append(deep)
+    for mode in MODES.values():
+        compare_batch(c1, c1_dev, progs, mode)
+
+
+def test_kb_without_roles_or_props():
+    kb = K.generate(K.CONFIGS["c1"].scaled(3000, seed=3, n_roles=0, n_props=0))
+    dkb = device_kb(kb)
+    progs = [P.compile_text(t) for t in ("(and A1 (not A2))", "(or A3 TOP)", "BOT")]
+    compare_batch(kb, dkb, progs, 0)
+
+
+def test_examples_counts(c1, c1_dev):
+    assert H.hedl_examples_counts(c1_dev.handle) == (c1.pos_idx.size, c1.neg_idx.size)
+
+
+def test_replay_and_workspace_checks(c1, c1_dev):
+    import torch
+    progs = hyps.batch_hyps(c1, 31, 0, 200)
+    flat, offs = P.pack_batch(progs)
+    plan = H.hedl_plan_batch(c1_dev.handle, flat, offs)
+    info = H.hedl_plan_info_get(plan)
+    ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
+    counts = torch.zeros((200, 4), dtype=torch.int32, device="cuda")
+    H.hedl_plan_execute(c1_dev.handle, plan, counts, None, ws)
+    first = counts.clone()
+    for _ in range(3):
+        counts.zero_()
+        H.hedl_plan_replay(c1_dev.handle, plan, counts, None, ws)
+        H.hedl_sync_status(c1_dev.handle)
+        assert torch.equal(counts, first)
+    small = torch.empty(info["workspace_bytes"] - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_plan_execute(c1_dev.handle, plan, counts, None, small)
+    assert e.value.code == -3
+    big = torch.empty(info["workspace_bytes"] + 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(H.HedlError) as e:   # large enough, but not 256-byte aligned
+        H.hedl_plan_execute(c1_dev.handle, plan, counts, None, big[1:])
+    assert e.value.code == -1
+
+
+def test_score_batch_one_shot(c1, c1_dev):
+    import torch
+    progs = hyps.batch_hyps(c1, 32, 0, 100)
+    flat, offs = P.pack_batch(progs)
+    n = H.hedl_workspace_size(c1_dev.handle, flat, offs)
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    counts = torch.zeros((100, 4), dtype=torch.int32, device="cuda")
+    H.hedl_score_batch(c1_dev.handle, flat, offs, counts, ws)
+    H.hedl_sync_status(c1_dev.handle)
+    okb = oracle.from_synth(c1)
+    oc, _, _ = oracle.eval_batch(okb, flat, offs, threads=4)
+    assert np.array_equal(counts.cpu().numpy().astype(np.int64), oc)
+
+
+def test_bounded_wait_reports_timeout(c1):
+    """A dependency nothing satisfies: the device wait gives up, the call reports
+    HEDL_ERR_TIMEOUT, and the context stays usable."""
+    dkb = device_kb(c1)
+    H.hedl_tuning_set(dkb.handle, wait_timeout_ms=100)
+    progs = hyps.batch_hyps(c1, 33, 0, 50)
+    flat, offs = P.pack_batch(progs)
+    with pytest.raises(H.HedlError) as e:
+        dkb.score(flat, offs, H.HEDL_TEST_UNSAT_DEP | H.HEDL_NO_GRAPH)
+    assert e.value.code == -5
+    compare_batch(c1, dkb, progs, 0)
+
+
+def test_bad_kb_rejected():
+    import torch
+    kb = K.generate(K.CONFIGS["c1"].scaled(500, seed=4, n_roles=2))
+    cases = {}
+    col = kb.col[0].copy()
+    k = int(np.nonzero(np.diff(kb.row_ptr[0].astype(np.int64)) >= 2)[0][0])
+    s = int(kb.row_ptr[0][k])
+    col[s], col[s + 1] = col[s + 1], col[s]
+    cases["unsorted row"] = dict(col0=col)
+    col = kb.col[0].copy()
+    col[s + 1] = col[s]
+    cases["duplicate assertion"] = dict(col0=col)
+    col = kb.col[0].copy()
+    col[0] = 500
+    cases["id out of range"] = dict(col0=col)
+    icol = kb.inv_col[0].copy()
+    icol[[0, -1]] = icol[[-1, 0]]
+    cases["not the transpose"] = dict(icol0=icol)
+    cb = kb.concept_bits.copy()
+    cb[0, kb.w - 1] |= np.uint32(1 << 31)
+    cases["concept tail"] = dict(cb=cb)
+    for what, ch in cases.items():
+        cols = list(kb.col)
+        icols = list(kb.inv_col)
+        if "col0" in ch:
+            cols[0] = ch["col0"]
+        if "icol0" in ch:
+            icols[0] = ch["icol0"]
+        with pytest.raises(H.HedlError) as e:
+            H.DeviceKB(kb.n, ch.get("cb", kb.concept_bits), kb.row_ptr, cols, kb.inv_row_ptr, icols, kb.prop_vals)
+        assert e.value.code == -6, what

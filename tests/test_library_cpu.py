@@ -1,0 +1,151 @@
+"""The C-ABI library without a GPU: it loads, exports every declared symbol,
+and its host-side logic (validation, planning) behaves (no compute calls)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2412_00802_gb300 as H
+from synth import hyps, kb as K, programs as P
+from tests import oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hedl.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2412_00802_gb300 import build
+    build.build()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hedl_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 18
+    out = subprocess.run(["nm", "-D", "--defined-only", H.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (hedl_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert sorted(H.SYMBOLS) == names
+    lib = H.library()
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_op_codes_agree_with_the_format():
+    hdr = open(HEADER).read()
+    ops = dict((k, int(v)) for k, v in re.findall(r"HEDL_OP_(\w+)\s*=\s*(\d+)", hdr))
+    for code, name in P.OP_NAMES.items():
+        assert ops[name] == code
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "hedl_oracle.c")).read()
+    for name, code in ops.items():
+        assert getattr(P, name) == code
+        assert re.search(rf"#define O_{name} {code}\b", src), name
+
+
+def test_row_words():
+    for n in (1, 31, 32, 33, 127, 128, 129, 10_000, 1_000_000):
+        w = (n + 31) // 32
+        assert H.hedl_row_words(n) == (w + 3) // 4 * 4
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return K.generate(K.CONFIGS["c1"])
+
+
+def plan_kb(kb):
+    return H.hedl_kb_plan_only(kb.n, kb.n_concepts, [kb.n_edges(r) for r in range(kb.n_roles)], kb.n_props)
+
+
+def test_validation_agrees_with_the_oracle(c1):
+    """Accept / reject decisions match the oracle's on malformed programs."""
+    hk = plan_kb(c1)
+    okb = oracle.from_synth(c1)
+    r = np.random.default_rng(3)
+    good = hyps.small_hyps(c1, 5, 30)
+    cases = []
+    for g in good:
+        cases.append(g)
+        g = g.copy()
+        i = r.integers(len(g))
+        kind = r.integers(5)
+        if kind == 0:
+            g[i] = (int(g[i]) & ~0xFF) | int(r.integers(15, 256))        # bad op
+        elif kind == 1:
+            g = g[:-1] if len(g) > 1 else g[:0]                            # truncated
+        elif kind == 2:
+            g = np.concatenate([g, g])                                    # two values left
+        elif kind == 3:
+            g[i] = P.insn(P.ATOM, 0, 50)                                  # id out of range
+        else:
+            g = np.concatenate([g, [P.insn(P.AND)]])                      # underflow
+        cases.append(g)
+    cases += [np.array([P.insn(P.ATOM, 0, 0)] * 65 + [P.insn(P.AND)] * 64, np.uint64),
+              np.array([P.insn(P.ATOM, 0, 0)] * 64 + [P.insn(P.AND)] * 63, np.uint64),
+              np.array([P.insn(P.EXISTS, 1, 8)], np.uint64), np.array([P.insn(P.DGE, 0, 4, 0)], np.uint64),
+              np.zeros(0, np.uint64)]
+    for c in cases:
+        want_ok = oracle.validate(okb, c) == 0
+        try:
+            H.hedl_validate(hk, c)
+            got_ok = True
+        except H.HedlError as e:
+            assert e.code == -2
+            got_ok = False
+        assert got_ok == want_ok, P.to_text(P.from_postfix(c)) if want_ok else c
+
+
+def test_plan_batch_rejects_and_names_the_program(c1):
+    hk = plan_kb(c1)
+    progs = hyps.small_hyps(c1, 5, 10)
+    progs[7] = np.array([P.insn(P.AND)], np.uint64)
+    flat, offs = P.pack_batch(progs)
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_plan_batch(hk, flat, offs)
+    assert "program 7" in str(e.value)
+
+
+def test_plan_sharing_and_levels(c1):
+    hk = plan_kb(c1)
+    x = "(and A1 (some r2 (min 2 r3- (or A4 (le p1 20)))))"
+    progs = [P.compile_text(x)] * 10 + [P.compile_text(f"(or A{i} {x})") for i in range(5)]
+    flat, offs = P.pack_batch(progs)
+    shared = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs))
+    plain = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, H.HEDL_NO_CSE))
+    # two role restrictions in x, evaluated once with sharing
+    assert shared["n_role_ops"] == 2 and plain["n_role_ops"] == 30
+    # filler, min-restriction, the shared conjunction (materialized), the roots
+    assert shared["n_levels"] == 4
+    assert shared["n_nodes"] < plain["n_nodes"]
+    assert shared["model_bytes"] < plain["model_bytes"]
+    # commuted operands and double negation share too
+    a = [P.compile_text("(and A1 (some r0 A2))"), P.compile_text("(and (some r0 A2) A1)"),
+         P.compile_text("(not (not (and A1 (some r0 A2))))")]
+    i = H.hedl_plan_info_get(H.hedl_plan_batch(hk, *P.pack_batch(a)))
+    assert i["n_role_ops"] == 1
+
+
+def test_workspace_accounts_for_slots(c1):
+    hk = plan_kb(c1)
+    progs = hyps.batch_hyps(c1, 9, 0, 200)
+    flat, offs = P.pack_batch(progs)
+    info = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs))
+    assert info["workspace_bytes"] >= info["n_slots"] * 4 * c1.wp
+    assert info["n_items"] == info["n_segments"] * -(-c1.wp // info["tile_words"])
+
+
+def test_planning_only_handle_refuses_launches(c1):
+    hk = plan_kb(c1)
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_sync_status(hk, stream=0)
+    assert e.value.code == -1
