@@ -49,6 +49,17 @@ def shard_batches(rank: int, world: int, warmup: int, steps: int):
     return list(range(base, base + warmup)), list(range(base + warmup, base + per))
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -132,9 +143,9 @@ def make_workload(seed_kb: int = 3):
     return K.generate(K.CONFIGS["c3"])
 
 
-def make_batch(kb, idx: int, gen=None):
+def make_batch(kb, idx: int, gen=None, count: int = None):
     from synth import hyps
-    return hyps.batch_hyps(kb, 1003, idx, BATCH, gen=gen)
+    return hyps.batch_hyps(kb, 1003, idx, count or BATCH, gen=gen)
 
 
 def cpu_baseline(kb, progs, budget_s: float = 12.0):
@@ -240,9 +251,7 @@ def run_ours(args, rank, world, local_rank):
     H.hedl_sync_status(dkb.handle)
     elapsed = t_all0.elapsed_time(t_all1) / 1000.0
     if dist:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dev)
         torch.distributed.barrier()
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     value = world * len(timed_ids) * BATCH / elapsed
@@ -338,7 +347,10 @@ def main():
     ap.add_argument("--flags", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="hypotheses per step (smaller only for profiling captures)")
     args = ap.parse_args()
+    globals()["BATCH"] = args.batch
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = int(os.environ.get("RANK", 0))
