@@ -241,6 +241,32 @@ int hedl_score_batch(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
 int hedl_eval_concept(hedl_kb *kb, const uint64_t *prog, uint32_t len, uint32_t *out_bits,
                       void *ws, size_t ws_bytes, unsigned flags, hedl_stream s);
 
+/* Size of the scratch array built into the library for
+ * hedl_eval_concept_noalloc (device memory held on every GPU that loads the
+ * library, until the process exits). */
+#define HEDL_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* hedl_eval_concept without a caller workspace and without allocating: for
+ * callers that cannot call cudaMalloc (or any device allocator) when they
+ * evaluate, and so cannot provide the workspace hedl_eval_concept needs.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *   - Scratch: a fixed HEDL_NOALLOC_SCRATCH_BYTES device array inside the
+ *     library; a program whose plan needs more (hedl_workspace_size with H = 1
+ *     and flags HEDL_NO_GRAPH tells) is rejected with
+ *     HEDL_ERR_WORKSPACE_TOO_SMALL before anything is launched.
+ *   - Set-up: the first call on each device (that device current) looks up
+ *     the array's device address; make that first call before any stream
+ *     capture.
+ *   - Sharing: every call uses the same array and brings its own zeroed
+ *     counters, so nothing carries over between calls; calls whose GPU work
+ *     overlaps race on the array and must be ordered by the caller.
+ *   - Calls no cudaMalloc / cudaFree or other allocating routine, and builds no
+ *     CUDA graph.
+ * prog (HOST uint64[len]) and out_bits (device, hedl_row_words(n) words) as in
+ * hedl_eval_concept.  Asynchronous. */
+int hedl_eval_concept_noalloc(hedl_kb *kb, const uint64_t *prog, uint32_t len, uint32_t *out_bits,
+                              hedl_stream s);
+
 /* Wait for s, then report (and clear) the first device-side failure recorded
  * by work launched on this handle since the last call: HEDL_OK,
  * HEDL_ERR_TIMEOUT, or HEDL_ERR_CUDA for an asynchronous CUDA error. */

@@ -36,12 +36,14 @@ HEDL_PLAIN = 4
 HEDL_LEVELS = 8
 HEDL_TEST_UNSAT_DEP = 0x100
 HEDL_MAX_STACK = 64
+HEDL_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 # exported symbols (one per declaration in include/hedl.h)
 SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free", "hedl_examples_set", "hedl_examples_counts",
            "hedl_validate", "hedl_plan_batch", "hedl_plan_info_get", "hedl_plan_free", "hedl_plan_execute",
            "hedl_plan_replay", "hedl_workspace_size", "hedl_score_batch", "hedl_eval_concept",
-           "hedl_sync_status", "hedl_tuning_get", "hedl_tuning_set", "hedl_last_error")
+           "hedl_eval_concept_noalloc", "hedl_sync_status", "hedl_tuning_get", "hedl_tuning_set",
+           "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -103,6 +105,7 @@ def library(path: Optional[str] = None):
             "hedl_workspace_size": (I, [P, P, P, U32, ctypes.c_uint, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_score_batch": (I, [P, P, P, U32, P, P, ctypes.c_size_t, ctypes.c_uint, P]),
             "hedl_eval_concept": (I, [P, P, U32, P, P, ctypes.c_size_t, ctypes.c_uint, P]),
+            "hedl_eval_concept_noalloc": (I, [P, P, U32, P, P]),
             "hedl_sync_status": (I, [P, P]),
             "hedl_tuning_get": (I, [P, ctypes.POINTER(hedl_tuning)]),
             "hedl_tuning_set": (I, [P, ctypes.POINTER(hedl_tuning)]),
@@ -294,6 +297,13 @@ def hedl_eval_concept(kb: KBHandle, prog, out_bits, ws, flags: int = 0, stream=N
     p = _host_u64(prog)
     _check(library().hedl_eval_concept(kb.ptr, p.ctypes.data if p.size else None, p.size, _dptr(out_bits),
                                        _dptr(ws), ws.numel() * ws.element_size(), flags, _stream(stream)))
+
+
+def hedl_eval_concept_noalloc(kb: KBHandle, prog, out_bits, stream=None):
+    """Evaluate one program into out_bits using the library's built-in scratch (no allocation)."""
+    p = _host_u64(prog)
+    _check(library().hedl_eval_concept_noalloc(kb.ptr, p.ctypes.data if p.size else None, p.size,
+                                               _dptr(out_bits), _stream(stream)))
 
 
 def hedl_sync_status(kb: KBHandle, stream=None):

@@ -258,7 +258,9 @@ void hedl_plan_free(hedl_plan *p) {
     delete p;
 }
 
-static int execute(hedl_kb *kb, const PlanImpl *pc, uint32_t *counts, uint32_t *out_bits, void *ws, size_t ws_bytes,
+}  // extern "C"
+
+int execute(hedl_kb *kb, const PlanImpl *pc, uint32_t *counts, uint32_t *out_bits, void *ws, size_t ws_bytes,
                    hedl_stream s, bool upload) {
     PlanImpl *p = const_cast<PlanImpl *>(pc);
     if (kb->plan_only) return fail(HEDL_ERR_INVALID_ARG, "planning-only handle: nothing can be launched");
@@ -328,6 +330,9 @@ static int execute(hedl_kb *kb, const PlanImpl *pc, uint32_t *counts, uint32_t *
     return e ? cuda_fail(e, "graph launch") : HEDL_OK;
 }
 
+extern "C" {
+
+
 int hedl_plan_execute(hedl_kb *kb, const hedl_plan *p, uint32_t *counts, uint32_t *out_bits, void *ws,
                       size_t ws_bytes, hedl_stream s) {
     if (!kb || !p) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
@@ -340,7 +345,9 @@ int hedl_plan_replay(hedl_kb *kb, const hedl_plan *p, uint32_t *counts, uint32_t
     return execute(kb, p->impl, counts, out_bits, ws, ws_bytes, s, false);
 }
 
-static int cached_plan(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, unsigned flags,
+}  // extern "C"
+
+int cached_plan(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, unsigned flags,
                        const PlanImpl **out) {
     if (!offs || (H && offs[H] && !progs)) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     if (H == 0) return fail(HEDL_ERR_INVALID_ARG, "empty batch (H = 0)");
@@ -362,6 +369,9 @@ static int cached_plan(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs,
     *out = np->impl;
     return HEDL_OK;
 }
+
+extern "C" {
+
 
 int hedl_workspace_size(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, unsigned flags,
                         size_t *bytes) {

@@ -172,6 +172,16 @@ struct PlanImpl {
 };
 
 int validate_program(const hedl_kb *kb, const uint64_t *prog, uint32_t len, std::string *why);
+
+}  // namespace hedl
+
+// api.cu: shared by the entry points (C++ linkage)
+int execute(hedl_kb *kb, const hedl::PlanImpl *pc, uint32_t *counts, uint32_t *out_bits, void *ws, size_t ws_bytes,
+            hedl_stream s, bool upload);
+int cached_plan(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, unsigned flags,
+                const hedl::PlanImpl **out);
+
+namespace hedl {
 int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
                unsigned flags, PlanImpl **out);
 uint64_t hash_programs(const uint64_t *progs, const uint32_t *offs, uint32_t H);
