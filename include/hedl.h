@@ -275,11 +275,14 @@ int hedl_sync_status(hedl_kb *kb, hedl_stream s);
 /* ------------------------------------------------------------------ tuning */
 
 typedef struct {
-    uint32_t warps_per_cta;    /* 4, 8 or 16 */
+    uint32_t warps_per_cta;    /* 4, 8, 16 or 32 */
     uint32_t words_per_lane;   /* 1 or 4: bitset words a lane holds per pass */
     uint32_t rounds;           /* warp passes per work item (tile = warps*32*words_per_lane*rounds words) */
     uint32_t ctas_per_sm;      /* 0 = as many as fit */
     uint32_t wait_timeout_ms;  /* bound of every device-side dependency wait */
+    uint32_t stage_fillers;    /* 1: copy a role restriction's filler row into shared memory once per
+                                  work item when it fits (then a segment reads at most one role
+                                  restriction); 0: gather filler bits from global memory */
 } hedl_tuning;
 
 int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t);

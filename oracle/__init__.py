@@ -115,11 +115,13 @@ class OracleKB:
             s = np.asarray(s, dtype=np.uint32)
             o = np.asarray(o, dtype=np.uint32)
             if s.size:
-                key = s.astype(np.uint64) * np.uint64(max(n, 1)) + o.astype(np.uint64)
-                if np.unique(key).size != key.size:
-                    raise ValueError("role assertions must be a set (duplicate pair)")
                 if int(s.max()) >= n or int(o.max()) >= n:
                     raise ValueError("assertion names an individual >= n")
+                key = s.astype(np.uint64) * np.uint64(max(n, 1)) + o.astype(np.uint64)
+                # strictly increasing keys are duplicate-free; otherwise sort to check
+                if not (key.size < 2 or bool(np.all(key[1:] > key[:-1]))):
+                    if np.unique(key).size != key.size:
+                        raise ValueError("role assertions must be a set (duplicate pair)")
             subj.append(s)
             obj.append(o)
             offs.append(offs[-1] + s.size)

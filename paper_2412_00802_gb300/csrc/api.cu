@@ -117,6 +117,9 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
     }
     cudaError_t e = cudaGetDevice(&kb->device);
     if (!e) e = cudaDeviceGetAttribute(&kb->n_sms, cudaDevAttrMultiProcessorCount, kb->device);
+    int optin = 0;
+    if (!e) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, kb->device);
+    if (!e) kb->smem_optin = (size_t)optin;
     if (!e) e = cudaMalloc(&kb->status_dev, 8 * sizeof(uint32_t));
     if (!e) e = cudaMemsetAsync(kb->status_dev, 0, 8 * sizeof(uint32_t), (cudaStream_t)s);
     if (!e && d->n_roles) e = cudaMalloc(&kb->csr_dev, sizeof(DevCSR) * kb->csr_host.size());
@@ -425,13 +428,24 @@ int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t) {
     t->rounds = kb->tuning.rounds;
     t->ctas_per_sm = kb->tuning.ctas_per_sm;
     t->wait_timeout_ms = kb->tuning.timeout_ms;
+    t->stage_fillers = kb->tuning.stage;
     return HEDL_OK;
 }
 
 int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
     if (!kb || !t) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
-    if (!(t->warps_per_cta == 4 || t->warps_per_cta == 8 || t->warps_per_cta == 16))
-        return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta must be 4, 8 or 16");
+    if (!(t->warps_per_cta == 4 || t->warps_per_cta == 8 || t->warps_per_cta == 16 || t->warps_per_cta == 32))
+        return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta must be 4, 8, 16 or 32");
+    if (t->stage_fillers > 1) return fail(HEDL_ERR_INVALID_ARG, "stage_fillers must be 0 or 1");
+    {
+        Tuning probe = kb->tuning;
+        probe.warps = t->warps_per_cta;
+        probe.wpl = t->words_per_lane;
+        if (stack_smem_bytes(probe) + 16 > kb->smem_optin)
+            return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta x words_per_lane: the interpreter's stack (" +
+                                                  std::to_string(stack_smem_bytes(probe)) +
+                                                  " bytes) does not fit in a CTA's shared memory");
+    }
     if (!(t->words_per_lane == 1 || t->words_per_lane == 4))
         return fail(HEDL_ERR_INVALID_ARG, "words_per_lane must be 1 or 4");
     if (t->rounds < 1 || t->rounds > 64) return fail(HEDL_ERR_INVALID_ARG, "rounds must be in 1..64");
@@ -442,6 +456,7 @@ int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
     kb->tuning.rounds = t->rounds;
     kb->tuning.ctas_per_sm = t->ctas_per_sm;
     kb->tuning.timeout_ms = t->wait_timeout_ms;
+    kb->tuning.stage = t->stage_fillers;
     drop_cached_plan(kb);
     return HEDL_OK;
 }

@@ -100,6 +100,17 @@ __device__ __forceinline__ bool role_pred(uint32_t kind, uint32_t cnt, uint32_t 
     }
 }
 
+// Streaming read of KB arrays (CSR): read-only for the kernel's lifetime and
+// used once per pass, so they do not take L1 lines from the filler bitsets.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+constexpr uint32_t NO_EDGE = 0xFFFFFFFFu;  // never a valid individual id (ids < 2^31)
+constexpr int ROLE_UNROLL = 4;             // 32-edge chunks in flight per warp
+
 // Role restriction over the warp's 32*WPL words (Algorithms 3-8 of the
 // paper, recast): for each word, the warp streams the CSR edge range of the
 // word's 32 individuals in coalesced chunks of 32 edges; lane e tests the
@@ -107,6 +118,10 @@ __device__ __forceinline__ bool role_pred(uint32_t kind, uint32_t cnt, uint32_t 
 // counts the set bits that fall inside its own row.  Counts stay in registers
 // (no atomics, no counter matrix); the walk stops as soon as every lane's
 // answer is decided.  FORALL counts successors outside the filler.
+//
+// Latency: ROLE_UNROLL chunks are issued together (all their column loads,
+// then all their filler gathers), and the next word's row pointers are
+// fetched while the current word is walked.
 template <int WPL>
 __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *filler, uint32_t kind, uint32_t n_arg,
                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
@@ -115,6 +130,15 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
     const uint64_t cap = decide_cap(kind, n_arg);
     const uint32_t *__restrict__ rp = g.rp;
     const uint32_t *__restrict__ col = g.col;
+    // row pointers of the first word
+    uint32_t nlo = 0, nhi = 0;
+    {
+        const uint32_t i = wb * 32u + lane;
+        if (wb < n_words && i < n) {
+            nlo = ld_stream(rp + i);
+            nhi = ld_stream(rp + i + 1);
+        }
+    }
 #pragma unroll 1
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
@@ -124,10 +148,13 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
             if (w < n_words) {
                 const uint32_t i = w * 32u + lane;
                 const bool valid = i < n;
-                uint32_t lo = 0, hi = 0;
-                if (valid) {
-                    lo = __ldg(rp + i);
-                    hi = __ldg(rp + i + 1);
+                const uint32_t lo = nlo, hi = nhi;
+                {   // prefetch the next word's row pointers
+                    const uint32_t i2 = i + 32u;
+                    if (w + 1 < n_words && i2 < n) {
+                        nlo = ld_stream(rp + i2);
+                        nhi = ld_stream(rp + i2 + 1);
+                    }
                 }
                 const uint32_t nv = min(32u, n - w * 32u);
                 const uint32_t e0 = __shfl_sync(FULL, lo, 0);
@@ -135,18 +162,26 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
                 uint32_t cnt = 0;
                 if (cap > 0) {
 #pragma unroll 1
-                    for (uint32_t k0 = e0; k0 < e1; k0 += 32u) {
-                        const uint32_t k = k0 + lane;
-                        uint32_t hit = 0;
-                        if (k < e1) {
-                            const uint32_t b = __ldg(col + k);
-                            hit = ((filler[b >> 5] >> (b & 31u)) & 1u) ^ neg;
+                    for (uint32_t k0 = e0; k0 < e1; k0 += 32u * ROLE_UNROLL) {
+                        uint32_t b[ROLE_UNROLL];
+#pragma unroll
+                        for (int u = 0; u < ROLE_UNROLL; ++u) {
+                            const uint32_t k = k0 + 32u * u + lane;
+                            b[u] = k < e1 ? ld_stream(col + k) : NO_EDGE;
                         }
-                        const uint32_t m = __ballot_sync(FULL, hit);
-                        const uint32_t a0 = lo > k0 ? lo - k0 : 0u;
-                        const uint32_t a1 = hi > k0 ? min(hi - k0, 32u) : 0u;
-                        if (a0 < a1) cnt += __popc(m & range_mask(a0, a1));
-                        const bool done = !valid || hi <= k0 + 32u || (uint64_t)cnt >= cap;
+                        uint32_t hit[ROLE_UNROLL];
+#pragma unroll
+                        for (int u = 0; u < ROLE_UNROLL; ++u)
+                            hit[u] = b[u] != NO_EDGE ? (((filler[b[u] >> 5] >> (b[u] & 31u)) & 1u) ^ neg) : 0u;
+#pragma unroll
+                        for (int u = 0; u < ROLE_UNROLL; ++u) {
+                            const uint32_t m = __ballot_sync(FULL, hit[u]);
+                            const uint32_t kk = k0 + 32u * u;
+                            const uint32_t a0 = lo > kk ? min(lo - kk, 32u) : 0u;
+                            const uint32_t a1 = hi > kk ? min(hi - kk, 32u) : 0u;
+                            if (a0 < a1) cnt += __popc(m & range_mask(a0, a1));
+                        }
+                        const bool done = !valid || hi <= k0 + 32u * ROLE_UNROLL || (uint64_t)cnt >= cap;
                         if (__all_sync(FULL, done)) break;
                     }
                 }

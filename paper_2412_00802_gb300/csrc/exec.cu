@@ -34,6 +34,8 @@ struct Smem {
     uint32_t stk[NW][STACK_MAX][WPL][32];
     uint32_t item;
     uint32_t ok;
+    uint32_t pad[2];
+    uint32_t filler[1];   // staged plans: the segment's filler row (wp words) from here on
 };
 
 __device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_groups, uint32_t item) {
@@ -46,7 +48,7 @@ __device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_g
     return lo;
 }
 
-template <int NW, int WPL>
+template <int NW, int WPL, bool STAGE>
 __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg, uint32_t tile,
                          Smem<NW, WPL> &sm, uint32_t *slots, uint32_t *acc) {
     const KBView &kb = A.kb;
@@ -105,9 +107,13 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
             default: {  // D_ROLE
                 const uint32_t inv = (d.op >> 8) & 1u;
                 const DevCSR g = kb.csr[2u * d.a + inv];
-                const uint32_t *filler = (d.ref & REF_SLOT) ? slots + (uint64_t)(d.ref & ~REF_SLOT) * kb.wp
-                                                            : kb.concepts + (uint64_t)d.ref * kb.wp;
-                role_words<WPL>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                if constexpr (STAGE) {
+                    role_words<WPL>(g, sm.filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                } else {
+                    const uint32_t *filler = (d.ref & REF_SLOT) ? slots + (uint64_t)(d.ref & ~REF_SLOT) * kb.wp
+                                                                : kb.concepts + (uint64_t)d.ref * kb.wp;
+                    role_words<WPL>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                }
                 break;
             }
             }
@@ -162,7 +168,16 @@ __device__ bool wait_deps(const PlanHeader &hd, const uint32_t *deps, const Seg 
     return true;
 }
 
-template <int NW, int WPL>
+// Copy the segment's filler row into shared memory (all threads of the CTA).
+__device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *slots, uint32_t ref, uint32_t *dst) {
+    const uint32_t *src = (ref & REF_SLOT) ? slots + (uint64_t)(ref & ~REF_SLOT) * kb.wp
+                                           : kb.concepts + (uint64_t)ref * kb.wp;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (uint32_t q = threadIdx.x; q < kb.wp / 4; q += blockDim.x) d4[q] = s4[q];
+}
+
+template <int NW, int WPL, bool STAGE>
 __global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
@@ -202,7 +217,13 @@ __global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
             __syncthreads();
             if (!sm.ok) break;
         }
-        run_tile<NW, WPL>(A, hd, seg, tile, sm, slots, acc);
+        if constexpr (STAGE) {
+            if (seg.filler != NO_FILLER) {
+                stage_filler(A.kb, slots, seg.filler, sm.filler);
+                __syncthreads();
+            }
+        }
+        run_tile<NW, WPL, STAGE>(A, hd, seg, tile, sm, slots, acc);
         __syncthreads();
         if (threadIdx.x == 0 && A.use_queue) {
             __threadfence();
@@ -227,26 +248,42 @@ __global__ void finalize_kernel(KBView kb, const uint8_t *ws, uint32_t *counts) 
 
 using KernelFn = void (*)(ExecArgs);
 
-KernelFn pick(uint32_t warps, uint32_t wpl) {
+template <bool STAGE>
+KernelFn pick_t(uint32_t warps, uint32_t wpl) {
     if (wpl == 4) {
-        if (warps == 4) return exec_kernel<4, 4>;
-        if (warps == 16) return exec_kernel<16, 4>;
-        return exec_kernel<8, 4>;
+        if (warps == 4) return exec_kernel<4, 4, STAGE>;
+        if (warps == 16) return exec_kernel<16, 4, STAGE>;
+        if (warps == 32) return exec_kernel<32, 4, STAGE>;
+        return exec_kernel<8, 4, STAGE>;
     }
-    if (warps == 4) return exec_kernel<4, 1>;
-    if (warps == 16) return exec_kernel<16, 1>;
-    return exec_kernel<8, 1>;
+    if (warps == 4) return exec_kernel<4, 1, STAGE>;
+    if (warps == 16) return exec_kernel<16, 1, STAGE>;
+    if (warps == 32) return exec_kernel<32, 1, STAGE>;
+    return exec_kernel<8, 1, STAGE>;
+}
+
+KernelFn pick(uint32_t warps, uint32_t wpl, bool stage) {
+    return stage ? pick_t<true>(warps, wpl) : pick_t<false>(warps, wpl);
+}
+
+size_t smem_bytes(const hedl_kb *kb, const Tuning &t, bool stage) {
+    size_t b = stack_smem_bytes(t) + 16;
+    if (stage) b += 4ull * kb->wp;
+    return b;
 }
 
 }  // namespace
 
-size_t exec_smem_bytes(const Tuning &t) {
-    return sizeof(uint32_t) * (size_t)t.warps * STACK_MAX * t.wpl * 32 + 16;
+bool use_staging(const hedl_kb *kb, const Tuning &t) {
+    return t.stage && smem_bytes(kb, t, true) <= kb->smem_optin;
 }
 
+size_t exec_smem_bytes(const Tuning &t) { return stack_smem_bytes(t) + 16; }
+
 int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm) {
-    KernelFn fn = pick(t.warps, t.wpl);
-    size_t smem = exec_smem_bytes(t);
+    const bool stage = use_staging(kb, t);
+    KernelFn fn = pick(t.warps, t.wpl, stage);
+    size_t smem = smem_bytes(kb, t, stage);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, (int)(t.warps * 32), smem);
@@ -257,8 +294,8 @@ int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t
                 void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Tuning &t = p->tuning;
-    KernelFn fn = pick(t.warps, t.wpl);
-    size_t smem = exec_smem_bytes(t);
+    KernelFn fn = pick(t.warps, t.wpl, p->staged);
+    size_t smem = smem_bytes(kb, t, p->staged);
     int bps = p->bps;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     if (t.ctas_per_sm && (int)t.ctas_per_sm < bps) bps = (int)t.ctas_per_sm;

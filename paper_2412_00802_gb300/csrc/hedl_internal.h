@@ -57,6 +57,8 @@ inline uint32_t dop(uint32_t w) { return w & 0xFF; }
 constexpr uint32_t NO_SLOT = 0xFFFFFFFFu;
 constexpr uint32_t NO_HYP = 0xFFFFFFFFu;
 
+constexpr uint32_t NO_FILLER = 0xFFFFFFFFu;
+
 struct Seg {
     uint32_t code_off;   // index into code[]
     uint32_t code_len;
@@ -64,8 +66,8 @@ struct Seg {
     uint32_t hyp;        // NO_HYP if not a hypothesis root
     uint32_t dep_off;    // index into deps[]
     uint32_t dep_cnt;
+    uint32_t filler;     // filler ref of its role leaf (staged plans hold at most one), or NO_FILLER
     uint32_t level;
-    uint32_t stack;      // stack depth its code needs
 };
 
 struct Group {
@@ -98,13 +100,19 @@ constexpr int STACK_MAX = 16;
 
 // ------------------------------------------------------------------ host objects
 struct Tuning {
-    uint32_t warps = 8;
+    uint32_t warps = 32;
     uint32_t wpl = 1;        // words per lane
     uint32_t rounds = 1;
     uint32_t ctas_per_sm = 0;
     uint32_t timeout_ms = 2000;
+    uint32_t stage = 1;      // stage role fillers in shared memory when a row fits
     uint32_t tile_words() const { return warps * 32u * wpl * rounds; }
 };
+
+constexpr size_t SMEM_OPTIN_DEFAULT = 232448;   // bytes of shared memory a CTA may opt into
+
+// Shared-memory bytes of the interpreter's stack (per CTA).
+inline size_t stack_smem_bytes(const Tuning &t) { return sizeof(uint32_t) * (size_t)t.warps * STACK_MAX * t.wpl * 32; }
 
 struct PlanImpl;
 
@@ -126,6 +134,7 @@ struct hedl_kb {
     int device = 0;
     int n_sms = 0;
     bool plan_only = false;                 // sizes only, no device state
+    size_t smem_optin = hedl::SMEM_OPTIN_DEFAULT;
     void *capture_stream = nullptr;         // private stream that CUDA graphs are captured on
     hedl::Tuning tuning;
     // one cached plan for the one-shot calls
@@ -159,6 +168,7 @@ struct PlanImpl {
     uint32_t max_stack = 0;
     Tuning tuning;
     int bps = 0;                         // resident CTAs per SM of the interpreter
+    bool staged = false;                 // role fillers staged in shared memory (one role leaf per segment)
     // plain path: validated programs
     std::vector<uint64_t> progs;
     std::vector<uint32_t> offs;
@@ -189,6 +199,8 @@ uint64_t hash_programs(const uint64_t *progs, const uint32_t *offs, uint32_t H);
 // exec.cu / plain.cu / kb.cu launchers (return cudaError_t as int)
 int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t *out_bits, void *ws,
                 void *stream);
+// Whether plans for this KB and launch shape stage role fillers in shared memory.
+bool use_staging(const hedl_kb *kb, const Tuning &t);
 int launch_plain(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t *out_bits, void *ws,
                  void *stream);
 int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm);

@@ -276,6 +276,38 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         } else need[i] = 1;
     }
 
+    // With staged fillers each segment may read one role restriction (its
+    // filler is copied to shared memory once per work item): any further role
+    // restriction in a segment's inline expansion becomes its own segment.
+    const bool staged = use_staging(kb, kb->tuning);
+    p->staged = staged;
+    if (staged) {
+        std::vector<int32_t> seg_roots;
+        for (uint32_t i = 0; i < NN; ++i)
+            if (mat[i]) seg_roots.push_back((int32_t)i);
+        for (uint32_t h = 0; h < H; ++h)
+            if (!mat[roots[h]]) seg_roots.push_back(roots[h]);
+        std::vector<int32_t> dfs;
+        for (int32_t r : seg_roots) {
+            bool kept = false;
+            dfs.clear();
+            dfs.push_back(r);
+            while (!dfs.empty()) {
+                int32_t i = dfs.back();
+                dfs.pop_back();
+                if (i != r && mat[i]) continue;
+                const PNode &n = nodes[i];
+                if (is_role(n.op)) {
+                    if (kept && i != r) mat[i] = 1;
+                    kept = true;
+                    continue;   // its filler is a slot or a concept row, not inline
+                }
+                if (n.k1 >= 0) dfs.push_back(n.k1);
+                if (n.k0 >= 0) dfs.push_back(n.k0);
+            }
+        }
+    }
+
     // slots and segments
     std::vector<uint32_t> slot_of(NN, NO_SLOT);
     uint32_t n_slots = 0;
@@ -294,6 +326,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         s.code_off = (uint32_t)code.size();
         s.out_slot = out_slot;
         s.hyp = hyp;
+        s.filler = NO_FILLER;
         std::vector<uint32_t> reads;
         uint32_t rk = 0xFFFFFFFFu;
         // iterative post-order emission, larger stack need first
@@ -337,6 +370,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                         reads.push_back(slot_of[c]);
                     }
                     if (rk == 0xFFFFFFFFu) rk = n.a * 2 + n.inv;
+                    if (s.filler == NO_FILLER) s.filler = d.ref;
                     const DevCSR &g = kb->csr_host[2 * n.a + n.inv];
                     model += 4 * (N + 1) + 4ull * g.n_edges + B;
                     p->info.n_role_ops++;
@@ -378,7 +412,6 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
             }
         }
         s.code_len = (uint32_t)code.size() - s.code_off;
-        s.stack = (uint32_t)maxdepth;
         p->max_stack = std::max(p->max_stack, (uint32_t)maxdepth);
         model += B;  // output row (slot, instance set or score input)
         if (hyp != NO_HYP) model += 2 * B + 16;
@@ -400,7 +433,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
             s.code_len = 1;
             s.out_slot = NO_SLOT;
             s.hyp = h;
-            s.stack = 1;
+            s.filler = NO_FILLER;
             DInsn d{};
             d.op = D_SLOT;
             d.ref = slot_of[roots[h]];

@@ -68,11 +68,23 @@ def test_c1_batched_shapes(c1, c1_dev):
 
 @pytest.mark.parametrize("tuning", [dict(warps_per_cta=4, words_per_lane=4, rounds=2),
                                     dict(warps_per_cta=16, words_per_lane=1, rounds=3),
-                                    dict(warps_per_cta=8, words_per_lane=4, rounds=1, ctas_per_sm=1)])
+                                    dict(warps_per_cta=8, words_per_lane=4, rounds=1, ctas_per_sm=1),
+                                    dict(warps_per_cta=32, words_per_lane=1, stage_fillers=1),
+                                    dict(warps_per_cta=8, words_per_lane=1, stage_fillers=0),
+                                    dict(warps_per_cta=16, words_per_lane=4, rounds=2, stage_fillers=0)])
 def test_launch_shapes(c1, tuning):
     dkb = device_kb(c1)
     H.hedl_tuning_set(dkb.handle, **tuning)
     compare_batch(c1, dkb, hyps.batch_hyps(c1, 22, 0, 300), 0)
+
+
+def test_launch_shape_that_does_not_fit_is_rejected(c1):
+    dkb = device_kb(c1)
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_tuning_set(dkb.handle, warps_per_cta=32, words_per_lane=4)
+    assert e.value.code == -1
+    with pytest.raises(H.HedlError):
+        H.hedl_tuning_set(dkb.handle, warps_per_cta=12)
 
 
 def test_eval_concept(c1, c1_dev):
@@ -227,3 +239,28 @@ def test_bad_kb_rejected():
         with pytest.raises(H.HedlError) as e:
             H.DeviceKB(kb.n, ch.get("cb", kb.concept_bits), kb.row_ptr, cols, kb.inv_row_ptr, icols, kb.prop_vals)
         assert e.value.code == -6, what
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return K.generate(K.CONFIGS["c3"])
+
+
+@pytest.mark.parametrize("stage", [1, 0])
+def test_c3_full_size_batch_sampled(c3, stage):
+    """Workload 3 at full size (N = 1,000,000) in the bench's launch configuration: a whole
+    4,096-hypothesis batch on the GPU; 48 sampled hypotheses checked bit-exactly (sets and
+    counts) against the oracle, and the counts of all against the plain path."""
+    dkb = device_kb(c3)
+    H.hedl_tuning_set(dkb.handle, stage_fillers=stage)
+    progs = hyps.batch_hyps(c3, 1003, 0, 4096, gen=hyps.TreeGen(c3, 1003, share=0.3))
+    sample = sorted(set(list(range(8)) + list(range(0, 4096, 97)) + [4095]))
+    counts, _ = compare_batch(c3, dkb, progs, 0, sample=sample, check_bits=False)
+    # instance sets of the sampled hypotheses, through eval (bench-shaped plan for the counts above)
+    okb = oracle.from_synth(c3)
+    for h in sample[:12]:
+        got = K.unpack_bits(dkb.eval(progs[h]), c3.n)
+        assert np.array_equal(got, oracle.eval_program(okb, progs[h])), h
+    if stage:
+        plain = dkb.score(*P.pack_batch(progs), H.HEDL_PLAIN)
+        assert np.array_equal(plain, counts)
