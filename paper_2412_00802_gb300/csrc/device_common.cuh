@@ -109,29 +109,28 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
 }
 
 constexpr uint32_t NO_EDGE = 0xFFFFFFFFu;  // never a valid individual id (ids < 2^31)
-constexpr int ROLE_UNROLL = 4;             // 32-edge chunks in flight per warp
+constexpr int ROLE_BLOCK = 8;              // 32-edge chunks walked per step (<= 32)
 
 // Role restriction over the warp's 32*WPL words (Algorithms 3-8 of the
-// paper, recast): for each word, the warp streams the CSR edge range of the
-// word's 32 individuals in coalesced chunks of 32 edges; lane e tests the
-// filler bit of edge e's object, a ballot packs the 32 tests, and lane i
-// counts the set bits that fall inside its own row.  Counts stay in registers
-// (no atomics, no counter matrix); the walk stops as soon as every lane's
-// answer is decided.  FORALL counts successors outside the filler.
-//
-// Latency: ROLE_UNROLL chunks are issued together (all their column loads,
-// then all their filler gathers), and the next word's row pointers are
-// fetched while the current word is walked.
+// paper, recast).  For each word (32 individuals) the warp walks the word's
+// CSR edge range, a block of ROLE_BLOCK chunks of 32 edges at a time: lane e
+// loads edge e of each chunk (coalesced), tests the filler bit of its object,
+// and a ballot packs each chunk's tests into a mask that lane c keeps for
+// chunk c.  A warp scan turns the masks' popcounts into prefix counts, so
+// lane i counts the hits inside its own row [lo, hi) with two rank lookups,
+// however many chunks the row spans.  Counts stay in registers (no atomics,
+// no counter matrix), and the walk stops once every lane's answer is decided.
+// FORALL counts successors outside the filler.
 template <int WPL>
 __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *filler, uint32_t kind, uint32_t n_arg,
                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
                                            uint32_t (&v)[WPL]) {
+    constexpr uint32_t BE = 32u * ROLE_BLOCK;     // edges per block
     const uint32_t neg = kind == HEDL_OP_FORALL ? 1u : 0u;
     const uint64_t cap = decide_cap(kind, n_arg);
     const uint32_t *__restrict__ rp = g.rp;
     const uint32_t *__restrict__ col = g.col;
-    // row pointers of the first word
-    uint32_t nlo = 0, nhi = 0;
+    uint32_t nlo = 0, nhi = 0;   // row pointers of the next word, fetched ahead
     {
         const uint32_t i = wb * 32u + lane;
         if (wb < n_words && i < n) {
@@ -149,7 +148,7 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
                 const uint32_t i = w * 32u + lane;
                 const bool valid = i < n;
                 const uint32_t lo = nlo, hi = nhi;
-                {   // prefetch the next word's row pointers
+                {
                     const uint32_t i2 = i + 32u;
                     if (w + 1 < n_words && i2 < n) {
                         nlo = ld_stream(rp + i2);
@@ -159,29 +158,49 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
                 const uint32_t nv = min(32u, n - w * 32u);
                 const uint32_t e0 = __shfl_sync(FULL, lo, 0);
                 const uint32_t e1 = __shfl_sync(FULL, hi, nv - 1);
+                // my row relative to the word's first edge (empty for lanes past n)
+                const uint32_t r0 = valid ? lo - e0 : 0u, r1 = valid ? hi - e0 : 0u;
                 uint32_t cnt = 0;
                 if (cap > 0) {
 #pragma unroll 1
-                    for (uint32_t k0 = e0; k0 < e1; k0 += 32u * ROLE_UNROLL) {
-                        uint32_t b[ROLE_UNROLL];
+                    for (uint32_t rb = 0; rb < e1 - e0; rb += BE) {
+                        const uint32_t base = e0 + rb;
+                        uint32_t hit[ROLE_BLOCK];
 #pragma unroll
-                        for (int u = 0; u < ROLE_UNROLL; ++u) {
-                            const uint32_t k = k0 + 32u * u + lane;
-                            b[u] = k < e1 ? ld_stream(col + k) : NO_EDGE;
+                        for (int u = 0; u < ROLE_BLOCK; ++u) {
+                            const uint32_t k = base + 32u * u + lane;
+                            hit[u] = k < e1 ? ld_stream(col + k) : NO_EDGE;
                         }
-                        uint32_t hit[ROLE_UNROLL];
 #pragma unroll
-                        for (int u = 0; u < ROLE_UNROLL; ++u)
-                            hit[u] = b[u] != NO_EDGE ? (((filler[b[u] >> 5] >> (b[u] & 31u)) & 1u) ^ neg) : 0u;
+                        for (int u = 0; u < ROLE_BLOCK; ++u)
+                            hit[u] = hit[u] != NO_EDGE ? (((filler[hit[u] >> 5] >> (hit[u] & 31u)) & 1u) ^ neg) : 0u;
+                        uint32_t mc = 0;   // lane c < ROLE_BLOCK: mask of chunk c
 #pragma unroll
-                        for (int u = 0; u < ROLE_UNROLL; ++u) {
+                        for (int u = 0; u < ROLE_BLOCK; ++u) {
                             const uint32_t m = __ballot_sync(FULL, hit[u]);
-                            const uint32_t kk = k0 + 32u * u;
-                            const uint32_t a0 = lo > kk ? min(lo - kk, 32u) : 0u;
-                            const uint32_t a1 = hi > kk ? min(hi - kk, 32u) : 0u;
-                            if (a0 < a1) cnt += __popc(m & range_mask(a0, a1));
+                            if (lane == (uint32_t)u) mc = m;
                         }
-                        const bool done = !valid || hi <= k0 + 32u * ROLE_UNROLL || (uint64_t)cnt >= cap;
+                        // exclusive prefix of the chunks' popcounts over lanes 0..ROLE_BLOCK-1
+                        const uint32_t pc = __popc(mc);
+                        uint32_t incl = pc;
+#pragma unroll
+                        for (int o = 1; o < ROLE_BLOCK; o <<= 1) {
+                            const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                            if (lane >= (uint32_t)o) incl += t;
+                        }
+                        const uint32_t excl = incl - pc;
+                        // hits before block-relative position x in [0, BE]
+                        auto rank = [&](uint32_t x) -> uint32_t {
+                            const uint32_t c = min(x >> 5, (uint32_t)ROLE_BLOCK - 1);
+                            const uint32_t e = __shfl_sync(FULL, excl, c);
+                            const uint32_t m = __shfl_sync(FULL, mc, c);
+                            const uint32_t sh = x - 32u * c;   // 0..32
+                            return e + __popc(sh >= 32u ? m : (m & ((1u << sh) - 1u)));
+                        };
+                        const uint32_t a = r0 > rb ? min(r0 - rb, BE) : 0u;
+                        const uint32_t z = r1 > rb ? min(r1 - rb, BE) : 0u;
+                        cnt += rank(z) - rank(a);
+                        const bool done = !valid || r1 <= rb + BE || (uint64_t)cnt >= cap;
                         if (__all_sync(FULL, done)) break;
                     }
                 }
