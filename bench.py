@@ -213,6 +213,13 @@ def run_ours(args, rank, world, local_rank):
     warm_ids, timed_ids = shard_batches(rank, world, args.warmup, args.steps)
     ids = warm_ids + timed_ids
     batches = {i: P.pack_batch(make_batch(kb, i, gen)) for i in ids}
+    tune_s = None
+    if not args.no_tune:
+        # launch shape picked by the autotuner on a probe batch (not a timed one)
+        probe = P.pack_batch(make_batch(kb, 10_000 + rank, gen, count=512))
+        t0 = time.perf_counter()
+        dkb.autotune(*probe)
+        tune_s = time.perf_counter() - t0
 
     stream = torch.cuda.current_stream(dev)
     # ---- plan every batch (host), give each its own workspace, upload once
@@ -317,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": BATCH, "l2": "inputs larger than L2 (KB ~0.95 GB + workspaces)",
                    "parallelism": f"replicas{world}", "flags": args.flags,
-                   "tuning": H.hedl_tuning_get(dkb.handle)},
+                   "tuning": H.hedl_tuning_get(dkb.handle), "autotune_s": tune_s},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "kernel": "exec_kernel (persistent segment interpreter)",
@@ -347,6 +354,7 @@ def main():
     ap.add_argument("--flags", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="hypotheses per step (smaller only for profiling captures)")
     args = ap.parse_args()

@@ -283,12 +283,31 @@ typedef struct {
     uint32_t stage_fillers;    /* 1: copy a role restriction's filler row into shared memory once per
                                   work item when it fits (then a segment reads at most one role
                                   restriction); 0: gather filler bits from global memory */
+    uint32_t role_block;       /* 4 or 8: 32-edge chunks the role walk loads per step */
 } hedl_tuning;
 
 int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t);
 /* Set the launch shape used by later plans and executions on this handle;
  * rejects unsupported values with HEDL_ERR_INVALID_ARG. */
 int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t);
+
+/* Workspace bytes hedl_autotune needs for this probe batch: the largest plan
+ * over every candidate launch shape.  Host-only. */
+int hedl_autotune_workspace_size(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+                                 size_t *bytes);
+
+/* Autotuner for the launch shape (warps per CTA, words per lane, rounds per
+ * work item, chunks per role-walk step, filler staging).  No counterpart in
+ * the paper.  Each candidate shape plans the probe batch (HOST progs / offs as
+ * in hedl_plan_batch, scored against the handle's examples), runs it once,
+ * then times three replays with CUDA events on s; the fastest becomes the
+ * handle's tuning and is written to *chosen (may be NULL).  With cache_path
+ * (may be NULL), a result stored earlier for the same KB shape and GPU is
+ * reused without timing, and a new result is appended to that text file.
+ * ws (>= hedl_autotune_workspace_size, 256-byte aligned) is scratch for the
+ * duration of the call.  SYNCHRONIZES s.  On failure the tuning is unchanged. */
+int hedl_autotune(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, void *ws,
+                  size_t ws_bytes, const char *cache_path, hedl_stream s, hedl_tuning *chosen);
 
 /* Description of the calling thread's last failure ("" if none). */
 const char *hedl_last_error(void);

@@ -43,7 +43,7 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_validate", "hedl_plan_batch", "hedl_plan_info_get", "hedl_plan_free", "hedl_plan_execute",
            "hedl_plan_replay", "hedl_workspace_size", "hedl_score_batch", "hedl_eval_concept",
            "hedl_eval_concept_noalloc", "hedl_sync_status", "hedl_tuning_get", "hedl_tuning_set",
-           "hedl_last_error")
+           "hedl_autotune_workspace_size", "hedl_autotune", "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -71,7 +71,7 @@ class hedl_plan_info(ctypes.Structure):
 
 class hedl_tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("warps_per_cta", "words_per_lane", "rounds", "ctas_per_sm",
-                                                "wait_timeout_ms", "stage_fillers")]
+                                                "wait_timeout_ms", "stage_fillers", "role_block")]
 
 
 _lib = None
@@ -109,6 +109,8 @@ def library(path: Optional[str] = None):
             "hedl_sync_status": (I, [P, P]),
             "hedl_tuning_get": (I, [P, ctypes.POINTER(hedl_tuning)]),
             "hedl_tuning_set": (I, [P, ctypes.POINTER(hedl_tuning)]),
+            "hedl_autotune_workspace_size": (I, [P, P, P, U32, ctypes.POINTER(ctypes.c_size_t)]),
+            "hedl_autotune": (I, [P, P, P, U32, P, ctypes.c_size_t, ctypes.c_char_p, P, ctypes.POINTER(hedl_tuning)]),
             "hedl_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -321,6 +323,24 @@ def hedl_tuning_set(kb: KBHandle, **kw):
     _check(library().hedl_tuning_set(kb.ptr, ctypes.byref(t)))
 
 
+def hedl_autotune_workspace_size(kb: KBHandle, progs, offs) -> int:
+    p, o = _host_u64(progs), _host_u32(offs)
+    out = ctypes.c_size_t()
+    _check(library().hedl_autotune_workspace_size(kb.ptr, p.ctypes.data if p.size else None, o.ctypes.data,
+                                                  o.size - 1, ctypes.byref(out)))
+    return out.value
+
+
+def hedl_autotune(kb: KBHandle, progs, offs, ws, cache_path: Optional[str] = None, stream=None) -> Dict[str, int]:
+    """Time candidate launch shapes on the probe batch and keep the fastest; returns it."""
+    p, o = _host_u64(progs), _host_u32(offs)
+    t = hedl_tuning()
+    _check(library().hedl_autotune(kb.ptr, p.ctypes.data if p.size else None, o.ctypes.data, o.size - 1, _dptr(ws),
+                                   ws.numel() * ws.element_size(), cache_path.encode() if cache_path else None,
+                                   _stream(stream), ctypes.byref(t)))
+    return {k: int(getattr(t, k)) for k, _ in hedl_tuning._fields_}
+
+
 # ---------------------------------------------------------------------------- convenience owner
 class DeviceKB:
     """Device copy (torch tensors) of a KB given as host numpy arrays, registered with the library."""
@@ -384,6 +404,13 @@ class DeviceKB:
         if out_bits:
             return c, bits.cpu().numpy().view(np.uint32)
         return c
+
+    def autotune(self, progs, offs, cache_path: Optional[str] = None) -> Dict[str, int]:
+        """Pick the fastest launch shape on a probe batch (allocates its scratch with torch)."""
+        torch = self.torch
+        need = hedl_autotune_workspace_size(self.handle, progs, offs)
+        ws = torch.empty(need + 256 + 16 * (len(offs) - 1) + 256, dtype=torch.uint8, device=self.device)
+        return hedl_autotune(self.handle, progs, offs, ws, cache_path)
 
     def eval(self, prog, flags: int = 0) -> np.ndarray:
         torch = self.torch

@@ -429,6 +429,7 @@ int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t) {
     t->ctas_per_sm = kb->tuning.ctas_per_sm;
     t->wait_timeout_ms = kb->tuning.timeout_ms;
     t->stage_fillers = kb->tuning.stage;
+    t->role_block = kb->tuning.role_block;
     return HEDL_OK;
 }
 
@@ -437,6 +438,9 @@ int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
     if (!(t->warps_per_cta == 4 || t->warps_per_cta == 8 || t->warps_per_cta == 16 || t->warps_per_cta == 32))
         return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta must be 4, 8, 16 or 32");
     if (t->stage_fillers > 1) return fail(HEDL_ERR_INVALID_ARG, "stage_fillers must be 0 or 1");
+    if (!(t->role_block == 4 || t->role_block == 8)) return fail(HEDL_ERR_INVALID_ARG, "role_block must be 4 or 8");
+    if (t->words_per_lane == 4 && t->warps_per_cta == 32)
+        return fail(HEDL_ERR_INVALID_ARG, "words_per_lane 4 supports at most 16 warps per CTA");
     {
         Tuning probe = kb->tuning;
         probe.warps = t->warps_per_cta;
@@ -457,6 +461,7 @@ int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
     kb->tuning.ctas_per_sm = t->ctas_per_sm;
     kb->tuning.timeout_ms = t->wait_timeout_ms;
     kb->tuning.stage = t->stage_fillers;
+    kb->tuning.role_block = t->role_block;
     drop_cached_plan(kb);
     return HEDL_OK;
 }

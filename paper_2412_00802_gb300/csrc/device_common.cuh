@@ -108,12 +108,10 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
     return v;
 }
 
-constexpr uint32_t NO_EDGE = 0xFFFFFFFFu;  // never a valid individual id (ids < 2^31)
-constexpr int ROLE_BLOCK = 8;              // 32-edge chunks walked per step (<= 32)
 
 // Role restriction over the warp's 32*WPL words (Algorithms 3-8 of the
 // paper, recast).  For each word (32 individuals) the warp walks the word's
-// CSR edge range, a block of ROLE_BLOCK chunks of 32 edges at a time: lane e
+// CSR edge range, a block of BLK (<= 32) chunks of 32 edges at a time: lane e
 // loads edge e of each chunk (coalesced), tests the filler bit of its object,
 // and a ballot packs each chunk's tests into a mask that lane c keeps for
 // chunk c.  A warp scan turns the masks' popcounts into prefix counts, so
@@ -121,12 +119,15 @@ constexpr int ROLE_BLOCK = 8;              // 32-edge chunks walked per step (<=
 // however many chunks the row spans.  Counts stay in registers (no atomics,
 // no counter matrix), and the walk stops once every lane's answer is decided.
 // FORALL counts successors outside the filler.
-template <int WPL>
+// filler_inverted: the caller already complemented a FORALL filler.
+template <int WPL, int BLK>
 __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *filler, uint32_t kind, uint32_t n_arg,
                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
-                                           uint32_t (&v)[WPL]) {
+                                           uint32_t (&v)[WPL], bool filler_inverted = false) {
+    static_assert(BLK >= 1 && BLK <= 32, "a block holds 1..32 chunks");
+    constexpr int ROLE_BLOCK = BLK;
     constexpr uint32_t BE = 32u * ROLE_BLOCK;     // edges per block
-    const uint32_t neg = kind == HEDL_OP_FORALL ? 1u : 0u;
+    const uint32_t neg = (kind == HEDL_OP_FORALL && !filler_inverted) ? 1u : 0u;
     const uint64_t cap = decide_cap(kind, n_arg);
     const uint32_t *__restrict__ rp = g.rp;
     const uint32_t *__restrict__ col = g.col;
@@ -165,15 +166,15 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
 #pragma unroll 1
                     for (uint32_t rb = 0; rb < e1 - e0; rb += BE) {
                         const uint32_t base = e0 + rb;
+                        // Edge index clamped to the word's last edge: lanes past the end reload
+                        // a valid edge, and their bits lie beyond every row so no rank counts them.
                         uint32_t hit[ROLE_BLOCK];
 #pragma unroll
-                        for (int u = 0; u < ROLE_BLOCK; ++u) {
-                            const uint32_t k = base + 32u * u + lane;
-                            hit[u] = k < e1 ? ld_stream(col + k) : NO_EDGE;
-                        }
+                        for (int u = 0; u < ROLE_BLOCK; ++u)
+                            hit[u] = ld_stream(col + min(base + 32u * u + lane, e1 - 1u));
 #pragma unroll
                         for (int u = 0; u < ROLE_BLOCK; ++u)
-                            hit[u] = hit[u] != NO_EDGE ? (((filler[hit[u] >> 5] >> (hit[u] & 31u)) & 1u) ^ neg) : 0u;
+                            hit[u] = (__funnelshift_r(filler[hit[u] >> 5], 0u, hit[u]) & 1u) ^ neg;
                         uint32_t mc = 0;   // lane c < ROLE_BLOCK: mask of chunk c
 #pragma unroll
                         for (int u = 0; u < ROLE_BLOCK; ++u) {

@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_g
     return lo;
 }
 
-template <int NW, int WPL, bool STAGE>
+template <int NW, int WPL, bool STAGE, int BLK>
 __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg, uint32_t tile,
                          Smem<NW, WPL> &sm, uint32_t *slots, uint32_t *acc) {
     const KBView &kb = A.kb;
@@ -108,11 +108,12 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 const uint32_t inv = (d.op >> 8) & 1u;
                 const DevCSR g = kb.csr[2u * d.a + inv];
                 if constexpr (STAGE) {
-                    role_words<WPL>(g, sm.filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                    const uint32_t kind = (d.op >> 16) & 0xFFu;
+                    role_words<WPL, BLK>(g, sm.filler, kind, d.b, kb.n, kb.w, wb, lane, top, kind == HEDL_OP_FORALL);
                 } else {
                     const uint32_t *filler = (d.ref & REF_SLOT) ? slots + (uint64_t)(d.ref & ~REF_SLOT) * kb.wp
                                                                 : kb.concepts + (uint64_t)d.ref * kb.wp;
-                    role_words<WPL>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                    role_words<WPL, BLK>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
                 }
                 break;
             }
@@ -169,15 +170,21 @@ __device__ bool wait_deps(const PlanHeader &hd, const uint32_t *deps, const Seg 
 }
 
 // Copy the segment's filler row into shared memory (all threads of the CTA).
+// A FORALL filler is staged complemented (REF_NEG), so the walk counts
+// successors outside C without a per-edge complement.
 __device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *slots, uint32_t ref, uint32_t *dst) {
-    const uint32_t *src = (ref & REF_SLOT) ? slots + (uint64_t)(ref & ~REF_SLOT) * kb.wp
-                                           : kb.concepts + (uint64_t)ref * kb.wp;
+    const uint32_t id = ref & REF_ID;
+    const uint32_t *src = (ref & REF_SLOT) ? slots + (uint64_t)id * kb.wp : kb.concepts + (uint64_t)id * kb.wp;
+    const uint32_t x = (ref & REF_NEG) ? 0xFFFFFFFFu : 0u;
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-    for (uint32_t q = threadIdx.x; q < kb.wp / 4; q += blockDim.x) d4[q] = s4[q];
+    for (uint32_t q = threadIdx.x; q < kb.wp / 4; q += blockDim.x) {
+        uint4 v = s4[q];
+        d4[q] = make_uint4(v.x ^ x, v.y ^ x, v.z ^ x, v.w ^ x);
+    }
 }
 
-template <int NW, int WPL, bool STAGE>
+template <int NW, int WPL, bool STAGE, int BLK>
 __global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
                 __syncthreads();
             }
         }
-        run_tile<NW, WPL, STAGE>(A, hd, seg, tile, sm, slots, acc);
+        run_tile<NW, WPL, STAGE, BLK>(A, hd, seg, tile, sm, slots, acc);
         __syncthreads();
         if (threadIdx.x == 0 && A.use_queue) {
             __threadfence();
@@ -248,22 +255,23 @@ __global__ void finalize_kernel(KBView kb, const uint8_t *ws, uint32_t *counts) 
 
 using KernelFn = void (*)(ExecArgs);
 
-template <bool STAGE>
+// Instantiated launch shapes: warps x words per lane x staging x chunks per block.
+template <bool STAGE, int BLK>
 KernelFn pick_t(uint32_t warps, uint32_t wpl) {
     if (wpl == 4) {
-        if (warps == 4) return exec_kernel<4, 4, STAGE>;
-        if (warps == 16) return exec_kernel<16, 4, STAGE>;
-        if (warps == 32) return exec_kernel<32, 4, STAGE>;
-        return exec_kernel<8, 4, STAGE>;
+        if (warps == 4) return exec_kernel<4, 4, STAGE, BLK>;
+        if (warps == 16) return exec_kernel<16, 4, STAGE, BLK>;
+        return exec_kernel<8, 4, STAGE, BLK>;
     }
-    if (warps == 4) return exec_kernel<4, 1, STAGE>;
-    if (warps == 16) return exec_kernel<16, 1, STAGE>;
-    if (warps == 32) return exec_kernel<32, 1, STAGE>;
-    return exec_kernel<8, 1, STAGE>;
+    if (warps == 4) return exec_kernel<4, 1, STAGE, BLK>;
+    if (warps == 16) return exec_kernel<16, 1, STAGE, BLK>;
+    if (warps == 32) return exec_kernel<32, 1, STAGE, BLK>;
+    return exec_kernel<8, 1, STAGE, BLK>;
 }
 
-KernelFn pick(uint32_t warps, uint32_t wpl, bool stage) {
-    return stage ? pick_t<true>(warps, wpl) : pick_t<false>(warps, wpl);
+KernelFn pick(const Tuning &t, bool stage) {
+    if (t.role_block == 4) return stage ? pick_t<true, 4>(t.warps, t.wpl) : pick_t<false, 4>(t.warps, t.wpl);
+    return stage ? pick_t<true, 8>(t.warps, t.wpl) : pick_t<false, 8>(t.warps, t.wpl);
 }
 
 size_t smem_bytes(const hedl_kb *kb, const Tuning &t, bool stage) {
@@ -282,7 +290,7 @@ size_t exec_smem_bytes(const Tuning &t) { return stack_smem_bytes(t) + 16; }
 
 int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm) {
     const bool stage = use_staging(kb, t);
-    KernelFn fn = pick(t.warps, t.wpl, stage);
+    KernelFn fn = pick(t, stage);
     size_t smem = smem_bytes(kb, t, stage);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -294,7 +302,7 @@ int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t
                 void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Tuning &t = p->tuning;
-    KernelFn fn = pick(t.warps, t.wpl, p->staged);
+    KernelFn fn = pick(t, p->staged);
     size_t smem = smem_bytes(kb, t, p->staged);
     int bps = p->bps;
     if (bps < 1) return cudaErrorInvalidConfiguration;

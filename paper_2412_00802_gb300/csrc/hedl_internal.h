@@ -45,6 +45,8 @@ enum : uint32_t {
     D_SLOT = 32      // a materialized bitset: ref = slot index
 };
 constexpr uint32_t REF_SLOT = 0x80000000u;   // filler ref: slot (low bits) vs concept id
+constexpr uint32_t REF_NEG = 0x40000000u;    // Seg.filler only: stage the complement (FORALL)
+constexpr uint32_t REF_ID = 0x3FFFFFFFu;     // slot or concept id bits of a ref
 
 struct DInsn {
     uint32_t op;     // D_*
@@ -106,6 +108,7 @@ struct Tuning {
     uint32_t ctas_per_sm = 0;
     uint32_t timeout_ms = 2000;
     uint32_t stage = 1;      // stage role fillers in shared memory when a row fits
+    uint32_t role_block = 8; // 32-edge chunks per step of the role walk (4 or 8)
     uint32_t tile_words() const { return warps * 32u * wpl * rounds; }
 };
 

@@ -48,7 +48,7 @@ __global__ void role_kernel(DevCSR g, const uint32_t *filler, uint32_t kind, uin
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg * 32u < wp; wg += warps) {
         uint32_t v[1];
-        role_words<1>(g, filler, kind, n_arg, n, n_words, wg * 32u, lane, v);
+        role_words<1, 8>(g, filler, kind, n_arg, n, n_words, wg * 32u, lane, v);
         if (wg * 32u + lane < wp) out[wg * 32u + lane] = v[0];
     }
 }

@@ -313,6 +313,10 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     uint32_t n_slots = 0;
     for (uint32_t i = 0; i < NN; ++i)
         if (mat[i]) slot_of[i] = n_slots++;
+    if (n_slots > REF_ID) {
+        delete p;
+        return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^30 materialized intermediate sets");
+    }
     std::vector<Seg> segs;
     std::vector<DInsn> code;
     std::vector<std::vector<uint32_t>> seg_slots_read;
@@ -370,7 +374,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                         reads.push_back(slot_of[c]);
                     }
                     if (rk == 0xFFFFFFFFu) rk = n.a * 2 + n.inv;
-                    if (s.filler == NO_FILLER) s.filler = d.ref;
+                    if (s.filler == NO_FILLER) s.filler = d.ref | (n.op == HEDL_OP_FORALL ? REF_NEG : 0u);
                     const DevCSR &g = kb->csr_host[2 * n.a + n.inv];
                     model += 4 * (N + 1) + 4ull * g.n_edges + B;
                     p->info.n_role_ops++;

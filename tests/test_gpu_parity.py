@@ -71,11 +71,26 @@ def test_c1_batched_shapes(c1, c1_dev):
                                     dict(warps_per_cta=8, words_per_lane=4, rounds=1, ctas_per_sm=1),
                                     dict(warps_per_cta=32, words_per_lane=1, stage_fillers=1),
                                     dict(warps_per_cta=8, words_per_lane=1, stage_fillers=0),
-                                    dict(warps_per_cta=16, words_per_lane=4, rounds=2, stage_fillers=0)])
+                                    dict(warps_per_cta=16, words_per_lane=4, rounds=2, stage_fillers=0),
+                                    dict(warps_per_cta=16, role_block=4, rounds=2, stage_fillers=1),
+                                    dict(warps_per_cta=8, role_block=4, stage_fillers=0)])
 def test_launch_shapes(c1, tuning):
     dkb = device_kb(c1)
     H.hedl_tuning_set(dkb.handle, **tuning)
     compare_batch(c1, dkb, hyps.batch_hyps(c1, 22, 0, 300), 0)
+
+
+def test_autotune_picks_a_shape_and_stays_exact(c1, tmp_path):
+    dkb = device_kb(c1)
+    probe = P.pack_batch(hyps.batch_hyps(c1, 41, 0, 128))
+    cache = str(tmp_path / "tune.txt")
+    chosen = dkb.autotune(*probe, cache_path=cache)
+    assert H.hedl_tuning_get(dkb.handle) == chosen
+    assert open(cache).read().count("\n") == 1
+    compare_batch(c1, dkb, hyps.batch_hyps(c1, 42, 0, 200), 0)
+    other = device_kb(c1)                      # the cached result is reused
+    assert other.autotune(*probe, cache_path=cache) == chosen
+    assert open(cache).read().count("\n") == 1
 
 
 def test_launch_shape_that_does_not_fit_is_rejected(c1):
