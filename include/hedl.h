@@ -309,6 +309,70 @@ int hedl_autotune_workspace_size(hedl_kb *kb, const uint64_t *progs, const uint3
 int hedl_autotune(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, void *ws,
                   size_t ws_bytes, const char *cache_path, hedl_stream s, hedl_tuning *chosen);
 
+/* ------------------------------------------------------------------ surrogate */
+/* A learned surrogate that predicts a hypothesis' (accuracy, F1) from a
+ * structural encoding, used only to order and prune the queue of exact
+ * evaluations; every reported score still comes from exact evaluation.  The
+ * paper has no learned component.  Network: 512 -> 512 -> 512 -> 2, ReLU,
+ * BF16 weights and activations, FP32 accumulation on the tensor cores;
+ * trained by mean squared error with Adam on FP32 master weights. */
+typedef struct hedl_mlp hedl_mlp;
+
+#define HEDL_ENC_DIM 512
+#define HEDL_ENC_MAXLEN 256   /* longer programs are encoded by their last 256 instructions */
+
+/* Number of parameters: W1[512][512], b1[512], W2[512][512], b2[512],
+ * W3[2][512], b3[2], concatenated in that order (row-major). */
+uint64_t hedl_mlp_param_count(void);
+
+/* Create a network from HOST params (float32[hedl_mlp_param_count()]).
+ * Allocates its device state; SYNCHRONIZES the device. */
+int hedl_mlp_create(const float *params, hedl_mlp **out);
+void hedl_mlp_free(hedl_mlp *m);
+
+/* Copy the FP32 master weights and/or the last gradients (HOST arrays of
+ * hedl_mlp_param_count() floats, either may be NULL) and the Adam step count.
+ * SYNCHRONIZES the device. */
+int hedl_mlp_get(const hedl_mlp *m, float *params, float *grads, uint32_t *step);
+
+/* Workspace bytes for a batch of B rows (activations and their gradients). */
+int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
+
+/* Structural encoding of H programs (DEVICE progs uint64[offs[H]], offs
+ * uint32[H+1]) into X (DEVICE bf16 [H][512] as uint16 bit patterns): integer
+ * feature counts scaled by 1/4 (op histogram per depth, concept / role /
+ * property / cardinality / threshold-exponent histograms, length and height
+ * one-hots, totals, a constant).  Instructions that are not op codes are
+ * ignored.  Asynchronous. */
+int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, uint16_t *X, hedl_stream s);
+
+/* Y (DEVICE float [B][2]) = the network applied to X (DEVICE bf16 [B][512]). */
+int hedl_mlp_forward(hedl_mlp *m, const uint16_t *X, uint32_t B, float *Y, void *ws, size_t ws_bytes,
+                     hedl_stream s);
+
+/* Gradients of the loss mean_b sum_j (Y_bj - T_bj)^2 for targets T (DEVICE
+ * float [B][2]) into the network's gradient buffer; *loss (DEVICE float, may
+ * be NULL) receives the loss. */
+int hedl_mlp_gradients(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t B, float *loss, void *ws,
+                       size_t ws_bytes, hedl_stream s);
+
+/* hedl_mlp_gradients followed by one Adam step (beta 0.9 / 0.999, eps 1e-8,
+ * learning rate lr) on the master weights, refreshing their BF16 copies. */
+int hedl_mlp_train_step(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t B, float lr, float *loss,
+                        void *ws, size_t ws_bytes, hedl_stream s);
+
+/* Exact scores from coverage counts (DEVICE uint32 [H][4] TP, FP, FN, TN) into
+ * DEVICE float [H][2]: accuracy (TP+TN)/(TP+FP+FN+TN) and F1 2TP/(2TP+FP+FN)
+ * (0 where the denominator is 0), computed in double, stored as float. */
+int hedl_scores_from_counts(const uint32_t *counts, uint32_t H, float *scores, hedl_stream s);
+
+/* Indices (DEVICE uint32 [k], ascending) of the k best rows of Y (DEVICE
+ * float [H][2]) ordered by Y[.][0] descending, then Y[.][1] descending, then
+ * index ascending (NaN last).  ws >= hedl_select_workspace_size(H). */
+int hedl_select_workspace_size(uint32_t H, size_t *bytes);
+int hedl_select_top(const float *Y, uint32_t H, uint32_t k, uint32_t *idx, void *ws, size_t ws_bytes,
+                    hedl_stream s);
+
 /* Description of the calling thread's last failure ("" if none). */
 const char *hedl_last_error(void);
 

@@ -1,0 +1,205 @@
+"""Oracle of the learned surrogate (TEST INFRASTRUCTURE).
+
+The paper has no learned component; the surrogate only orders and prunes the
+exact-evaluation queue.  This module is the plain reference it is checked
+against, written from the definitions below (no code shared with the GPU
+library):
+
+* ``encode``: the 512-dimensional structural encoding of a postfix program,
+  computed by direct counting over the program;
+* ``forward`` / ``backward``: the MLP 512 -> 512 -> 512 -> 2 with ReLU,
+  mean-squared-error loss, in float64; ``bf16`` rounding (round to nearest,
+  ties to even, from the float32 bit pattern) is applied where the GPU stores
+  bfloat16 (inputs, weights, hidden activations, their gradients);
+* ``adam``: one Adam step (Kingma and Ba, 2015) on float32 master weights;
+* ``ranking``: the total order used to rank hypotheses (accuracy desc, F1
+  desc, length asc, program bytes asc, index asc) and recall@k.
+
+Encoding (feature index ranges; every value is an integer count scaled by
+1/4, exact in bfloat16).  Node depth is the distance from the root (root 0),
+clamped to 7; "height" is the tree height (leaves 1), clamped to 8.
+  [  0,112) op histogram per depth: 14 ops x 8 depths, index depth*14 + op-1
+  [112,240) atomic concept histogram: concept id mod 128
+  [240,304) role histogram: (role id mod 32)*2 + inverse flag
+  [304,344) role-restriction kind per depth: depth*5 + (op - EXISTS)
+  [344,368) cardinality: (op - ATLEAST)*8 + min(n, 7)
+  [368,392) data restriction: (property id mod 8)*3 + (op - DGE)
+  [392,440) threshold magnitude: (op - DGE)*16 + bucket, bucket from the
+            float32 exponent field e of the threshold: clamp(e - 118, 0, 15)
+  [440,480) program length one-hot: min(len, 40) - 1
+  [480,488) height one-hot: min(height, 8) - 1
+  [488,492) counts of leaves, role restrictions, data restrictions, NOTs
+  [492]     constant 4 (a bias input; 4 * 1/4 = 1)
+  [493,512) zero
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+D_IN = 512
+D_H = 512
+D_OUT = 2
+_ATOM, _TOP, _BOT, _NOT, _AND, _OR = 1, 2, 3, 4, 5, 6
+_EX, _ALL, _MIN, _MAX, _EXACT = 7, 8, 9, 10, 11
+_GE, _LE, _EQ = 12, 13, 14
+
+
+def _arity(op: int) -> int:
+    if op in (_NOT, _EX, _ALL, _MIN, _MAX, _EXACT):
+        return 1
+    if op in (_AND, _OR):
+        return 2
+    return 0
+
+
+def encode(prog: Sequence[int]) -> np.ndarray:
+    """Structural encoding of one postfix program (float32[512]).
+
+    A program longer than 256 instructions is encoded by its last 256 (the
+    root and the nodes nearest to it)."""
+    prog = list(prog)[-256:]
+    L = len(prog)
+    # node depths: read the postfix backwards (a pre-order walk, right child first)
+    depth = [0] * L
+    pending = [0]
+    height = 0
+    for k in range(L - 1, -1, -1):
+        d = pending.pop()
+        depth[k] = d
+        height = max(height, d + 1)
+        op = int(prog[k]) & 0xFF
+        for _ in range(_arity(op)):
+            pending.append(d + 1)
+    f = np.zeros(D_IN, dtype=np.int64)
+    leaves = roles = datas = nots = 0
+    for k in range(L):
+        w = int(prog[k])
+        op, inv, a, b = w & 0xFF, (w >> 8) & 1, (w >> 16) & 0xFFFF, (w >> 32) & 0xFFFFFFFF
+        d = min(depth[k], 7)
+        f[d * 14 + op - 1] += 1
+        if _arity(op) == 0:
+            leaves += 1
+        if op == _ATOM:
+            f[112 + a % 128] += 1
+        elif _EX <= op <= _EXACT:
+            roles += 1
+            f[240 + (a % 32) * 2 + inv] += 1
+            f[304 + d * 5 + (op - _EX)] += 1
+            if op >= _MIN:
+                f[344 + (op - _MIN) * 8 + min(b, 7)] += 1
+        elif _GE <= op <= _EQ:
+            datas += 1
+            f[368 + (a % 8) * 3 + (op - _GE)] += 1
+            e = (b >> 23) & 0xFF
+            f[392 + (op - _GE) * 16 + min(max(e - 118, 0), 15)] += 1
+        elif op == _NOT:
+            nots += 1
+    f[440 + min(L, 40) - 1] += 1
+    f[480 + min(height, 8) - 1] += 1
+    f[488] += leaves
+    f[489] += roles
+    f[490] += datas
+    f[491] += nots
+    f[492] += 4
+    return (f.astype(np.float64) * 0.25).astype(np.float32)
+
+
+def encode_batch(progs: Sequence[Sequence[int]]) -> np.ndarray:
+    return np.stack([encode(p) for p in progs]) if len(progs) else np.zeros((0, D_IN), np.float32)
+
+
+# ---------------------------------------------------------------------------- bfloat16
+def bf16(x) -> np.ndarray:
+    """Round float32 values to bfloat16 (nearest, ties to even), returned as float32."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    nan = np.isnan(a)
+    out = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+    out = np.where(nan, a, out)
+    return out.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------- MLP
+def init_params(seed: int) -> Dict[str, np.ndarray]:
+    """Weights uniform in +-1/sqrt(fan_in) from a seeded numpy generator, zero biases (float32)."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, (o, i) in (("w1", (D_H, D_IN)), ("w2", (D_H, D_H)), ("w3", (D_OUT, D_H))):
+        lim = 1.0 / math.sqrt(i)
+        p[name] = rng.uniform(-lim, lim, size=(o, i)).astype(np.float32)
+    p["b1"] = np.zeros(D_H, np.float32)
+    p["b2"] = np.zeros(D_H, np.float32)
+    p["b3"] = np.zeros(D_OUT, np.float32)
+    return p
+
+
+def forward(p: Dict[str, np.ndarray], X: np.ndarray, rounding: bool = True) -> Tuple[np.ndarray, dict]:
+    """Y = (relu(relu(X W1^T + b1) W2^T + b2)) W3^T + b3, float64 accumulation.
+
+    With rounding, X, the weights and the hidden activations are rounded to
+    bfloat16 where the GPU stores them."""
+    r = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
+    x = np.asarray(r(X), np.float64)
+    w1, w2, w3 = (np.asarray(r(p[k]), np.float64) for k in ("w1", "w2", "w3"))
+    h1 = np.maximum(x @ w1.T + p["b1"], 0.0)
+    h1 = np.asarray(r(h1), np.float64)
+    h2 = np.maximum(h1 @ w2.T + p["b2"], 0.0)
+    h2 = np.asarray(r(h2), np.float64)
+    y = h2 @ w3.T + p["b3"]
+    return y, {"x": x, "h1": h1, "h2": h2, "w1": w1, "w2": w2, "w3": w3}
+
+
+def loss(y: np.ndarray, t: np.ndarray) -> float:
+    """Mean over the batch of the summed squared error of the two outputs."""
+    return float(((y - t) ** 2).sum() / y.shape[0])
+
+
+def backward(p: Dict[str, np.ndarray], X: np.ndarray, T: np.ndarray, rounding: bool = True) -> Tuple[float, dict]:
+    """Gradients of ``loss`` by the chain rule (relu'(0) = 0), float64.
+
+    With rounding, the gradients flowing into the hidden layers are rounded to
+    bfloat16 where the GPU stores them."""
+    r = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
+    y, c = forward(p, X, rounding)
+    B = y.shape[0]
+    dy = 2.0 * (y - T) / B
+    g = {"w3": dy.T @ c["h2"], "b3": dy.sum(0)}
+    dh2 = (dy @ c["w3"]) * (c["h2"] > 0)
+    dh2 = np.asarray(r(dh2), np.float64)
+    g["w2"] = dh2.T @ c["h1"]
+    g["b2"] = dh2.sum(0)
+    dh1 = (dh2 @ c["w2"]) * (c["h1"] > 0)
+    dh1 = np.asarray(r(dh1), np.float64)
+    g["w1"] = dh1.T @ c["x"]
+    g["b1"] = dh1.sum(0)
+    return loss(y, T), g
+
+
+def adam(p: Dict[str, np.ndarray], g: Dict[str, np.ndarray], m: dict, v: dict, step: int, lr: float,
+         b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8) -> None:
+    """One Adam step in place (bias-corrected moments), float64 then stored float32."""
+    for k in p:
+        m[k] = b1 * m.get(k, 0.0) + (1 - b1) * g[k]
+        v[k] = b2 * v.get(k, 0.0) + (1 - b2) * g[k] ** 2
+        mh = m[k] / (1 - b1 ** step)
+        vh = v[k] / (1 - b2 ** step)
+        p[k] = (p[k] - lr * mh / (np.sqrt(vh) + eps)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------- ranking
+def rank_order(acc: np.ndarray, f1: np.ndarray, progs: Sequence[Sequence[int]]) -> List[int]:
+    """Indices sorted by accuracy desc, F1 desc, length asc, program bytes asc, index asc."""
+    keys = [(-float(acc[i]), -float(f1[i]), len(progs[i]), np.asarray(progs[i], np.uint64).tobytes(), i)
+            for i in range(len(progs))]
+    return [k[-1] for k in sorted(keys)]
+
+
+def recall_at(k: int, exact_order: Sequence[int], selected: Sequence[int]) -> float:
+    """|top-k of the exact order  intersect  selected| / k."""
+    top = set(exact_order[:k])
+    return len(top & set(selected)) / float(k)

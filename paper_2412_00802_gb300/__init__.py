@@ -43,7 +43,10 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_validate", "hedl_plan_batch", "hedl_plan_info_get", "hedl_plan_free", "hedl_plan_execute",
            "hedl_plan_replay", "hedl_workspace_size", "hedl_score_batch", "hedl_eval_concept",
            "hedl_eval_concept_noalloc", "hedl_sync_status", "hedl_tuning_get", "hedl_tuning_set",
-           "hedl_autotune_workspace_size", "hedl_autotune", "hedl_last_error")
+           "hedl_autotune_workspace_size", "hedl_autotune", "hedl_mlp_param_count", "hedl_mlp_create",
+           "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
+           "hedl_mlp_gradients", "hedl_mlp_train_step", "hedl_scores_from_counts", "hedl_select_workspace_size",
+           "hedl_select_top", "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -111,6 +114,18 @@ def library(path: Optional[str] = None):
             "hedl_tuning_set": (I, [P, ctypes.POINTER(hedl_tuning)]),
             "hedl_autotune_workspace_size": (I, [P, P, P, U32, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_autotune": (I, [P, P, P, U32, P, ctypes.c_size_t, ctypes.c_char_p, P, ctypes.POINTER(hedl_tuning)]),
+            "hedl_mlp_param_count": (U64, []),
+            "hedl_mlp_create": (I, [P, ctypes.POINTER(P)]),
+            "hedl_mlp_free": (None, [P]),
+            "hedl_mlp_get": (I, [P, P, P, ctypes.POINTER(U32)]),
+            "hedl_mlp_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
+            "hedl_encode": (I, [P, P, U32, P, P]),
+            "hedl_mlp_forward": (I, [P, P, U32, P, P, ctypes.c_size_t, P]),
+            "hedl_mlp_gradients": (I, [P, P, P, U32, P, P, ctypes.c_size_t, P]),
+            "hedl_mlp_train_step": (I, [P, P, P, U32, ctypes.c_float, P, P, ctypes.c_size_t, P]),
+            "hedl_scores_from_counts": (I, [P, U32, P, P]),
+            "hedl_select_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
+            "hedl_select_top": (I, [P, U32, U32, P, P, ctypes.c_size_t, P]),
             "hedl_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -339,6 +354,93 @@ def hedl_autotune(kb: KBHandle, progs, offs, ws, cache_path: Optional[str] = Non
                                    ws.numel() * ws.element_size(), cache_path.encode() if cache_path else None,
                                    _stream(stream), ctypes.byref(t)))
     return {k: int(getattr(t, k)) for k, _ in hedl_tuning._fields_}
+
+
+# ---------------------------------------------------------------------------- surrogate
+ENC_DIM = 512
+
+
+def hedl_mlp_param_count() -> int:
+    return int(library().hedl_mlp_param_count())
+
+
+class MLPHandle:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                library().hedl_mlp_free(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def hedl_mlp_create(params: np.ndarray) -> MLPHandle:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != hedl_mlp_param_count():
+        raise ValueError("wrong parameter count")
+    out = ctypes.c_void_p()
+    _check(library().hedl_mlp_create(p.ctypes.data, ctypes.byref(out)))
+    return MLPHandle(out.value)
+
+
+def hedl_mlp_free(m: MLPHandle):
+    if m.ptr:
+        library().hedl_mlp_free(m.ptr)
+        m.ptr = None
+
+
+def hedl_mlp_get(m: MLPHandle):
+    n = hedl_mlp_param_count()
+    p = np.zeros(n, np.float32)
+    g = np.zeros(n, np.float32)
+    step = ctypes.c_uint32()
+    _check(library().hedl_mlp_get(m.ptr, p.ctypes.data, g.ctypes.data, ctypes.byref(step)))
+    return p, g, step.value
+
+
+def hedl_mlp_workspace_size(B: int) -> int:
+    out = ctypes.c_size_t()
+    _check(library().hedl_mlp_workspace_size(B, ctypes.byref(out)))
+    return out.value
+
+
+def hedl_encode(progs_dev, offs_dev, X, stream=None):
+    """progs_dev: CUDA int64 tensor of instructions; offs_dev: CUDA int32 [H+1]; X: CUDA bf16 [H][512]."""
+    H = offs_dev.numel() - 1
+    _check(library().hedl_encode(_dptr(progs_dev), _dptr(offs_dev), H, _dptr(X), _stream(stream)))
+
+
+def hedl_mlp_forward(m: MLPHandle, X, Y, ws, stream=None):
+    _check(library().hedl_mlp_forward(m.ptr, _dptr(X), X.shape[0], _dptr(Y), _dptr(ws),
+                                      ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def hedl_mlp_gradients(m: MLPHandle, X, T, ws, loss=None, stream=None):
+    _check(library().hedl_mlp_gradients(m.ptr, _dptr(X), _dptr(T), X.shape[0], _dptr(loss), _dptr(ws),
+                                        ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def hedl_mlp_train_step(m: MLPHandle, X, T, lr: float, ws, loss=None, stream=None):
+    _check(library().hedl_mlp_train_step(m.ptr, _dptr(X), _dptr(T), X.shape[0], lr, _dptr(loss), _dptr(ws),
+                                         ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def hedl_scores_from_counts(counts, scores, stream=None):
+    _check(library().hedl_scores_from_counts(_dptr(counts), counts.shape[0], _dptr(scores), _stream(stream)))
+
+
+def hedl_select_workspace_size(H: int) -> int:
+    out = ctypes.c_size_t()
+    _check(library().hedl_select_workspace_size(H, ctypes.byref(out)))
+    return out.value
+
+
+def hedl_select_top(Y, k: int, idx, ws, stream=None):
+    _check(library().hedl_select_top(_dptr(Y), Y.shape[0], k, _dptr(idx), _dptr(ws),
+                                     ws.numel() * ws.element_size(), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------- convenience owner

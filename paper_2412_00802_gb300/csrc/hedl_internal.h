@@ -104,7 +104,7 @@ constexpr int STACK_MAX = 16;
 struct Tuning {
     uint32_t warps = 32;
     uint32_t wpl = 1;        // words per lane
-    uint32_t rounds = 1;
+    uint32_t rounds = 2;
     uint32_t ctas_per_sm = 0;
     uint32_t timeout_ms = 2000;
     uint32_t stage = 1;      // stage role fillers in shared memory when a row fits

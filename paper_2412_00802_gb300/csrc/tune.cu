@@ -18,7 +18,7 @@ std::vector<Tuning> candidates(const Tuning &base) {
     std::vector<Tuning> out;
     for (uint32_t stage : {1u, 0u})
         for (uint32_t warps : {8u, 16u, 32u})
-            for (uint32_t rounds : {1u, 2u})
+            for (uint32_t rounds : {1u, 2u, 4u})
                 for (uint32_t blk : {4u, 8u}) {
                     Tuning t = base;
                     t.stage = stage;

@@ -32,6 +32,8 @@ S_DAG = 2
 S_PROP_VAL = 3
 S_PROP_MISS = 4
 S_EXAMPLES = 5
+S_LATENT = 6
+S_BIAS = 5 << 16
 S_CONCEPT = 1 << 16
 S_ROLE_DEG = 2 << 16
 S_ROLE_TGT = 3 << 16
@@ -54,6 +56,7 @@ class KBConfig:
     missing: float
     n_pos: int
     n_neg: int
+    planted: bool = False    # examples from a latent class that some concepts, role 0 and property 0 track
 
     def scaled(self, n: int, **kw) -> "KBConfig":
         """Same distributions on ``n`` individuals (example counts scaled)."""
@@ -75,9 +78,20 @@ CONFIGS = {
                    ("uniform", 0.0, 1000.0), 0.0, 10_000, 10_000),
     # refinement search
     "c5": KBConfig("c5", 5, 4_000_000, 300, 0.01, 0.50, False, 64, ("zipf", 2.3, 10.0, 10_000), 32,
-                   ("normal", 50.0, 15.0), 0.15, 50_000, 50_000),
+                   ("normal", 50.0, 15.0), 0.15, 50_000, 50_000, planted=True),
 }
-CONFIGS["c4"] = replace(CONFIGS["c2"], name="c4")
+CONFIGS["c4"] = replace(CONFIGS["c2"], name="c4", seed=4, planted=True)
+
+# Planted structure (workloads that search or learn need a signal): a latent
+# class Z (a uniform 20 % of the individuals) supplies the positives, its
+# complement the negatives; concepts 0-2 have higher membership inside Z,
+# role 0 sends 70 % of a Z member's edges to members of concept 3, and
+# property 0 is shifted upwards inside Z.  Only random draws are correlated:
+# no concept is evaluated to make the examples.
+LATENT_FRAC = 0.2
+PLANT_P_IN = (0.7, 0.5, 0.4)
+PLANT_P_OUT = (0.1, 0.15, 0.2)
+PLANT_ROLE_BIAS = 0.7
 
 
 def words(n: int) -> Tuple[int, int]:
@@ -159,8 +173,12 @@ def draw_degrees(cfg: KBConfig, r: int, n: int) -> Tuple[np.ndarray, dict]:
     return np.minimum(deg.astype(np.int64), n), meta
 
 
-def draw_targets(cfg: KBConfig, r: int, deg: np.ndarray, n: int) -> np.ndarray:
-    """Uniform targets, without replacement within a row, rows sorted ascending."""
+def draw_targets(cfg: KBConfig, r: int, deg: np.ndarray, n: int, bias=None) -> np.ndarray:
+    """Uniform targets, without replacement within a row, rows sorted ascending.
+
+    bias = (subject mask, target pool, p): an edge of a masked subject takes a
+    uniform target from the pool with probability p (before duplicates are
+    redrawn uniformly)."""
     e = int(deg.sum())
     rows = np.repeat(np.arange(n, dtype=np.int64), deg)
     if cfg.degree[0] == "unique":
@@ -168,6 +186,13 @@ def draw_targets(cfg: KBConfig, r: int, deg: np.ndarray, n: int) -> np.ndarray:
         key = rng.u64(cfg.seed, S_ROLE_TGT + r, np.arange(n, dtype=np.uint64))
         return np.argsort(key, kind="stable").astype(np.uint32)
     tgt = rng.randint(cfg.seed, S_ROLE_TGT + r, np.arange(e, dtype=np.uint64), n)
+    if bias is not None and e:
+        smask, pool, pb = bias
+        ei = np.arange(e, dtype=np.uint64)
+        take = smask[rows] & (rng.uniform(cfg.seed, S_BIAS + r, ei) < pb)
+        pick = rng.randint(cfg.seed, S_BIAS + 1000 + r, ei, max(pool.size, 1))
+        if pool.size:
+            tgt = np.where(take, pool[np.minimum(pick, pool.size - 1)], tgt)
     attempt = 0
     while True:
         key = rows * n + tgt
@@ -240,12 +265,20 @@ class KB:
         return t
 
 
-def gen_concepts(cfg: KBConfig, wp: int, meta: dict) -> np.ndarray:
+def latent_class(cfg: KBConfig) -> np.ndarray:
+    return rng.uniform_range(cfg.seed, S_LATENT, cfg.n) < LATENT_FRAC
+
+
+def gen_concepts(cfg: KBConfig, wp: int, meta: dict, z=None) -> np.ndarray:
     n, c = cfg.n, cfg.n_concepts
     p = cfg.p_lo + (cfg.p_hi - cfg.p_lo) * rng.uniform_range(cfg.seed, S_CONCEPT_P, c)
     bits = np.zeros((c, wp), dtype=np.uint32)
     for j in range(c):
-        member = rng.uniform_range(cfg.seed, S_CONCEPT + j, n) < p[j]
+        u = rng.uniform_range(cfg.seed, S_CONCEPT + j, n)
+        if z is not None and j < len(PLANT_P_IN):
+            member = u < np.where(z, PLANT_P_IN[j], PLANT_P_OUT[j])
+        else:
+            member = u < p[j]
         bits[j] = pack_bits(member, wp)
     if cfg.dag and c > 1:
         # random subsumption forest: concept j < C has parent pj < j with prob 1/2
@@ -264,7 +297,7 @@ def gen_concepts(cfg: KBConfig, wp: int, meta: dict) -> np.ndarray:
     return bits
 
 
-def gen_props(cfg: KBConfig) -> np.ndarray:
+def gen_props(cfg: KBConfig, z=None) -> np.ndarray:
     n = cfg.n
     out = np.empty((cfg.n_props, n), dtype=np.float32)
     kind = cfg.prop_dist[0]
@@ -279,6 +312,9 @@ def gen_props(cfg: KBConfig) -> np.ndarray:
             v = cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, st, n)
         else:
             raise ValueError(kind)
+        if z is not None and p == 0:   # planted: property 0 shifted up inside the latent class
+            lo, hi = np.nanmin(v), np.nanmax(v)
+            v = np.where(z, v + 0.25 * (hi - lo), v)
         v = v.astype(np.float32)
         if cfg.missing > 0:
             miss = rng.uniform_range(cfg.seed, S_PROP_MISS * 1000 + p, n) < cfg.missing
@@ -287,13 +323,19 @@ def gen_props(cfg: KBConfig) -> np.ndarray:
     return out
 
 
-def gen_examples(cfg: KBConfig, wp: int) -> Tuple[np.ndarray, np.ndarray]:
-    """Disjoint uniform positive / negative sets (sorted index arrays)."""
+def gen_examples(cfg: KBConfig, wp: int, z=None) -> Tuple[np.ndarray, np.ndarray]:
+    """Disjoint uniform positive / negative sets (sorted index arrays); with a
+    latent class z, positives are drawn inside it and negatives outside."""
     n = cfg.n
     if cfg.n_pos + cfg.n_neg > n:
         raise ValueError("more examples than individuals")
     key = rng.u64(cfg.seed, S_EXAMPLES, np.arange(n, dtype=np.uint64))
     perm = np.argsort(key, kind="stable")
+    if z is not None:
+        inside, outside = perm[z[perm]], perm[~z[perm]]
+        if inside.size < cfg.n_pos or outside.size < cfg.n_neg:
+            raise ValueError("latent class too small for the examples")
+        return (np.sort(inside[: cfg.n_pos]).astype(np.int64), np.sort(outside[: cfg.n_neg]).astype(np.int64))
     pos = np.sort(perm[: cfg.n_pos]).astype(np.int64)
     neg = np.sort(perm[cfg.n_pos: cfg.n_pos + cfg.n_neg]).astype(np.int64)
     return pos, neg
@@ -303,12 +345,17 @@ def generate(cfg: KBConfig, roles: Optional[int] = None) -> KB:
     n = cfg.n
     w, wp = words(n)
     meta = {"seed": cfg.seed, "config": cfg.name}
-    cb = gen_concepts(cfg, wp, meta)
+    z = latent_class(cfg) if cfg.planted else None
+    cb = gen_concepts(cfg, wp, meta, z)
+    pool = None
+    if z is not None and cfg.n_concepts > 3:
+        pool = np.nonzero(unpack_bits(cb[3], n))[0].astype(np.int64)
     rps, cols, irps, icols = [], [], [], []
     for r in range(cfg.n_roles if roles is None else roles):
         deg, m = draw_degrees(cfg, r, n)
         meta.update(m)
-        tgt = draw_targets(cfg, r, deg, n)
+        bias = (z, pool, PLANT_ROLE_BIAS) if (r == 0 and pool is not None) else None
+        tgt = draw_targets(cfg, r, deg, n, bias)
         rp = np.zeros(n + 1, dtype=np.uint32)
         np.cumsum(deg, out=rp[1:])
         rps.append(rp)
@@ -316,8 +363,8 @@ def generate(cfg: KBConfig, roles: Optional[int] = None) -> KB:
         ip, ic = transpose_csr(rp, tgt, n)
         irps.append(ip)
         icols.append(ic)
-    props = gen_props(cfg)
-    pos, neg = gen_examples(cfg, wp)
+    props = gen_props(cfg, z)
+    pos, neg = gen_examples(cfg, wp, z)
     mp = np.zeros(n, dtype=bool)
     mp[pos] = True
     mn = np.zeros(n, dtype=bool)

@@ -1,0 +1,158 @@
+"""The surrogate's kernels against its oracle (oracle/surrogate.py), and a
+check that the trained network ranks better than chance."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import surrogate as S
+from synth import hyps, kb as K, programs as P
+from synth.rng import Rng
+from tests import oracle_pins as pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2412_00802_gb300 import build
+    build.build()
+    import paper_2412_00802_gb300 as H
+    from paper_2412_00802_gb300 import surrogate as sg
+    kb = K.generate(K.CONFIGS["c1"])
+    return torch, H, sg, kb
+
+
+def _programs(kb, n=600):
+    r = Rng(8, 8)
+    progs = [np.array(pins.random_program(r, kb, r.randint(1, 7)).postfix(), np.uint64) for _ in range(n // 2)]
+    return progs + hyps.batch_hyps(kb, 9, 0, n - n // 2)
+
+
+def test_encoder_bit_exact(env):
+    torch, H, sg, kb = env
+    progs = _programs(kb)
+    long = [P.insn(P.ATOM, 0, 1)]
+    for i in range(149):                       # a valid 299-instruction program (left-deep AND chain)
+        long += [P.insn(P.ATOM, 0, (i * 7) % 50), P.insn(P.AND)]
+    progs.append(np.array(long, np.uint64))
+    flat, offs = P.pack_batch(progs)
+    got = sg.Surrogate().encode(flat, offs).float().cpu().numpy()
+    want = S.encode_batch(progs)
+    assert np.array_equal(got, want)
+
+
+def _xt(torch, kb, n, seed):
+    progs = hyps.batch_hyps(kb, seed, 0, n)
+    X = S.encode_batch(progs)
+    T = np.random.default_rng(seed).uniform(size=(n, 2)).astype(np.float32)
+    return X, T
+
+
+def test_forward_matches_oracle(env):
+    torch, H, sg, kb = env
+    X, _ = _xt(torch, kb, 700, 3)
+    p = sg.init_params(5)
+    s = sg.Surrogate(p)
+    Y = s.predict(torch.from_numpy(X).to("cuda").to(torch.bfloat16)).cpu().numpy()
+    ref, _ = S.forward(sg.split_params(p), X, rounding=True)
+    err = np.abs(Y - ref)
+    # bf16 storage of the hidden layers: a sum in float32 may round to a neighbouring
+    # bf16 value where float64 does not (one ulp, 2^-8 relative) -> small output error
+    assert err.max() <= 2e-2 * max(1.0, np.abs(ref).max()), err.max()
+    assert err.mean() <= 2e-3 * max(1.0, np.abs(ref).mean())
+
+
+def test_gradients_match_oracle(env):
+    torch, H, sg, kb = env
+    X, T = _xt(torch, kb, 1024, 4)
+    p = sg.init_params(6)
+    s = sg.Surrogate(p)
+    Xd = torch.from_numpy(X).to("cuda").to(torch.bfloat16)
+    Td = torch.from_numpy(T).to("cuda")
+    loss = torch.zeros(1, device="cuda")
+    H.hedl_mlp_gradients(s.mlp, Xd, Td, s._workspace(1024), loss)
+    _, g, _ = H.hedl_mlp_get(s.mlp)
+    ref_loss, ref = S.backward(sg.split_params(p), X, T, rounding=True)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-3 * abs(ref_loss)
+    gd = sg.split_params(g)
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        rel = np.linalg.norm(gd[name] - ref[name]) / max(np.linalg.norm(ref[name]), 1e-12)
+        assert rel <= 2e-2, (name, rel)
+
+
+def test_train_step_matches_oracle_adam(env):
+    torch, H, sg, kb = env
+    X, T = _xt(torch, kb, 512, 7)
+    p = sg.init_params(8)
+    s = sg.Surrogate(p)
+    Xd = torch.from_numpy(X).to("cuda").to(torch.bfloat16)
+    Td = torch.from_numpy(T).to("cuda")
+    H.hedl_mlp_train_step(s.mlp, Xd, Td, 1e-3, s._workspace(512))
+    got = sg.split_params(s.params())
+    ref_p = {k: v.copy() for k, v in sg.split_params(p).items()}
+    _, g = S.backward(ref_p, X, T, rounding=True)
+    S.adam(ref_p, g, {}, {}, step=1, lr=1e-3)
+    for name in ref_p:
+        # a first Adam step moves each weight by about lr * sign(g); weights whose gradient is
+        # tiny may flip sign between float32 and float64, so compare the update norms
+        du = got[name] - sg.split_params(p)[name]
+        dr = ref_p[name] - sg.split_params(p)[name]
+        agree = np.mean(np.sign(du) == np.sign(dr))
+        assert agree >= 0.95, (name, agree)
+
+
+def test_scores_from_counts_exact(env):
+    torch, H, sg, kb = env
+    rng = np.random.default_rng(2)
+    c = rng.integers(0, 1000, size=(5000, 4)).astype(np.uint32)
+    c[:10] = 0
+    got = torch.empty((5000, 2), device="cuda")
+    H.hedl_scores_from_counts(torch.from_numpy(c.view(np.int32)).to("cuda"), got)
+    acc, f1 = oracle.accuracy_f1(c)
+    assert np.array_equal(got.cpu().numpy(), np.stack([acc, f1], 1).astype(np.float32))
+
+
+@pytest.mark.parametrize("H_,k", [(1, 1), (100, 7), (5000, 250), (65536, 3277)])
+def test_select_top_exact(env, H_, k):
+    """Documented order: accuracy desc, F1 desc, index asc; NaN last; values compare by
+    their float ordering with -0.0 below +0.0."""
+    torch, H, sg, kb = env
+    rng = np.random.default_rng(H_)
+    Y = rng.integers(0, 20, size=(H_, 2)).astype(np.float32) / 20.0   # many ties
+    if H_ > 10:
+        Y[3, 0] = np.nan
+        Y[5, 0] = -0.0
+        Y[6, 0] = 0.0
+    idx = sg.Surrogate().select(torch.from_numpy(Y).to("cuda"), k).cpu().numpy()
+
+    def key(x):
+        if np.isnan(x):
+            return (0, 0.0)
+        return (1, float(x) if not (x == 0 and np.signbit(x)) else -1e-300)
+    ranked = sorted(range(H_), key=lambda i: (key(Y[i, 0]), key(Y[i, 1]), -i), reverse=True)
+    assert np.array_equal(idx, np.sort(ranked[:k]))
+
+
+def test_trained_surrogate_ranks_better_than_chance(env):
+    """On a planted KB (the surrogate workload's shape, 20,000 individuals) the network, trained
+    on exactly scored hypotheses, keeps most of the exact top 100 in its top 5 %."""
+    torch, H, sg, _ = env
+    kb = K.generate(K.CONFIGS["c4"].scaled(20000, n_pos=500, n_neg=500, n_roles=8, n_props=4, n_concepts=50))
+    dkb = H.DeviceKB.from_synth(kb)
+    gen = hyps.TreeGen(kb, 51, share=0.3)
+    train = hyps.batch_hyps(kb, 51, 0, 24576, lmax=20, dmax=6, gen=gen)
+    flat, offs = P.pack_batch(train)
+    _, T = sg.exact_scores(dkb, flat, offs)
+    s = sg.Surrogate(seed=1)
+    X = s.encode(flat, offs)
+    losses = s.train(X, T, epochs=20, batch=2048, lr=2e-3)
+    assert losses[-1] < losses[0]
+    cand = hyps.batch_hyps(kb, 52, 0, 8192, lmax=20, dmax=6, gen=gen)
+    cflat, coffs = P.pack_batch(cand)
+    _, Tc = sg.exact_scores(dkb, cflat, coffs)
+    sel = s.select(s.predict(s.encode(cflat, coffs)), 410).cpu().numpy()   # top 5 %
+    Tc = Tc.cpu().numpy()
+    order = S.rank_order(Tc[:, 0], Tc[:, 1], cand)
+    recall = S.recall_at(100, order, sel)
+    assert recall >= 0.35, recall         # chance is 0.05

@@ -1,0 +1,83 @@
+"""Pins of the surrogate's oracle (no GPU): hand-computed encodings, bf16
+rounding against a library conversion and hand cases, finite-difference
+gradients, Adam's first step in closed form, ranking and recall."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+from synth import programs as P
+
+
+def test_encoding_hand_worked():
+    # (and A1 (some r2- A3)): AND depth 0; A1, EXISTS depth 1; A3 depth 2
+    f = S.encode(P.compile_text("(and A1 (some r2- A3))"))
+    want = np.zeros(512, np.float32)
+    for i, c in {0 * 14 + 4: 1, 1 * 14 + 0: 1, 1 * 14 + 6: 1, 2 * 14 + 0: 1,   # op x depth
+                 112 + 1: 1, 112 + 3: 1,                                         # concepts
+                 240 + 2 * 2 + 1: 1,                                             # role 2 inverted
+                 304 + 1 * 5 + 0: 1,                                             # EXISTS at depth 1
+                 440 + 3: 1, 480 + 2: 1,                                         # length 4, height 3
+                 488: 2, 489: 1, 492: 4}.items():                                # leaves, roles, bias
+        want[i] = 0.25 * c
+    assert np.array_equal(f, want)
+    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1; prop 9 mod 8 = 1; exponent of 1.0 is 127
+    f = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"))
+    want = np.zeros(512, np.float32)
+    for i, c in {0 * 14 + 8: 1, 1 * 14 + 11: 1, 240 + 0: 1, 304 + 2: 1, 344 + 0 * 8 + 3: 1,
+                 368 + 1 * 3 + 0: 1, 392 + 0 * 16 + 9: 1, 440 + 1: 1, 480 + 1: 1, 488: 1, 489: 1, 490: 1,
+                 492: 4}.items():
+        want[i] = 0.25 * c
+    assert np.array_equal(f, want)
+
+
+def test_bf16_rounding():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([np.random.default_rng(1).normal(size=4000).astype(np.float32) * 10.0 ** np.arange(-20, 20)
+                        .repeat(100)[:4000].astype(np.float32),
+                        np.array([0.0, -0.0, 1.0, 65504.0, 3.4e38, -3.4e38, 1e-40], np.float32)])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(S.bf16(x), ref)
+    # hand cases: 1 + 2^-8 ties to 1; 1 + 3 * 2^-8 ties to 1 + 2^-6 (even mantissa)
+    assert S.bf16(np.float32(1 + 2 ** -8)) == 1.0
+    assert S.bf16(np.float32(1 + 3 * 2 ** -8)) == np.float32(1 + 2 ** -6)
+
+
+def test_backward_matches_finite_differences():
+    p = S.init_params(3)
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(6, 512)).astype(np.float32)
+    T = rng.uniform(size=(6, 2)).astype(np.float32)
+    p64 = {k: v.astype(np.float64) for k, v in p.items()}
+    _, g = S.backward(p64, X, T, rounding=False)
+    eps = 1e-6
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        flat = p64[name].reshape(-1)
+        for i in rng.choice(flat.size, size=min(8, flat.size), replace=False):
+            old = flat[i]
+            flat[i] = old + eps
+            lp = S.loss(S.forward(p64, X, rounding=False)[0], T)
+            flat[i] = old - eps
+            lm = S.loss(S.forward(p64, X, rounding=False)[0], T)
+            flat[i] = old
+            fd = (lp - lm) / (2 * eps)
+            an = g[name].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 + 1e-5 * abs(fd), (name, i, fd, an)
+
+
+def test_adam_first_step_closed_form():
+    p = {"w": np.array([1.0, -2.0, 3.0], np.float32)}
+    g = {"w": np.array([0.5, -0.25, 1e-3])}
+    m, v = {}, {}
+    S.adam(p, g, m, v, step=1, lr=0.01)
+    # bias-corrected first step moves each weight by lr * g / (|g| + eps)
+    np.testing.assert_allclose(p["w"], np.array([1.0, -2.0, 3.0]) - 0.01 * np.sign(g["w"]), rtol=1e-5)
+
+
+def test_ranking_and_recall():
+    progs = [[1], [1, 1, 5], [2], [3]]
+    acc = np.array([0.5, 0.9, 0.9, 0.1])
+    f1 = np.array([0.2, 0.3, 0.3, 0.9])
+    order = S.rank_order(acc, f1, progs)
+    assert order == [2, 1, 0, 3]                      # tie on (acc, F1): shorter program first
+    assert S.recall_at(2, order, [1, 2, 3]) == 1.0
+    assert S.recall_at(2, order, [0, 3]) == 0.0
