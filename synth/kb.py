@@ -18,13 +18,51 @@ It holds none of the evaluation method's arithmetic.
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
+import threading
 from dataclasses import dataclass, replace
 from typing import List, Optional, Tuple
 
 import numpy as np
 
 from . import rng
+
+# The heavy loops (per-row target draws, transposes, Bernoulli bitsets) have a
+# multithreaded C twin in fastgen.c that produces the same arrays; the numpy
+# versions below define the recipe and are kept for checking it.
+USE_C = True
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_FAST = None
+_FAST_LOCK = threading.Lock()
+
+
+def _fast():
+    global _FAST
+    with _FAST_LOCK:
+        if _FAST is None:
+            src = os.path.join(_HERE, "fastgen.c")
+            lib = os.path.join(_HERE, "libfastgen.so")
+            if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+                tmp = lib + f".{os.getpid()}.tmp"
+                subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-pthread", "-o", tmp, src])
+                os.replace(tmp, lib)
+            L = ctypes.CDLL(lib)
+            P, U64, I64, I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32
+            L.fastgen_targets.argtypes = [U64, U64, U64, U64, P, I64, U64, P, P, I64, ctypes.c_double, P, I32]
+            L.fastgen_targets.restype = ctypes.c_int
+            L.fastgen_transpose.argtypes = [P, P, I64, P, P]
+            L.fastgen_transpose.restype = None
+            L.fastgen_bernoulli.argtypes = [U64, U64, U64, ctypes.c_double, ctypes.c_double, P, P, I32]
+            L.fastgen_bernoulli.restype = None
+            _FAST = L
+    return _FAST
+
+
+def _threads() -> int:
+    return max(1, min(64, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()))
 
 # sub-stream ids (one per component, so components are independent)
 S_CONCEPT_P = 1
@@ -185,6 +223,23 @@ def draw_targets(cfg: KBConfig, r: int, deg: np.ndarray, n: int, bias=None) -> n
         # a permutation: subject i -> pi(i)
         key = rng.u64(cfg.seed, S_ROLE_TGT + r, np.arange(n, dtype=np.uint64))
         return np.argsort(key, kind="stable").astype(np.uint32)
+    if USE_C and e:
+        rp = np.zeros(n + 1, dtype=np.uint64)
+        np.cumsum(deg, out=rp[1:])
+        col = np.empty(e, dtype=np.uint32)
+        smask = pool = None
+        pb = 0.0
+        if bias is not None:
+            smask = np.ascontiguousarray(bias[0], dtype=np.uint8)
+            pool = np.ascontiguousarray(bias[1], dtype=np.int64)
+            pb = float(bias[2])
+        rc = _fast().fastgen_targets(cfg.seed, S_ROLE_TGT + r, S_BIAS + r, S_BIAS + 1000 + r, rp.ctypes.data, n, n,
+                                     smask.ctypes.data if smask is not None else None,
+                                     pool.ctypes.data if pool is not None and pool.size else None,
+                                     0 if pool is None else pool.size, pb, col.ctypes.data, _threads())
+        if rc:
+            raise RuntimeError("could not draw distinct targets")
+        return col
     tgt = rng.randint(cfg.seed, S_ROLE_TGT + r, np.arange(e, dtype=np.uint64), n)
     if bias is not None and e:
         smask, pool, pb = bias
@@ -214,6 +269,13 @@ def draw_targets(cfg: KBConfig, r: int, deg: np.ndarray, n: int, bias=None) -> n
 
 def transpose_csr(row_ptr: np.ndarray, col: np.ndarray, n: int) -> Tuple[np.ndarray, np.ndarray]:
     """Inverse CSR: a stable sort of the edges by object keeps subjects ascending per row."""
+    if USE_C and col.size:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+        c = np.ascontiguousarray(col, dtype=np.uint32)
+        irp = np.empty(n + 1, dtype=np.uint64)
+        icol = np.empty(c.size, dtype=np.uint32)
+        _fast().fastgen_transpose(rp.ctypes.data, c.ctypes.data, n, irp.ctypes.data, icol.ctypes.data)
+        return irp.astype(np.uint32), icol
     deg = np.diff(row_ptr.astype(np.int64))
     subj = np.repeat(np.arange(n, dtype=np.uint32), deg)
     order = np.argsort(col, kind="stable")
@@ -273,9 +335,18 @@ def gen_concepts(cfg: KBConfig, wp: int, meta: dict, z=None) -> np.ndarray:
     n, c = cfg.n, cfg.n_concepts
     p = cfg.p_lo + (cfg.p_hi - cfg.p_lo) * rng.uniform_range(cfg.seed, S_CONCEPT_P, c)
     bits = np.zeros((c, wp), dtype=np.uint32)
+    zz = np.ascontiguousarray(z, dtype=np.uint8) if z is not None else None
     for j in range(c):
+        planted = z is not None and j < len(PLANT_P_IN)
+        if USE_C:
+            buf = np.zeros(wp * 4, dtype=np.uint8)
+            p_out, p_in = (PLANT_P_OUT[j], PLANT_P_IN[j]) if planted else (p[j], p[j])
+            _fast().fastgen_bernoulli(cfg.seed, S_CONCEPT + j, n, float(p_out), float(p_in),
+                                      zz.ctypes.data if planted else None, buf.ctypes.data, _threads())
+            bits[j] = buf.view("<u4")
+            continue
         u = rng.uniform_range(cfg.seed, S_CONCEPT + j, n)
-        if z is not None and j < len(PLANT_P_IN):
+        if planted:
             member = u < np.where(z, PLANT_P_IN[j], PLANT_P_OUT[j])
         else:
             member = u < p[j]

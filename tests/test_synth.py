@@ -101,3 +101,24 @@ def test_text_roundtrip():
     assert P.to_text(P.parse("(some r2--- A0)")) == "(some r2- A0)"
     prog = P.compile_text("(min 3 r7- A9)")
     assert P.fields(prog[-1]) == (P.ATLEAST, 1, 7, 3)
+
+
+@pytest.mark.parametrize("cfg", [K.CONFIGS["c1"].scaled(3001, seed=9),
+                                 K.CONFIGS["c2"].scaled(20_000, seed=8, n_roles=3, n_concepts=6),
+                                 K.CONFIGS["c4"].scaled(5_000, n_roles=2, n_concepts=6),
+                                 K.CONFIGS["c1"].scaled(300, seed=3, degree=("single", 250), n_roles=1)])
+def test_c_helpers_match_numpy(cfg):
+    """fastgen.c reproduces the numpy recipe array for array."""
+    try:
+        K.USE_C = True
+        a = K.generate(cfg)
+        K.USE_C = False
+        b = K.generate(cfg)
+    finally:
+        K.USE_C = True
+    assert np.array_equal(a.concept_bits, b.concept_bits)
+    for r in range(a.n_roles):
+        assert np.array_equal(a.row_ptr[r], b.row_ptr[r])
+        assert np.array_equal(a.col[r], b.col[r])
+        assert np.array_equal(a.inv_row_ptr[r], b.inv_row_ptr[r])
+        assert np.array_equal(a.inv_col[r], b.inv_col[r])
