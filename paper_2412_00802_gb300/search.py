@@ -1,0 +1,159 @@
+"""Refinement beam search over hypotheses, evaluated exactly on the GPU.
+
+Each step refines the beam into candidates (a caller-supplied seeded
+generator), puts every candidate in canonical form (AND / OR operands sorted
+by their canonical instruction bytes), drops duplicates, scores candidates
+exactly in batches through the library (hedl_plan_batch / hedl_plan_execute:
+one persistent, graph-replayed launch per batch), and keeps the best `width`
+of old beam plus candidates in the total order
+    accuracy desc, F1 desc, length asc, canonical bytes asc, position asc
+(old beam members first, then candidates in generation order).
+
+With a surrogate, candidates are evaluated in the order of their predicted
+scores; with pruning, only the predicted top fraction is evaluated.  Without
+pruning the surrogate changes only the evaluation order, so the final beam
+is the exhaustive search's.  Scores always come from exact evaluation.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_ARITY = {1: 0, 2: 0, 3: 0, 4: 1, 5: 2, 6: 2, 7: 1, 8: 1, 9: 1, 10: 1, 11: 1, 12: 0, 13: 0, 14: 0}
+_AND, _OR = 5, 6
+
+
+def canonical(prog: Sequence[int]) -> np.ndarray:
+    """Canonical postfix: every AND / OR has its operands in ascending byte order."""
+    stack: List[np.ndarray] = []
+    for w in prog:
+        w = int(w)
+        op = w & 0xFF
+        a = _ARITY[op]
+        if a == 0:
+            stack.append(np.array([w], np.uint64))
+        elif a == 1:
+            x = stack.pop()
+            stack.append(np.concatenate([x, np.array([w], np.uint64)]))
+        else:
+            y = stack.pop()
+            x = stack.pop()
+            if op in (_AND, _OR) and y.tobytes() < x.tobytes():
+                x, y = y, x
+            stack.append(np.concatenate([x, y, np.array([w], np.uint64)]))
+    assert len(stack) == 1
+    return stack[0]
+
+
+@dataclass
+class Entry:
+    prog: np.ndarray        # canonical postfix
+    acc: float
+    f1: float
+    counts: Tuple[int, int, int, int]
+
+    def key(self, pos: int):
+        return (-self.acc, -self.f1, len(self.prog), self.prog.tobytes(), pos)
+
+
+def scores(counts: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    c = counts.astype(np.float64)
+    tp, fp, fn, tn = c[:, 0], c[:, 1], c[:, 2], c[:, 3]
+    tot = tp + fp + fn + tn
+    acc = np.where(tot > 0, (tp + tn) / np.where(tot > 0, tot, 1), 0.0)
+    den = 2 * tp + fp + fn
+    f1 = np.where(den > 0, 2 * tp / np.where(den > 0, den, 1), 0.0)
+    return acc, f1
+
+
+def beam_update(beam: List[Entry], cands: List[Entry], width: int) -> List[Entry]:
+    pool = list(beam) + list(cands)
+    order = sorted(range(len(pool)), key=lambda i: pool[i].key(i))
+    out, seen = [], set()
+    for i in order:
+        b = pool[i].prog.tobytes()
+        if b in seen:
+            continue
+        seen.add(b)
+        out.append(pool[i])
+        if len(out) == width:
+            break
+    return out
+
+
+@dataclass
+class StepLog:
+    step: int
+    candidates: int
+    evaluated: int
+    best_acc: float
+    seconds: float
+    events: List[Tuple[float, float]] = field(default_factory=list)   # (time since start, best acc so far)
+
+
+class BeamSearch:
+    def __init__(self, dkb, refine: Callable[[List[np.ndarray], int, int], List[np.ndarray]], width: int = 64,
+                 per_step: int = 8192, batch: int = 2048, surrogate=None, keep_fraction: Optional[float] = None):
+        self.dkb = dkb
+        self.refine = refine
+        self.width = width
+        self.per_step = per_step
+        self.batch = batch
+        self.surrogate = surrogate
+        self.keep = keep_fraction
+
+    def _score(self, progs: List[np.ndarray]):
+        from .surrogate import exact_scores
+        from . import hedl_sync_status
+        flat = np.concatenate(progs).astype(np.uint64)
+        offs = np.zeros(len(progs) + 1, np.uint32)
+        np.cumsum([len(p) for p in progs], out=offs[1:])
+        counts, _ = exact_scores(self.dkb, flat, offs)
+        return counts.cpu().numpy().view(np.uint32)
+
+    def run(self, start: List[np.ndarray], steps: int):
+        t0 = time.perf_counter()
+        beam = [Entry(canonical(p), 0.0, 0.0, (0, 0, 0, 0)) for p in start]
+        c = self._score([e.prog for e in beam])
+        a, f = scores(c)
+        beam = [Entry(e.prog, float(a[i]), float(f[i]), tuple(int(x) for x in c[i])) for i, e in enumerate(beam)]
+        beam = beam_update(beam, [], self.width)
+        logs = []
+        best = beam[0].acc
+        for s in range(1, steps + 1):
+            ts = time.perf_counter()
+            raw = self.refine([e.prog for e in beam], s, self.per_step)
+            cands, seen = [], {e.prog.tobytes() for e in beam}
+            for p in raw:
+                cp = canonical(p)
+                b = cp.tobytes()
+                if b not in seen:
+                    seen.add(b)
+                    cands.append(cp)
+            order = list(range(len(cands)))
+            if self.surrogate is not None and cands:
+                flat = np.concatenate(cands).astype(np.uint64)
+                offs = np.zeros(len(cands) + 1, np.uint32)
+                np.cumsum([len(p) for p in cands], out=offs[1:])
+                Y = self.surrogate.predict(self.surrogate.encode(flat, offs)).cpu().numpy()
+                order = sorted(order, key=lambda i: (-Y[i, 0], -Y[i, 1], i))
+                if self.keep is not None:
+                    order = order[:max(1, int(round(self.keep * len(order))))]
+            entries = [None] * len(cands)
+            log = StepLog(s, len(cands), len(order), best, 0.0)
+            for b0 in range(0, len(order), self.batch):
+                ids = order[b0:b0 + self.batch]
+                c = self._score([cands[i] for i in ids])
+                a, f = scores(c)
+                for j, i in enumerate(ids):
+                    entries[i] = Entry(cands[i], float(a[j]), float(f[j]), tuple(int(x) for x in c[j]))
+                best = max(best, float(a.max()) if len(a) else best)
+                log.events.append((time.perf_counter() - t0, best))
+            beam = beam_update(beam, [e for e in entries if e is not None], self.width)
+            log.best_acc = beam[0].acc
+            log.seconds = time.perf_counter() - ts
+            logs.append(log)
+        return beam, logs
