@@ -167,6 +167,139 @@ def cpu_baseline(kb, progs, budget_s: float = 12.0):
                       f"hypothesis-parallel on {cores} host threads ({dt:.1f} s)"}
 
 
+def _pack(progs):
+    from synth import programs as P
+    return P.pack_batch(progs)
+
+
+def surrogate_round(args, dev):
+    """One surrogate-ranked round on a planted KB with the single-hypothesis workload's
+    distributions: train on engine-scored hypotheses, rank 65,536 candidates, score the
+    predicted top 5 % exactly; recall@100 against the exact ranking and best-found/sec
+    against the plain batched path (every candidate scored, in generation order)."""
+    import torch
+    import paper_2412_00802_gb300 as H
+    from paper_2412_00802_gb300 import surrogate as sg
+    from oracle import surrogate as OS
+    from synth import hyps, kb as K
+    full = args.surrogate_full
+    cfg = K.CONFIGS["c4"] if full else K.CONFIGS["c4"].scaled(1_000_000)
+    t0 = time.perf_counter()
+    kb = K.generate(cfg)
+    gen_s = time.perf_counter() - t0
+    dkb = H.DeviceKB.from_synth(kb, device=str(dev))
+    tg = hyps.TreeGen(kb, 404, share=0.3)
+    n_train = 1_000_000 if full else 65_536
+    B = 4096
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    s = sg.Surrogate(seed=4, device=str(dev), grid=sg.threshold_grid(kb.prop_vals))
+    for b in range(n_train // B):
+        flat, offs = _pack(hyps.batch_hyps(kb, 404, b, B, gen=tg))
+        _, T = sg.exact_scores(dkb, flat, offs)
+        Xs.append(s.encode(flat, offs))
+        Ts.append(T)
+    X = torch.cat(Xs)
+    T = torch.cat(Ts)
+    torch.cuda.synchronize()
+    score_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = s.train(X, T, epochs=20, batch=B, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    cand = hyps.batch_hyps(kb, 405, 0, 65_536, gen=tg)
+    cflat, coffs = _pack(cand)
+    # plain batched path: all candidates, in generation order
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_at, exact = [], []
+    for b0 in range(0, len(cand), B):
+        f, o = _pack(cand[b0:b0 + B])
+        _, T = sg.exact_scores(dkb, f, o)
+        exact.append(T.cpu().numpy())
+        done_at.append(time.perf_counter() - t0)
+    exact = np.concatenate(exact)
+    order = OS.rank_order(exact[:, 0], exact[:, 1], cand)
+    best = order[0]
+    plain_s = done_at[best // B]
+    # surrogate path: encode, predict, keep the top 5 %, score those exactly
+    k = int(round(0.05 * len(cand)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Y = s.predict(s.encode(cflat, coffs))
+    sel = s.select(Y, k).cpu().numpy()
+    f, o = _pack([cand[i] for i in sel])
+    _, Tsel = sg.exact_scores(dkb, f, o)
+    Tsel = Tsel.cpu().numpy()
+    sur_s = time.perf_counter() - t0
+    found = bool(best in set(sel.tolist()))
+    top_pred = np.argsort(-Y[:, 0].cpu().numpy(), kind="stable")[:100]
+    return {"workload": ("planted KB with the single-hypothesis workload's distributions, N=" + f"{cfg.n:,}"
+                         + f"; {n_train:,} engine-scored training hypotheses; 65,536 candidates, top 5 % scored"),
+            "kb_gen_s": gen_s, "train_scoring_s": score_s, "train_s": train_s, "train_loss": [losses[0], losses[-1]],
+            "recall_at_100": OS.recall_at(100, order, sel), "recall_strict_top100": OS.recall_at(100, order, top_pred),
+            "selected": k, "best_found": found, "best_acc": float(exact[best, 0]),
+            "best_found_per_s": (1.0 / sur_s) if found else 0.0, "best_found_per_s_plain": 1.0 / plain_s,
+            "surrogate_round_s": sur_s, "plain_time_to_best_s": plain_s}
+
+
+def search_run(args, dev):
+    """The refinement beam search on a planted KB with the search workload's distributions:
+    exhaustive (every candidate scored) against surrogate-ordered with pruning."""
+    import torch
+    import paper_2412_00802_gb300 as H
+    from paper_2412_00802_gb300.search import BeamSearch
+    from paper_2412_00802_gb300.surrogate import Surrogate, exact_scores
+    from synth import hyps, kb as K, programs as P
+    from synth.refine import Refiner
+    full = args.search_full
+    cfg = K.CONFIGS["c5"] if full else K.CONFIGS["c5"].scaled(500_000, n_roles=16, n_props=8, n_concepts=100)
+    kb = K.generate(cfg)
+    dkb = H.DeviceKB.from_synth(kb, device=str(dev))
+    ref = Refiner(kb, 505)
+
+    def refine(beam_progs, step, count):
+        return [np.array(n.postfix(), np.uint64) for n in ref.refine([P.from_postfix(p) for p in beam_progs], step,
+                                                                      count)]
+    start = [np.array(n.postfix(), np.uint64) for n in ref.start()]
+    steps = 20 if full else 5
+    from paper_2412_00802_gb300.surrogate import threshold_grid
+    sur = Surrogate(seed=5, device=str(dev), grid=threshold_grid(kb.prop_vals))
+    tg = hyps.TreeGen(kb, 506, share=0.3)
+    Xs, Ts = [], []
+    for b in range(8):
+        flat, offs = _pack(hyps.batch_hyps(kb, 506, b, 4096, gen=tg))
+        _, T = exact_scores(dkb, flat, offs)
+        Xs.append(sur.encode(flat, offs))
+        Ts.append(T)
+    sur.train(torch.cat(Xs), torch.cat(Ts), epochs=20, batch=4096, lr=2e-3)
+    out = {"workload": f"planted KB with the search workload's distributions, N={cfg.n:,}, {kb.n_roles} roles; "
+                       f"beam 64, 8,192 refinements per step, {steps} steps"}
+    res = {}
+    for name, kw in (("exhaustive", {}), ("surrogate_pruned", {"surrogate": sur, "keep_fraction": 0.25})):
+        t0 = time.perf_counter()
+        beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=4096, **kw).run(start, steps)
+        res[name] = (beam, logs, time.perf_counter() - t0)
+    eb, el, et = res["exhaustive"]
+    sb, sl, st = res["surrogate_pruned"]
+    target = eb[0].acc
+
+    def first_reach(logs):
+        for l in logs:
+            for t, b in l.events:
+                if b >= target:
+                    return t
+        return None
+    te, ts = first_reach(el), first_reach(sl)
+    out.update({"exhaustive_s": et, "pruned_s": st, "best_acc": target, "pruned_best_acc": sb[0].acc,
+                "best_found_per_s_exhaustive": 1.0 / te if te else 0.0,
+                "best_found_per_s_surrogate": 1.0 / ts if ts else 0.0,
+                "evaluated_exhaustive": sum(l.evaluated for l in el), "evaluated_pruned": sum(l.evaluated for l in sl),
+                "same_final_beam": [e.prog.tobytes() for e in eb] == [e.prog.tobytes() for e in sb],
+                "best": P.to_text(P.from_postfix(eb[0].prog))})
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -318,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
         return
     cpu = None if args.no_cpu else cpu_baseline(kb, make_batch(kb, timed_ids[0], gen))
     clocks = clk.summary()
+    surrogate = None if args.no_surrogate else surrogate_round(args, dev)
+    search = None if args.no_search else search_run(args, dev)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_ids),
         "warmup": len(warm_ids), "ms_per_step": 1000.0 * elapsed / len(timed_ids), "higher_is_better": True,
@@ -341,6 +476,8 @@ def run_ours(args, rank, world, local_rank):
                  "role_ops": info0["n_role_ops"], "role_ops_without_sharing": ncse["n_role_ops"],
                  "model_bytes": info0["model_bytes"], "model_bytes_without_sharing": ncse["model_bytes"]},
         "effective_frac_unshared": value / world * (ncse["model_bytes"] / BATCH) / 1e9 / peak,
+        "surrogate": surrogate,
+        "search": search,
     }
     print(json.dumps(out), flush=True)
 
@@ -355,6 +492,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-ranked round")
+    ap.add_argument("--no-search", action="store_true", help="skip the beam-search comparison")
+    ap.add_argument("--surrogate-full", action="store_true",
+                    help="surrogate round at full size (10M individuals, 1M training hypotheses)")
+    ap.add_argument("--search-full", action="store_true",
+                    help="search at full size (4M individuals, 64 roles, 20 steps)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="hypotheses per step (smaller only for profiling captures)")
     args = ap.parse_args()

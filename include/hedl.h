@@ -341,10 +341,13 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
 /* Structural encoding of H programs (DEVICE progs uint64[offs[H]], offs
  * uint32[H+1]) into X (DEVICE bf16 [H][512] as uint16 bit patterns): integer
  * feature counts scaled by 1/4 (op histogram per depth, concept / role /
- * property / cardinality / threshold-exponent histograms, length and height
- * one-hots, totals, a constant).  Instructions that are not op codes are
- * ignored.  Asynchronous. */
-int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, uint16_t *X, hedl_stream s);
+ * property / cardinality histograms, role-over-atom pairs, data thresholds
+ * bucketed by grid, length and height, totals, a constant).  grid (DEVICE
+ * float [n_grid][15], or NULL) holds each property's 15 increasing threshold
+ * boundaries: a threshold t of property p lands in bucket #{g < t}.
+ * Instructions that are not op codes are ignored.  Asynchronous. */
+int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
+                uint16_t *X, hedl_stream s);
 
 /* Y (DEVICE float [B][2]) = the network applied to X (DEVICE bf16 [B][512]). */
 int hedl_mlp_forward(hedl_mlp *m, const uint16_t *X, uint32_t B, float *Y, void *ws, size_t ws_bytes,

@@ -17,20 +17,23 @@ library):
 
 Encoding (feature index ranges; every value is an integer count scaled by
 1/4, exact in bfloat16).  Node depth is the distance from the root (root 0),
-clamped to 7; "height" is the tree height (leaves 1), clamped to 8.
+clamped to 7; "height" is the tree height (leaves 1), clamped to 8.  A data
+threshold t of property p falls in bucket q = #{g in grid[p] : g < t} of a
+per-property grid of 15 increasing boundaries (the property's quantiles,
+supplied with the programs; q = 0 without a grid or for NaN t).
   [  0,112) op histogram per depth: 14 ops x 8 depths, index depth*14 + op-1
-  [112,240) atomic concept histogram: concept id mod 128
-  [240,304) role histogram: (role id mod 32)*2 + inverse flag
-  [304,344) role-restriction kind per depth: depth*5 + (op - EXISTS)
-  [344,368) cardinality: (op - ATLEAST)*8 + min(n, 7)
-  [368,392) data restriction: (property id mod 8)*3 + (op - DGE)
-  [392,440) threshold magnitude: (op - DGE)*16 + bucket, bucket from the
-            float32 exponent field e of the threshold: clamp(e - 118, 0, 15)
-  [440,480) program length one-hot: min(len, 40) - 1
-  [480,488) height one-hot: min(height, 8) - 1
-  [488,492) counts of leaves, role restrictions, data restrictions, NOTs
-  [492]     constant 4 (a bias input; 4 * 1/4 = 1)
-  [493,512) zero
+  [112,208) atomic concept histogram: concept id mod 96
+  [208,272) role histogram: (role id mod 32)*2 + inverse flag
+  [272,312) role-restriction kind per depth: depth*5 + (op - EXISTS)
+  [312,336) cardinality: (op - ATLEAST)*8 + min(n, 7)
+  [336,384) data restriction: (property id mod 16)*3 + (op - DGE)
+  [384,432) threshold bucket: (op - DGE)*16 + q
+  [432,496) role restriction over an atom: ((role*2 + inverse)*131 + concept) mod 64
+  [496,504) length bucket: min(len, 39) // 5
+  [504,508) counts of leaves, role restrictions, data restrictions, NOTs
+  [508]     height - 1 (clamped to 7)
+  [509]     constant 4 (a bias input; 4 * 1/4 = 1)
+  [510,512) zero
 """
 from __future__ import annotations
 
@@ -55,9 +58,10 @@ def _arity(op: int) -> int:
     return 0
 
 
-def encode(prog: Sequence[int]) -> np.ndarray:
+def encode(prog: Sequence[int], grid=None) -> np.ndarray:
     """Structural encoding of one postfix program (float32[512]).
 
+    grid: per-property threshold boundaries, float32 [n_props][15], or None.
     A program longer than 256 instructions is encoded by its last 256 (the
     root and the nodes nearest to it)."""
     prog = list(prog)[-256:]
@@ -83,32 +87,48 @@ def encode(prog: Sequence[int]) -> np.ndarray:
         if _arity(op) == 0:
             leaves += 1
         if op == _ATOM:
-            f[112 + a % 128] += 1
+            f[112 + a % 96] += 1
         elif _EX <= op <= _EXACT:
             roles += 1
-            f[240 + (a % 32) * 2 + inv] += 1
-            f[304 + d * 5 + (op - _EX)] += 1
+            f[208 + (a % 32) * 2 + inv] += 1
+            f[272 + d * 5 + (op - _EX)] += 1
             if op >= _MIN:
-                f[344 + (op - _MIN) * 8 + min(b, 7)] += 1
+                f[312 + (op - _MIN) * 8 + min(b, 7)] += 1
+            child = int(prog[k - 1])       # the filler ends right before its restriction
+            if child & 0xFF == _ATOM:
+                f[432 + (((a * 2 + inv) * 131 + ((child >> 16) & 0xFFFF)) % 64)] += 1
         elif _GE <= op <= _EQ:
             datas += 1
-            f[368 + (a % 8) * 3 + (op - _GE)] += 1
-            e = (b >> 23) & 0xFF
-            f[392 + (op - _GE) * 16 + min(max(e - 118, 0), 15)] += 1
+            f[336 + (a % 16) * 3 + (op - _GE)] += 1
+            t = np.array([b], np.uint32).view(np.float32)[0]
+            q = 0
+            if grid is not None and a < len(grid) and not np.isnan(t):
+                q = int(np.sum(np.asarray(grid[a], np.float32) < t))
+            f[384 + (op - _GE) * 16 + q] += 1
         elif op == _NOT:
             nots += 1
-    f[440 + min(L, 40) - 1] += 1
-    f[480 + min(height, 8) - 1] += 1
-    f[488] += leaves
-    f[489] += roles
-    f[490] += datas
-    f[491] += nots
-    f[492] += 4
+    f[496 + min(L, 39) // 5] += 1
+    f[504] += leaves
+    f[505] += roles
+    f[506] += datas
+    f[507] += nots
+    f[508] += min(height, 8) - 1
+    f[509] += 4
     return (f.astype(np.float64) * 0.25).astype(np.float32)
 
 
-def encode_batch(progs: Sequence[Sequence[int]]) -> np.ndarray:
-    return np.stack([encode(p) for p in progs]) if len(progs) else np.zeros((0, D_IN), np.float32)
+def threshold_grid(prop_vals: np.ndarray) -> np.ndarray:
+    """15 quantile boundaries (1/16 .. 15/16) of each property's present values, float32."""
+    out = np.zeros((prop_vals.shape[0], 15), np.float32)
+    for p in range(prop_vals.shape[0]):
+        v = prop_vals[p][~np.isnan(prop_vals[p])]
+        if v.size:
+            out[p] = np.quantile(v.astype(np.float64), np.arange(1, 16) / 16.0).astype(np.float32)
+    return out
+
+
+def encode_batch(progs: Sequence[Sequence[int]], grid=None) -> np.ndarray:
+    return np.stack([encode(p, grid) for p in progs]) if len(progs) else np.zeros((0, D_IN), np.float32)
 
 
 # ---------------------------------------------------------------------------- bfloat16

@@ -37,7 +37,7 @@ constexpr int ENC_MAXLEN = 256;
 // postfix is a pre-order walk), then the lanes count features into shared
 // memory and write the row as bf16 (counts x 1/4, exact).
 __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t *__restrict__ offs, uint32_t H,
-                              __nv_bfloat16 *__restrict__ X) {
+                              const float *__restrict__ grid, uint32_t n_grid, __nv_bfloat16 *__restrict__ X) {
     constexpr int WARPS = 4;
     __shared__ uint32_t feat[WARPS][DI];
     __shared__ uint8_t depth[WARPS][ENC_MAXLEN];
@@ -74,28 +74,36 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             if (op < HEDL_OP_ATOM || op > HEDL_OP_DEQ) continue;   // not an op code: ignored
             const uint32_t d = min((uint32_t)depth[warp][k], 7u);
             atomicAdd(&feat[warp][d * 14 + op - 1], 1u);
-            if (arity_of(op) == 0) atomicAdd(&feat[warp][488], 1u);
+            if (arity_of(op) == 0) atomicAdd(&feat[warp][504], 1u);
             if (op == HEDL_OP_ATOM) {
-                atomicAdd(&feat[warp][112 + a % 128], 1u);
+                atomicAdd(&feat[warp][112 + a % 96], 1u);
             } else if (op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY) {
-                atomicAdd(&feat[warp][489], 1u);
-                atomicAdd(&feat[warp][240 + (a % 32) * 2 + inv], 1u);
-                atomicAdd(&feat[warp][304 + d * 5 + (op - HEDL_OP_EXISTS)], 1u);
-                if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][344 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1u);
+                atomicAdd(&feat[warp][505], 1u);
+                atomicAdd(&feat[warp][208 + (a % 32) * 2 + inv], 1u);
+                atomicAdd(&feat[warp][272 + d * 5 + (op - HEDL_OP_EXISTS)], 1u);
+                if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][312 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1u);
+                if (k > 0) {   // the filler ends right before its restriction
+                    const uint64_t c = progs[o0 + k - 1];
+                    if ((c & 0xFF) == HEDL_OP_ATOM)
+                        atomicAdd(&feat[warp][432 + ((a * 2 + inv) * 131 + (uint32_t)((c >> 16) & 0xFFFF)) % 64], 1u);
+                }
             } else if (op >= HEDL_OP_DGE) {
-                atomicAdd(&feat[warp][490], 1u);
-                atomicAdd(&feat[warp][368 + (a % 8) * 3 + (op - HEDL_OP_DGE)], 1u);
-                const int e = (int)((b >> 23) & 0xFF);
-                atomicAdd(&feat[warp][392 + (op - HEDL_OP_DGE) * 16 + min(max(e - 118, 0), 15)], 1u);
+                atomicAdd(&feat[warp][506], 1u);
+                atomicAdd(&feat[warp][336 + (a % 16) * 3 + (op - HEDL_OP_DGE)], 1u);
+                const float t = __uint_as_float(b);
+                uint32_t q = 0;
+                if (grid && a < n_grid && !(t != t))
+                    for (int g = 0; g < 15; ++g) q += grid[a * 15 + g] < t ? 1u : 0u;
+                atomicAdd(&feat[warp][384 + (op - HEDL_OP_DGE) * 16 + q], 1u);
             } else if (op == HEDL_OP_NOT) {
-                atomicAdd(&feat[warp][491], 1u);
+                atomicAdd(&feat[warp][507], 1u);
             }
         }
         __syncwarp();
         if (lane == 0) {
-            feat[warp][440 + min(L, 40u) - 1] += 1;
-            feat[warp][480 + min(height[warp], 8u) - 1] += 1;
-            feat[warp][492] += 4;
+            feat[warp][496 + min(L, 39u) / 5] += 1;
+            feat[warp][508] += min(height[warp], 8u) - 1;
+            feat[warp][509] += 4;
         }
         __syncwarp();
         for (int i = lane; i < DI; i += 32)
@@ -633,11 +641,12 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes) {
     return HEDL_OK;
 }
 
-int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, uint16_t *X, hedl_stream s) {
+int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
+                uint16_t *X, hedl_stream s) {
     if (!progs || !offs || !X) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     if (H == 0) return HEDL_OK;
-    encode_kernel<<<std::min<uint32_t>((H + 3) / 4, 8192), 128, 0, (cudaStream_t)s>>>(progs, offs, H,
-                                                                                      (__nv_bfloat16 *)X);
+    encode_kernel<<<std::min<uint32_t>((H + 3) / 4, 8192), 128, 0, (cudaStream_t)s>>>(
+        progs, offs, H, grid, grid ? n_grid : 0u, (__nv_bfloat16 *)X);
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(e, "encode launch") : HEDL_OK;
 }

@@ -44,12 +44,24 @@ def split_params(p: np.ndarray) -> dict:
     return out
 
 
+def threshold_grid(prop_vals: np.ndarray) -> np.ndarray:
+    """15 quantile boundaries (1/16 .. 15/16) of each property's present values (a KB statistic)."""
+    out = np.zeros((prop_vals.shape[0], 15), np.float32)
+    for p in range(prop_vals.shape[0]):
+        v = prop_vals[p][~np.isnan(prop_vals[p])]
+        if v.size:
+            out[p] = np.quantile(v.astype(np.float64), np.arange(1, 16) / 16.0).astype(np.float32)
+    return out
+
+
 class Surrogate:
-    def __init__(self, params: Optional[np.ndarray] = None, seed: int = 0, device: str = "cuda"):
+    def __init__(self, params: Optional[np.ndarray] = None, seed: int = 0, device: str = "cuda",
+                 grid: Optional[np.ndarray] = None):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.mlp = hedl_mlp_create(init_params(seed) if params is None else params)
+        self.grid = None if grid is None else torch.from_numpy(np.ascontiguousarray(grid, np.float32)).to(self.device)
         self._ws = None
 
     def _workspace(self, B: int):
@@ -67,7 +79,7 @@ class Surrogate:
         p = torch.from_numpy(np.ascontiguousarray(progs, np.uint64).view(np.int64)).to(self.device)
         o = torch.from_numpy(np.ascontiguousarray(offs, np.uint32).view(np.int32)).to(self.device)
         X = torch.empty((len(offs) - 1, D_IN), dtype=torch.bfloat16, device=self.device)
-        hedl_encode(p, o, X)
+        hedl_encode(p, o, X, self.grid)
         return X
 
     def predict(self, X, batch: int = 65536):

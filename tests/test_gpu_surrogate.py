@@ -40,6 +40,10 @@ def test_encoder_bit_exact(env):
     got = sg.Surrogate().encode(flat, offs).float().cpu().numpy()
     want = S.encode_batch(progs)
     assert np.array_equal(got, want)
+    grid = S.threshold_grid(kb.prop_vals)
+    got = sg.Surrogate(grid=grid).encode(flat, offs).float().cpu().numpy()
+    assert np.array_equal(got, S.encode_batch(progs, grid))
+    assert np.array_equal(grid, sg.threshold_grid(kb.prop_vals))
 
 
 def _xt(torch, kb, n, seed):
@@ -144,7 +148,7 @@ def test_trained_surrogate_ranks_better_than_chance(env):
     train = hyps.batch_hyps(kb, 51, 0, 24576, lmax=20, dmax=6, gen=gen)
     flat, offs = P.pack_batch(train)
     _, T = sg.exact_scores(dkb, flat, offs)
-    s = sg.Surrogate(seed=1)
+    s = sg.Surrogate(seed=1, grid=sg.threshold_grid(kb.prop_vals))
     X = s.encode(flat, offs)
     losses = s.train(X, T, epochs=20, batch=2048, lr=2e-3)
     assert losses[-1] < losses[0]

@@ -9,25 +9,30 @@ from synth import programs as P
 
 
 def test_encoding_hand_worked():
-    # (and A1 (some r2- A3)): AND depth 0; A1, EXISTS depth 1; A3 depth 2
+    # (and A1 (some r2- A3)), postfix A1 A3 EXISTS AND: AND depth 0; A1, EXISTS depth 1; A3 depth 2
     f = S.encode(P.compile_text("(and A1 (some r2- A3))"))
     want = np.zeros(512, np.float32)
     for i, c in {0 * 14 + 4: 1, 1 * 14 + 0: 1, 1 * 14 + 6: 1, 2 * 14 + 0: 1,   # op x depth
                  112 + 1: 1, 112 + 3: 1,                                         # concepts
-                 240 + 2 * 2 + 1: 1,                                             # role 2 inverted
-                 304 + 1 * 5 + 0: 1,                                             # EXISTS at depth 1
-                 440 + 3: 1, 480 + 2: 1,                                         # length 4, height 3
-                 488: 2, 489: 1, 492: 4}.items():                                # leaves, roles, bias
+                 208 + 2 * 2 + 1: 1,                                             # role 2 inverted
+                 272 + 1 * 5 + 0: 1,                                             # EXISTS at depth 1
+                 432 + ((2 * 2 + 1) * 131 + 3) % 64: 1,                          # role 2^- over atom 3
+                 496 + 4 // 5: 1,                                                # length 4
+                 504: 2, 505: 1, 508: 3 - 1, 509: 4}.items():                    # leaves, roles, height, bias
         want[i] = 0.25 * c
     assert np.array_equal(f, want)
-    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1; prop 9 mod 8 = 1; exponent of 1.0 is 127
+    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1, no atom filler
     f = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"))
     want = np.zeros(512, np.float32)
-    for i, c in {0 * 14 + 8: 1, 1 * 14 + 11: 1, 240 + 0: 1, 304 + 2: 1, 344 + 0 * 8 + 3: 1,
-                 368 + 1 * 3 + 0: 1, 392 + 0 * 16 + 9: 1, 440 + 1: 1, 480 + 1: 1, 488: 1, 489: 1, 490: 1,
-                 492: 4}.items():
+    for i, c in {0 * 14 + 8: 1, 1 * 14 + 11: 1, 208 + 0: 1, 272 + 2: 1, 312 + 0 * 8 + 3: 1,
+                 336 + 9 * 3 + 0: 1, 384 + 0: 1, 496: 1, 504: 1, 505: 1, 506: 1, 508: 1, 509: 4}.items():
         want[i] = 0.25 * c
     assert np.array_equal(f, want)
+    # with a grid, 1.0 lies above 7 of property 9's 15 boundaries (0.3 .. 1.7 step 0.1, 1.0 excluded)
+    grid = np.zeros((10, 15), np.float32)
+    grid[9] = np.float32(0.3) + np.float32(0.1) * np.arange(15, dtype=np.float32)
+    g = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"), grid)
+    assert g[384 + 7] == 0.25 and g[384] == 0.0 and int(np.sum(grid[9] < np.float32(1.0))) == 7
 
 
 def test_bf16_rounding():
