@@ -175,6 +175,9 @@ typedef struct hedl_plan hedl_plan;
 #define HEDL_NO_GRAPH   2u   /* launch directly instead of replaying a CUDA graph */
 #define HEDL_PLAIN      4u   /* one launch per operation per hypothesis */
 #define HEDL_LEVELS     8u   /* one launch per dependency level, no device waits */
+#define HEDL_NO_SLICE  16u   /* evaluate every role restriction on its own CSR walk
+                                (default: up to 32 restrictions of one role and
+                                direction that become ready together share one walk) */
 #define HEDL_TEST_UNSAT_DEP 0x100u  /* TEST HOOK: add a dependency nothing
                                         satisfies, so the bounded device wait
                                         gives up (the call then reports
@@ -189,6 +192,7 @@ typedef struct {
     uint32_t n_items;        /* (segment, tile) work items */
     uint32_t tile_words;
     uint32_t n_role_ops;     /* role restrictions evaluated (after sharing) */
+    uint32_t n_role_groups;  /* shared CSR walks of bit-sliced role restrictions */
     uint32_t n_data_ops;
     uint32_t n_atom_loads;
     uint64_t total_insns;    /* instructions in the input programs */

@@ -34,6 +34,7 @@ HEDL_NO_CSE = 1
 HEDL_NO_GRAPH = 2
 HEDL_PLAIN = 4
 HEDL_LEVELS = 8
+HEDL_NO_SLICE = 16
 HEDL_TEST_UNSAT_DEP = 0x100
 HEDL_MAX_STACK = 64
 HEDL_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -68,7 +69,8 @@ class hedl_kb_desc(ctypes.Structure):
 
 class hedl_plan_info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("n_hyps", "n_nodes", "n_segments", "n_slots", "n_levels", "n_items",
-                                                "tile_words", "n_role_ops", "n_data_ops", "n_atom_loads")] + \
+                                                "tile_words", "n_role_ops", "n_role_groups", "n_data_ops",
+                                                "n_atom_loads")] + \
                [(k, ctypes.c_uint64) for k in ("total_insns", "workspace_bytes", "model_bytes")]
 
 

@@ -147,6 +147,149 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
     }
 }
 
+// ------------------------------------------------------------------ bit-sliced role groups
+// 32 x 32 bit transpose across a warp: lane r holds row r (bit c = column c)
+// on entry and column r on exit.  Five butterfly stages swap the
+// off-diagonal blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const uint32_t j = 16u >> st, m = masks[st];
+        const uint32_t t = __shfl_xor_sync(FULL, x, j);
+        x = (lane & j) ? ((x & ~m) | ((t >> j) & m)) : ((x & m) | ((t & m) << j));
+    }
+    return x;
+}
+
+// Transpose task: FT[i] bit s = slice s's filler at individual i (its
+// complement for REF_NEG slices), one 32-word pass per warp at a time.
+template <int NW>
+__device__ void run_transpose(const ExecArgs &A, const PlanHeader &hd, const RGroup *gp, uint32_t tile,
+                              const uint32_t *slots) {
+    const KBView &kb = A.kb;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t n = gp->n;
+    const uint32_t ref = lane < n ? gp->filler[lane] : 0u;
+    const uint32_t id = ref & REF_ID;
+    const uint32_t *src = (ref & REF_SLOT) ? slots + (uint64_t)id * kb.wp : kb.concepts + (uint64_t)id * kb.wp;
+    const uint32_t x = (ref & REF_NEG) ? FULL : 0u;
+    uint32_t *ft = reinterpret_cast<uint32_t *>(A.ws + gp->ft_off);
+    const uint32_t passes = hd.tile_words / (NW * 32u);
+    for (uint32_t p = 0; p < passes; ++p) {
+        const uint32_t wb = tile * hd.tile_words + (p * NW + warp) * 32u;
+        if (wb >= kb.w) break;
+        for (uint32_t j = 0; j < 32u; ++j) {
+            const uint32_t w = wb + j;
+            if (w >= kb.w) break;
+            const uint32_t v = lane < n ? (src[w] ^ x) : 0u;
+            ft[32ull * w + lane] = transpose32(v, lane);
+        }
+    }
+}
+
+// v = v + x per slice, saturating at 7 (planes c0 < c1 < c2).
+__device__ __forceinline__ void sat_add1(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t x) {
+    x &= ~(c0 & c1 & c2);
+    const uint32_t k1 = c0 & x;
+    c0 ^= x;
+    const uint32_t k2 = c1 & k1;
+    c1 ^= k1;
+    c2 |= k2;
+}
+
+// a = a + b per slice (3-bit values), saturating at 7.
+__device__ __forceinline__ void sat_add3(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t b0, uint32_t b1,
+                                         uint32_t b2) {
+    const uint32_t s0 = a0 ^ b0, k0 = a0 & b0;
+    const uint32_t s1 = a1 ^ b1 ^ k0, k1 = (a1 & b1) | (k0 & (a1 ^ b1));
+    const uint32_t s2 = a2 ^ b2 ^ k1, k2 = (a2 & b2) | (k1 & (a2 ^ b2));
+    a0 = s0 | k2;
+    a1 = s1 | k2;
+    a2 = s2 | k2;
+}
+
+constexpr uint32_t HEAVY_ROW = 64;   // longer rows are walked by the whole warp
+
+// Walk task: for each individual, the saturating per-slice count of its
+// successors' FT words, mapped through the group's truth table, transposed
+// back into the 32 output slots.  Rows longer than HEAVY_ROW are walked by
+// the whole warp, 32 edges at a time, and their counts reduced across lanes.
+template <int NW>
+__device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *gp, uint32_t tile,
+                         uint32_t *slots) {
+    const KBView &kb = A.kb;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const DevCSR g = kb.csr[gp->role2];
+    const uint32_t *__restrict__ rp = g.rp;
+    const uint32_t *__restrict__ col = g.col;
+    const uint32_t *ft = reinterpret_cast<const uint32_t *>(A.ws + gp->ft_off);
+    uint32_t want[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) want[v] = gp->want[v];
+    const uint32_t n = gp->n;
+    const uint32_t my_out = lane < n ? gp->out[lane] : 0u;
+    const uint32_t passes = hd.tile_words / (NW * 32u);
+    for (uint32_t p = 0; p < passes; ++p) {
+        const uint32_t wb = tile * hd.tile_words + (p * NW + warp) * 32u;
+        if (wb >= kb.wp) break;
+        for (uint32_t j = 0; j < 32u; ++j) {
+            const uint32_t w = wb + j;
+            if (w >= kb.wp) break;
+            const uint32_t i = w * 32u + lane;
+            const bool valid = w < kb.w && i < kb.n;
+            uint32_t lo = 0, hi = 0;
+            if (valid) {
+                lo = ld_stream(rp + i);
+                hi = ld_stream(rp + i + 1);
+            }
+            uint32_t c0 = 0, c1 = 0, c2 = 0;
+            const bool heavy = hi - lo > HEAVY_ROW;
+            if (!heavy) {
+                uint32_t k = lo;
+                for (; k + 4 <= hi; k += 4) {
+                    const uint32_t b0 = ld_stream(col + k), b1 = ld_stream(col + k + 1);
+                    const uint32_t b2 = ld_stream(col + k + 2), b3 = ld_stream(col + k + 3);
+                    const uint32_t x0 = ft[b0], x1 = ft[b1], x2 = ft[b2], x3 = ft[b3];
+                    sat_add1(c0, c1, c2, x0);
+                    sat_add1(c0, c1, c2, x1);
+                    sat_add1(c0, c1, c2, x2);
+                    sat_add1(c0, c1, c2, x3);
+                }
+                for (; k < hi; ++k) sat_add1(c0, c1, c2, ft[ld_stream(col + k)]);
+            }
+            uint32_t hm = __ballot_sync(FULL, heavy);
+            while (hm) {
+                const uint32_t h = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const uint32_t hlo = __shfl_sync(FULL, lo, h), hhi = __shfl_sync(FULL, hi, h);
+                uint32_t d0 = 0, d1 = 0, d2 = 0;
+                for (uint32_t k = hlo + lane; k < hhi; k += 32u) sat_add1(d0, d1, d2, ft[ld_stream(col + k)]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint32_t e0 = __shfl_xor_sync(FULL, d0, o), e1 = __shfl_xor_sync(FULL, d1, o);
+                    const uint32_t e2 = __shfl_xor_sync(FULL, d2, o);
+                    sat_add3(d0, d1, d2, e0, e1, e2);
+                }
+                if (lane == h) {
+                    c0 = d0;
+                    c1 = d1;
+                    c2 = d2;
+                }
+            }
+            uint32_t r = 0;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t m = ((v & 4) ? c2 : ~c2) & ((v & 2) ? c1 : ~c1) & ((v & 1) ? c0 : ~c0);
+                r |= m & want[v];
+            }
+            r = valid ? r : 0u;
+            r = transpose32(r, lane);   // lane s: slice s's word w
+            if (lane < n) slots[(uint64_t)my_out * kb.wp + w] = r;
+        }
+    }
+}
+
 // Bounded wait for every producer segment of `seg` (thread 0 only).
 __device__ bool wait_deps(const PlanHeader &hd, const uint32_t *deps, const Seg &seg, uint32_t *done,
                           Counters *ctr) {
@@ -197,6 +340,7 @@ __global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
     uint32_t *done = reinterpret_cast<uint32_t *>(ctr + 1);
     uint32_t *acc = done + hd.n_segs + 1;
     uint32_t *slots = reinterpret_cast<uint32_t *>(A.ws + hd.off_slots);
+    const RGroup *rgroups = reinterpret_cast<const RGroup *>(A.ws + hd.off_rgroups);
 
     uint32_t stride_next = A.item_begin + blockIdx.x;
     for (;;) {
@@ -224,13 +368,19 @@ __global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
             __syncthreads();
             if (!sm.ok) break;
         }
-        if constexpr (STAGE) {
-            if (seg.filler != NO_FILLER) {
-                stage_filler(A.kb, slots, seg.filler, sm.filler);
-                __syncthreads();
+        if (seg.kind == TASK_TRANSPOSE) {
+            run_transpose<NW>(A, hd, rgroups + seg.code_off, tile, slots);
+        } else if (seg.kind == TASK_WALK) {
+            run_walk<NW>(A, hd, rgroups + seg.code_off, tile, slots);
+        } else {
+            if constexpr (STAGE) {
+                if (seg.filler != NO_FILLER) {
+                    stage_filler(A.kb, slots, seg.filler, sm.filler);
+                    __syncthreads();
+                }
             }
+            run_tile<NW, WPL, STAGE, BLK>(A, hd, seg, tile, sm, slots, acc);
         }
-        run_tile<NW, WPL, STAGE, BLK>(A, hd, seg, tile, sm, slots, acc);
         __syncthreads();
         if (threadIdx.x == 0 && A.use_queue) {
             __threadfence();

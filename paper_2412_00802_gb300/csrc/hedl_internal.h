@@ -61,15 +61,36 @@ constexpr uint32_t NO_HYP = 0xFFFFFFFFu;
 
 constexpr uint32_t NO_FILLER = 0xFFFFFFFFu;
 
+// A task of the work queue: a segment (kind 0), or the transpose (kind 1)
+// or walk (kind 2) of a role group (code_off = the group's index).
+enum : uint32_t { TASK_SEGMENT = 0, TASK_TRANSPOSE = 1, TASK_WALK = 2 };
+
 struct Seg {
-    uint32_t code_off;   // index into code[]
+    uint32_t code_off;   // index into code[] (segments) or rgroups[] (role groups)
     uint32_t code_len;
     uint32_t out_slot;   // NO_SLOT if none
     uint32_t hyp;        // NO_HYP if not a hypothesis root
     uint32_t dep_off;    // index into deps[]
     uint32_t dep_cnt;
     uint32_t filler;     // filler ref of its role leaf (staged plans hold at most one), or NO_FILLER
-    uint32_t level;
+    uint32_t kind;       // TASK_*
+};
+
+// Up to 32 role restrictions of one role and direction, evaluated together:
+// the transpose turns the fillers into one word per individual (bit s =
+// slice s's filler), the walk adds those words over each individual's
+// successors in bit-sliced 3-bit saturating counters and maps the counts
+// through a truth table.
+constexpr uint32_t SLICES = 32;
+constexpr uint32_t SLICE_MAX_N = 6;  // counting restrictions with n <= 6 can be sliced
+
+struct RGroup {
+    uint32_t role2;             // 2 * role + inverse
+    uint32_t n;                 // slices in use
+    uint64_t ft_off;            // byte offset of the transposed fillers (uint32 per individual)
+    uint32_t want[8];           // bit s of want[v]: slice s holds at count v (v = 7: seven or more)
+    uint32_t filler[SLICES];    // filler refs (REF_NEG: count successors outside the filler)
+    uint32_t out[SLICES];       // output slots
 };
 
 struct Group {
@@ -83,9 +104,10 @@ struct Group {
 struct PlanHeader {
     uint32_t n_items, n_segs, n_groups, n_hyps;
     uint32_t n_tiles, tile_words, n_slots, flags;
-    uint32_t n_levels, n_deps, pad0, pad1;
+    uint32_t n_levels, n_deps, n_rgroups, pad1;
     uint64_t off_segs, off_groups, off_gsegs, off_deps;
     uint64_t off_code, off_level_items, off_ctr, off_slots;
+    uint64_t off_rgroups, off_ft;
     uint64_t timeout_ns;
 };
 
@@ -172,6 +194,7 @@ struct PlanImpl {
     Tuning tuning;
     int bps = 0;                         // resident CTAs per SM of the interpreter
     bool staged = false;                 // role fillers staged in shared memory (one role leaf per segment)
+    uint32_t n_rgroups = 0;              // bit-sliced role groups
     // plain path: validated programs
     std::vector<uint64_t> progs;
     std::vector<uint32_t> offs;

@@ -253,6 +253,18 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     std::vector<uint8_t> mat(NN, 0);
     for (uint32_t i = 0; i < NN; ++i)
         if (is_role(nodes[i].op) && nodes[nodes[i].k0].op != HEDL_OP_ATOM) mat[nodes[i].k0] = 1;
+    // Bit-sliced role restrictions: each is materialized and evaluated by its
+    // role group's shared walk (counting ones need n <= SLICE_MAX_N).
+    const bool sliced = !(flags & HEDL_NO_SLICE);
+    std::vector<uint8_t> sl(NN, 0);
+    if (sliced)
+        for (uint32_t i = 0; i < NN; ++i) {
+            const PNode &n = nodes[i];
+            if (is_role(n.op) && (n.op == HEDL_OP_EXISTS || n.op == HEDL_OP_FORALL || n.b <= SLICE_MAX_N)) {
+                sl[i] = 1;
+                mat[i] = 1;
+            }
+        }
     std::vector<uint8_t> role_inline(NN, 0);
     std::vector<uint32_t> need(NN, 1);
     for (uint32_t i = 0; i < NN; ++i) {
@@ -426,7 +438,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         segs.push_back(s);
     };
     for (uint32_t i = 0; i < NN; ++i)
-        if (mat[i]) {
+        if (mat[i] && !sl[i]) {
             seg_of_slot[slot_of[i]] = (uint32_t)segs.size();
             emit_segment((int32_t)i, slot_of[i], NO_HYP);
         }
@@ -455,28 +467,132 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         delete p;
         return fail(HEDL_ERR_BAD_PROGRAM, "internal: segment stack exceeds the device limit");
     }
+    const uint32_t NSEG = (uint32_t)segs.size();
+    const uint64_t FT_BYTES = 4ull * 32ull * kb->wp;   // transposed fillers of one role group (>= 4 N)
+
+    // Production level of every slot and level of every segment, in node order
+    // (children first).  A segment reading nothing is at level 0 and one level
+    // above the slots it reads; a sliced role restriction's transpose runs one
+    // level above its filler's producer (level 0 for a concept row) and its
+    // walk, which produces its slot, one level above that.
+    std::vector<uint32_t> slot_level(n_slots, 0), seg_level(NSEG, 0);
+    auto seg_lvl = [&](uint32_t sidx) {
+        uint32_t lvl = 0;
+        for (uint32_t sl2 : seg_slots_read[sidx]) lvl = std::max(lvl, slot_level[sl2] + 1);
+        return lvl;
+    };
+    for (uint32_t i = 0; i < NN; ++i) {
+        if (!mat[i]) continue;
+        if (sl[i]) {
+            const int32_t f = nodes[i].k0;
+            const bool concept_filler = nodes[f].op == HEDL_OP_ATOM && !mat[f];
+            slot_level[slot_of[i]] = concept_filler ? 1u : slot_level[slot_of[f]] + 2u;
+        } else {
+            const uint32_t sidx = seg_of_slot[slot_of[i]];
+            seg_level[sidx] = seg_lvl(sidx);
+            slot_level[slot_of[i]] = seg_level[sidx];
+        }
+    }
+    for (uint32_t sidx = 0; sidx < NSEG; ++sidx)
+        if (segs[sidx].hyp != NO_HYP) seg_level[sidx] = seg_lvl(sidx);
+
+    // role groups: sliced restrictions keyed by (walk level, role, direction), 32 at a time
+    std::vector<RGroup> rgroups;
+    std::vector<uint32_t> task_level(seg_level);
+    std::vector<uint32_t> task_key(role_key);
+    std::vector<std::vector<uint32_t>> task_reads(seg_slots_read);
+    {
+        std::vector<std::pair<uint64_t, uint32_t>> keyed;   // ((level << 32) | role2, node)
+        for (uint32_t i = 0; i < NN; ++i)
+            if (sl[i]) keyed.push_back({((uint64_t)slot_level[slot_of[i]] << 32) | (nodes[i].a * 2 + nodes[i].inv), i});
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const std::pair<uint64_t, uint32_t> &x, const std::pair<uint64_t, uint32_t> &y) {
+                             return x.first < y.first;
+                         });
+        for (size_t k = 0; k < keyed.size();) {
+            size_t k2 = k;
+            while (k2 < keyed.size() && keyed[k2].first == keyed[k].first && k2 - k < SLICES) ++k2;
+            RGroup g{};
+            g.role2 = (uint32_t)(keyed[k].first & 0xFFFFFFFFu);
+            g.n = (uint32_t)(k2 - k);
+            std::vector<uint32_t> reads;
+            for (size_t q = k; q < k2; ++q) {
+                const uint32_t i = keyed[q].second;
+                const PNode &n = nodes[i];
+                const int32_t f = n.k0;
+                const uint32_t s_ = (uint32_t)(q - k);
+                if (nodes[f].op == HEDL_OP_ATOM && !mat[f]) {
+                    g.filler[s_] = nodes[f].a;
+                    model += B;
+                } else {
+                    g.filler[s_] = REF_SLOT | slot_of[f];
+                    reads.push_back(slot_of[f]);
+                    model += B;
+                }
+                if (n.op == HEDL_OP_FORALL) g.filler[s_] |= REF_NEG;
+                g.out[s_] = slot_of[i];
+                for (uint32_t v = 0; v < 8; ++v) {
+                    bool holds;
+                    switch (n.op) {
+                    case HEDL_OP_EXISTS: holds = v >= 1; break;
+                    case HEDL_OP_FORALL: holds = v == 0; break;   // successors outside C
+                    case HEDL_OP_ATLEAST: holds = v >= n.b; break;
+                    case HEDL_OP_ATMOST: holds = v <= n.b; break;
+                    default: holds = v == n.b; break;
+                    }
+                    if (holds) g.want[v] |= 1u << s_;
+                }
+                p->info.n_role_ops++;
+            }
+            std::sort(reads.begin(), reads.end());
+            reads.erase(std::unique(reads.begin(), reads.end()), reads.end());
+            const uint32_t gi = (uint32_t)rgroups.size();
+            const uint32_t wl = (uint32_t)(keyed[k].first >> 32);
+            // transpose task, then walk task
+            Seg t{};
+            t.code_off = gi;
+            t.out_slot = NO_SLOT;
+            t.hyp = NO_HYP;
+            t.filler = NO_FILLER;
+            t.kind = TASK_TRANSPOSE;
+            segs.push_back(t);
+            task_level.push_back(wl - 1);
+            task_key.push_back(g.role2 | 0x80000000u);
+            task_reads.push_back(reads);
+            Seg w = t;
+            w.kind = TASK_WALK;
+            const uint32_t walk_task = (uint32_t)segs.size();
+            segs.push_back(w);
+            task_level.push_back(wl);
+            task_key.push_back(g.role2);
+            task_reads.push_back({});
+            for (uint32_t s_ = 0; s_ < g.n; ++s_) seg_of_slot[g.out[s_]] = walk_task;
+            const DevCSR &csr = kb->csr_host[g.role2];
+            model += 4 * N + 4 * (N + 1) + 4ull * csr.n_edges + 4 * N + (uint64_t)g.n * B;
+            rgroups.push_back(g);
+            k = k2;
+        }
+    }
     const uint32_t NS = (uint32_t)segs.size();
 
-    // dependencies and levels
+    // dependencies (the producer task of every slot read; a walk waits for its transpose)
     std::vector<uint32_t> deps;
     uint32_t n_levels = 0;
-    for (uint32_t s = 0; s < NS; ++s) {
-        segs[s].dep_off = (uint32_t)deps.size();
-        uint32_t lvl = 0;
-        for (uint32_t sl : seg_slots_read[s]) {
-            uint32_t prod = seg_of_slot[sl];
-            deps.push_back(prod);
-            lvl = std::max(lvl, segs[prod].level + 1);
+    for (uint32_t s_ = 0; s_ < NS; ++s_) {
+        segs[s_].dep_off = (uint32_t)deps.size();
+        if (segs[s_].kind == TASK_WALK) {
+            deps.push_back(s_ - 1);
+        } else {
+            for (uint32_t sl2 : task_reads[s_]) deps.push_back(seg_of_slot[sl2]);
         }
-        segs[s].dep_cnt = (uint32_t)deps.size() - segs[s].dep_off;
-        segs[s].level = lvl;
-        n_levels = std::max(n_levels, lvl + 1);
+        segs[s_].dep_cnt = (uint32_t)deps.size() - segs[s_].dep_off;
+        n_levels = std::max(n_levels, task_level[s_] + 1);
     }
     if (flags & HEDL_TEST_UNSAT_DEP) {
         // the last segment additionally waits on a counter past the real
         // ones, which nothing ever increments
-        segs[NS - 1].dep_off = (uint32_t)deps.size();
-        segs[NS - 1].dep_cnt = 1;
+        segs[NSEG - 1].dep_off = (uint32_t)deps.size();
+        segs[NSEG - 1].dep_cnt = 1;
         deps.push_back(NS);
     }
 
@@ -487,8 +603,8 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     std::vector<uint32_t> order(NS);
     for (uint32_t s = 0; s < NS; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-        if (segs[x].level != segs[y].level) return segs[x].level < segs[y].level;
-        return role_key[x] < role_key[y];
+        if (task_level[x] != task_level[y]) return task_level[x] < task_level[y];
+        return task_key[x] < task_key[y];
     });
     std::vector<Group> groups;
     std::vector<uint32_t> gsegs;
@@ -499,9 +615,9 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         Group g{};
         g.item_begin = (uint32_t)items;
         g.seg_begin = (uint32_t)gsegs.size();
-        g.level = segs[s0].level;
+        g.level = task_level[s0];
         uint32_t k2 = k;
-        while (k2 < NS && segs[order[k2]].level == g.level && role_key[order[k2]] == role_key[s0]) {
+        while (k2 < NS && task_level[order[k2]] == g.level && task_key[order[k2]] == task_key[s0]) {
             gsegs.push_back(order[k2]);
             ++k2;
         }
@@ -537,18 +653,25 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     hd.off_deps = put(img, deps);
     hd.off_code = put(img, code);
     hd.off_level_items = put(img, level_items);
+    hd.n_rgroups = (uint32_t)rgroups.size();
     // counters: Counters + done[NS + 1] + acc[H][2]
     std::vector<uint32_t> zeros(4 + (NS + 1) + 2ull * H, 0);
     hd.off_ctr = put(img, zeros);
     p->ctr_off = hd.off_ctr;
     p->ctr_bytes = zeros.size() * 4;
+    hd.off_rgroups = put(img, rgroups);   // FT offsets patched below, once the slots are placed
     img.resize((img.size() + 255) & ~size_t(255));
     hd.off_slots = img.size();
+    hd.off_ft = (hd.off_slots + (uint64_t)n_slots * B + 255) & ~uint64_t(255);
+    for (size_t g = 0; g < rgroups.size(); ++g) rgroups[g].ft_off = hd.off_ft + g * FT_BYTES;
+    if (!rgroups.empty()) memcpy(img.data() + hd.off_rgroups, rgroups.data(), rgroups.size() * sizeof(RGroup));
     hd.timeout_ns = (uint64_t)t.timeout_ms * 1000000ull;
     memcpy(img.data(), &hd, sizeof hd);
     p->image_bytes = img.size();
     p->slots_off = hd.off_slots;
-    p->ws_bytes = hd.off_slots + (uint64_t)n_slots * B;
+    p->ws_bytes = hd.off_ft + (uint64_t)rgroups.size() * FT_BYTES;
+    p->n_rgroups = (uint32_t)rgroups.size();
+    p->info.n_role_groups = (uint32_t)rgroups.size();
     p->level_items = level_items;
 
     p->info.n_segments = NS;

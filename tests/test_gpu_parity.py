@@ -13,7 +13,7 @@ from tests.gpu_util import compare_batch, device_kb
 pytestmark = pytest.mark.gpu
 
 MODES = {"default": 0, "no_cse": H.HEDL_NO_CSE, "no_graph": H.HEDL_NO_GRAPH, "levels": H.HEDL_LEVELS,
-         "plain": H.HEDL_PLAIN}
+         "plain": H.HEDL_PLAIN, "no_slice": H.HEDL_NO_SLICE, "no_slice_levels": H.HEDL_NO_SLICE | H.HEDL_LEVELS}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -122,7 +122,7 @@ def test_ragged_sizes_every_constructor(n):
     dkb = device_kb(kb)
     r = Rng(n, 3)
     progs = [np.array(pins.random_program(r, kb, r.randint(1, 5)).postfix(), np.uint64) for _ in range(120)]
-    for mode in (0, H.HEDL_PLAIN):
+    for mode in (0, H.HEDL_PLAIN, H.HEDL_NO_SLICE):
         compare_batch(kb, dkb, progs, mode)
 
 
@@ -137,7 +137,7 @@ def test_stress_shapes_single_and_unique_subject():
         progs = [np.array(pins.random_program(r, kb, r.randint(2, 4)).postfix(), np.uint64) for _ in range(80)]
         progs += [P.compile_text(t) for t in ("(min 3000 r0 A1)", "(max 2999 r0 TOP)", "(exactly 6000 r0 TOP)",
                                                 "(all r0 A2)", "(some r0- A0)", "(min 1 r1- (not A3))")]
-        for mode in (0, H.HEDL_LEVELS, H.HEDL_PLAIN):
+        for mode in (0, H.HEDL_LEVELS, H.HEDL_PLAIN, H.HEDL_NO_SLICE):
             compare_batch(kb, dkb, progs, mode)
 
 
@@ -146,6 +146,7 @@ def test_zipf_heavy_rows():
     dkb = device_kb(kb)
     progs = hyps.batch_hyps(kb, 5, 0, 300, lmax=30, dmax=7)
     compare_batch(kb, dkb, progs, 0)
+    compare_batch(kb, dkb, progs, H.HEDL_NO_SLICE)
 
 
 def test_special_thresholds_and_counts(c1, c1_dev):
@@ -157,6 +158,21 @@ def test_special_thresholds_and_counts(c1, c1_dev):
                     np.uint64)
     progs.append(deep)
     for mode in MODES.values():
+        compare_batch(c1, c1_dev, progs, mode)
+
+
+def test_role_groups_with_every_kind_and_many_slices(c1, c1_dev):
+    """More than 32 restrictions of one role in one level, every kind, n = 0..6 sliced and
+    n = 7.. on the per-restriction walk, complemented fillers, heavy rows."""
+    texts = []
+    for k, kind in enumerate(("some", "all", "min", "max", "exactly")):
+        for n in range(0, 9):
+            for inv in ("", "-"):
+                c = f"A{(k * 9 + n) % 50}"
+                texts.append(f"({kind} r1{inv} {c})" if kind in ("some", "all") else f"({kind} {n} r1{inv} {c})")
+    texts += [f"(and A{i} (some r2 (or A{i + 1} (min {i % 5} r2- A{i + 2}))))" for i in range(40)]
+    progs = [P.compile_text(t) for t in texts]
+    for mode in (0, H.HEDL_LEVELS, H.HEDL_NO_SLICE):
         compare_batch(c1, c1_dev, progs, mode)
 
 
@@ -261,8 +277,8 @@ def c3():
     return K.generate(K.CONFIGS["c3"])
 
 
-@pytest.mark.parametrize("stage", [1, 0])
-def test_c3_full_size_batch_sampled(c3, stage):
+@pytest.mark.parametrize("stage,flags", [(1, 0), (0, 0), (1, 16)])
+def test_c3_full_size_batch_sampled(c3, stage, flags):
     """Workload 3 at full size (N = 1,000,000) in the bench's launch configuration: a whole
     4,096-hypothesis batch on the GPU; 48 sampled hypotheses checked bit-exactly (sets and
     counts) against the oracle, and the counts of all against the plain path."""
@@ -270,12 +286,12 @@ def test_c3_full_size_batch_sampled(c3, stage):
     H.hedl_tuning_set(dkb.handle, stage_fillers=stage)
     progs = hyps.batch_hyps(c3, 1003, 0, 4096, gen=hyps.TreeGen(c3, 1003, share=0.3))
     sample = sorted(set(list(range(8)) + list(range(0, 4096, 97)) + [4095]))
-    counts, _ = compare_batch(c3, dkb, progs, 0, sample=sample, check_bits=False)
+    counts, _ = compare_batch(c3, dkb, progs, flags, sample=sample, check_bits=False)
     # instance sets of the sampled hypotheses, through eval (bench-shaped plan for the counts above)
     okb = oracle.from_synth(c3)
     for h in sample[:12]:
         got = K.unpack_bits(dkb.eval(progs[h]), c3.n)
         assert np.array_equal(got, oracle.eval_program(okb, progs[h])), h
-    if stage:
+    if stage and not flags:
         plain = dkb.score(*P.pack_batch(progs), H.HEDL_PLAIN)
         assert np.array_equal(plain, counts)

@@ -124,8 +124,14 @@ def test_plan_sharing_and_levels(c1):
     plain = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, H.HEDL_NO_CSE))
     # two role restrictions in x, evaluated once with sharing
     assert shared["n_role_ops"] == 2 and plain["n_role_ops"] == 30
-    # filler, min-restriction, the shared conjunction (materialized), the roots
-    assert shared["n_levels"] == 4
+    # bit-sliced (default): filler 0, the min-restriction's transpose 1 and walk 2, the
+    # some-restriction's transpose 3 and walk 4, the roots 5 (the shared conjunction is
+    # inlined: its role restriction is already a slot)
+    assert shared["n_levels"] == 6 and shared["n_role_groups"] == 2
+    # one walk per restriction: filler, the min-restriction, the shared conjunction
+    # (materialized, it holds a role restriction), the roots
+    solo = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, H.HEDL_NO_SLICE))
+    assert solo["n_levels"] == 4 and solo["n_role_groups"] == 0 and solo["n_role_ops"] == 2
     assert shared["n_nodes"] < plain["n_nodes"]
     assert shared["model_bytes"] < plain["model_bytes"]
     # commuted operands and double negation share too
