@@ -197,6 +197,7 @@ typedef struct {
     uint32_t n_atom_loads;
     uint64_t total_insns;    /* instructions in the input programs */
     uint64_t workspace_bytes;
+    uint64_t image_bytes;    /* plan image copied host-to-device by hedl_plan_execute */
     uint64_t model_bytes;    /* algorithmic bytes of the plan (one pass) */
 } hedl_plan_info;
 

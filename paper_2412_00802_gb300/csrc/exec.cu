@@ -210,11 +210,14 @@ __device__ __forceinline__ void sat_add3(uint32_t &a0, uint32_t &a1, uint32_t &a
 }
 
 constexpr uint32_t HEAVY_ROW = 64;   // longer rows are walked by the whole warp
+constexpr uint32_t WALK_STEP = 8;    // edges a lane loads per step (predicated)
 
 // Walk task: for each individual, the saturating per-slice count of its
 // successors' FT words, mapped through the group's truth table, transposed
-// back into the 32 output slots.  Rows longer than HEAVY_ROW are walked by
-// the whole warp, 32 edges at a time, and their counts reduced across lanes.
+// back into the 32 output slots (four words per lane per 16-byte store).
+// A lane walks its own row WALK_STEP edges at a time, all loads of a step
+// issued together; rows longer than HEAVY_ROW are walked by the whole warp,
+// 32 edges at a time, and their counts reduced across lanes.
 template <int NW>
 __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *gp, uint32_t tile,
                          uint32_t *slots) {
@@ -228,35 +231,42 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
 #pragma unroll
     for (int v = 0; v < 8; ++v) want[v] = gp->want[v];
     const uint32_t n = gp->n;
-    const uint32_t my_out = lane < n ? gp->out[lane] : 0u;
+    uint32_t *my_row = slots + (uint64_t)(lane < n ? gp->out[lane] : 0u) * kb.wp;
     const uint32_t passes = hd.tile_words / (NW * 32u);
     for (uint32_t p = 0; p < passes; ++p) {
         const uint32_t wb = tile * hd.tile_words + (p * NW + warp) * 32u;
         if (wb >= kb.wp) break;
-        for (uint32_t j = 0; j < 32u; ++j) {
-            const uint32_t w = wb + j;
-            if (w >= kb.wp) break;
+        uint32_t nlo = 0, nhi = 0;   // row pointers of the next word, fetched ahead
+        if (wb < kb.w && wb * 32u + lane < kb.n) {
+            nlo = ld_stream(rp + wb * 32u + lane);
+            nhi = ld_stream(rp + wb * 32u + lane + 1);
+        }
+        for (uint32_t jj = 0; jj < 32u; jj += 4) {
+          if (wb + jj >= kb.wp) break;   // wp and wb are multiples of 4: whole groups of four words
+          uint32_t outw[4];
+#pragma unroll
+          for (uint32_t q = 0; q < 4; ++q) {
+            const uint32_t w = wb + jj + q;
             const uint32_t i = w * 32u + lane;
             const bool valid = w < kb.w && i < kb.n;
-            uint32_t lo = 0, hi = 0;
-            if (valid) {
-                lo = ld_stream(rp + i);
-                hi = ld_stream(rp + i + 1);
+            const uint32_t lo = nlo, hi = nhi;
+            if (w + 1 < kb.w && i + 32u < kb.n) {
+                nlo = ld_stream(rp + i + 32u);
+                nhi = ld_stream(rp + i + 33u);
             }
             uint32_t c0 = 0, c1 = 0, c2 = 0;
             const bool heavy = hi - lo > HEAVY_ROW;
             if (!heavy) {
-                uint32_t k = lo;
-                for (; k + 4 <= hi; k += 4) {
-                    const uint32_t b0 = ld_stream(col + k), b1 = ld_stream(col + k + 1);
-                    const uint32_t b2 = ld_stream(col + k + 2), b3 = ld_stream(col + k + 3);
-                    const uint32_t x0 = ft[b0], x1 = ft[b1], x2 = ft[b2], x3 = ft[b3];
-                    sat_add1(c0, c1, c2, x0);
-                    sat_add1(c0, c1, c2, x1);
-                    sat_add1(c0, c1, c2, x2);
-                    sat_add1(c0, c1, c2, x3);
+                for (uint32_t k0 = lo; k0 < hi; k0 += WALK_STEP) {
+                    uint32_t b[WALK_STEP];
+#pragma unroll
+                    for (uint32_t u = 0; u < WALK_STEP; ++u) b[u] = k0 + u < hi ? ld_stream(col + k0 + u) : 0u;
+                    uint32_t x[WALK_STEP];
+#pragma unroll
+                    for (uint32_t u = 0; u < WALK_STEP; ++u) x[u] = k0 + u < hi ? ft[b[u]] : 0u;
+#pragma unroll
+                    for (uint32_t u = 0; u < WALK_STEP; ++u) sat_add1(c0, c1, c2, x[u]);
                 }
-                for (; k < hi; ++k) sat_add1(c0, c1, c2, ft[ld_stream(col + k)]);
             }
             uint32_t hm = __ballot_sync(FULL, heavy);
             while (hm) {
@@ -284,8 +294,10 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                 r |= m & want[v];
             }
             r = valid ? r : 0u;
-            r = transpose32(r, lane);   // lane s: slice s's word w
-            if (lane < n) slots[(uint64_t)my_out * kb.wp + w] = r;
+            outw[q] = transpose32(r, lane);   // lane s: slice s's word w
+          }
+          if (lane < n)   // 16-byte aligned: wb + jj is a multiple of 4
+              *reinterpret_cast<uint4 *>(my_row + wb + jj) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
         }
     }
 }

@@ -124,13 +124,13 @@ constexpr int STACK_MAX = 16;
 
 // ------------------------------------------------------------------ host objects
 struct Tuning {
-    uint32_t warps = 32;
+    uint32_t warps = 8;
     uint32_t wpl = 1;        // words per lane
     uint32_t rounds = 2;
     uint32_t ctas_per_sm = 0;
     uint32_t timeout_ms = 2000;
-    uint32_t stage = 1;      // stage role fillers in shared memory when a row fits
-    uint32_t role_block = 8; // 32-edge chunks per step of the role walk (4 or 8)
+    uint32_t stage = 0;      // stage role fillers in shared memory when a row fits
+    uint32_t role_block = 4; // 32-edge chunks per step of the role walk (4 or 8)
     uint32_t tile_words() const { return warps * 32u * wpl * rounds; }
 };
 

@@ -680,6 +680,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     p->info.n_items = (uint32_t)items;
     p->info.tile_words = TW;
     p->info.workspace_bytes = p->ws_bytes;
+    p->info.image_bytes = p->image_bytes;
     p->info.model_bytes = model;
     *out = p;
     return HEDL_OK;
