@@ -300,6 +300,58 @@ def search_run(args, dev):
     return out
 
 
+def run_latency(args, local_rank):
+    """Single large hypothesis latency: the 10,000,000-individual KB (32 Zipf(2.1) roles,
+    ~2.6 G assertions), 64 depth-6 hypotheses with chains of 3 nested EXISTS / ATLEAST,
+    each evaluated alone through hedl_eval_concept (plan + upload + launch) and timed with
+    CUDA events; algorithmic bytes per hypothesis from its plan."""
+    import torch
+    import paper_2412_00802_gb300 as H
+    from paper_2412_00802_gb300 import build
+    from synth import hyps, kb as K
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    build.build()
+    t0 = time.perf_counter()
+    kb = K.generate(K.CONFIGS["c2"])
+    gen_s = time.perf_counter() - t0
+    dkb = H.DeviceKB.from_synth(kb, device=str(dev))
+    progs = hyps.chain_hyps(kb, 2002, 64)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.zeros(dkb.wp, dtype=torch.int32, device=dev)
+    for p in progs[:3]:                       # warm-up
+        dkb.eval(p)
+    lat, model = [], []
+    offs = lambda p: np.array([0, len(p)], np.uint32)
+    with ClockSampler(local_rank) as clk:
+        for p in progs:
+            nbytes = H.hedl_workspace_size(dkb.handle, p, offs(p))
+            ws = dkb.workspace(nbytes)
+            model.append(H.hedl_plan_info_get(H.hedl_plan_batch(dkb.handle, p, offs(p)))["model_bytes"])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            H.hedl_eval_concept(dkb.handle, p, out, ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            lat.append(a.elapsed_time(b) / 1000.0)
+    H.hedl_sync_status(dkb.handle)
+    peak, kind = measured_peaks()
+    gbs = [m / t / 1e9 for m, t in zip(model, lat)]
+    print(json.dumps({
+        "metric": "single-hypothesis latency", "value": 1000 * statistics.median(lat), "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": len(progs), "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "N=10,000,000 individuals, 200 concepts, 32 roles Zipf(2.1) mean 8 cap 10^4 + "
+                               "inverses, 16 props lognormal(0,1) 10% missing, 100k/100k examples; 64 depth-6 "
+                               "hypotheses with 3-chains of EXISTS/ATLEAST, one at a time", "kb_gen_s": gen_s},
+        "latency_ms": {"median": 1000 * statistics.median(lat), "min": 1000 * min(lat), "max": 1000 * max(lat)},
+        "roofline": {"bound": "hbm", "achieved": statistics.median(gbs), "peak": peak, "unit": "GB/s",
+                     "frac": statistics.median(gbs) / peak, "traffic": None,
+                     "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "model_bytes_median": statistics.median(model)},
+        "clocks": clk.summary()}), flush=True)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -509,6 +561,8 @@ def main():
     ap.add_argument("--no-search", action="store_true", help="skip the beam-search comparison")
     ap.add_argument("--surrogate-full", action="store_true",
                     help="surrogate round at full size (10M individuals, 1M training hypotheses)")
+    ap.add_argument("--latency", action="store_true",
+                    help="the single-hypothesis latency workload (10M individuals) instead of the batched one")
     ap.add_argument("--search-full", action="store_true",
                     help="search at full size (4M individuals, 64 roles, 20 steps)")
     ap.add_argument("--batch", type=int, default=BATCH,
@@ -529,6 +583,8 @@ def main():
         td.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.latency:
+        run_latency(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -289,6 +289,8 @@ typedef struct {
                                   work item when it fits (then a segment reads at most one role
                                   restriction); 0: gather filler bits from global memory */
     uint32_t role_block;       /* 4 or 8: 32-edge chunks the role walk loads per step */
+    uint32_t full_occupancy;   /* 1: with 8 warps, 1 word per lane and no staging, use the build
+                                  limited to 32 registers so 8 CTAs fit per SM */
 } hedl_tuning;
 
 int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t);

@@ -76,7 +76,7 @@ class hedl_plan_info(ctypes.Structure):
 
 class hedl_tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("warps_per_cta", "words_per_lane", "rounds", "ctas_per_sm",
-                                                "wait_timeout_ms", "stage_fillers", "role_block")]
+                                                "wait_timeout_ms", "stage_fillers", "role_block", "full_occupancy")]
 
 
 _lib = None

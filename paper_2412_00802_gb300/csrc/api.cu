@@ -430,6 +430,7 @@ int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t) {
     t->wait_timeout_ms = kb->tuning.timeout_ms;
     t->stage_fillers = kb->tuning.stage;
     t->role_block = kb->tuning.role_block;
+    t->full_occupancy = kb->tuning.full_occupancy;
     return HEDL_OK;
 }
 
@@ -439,6 +440,7 @@ int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
         return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta must be 4, 8, 16 or 32");
     if (t->stage_fillers > 1) return fail(HEDL_ERR_INVALID_ARG, "stage_fillers must be 0 or 1");
     if (!(t->role_block == 4 || t->role_block == 8)) return fail(HEDL_ERR_INVALID_ARG, "role_block must be 4 or 8");
+    if (t->full_occupancy > 1) return fail(HEDL_ERR_INVALID_ARG, "full_occupancy must be 0 or 1");
     if (t->words_per_lane == 4 && t->warps_per_cta == 32)
         return fail(HEDL_ERR_INVALID_ARG, "words_per_lane 4 supports at most 16 warps per CTA");
     {
@@ -462,6 +464,7 @@ int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
     kb->tuning.timeout_ms = t->wait_timeout_ms;
     kb->tuning.stage = t->stage_fillers;
     kb->tuning.role_block = t->role_block;
+    kb->tuning.full_occupancy = t->full_occupancy;
     drop_cached_plan(kb);
     return HEDL_OK;
 }

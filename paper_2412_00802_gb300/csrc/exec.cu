@@ -339,8 +339,10 @@ __device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *s
     }
 }
 
-template <int NW, int WPL, bool STAGE, int BLK>
-__global__ void __launch_bounds__(NW * 32) exec_kernel(ExecArgs A) {
+// MINB > 1 asks the compiler for at most 65536 / (NW * 32 * MINB) registers so
+// that MINB CTAs fit on an SM (higher occupancy, possibly spills).
+template <int NW, int WPL, bool STAGE, int BLK, int MINB = 1>
+__global__ void __launch_bounds__(NW * 32, MINB) exec_kernel(ExecArgs A) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
     const PlanHeader hd = *reinterpret_cast<const PlanHeader *>(A.ws);
@@ -432,6 +434,8 @@ KernelFn pick_t(uint32_t warps, uint32_t wpl) {
 }
 
 KernelFn pick(const Tuning &t, bool stage) {
+    if (t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage)
+        return t.role_block == 4 ? exec_kernel<8, 1, false, 4, 8> : exec_kernel<8, 1, false, 8, 8>;
     if (t.role_block == 4) return stage ? pick_t<true, 4>(t.warps, t.wpl) : pick_t<false, 4>(t.warps, t.wpl);
     return stage ? pick_t<true, 8>(t.warps, t.wpl) : pick_t<false, 8>(t.warps, t.wpl);
 }

@@ -131,6 +131,7 @@ struct Tuning {
     uint32_t timeout_ms = 2000;
     uint32_t stage = 0;      // stage role fillers in shared memory when a row fits
     uint32_t role_block = 4; // 32-edge chunks per step of the role walk (4 or 8)
+    uint32_t full_occupancy = 0;  // 8-warp CTAs compiled for 8 CTAs per SM (<= 32 registers)
     uint32_t tile_words() const { return warps * 32u * wpl * rounds; }
 };
 

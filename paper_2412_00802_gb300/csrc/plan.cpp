@@ -172,9 +172,9 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 maxd = std::max<uint32_t>(maxd, (uint32_t)d);
                 if (op == HEDL_OP_ATOM) mb += B, p->info.n_atom_loads++;
                 else if (is_data(op)) mb += 4 * N, p->info.n_data_ops++;
-                else if (is_role(op)) mb += 4 * (N + 1) + 4ull * kb->role_edges[a] + B, p->info.n_role_ops++;
+                else if (is_role(op)) mb += 4 * (N + 1) + 4ull * kb->role_edges[a] + 2 * B, p->info.n_role_ops++;
             }
-            mb += B + 2 * B + 16;  // result row, scoring
+            mb += 2 * B + 16;  // scoring
         }
         p->plain_depth = maxd;
         p->info.model_bytes = mb;
@@ -334,6 +334,11 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     std::vector<std::vector<uint32_t>> seg_slots_read;
     std::vector<uint32_t> seg_of_slot(n_slots, 0);
     std::vector<uint32_t> role_key;  // first role read, for grouping
+    // Algorithmic bytes, the per-operation model (no credit for sharing a CSR
+    // walk or for caches): an atom read B, a data range 4N, a role
+    // restriction 4(N+1) + 4E + 2B (row pointers, columns, filler written and
+    // read), a hypothesis score 2B + 16, over the operations left after
+    // common sub-concepts are shared.
     uint64_t model = 0;
 
     std::vector<int32_t> work;
@@ -360,8 +365,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 if (i != root && mat[i]) {
                     d.op = D_SLOT;
                     d.ref = slot_of[i];
-                    reads.push_back(slot_of[i]);
-                    model += B;
+                    reads.push_back(slot_of[i]);   // bytes counted with the restriction that made it
                 } else if (n.op == HEDL_OP_ATOM) {
                     d.op = D_ATOM;
                     d.a = n.a;
@@ -388,7 +392,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                     if (rk == 0xFFFFFFFFu) rk = n.a * 2 + n.inv;
                     if (s.filler == NO_FILLER) s.filler = d.ref | (n.op == HEDL_OP_FORALL ? REF_NEG : 0u);
                     const DevCSR &g = kb->csr_host[2 * n.a + n.inv];
-                    model += 4 * (N + 1) + 4ull * g.n_edges + B;
+                    model += 4 * (N + 1) + 4ull * g.n_edges + 2 * B;
                     p->info.n_role_ops++;
                 }
                 code.push_back(d);
@@ -429,7 +433,6 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         }
         s.code_len = (uint32_t)code.size() - s.code_off;
         p->max_stack = std::max(p->max_stack, (uint32_t)maxdepth);
-        model += B;  // output row (slot, instance set or score input)
         if (hyp != NO_HYP) model += 2 * B + 16;
         std::sort(reads.begin(), reads.end());
         reads.erase(std::unique(reads.begin(), reads.end()), reads.end());
@@ -454,7 +457,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
             d.op = D_SLOT;
             d.ref = slot_of[roots[h]];
             code.push_back(d);
-            model += B + B + 2 * B + 16;
+            model += 2 * B + 16;
             seg_slots_read.push_back({slot_of[roots[h]]});
             role_key.push_back(0xFFFFFFFFu);
             segs.push_back(s);
@@ -523,11 +526,9 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 const uint32_t s_ = (uint32_t)(q - k);
                 if (nodes[f].op == HEDL_OP_ATOM && !mat[f]) {
                     g.filler[s_] = nodes[f].a;
-                    model += B;
                 } else {
                     g.filler[s_] = REF_SLOT | slot_of[f];
                     reads.push_back(slot_of[f]);
-                    model += B;
                 }
                 if (n.op == HEDL_OP_FORALL) g.filler[s_] |= REF_NEG;
                 g.out[s_] = slot_of[i];
@@ -568,7 +569,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
             task_reads.push_back({});
             for (uint32_t s_ = 0; s_ < g.n; ++s_) seg_of_slot[g.out[s_]] = walk_task;
             const DevCSR &csr = kb->csr_host[g.role2];
-            model += 4 * N + 4 * (N + 1) + 4ull * csr.n_edges + 4 * N + (uint64_t)g.n * B;
+            model += (uint64_t)g.n * (4 * (N + 1) + 4ull * csr.n_edges + 2 * B);
             rgroups.push_back(g);
             k = k2;
         }

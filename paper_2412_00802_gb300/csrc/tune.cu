@@ -27,8 +27,21 @@ std::vector<Tuning> candidates(const Tuning &base) {
                     t.rounds = rounds;
                     t.role_block = blk;
                     t.ctas_per_sm = 0;
+                    t.full_occupancy = 0;
                     out.push_back(t);
                 }
+    for (uint32_t rounds : {1u, 2u, 4u})
+        for (uint32_t blk : {4u, 8u}) {
+            Tuning t = base;
+            t.stage = 0;
+            t.warps = 8;
+            t.wpl = 1;
+            t.rounds = rounds;
+            t.role_block = blk;
+            t.ctas_per_sm = 0;
+            t.full_occupancy = 1;
+            out.push_back(t);
+        }
     for (uint32_t stage : {1u, 0u})
         for (uint32_t warps : {8u, 16u}) {
             Tuning t = base;
@@ -38,6 +51,7 @@ std::vector<Tuning> candidates(const Tuning &base) {
             t.rounds = 1;
             t.role_block = 8;
             t.ctas_per_sm = 0;
+            t.full_occupancy = 0;
             out.push_back(t);
         }
     return out;
@@ -70,7 +84,7 @@ bool cache_lookup(const char *path, const std::string &key, Tuning *t) {
         std::istringstream is(line);
         std::string k;
         Tuning c = *t;
-        if (is >> k >> c.warps >> c.wpl >> c.rounds >> c.stage >> c.role_block && k == key) {
+        if (is >> k >> c.warps >> c.wpl >> c.rounds >> c.stage >> c.role_block >> c.full_occupancy && k == key) {
             *t = c;       // the last matching line wins
             found = true;
         }
@@ -162,10 +176,11 @@ extern "C" int hedl_autotune(hedl_kb *kb, const uint64_t *progs, const uint32_t 
         if (cache_path) {
             std::ofstream f(cache_path, std::ios::app);
             f << key << ' ' << best.warps << ' ' << best.wpl << ' ' << best.rounds << ' ' << best.stage << ' '
-              << best.role_block << '\n';
+              << best.role_block << ' ' << best.full_occupancy << '\n';
         }
     }
-    hedl_tuning ht{best.warps, best.wpl, best.rounds, 0, saved.timeout_ms, best.stage, best.role_block};
+    hedl_tuning ht{best.warps, best.wpl, best.rounds, 0, saved.timeout_ms, best.stage, best.role_block,
+                   best.full_occupancy};
     int e = hedl_tuning_set(kb, &ht);
     if (e) return e;
     if (chosen) *chosen = ht;
