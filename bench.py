@@ -123,15 +123,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for(workload_key: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel build."""
+def traffic_for(workload_key: str, tuning: dict):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel build with the same launch shape."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         from paper_2412_00802_gb300 import build
         with open(p) as f:
             d = json.load(f)
         e = d.get(workload_key)
-        if e and e.get("build_digest") == build._digest():
+        if e and e.get("build_digest") == build._digest() and e.get("tuning") == tuning:
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -452,7 +453,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     model = [infos[i]["model_bytes"] for i in timed_ids]
     achieved = statistics.mean(m / (t / 1000.0) for m, t in zip(model, launch_ms)) / 1e9
-    traffic = traffic_for("c3_batch")
+    traffic = traffic_for("c3_batch", H.hedl_tuning_get(dkb.handle))
 
     # ---- end to end through the public C ABI from host programs: each step plans a batch
     # on the host (hedl_plan_batch), uploads and launches it (hedl_plan_execute) and copies

@@ -172,12 +172,18 @@ int hedl_validate(const hedl_kb *kb, const uint64_t *prog, uint32_t len);
 typedef struct hedl_plan hedl_plan;
 
 #define HEDL_NO_CSE     1u   /* no sharing of common sub-concepts */
-#define HEDL_NO_GRAPH   2u   /* launch directly instead of replaying a CUDA graph */
+#define HEDL_NO_GRAPH   2u   /* always launch directly (default: a plan's first execution
+                                launches directly, later ones capture and then replay a
+                                CUDA graph) */
 #define HEDL_PLAIN      4u   /* one launch per operation per hypothesis */
 #define HEDL_LEVELS     8u   /* one launch per dependency level, no device waits */
 #define HEDL_NO_SLICE  16u   /* evaluate every role restriction on its own CSR walk
                                 (default: up to 32 restrictions of one role and
-                                direction that become ready together share one walk) */
+                                direction that become ready together share one walk,
+                                formed where at least two restrictions have the same
+                                role, direction and nesting depth of role restrictions) */
+#define HEDL_SLICE_ALL 32u   /* put every eligible role restriction in a shared walk,
+                                even a group of one (ignored with HEDL_NO_SLICE) */
 #define HEDL_TEST_UNSAT_DEP 0x100u  /* TEST HOOK: add a dependency nothing
                                         satisfies, so the bounded device wait
                                         gives up (the call then reports

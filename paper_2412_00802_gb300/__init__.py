@@ -35,6 +35,7 @@ HEDL_NO_GRAPH = 2
 HEDL_PLAIN = 4
 HEDL_LEVELS = 8
 HEDL_NO_SLICE = 16
+HEDL_SLICE_ALL = 32
 HEDL_TEST_UNSAT_DEP = 0x100
 HEDL_MAX_STACK = 64
 HEDL_NOALLOC_SCRATCH_BYTES = 16 << 20

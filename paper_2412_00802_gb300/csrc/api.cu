@@ -297,7 +297,7 @@ int execute(hedl_kb *kb, const PlanImpl *pc, uint32_t *counts, uint32_t *out_bit
         e = cudaMemsetAsync((uint8_t *)ws + p->ctr_off, 0, p->ctr_bytes, st);
         if (e) return cuda_fail(e, "counter reset");
     }
-    const bool use_graph = !(p->flags & (HEDL_NO_GRAPH | HEDL_LEVELS));
+    const bool use_graph = !(p->flags & (HEDL_NO_GRAPH | HEDL_LEVELS)) && p->runs++ > 0;
     if (!use_graph) {
         int le = launch_exec(kb, p, counts, out_bits, ws, st);
         return le ? cuda_fail(le, "exec launch") : HEDL_OK;

@@ -200,7 +200,9 @@ struct PlanImpl {
     std::vector<uint64_t> progs;
     std::vector<uint32_t> offs;
     uint32_t plain_depth = 0;
-    // graph cache
+    // graph cache (a plan is captured at its second execution: a one-shot
+    // plan launches directly and pays no capture)
+    uint32_t runs = 0;
     void *graph_exec = nullptr;
     void *graph_ws = nullptr;
     uint32_t *graph_counts = nullptr;

@@ -254,17 +254,36 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     for (uint32_t i = 0; i < NN; ++i)
         if (is_role(nodes[i].op) && nodes[nodes[i].k0].op != HEDL_OP_ATOM) mat[nodes[i].k0] = 1;
     // Bit-sliced role restrictions: each is materialized and evaluated by its
-    // role group's shared walk (counting ones need n <= SLICE_MAX_N).
+    // role group's shared walk (counting ones need n <= SLICE_MAX_N).  A walk
+    // shared by one restriction only costs a transpose and a 32-times larger
+    // filler, so by default a restriction is sliced only when another one has
+    // the same role, direction and depth (role restrictions nested below it,
+    // itself included), the depth standing in for the level it becomes ready at.
     const bool sliced = !(flags & HEDL_NO_SLICE);
     std::vector<uint8_t> sl(NN, 0);
-    if (sliced)
+    if (sliced) {
+        auto eligible = [&](const PNode &n) {
+            return is_role(n.op) && (n.op == HEDL_OP_EXISTS || n.op == HEDL_OP_FORALL || n.b <= SLICE_MAX_N);
+        };
+        std::vector<uint32_t> rdepth(NN, 0);
+        std::unordered_map<uint64_t, uint32_t> same;
         for (uint32_t i = 0; i < NN; ++i) {
             const PNode &n = nodes[i];
-            if (is_role(n.op) && (n.op == HEDL_OP_EXISTS || n.op == HEDL_OP_FORALL || n.b <= SLICE_MAX_N)) {
+            uint32_t d = 0;
+            if (n.k0 >= 0) d = std::max(d, rdepth[n.k0]);
+            if (n.k1 >= 0) d = std::max(d, rdepth[n.k1]);
+            rdepth[i] = d + (is_role(n.op) ? 1u : 0u);
+            if (eligible(n)) same[((uint64_t)rdepth[i] << 32) | (n.a * 2u + n.inv)]++;
+        }
+        for (uint32_t i = 0; i < NN; ++i) {
+            const PNode &n = nodes[i];
+            if (eligible(n) &&
+                ((flags & HEDL_SLICE_ALL) || same[((uint64_t)rdepth[i] << 32) | (n.a * 2u + n.inv)] >= 2)) {
                 sl[i] = 1;
                 mat[i] = 1;
             }
         }
+    }
     std::vector<uint8_t> role_inline(NN, 0);
     std::vector<uint32_t> need(NN, 1);
     for (uint32_t i = 0; i < NN; ++i) {

@@ -13,7 +13,8 @@ from tests.gpu_util import compare_batch, device_kb
 pytestmark = pytest.mark.gpu
 
 MODES = {"default": 0, "no_cse": H.HEDL_NO_CSE, "no_graph": H.HEDL_NO_GRAPH, "levels": H.HEDL_LEVELS,
-         "plain": H.HEDL_PLAIN, "no_slice": H.HEDL_NO_SLICE, "no_slice_levels": H.HEDL_NO_SLICE | H.HEDL_LEVELS}
+         "plain": H.HEDL_PLAIN, "no_slice": H.HEDL_NO_SLICE, "no_slice_levels": H.HEDL_NO_SLICE | H.HEDL_LEVELS,
+         "slice_all": H.HEDL_SLICE_ALL, "slice_all_levels": H.HEDL_SLICE_ALL | H.HEDL_LEVELS}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -57,6 +58,27 @@ def c1_progs(c1):
 def test_c1_all_hypotheses(c1, c1_dev, c1_progs, mode):
     """Workload 1: 1,000 hypotheses of depth <= 4, every instance set and count."""
     compare_batch(c1, c1_dev, c1_progs, MODES[mode])
+
+
+@pytest.mark.parametrize("flags", [0, H.HEDL_SLICE_ALL, H.HEDL_NO_SLICE])
+def test_repeated_execution_through_the_graph(c1, c1_dev, c1_progs, flags):
+    """First execution launches directly, the second captures a CUDA graph, the third and
+    a replay run the graph: every one matches the oracle."""
+    import torch
+    flat, offs = P.pack_batch(c1_progs)
+    okb = oracle.from_synth(c1)
+    oc, osets, errs = oracle.eval_batch(okb, flat, offs, threads=4, keep_sets=True)
+    plan = H.hedl_plan_batch(c1_dev.handle, flat, offs, flags)
+    ws = c1_dev.workspace(H.hedl_plan_info_get(plan)["workspace_bytes"])
+    for call in (H.hedl_plan_execute, H.hedl_plan_execute, H.hedl_plan_execute, H.hedl_plan_replay):
+        counts = torch.zeros((len(c1_progs), 4), dtype=torch.int32, device=c1_dev.device)
+        bits = torch.zeros((len(c1_progs), c1_dev.wp), dtype=torch.int32, device=c1_dev.device)
+        call(c1_dev.handle, plan, counts, bits, ws)
+        H.hedl_sync_status(c1_dev.handle)
+        assert np.array_equal(counts.cpu().numpy().astype(np.int64), oc)
+        bb = bits.cpu().numpy().view(np.uint32)
+        for h in range(len(c1_progs)):
+            assert np.array_equal(K.unpack_bits(bb[h], c1.n), osets[h].astype(bool)), (call, h)
 
 
 def test_c1_batched_shapes(c1, c1_dev):
@@ -108,8 +130,10 @@ def test_eval_concept(c1, c1_dev):
     r = Rng(9, 9)
     for i in range(40):
         prog = pins.random_program(r, c1, r.randint(1, 6)).postfix()
-        got = K.unpack_bits(c1_dev.eval(np.array(prog, np.uint64)), c1.n)
-        assert np.array_equal(got, oracle.eval_program(okb, prog)), P.to_text(P.from_postfix(prog))
+        want = oracle.eval_program(okb, prog)
+        for flags in (0, H.HEDL_SLICE_ALL):
+            got = K.unpack_bits(c1_dev.eval(np.array(prog, np.uint64), flags), c1.n)
+            assert np.array_equal(got, want), (flags, P.to_text(P.from_postfix(prog)))
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 63, 64, 65, 100, 127, 129, 1000, 4097])
@@ -123,7 +147,7 @@ def test_ragged_sizes_every_constructor(n):
     dkb = device_kb(kb)
     r = Rng(n, 3)
     progs = [np.array(pins.random_program(r, kb, r.randint(1, 5)).postfix(), np.uint64) for _ in range(120)]
-    for mode in (0, H.HEDL_PLAIN, H.HEDL_NO_SLICE):
+    for mode in (0, H.HEDL_PLAIN, H.HEDL_NO_SLICE, H.HEDL_SLICE_ALL):
         compare_batch(kb, dkb, progs, mode)
 
 
@@ -138,7 +162,7 @@ def test_stress_shapes_single_and_unique_subject():
         progs = [np.array(pins.random_program(r, kb, r.randint(2, 4)).postfix(), np.uint64) for _ in range(80)]
         progs += [P.compile_text(t) for t in ("(min 3000 r0 A1)", "(max 2999 r0 TOP)", "(exactly 6000 r0 TOP)",
                                                 "(all r0 A2)", "(some r0- A0)", "(min 1 r1- (not A3))")]
-        for mode in (0, H.HEDL_LEVELS, H.HEDL_PLAIN, H.HEDL_NO_SLICE):
+        for mode in (0, H.HEDL_LEVELS, H.HEDL_PLAIN, H.HEDL_NO_SLICE, H.HEDL_SLICE_ALL):
             compare_batch(kb, dkb, progs, mode)
 
 
@@ -148,6 +172,7 @@ def test_zipf_heavy_rows():
     progs = hyps.batch_hyps(kb, 5, 0, 300, lmax=30, dmax=7)
     compare_batch(kb, dkb, progs, 0)
     compare_batch(kb, dkb, progs, H.HEDL_NO_SLICE)
+    compare_batch(kb, dkb, progs, H.HEDL_SLICE_ALL)
 
 
 def test_special_thresholds_and_counts(c1, c1_dev):
@@ -173,7 +198,7 @@ def test_role_groups_with_every_kind_and_many_slices(c1, c1_dev):
                 texts.append(f"({kind} r1{inv} {c})" if kind in ("some", "all") else f"({kind} {n} r1{inv} {c})")
     texts += [f"(and A{i} (some r2 (or A{i + 1} (min {i % 5} r2- A{i + 2}))))" for i in range(40)]
     progs = [P.compile_text(t) for t in texts]
-    for mode in (0, H.HEDL_LEVELS, H.HEDL_NO_SLICE):
+    for mode in (0, H.HEDL_LEVELS, H.HEDL_NO_SLICE, H.HEDL_SLICE_ALL):
         compare_batch(c1, c1_dev, progs, mode)
 
 

@@ -124,16 +124,30 @@ def test_plan_sharing_and_levels(c1):
     plain = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, H.HEDL_NO_CSE))
     # two role restrictions in x, evaluated once with sharing
     assert shared["n_role_ops"] == 2 and plain["n_role_ops"] == 30
-    # bit-sliced (default): filler 0, the min-restriction's transpose 1 and walk 2, the
-    # some-restriction's transpose 3 and walk 4, the roots 5 (the shared conjunction is
-    # inlined: its role restriction is already a slot)
-    assert shared["n_levels"] == 6 and shared["n_role_groups"] == 2
+    # every restriction bit-sliced: filler 0, the min-restriction's transpose 1 and walk 2,
+    # the some-restriction's transpose 3 and walk 4, the roots 5 (the shared conjunction
+    # is inlined: its role restriction is already a slot)
+    every = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, H.HEDL_SLICE_ALL))
+    assert every["n_levels"] == 6 and every["n_role_groups"] == 2
     # one walk per restriction: filler, the min-restriction, the shared conjunction
-    # (materialized, it holds a role restriction), the roots
+    # (materialized, it holds a role restriction), the roots.  By default too: the two
+    # restrictions differ in role, so neither has a partner to share a walk with.
     solo = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, H.HEDL_NO_SLICE))
     assert solo["n_levels"] == 4 and solo["n_role_groups"] == 0 and solo["n_role_ops"] == 2
+    assert (shared["n_levels"], shared["n_role_groups"]) == (4, 0)
     assert shared["n_nodes"] < plain["n_nodes"]
     assert shared["model_bytes"] < plain["model_bytes"]
+    # two restrictions of one role and direction at the same depth share a walk; at
+    # different depths, or with different directions, they do not
+    def groups(texts, flags=0):
+        return H.hedl_plan_info_get(H.hedl_plan_batch(hk, *P.pack_batch([P.compile_text(t) for t in texts]),
+                                                       flags))["n_role_groups"]
+    assert groups(["(some r1 A2)", "(all r1 A3)"]) == 1
+    assert groups(["(some r1 A2)", "(some r1- A3)"]) == 0
+    assert groups(["(some r1 A2)", "(some r1 (some r2 A3))"]) == 0
+    assert groups(["(some r1 A2)", "(some r1 (some r2 A3))"], H.HEDL_SLICE_ALL) == 3
+    assert groups(["(some r1 A2)", "(some r1 (some r1 A3))"]) == 1     # the two inner ones
+    assert groups(["(some r1 A2)", "(all r1 A3)"], H.HEDL_NO_SLICE | H.HEDL_SLICE_ALL) == 0
     # commuted operands and double negation share too
     a = [P.compile_text("(and A1 (some r0 A2))"), P.compile_text("(and (some r0 A2) A1)"),
          P.compile_text("(not (not (and A1 (some r0 A2))))")]
