@@ -309,33 +309,56 @@ def run_latency(args, local_rank):
     import torch
     import paper_2412_00802_gb300 as H
     from paper_2412_00802_gb300 import build
-    from synth import hyps, kb as K
+    from synth import hyps, kb as K, programs as P
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     build.build()
     t0 = time.perf_counter()
-    kb = K.generate(K.CONFIGS["c2"])
+    cfg = K.CONFIGS["c2"]
+    if args.latency_n:                       # smaller KB of the same distributions (profiling)
+        cfg = cfg.scaled(args.latency_n)
+    kb = K.generate(cfg)
     gen_s = time.perf_counter() - t0
     dkb = H.DeviceKB.from_synth(kb, device=str(dev))
     progs = hyps.chain_hyps(kb, 2002, 64)
+    tune_s = None
+    if not args.no_tune:
+        # launch shape picked on 16 other hypotheses of the same shape, evaluated together
+        t0 = time.perf_counter()
+        dkb.autotune(*P.pack_batch(hyps.chain_hyps(kb, 2003, 16)))
+        tune_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
     out = torch.zeros(dkb.wp, dtype=torch.int32, device=dev)
     for p in progs[:3]:                       # warm-up
         dkb.eval(p)
-    lat, model = [], []
+    lat, model, host, replay, levels = [], [], [], [], []
     offs = lambda p: np.array([0, len(p)], np.uint32)
     with ClockSampler(local_rank) as clk:
         for p in progs:
             nbytes = H.hedl_workspace_size(dkb.handle, p, offs(p))
             ws = dkb.workspace(nbytes)
-            model.append(H.hedl_plan_info_get(H.hedl_plan_batch(dkb.handle, p, offs(p)))["model_bytes"])
+            plan = H.hedl_plan_batch(dkb.handle, p, offs(p))
+            info = H.hedl_plan_info_get(plan)
+            model.append(info["model_bytes"])
+            levels.append(info["n_levels"])
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             a.record(stream)
+            h0 = time.perf_counter()
             H.hedl_eval_concept(dkb.handle, p, out, ws)
+            host.append(time.perf_counter() - h0)
             b.record(stream)
             torch.cuda.synchronize()
             lat.append(a.elapsed_time(b) / 1000.0)
+            # the same plan again, resident: device time without planning and upload
+            H.hedl_plan_execute(dkb.handle, plan, None, out, ws)
+            H.hedl_plan_replay(dkb.handle, plan, None, out, ws)
+            torch.cuda.synchronize()
+            a.record(stream)
+            H.hedl_plan_replay(dkb.handle, plan, None, out, ws)
+            b.record(stream)
+            torch.cuda.synchronize()
+            replay.append(a.elapsed_time(b) / 1000.0)
     H.hedl_sync_status(dkb.handle)
     peak, kind = measured_peaks()
     gbs = [m / t / 1e9 for m, t in zip(model, lat)]
@@ -344,8 +367,12 @@ def run_latency(args, local_rank):
         "higher_is_better": False, "n_gpus": 1, "steps": len(progs), "dtype": "u32", "data": "synthetic",
         "config": {"workload": "N=10,000,000 individuals, 200 concepts, 32 roles Zipf(2.1) mean 8 cap 10^4 + "
                                "inverses, 16 props lognormal(0,1) 10% missing, 100k/100k examples; 64 depth-6 "
-                               "hypotheses with 3-chains of EXISTS/ATLEAST, one at a time", "kb_gen_s": gen_s},
-        "latency_ms": {"median": 1000 * statistics.median(lat), "min": 1000 * min(lat), "max": 1000 * max(lat)},
+                               "hypotheses with 3-chains of EXISTS/ATLEAST, one at a time", "kb_gen_s": gen_s,
+                   "n": kb.n, "tuning": H.hedl_tuning_get(dkb.handle), "autotune_s": tune_s},
+        "latency_ms": {"median": 1000 * statistics.median(lat), "min": 1000 * min(lat), "max": 1000 * max(lat),
+                       "host_call_median": 1000 * statistics.median(host),
+                       "resident_replay_median": 1000 * statistics.median(replay)},
+        "levels_median": statistics.median(levels),
         "roofline": {"bound": "hbm", "achieved": statistics.median(gbs), "peak": peak, "unit": "GB/s",
                      "frac": statistics.median(gbs) / peak, "traffic": None,
                      "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -421,6 +448,8 @@ def run_ours(args, rank, world, local_rank):
     for i in ids:
         H.hedl_plan_execute(dkb.handle, plans[i], counts, None, wss[i])
     H.hedl_sync_status(dkb.handle)
+    for i in timed_ids:          # second execution: the plan's CUDA graph is captured here
+        H.hedl_plan_replay(dkb.handle, plans[i], counts, None, wss[i])
     for i in warm_ids:
         H.hedl_plan_replay(dkb.handle, plans[i], counts, None, wss[i])
     H.hedl_sync_status(dkb.handle)
@@ -434,6 +463,7 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         t_all0 = torch.cuda.Event(enable_timing=True)
         t_all1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")    # lets a profiler capture only these launches
         t_all0.record(stream)
         for (a, b), i in zip(ev, timed_ids):
             a.record(stream)
@@ -441,6 +471,7 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
         t_all1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     H.hedl_sync_status(dkb.handle)
     elapsed = t_all0.elapsed_time(t_all1) / 1000.0
     if dist:
@@ -564,6 +595,8 @@ def main():
                     help="surrogate round at full size (10M individuals, 1M training hypotheses)")
     ap.add_argument("--latency", action="store_true",
                     help="the single-hypothesis latency workload (10M individuals) instead of the batched one")
+    ap.add_argument("--latency-n", type=int, default=0,
+                    help="individuals of the latency workload's KB (default: its full 10,000,000)")
     ap.add_argument("--search-full", action="store_true",
                     help="search at full size (4M individuals, 64 roles, 20 steps)")
     ap.add_argument("--batch", type=int, default=BATCH,

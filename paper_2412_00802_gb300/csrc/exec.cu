@@ -339,10 +339,11 @@ __device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *s
     }
 }
 
-// MINB > 1 asks the compiler for at most 65536 / (NW * 32 * MINB) registers so
-// that MINB CTAs fit on an SM (higher occupancy, possibly spills).
-template <int NW, int WPL, bool STAGE, int BLK, int MINB = 1>
-__global__ void __launch_bounds__(NW * 32, MINB) exec_kernel(ExecArgs A) {
+// Register budget: every shape is compiled for 1,024 resident threads per SM
+// (64 registers a thread, half occupancy); FULL ones for 2,048 (32 registers,
+// full occupancy, at the price of spills).
+template <int NW, int WPL, bool STAGE, int BLK, bool FULL = false>
+__global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(ExecArgs A) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
     const PlanHeader hd = *reinterpret_cast<const PlanHeader *>(A.ws);
@@ -435,7 +436,7 @@ KernelFn pick_t(uint32_t warps, uint32_t wpl) {
 
 KernelFn pick(const Tuning &t, bool stage) {
     if (t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage)
-        return t.role_block == 4 ? exec_kernel<8, 1, false, 4, 8> : exec_kernel<8, 1, false, 8, 8>;
+        return t.role_block == 4 ? exec_kernel<8, 1, false, 4, true> : exec_kernel<8, 1, false, 8, true>;
     if (t.role_block == 4) return stage ? pick_t<true, 4>(t.warps, t.wpl) : pick_t<false, 4>(t.warps, t.wpl);
     return stage ? pick_t<true, 8>(t.warps, t.wpl) : pick_t<false, 8>(t.warps, t.wpl);
 }
