@@ -141,8 +141,9 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
 /* A planning-only handle: reads only the sizes in d (n_indiv, the counts and
  * each role's n_edges; pointers may be NULL) and makes no CUDA call, so it
  * works on a host without a GPU.  hedl_validate, hedl_plan_batch and
- * hedl_plan_info_get accept it; every call that would launch work returns
- * HEDL_ERR_INVALID_ARG.  Release it with hedl_kb_free. */
+ * hedl_plan_info_get accept it (its plans are shaped for a 152-SM GB300);
+ * every call that would launch work returns HEDL_ERR_INVALID_ARG.  Release
+ * it with hedl_kb_free. */
 int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out);
 
 /* Release a handle (waits for the device to go idle first).  NULL is fine. */
@@ -201,6 +202,9 @@ typedef struct {
     uint32_t n_role_groups;  /* shared CSR walks of bit-sliced role restrictions */
     uint32_t n_data_ops;
     uint32_t n_atom_loads;
+    uint32_t warp_words;     /* words a warp covers per round: 32, or 16 / 8 / 4 when a
+                                level walking a role has too few segments to fill the GPU
+                                (0 with HEDL_PLAIN, which has no tiles) */
     uint64_t total_insns;    /* instructions in the input programs */
     uint64_t workspace_bytes;
     uint64_t image_bytes;    /* plan image copied host-to-device by hedl_plan_execute */

@@ -71,7 +71,7 @@ class hedl_kb_desc(ctypes.Structure):
 class hedl_plan_info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("n_hyps", "n_nodes", "n_segments", "n_slots", "n_levels", "n_items",
                                                 "tile_words", "n_role_ops", "n_role_groups", "n_data_ops",
-                                                "n_atom_loads")] + \
+                                                "n_atom_loads", "warp_words")] + \
                [(k, ctypes.c_uint64) for k in ("total_insns", "workspace_bytes", "image_bytes", "model_bytes")]
 
 

@@ -165,6 +165,7 @@ int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out) {
     kb->n_concepts = d->n_concepts;
     kb->n_roles = d->n_roles;
     kb->n_props = d->n_props;
+    kb->n_sms = PLAN_ONLY_SMS;
     kb->csr_host.resize(2ull * d->n_roles);
     kb->role_edges.resize(d->n_roles);
     for (uint32_t r = 0; r < d->n_roles; ++r) {

@@ -54,11 +54,16 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
     const KBView &kb = A.kb;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const DInsn *code = reinterpret_cast<const DInsn *>(A.ws + hd.off_code) + seg.code_off;
-    const uint32_t rounds = hd.tile_words / (NW * 32u * WPL);
+    // a warp covers ww * WPL words a round; with ww < 32, lanes ww..31 hold
+    // words of no one: every load, store and walk stops at the warp's limit
+    const uint32_t ww = hd.warp_words;
+    const uint32_t rounds = hd.tile_words / (NW * ww * WPL);
     uint32_t tp = 0, fp = 0;
     for (uint32_t r = 0; r < rounds; ++r) {
-        const uint32_t wb = tile * hd.tile_words + (r * NW + warp) * 32u * WPL;
+        const uint32_t wb = tile * hd.tile_words + (r * NW + warp) * ww * WPL;
         if (wb >= kb.wp) break;
+        const uint32_t lim_p = min(kb.wp, wb + ww * WPL);   // padded row words
+        const uint32_t lim_w = min(kb.w, wb + ww * WPL);    // words holding individuals
         uint32_t top[WPL];
         uint32_t sp = 0;  // values on the stack, top included
         for (uint32_t pc = 0; pc < seg.code_len; ++pc) {
@@ -87,10 +92,10 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
             sp += 1;
             switch (op) {
             case D_ATOM:
-                load_row_ro<WPL>(kb.concepts + (uint64_t)d.a * kb.wp, wb, lane, kb.wp, top);
+                load_row_ro<WPL>(kb.concepts + (uint64_t)d.a * kb.wp, wb, lane, lim_p, top);
                 break;
             case D_SLOT:
-                load_row_rw<WPL>(slots + (uint64_t)d.ref * kb.wp, wb, lane, kb.wp, top);
+                load_row_rw<WPL>(slots + (uint64_t)d.ref * kb.wp, wb, lane, lim_p, top);
                 break;
             case D_TOP:
 #pragma unroll
@@ -102,30 +107,30 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 break;
             case D_DATA:
                 data_words<WPL>(kb.props + (uint64_t)d.a * kb.prop_stride, (d.op >> 16) & 0xFFu,
-                                __uint_as_float(d.b), kb.n, kb.w, wb, lane, top);
+                                __uint_as_float(d.b), kb.n, lim_w, wb, lane, top);
                 break;
             default: {  // D_ROLE
                 const uint32_t inv = (d.op >> 8) & 1u;
                 const DevCSR g = kb.csr[2u * d.a + inv];
                 if constexpr (STAGE) {
                     const uint32_t kind = (d.op >> 16) & 0xFFu;
-                    role_words<WPL, BLK>(g, sm.filler, kind, d.b, kb.n, kb.w, wb, lane, top, kind == HEDL_OP_FORALL);
+                    role_words<WPL, BLK>(g, sm.filler, kind, d.b, kb.n, lim_w, wb, lane, top, kind == HEDL_OP_FORALL);
                 } else {
                     const uint32_t *filler = (d.ref & REF_SLOT) ? slots + (uint64_t)(d.ref & ~REF_SLOT) * kb.wp
                                                                 : kb.concepts + (uint64_t)d.ref * kb.wp;
-                    role_words<WPL, BLK>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, kb.w, wb, lane, top);
+                    role_words<WPL, BLK>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, lim_w, wb, lane, top);
                 }
                 break;
             }
             }
         }
-        if (seg.out_slot != NO_SLOT) store_row<WPL>(slots + (uint64_t)seg.out_slot * kb.wp, wb, lane, kb.wp, top);
+        if (seg.out_slot != NO_SLOT) store_row<WPL>(slots + (uint64_t)seg.out_slot * kb.wp, wb, lane, lim_p, top);
         if (seg.hyp != NO_HYP) {
-            if (A.out_bits) store_row<WPL>(A.out_bits + (uint64_t)seg.hyp * kb.wp, wb, lane, kb.wp, top);
+            if (A.out_bits) store_row<WPL>(A.out_bits + (uint64_t)seg.hyp * kb.wp, wb, lane, lim_p, top);
             if (A.counts) {
                 uint32_t pv[WPL], nv[WPL];
-                load_row_ro<WPL>(kb.pos, wb, lane, kb.wp, pv);
-                load_row_ro<WPL>(kb.neg, wb, lane, kb.wp, nv);
+                load_row_ro<WPL>(kb.pos, wb, lane, lim_p, pv);
+                load_row_ro<WPL>(kb.neg, wb, lane, lim_p, nv);
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
                     tp += __popc(top[s] & pv[s]);

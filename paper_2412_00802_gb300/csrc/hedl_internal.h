@@ -104,7 +104,7 @@ struct Group {
 struct PlanHeader {
     uint32_t n_items, n_segs, n_groups, n_hyps;
     uint32_t n_tiles, tile_words, n_slots, flags;
-    uint32_t n_levels, n_deps, n_rgroups, pad1;
+    uint32_t n_levels, n_deps, n_rgroups, warp_words;   // words a warp covers per round (32, 16, 8 or 4)
     uint64_t off_segs, off_groups, off_gsegs, off_deps;
     uint64_t off_code, off_level_items, off_ctr, off_slots;
     uint64_t off_rgroups, off_ft;
@@ -136,6 +136,7 @@ struct Tuning {
 };
 
 constexpr size_t SMEM_OPTIN_DEFAULT = 232448;   // bytes of shared memory a CTA may opt into
+constexpr int PLAN_ONLY_SMS = 152;               // planning-only handles plan for a 152-SM GB300
 
 // Shared-memory bytes of the interpreter's stack (per CTA).
 inline size_t stack_smem_bytes(const Tuning &t) { return sizeof(uint32_t) * (size_t)t.warps * STACK_MAX * t.wpl * 32; }

@@ -616,9 +616,34 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         deps.push_back(NS);
     }
 
-    // groups: (level, role key), items tile-major inside a group
+    // Tile shape.  A warp covers 32 words a round by default.  When some level
+    // that walks a role holds only a few segments (a small batch, a single
+    // hypothesis), its tiles would keep only a fraction of the resident warps
+    // busy, each walking 32 words in sequence: then a warp covers fewer words
+    // (down to 4, one round per item) so that the level spreads over about
+    // four times as many warp-rounds as there are resident warps (32 per SM at
+    // 64 registers), which also balances rows of very different degree.  Role
+    // groups walk 32 words per warp and keep the default shape.
     const Tuning &t = p->tuning;
-    const uint32_t TW = t.tile_words();
+    uint32_t WW = 32, rounds = t.rounds;
+    if (rgroups.empty() && kb->n_sms > 0) {
+        std::vector<uint32_t> segs_at(n_levels, 0);
+        std::vector<uint8_t> walks_at(n_levels, 0);
+        for (uint32_t s_ = 0; s_ < NS; ++s_) {
+            const uint32_t L = task_level[s_];
+            segs_at[L]++;
+            for (uint32_t pc = 0; pc < segs[s_].code_len; ++pc)
+                if ((code[segs[s_].code_off + pc].op & 0xFFu) == D_ROLE) walks_at[L] = 1;
+        }
+        uint64_t smin = UINT64_MAX;
+        for (uint32_t L = 0; L < n_levels; ++L)
+            if (walks_at[L]) smin = std::min<uint64_t>(smin, segs_at[L]);
+        const uint64_t resident = 32ull * (uint64_t)kb->n_sms;
+        if (smin != UINT64_MAX)
+            while (WW > 4 && smin * kb->wp < 4ull * resident * WW * t.wpl) WW >>= 1;
+        if (WW < 32) rounds = 1;
+    }
+    const uint32_t TW = t.warps * WW * t.wpl * rounds;
     const uint32_t n_tiles = (kb->wp + TW - 1) / TW;
     std::vector<uint32_t> order(NS);
     for (uint32_t s = 0; s < NS; ++s) order[s] = s;
@@ -663,6 +688,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     hd.n_hyps = H;
     hd.n_tiles = n_tiles;
     hd.tile_words = TW;
+    hd.warp_words = WW;
     hd.n_slots = n_slots;
     hd.flags = flags;
     hd.n_levels = n_levels;
@@ -699,6 +725,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     p->info.n_levels = n_levels;
     p->info.n_items = (uint32_t)items;
     p->info.tile_words = TW;
+    p->info.warp_words = WW;
     p->info.workspace_bytes = p->ws_bytes;
     p->info.image_bytes = p->image_bytes;
     p->info.model_bytes = model;

@@ -169,3 +169,17 @@ def test_planning_only_handle_refuses_launches(c1):
     with pytest.raises(H.HedlError) as e:
         H.hedl_sync_status(hk, stream=0)
     assert e.value.code == -1
+
+
+def test_narrow_tiles_for_single_hypotheses():
+    """A lone hypothesis's walks would leave most warps idle with 32-word warps: the plan
+    narrows them (one round per item); a large batch keeps 32.  Role groups keep 32."""
+    hk = H.hedl_kb_plan_only(1_000_000, 200, [8_000_000] * 32, 16)   # sizes only
+    one = H.hedl_plan_info_get(H.hedl_plan_batch(hk, *P.pack_batch([P.compile_text("(some r1 (min 2 r2 A3))")])))
+    assert one["warp_words"] == 4 and one["tile_words"] == 8 * 4
+    batch = [P.compile_text(f"(some r{i % 8} (min 2 r{(i + 3) % 8} A{i % 50}))") for i in range(2000)]
+    many = H.hedl_plan_info_get(H.hedl_plan_batch(hk, *P.pack_batch(batch)))
+    assert many["warp_words"] == 32
+    paired = H.hedl_plan_info_get(H.hedl_plan_batch(hk, *P.pack_batch([P.compile_text("(some r1 A2)"),
+                                                                         P.compile_text("(all r1 A3)")])))
+    assert paired["n_role_groups"] == 1 and paired["warp_words"] == 32
