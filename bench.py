@@ -330,14 +330,14 @@ def run_latency(args, local_rank):
     stream = torch.cuda.current_stream(dev)
     out = torch.zeros(dkb.wp, dtype=torch.int32, device=dev)
     for p in progs[:3]:                       # warm-up
-        dkb.eval(p)
+        dkb.eval(p, args.flags)
     lat, model, host, replay, levels = [], [], [], [], []
     offs = lambda p: np.array([0, len(p)], np.uint32)
     with ClockSampler(local_rank) as clk:
         for p in progs:
-            nbytes = H.hedl_workspace_size(dkb.handle, p, offs(p))
+            nbytes = H.hedl_workspace_size(dkb.handle, p, offs(p), args.flags)
             ws = dkb.workspace(nbytes)
-            plan = H.hedl_plan_batch(dkb.handle, p, offs(p))
+            plan = H.hedl_plan_batch(dkb.handle, p, offs(p), args.flags)
             info = H.hedl_plan_info_get(plan)
             model.append(info["model_bytes"])
             levels.append(info["n_levels"])
@@ -345,7 +345,7 @@ def run_latency(args, local_rank):
             torch.cuda.synchronize()
             a.record(stream)
             h0 = time.perf_counter()
-            H.hedl_eval_concept(dkb.handle, p, out, ws)
+            H.hedl_eval_concept(dkb.handle, p, out, ws, args.flags)
             host.append(time.perf_counter() - h0)
             b.record(stream)
             torch.cuda.synchronize()
@@ -368,7 +368,7 @@ def run_latency(args, local_rank):
         "config": {"workload": "N=10,000,000 individuals, 200 concepts, 32 roles Zipf(2.1) mean 8 cap 10^4 + "
                                "inverses, 16 props lognormal(0,1) 10% missing, 100k/100k examples; 64 depth-6 "
                                "hypotheses with 3-chains of EXISTS/ATLEAST, one at a time", "kb_gen_s": gen_s,
-                   "n": kb.n, "tuning": H.hedl_tuning_get(dkb.handle), "autotune_s": tune_s},
+                   "n": kb.n, "flags": args.flags, "tuning": H.hedl_tuning_get(dkb.handle), "autotune_s": tune_s},
         "latency_ms": {"median": 1000 * statistics.median(lat), "min": 1000 * min(lat), "max": 1000 * max(lat),
                        "host_call_median": 1000 * statistics.median(host),
                        "resident_replay_median": 1000 * statistics.median(replay)},

@@ -212,6 +212,147 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
     }
 }
 
+// Role restriction over the warp's words as ONE edge stream (the interpreter's
+// walk).  The words wb .. wb+K-1 are consecutive individuals, so their CSR
+// rows form one contiguous edge range [E0, E1).  The warp reads that range in
+// blocks of BLK 32-edge chunks, always loading the next block while it tests
+// the current one (the gather's DRAM latency overlaps the filler lookups),
+// and attributes each block's hits to the words whose rows it covers: lane i
+// of word k counts the hits inside its row with two rank lookups, as in
+// role_words, and a word is emitted (ballot) once its last edge has passed.
+// A word whose every lane is decided (cap reached or row ended) makes the
+// stream jump to the next word's first edge.  Word k of the warp goes to lane
+// k / WPL, slot k % WPL.  n_words bounds the warp's words; lanes of
+// individuals >= n hold empty rows and emit 0.
+template <int WPL, int BLK>
+__device__ __forceinline__ void role_stream(const DevCSR g, const uint32_t *filler, uint32_t kind, uint32_t n_arg,
+                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
+                                            uint32_t (&v)[WPL], bool filler_inverted = false) {
+    static_assert(BLK >= 1 && BLK <= 32, "a block holds 1..32 chunks");
+    constexpr uint32_t BE = 32u * BLK;     // edges per block
+    const uint32_t neg = (kind == HEDL_OP_FORALL && !filler_inverted) ? 1u : 0u;
+    const uint64_t cap = decide_cap(kind, n_arg);
+    const uint32_t *__restrict__ rp = g.rp;
+    const uint32_t *__restrict__ col = g.col;
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) v[s] = 0u;
+    if (wb >= n_words) return;
+    const uint32_t K = min(32u * WPL, n_words - wb);
+    auto put = [&](uint32_t k, uint32_t word) {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s)
+            if (lane == k / WPL && k % WPL == (uint32_t)s) v[s] = word;
+    };
+    auto lane_valid = [&](uint32_t k) { return (wb + k) * 32u + lane < n; };
+    if (cap == 0) {   // decided before any edge (at least 0): every individual
+        for (uint32_t k = 0; k < K; ++k) put(k, __ballot_sync(FULL, lane_valid(k)));
+        return;
+    }
+    // row pointers of words k, k+1, k+2 (empty rows for lanes past n or words past K)
+    auto ld_rows = [&](uint32_t k, uint32_t &lo, uint32_t &hi) {
+        const uint32_t i = (wb + k) * 32u + lane;
+        if (k < K && i < n) {
+            lo = ld_stream(rp + i);
+            hi = ld_stream(rp + i + 1);
+        } else {
+            lo = 0u;
+            hi = 0u;
+        }
+    };
+    // last edge (exclusive) of word k, from its last valid lane
+    auto word_end = [&](uint32_t k, uint32_t hi) {
+        const uint32_t nv = min(32u, n - (wb + k) * 32u);
+        return __shfl_sync(FULL, hi, nv - 1u);
+    };
+    uint32_t lo0, hi0, lo1, hi1, lo2, hi2;
+    ld_rows(0, lo0, hi0);
+    ld_rows(1, lo1, hi1);
+    ld_rows(2, lo2, hi2);
+    const uint32_t E0 = __shfl_sync(FULL, lo0, 0);
+    const uint32_t E1 = ld_stream(rp + min(n, (wb + K) * 32u));
+    uint32_t k = 0, cnt = 0;
+    uint32_t ew1 = word_end(0, hi0);
+    auto next_word = [&]() {
+        lo0 = lo1, hi0 = hi1, lo1 = lo2, hi1 = hi2;
+        ld_rows(k + 2, lo2, hi2);
+        ew1 = word_end(k, hi0);
+        cnt = 0;
+    };
+    uint32_t pf[BLK];
+    auto fetch = [&](uint32_t at) {
+#pragma unroll
+        for (int u = 0; u < BLK; ++u) pf[u] = ld_stream(col + min(at + 32u * u + lane, E1 - 1u));
+    };
+    uint32_t base = E0;
+    if (base < E1) fetch(base);
+#pragma unroll 1
+    while (base < E1) {
+        uint32_t hit[BLK];
+#pragma unroll
+        for (int u = 0; u < BLK; ++u) hit[u] = pf[u];
+        const uint32_t nb = base + BE;
+        if (nb < E1) fetch(nb);
+        // Positions past E1 reloaded edge E1-1; they lie beyond every row, so no rank counts them.
+#pragma unroll
+        for (int u = 0; u < BLK; ++u) hit[u] = (__funnelshift_r(filler[hit[u] >> 5], 0u, hit[u]) & 1u) ^ neg;
+        uint32_t mc = 0;   // lane c < BLK: mask of chunk c
+#pragma unroll
+        for (int u = 0; u < BLK; ++u) {
+            const uint32_t m = __ballot_sync(FULL, hit[u]);
+            if (lane == (uint32_t)u) mc = m;
+        }
+        const uint32_t pc = __popc(mc);
+        uint32_t incl = pc;
+#pragma unroll
+        for (int o = 1; o < BLK; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        const uint32_t excl = incl - pc;
+        // hits before block-relative position x in [0, BE]
+        auto rank = [&](uint32_t x) -> uint32_t {
+            const uint32_t c = min(x >> 5, (uint32_t)BLK - 1);
+            const uint32_t e = __shfl_sync(FULL, excl, c);
+            const uint32_t m = __shfl_sync(FULL, mc, c);
+            const uint32_t sh = x - 32u * c;   // 0..32
+            return e + __popc(sh >= 32u ? m : (m & ((1u << sh) - 1u)));
+        };
+        // the words whose rows meet this block, in order
+        bool finished = false;
+#pragma unroll 1
+        for (;;) {
+            const uint32_t a = lo0 > base ? min(lo0 - base, BE) : 0u;
+            const uint32_t z = hi0 > base ? min(hi0 - base, BE) : 0u;
+            cnt += rank(z) - rank(a);
+            if (ew1 > nb) break;                       // word k goes on in the next block
+            put(k, __ballot_sync(FULL, lane_valid(k) && role_pred(kind, cnt, n_arg)));
+            if (++k == K) {
+                finished = true;
+                break;
+            }
+            next_word();
+        }
+        if (finished) return;
+        // word k spans past this block: skip the rest of it once every lane is decided
+        const bool decided = !lane_valid(k) || hi0 <= nb || (uint64_t)cnt >= cap;
+        if (__all_sync(FULL, decided)) {
+            put(k, __ballot_sync(FULL, lane_valid(k) && role_pred(kind, cnt, n_arg)));
+            if (++k == K) return;
+            const uint32_t nxt = ew1;                  // the next word's first edge
+            next_word();
+            if (nxt != nb && nxt < E1) fetch(nxt);
+            base = nxt;
+        } else {
+            base = nb;
+        }
+    }
+    // the stream ended (or was empty): the remaining words have no edges left
+    for (; k < K; ++k) {
+        put(k, __ballot_sync(FULL, lane_valid(k) && role_pred(kind, cnt, n_arg)));
+        cnt = 0;
+    }
+}
+
 // Numeric data-range restriction (Algorithms 9-10): one float compare per
 // individual, a ballot packs 32 of them into a word.  NaN (missing) compares
 // false.

@@ -114,11 +114,11 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 const DevCSR g = kb.csr[2u * d.a + inv];
                 if constexpr (STAGE) {
                     const uint32_t kind = (d.op >> 16) & 0xFFu;
-                    role_words<WPL, BLK>(g, sm.filler, kind, d.b, kb.n, lim_w, wb, lane, top, kind == HEDL_OP_FORALL);
+                    role_stream<WPL, BLK>(g, sm.filler, kind, d.b, kb.n, lim_w, wb, lane, top, kind == HEDL_OP_FORALL);
                 } else {
                     const uint32_t *filler = (d.ref & REF_SLOT) ? slots + (uint64_t)(d.ref & ~REF_SLOT) * kb.wp
                                                                 : kb.concepts + (uint64_t)d.ref * kb.wp;
-                    role_words<WPL, BLK>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, lim_w, wb, lane, top);
+                    role_stream<WPL, BLK>(g, filler, (d.op >> 16) & 0xFFu, d.b, kb.n, lim_w, wb, lane, top);
                 }
                 break;
             }
