@@ -290,7 +290,9 @@ int hedl_sync_status(hedl_kb *kb, hedl_stream s);
 /* ------------------------------------------------------------------ tuning */
 
 typedef struct {
-    uint32_t warps_per_cta;    /* 4, 8, 16 or 32 */
+    uint32_t warps_per_cta;    /* 1, 2, 4, 8, 16 or 32 (1 and 2: one word per lane, no
+                                  staging; a CTA's warps share each work item, so small
+                                  CTAs wait less on their slowest warp) */
     uint32_t words_per_lane;   /* 1 or 4: bitset words a lane holds per pass */
     uint32_t rounds;           /* warp passes per work item (tile = warps*32*words_per_lane*rounds words) */
     uint32_t ctas_per_sm;      /* 0 = as many as fit */

@@ -437,8 +437,11 @@ int hedl_tuning_get(const hedl_kb *kb, hedl_tuning *t) {
 
 int hedl_tuning_set(hedl_kb *kb, const hedl_tuning *t) {
     if (!kb || !t) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
-    if (!(t->warps_per_cta == 4 || t->warps_per_cta == 8 || t->warps_per_cta == 16 || t->warps_per_cta == 32))
-        return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta must be 4, 8, 16 or 32");
+    if (!(t->warps_per_cta == 1 || t->warps_per_cta == 2 || t->warps_per_cta == 4 || t->warps_per_cta == 8 ||
+          t->warps_per_cta == 16 || t->warps_per_cta == 32))
+        return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta must be 1, 2, 4, 8, 16 or 32");
+    if (t->warps_per_cta < 4 && t->words_per_lane != 1)
+        return fail(HEDL_ERR_INVALID_ARG, "warps_per_cta 1 and 2 take words_per_lane 1");
     if (t->stage_fillers > 1) return fail(HEDL_ERR_INVALID_ARG, "stage_fillers must be 0 or 1");
     if (!(t->role_block == 4 || t->role_block == 8)) return fail(HEDL_ERR_INVALID_ARG, "role_block must be 4 or 8");
     if (t->full_occupancy > 1) return fail(HEDL_ERR_INVALID_ARG, "full_occupancy must be 0 or 1");

@@ -425,13 +425,18 @@ __global__ void finalize_kernel(KBView kb, const uint8_t *ws, uint32_t *counts) 
 
 using KernelFn = void (*)(ExecArgs);
 
-// Instantiated launch shapes: warps x words per lane x staging x chunks per block.
+// Instantiated launch shapes: warps x words per lane x staging x chunks per block
+// (1- and 2-warp CTAs only with one word per lane and no staging).
 template <bool STAGE, int BLK>
 KernelFn pick_t(uint32_t warps, uint32_t wpl) {
     if (wpl == 4) {
         if (warps == 4) return exec_kernel<4, 4, STAGE, BLK>;
         if (warps == 16) return exec_kernel<16, 4, STAGE, BLK>;
         return exec_kernel<8, 4, STAGE, BLK>;
+    }
+    if constexpr (!STAGE) {
+        if (warps == 1) return exec_kernel<1, 1, false, BLK>;
+        if (warps == 2) return exec_kernel<2, 1, false, BLK>;
     }
     if (warps == 4) return exec_kernel<4, 1, STAGE, BLK>;
     if (warps == 16) return exec_kernel<16, 1, STAGE, BLK>;
@@ -455,7 +460,7 @@ size_t smem_bytes(const hedl_kb *kb, const Tuning &t, bool stage) {
 }  // namespace
 
 bool use_staging(const hedl_kb *kb, const Tuning &t) {
-    return t.stage && smem_bytes(kb, t, true) <= kb->smem_optin;
+    return t.stage && t.warps >= 4 && smem_bytes(kb, t, true) <= kb->smem_optin;
 }
 
 size_t exec_smem_bytes(const Tuning &t) { return stack_smem_bytes(t) + 16; }

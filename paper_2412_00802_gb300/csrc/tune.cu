@@ -30,6 +30,19 @@ std::vector<Tuning> candidates(const Tuning &base) {
                     t.full_occupancy = 0;
                     out.push_back(t);
                 }
+    for (uint32_t warps : {1u, 2u})
+        for (uint32_t rounds : {1u, 2u, 4u})
+            for (uint32_t blk : {4u, 8u}) {
+                Tuning t = base;
+                t.stage = 0;
+                t.warps = warps;
+                t.wpl = 1;
+                t.rounds = rounds;
+                t.role_block = blk;
+                t.ctas_per_sm = 0;
+                t.full_occupancy = 0;
+                out.push_back(t);
+            }
     for (uint32_t rounds : {1u, 2u, 4u})
         for (uint32_t blk : {4u, 8u}) {
             Tuning t = base;

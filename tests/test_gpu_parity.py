@@ -96,7 +96,9 @@ def test_c1_batched_shapes(c1, c1_dev):
                                     dict(warps_per_cta=16, words_per_lane=4, rounds=2, stage_fillers=0),
                                     dict(warps_per_cta=16, role_block=4, rounds=2, stage_fillers=1),
                                     dict(warps_per_cta=8, role_block=4, stage_fillers=0),
-                                    dict(warps_per_cta=8, role_block=8, stage_fillers=0, full_occupancy=1, rounds=4)])
+                                    dict(warps_per_cta=8, role_block=8, stage_fillers=0, full_occupancy=1, rounds=4),
+                                    dict(warps_per_cta=1, role_block=8, rounds=1),
+                                    dict(warps_per_cta=2, role_block=4, rounds=4, stage_fillers=1)])
 def test_launch_shapes(c1, tuning):
     dkb = device_kb(c1)
     H.hedl_tuning_set(dkb.handle, **tuning)
