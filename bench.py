@@ -277,11 +277,17 @@ def search_run(args, dev):
     out = {"workload": f"planted KB with the search workload's distributions, N={cfg.n:,}, {kb.n_roles} roles; "
                        f"beam 64, 8,192 refinements per step, {steps} steps"}
     res = {}
-    for name, kw in (("exhaustive", {}), ("surrogate_pruned", {"surrogate": sur, "keep_fraction": 0.25})):
+    state = sur.params().copy()
+    for name, kw in (("exhaustive", {}),
+                     ("surrogate_ordered", {"online_epochs": 4}),
+                     ("surrogate_pruned", {"keep_fraction": 0.25, "online_epochs": 4, "warmup_steps": 1})):
+        if "online_epochs" in kw:     # each surrogate run starts from the same pre-trained network
+            kw = dict(kw, surrogate=Surrogate(params=state, device=str(dev), grid=threshold_grid(kb.prop_vals)))
         t0 = time.perf_counter()
-        beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=4096, **kw).run(start, steps)
+        beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=2048, **kw).run(start, steps)
         res[name] = (beam, logs, time.perf_counter() - t0)
     eb, el, et = res["exhaustive"]
+    ob, ol, ot = res["surrogate_ordered"]
     sb, sl, st = res["surrogate_pruned"]
     target = eb[0].acc
 
@@ -291,11 +297,14 @@ def search_run(args, dev):
                 if b >= target:
                     return t
         return None
-    te, ts = first_reach(el), first_reach(sl)
-    out.update({"exhaustive_s": et, "pruned_s": st, "best_acc": target, "pruned_best_acc": sb[0].acc,
+    te, to, ts = first_reach(el), first_reach(ol), first_reach(sl)
+    out.update({"exhaustive_s": et, "ordered_s": ot, "pruned_s": st, "best_acc": target,
+                "ordered_best_acc": ob[0].acc, "pruned_best_acc": sb[0].acc,
                 "best_found_per_s_exhaustive": 1.0 / te if te else 0.0,
+                "best_found_per_s_ordered": 1.0 / to if to else 0.0,
                 "best_found_per_s_surrogate": 1.0 / ts if ts else 0.0,
                 "evaluated_exhaustive": sum(l.evaluated for l in el), "evaluated_pruned": sum(l.evaluated for l in sl),
+                "same_final_beam_ordered": [e.prog.tobytes() for e in eb] == [e.prog.tobytes() for e in ob],
                 "same_final_beam": [e.prog.tobytes() for e in eb] == [e.prog.tobytes() for e in sb],
                 "best": P.to_text(P.from_postfix(eb[0].prog))})
     return out

@@ -358,15 +358,20 @@ int hedl_mlp_get(const hedl_mlp *m, float *params, float *grads, uint32_t *step)
 int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
 
 /* Structural encoding of H programs (DEVICE progs uint64[offs[H]], offs
- * uint32[H+1]) into X (DEVICE bf16 [H][512] as uint16 bit patterns): integer
- * feature counts scaled by 1/4 (op histogram per depth, concept / role /
- * property / cardinality histograms, role-over-atom pairs, data thresholds
- * bucketed by grid, length and height, totals, a constant).  grid (DEVICE
- * float [n_grid][15], or NULL) holds each property's 15 increasing threshold
- * boundaries: a threshold t of property p lands in bucket #{g < t}.
+ * uint32[H+1]) into X (DEVICE bf16 [H][512] as uint16 bit patterns).  The
+ * paper has no learned component: this is the surrogate's input.  Features
+ * 0..509 are integer counts scaled by 1/4: op histogram per depth, atomic
+ * concepts by polarity (NOT and ATMOST flip it), roles, restriction kinds per
+ * depth, cardinalities, data restrictions by property, compare and polarity,
+ * thresholds by property and bucket, role-over-atom pairs by polarity,
+ * length, totals, a constant.  grid (DEVICE float [n_grid][15], or NULL)
+ * holds each property's 15 increasing threshold boundaries: a threshold t of
+ * property p lands in bucket #{g < t}.  prior (DEVICE float [H][2], or NULL
+ * for zeros) gives features 510-511 per program, rounded to bf16 (the search
+ * passes the exact accuracy and F1 of the hypothesis a candidate refines).
  * Instructions that are not op codes are ignored.  Asynchronous. */
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
-                uint16_t *X, hedl_stream s);
+                const float *prior, uint16_t *X, hedl_stream s);
 
 /* Y (DEVICE float [B][2]) = the network applied to X (DEVICE bf16 [B][512]). */
 int hedl_mlp_forward(hedl_mlp *m, const uint16_t *X, uint32_t B, float *Y, void *ws, size_t ws_bytes,

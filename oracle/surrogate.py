@@ -15,25 +15,32 @@ library):
 * ``ranking``: the total order used to rank hypotheses (accuracy desc, F1
   desc, length asc, program bytes asc, index asc) and recall@k.
 
-Encoding (feature index ranges; every value is an integer count scaled by
-1/4, exact in bfloat16).  Node depth is the distance from the root (root 0),
-clamped to 7; "height" is the tree height (leaves 1), clamped to 8.  A data
-threshold t of property p falls in bucket q = #{g in grid[p] : g < t} of a
-per-property grid of 15 increasing boundaries (the property's quantiles,
-supplied with the programs; q = 0 without a grid or for NaN t).
+Encoding (feature index ranges; every value but the prior is an integer
+count scaled by 1/4, exact in bfloat16).  Node depth is the distance from the
+root (root 0), clamped to 7; "height" is the tree height (leaves 1), clamped
+to 8.  Polarity is 0 at the root; NOT and ATMOST flip it for their operand,
+every other constructor passes it on (ALL, EXISTS, ATLEAST and EXACTLY do not
+flip it), so a node's polarity says whether the hypothesis grows (0) or
+shrinks (1) with its instance set.  A data threshold t of property p falls in
+bucket q = #{g in grid[p] : g < t} of a per-property grid of 15 increasing
+boundaries (the property's quantiles, supplied with the programs; q = 0
+without a grid or for NaN t).
   [  0,112) op histogram per depth: 14 ops x 8 depths, index depth*14 + op-1
-  [112,208) atomic concept histogram: concept id mod 96
-  [208,272) role histogram: (role id mod 32)*2 + inverse flag
-  [272,312) role-restriction kind per depth: depth*5 + (op - EXISTS)
-  [312,336) cardinality: (op - ATLEAST)*8 + min(n, 7)
-  [336,384) data restriction: (property id mod 16)*3 + (op - DGE)
-  [384,432) threshold bucket: (op - DGE)*16 + q
-  [432,496) role restriction over an atom: ((role*2 + inverse)*131 + concept) mod 64
+  [112,208) atomic concept: (concept id mod 48)*2 + polarity
+  [208,240) role: (role id mod 16)*2 + inverse flag
+  [240,280) role-restriction kind per depth: depth*5 + (op - EXISTS)
+  [280,304) cardinality: (op - ATLEAST)*8 + min(n, 7)
+  [304,352) data restriction: (property id mod 8)*6 + (op - DGE)*2 + polarity
+  [352,480) threshold of >= and <=: ((property id mod 8)*2 + (op - DGE))*8 + q // 2
+  [480,496) role restriction over an atom:
+            (((role*2 + inverse)*131 + concept) mod 8)*2 + polarity
   [496,504) length bucket: min(len, 39) // 5
   [504,508) counts of leaves, role restrictions, data restrictions, NOTs
   [508]     height - 1 (clamped to 7)
   [509]     constant 4 (a bias input; 4 * 1/4 = 1)
-  [510,512) zero
+  [510,512) prior: two caller-supplied values per program (the search passes
+            the exact accuracy and F1 of the hypothesis a candidate refines),
+            rounded to bfloat16, not scaled; 0 without a prior
 """
 from __future__ import annotations
 
@@ -58,25 +65,30 @@ def _arity(op: int) -> int:
     return 0
 
 
-def encode(prog: Sequence[int], grid=None) -> np.ndarray:
+def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
     """Structural encoding of one postfix program (float32[512]).
 
     grid: per-property threshold boundaries, float32 [n_props][15], or None.
+    prior: two floats (features 510, 511), or None.
     A program longer than 256 instructions is encoded by its last 256 (the
     root and the nodes nearest to it)."""
     prog = list(prog)[-256:]
     L = len(prog)
-    # node depths: read the postfix backwards (a pre-order walk, right child first)
+    # node depths and polarities: read the postfix backwards (a pre-order
+    # walk, right child first); NOT and ATMOST flip their operand's polarity
     depth = [0] * L
-    pending = [0]
+    pol = [0] * L
+    pending = [(0, 0)]
     height = 0
     for k in range(L - 1, -1, -1):
-        d = pending.pop()
+        d, pl = pending.pop()
         depth[k] = d
+        pol[k] = pl
         height = max(height, d + 1)
         op = int(prog[k]) & 0xFF
+        child_pol = pl ^ 1 if op in (_NOT, _MAX) else pl
         for _ in range(_arity(op)):
-            pending.append(d + 1)
+            pending.append((d + 1, child_pol))
     f = np.zeros(D_IN, dtype=np.int64)
     leaves = roles = datas = nots = 0
     for k in range(L):
@@ -87,24 +99,25 @@ def encode(prog: Sequence[int], grid=None) -> np.ndarray:
         if _arity(op) == 0:
             leaves += 1
         if op == _ATOM:
-            f[112 + a % 96] += 1
+            f[112 + (a % 48) * 2 + pol[k]] += 1
         elif _EX <= op <= _EXACT:
             roles += 1
-            f[208 + (a % 32) * 2 + inv] += 1
-            f[272 + d * 5 + (op - _EX)] += 1
+            f[208 + (a % 16) * 2 + inv] += 1
+            f[240 + d * 5 + (op - _EX)] += 1
             if op >= _MIN:
-                f[312 + (op - _MIN) * 8 + min(b, 7)] += 1
+                f[280 + (op - _MIN) * 8 + min(b, 7)] += 1
             child = int(prog[k - 1])       # the filler ends right before its restriction
             if child & 0xFF == _ATOM:
-                f[432 + (((a * 2 + inv) * 131 + ((child >> 16) & 0xFFFF)) % 64)] += 1
+                f[480 + (((a * 2 + inv) * 131 + ((child >> 16) & 0xFFFF)) % 8) * 2 + pol[k]] += 1
         elif _GE <= op <= _EQ:
             datas += 1
-            f[336 + (a % 16) * 3 + (op - _GE)] += 1
+            f[304 + (a % 8) * 6 + (op - _GE) * 2 + pol[k]] += 1
             t = np.array([b], np.uint32).view(np.float32)[0]
             q = 0
             if grid is not None and a < len(grid) and not np.isnan(t):
                 q = int(np.sum(np.asarray(grid[a], np.float32) < t))
-            f[384 + (op - _GE) * 16 + q] += 1
+            if op != _EQ:
+                f[352 + ((a % 8) * 2 + (op - _GE)) * 8 + q // 2] += 1
         elif op == _NOT:
             nots += 1
     f[496 + min(L, 39) // 5] += 1
@@ -114,7 +127,10 @@ def encode(prog: Sequence[int], grid=None) -> np.ndarray:
     f[507] += nots
     f[508] += min(height, 8) - 1
     f[509] += 4
-    return (f.astype(np.float64) * 0.25).astype(np.float32)
+    out = (f.astype(np.float64) * 0.25).astype(np.float32)
+    if prior is not None:
+        out[510:512] = bf16(np.asarray(prior, np.float32).reshape(2))
+    return out
 
 
 def threshold_grid(prop_vals: np.ndarray) -> np.ndarray:
@@ -127,8 +143,11 @@ def threshold_grid(prop_vals: np.ndarray) -> np.ndarray:
     return out
 
 
-def encode_batch(progs: Sequence[Sequence[int]], grid=None) -> np.ndarray:
-    return np.stack([encode(p, grid) for p in progs]) if len(progs) else np.zeros((0, D_IN), np.float32)
+def encode_batch(progs: Sequence[Sequence[int]], grid=None, prior=None) -> np.ndarray:
+    """prior: float [H][2] or None."""
+    if not len(progs):
+        return np.zeros((0, D_IN), np.float32)
+    return np.stack([encode(p, grid, None if prior is None else prior[i]) for i, p in enumerate(progs)])
 
 
 # ---------------------------------------------------------------------------- bfloat16

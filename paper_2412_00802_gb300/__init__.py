@@ -122,7 +122,7 @@ def library(path: Optional[str] = None):
             "hedl_mlp_free": (None, [P]),
             "hedl_mlp_get": (I, [P, P, P, ctypes.POINTER(U32)]),
             "hedl_mlp_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
-            "hedl_encode": (I, [P, P, U32, P, U32, P, P]),
+            "hedl_encode": (I, [P, P, U32, P, U32, P, P, P]),
             "hedl_mlp_forward": (I, [P, P, U32, P, P, ctypes.c_size_t, P]),
             "hedl_mlp_gradients": (I, [P, P, P, U32, P, P, ctypes.c_size_t, P]),
             "hedl_mlp_train_step": (I, [P, P, P, U32, ctypes.c_float, P, P, ctypes.c_size_t, P]),
@@ -410,12 +410,12 @@ def hedl_mlp_workspace_size(B: int) -> int:
     return out.value
 
 
-def hedl_encode(progs_dev, offs_dev, X, grid=None, stream=None):
+def hedl_encode(progs_dev, offs_dev, X, grid=None, prior=None, stream=None):
     """progs_dev: CUDA int64 tensor of instructions; offs_dev: CUDA int32 [H+1]; X: CUDA bf16 [H][512];
-    grid: CUDA float32 [n_props][15] threshold boundaries or None."""
+    grid: CUDA float32 [n_props][15] threshold boundaries or None; prior: CUDA float32 [H][2] or None."""
     H = offs_dev.numel() - 1
     _check(library().hedl_encode(_dptr(progs_dev), _dptr(offs_dev), H, _dptr(grid),
-                                 0 if grid is None else grid.shape[0], _dptr(X), _stream(stream)))
+                                 0 if grid is None else grid.shape[0], _dptr(prior), _dptr(X), _stream(stream)))
 
 
 def hedl_mlp_forward(m: MLPHandle, X, Y, ws, stream=None):

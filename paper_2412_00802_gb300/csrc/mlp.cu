@@ -33,15 +33,26 @@ __device__ __forceinline__ int arity_of(uint32_t op) {
 
 constexpr int ENC_MAXLEN = 256;
 
-// One warp per program: lane 0 computes node depths (a reversed walk of the
-// postfix is a pre-order walk), then the lanes count features into shared
-// memory and write the row as bf16 (counts x 1/4, exact).
+// One warp per program: lane 0 computes node depths and polarities (a
+// reversed walk of the postfix is a pre-order walk; NOT and ATMOST flip the
+// polarity of their operand), then the lanes count features into shared
+// memory and write the row as bf16 (counts x 1/4, exact), the two prior
+// inputs as bf16 of the caller's values.
+//   [  0,112) op x depth          [112,208) concept mod 48 x polarity
+//   [208,240) role mod 16 x inv   [240,280) restriction kind x depth
+//   [280,304) cardinality         [304,352) property mod 8 x compare x polarity
+//   [352,480) property mod 8 x (>=, <=) x threshold bucket / 2
+//   [480,496) role-over-atom hash mod 8 x polarity
+//   [496,504) length bucket       [504,510) totals, height, constant
+//   [510,512) prior
 __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t *__restrict__ offs, uint32_t H,
-                              const float *__restrict__ grid, uint32_t n_grid, __nv_bfloat16 *__restrict__ X) {
+                              const float *__restrict__ grid, uint32_t n_grid, const float *__restrict__ prior,
+                              __nv_bfloat16 *__restrict__ X) {
     constexpr int WARPS = 4;
     __shared__ uint32_t feat[WARPS][DI];
     __shared__ uint8_t depth[WARPS][ENC_MAXLEN];
-    __shared__ uint8_t pend[WARPS][ENC_MAXLEN + 1];
+    __shared__ uint8_t pol[WARPS][ENC_MAXLEN];
+    __shared__ uint8_t pend[WARPS][ENC_MAXLEN + 1];    // pending depth (7 bits) | polarity << 7
     __shared__ uint32_t height[WARPS];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (uint32_t h = blockIdx.x * WARPS + warp; h < H; h += gridDim.x * WARPS) {
@@ -54,15 +65,20 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             pend[warp][sp++] = 0;
             uint32_t ht = 0;
             for (int k = (int)L - 1; k >= 0; --k) {
-                if (sp == 0) {   // not a well-formed program: remaining nodes get depth 0
-                    for (; k >= 0; --k) depth[warp][k] = 0;
+                if (sp == 0) {   // not a well-formed program: remaining nodes get depth 0, polarity 0
+                    for (; k >= 0; --k) depth[warp][k] = 0, pol[warp][k] = 0;
                     break;
                 }
-                const uint32_t d = pend[warp][--sp];
-                depth[warp][k] = (uint8_t)min(d, 255u);
+                const uint32_t e = pend[warp][--sp];
+                const uint32_t d = e & 0x7Fu, pl = e >> 7;
+                depth[warp][k] = (uint8_t)d;
+                pol[warp][k] = (uint8_t)pl;
                 ht = max(ht, d + 1);
-                const int a = arity_of((uint32_t)(progs[o0 + k] & 0xFF));
-                for (int j = 0; j < a && sp <= ENC_MAXLEN; ++j) pend[warp][sp++] = (uint8_t)min(d + 1, 255u);
+                const uint32_t op = (uint32_t)(progs[o0 + k] & 0xFF);
+                const int a = arity_of(op);
+                // depths beyond 127 only feed clamped features (depth 7, height 8)
+                const uint32_t ce = min(d + 1, 127u) | ((pl ^ ((op == HEDL_OP_NOT || op == HEDL_OP_ATMOST) ? 1u : 0u)) << 7);
+                for (int j = 0; j < a && sp <= ENC_MAXLEN; ++j) pend[warp][sp++] = (uint8_t)ce;
             }
             height[warp] = ht;
         }
@@ -72,29 +88,32 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             const uint32_t op = (uint32_t)(w & 0xFF), inv = (uint32_t)((w >> 8) & 1);
             const uint32_t a = (uint32_t)((w >> 16) & 0xFFFF), b = (uint32_t)(w >> 32);
             if (op < HEDL_OP_ATOM || op > HEDL_OP_DEQ) continue;   // not an op code: ignored
-            const uint32_t d = min((uint32_t)depth[warp][k], 7u);
+            const uint32_t d = min((uint32_t)depth[warp][k], 7u), pl = pol[warp][k];
             atomicAdd(&feat[warp][d * 14 + op - 1], 1u);
             if (arity_of(op) == 0) atomicAdd(&feat[warp][504], 1u);
             if (op == HEDL_OP_ATOM) {
-                atomicAdd(&feat[warp][112 + a % 96], 1u);
+                atomicAdd(&feat[warp][112 + (a % 48) * 2 + pl], 1u);
             } else if (op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY) {
                 atomicAdd(&feat[warp][505], 1u);
-                atomicAdd(&feat[warp][208 + (a % 32) * 2 + inv], 1u);
-                atomicAdd(&feat[warp][272 + d * 5 + (op - HEDL_OP_EXISTS)], 1u);
-                if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][312 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1u);
+                atomicAdd(&feat[warp][208 + (a % 16) * 2 + inv], 1u);
+                atomicAdd(&feat[warp][240 + d * 5 + (op - HEDL_OP_EXISTS)], 1u);
+                if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][280 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1u);
                 if (k > 0) {   // the filler ends right before its restriction
                     const uint64_t c = progs[o0 + k - 1];
                     if ((c & 0xFF) == HEDL_OP_ATOM)
-                        atomicAdd(&feat[warp][432 + ((a * 2 + inv) * 131 + (uint32_t)((c >> 16) & 0xFFFF)) % 64], 1u);
+                        atomicAdd(&feat[warp][480 + (((a * 2 + inv) * 131 + (uint32_t)((c >> 16) & 0xFFFF)) % 8) * 2 + pl],
+                                  1u);
                 }
             } else if (op >= HEDL_OP_DGE) {
                 atomicAdd(&feat[warp][506], 1u);
-                atomicAdd(&feat[warp][336 + (a % 16) * 3 + (op - HEDL_OP_DGE)], 1u);
-                const float t = __uint_as_float(b);
-                uint32_t q = 0;
-                if (grid && a < n_grid && !(t != t))
-                    for (int g = 0; g < 15; ++g) q += grid[a * 15 + g] < t ? 1u : 0u;
-                atomicAdd(&feat[warp][384 + (op - HEDL_OP_DGE) * 16 + q], 1u);
+                atomicAdd(&feat[warp][304 + (a % 8) * 6 + (op - HEDL_OP_DGE) * 2 + pl], 1u);
+                if (op != HEDL_OP_DEQ) {
+                    const float t = __uint_as_float(b);
+                    uint32_t q = 0;
+                    if (grid && a < n_grid && !(t != t))
+                        for (int g = 0; g < 15; ++g) q += grid[a * 15 + g] < t ? 1u : 0u;
+                    atomicAdd(&feat[warp][352 + ((a % 8) * 2 + (op - HEDL_OP_DGE)) * 8 + q / 2], 1u);
+                }
             } else if (op == HEDL_OP_NOT) {
                 atomicAdd(&feat[warp][507], 1u);
             }
@@ -106,8 +125,12 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             feat[warp][509] += 4;
         }
         __syncwarp();
-        for (int i = lane; i < DI; i += 32)
-            X[(uint64_t)h * DI + i] = __float2bfloat16_rn(0.25f * (float)feat[warp][i]);
+        for (int i = lane; i < DI; i += 32) {
+            __nv_bfloat16 x;
+            if (i >= DI - 2) x = __float2bfloat16_rn(prior ? prior[2ull * h + (i - (DI - 2))] : 0.0f);
+            else x = __float2bfloat16_rn(0.25f * (float)feat[warp][i]);
+            X[(uint64_t)h * DI + i] = x;
+        }
         __syncwarp();
     }
 }
@@ -642,11 +665,11 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes) {
 }
 
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
-                uint16_t *X, hedl_stream s) {
+                const float *prior, uint16_t *X, hedl_stream s) {
     if (!progs || !offs || !X) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     if (H == 0) return HEDL_OK;
     encode_kernel<<<std::min<uint32_t>((H + 3) / 4, 8192), 128, 0, (cudaStream_t)s>>>(
-        progs, offs, H, grid, grid ? n_grid : 0u, (__nv_bfloat16 *)X);
+        progs, offs, H, grid, grid ? n_grid : 0u, prior, (__nv_bfloat16 *)X);
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(e, "encode launch") : HEDL_OK;
 }

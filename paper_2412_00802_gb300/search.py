@@ -10,9 +10,15 @@ of old beam plus candidates in the total order
 (old beam members first, then candidates in generation order).
 
 With a surrogate, candidates are evaluated in the order of their predicted
-scores; with pruning, only the predicted top fraction is evaluated.  Without
-pruning the surrogate changes only the evaluation order, so the final beam
-is the exhaustive search's.  Scores always come from exact evaluation.
+scores; each candidate's encoding carries, as its prior inputs, the exact
+accuracy and F1 of the beam member it refines (candidate k refines member
+k mod |beam|, the generator's convention, unless `parent_of` says
+otherwise).  With pruning, only the predicted top fraction is evaluated, from
+the step after `warmup_steps` on.  With `online_epochs`, the surrogate is
+trained after every step on all candidates scored exactly so far (with
+their priors), so it learns the search's own distribution.  Without pruning
+the surrogate changes only the evaluation order, so the final beam is the
+exhaustive search's.  Scores always come from exact evaluation.
 """
 from __future__ import annotations
 
@@ -96,7 +102,9 @@ class StepLog:
 
 class BeamSearch:
     def __init__(self, dkb, refine: Callable[[List[np.ndarray], int, int], List[np.ndarray]], width: int = 64,
-                 per_step: int = 8192, batch: int = 2048, surrogate=None, keep_fraction: Optional[float] = None):
+                 per_step: int = 8192, batch: int = 2048, surrogate=None, keep_fraction: Optional[float] = None,
+                 parent_of: Optional[Callable[[int, int], int]] = None, online_epochs: int = 0,
+                 warmup_steps: int = 0, online_lr: float = 1e-3):
         self.dkb = dkb
         self.refine = refine
         self.width = width
@@ -104,6 +112,11 @@ class BeamSearch:
         self.batch = batch
         self.surrogate = surrogate
         self.keep = keep_fraction
+        self.parent_of = parent_of or (lambda k, n_beam: k % n_beam)
+        self.online_epochs = online_epochs
+        self.warmup_steps = warmup_steps
+        self.online_lr = online_lr
+        self._seen_X, self._seen_T = [], []
 
     def _score(self, progs: List[np.ndarray]):
         from .surrogate import exact_scores
@@ -126,21 +139,25 @@ class BeamSearch:
         for s in range(1, steps + 1):
             ts = time.perf_counter()
             raw = self.refine([e.prog for e in beam], s, self.per_step)
-            cands, seen = [], {e.prog.tobytes() for e in beam}
-            for p in raw:
+            cands, parents, seen = [], [], {e.prog.tobytes() for e in beam}
+            for k, p in enumerate(raw):
                 cp = canonical(p)
                 b = cp.tobytes()
                 if b not in seen:
                     seen.add(b)
                     cands.append(cp)
+                    parents.append(self.parent_of(k, len(beam)))
             order = list(range(len(cands)))
+            X = None
             if self.surrogate is not None and cands:
                 flat = np.concatenate(cands).astype(np.uint64)
                 offs = np.zeros(len(cands) + 1, np.uint32)
                 np.cumsum([len(p) for p in cands], out=offs[1:])
-                Y = self.surrogate.predict(self.surrogate.encode(flat, offs)).cpu().numpy()
+                prior = np.array([[beam[j].acc, beam[j].f1] for j in parents], np.float32)
+                X = self.surrogate.encode(flat, offs, prior)
+                Y = self.surrogate.predict(X).cpu().numpy()
                 order = sorted(order, key=lambda i: (-Y[i, 0], -Y[i, 1], i))
-                if self.keep is not None:
+                if self.keep is not None and s > self.warmup_steps:
                     order = order[:max(1, int(round(self.keep * len(order))))]
             entries = [None] * len(cands)
             log = StepLog(s, len(cands), len(order), best, 0.0)
@@ -152,8 +169,22 @@ class BeamSearch:
                     entries[i] = Entry(cands[i], float(a[j]), float(f[j]), tuple(int(x) for x in c[j]))
                 best = max(best, float(a.max()) if len(a) else best)
                 log.events.append((time.perf_counter() - t0, best))
+            if self.online_epochs and X is not None:
+                self._learn(X, order, entries)
             beam = beam_update(beam, [e for e in entries if e is not None], self.width)
             log.best_acc = beam[0].acc
             log.seconds = time.perf_counter() - ts
             logs.append(log)
         return beam, logs
+
+    def _learn(self, X, evaluated: List[int], entries: List[Entry]):
+        """Train the surrogate on every candidate scored exactly so far."""
+        torch = self.surrogate.torch
+        idx = torch.tensor(evaluated, dtype=torch.int64, device=X.device)
+        self._seen_X.append(X.index_select(0, idx))
+        self._seen_T.append(torch.tensor([[entries[i].acc, entries[i].f1] for i in evaluated], dtype=torch.float32,
+                                         device=X.device))
+        Xa, Ta = torch.cat(self._seen_X), torch.cat(self._seen_T)
+        batch = min(1024, Xa.shape[0])
+        self.surrogate.train(Xa, Ta, epochs=self.online_epochs, batch=batch, lr=self.online_lr,
+                             seed=len(self._seen_X))

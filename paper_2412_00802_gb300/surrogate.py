@@ -73,13 +73,15 @@ class Surrogate:
     def params(self) -> np.ndarray:
         return hedl_mlp_get(self.mlp)[0]
 
-    def encode(self, progs: np.ndarray, offs: np.ndarray):
-        """bf16 [H][512] encodings of host programs (copied to the device first)."""
+    def encode(self, progs: np.ndarray, offs: np.ndarray, prior: Optional[np.ndarray] = None):
+        """bf16 [H][512] encodings of host programs (copied to the device first); prior: float
+        [H][2] per-program inputs (features 510-511) or None."""
         torch = self.torch
         p = torch.from_numpy(np.ascontiguousarray(progs, np.uint64).view(np.int64)).to(self.device)
         o = torch.from_numpy(np.ascontiguousarray(offs, np.uint32).view(np.int32)).to(self.device)
+        pr = None if prior is None else torch.from_numpy(np.ascontiguousarray(prior, np.float32)).to(self.device)
         X = torch.empty((len(offs) - 1, D_IN), dtype=torch.bfloat16, device=self.device)
-        hedl_encode(p, o, X, self.grid)
+        hedl_encode(p, o, X, self.grid, pr)
         return X
 
     def predict(self, X, batch: int = 65536):

@@ -49,9 +49,14 @@ def test_surrogate_order_without_pruning_keeps_the_beam(env):
     plain, _ = BeamSearch(dkb, _refine_fn(ref), width=16, per_step=512).run(start, 3)
     ordered, logs = BeamSearch(dkb, _refine_fn(ref), width=16, per_step=512, surrogate=Surrogate(seed=3)).run(start, 3)
     assert [(e.prog.tobytes(), e.counts) for e in plain] == [(e.prog.tobytes(), e.counts) for e in ordered]
+    # trained online on its own exact scores, still without pruning: the same beam
+    online, _ = BeamSearch(dkb, _refine_fn(ref), width=16, per_step=512, surrogate=Surrogate(seed=3),
+                           online_epochs=2).run(start, 3)
+    assert [(e.prog.tobytes(), e.counts) for e in plain] == [(e.prog.tobytes(), e.counts) for e in online]
     pruned, plog = BeamSearch(dkb, _refine_fn(ref), width=16, per_step=512, surrogate=Surrogate(seed=3),
-                              keep_fraction=0.25).run(start, 3)
-    assert all(l.evaluated <= 0.26 * l.candidates + 1 for l in plog)
+                              keep_fraction=0.25, online_epochs=2, warmup_steps=1).run(start, 3)
+    assert plog[0].evaluated == plog[0].candidates          # the warm-up step scores everything
+    assert all(l.evaluated <= 0.26 * l.candidates + 1 for l in plog[1:])
     # every reported score is exact
     okb = oracle.from_synth(kb)
     for e in pruned:

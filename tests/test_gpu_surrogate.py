@@ -43,6 +43,9 @@ def test_encoder_bit_exact(env):
     grid = S.threshold_grid(kb.prop_vals)
     got = sg.Surrogate(grid=grid).encode(flat, offs).float().cpu().numpy()
     assert np.array_equal(got, S.encode_batch(progs, grid))
+    prior = np.random.default_rng(7).uniform(size=(len(progs), 2)).astype(np.float32)
+    got = sg.Surrogate(grid=grid).encode(flat, offs, prior).float().cpu().numpy()
+    assert np.array_equal(got, S.encode_batch(progs, grid, prior))
     assert np.array_equal(grid, sg.threshold_grid(kb.prop_vals))
 
 

@@ -9,30 +9,50 @@ from synth import programs as P
 
 
 def test_encoding_hand_worked():
-    # (and A1 (some r2- A3)), postfix A1 A3 EXISTS AND: AND depth 0; A1, EXISTS depth 1; A3 depth 2
+    # (and A1 (some r2- A3)), postfix A1 A3 EXISTS AND: AND depth 0; A1, EXISTS depth 1; A3 depth 2;
+    # every node has polarity 0
     f = S.encode(P.compile_text("(and A1 (some r2- A3))"))
     want = np.zeros(512, np.float32)
     for i, c in {0 * 14 + 4: 1, 1 * 14 + 0: 1, 1 * 14 + 6: 1, 2 * 14 + 0: 1,   # op x depth
-                 112 + 1: 1, 112 + 3: 1,                                         # concepts
+                 112 + 1 * 2: 1, 112 + 3 * 2: 1,                                 # concepts 1, 3 (polarity 0)
                  208 + 2 * 2 + 1: 1,                                             # role 2 inverted
-                 272 + 1 * 5 + 0: 1,                                             # EXISTS at depth 1
-                 432 + ((2 * 2 + 1) * 131 + 3) % 64: 1,                          # role 2^- over atom 3
+                 240 + 1 * 5 + 0: 1,                                             # EXISTS at depth 1
+                 480 + (((2 * 2 + 1) * 131 + 3) % 8) * 2: 1,                     # role 2^- over atom 3: 658 mod 8 = 2
                  496 + 4 // 5: 1,                                                # length 4
                  504: 2, 505: 1, 508: 3 - 1, 509: 4}.items():                    # leaves, roles, height, bias
         want[i] = 0.25 * c
     assert np.array_equal(f, want)
-    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1, no atom filler
+    assert 480 + 2 * 2 == 484
+    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1, no atom filler; property 9 -> 9 mod 8 = 1
     f = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"))
     want = np.zeros(512, np.float32)
-    for i, c in {0 * 14 + 8: 1, 1 * 14 + 11: 1, 208 + 0: 1, 272 + 2: 1, 312 + 0 * 8 + 3: 1,
-                 336 + 9 * 3 + 0: 1, 384 + 0: 1, 496: 1, 504: 1, 505: 1, 506: 1, 508: 1, 509: 4}.items():
+    for i, c in {0 * 14 + 8: 1, 1 * 14 + 11: 1, 208 + 0: 1, 240 + 2: 1, 280 + 0 * 8 + 3: 1,
+                 304 + 1 * 6 + 0: 1, 352 + (1 * 2 + 0) * 8 + 0: 1, 496: 1, 504: 1, 505: 1, 506: 1, 508: 1,
+                 509: 4}.items():
         want[i] = 0.25 * c
     assert np.array_equal(f, want)
-    # with a grid, 1.0 lies above 7 of property 9's 15 boundaries (0.3 .. 1.7 step 0.1, 1.0 excluded)
+    # with a grid, 1.0 lies above 7 of property 9's 15 boundaries (0.3 .. 1.7 step 0.1, 1.0 excluded):
+    # bucket 7, feature bucket 7 // 2 = 3
     grid = np.zeros((10, 15), np.float32)
     grid[9] = np.float32(0.3) + np.float32(0.1) * np.arange(15, dtype=np.float32)
     g = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"), grid)
-    assert g[384 + 7] == 0.25 and g[384] == 0.0 and int(np.sum(grid[9] < np.float32(1.0))) == 7
+    assert g[352 + 16 + 3] == 0.25 and g[352 + 16] == 0.0 and int(np.sum(grid[9] < np.float32(1.0))) == 7
+    # polarity: (not (and A1 (max 2 r1 A50))), postfix A1 A50 ATMOST AND NOT.  NOT flips the
+    # conjunction and its operands to polarity 1; ATMOST flips again, so A50 has polarity 0.
+    f = S.encode(P.compile_text("(not (and A1 (max 2 r1 A50)))"))
+    want = np.zeros(512, np.float32)
+    for i, c in {0 * 14 + 3: 1, 1 * 14 + 4: 1, 2 * 14 + 0: 1, 2 * 14 + 9: 1, 3 * 14 + 0: 1,
+                 112 + 1 * 2 + 1: 1,                    # A1 at polarity 1
+                 112 + (50 % 48) * 2 + 0: 1,            # A50 (50 mod 48 = 2) at polarity 0
+                 208 + 1 * 2: 1, 240 + 2 * 5 + 3: 1, 280 + 1 * 8 + 2: 1,
+                 480 + (((1 * 2) * 131 + 50) % 8) * 2 + 1: 1,   # 312 mod 8 = 0; the restriction at polarity 1
+                 496 + 5 // 5: 1, 504: 2, 505: 1, 507: 1, 508: 4 - 1, 509: 4}.items():
+        want[i] = 0.25 * c
+    assert np.array_equal(f, want)
+    # a prior lands in features 510 and 511, rounded to bfloat16 and not scaled
+    g = S.encode(P.compile_text("A0"), None, (0.8125, 0.3))
+    assert g[510] == np.float32(0.8125) and g[511] == np.float32(0.30078125)
+    assert np.array_equal(g[:510], S.encode(P.compile_text("A0"))[:510])
 
 
 def test_bf16_rounding():
