@@ -361,10 +361,10 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
  * uint32[H+1]) into X (DEVICE bf16 [H][512] as uint16 bit patterns).  The
  * paper has no learned component: this is the surrogate's input.  Features
  * 0..509 are integer counts scaled by 1/4: op histogram per depth, atomic
- * concepts by polarity (NOT and ATMOST flip it), roles, restriction kinds per
- * depth, cardinalities, data restrictions by property, compare and polarity,
- * thresholds by property and bucket, role-over-atom pairs by polarity,
- * length, totals, a constant.  grid (DEVICE float [n_grid][15], or NULL)
+ * concepts, roles, restriction kinds per depth, cardinalities, >= / <=
+ * restrictions by property and threshold bucket, role-over-atom pairs,
+ * length, totals, a constant; concepts, thresholds and role-over-atom pairs
+ * count -1 at odd polarity (under an odd number of NOT / ATMOST).  grid (DEVICE float [n_grid][15], or NULL)
  * holds each property's 15 increasing threshold boundaries: a threshold t of
  * property p lands in bucket #{g < t}.  prior (DEVICE float [H][2], or NULL
  * for zeros) gives features 510-511 per program, rounded to bf16 (the search

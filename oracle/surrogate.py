@@ -17,24 +17,22 @@ library):
 
 Encoding (feature index ranges; every value but the prior is an integer
 count scaled by 1/4, exact in bfloat16).  Node depth is the distance from the
-root (root 0), clamped to 7; "height" is the tree height (leaves 1), clamped
-to 8.  Polarity is 0 at the root; NOT and ATMOST flip it for their operand,
-every other constructor passes it on (ALL, EXISTS, ATLEAST and EXACTLY do not
-flip it), so a node's polarity says whether the hypothesis grows (0) or
-shrinks (1) with its instance set.  A data threshold t of property p falls in
-bucket q = #{g in grid[p] : g < t} of a per-property grid of 15 increasing
-boundaries (the property's quantiles, supplied with the programs; q = 0
-without a grid or for NaN t).
-  [  0,112) op histogram per depth: 14 ops x 8 depths, index depth*14 + op-1
-  [112,208) atomic concept: (concept id mod 48)*2 + polarity
-  [208,240) role: (role id mod 16)*2 + inverse flag
-  [240,280) role-restriction kind per depth: depth*5 + (op - EXISTS)
-  [280,304) cardinality: (op - ATLEAST)*8 + min(n, 7)
-  [304,352) data restriction: (property id mod 8)*6 + (op - DGE)*2 + polarity
-  [352,480) threshold of >= and <=: ((property id mod 8)*2 + (op - DGE))*8 + q // 2
-  [480,496) role restriction over an atom:
-            (((role*2 + inverse)*131 + concept) mod 8)*2 + polarity
-  [496,504) length bucket: min(len, 39) // 5
+root (root 0); "height" is the tree height (leaves 1), clamped to 8.
+Polarity is 0 at the root; NOT and ATMOST flip it for their operand, every
+other constructor passes it on, so a node's polarity says whether the
+hypothesis grows (0) or shrinks (1) with its instance set.  A *signed* count
+adds +1 for an occurrence at polarity 0 and -1 at polarity 1.  A data
+threshold t of property p falls in bucket q = #{g in grid[p] : g < t} of a
+per-property grid of 15 increasing boundaries (the property's quantiles,
+supplied with the programs; q = 0 without a grid or for NaN t).
+  [  0, 84) op histogram per depth: min(depth, 5)*14 + op-1
+  [ 84,180) atomic concept, signed: concept id mod 96
+  [180,244) role: (role id mod 32)*2 + inverse flag
+  [244,284) role-restriction kind per depth: min(depth, 7)*5 + (op - EXISTS)
+  [284,308) cardinality: (op - ATLEAST)*8 + min(n, 7)
+  [308,436) >= and <= restrictions, signed: ((property id mod 16)*2 + (op - DGE))*4 + q // 4
+  [436,500) role restriction over an atom, signed: ((role*2 + inverse)*131 + concept) mod 64
+  [500,504) length bucket: min(len, 39) // 10
   [504,508) counts of leaves, role restrictions, data restrictions, NOTs
   [508]     height - 1 (clamped to 7)
   [509]     constant 4 (a bias input; 4 * 1/4 = 1)
@@ -94,33 +92,32 @@ def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
     for k in range(L):
         w = int(prog[k])
         op, inv, a, b = w & 0xFF, (w >> 8) & 1, (w >> 16) & 0xFFFF, (w >> 32) & 0xFFFFFFFF
-        d = min(depth[k], 7)
-        f[d * 14 + op - 1] += 1
+        sign = 1 - 2 * pol[k]
+        f[min(depth[k], 5) * 14 + op - 1] += 1
         if _arity(op) == 0:
             leaves += 1
         if op == _ATOM:
-            f[112 + (a % 48) * 2 + pol[k]] += 1
+            f[84 + a % 96] += sign
         elif _EX <= op <= _EXACT:
             roles += 1
-            f[208 + (a % 16) * 2 + inv] += 1
-            f[240 + d * 5 + (op - _EX)] += 1
+            f[180 + (a % 32) * 2 + inv] += 1
+            f[244 + min(depth[k], 7) * 5 + (op - _EX)] += 1
             if op >= _MIN:
-                f[280 + (op - _MIN) * 8 + min(b, 7)] += 1
+                f[284 + (op - _MIN) * 8 + min(b, 7)] += 1
             child = int(prog[k - 1])       # the filler ends right before its restriction
             if child & 0xFF == _ATOM:
-                f[480 + (((a * 2 + inv) * 131 + ((child >> 16) & 0xFFFF)) % 8) * 2 + pol[k]] += 1
+                f[436 + ((a * 2 + inv) * 131 + ((child >> 16) & 0xFFFF)) % 64] += sign
         elif _GE <= op <= _EQ:
             datas += 1
-            f[304 + (a % 8) * 6 + (op - _GE) * 2 + pol[k]] += 1
-            t = np.array([b], np.uint32).view(np.float32)[0]
-            q = 0
-            if grid is not None and a < len(grid) and not np.isnan(t):
-                q = int(np.sum(np.asarray(grid[a], np.float32) < t))
             if op != _EQ:
-                f[352 + ((a % 8) * 2 + (op - _GE)) * 8 + q // 2] += 1
+                t = np.array([b], np.uint32).view(np.float32)[0]
+                q = 0
+                if grid is not None and a < len(grid) and not np.isnan(t):
+                    q = int(np.sum(np.asarray(grid[a], np.float32) < t))
+                f[308 + ((a % 16) * 2 + (op - _GE)) * 4 + q // 4] += sign
         elif op == _NOT:
             nots += 1
-    f[496 + min(L, 39) // 5] += 1
+    f[500 + min(L, 39) // 10] += 1
     f[504] += leaves
     f[505] += roles
     f[506] += datas

@@ -37,19 +37,19 @@ constexpr int ENC_MAXLEN = 256;
 // reversed walk of the postfix is a pre-order walk; NOT and ATMOST flip the
 // polarity of their operand), then the lanes count features into shared
 // memory and write the row as bf16 (counts x 1/4, exact), the two prior
-// inputs as bf16 of the caller's values.
-//   [  0,112) op x depth          [112,208) concept mod 48 x polarity
-//   [208,240) role mod 16 x inv   [240,280) restriction kind x depth
-//   [280,304) cardinality         [304,352) property mod 8 x compare x polarity
-//   [352,480) property mod 8 x (>=, <=) x threshold bucket / 2
-//   [480,496) role-over-atom hash mod 8 x polarity
-//   [496,504) length bucket       [504,510) totals, height, constant
+// inputs as bf16 of the caller's values.  Signed counts add +1 at polarity 0
+// and -1 at polarity 1.
+//   [  0, 84) op x min(depth, 5)          [ 84,180) concept mod 96, signed
+//   [180,244) role mod 32 x inverse       [244,284) restriction kind x depth
+//   [284,308) cardinality                 [308,436) property mod 16 x (>=, <=) x bucket / 4, signed
+//   [436,500) role-over-atom hash mod 64, signed
+//   [500,504) length / 10                 [504,510) totals, height, constant
 //   [510,512) prior
 __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t *__restrict__ offs, uint32_t H,
                               const float *__restrict__ grid, uint32_t n_grid, const float *__restrict__ prior,
                               __nv_bfloat16 *__restrict__ X) {
     constexpr int WARPS = 4;
-    __shared__ uint32_t feat[WARPS][DI];
+    __shared__ int feat[WARPS][DI];
     __shared__ uint8_t depth[WARPS][ENC_MAXLEN];
     __shared__ uint8_t pol[WARPS][ENC_MAXLEN];
     __shared__ uint8_t pend[WARPS][ENC_MAXLEN + 1];    // pending depth (7 bits) | polarity << 7
@@ -77,7 +77,8 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
                 const uint32_t op = (uint32_t)(progs[o0 + k] & 0xFF);
                 const int a = arity_of(op);
                 // depths beyond 127 only feed clamped features (depth 7, height 8)
-                const uint32_t ce = min(d + 1, 127u) | ((pl ^ ((op == HEDL_OP_NOT || op == HEDL_OP_ATMOST) ? 1u : 0u)) << 7);
+                const uint32_t flip = (op == HEDL_OP_NOT || op == HEDL_OP_ATMOST) ? 1u : 0u;
+                const uint32_t ce = min(d + 1, 127u) | ((pl ^ flip) << 7);
                 for (int j = 0; j < a && sp <= ENC_MAXLEN; ++j) pend[warp][sp++] = (uint8_t)ce;
             }
             height[warp] = ht;
@@ -88,40 +89,39 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             const uint32_t op = (uint32_t)(w & 0xFF), inv = (uint32_t)((w >> 8) & 1);
             const uint32_t a = (uint32_t)((w >> 16) & 0xFFFF), b = (uint32_t)(w >> 32);
             if (op < HEDL_OP_ATOM || op > HEDL_OP_DEQ) continue;   // not an op code: ignored
-            const uint32_t d = min((uint32_t)depth[warp][k], 7u), pl = pol[warp][k];
-            atomicAdd(&feat[warp][d * 14 + op - 1], 1u);
-            if (arity_of(op) == 0) atomicAdd(&feat[warp][504], 1u);
+            const uint32_t dk = depth[warp][k];
+            const int sign = pol[warp][k] ? -1 : 1;
+            atomicAdd(&feat[warp][min(dk, 5u) * 14 + op - 1], 1);
+            if (arity_of(op) == 0) atomicAdd(&feat[warp][504], 1);
             if (op == HEDL_OP_ATOM) {
-                atomicAdd(&feat[warp][112 + (a % 48) * 2 + pl], 1u);
+                atomicAdd(&feat[warp][84 + a % 96], sign);
             } else if (op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY) {
-                atomicAdd(&feat[warp][505], 1u);
-                atomicAdd(&feat[warp][208 + (a % 16) * 2 + inv], 1u);
-                atomicAdd(&feat[warp][240 + d * 5 + (op - HEDL_OP_EXISTS)], 1u);
-                if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][280 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1u);
+                atomicAdd(&feat[warp][505], 1);
+                atomicAdd(&feat[warp][180 + (a % 32) * 2 + inv], 1);
+                atomicAdd(&feat[warp][244 + min(dk, 7u) * 5 + (op - HEDL_OP_EXISTS)], 1);
+                if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][284 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1);
                 if (k > 0) {   // the filler ends right before its restriction
                     const uint64_t c = progs[o0 + k - 1];
                     if ((c & 0xFF) == HEDL_OP_ATOM)
-                        atomicAdd(&feat[warp][480 + (((a * 2 + inv) * 131 + (uint32_t)((c >> 16) & 0xFFFF)) % 8) * 2 + pl],
-                                  1u);
+                        atomicAdd(&feat[warp][436 + ((a * 2 + inv) * 131 + (uint32_t)((c >> 16) & 0xFFFF)) % 64], sign);
                 }
             } else if (op >= HEDL_OP_DGE) {
-                atomicAdd(&feat[warp][506], 1u);
-                atomicAdd(&feat[warp][304 + (a % 8) * 6 + (op - HEDL_OP_DGE) * 2 + pl], 1u);
+                atomicAdd(&feat[warp][506], 1);
                 if (op != HEDL_OP_DEQ) {
                     const float t = __uint_as_float(b);
                     uint32_t q = 0;
                     if (grid && a < n_grid && !(t != t))
                         for (int g = 0; g < 15; ++g) q += grid[a * 15 + g] < t ? 1u : 0u;
-                    atomicAdd(&feat[warp][352 + ((a % 8) * 2 + (op - HEDL_OP_DGE)) * 8 + q / 2], 1u);
+                    atomicAdd(&feat[warp][308 + ((a % 16) * 2 + (op - HEDL_OP_DGE)) * 4 + q / 4], sign);
                 }
             } else if (op == HEDL_OP_NOT) {
-                atomicAdd(&feat[warp][507], 1u);
+                atomicAdd(&feat[warp][507], 1);
             }
         }
         __syncwarp();
         if (lane == 0) {
-            feat[warp][496 + min(L, 39u) / 5] += 1;
-            feat[warp][508] += min(height[warp], 8u) - 1;
+            feat[warp][500 + min(L, 39u) / 10] += 1;
+            feat[warp][508] += (int)min(height[warp], 8u) - 1;
             feat[warp][509] += 4;
         }
         __syncwarp();

@@ -8,47 +8,50 @@ from oracle import surrogate as S
 from synth import programs as P
 
 
+def _want(entries):
+    w = np.zeros(512, np.float32)
+    for i, c in entries.items():
+        w[i] = 0.25 * c
+    return w
+
+
 def test_encoding_hand_worked():
     # (and A1 (some r2- A3)), postfix A1 A3 EXISTS AND: AND depth 0; A1, EXISTS depth 1; A3 depth 2;
-    # every node has polarity 0
+    # every node has polarity 0 (signed counts +1)
     f = S.encode(P.compile_text("(and A1 (some r2- A3))"))
-    want = np.zeros(512, np.float32)
-    for i, c in {0 * 14 + 4: 1, 1 * 14 + 0: 1, 1 * 14 + 6: 1, 2 * 14 + 0: 1,   # op x depth
-                 112 + 1 * 2: 1, 112 + 3 * 2: 1,                                 # concepts 1, 3 (polarity 0)
-                 208 + 2 * 2 + 1: 1,                                             # role 2 inverted
-                 240 + 1 * 5 + 0: 1,                                             # EXISTS at depth 1
-                 480 + (((2 * 2 + 1) * 131 + 3) % 8) * 2: 1,                     # role 2^- over atom 3: 658 mod 8 = 2
-                 496 + 4 // 5: 1,                                                # length 4
-                 504: 2, 505: 1, 508: 3 - 1, 509: 4}.items():                    # leaves, roles, height, bias
-        want[i] = 0.25 * c
-    assert np.array_equal(f, want)
-    assert 480 + 2 * 2 == 484
-    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1, no atom filler; property 9 -> 9 mod 8 = 1
+    assert ((2 * 2 + 1) * 131 + 3) % 64 == 18
+    assert np.array_equal(f, _want({0 * 14 + 4: 1, 1 * 14 + 0: 1, 1 * 14 + 6: 1, 2 * 14 + 0: 1,   # op x depth
+                                    84 + 1: 1, 84 + 3: 1,                 # concepts 1 and 3
+                                    180 + 2 * 2 + 1: 1,                   # role 2 inverted
+                                    244 + 1 * 5 + 0: 1,                   # EXISTS at depth 1
+                                    436 + 18: 1,                          # role 2^- over atom 3
+                                    500 + 4 // 10: 1,                     # length 4
+                                    504: 2, 505: 1, 508: 3 - 1, 509: 4}))  # leaves, roles, height, bias
+    # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1; property 9, >=, bucket 0 without a grid
     f = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"))
-    want = np.zeros(512, np.float32)
-    for i, c in {0 * 14 + 8: 1, 1 * 14 + 11: 1, 208 + 0: 1, 240 + 2: 1, 280 + 0 * 8 + 3: 1,
-                 304 + 1 * 6 + 0: 1, 352 + (1 * 2 + 0) * 8 + 0: 1, 496: 1, 504: 1, 505: 1, 506: 1, 508: 1,
-                 509: 4}.items():
-        want[i] = 0.25 * c
-    assert np.array_equal(f, want)
+    assert np.array_equal(f, _want({0 * 14 + 8: 1, 1 * 14 + 11: 1, 180 + 0: 1, 244 + 2: 1, 284 + 0 * 8 + 3: 1,
+                                    308 + (9 * 2 + 0) * 4 + 0: 1, 500: 1, 504: 1, 505: 1, 506: 1, 508: 1,
+                                    509: 4}))
     # with a grid, 1.0 lies above 7 of property 9's 15 boundaries (0.3 .. 1.7 step 0.1, 1.0 excluded):
-    # bucket 7, feature bucket 7 // 2 = 3
+    # bucket 7, feature bucket 7 // 4 = 1
     grid = np.zeros((10, 15), np.float32)
     grid[9] = np.float32(0.3) + np.float32(0.1) * np.arange(15, dtype=np.float32)
     g = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"), grid)
-    assert g[352 + 16 + 3] == 0.25 and g[352 + 16] == 0.0 and int(np.sum(grid[9] < np.float32(1.0))) == 7
-    # polarity: (not (and A1 (max 2 r1 A50))), postfix A1 A50 ATMOST AND NOT.  NOT flips the
-    # conjunction and its operands to polarity 1; ATMOST flips again, so A50 has polarity 0.
+    assert int(np.sum(grid[9] < np.float32(1.0))) == 7
+    assert g[308 + 18 * 4 + 1] == 0.25 and g[308 + 18 * 4] == 0.0
+    # polarity: (not (and A1 (max 2 r1 A50))), postfix A1 A50 ATMOST AND NOT.  NOT puts the
+    # conjunction and its operands at polarity 1 (count -1); ATMOST flips again, A50 is at 0.
+    assert ((1 * 2) * 131 + 50) % 64 == 56
     f = S.encode(P.compile_text("(not (and A1 (max 2 r1 A50)))"))
-    want = np.zeros(512, np.float32)
-    for i, c in {0 * 14 + 3: 1, 1 * 14 + 4: 1, 2 * 14 + 0: 1, 2 * 14 + 9: 1, 3 * 14 + 0: 1,
-                 112 + 1 * 2 + 1: 1,                    # A1 at polarity 1
-                 112 + (50 % 48) * 2 + 0: 1,            # A50 (50 mod 48 = 2) at polarity 0
-                 208 + 1 * 2: 1, 240 + 2 * 5 + 3: 1, 280 + 1 * 8 + 2: 1,
-                 480 + (((1 * 2) * 131 + 50) % 8) * 2 + 1: 1,   # 312 mod 8 = 0; the restriction at polarity 1
-                 496 + 5 // 5: 1, 504: 2, 505: 1, 507: 1, 508: 4 - 1, 509: 4}.items():
-        want[i] = 0.25 * c
-    assert np.array_equal(f, want)
+    assert np.array_equal(f, _want({0 * 14 + 3: 1, 1 * 14 + 4: 1, 2 * 14 + 0: 1, 2 * 14 + 9: 1, 3 * 14 + 0: 1,
+                                    84 + 1: -1, 84 + 50: 1,
+                                    180 + 1 * 2: 1, 244 + 2 * 5 + 3: 1, 284 + 1 * 8 + 2: 1,
+                                    436 + 56: -1,                          # the restriction sits at polarity 1
+                                    500 + 5 // 10: 1, 504: 2, 505: 1, 507: 1, 508: 4 - 1, 509: 4}))
+    # seven nested NOTs over A0: depths 0..6 and 7, op x depth clamps depth at 5, A0 at polarity 1
+    f = S.encode(P.compile_text("(not " * 7 + "A0" + ")" * 7))
+    assert np.array_equal(f, _want({**{d * 14 + 3: 1 for d in range(5)}, 5 * 14 + 3: 2, 5 * 14 + 0: 1,
+                                    84 + 0: -1, 500: 1, 504: 1, 507: 7, 508: 7, 509: 4}))
     # a prior lands in features 510 and 511, rounded to bfloat16 and not scaled
     g = S.encode(P.compile_text("A0"), None, (0.8125, 0.3))
     assert g[510] == np.float32(0.8125) and g[511] == np.float32(0.30078125)
