@@ -278,17 +278,17 @@ def search_run(args, dev):
                        f"beam 64, 8,192 refinements per step, {steps} steps"}
     res = {}
     state = sur.params().copy()
-    for name, kw in (("exhaustive", {}),
-                     ("surrogate_ordered", {"online_epochs": 4}),
-                     ("surrogate_pruned", {"keep_fraction": 0.25, "online_epochs": 4, "warmup_steps": 1})):
+    variants = (("exhaustive", {}, 2048),
+                ("surrogate_ordered", {"online_epochs": 4}, 2048),
+                ("surrogate_pruned", {"keep_fraction": 0.25, "online_epochs": 4, "warmup_steps": 1}, 2048),
+                ("surrogate_adaptive", {"adaptive": True, "online_epochs": 4, "warmup_steps": 1}, 1024))
+    for name, kw, batch in variants:
         if "online_epochs" in kw:     # each surrogate run starts from the same pre-trained network
             kw = dict(kw, surrogate=Surrogate(params=state, device=str(dev), grid=threshold_grid(kb.prop_vals)))
         t0 = time.perf_counter()
-        beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=2048, **kw).run(start, steps)
+        beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=batch, **kw).run(start, steps)
         res[name] = (beam, logs, time.perf_counter() - t0)
-    eb, el, et = res["exhaustive"]
-    ob, ol, ot = res["surrogate_ordered"]
-    sb, sl, st = res["surrogate_pruned"]
+    eb = res["exhaustive"][0]
     target = eb[0].acc
 
     def first_reach(logs):
@@ -297,16 +297,16 @@ def search_run(args, dev):
                 if b >= target:
                     return t
         return None
-    te, to, ts = first_reach(el), first_reach(ol), first_reach(sl)
-    out.update({"exhaustive_s": et, "ordered_s": ot, "pruned_s": st, "best_acc": target,
-                "ordered_best_acc": ob[0].acc, "pruned_best_acc": sb[0].acc,
-                "best_found_per_s_exhaustive": 1.0 / te if te else 0.0,
-                "best_found_per_s_ordered": 1.0 / to if to else 0.0,
-                "best_found_per_s_surrogate": 1.0 / ts if ts else 0.0,
-                "evaluated_exhaustive": sum(l.evaluated for l in el), "evaluated_pruned": sum(l.evaluated for l in sl),
-                "same_final_beam_ordered": [e.prog.tobytes() for e in eb] == [e.prog.tobytes() for e in ob],
-                "same_final_beam": [e.prog.tobytes() for e in eb] == [e.prog.tobytes() for e in sb],
-                "best": P.to_text(P.from_postfix(eb[0].prog))})
+    out["best_acc"] = target
+    out["best"] = P.to_text(P.from_postfix(eb[0].prog))
+    for name, (beam, logs, secs) in res.items():
+        t = first_reach(logs)
+        out[name] = {"seconds": secs, "best_acc": beam[0].acc, "evaluated": sum(l.evaluated for l in logs),
+                     "candidates": sum(l.candidates for l in logs),
+                     "best_found_per_s": 1.0 / t if t else 0.0,
+                     "same_final_beam": [e.prog.tobytes() for e in beam] == [e.prog.tobytes() for e in eb],
+                     "seconds_by_part": {k: round(sum(l.times.get(k, 0.0) for l in logs), 4)
+                                         for k in ("refine", "surrogate", "eval", "learn")}}
     return out
 
 

@@ -14,7 +14,9 @@ scores; each candidate's encoding carries, as its prior inputs, the exact
 accuracy and F1 of the beam member it refines (candidate k refines member
 k mod |beam|, the generator's convention, unless `parent_of` says
 otherwise).  With pruning, only the predicted top fraction is evaluated, from
-the step after `warmup_steps` on.  With `online_epochs`, the surrogate is
+the step after `warmup_steps` on.  With `adaptive`, candidates are
+evaluated in predicted order one batch at a time, and a step ends at the
+first batch none of whose candidates would enter the beam.  With `online_epochs`, the surrogate is
 trained after every step on all candidates scored exactly so far (with
 their priors), so it learns the search's own distribution.  Without pruning
 the surrogate changes only the evaluation order, so the final beam is the
@@ -98,13 +100,14 @@ class StepLog:
     best_acc: float
     seconds: float
     events: List[Tuple[float, float]] = field(default_factory=list)   # (time since start, best acc so far)
+    times: dict = field(default_factory=dict)   # seconds in refine / surrogate / eval / learn
 
 
 class BeamSearch:
     def __init__(self, dkb, refine: Callable[[List[np.ndarray], int, int], List[np.ndarray]], width: int = 64,
                  per_step: int = 8192, batch: int = 2048, surrogate=None, keep_fraction: Optional[float] = None,
                  parent_of: Optional[Callable[[int, int], int]] = None, online_epochs: int = 0,
-                 warmup_steps: int = 0, online_lr: float = 1e-3):
+                 warmup_steps: int = 0, online_lr: float = 1e-3, adaptive: bool = False):
         self.dkb = dkb
         self.refine = refine
         self.width = width
@@ -116,6 +119,7 @@ class BeamSearch:
         self.online_epochs = online_epochs
         self.warmup_steps = warmup_steps
         self.online_lr = online_lr
+        self.adaptive = adaptive
         self._seen_X, self._seen_T = [], []
 
     def _score(self, progs: List[np.ndarray]):
@@ -138,6 +142,7 @@ class BeamSearch:
         best = beam[0].acc
         for s in range(1, steps + 1):
             ts = time.perf_counter()
+            tm = {}
             raw = self.refine([e.prog for e in beam], s, self.per_step)
             cands, parents, seen = [], [], {e.prog.tobytes() for e in beam}
             for k, p in enumerate(raw):
@@ -149,6 +154,8 @@ class BeamSearch:
                     parents.append(self.parent_of(k, len(beam)))
             order = list(range(len(cands)))
             X = None
+            t1 = time.perf_counter()
+            tm["refine"] = t1 - ts
             if self.surrogate is not None and cands:
                 flat = np.concatenate(cands).astype(np.uint64)
                 offs = np.zeros(len(cands) + 1, np.uint32)
@@ -159,18 +166,36 @@ class BeamSearch:
                 order = sorted(order, key=lambda i: (-Y[i, 0], -Y[i, 1], i))
                 if self.keep is not None and s > self.warmup_steps:
                     order = order[:max(1, int(round(self.keep * len(order))))]
+            t2 = time.perf_counter()
+            tm["surrogate"] = t2 - t1
             entries = [None] * len(cands)
             log = StepLog(s, len(cands), len(order), best, 0.0)
+            adaptive = self.adaptive and X is not None and s > self.warmup_steps
+            evaluated = []
             for b0 in range(0, len(order), self.batch):
                 ids = order[b0:b0 + self.batch]
+                if adaptive:   # the width-th best key before this batch
+                    pool = [e.key(i) for i, e in enumerate(beam)] + \
+                           [entries[i].key(len(beam) + i) for i in evaluated]
+                    thr = sorted(pool)[self.width - 1] if len(pool) >= self.width else None
                 c = self._score([cands[i] for i in ids])
                 a, f = scores(c)
                 for j, i in enumerate(ids):
                     entries[i] = Entry(cands[i], float(a[j]), float(f[j]), tuple(int(x) for x in c[j]))
+                evaluated += ids
                 best = max(best, float(a.max()) if len(a) else best)
                 log.events.append((time.perf_counter() - t0, best))
+                # predicted order: a batch none of whose candidates would enter the beam ends the step
+                if adaptive and thr is not None and not any(entries[i].key(len(beam) + i) < thr for i in ids):
+                    break
+            order = evaluated
+            log.evaluated = len(evaluated)
+            t3 = time.perf_counter()
+            tm["eval"] = t3 - t2
             if self.online_epochs and X is not None:
                 self._learn(X, order, entries)
+            tm["learn"] = time.perf_counter() - t3
+            log.times = tm
             beam = beam_update(beam, [e for e in entries if e is not None], self.width)
             log.best_acc = beam[0].acc
             log.seconds = time.perf_counter() - ts

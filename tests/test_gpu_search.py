@@ -57,8 +57,12 @@ def test_surrogate_order_without_pruning_keeps_the_beam(env):
                               keep_fraction=0.25, online_epochs=2, warmup_steps=1).run(start, 3)
     assert plog[0].evaluated == plog[0].candidates          # the warm-up step scores everything
     assert all(l.evaluated <= 0.26 * l.candidates + 1 for l in plog[1:])
+    adaptive, alog = BeamSearch(dkb, _refine_fn(ref), width=16, per_step=512, batch=64, surrogate=Surrogate(seed=3),
+                                adaptive=True, online_epochs=2, warmup_steps=1).run(start, 3)
+    assert alog[0].evaluated == alog[0].candidates
+    assert all(1 <= l.evaluated <= l.candidates for l in alog)
     # every reported score is exact
     okb = oracle.from_synth(kb)
-    for e in pruned:
+    for e in pruned + adaptive:
         c, _, _ = oracle.eval_batch(okb, e.prog, np.array([0, len(e.prog)]))
         assert tuple(int(x) for x in c[0]) == e.counts
