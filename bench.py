@@ -260,8 +260,7 @@ def search_run(args, dev):
     ref = Refiner(kb, 505)
 
     def refine(beam_progs, step, count):
-        return [np.array(n.postfix(), np.uint64) for n in ref.refine([P.from_postfix(p) for p in beam_progs], step,
-                                                                      count)]
+        return ref.refine_postfix(beam_progs, step, count)
     start = [np.array(n.postfix(), np.uint64) for n in ref.start()]
     steps = 20 if full else 5
     from paper_2412_00802_gb300.surrogate import threshold_grid

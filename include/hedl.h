@@ -328,6 +328,18 @@ int hedl_autotune_workspace_size(hedl_kb *kb, const uint64_t *progs, const uint3
 int hedl_autotune(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, void *ws,
                   size_t ws_bytes, const char *cache_path, hedl_stream s, hedl_tuning *chosen);
 
+/* ------------------------------------------------------------------ refinement search */
+
+/* Canonical form of H programs (HOST arrays as in hedl_plan_batch) for the
+ * beam search's duplicate removal (the paper has no search loop): every AND /
+ * OR gets its two operands in ascending order of their canonical instruction
+ * bytes (the little-endian instruction words compared byte by byte, a proper
+ * prefix first); everything else keeps its place.  out (HOST uint64[offs[H]],
+ * may alias progs) receives the programs at the same offsets.  Host-only.
+ * HEDL_ERR_BAD_PROGRAM names the first program that is not a valid postfix
+ * program. */
+int hedl_canonical_batch(const uint64_t *progs, const uint32_t *offs, uint32_t H, uint64_t *out);
+
 /* ------------------------------------------------------------------ surrogate */
 /* A learned surrogate that predicts a hypothesis' (accuracy, F1) from a
  * structural encoding, used only to order and prune the queue of exact

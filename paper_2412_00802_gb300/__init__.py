@@ -48,7 +48,7 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_autotune_workspace_size", "hedl_autotune", "hedl_mlp_param_count", "hedl_mlp_create",
            "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
            "hedl_mlp_gradients", "hedl_mlp_train_step", "hedl_scores_from_counts", "hedl_select_workspace_size",
-           "hedl_select_top", "hedl_last_error")
+           "hedl_select_top", "hedl_canonical_batch", "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -103,6 +103,7 @@ def library(path: Optional[str] = None):
             "hedl_examples_set": (I, [P, P, P, P]),
             "hedl_examples_counts": (I, [P, ctypes.POINTER(U32), ctypes.POINTER(U32)]),
             "hedl_validate": (I, [P, P, U32]),
+            "hedl_canonical_batch": (I, [P, P, U32, P]),
             "hedl_plan_batch": (I, [P, P, P, U32, ctypes.c_uint, ctypes.POINTER(P)]),
             "hedl_plan_info_get": (I, [P, ctypes.POINTER(hedl_plan_info)]),
             "hedl_plan_free": (None, [P]),
@@ -253,6 +254,15 @@ def hedl_examples_counts(kb: KBHandle) -> Tuple[int, int]:
 def hedl_validate(kb: KBHandle, prog) -> None:
     p = _host_u64(prog)
     _check(library().hedl_validate(kb.ptr, p.ctypes.data if p.size else None, p.size))
+
+
+def hedl_canonical_batch(progs, offs) -> np.ndarray:
+    """Canonical forms (AND / OR operands in ascending byte order) of host programs, same offsets."""
+    p, o = _host_u64(progs), _host_u32(offs)
+    out = np.empty_like(p)
+    _check(library().hedl_canonical_batch(p.ctypes.data if p.size else None, o.ctypes.data, o.size - 1,
+                                          out.ctypes.data if out.size else None))
+    return out
 
 
 class Plan:

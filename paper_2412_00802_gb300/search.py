@@ -30,30 +30,13 @@ from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-_ARITY = {1: 0, 2: 0, 3: 0, 4: 1, 5: 2, 6: 2, 7: 1, 8: 1, 9: 1, 10: 1, 11: 1, 12: 0, 13: 0, 14: 0}
-_AND, _OR = 5, 6
+from . import hedl_canonical_batch
 
 
 def canonical(prog: Sequence[int]) -> np.ndarray:
-    """Canonical postfix: every AND / OR has its operands in ascending byte order."""
-    stack: List[np.ndarray] = []
-    for w in prog:
-        w = int(w)
-        op = w & 0xFF
-        a = _ARITY[op]
-        if a == 0:
-            stack.append(np.array([w], np.uint64))
-        elif a == 1:
-            x = stack.pop()
-            stack.append(np.concatenate([x, np.array([w], np.uint64)]))
-        else:
-            y = stack.pop()
-            x = stack.pop()
-            if op in (_AND, _OR) and y.tobytes() < x.tobytes():
-                x, y = y, x
-            stack.append(np.concatenate([x, y, np.array([w], np.uint64)]))
-    assert len(stack) == 1
-    return stack[0]
+    """Canonical postfix (hedl_canonical_batch): every AND / OR has its operands in ascending byte order."""
+    p = np.ascontiguousarray(prog, np.uint64)
+    return hedl_canonical_batch(p, np.array([0, p.size], np.uint32))
 
 
 @dataclass
@@ -144,9 +127,16 @@ class BeamSearch:
             ts = time.perf_counter()
             tm = {}
             raw = self.refine([e.prog for e in beam], s, self.per_step)
+            if isinstance(raw, tuple):       # (flat instructions, offsets)
+                rflat, roffs = np.asarray(raw[0], np.uint64), np.asarray(raw[1], np.int64)
+            else:
+                rflat = np.concatenate(raw).astype(np.uint64) if len(raw) else np.zeros(0, np.uint64)
+                roffs = np.zeros(len(raw) + 1, np.int64)
+                np.cumsum([len(p) for p in raw], out=roffs[1:])
+            canon = hedl_canonical_batch(rflat, roffs.astype(np.uint32))
             cands, parents, seen = [], [], {e.prog.tobytes() for e in beam}
-            for k, p in enumerate(raw):
-                cp = canonical(p)
+            for k in range(len(roffs) - 1):
+                cp = canon[roffs[k]:roffs[k + 1]]
                 b = cp.tobytes()
                 if b not in seen:
                     seen.add(b)

@@ -211,3 +211,141 @@ void fastgen_bernoulli(uint64_t seed, uint64_t stream, uint64_t n, double p_out,
     free(th);
     free(jobs);
 }
+
+/* ------------------------------------------------------------------ refinements
+ * The refinement generator of synth/refine.py (Refiner.refine) on postfix
+ * programs, draw for draw: candidate k refines beam member k mod n_beam with
+ * the sequential stream (seed, S_REFINE + (step << 40) + (member << 24) + k).
+ * Op codes and the instruction layout are those of synth/programs.py. */
+enum { R_ATOM = 1, R_AND = 5, R_OR = 6, R_EXISTS = 7, R_FORALL = 8, R_ATLEAST = 9, R_DGE = 12, R_DLE = 13 };
+#define S_REFINE (11ull << 16)
+
+typedef struct {
+    uint64_t key, k;
+} seq_rng;
+
+static inline uint64_t seq_next(seq_rng *r) {
+    r->k += 1;
+    return mix64(r->key + r->k * GOLDEN);
+}
+static inline double seq_random(seq_rng *r) { return (double)(seq_next(r) >> 11) * (1.0 / 9007199254740992.0); }
+static inline int64_t seq_randint(seq_rng *r, int64_t lo, int64_t hi) {   /* inclusive */
+    uint64_t span = (uint64_t)(hi - lo + 1);
+    return lo + (int64_t)(((seq_next(r) >> 32) * span) >> 32);
+}
+static inline uint64_t mk(uint32_t op, uint32_t flags, uint32_t a, uint32_t b) {
+    return (uint64_t)(op & 0xFF) | ((uint64_t)(flags & 0xFF) << 8) | ((uint64_t)(a & 0xFFFF) << 16) |
+           ((uint64_t)b << 32);
+}
+static inline uint32_t f32bits(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    return u;
+}
+static inline float bitsf32(uint32_t u) {
+    float x;
+    memcpy(&x, &u, 4);
+    return x;
+}
+
+/* a simple operand: atom (1/2), grid data restriction (3/10) or (some r A) (1/5) */
+static int64_t simple(seq_rng *r, int64_t nc, int64_t nr, int64_t np_, const float *grid, const int64_t *goff,
+                      uint64_t *out) {
+    double u = seq_random(r);
+    if (u < 0.5 || (np_ == 0 && nr == 0)) {
+        out[0] = mk(R_ATOM, 0, (uint32_t)seq_randint(r, 0, nc - 1), 0);
+        return 1;
+    }
+    if ((u < 0.8 && np_) || !nr) {
+        int64_t p = seq_randint(r, 0, np_ - 1);
+        int64_t gl = goff[p + 1] - goff[p];
+        float t = grid[goff[p] + seq_randint(r, 0, gl - 1)];
+        uint32_t op = seq_random(r) < 0.5 ? R_DGE : R_DLE;
+        out[0] = mk(op, 0, (uint32_t)p, f32bits(t));
+        return 1;
+    }
+    int64_t role = seq_randint(r, 0, nr - 1);
+    uint32_t inv = seq_random(r) < 0.5 ? 1u : 0u;
+    out[0] = mk(R_ATOM, 0, (uint32_t)seq_randint(r, 0, nc - 1), 0);
+    out[1] = mk(R_EXISTS, inv, (uint32_t)role, 0);
+    return 2;
+}
+
+/* Writes count candidates into out (capacity cap instructions) and their
+ * offsets into out_offs[count+1]; returns 0, or -1 if cap is too small. */
+int fastgen_refine(uint64_t seed, uint64_t step, const uint64_t *beam, const int64_t *boffs, int64_t n_beam,
+                   int64_t count, int64_t nc, int64_t nr, int64_t np_, const float *grid, const int64_t *goff,
+                   uint64_t *out, int64_t cap, int64_t *out_offs) {
+    int64_t o = 0;
+    out_offs[0] = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t m = k % n_beam;
+        const uint64_t *base = beam + boffs[m];
+        const int64_t bl = boffs[m + 1] - boffs[m];
+        if (o + bl + 3 > cap) return -1;
+        seq_rng r = {stream_key(seed, S_REFINE + (step << 40) + ((uint64_t)m << 24) + (uint64_t)k), 0};
+        uint64_t *dst = out + o;
+        memcpy(dst, base, sizeof(uint64_t) * (size_t)bl);
+        int64_t len = bl;
+        int64_t op = seq_randint(&r, 0, 3);
+        int done = 0;
+        if (op == 3) {
+            int64_t nd = 0;
+            for (int64_t i = 0; i < bl; ++i) {
+                uint32_t c = (uint32_t)(base[i] & 0xFF);
+                if (c == R_DGE || c == R_DLE) ++nd;
+            }
+            if (nd) {
+                int64_t pick = seq_randint(&r, 0, nd - 1), at = -1;
+                for (int64_t i = 0, seen = 0; i < bl; ++i) {
+                    uint32_t c = (uint32_t)(base[i] & 0xFF);
+                    if (c == R_DGE || c == R_DLE) {
+                        if (seen == pick) {
+                            at = i;
+                            break;
+                        }
+                        ++seen;
+                    }
+                }
+                const uint32_t c = (uint32_t)(base[at] & 0xFF), p = (uint32_t)((base[at] >> 16) & 0xFFFF);
+                const float t = bitsf32((uint32_t)(base[at] >> 32));
+                const float *g = grid + goff[p];
+                const int64_t gl = goff[p + 1] - goff[p];
+                int64_t i = 0;   /* first index with g[i] >= t (numpy searchsorted, NaN sorts last) */
+                if (t != t) i = gl;
+                else
+                    while (i < gl && g[i] < t) ++i;
+                int64_t j = c == R_DGE ? ((i < gl && g[i] == t) ? i + 1 : i) : i - 1;
+                if (j >= 0 && j < gl) {
+                    dst[at] = mk(c, 0, p, f32bits(g[j]));
+                    done = 1;
+                }
+            }
+            if (!done) op = 0;
+        }
+        if (!done) {
+            if (op == 0 || op == 1) {
+                len += simple(&r, nc, nr, np_, grid, goff, dst + len);
+                dst[len++] = mk(op == 0 ? R_AND : R_OR, 0, 0, 0);
+            } else {
+                int64_t w = seq_randint(&r, 0, 2);
+                int64_t role = nr ? seq_randint(&r, 0, nr - 1) : 0;
+                uint32_t inv = seq_random(&r) < 0.5 ? 1u : 0u;
+                if (w == 0 || !nr) {
+                    if (nr) dst[len++] = mk(R_EXISTS, inv, (uint32_t)role, 0);
+                    else {
+                        len += simple(&r, nc, nr, np_, grid, goff, dst + len);
+                        dst[len++] = mk(R_AND, 0, 0, 0);
+                    }
+                } else if (w == 1) {
+                    dst[len++] = mk(R_FORALL, inv, (uint32_t)role, 0);
+                } else {
+                    dst[len++] = mk(R_ATLEAST, inv, (uint32_t)role, (uint32_t)seq_randint(&r, 1, 4));
+                }
+            }
+        }
+        o += len;
+        out_offs[k + 1] = o;
+    }
+    return 0;
+}

@@ -57,6 +57,8 @@ def _fast():
             L.fastgen_transpose.restype = None
             L.fastgen_bernoulli.argtypes = [U64, U64, U64, ctypes.c_double, ctypes.c_double, P, P, I32]
             L.fastgen_bernoulli.restype = None
+            L.fastgen_refine.argtypes = [U64, U64, P, P, I64, I64, I64, I64, I64, P, P, P, I64, P]
+            L.fastgen_refine.restype = ctypes.c_int
             _FAST = L
     return _FAST
 

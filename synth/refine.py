@@ -13,8 +13,10 @@ operator drawn uniformly from
 X is a simple concept: an atom (prob. 1/2), a data restriction p >= t or
 p <= t with t on the grid (prob. 3/10), or (some r A) (prob. 1/5).
 Both the exhaustive and the surrogate-ordered search call the same
-generator, so they see the identical candidate list.  This module draws
-candidates only; it evaluates nothing.
+generator, so they see the identical candidate list.  ``refine_postfix`` is
+the same generator on postfix arrays, run by the C helper in fastgen.c draw
+for draw (a test checks the two agree).  This module draws candidates only;
+it evaluates nothing.
 """
 from __future__ import annotations
 
@@ -41,6 +43,9 @@ class Refiner:
             v = v[~np.isnan(v)]
             q = np.quantile(v, np.linspace(0.0, 1.0, GRID)).astype(np.float32) if v.size else np.zeros(1, np.float32)
             self.grid.append(np.unique(q))
+        self._gflat = np.concatenate(self.grid).astype(np.float32) if self.grid else np.zeros(1, np.float32)
+        self._goffs = np.zeros(len(self.grid) + 1, np.int64)
+        np.cumsum([len(g) for g in self.grid], out=self._goffs[1:])
 
     def _rng(self, step: int, member: int, k: int) -> rng.Rng:
         return rng.Rng(self.seed, S_REFINE + (step << 40) + (member << 24) + k)
@@ -109,6 +114,24 @@ class Refiner:
 
     def refine(self, beam: Sequence[Node], step: int, count: int) -> List[Node]:
         return [self.refine_one(beam[k % len(beam)], step, k % len(beam), k) for k in range(count)]
+
+    def refine_postfix(self, beam: Sequence[np.ndarray], step: int, count: int):
+        """``refine`` on postfix programs, in C: (flat uint64 instructions, offsets int64[count+1])."""
+        from .kb import _fast
+        bflat = np.ascontiguousarray(np.concatenate([np.asarray(b, np.uint64) for b in beam]), np.uint64)
+        boffs = np.zeros(len(beam) + 1, np.int64)
+        np.cumsum([len(b) for b in beam], out=boffs[1:])
+        lens = boffs[1:] - boffs[:-1]
+        M = len(beam)      # candidate k copies member k mod M and adds at most 3 instructions
+        cap = int((count // M) * lens.sum() + lens[: count % M].sum() + 3 * count)
+        out = np.zeros(max(cap, 1), np.uint64)
+        offs = np.zeros(count + 1, np.int64)
+        rc = _fast().fastgen_refine(self.seed, step, bflat.ctypes.data, boffs.ctypes.data, len(beam), count,
+                                    self.n_concepts, self.n_roles, self.n_props, self._gflat.ctypes.data,
+                                    self._goffs.ctypes.data, out.ctypes.data, out.size, offs.ctypes.data)
+        if rc:
+            raise RuntimeError("refinement output buffer too small")
+        return out[: offs[-1]], offs
 
     def start(self) -> List[Node]:
         """Initial beam: the top concept."""

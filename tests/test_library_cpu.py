@@ -10,6 +10,7 @@ import pytest
 import oracle
 import paper_2412_00802_gb300 as H
 from synth import hyps, kb as K, programs as P
+from synth.rng import Rng
 from tests import oracle_pins as pins
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -183,3 +184,17 @@ def test_narrow_tiles_for_single_hypotheses():
     paired = H.hedl_plan_info_get(H.hedl_plan_batch(hk, *P.pack_batch([P.compile_text("(some r1 A2)"),
                                                                          P.compile_text("(all r1 A3)")])))
     assert paired["n_role_groups"] == 1 and paired["warp_words"] == 32
+
+
+def test_canonical_batch_agrees_with_the_search_oracle(c1):
+    """The library's canonical form equals the independently written one of the search oracle."""
+    from oracle import search as OS
+    r = Rng(17, 4)
+    progs = [np.array(pins.random_program(r, c1, r.randint(1, 7)).postfix(), np.uint64) for _ in range(400)]
+    progs += [P.compile_text("(and (or A2 A1) (or A1 A2))"), P.compile_text("(and A1 A1)"), P.compile_text("TOP")]
+    flat, offs = P.pack_batch(progs)
+    got = H.hedl_canonical_batch(flat, offs)
+    for i, p in enumerate(progs):
+        assert got[offs[i]:offs[i + 1]].tobytes() == OS.canonical(p), i
+    with pytest.raises(H.HedlError):
+        H.hedl_canonical_batch(np.array([P.insn(P.AND)], np.uint64), np.array([0, 1], np.uint32))

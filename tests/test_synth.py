@@ -122,3 +122,20 @@ def test_c_helpers_match_numpy(cfg):
         assert np.array_equal(a.col[r], b.col[r])
         assert np.array_equal(a.inv_row_ptr[r], b.inv_row_ptr[r])
         assert np.array_equal(a.inv_col[r], b.inv_col[r])
+
+
+def test_refine_postfix_matches_the_python_generator():
+    """The C refinement generator draws exactly the Python generator's candidates."""
+    from synth.refine import Refiner
+    for cfg in (K.CONFIGS["c5"].scaled(3000, n_roles=6, n_props=4, n_concepts=20),
+                K.CONFIGS["c5"].scaled(2000, n_roles=0, n_props=3, n_concepts=9),
+                K.CONFIGS["c5"].scaled(2000, n_roles=4, n_props=0, n_concepts=7)):
+        kb = K.generate(cfg)
+        ref = Refiner(kb, 505)
+        beam = [P.Node(P.TOP)]
+        for step in range(1, 5):
+            want = [np.array(n.postfix(), np.uint64) for n in ref.refine(beam, step, 700)]
+            flat, offs = ref.refine_postfix([np.array(b.postfix(), np.uint64) for b in beam], step, 700)
+            got = [flat[offs[i]:offs[i + 1]] for i in range(700)]
+            assert all(np.array_equal(a, b) for a, b in zip(want, got)), step
+            beam = [P.from_postfix(w) for w in want[::23]]      # a varied beam for the next step
