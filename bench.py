@@ -254,15 +254,17 @@ def search_run(args, dev):
     from synth import hyps, kb as K, programs as P
     from synth.refine import Refiner
     full = args.search_full
-    cfg = K.CONFIGS["c5"] if full else K.CONFIGS["c5"].scaled(500_000, n_roles=16, n_props=8, n_concepts=100)
+    cfg = K.CONFIGS["c5"] if full else K.CONFIGS["c5"].scaled(1_000_000)
+    t0 = time.perf_counter()
     kb = K.generate(cfg)
+    gen_s = time.perf_counter() - t0
     dkb = H.DeviceKB.from_synth(kb, device=str(dev))
     ref = Refiner(kb, 505)
 
     def refine(beam_progs, step, count):
         return ref.refine_postfix(beam_progs, step, count)
     start = [np.array(n.postfix(), np.uint64) for n in ref.start()]
-    steps = 20 if full else 5
+    steps = 20 if full else 10
     from paper_2412_00802_gb300.surrogate import threshold_grid
     sur = Surrogate(seed=5, device=str(dev), grid=threshold_grid(kb.prop_vals))
     tg = hyps.TreeGen(kb, 506, share=0.3)
@@ -274,13 +276,14 @@ def search_run(args, dev):
         Ts.append(T)
     sur.train(torch.cat(Xs), torch.cat(Ts), epochs=20, batch=4096, lr=2e-3)
     out = {"workload": f"planted KB with the search workload's distributions, N={cfg.n:,}, {kb.n_roles} roles; "
-                       f"beam 64, 8,192 refinements per step, {steps} steps"}
+                       f"beam 64, 8,192 refinements per step, {steps} steps", "kb_gen_s": gen_s}
     res = {}
     state = sur.params().copy()
+    online = {"online_epochs": 2, "online_window": 16384}
     variants = (("exhaustive", {}, 2048),
-                ("surrogate_ordered", {"online_epochs": 4}, 2048),
-                ("surrogate_pruned", {"keep_fraction": 0.25, "online_epochs": 4, "warmup_steps": 1}, 2048),
-                ("surrogate_adaptive", {"adaptive": True, "online_epochs": 4, "warmup_steps": 1}, 1024))
+                ("surrogate_ordered", dict(online), 2048),
+                ("surrogate_pruned", dict(online, keep_fraction=0.25, warmup_steps=1), 2048),
+                ("surrogate_adaptive", dict(online, adaptive=True, warmup_steps=1), 1024))
     for name, kw, batch in variants:
         if "online_epochs" in kw:     # each surrogate run starts from the same pre-trained network
             kw = dict(kw, surrogate=Surrogate(params=state, device=str(dev), grid=threshold_grid(kb.prop_vals)))

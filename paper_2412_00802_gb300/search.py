@@ -17,8 +17,8 @@ otherwise).  With pruning, only the predicted top fraction is evaluated, from
 the step after `warmup_steps` on.  With `adaptive`, candidates are
 evaluated in predicted order one batch at a time, and a step ends at the
 first batch none of whose candidates would enter the beam.  With `online_epochs`, the surrogate is
-trained after every step on all candidates scored exactly so far (with
-their priors), so it learns the search's own distribution.  Without pruning
+trained after every step on the latest `online_window` candidates scored
+exactly (with their priors), so it learns the search's own distribution.  Without pruning
 the surrogate changes only the evaluation order, so the final beam is the
 exhaustive search's.  Scores always come from exact evaluation.
 """
@@ -90,7 +90,8 @@ class BeamSearch:
     def __init__(self, dkb, refine: Callable[[List[np.ndarray], int, int], List[np.ndarray]], width: int = 64,
                  per_step: int = 8192, batch: int = 2048, surrogate=None, keep_fraction: Optional[float] = None,
                  parent_of: Optional[Callable[[int, int], int]] = None, online_epochs: int = 0,
-                 warmup_steps: int = 0, online_lr: float = 1e-3, adaptive: bool = False):
+                 warmup_steps: int = 0, online_lr: float = 1e-3, adaptive: bool = False,
+                 online_window: int = 1 << 16):
         self.dkb = dkb
         self.refine = refine
         self.width = width
@@ -103,6 +104,7 @@ class BeamSearch:
         self.warmup_steps = warmup_steps
         self.online_lr = online_lr
         self.adaptive = adaptive
+        self.online_window = online_window
         self._seen_X, self._seen_T = [], []
 
     def _score(self, progs: List[np.ndarray]):
@@ -193,13 +195,16 @@ class BeamSearch:
         return beam, logs
 
     def _learn(self, X, evaluated: List[int], entries: List[Entry]):
-        """Train the surrogate on every candidate scored exactly so far."""
+        """Train the surrogate on the latest `online_window` candidates scored exactly."""
         torch = self.surrogate.torch
         idx = torch.tensor(evaluated, dtype=torch.int64, device=X.device)
         self._seen_X.append(X.index_select(0, idx))
         self._seen_T.append(torch.tensor([[entries[i].acc, entries[i].f1] for i in evaluated], dtype=torch.float32,
                                          device=X.device))
         Xa, Ta = torch.cat(self._seen_X), torch.cat(self._seen_T)
+        if Xa.shape[0] > self.online_window:
+            Xa, Ta = Xa[-self.online_window:].contiguous(), Ta[-self.online_window:].contiguous()
+            self._seen_X, self._seen_T = [Xa], [Ta]
         batch = min(1024, Xa.shape[0])
         self.surrogate.train(Xa, Ta, epochs=self.online_epochs, batch=batch, lr=self.online_lr,
                              seed=len(self._seen_X))
