@@ -190,7 +190,7 @@ def surrogate_round(args, dev):
     gen_s = time.perf_counter() - t0
     dkb = H.DeviceKB.from_synth(kb, device=str(dev))
     tg = hyps.TreeGen(kb, 404, share=0.3)
-    n_train = 1_000_000 if full else 65_536
+    n_train = args.surrogate_train or (1_000_000 if full else 65_536)
     B = 4096
     t0 = time.perf_counter()
     Xs, Ts = [], []
@@ -602,6 +602,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-ranked round")
     ap.add_argument("--no-search", action="store_true", help="skip the beam-search comparison")
+    ap.add_argument("--surrogate-train", type=int, default=0,
+                    help="training hypotheses of the surrogate round (default 65,536; 1,000,000 with --surrogate-full)")
     ap.add_argument("--surrogate-full", action="store_true",
                     help="surrogate round at full size (10M individuals, 1M training hypotheses)")
     ap.add_argument("--latency", action="store_true",
