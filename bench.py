@@ -205,7 +205,7 @@ def surrogate_round(args, dev):
     torch.cuda.synchronize()
     score_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    losses = s.train(X, T, epochs=20, batch=B, lr=2e-3)
+    losses = s.train(X, T, epochs=40, batch=B, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     cand = hyps.batch_hyps(kb, 405, 0, 65_536, gen=tg)
@@ -274,11 +274,11 @@ def search_run(args, dev):
         _, T = exact_scores(dkb, flat, offs)
         Xs.append(sur.encode(flat, offs))
         Ts.append(T)
-    sur.train(torch.cat(Xs), torch.cat(Ts), epochs=20, batch=4096, lr=2e-3)
+    sur.train(torch.cat(Xs), torch.cat(Ts), epochs=40, batch=4096, lr=2e-3)
     out = {"workload": f"planted KB with the search workload's distributions, N={cfg.n:,}, {kb.n_roles} roles; "
                        f"beam 64, 8,192 refinements per step, {steps} steps", "kb_gen_s": gen_s}
     res = {}
-    state = sur.params().copy()
+    state, tmap = sur.params().copy(), sur.target_map()
     online = {"online_epochs": 2, "online_window": 16384}
     variants = (("exhaustive", {}, 2048),
                 ("surrogate_ordered", dict(online), 2048),
@@ -286,7 +286,9 @@ def search_run(args, dev):
                 ("surrogate_adaptive", dict(online, adaptive=True, warmup_steps=1), 1024))
     for name, kw, batch in variants:
         if "online_epochs" in kw:     # each surrogate run starts from the same pre-trained network
-            kw = dict(kw, surrogate=Surrogate(params=state, device=str(dev), grid=threshold_grid(kb.prop_vals)))
+            net = Surrogate(params=state, device=str(dev), grid=threshold_grid(kb.prop_vals))
+            net.set_target_map(tmap)
+            kw = dict(kw, surrogate=net)
         t0 = time.perf_counter()
         beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=batch, **kw).run(start, steps)
         res[name] = (beam, logs, time.perf_counter() - t0)

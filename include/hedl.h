@@ -385,13 +385,18 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
                 const float *prior, uint16_t *X, hedl_stream s);
 
-/* Y (DEVICE float [B][2]) = the network applied to X (DEVICE bf16 [B][512]). */
+/* Y (DEVICE float [B][2]) = the network applied to X (DEVICE bf16 [B][512]),
+ * its raw output u mapped to the target scale: Y = u * scale + mean (the
+ * target map; identity until one is set). */
 int hedl_mlp_forward(hedl_mlp *m, const uint16_t *X, uint32_t B, float *Y, void *ws, size_t ws_bytes,
                      hedl_stream s);
 
-/* Gradients of the loss mean_b sum_j (Y_bj - T_bj)^2 for targets T (DEVICE
- * float [B][2]) into the network's gradient buffer; *loss (DEVICE float, may
- * be NULL) receives the loss. */
+/* Gradients of the loss mean_b w_b sum_j (u_bj - t_bj)^2, where u is the raw
+ * output, t = (T - mean) / scale the mapped targets T (DEVICE float [B][2])
+ * and w_b = 1 + tail * max(0, t_b0) (the upper tail of the first target
+ * weighs more), into the network's gradient buffer; *loss (DEVICE float, may
+ * be NULL) receives the loss.  With the identity map this is the plain mean
+ * squared error. */
 int hedl_mlp_gradients(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t B, float *loss, void *ws,
                        size_t ws_bytes, hedl_stream s);
 
@@ -399,6 +404,15 @@ int hedl_mlp_gradients(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t 
  * learning rate lr) on the master weights, refreshing their BF16 copies. */
 int hedl_mlp_train_step(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t B, float lr, float *loss,
                         void *ws, size_t ws_bytes, hedl_stream s);
+
+/* Target map (mean0, mean1, scale0, scale1, tail weight) of a network.
+ * fit: means and population standard deviations (1 where below 1e-6) of the
+ * columns of T (DEVICE float [B][2], B >= 1), and tail_weight >= 0;
+ * asynchronous.  set / get: HOST float[5]; scales must be > 0; SYNCHRONIZE.
+ * The map standardises the training targets and maps predictions back. */
+int hedl_mlp_fit_target_map(hedl_mlp *m, const float *T, uint32_t B, float tail_weight, hedl_stream s);
+int hedl_mlp_set_target_map(hedl_mlp *m, const float *map);
+int hedl_mlp_get_target_map(const hedl_mlp *m, float *map);
 
 /* Exact scores from coverage counts (DEVICE uint32 [H][4] TP, FP, FN, TN) into
  * DEVICE float [H][2]: accuracy (TP+TN)/(TP+FP+FN+TN) and F1 2TP/(2TP+FP+FN)

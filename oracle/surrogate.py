@@ -8,7 +8,8 @@ library):
 * ``encode``: the 512-dimensional structural encoding of a postfix program,
   computed by direct counting over the program;
 * ``forward`` / ``backward``: the MLP 512 -> 512 -> 512 -> 2 with ReLU,
-  mean-squared-error loss, in float64; ``bf16`` rounding (round to nearest,
+  mean-squared-error loss (optionally on targets standardised by a target
+  map, rows of the upper tail weighted more), in float64; ``bf16`` rounding (round to nearest,
   ties to even, from the float32 bit pattern) is applied where the GPU stores
   bfloat16 (inputs, weights, hidden activations, their gradients);
 * ``adam``: one Adam step (Kingma and Ba, 2015) on float32 master weights;
@@ -174,11 +175,13 @@ def init_params(seed: int) -> Dict[str, np.ndarray]:
     return p
 
 
-def forward(p: Dict[str, np.ndarray], X: np.ndarray, rounding: bool = True) -> Tuple[np.ndarray, dict]:
+def forward(p: Dict[str, np.ndarray], X: np.ndarray, rounding: bool = True, tmap=None) -> Tuple[np.ndarray, dict]:
     """Y = (relu(relu(X W1^T + b1) W2^T + b2)) W3^T + b3, float64 accumulation.
 
     With rounding, X, the weights and the hidden activations are rounded to
-    bfloat16 where the GPU stores them."""
+    bfloat16 where the GPU stores them.  With a target map tmap = (mean0,
+    mean1, scale0, scale1, tail), the raw output u is mapped back to the
+    target scale, Y = u * scale + mean (the raw u is in the cache)."""
     r = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
     x = np.asarray(r(X), np.float64)
     w1, w2, w3 = (np.asarray(r(p[k]), np.float64) for k in ("w1", "w2", "w3"))
@@ -186,8 +189,9 @@ def forward(p: Dict[str, np.ndarray], X: np.ndarray, rounding: bool = True) -> T
     h1 = np.asarray(r(h1), np.float64)
     h2 = np.maximum(h1 @ w2.T + p["b2"], 0.0)
     h2 = np.asarray(r(h2), np.float64)
-    y = h2 @ w3.T + p["b3"]
-    return y, {"x": x, "h1": h1, "h2": h2, "w1": w1, "w2": w2, "w3": w3}
+    u = h2 @ w3.T + p["b3"]
+    y = u if tmap is None else u * np.asarray(tmap[2:4], np.float64) + np.asarray(tmap[0:2], np.float64)
+    return y, {"x": x, "h1": h1, "h2": h2, "w1": w1, "w2": w2, "w3": w3, "u": u}
 
 
 def loss(y: np.ndarray, t: np.ndarray) -> float:
@@ -195,15 +199,40 @@ def loss(y: np.ndarray, t: np.ndarray) -> float:
     return float(((y - t) ** 2).sum() / y.shape[0])
 
 
-def backward(p: Dict[str, np.ndarray], X: np.ndarray, T: np.ndarray, rounding: bool = True) -> Tuple[float, dict]:
-    """Gradients of ``loss`` by the chain rule (relu'(0) = 0), float64.
+def mapped_targets(T: np.ndarray, tmap) -> Tuple[np.ndarray, np.ndarray]:
+    """(t, w): targets standardised by the map, t = (T - mean) / scale, and row
+    weights w = 1 + tail * max(0, t[:, 0])."""
+    T = np.asarray(T, np.float64)
+    if tmap is None:
+        return T, np.ones(T.shape[0])
+    t = (T - np.asarray(tmap[0:2], np.float64)) / np.asarray(tmap[2:4], np.float64)
+    return t, 1.0 + float(tmap[4]) * np.maximum(t[:, 0], 0.0)
+
+
+def fit_target_map(T: np.ndarray, tail: float) -> np.ndarray:
+    """Column means, population standard deviations (1 where below 1e-6), tail weight."""
+    T = np.asarray(T, np.float64)
+    m = T.mean(0)
+    sd = np.sqrt(((T - m) ** 2).mean(0))
+    sd = np.where(sd < 1e-6, 1.0, sd)
+    return np.array([m[0], m[1], sd[0], sd[1], tail], np.float64)
+
+
+def backward(p: Dict[str, np.ndarray], X: np.ndarray, T: np.ndarray, rounding: bool = True,
+             tmap=None) -> Tuple[float, dict]:
+    """Gradients of the (weighted) loss by the chain rule (relu'(0) = 0), float64:
+    mean_b w_b sum_j (u_bj - t_bj)^2 on the raw output u and the mapped targets
+    (``mapped_targets``); without a map, the plain ``loss`` of Y against T.
 
     With rounding, the gradients flowing into the hidden layers are rounded to
     bfloat16 where the GPU stores them."""
     r = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
-    y, c = forward(p, X, rounding)
-    B = y.shape[0]
-    dy = 2.0 * (y - T) / B
+    _, c = forward(p, X, rounding)
+    u = c["u"]
+    B = u.shape[0]
+    t, w = mapped_targets(T, tmap)
+    dy = 2.0 * (u - t) * w[:, None] / B
+    lval = float((w[:, None] * (u - t) ** 2).sum() / B)
     g = {"w3": dy.T @ c["h2"], "b3": dy.sum(0)}
     dh2 = (dy @ c["w3"]) * (c["h2"] > 0)
     dh2 = np.asarray(r(dh2), np.float64)
@@ -213,7 +242,7 @@ def backward(p: Dict[str, np.ndarray], X: np.ndarray, T: np.ndarray, rounding: b
     dh1 = np.asarray(r(dh1), np.float64)
     g["w1"] = dh1.T @ c["x"]
     g["b1"] = dh1.sum(0)
-    return loss(y, T), g
+    return lval, g
 
 
 def adam(p: Dict[str, np.ndarray], g: Dict[str, np.ndarray], m: dict, v: dict, step: int, lr: float,

@@ -48,7 +48,8 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_autotune_workspace_size", "hedl_autotune", "hedl_mlp_param_count", "hedl_mlp_create",
            "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
            "hedl_mlp_gradients", "hedl_mlp_train_step", "hedl_scores_from_counts", "hedl_select_workspace_size",
-           "hedl_select_top", "hedl_canonical_batch", "hedl_last_error")
+           "hedl_select_top", "hedl_canonical_batch", "hedl_mlp_fit_target_map", "hedl_mlp_set_target_map",
+           "hedl_mlp_get_target_map", "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -128,6 +129,9 @@ def library(path: Optional[str] = None):
             "hedl_mlp_gradients": (I, [P, P, P, U32, P, P, ctypes.c_size_t, P]),
             "hedl_mlp_train_step": (I, [P, P, P, U32, ctypes.c_float, P, P, ctypes.c_size_t, P]),
             "hedl_scores_from_counts": (I, [P, U32, P, P]),
+            "hedl_mlp_fit_target_map": (I, [P, P, U32, ctypes.c_float, P]),
+            "hedl_mlp_set_target_map": (I, [P, P]),
+            "hedl_mlp_get_target_map": (I, [P, P]),
             "hedl_select_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_select_top": (I, [P, U32, U32, P, P, ctypes.c_size_t, P]),
             "hedl_last_error": (ctypes.c_char_p, []),
@@ -441,6 +445,21 @@ def hedl_mlp_gradients(m: MLPHandle, X, T, ws, loss=None, stream=None):
 def hedl_mlp_train_step(m: MLPHandle, X, T, lr: float, ws, loss=None, stream=None):
     _check(library().hedl_mlp_train_step(m.ptr, _dptr(X), _dptr(T), X.shape[0], lr, _dptr(loss), _dptr(ws),
                                          ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def hedl_mlp_fit_target_map(m: MLPHandle, T, tail_weight: float, stream=None):
+    _check(library().hedl_mlp_fit_target_map(m.ptr, _dptr(T), T.shape[0], tail_weight, _stream(stream)))
+
+
+def hedl_mlp_set_target_map(m: MLPHandle, tmap):
+    a = np.ascontiguousarray(tmap, np.float32)
+    _check(library().hedl_mlp_set_target_map(m.ptr, a.ctypes.data))
+
+
+def hedl_mlp_get_target_map(m: MLPHandle) -> np.ndarray:
+    a = np.zeros(5, np.float32)
+    _check(library().hedl_mlp_get_target_map(m.ptr, a.ctypes.data))
+    return a
 
 
 def hedl_scores_from_counts(counts, scores, stream=None):

@@ -285,7 +285,10 @@ int gemm(const GemmArgs &a0, bool a_km, bool b_kn, int splits, cudaStream_t s) {
 
 // ------------------------------------------------------------------ output layer (N = 2)
 // Y[b][j] = sum_i H2[b][i] W3[j][i] + b3[j]: one warp per row.
-__global__ void out_fwd_kernel(const __nv_bfloat16 *H2, const __nv_bfloat16 *W3, const float *b3, float *Y, int B) {
+// With map (DEVICE float[5]: mean0, mean1, scale0, scale1, tail weight), the
+// raw output u is mapped back to the target scale: Y = u * scale + mean.
+__global__ void out_fwd_kernel(const __nv_bfloat16 *H2, const __nv_bfloat16 *W3, const float *b3, float *Y, int B,
+                               const float *map) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= B) return;
     float s0 = 0.f, s1 = 0.f;
@@ -300,22 +303,66 @@ __global__ void out_fwd_kernel(const __nv_bfloat16 *H2, const __nv_bfloat16 *W3,
         s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
     }
     if (lane == 0) {
-        Y[2 * warp] = s0 + b3[0];
-        Y[2 * warp + 1] = s1 + b3[1];
+        float u0 = s0 + b3[0], u1 = s1 + b3[1];
+        if (map) {
+            u0 = u0 * map[2] + map[0];
+            u1 = u1 * map[3] + map[1];
+        }
+        Y[2 * warp] = u0;
+        Y[2 * warp + 1] = u1;
     }
 }
 
-// dY = 2 (Y - T) / B; loss += sum (Y - T)^2 / B
-__global__ void loss_kernel(const float *Y, const float *T, float *dY, float *loss, int B) {
+// Raw outputs U against mapped targets t' = (T - mean) / scale, row weight
+// w = 1 + tail * max(0, t'_0) (the upper tail of the first target counts
+// more): dU = 2 w (U - t') / B; loss += w (U - t')^2 / B.
+__global__ void loss_kernel(const float *U, const float *T, float *dU, float *loss, int B, const float *map) {
     float l = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * B; i += gridDim.x * blockDim.x) {
-        const float d = Y[i] - T[i];
-        dY[i] = 2.f * d / (float)B;
-        l += d * d / (float)B;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const float t0 = (T[2 * b] - map[0]) / map[2], t1 = (T[2 * b + 1] - map[1]) / map[3];
+        const float w = 1.f + map[4] * fmaxf(t0, 0.f);
+        const float d0 = U[2 * b] - t0, d1 = U[2 * b + 1] - t1;
+        dU[2 * b] = 2.f * w * d0 / (float)B;
+        dU[2 * b + 1] = 2.f * w * d1 / (float)B;
+        l += w * (d0 * d0 + d1 * d1) / (float)B;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
     if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+// Target map from a target set: column means, column standard deviations
+// (population; 1 where below 1e-6), the tail weight.  One block, float64 sums.
+__global__ void fit_map_kernel(const float *T, int B, float tail, float *map) {
+    __shared__ double red[2][1024];
+    double s0 = 0, s1 = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) s0 += T[2 * b], s1 += T[2 * b + 1];
+    red[0][threadIdx.x] = s0, red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[0][threadIdx.x] += red[0][threadIdx.x + o], red[1][threadIdx.x] += red[1][threadIdx.x + o];
+        __syncthreads();
+    }
+    const double m0 = red[0][0] / B, m1 = red[1][0] / B;
+    __syncthreads();
+    double v0 = 0, v1 = 0;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const double d0 = T[2 * b] - m0, d1 = T[2 * b + 1] - m1;
+        v0 += d0 * d0, v1 += d1 * d1;
+    }
+    red[0][threadIdx.x] = v0, red[1][threadIdx.x] = v1;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[0][threadIdx.x] += red[0][threadIdx.x + o], red[1][threadIdx.x] += red[1][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sd0 = sqrt(red[0][0] / B), sd1 = sqrt(red[1][0] / B);
+        map[0] = (float)m0, map[1] = (float)m1;
+        map[2] = sd0 < 1e-6 ? 1.f : (float)sd0;
+        map[3] = sd1 < 1e-6 ? 1.f : (float)sd1;
+        map[4] = tail;
+    }
 }
 
 // dH2[b][i] = (dY[b][0] W3[0][i] + dY[b][1] W3[1][i]) * [H2[b][i] > 0]  (bf16)
@@ -503,8 +550,9 @@ __global__ void select_kernel(const unsigned long long *keys, uint32_t H, const 
 using namespace hedl;
 
 struct hedl_mlp {
-    // FP32 master weights, Adam moments, gradients; BF16 copies for compute
-    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    // FP32 master weights, Adam moments, gradients; BF16 copies for compute;
+    // the target map (mean0, mean1, scale0, scale1, tail weight)
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *map = nullptr;
     __nv_bfloat16 *wb = nullptr;
     size_t n = 0;
     uint32_t step = 0;
@@ -542,7 +590,8 @@ MlpWs carve(void *ws, uint32_t B) {
 
 uint32_t grid1(size_t n) { return (uint32_t)std::min<size_t>((n + 255) / 256, 4096); }
 
-int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs &w, cudaStream_t s) {
+int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs &w, cudaStream_t s,
+                 bool mapped) {
     GemmArgs a{};
     a.A = X;
     a.B = mlp->wb + OFF_W1;
@@ -559,18 +608,19 @@ int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs 
     a.K = DH, a.lda = DH, a.ldb = DH;
     e = gemm(a, false, false, 1, s);
     if (e) return e;
-    out_fwd_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B);
+    out_fwd_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B,
+                                                        mapped ? mlp->map : nullptr);
     return cudaGetLastError();
 }
 
 int grads_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, const float *T, uint32_t B, const MlpWs &w, cudaStream_t s) {
-    int e = forward_impl(mlp, X, B, w, s);
+    int e = forward_impl(mlp, X, B, w, s, false);
     if (e) return e;
     e = cudaMemsetAsync(w.loss, 0, 4, s);
     if (e) return e;
     e = cudaMemsetAsync(mlp->g, 0, N_PARAMS * 4, s);
     if (e) return e;
-    loss_kernel<<<grid1(2 * B), 256, 0, s>>>(w.y, T, w.dy, w.loss, (int)B);
+    loss_kernel<<<grid1(B), 256, 0, s>>>(w.y, T, w.dy, w.loss, (int)B, mlp->map);
     out_bwd_dw_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dy, w.h2, mlp->g + OFF_W3, mlp->g + OFF_B3, (int)B);
     out_bwd_dh_kernel<<<grid1((size_t)B * DH), 256, 0, s>>>(w.dy, mlp->wb + OFF_W3, w.h2, w.dh2, (int)B);
     colsum_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dh2, mlp->g + OFF_B2, (int)B, DH);
@@ -619,6 +669,11 @@ int hedl_mlp_create(const float *params, hedl_mlp **out) {
     if (!e) e = cudaMalloc(&m->v, N_PARAMS * 4);
     if (!e) e = cudaMalloc(&m->g, N_PARAMS * 4);
     if (!e) e = cudaMalloc(&m->wb, N_PARAMS * 2);
+    if (!e) e = cudaMalloc(&m->map, 5 * 4);
+    if (!e) {
+        const float ident[5] = {0.f, 0.f, 1.f, 1.f, 0.f};
+        e = cudaMemcpy(m->map, ident, sizeof(ident), cudaMemcpyHostToDevice);
+    }
     if (!e) e = cudaMemcpy(m->w, params, N_PARAMS * 4, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(m->m, 0, N_PARAMS * 4);
     if (!e) e = cudaMemset(m->v, 0, N_PARAMS * 4);
@@ -643,6 +698,7 @@ void hedl_mlp_free(hedl_mlp *m) {
     cudaFree(m->v);
     cudaFree(m->g);
     cudaFree(m->wb);
+    cudaFree(m->map);
     delete m;
 }
 
@@ -679,7 +735,7 @@ int hedl_mlp_forward(hedl_mlp *m, const uint16_t *X, uint32_t B, float *Y, void 
     if (!m || !X || !Y) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     if (!ws || ws_bytes < mlp_ws_bytes(B)) return fail(HEDL_ERR_WORKSPACE_TOO_SMALL, "MLP workspace too small");
     MlpWs w = carve(ws, B);
-    int e = forward_impl(m, (const __nv_bfloat16 *)X, B, w, (cudaStream_t)s);
+    int e = forward_impl(m, (const __nv_bfloat16 *)X, B, w, (cudaStream_t)s, true);
     if (e) return cuda_fail(e, "mlp forward");
     e = cudaMemcpyAsync(Y, w.y, (size_t)B * DO * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)s);
     return e ? cuda_fail(e, "mlp forward copy") : HEDL_OK;
@@ -710,6 +766,29 @@ int hedl_mlp_train_step(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t
                                                                 1e-8f, c1, c2);
     cudaError_t ce = cudaGetLastError();
     return ce ? cuda_fail(ce, "adam launch") : HEDL_OK;
+}
+
+int hedl_mlp_fit_target_map(hedl_mlp *m, const float *T, uint32_t B, float tail_weight, hedl_stream s) {
+    if (!m || !T) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    if (B == 0) return fail(HEDL_ERR_INVALID_ARG, "empty target set");
+    if (!(tail_weight >= 0.f)) return fail(HEDL_ERR_INVALID_ARG, "tail_weight must be >= 0");
+    fit_map_kernel<<<1, 1024, 0, (cudaStream_t)s>>>(T, (int)B, tail_weight, m->map);
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_fail(e, "fit map launch") : HEDL_OK;
+}
+
+int hedl_mlp_set_target_map(hedl_mlp *m, const float *map) {
+    if (!m || !map) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    if (!(map[2] > 0.f) || !(map[3] > 0.f) || !(map[4] >= 0.f))
+        return fail(HEDL_ERR_INVALID_ARG, "scales must be > 0 and the tail weight >= 0");
+    cudaError_t e = cudaMemcpy(m->map, map, 5 * 4, cudaMemcpyHostToDevice);
+    return e ? cuda_fail(e, "set map") : HEDL_OK;
+}
+
+int hedl_mlp_get_target_map(const hedl_mlp *m, float *map) {
+    if (!m || !map) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpy(map, m->map, 5 * 4, cudaMemcpyDeviceToHost);
+    return e ? cuda_fail(e, "get map") : HEDL_OK;
 }
 
 int hedl_scores_from_counts(const uint32_t *counts, uint32_t H, float *scores, hedl_stream s) {

@@ -207,4 +207,4 @@ class BeamSearch:
             self._seen_X, self._seen_T = [Xa], [Ta]
         batch = min(1024, Xa.shape[0])
         self.surrogate.train(Xa, Ta, epochs=self.online_epochs, batch=batch, lr=self.online_lr,
-                             seed=len(self._seen_X))
+                             seed=len(self._seen_X), tail_weight=None, schedule="const")

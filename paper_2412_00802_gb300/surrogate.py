@@ -14,7 +14,8 @@ from typing import Optional, Sequence, Tuple
 
 import numpy as np
 
-from . import (DeviceKB, hedl_encode, hedl_mlp_create, hedl_mlp_forward, hedl_mlp_get, hedl_mlp_param_count,
+from . import (DeviceKB, hedl_encode, hedl_mlp_create, hedl_mlp_fit_target_map, hedl_mlp_forward, hedl_mlp_get,
+               hedl_mlp_get_target_map, hedl_mlp_param_count, hedl_mlp_set_target_map,
                hedl_mlp_train_step, hedl_mlp_workspace_size, hedl_plan_batch, hedl_plan_execute,
                hedl_plan_info_get, hedl_scores_from_counts, hedl_select_top, hedl_select_workspace_size,
                hedl_sync_status)
@@ -92,26 +93,44 @@ class Surrogate:
             hedl_mlp_forward(self.mlp, xb, Y[b0:b0 + xb.shape[0]], self._workspace(xb.shape[0]))
         return Y
 
-    def train(self, X, T, epochs: int = 4, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
-        """Mini-batch Adam on (X, T); returns the mean loss of each epoch."""
+    def train(self, X, T, epochs: int = 4, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+              tail_weight: Optional[float] = 4.0, schedule: str = "cos"):
+        """Mini-batch Adam on (X, T); returns the mean loss of each epoch.
+
+        tail_weight: fit the target map on T first (standardised targets, the
+        upper tail of the accuracy weighted by 1 + tail_weight * z); None keeps
+        the network's current map.  schedule: "cos" decays the learning rate
+        from lr to 0 along a half cosine over all steps, "const" keeps it."""
         torch = self.torch
         n = X.shape[0]
+        if tail_weight is not None:
+            hedl_mlp_fit_target_map(self.mlp, T, tail_weight)
         g = torch.Generator(device="cpu").manual_seed(seed)
         loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         hist = []
+        per_epoch = max((n - batch) // batch + 1, 0)
+        total, step = max(epochs * per_epoch, 1), 0
         for ep in range(epochs):
             perm = torch.randperm(n, generator=g).to(self.device)
-            total = 0.0
+            tot = 0.0
             steps = 0
             for b0 in range(0, n - batch + 1, batch):
                 idx = perm[b0:b0 + batch]
                 xb = X.index_select(0, idx).contiguous()
                 tb = T.index_select(0, idx).contiguous()
-                hedl_mlp_train_step(self.mlp, xb, tb, lr, self._workspace(batch), loss)
-                total += float(loss.item())
+                lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * step / total)) if schedule == "cos" else lr
+                hedl_mlp_train_step(self.mlp, xb, tb, lr_t, self._workspace(batch), loss)
+                tot += float(loss.item())
                 steps += 1
-            hist.append(total / max(steps, 1))
+                step += 1
+            hist.append(tot / max(steps, 1))
         return hist
+
+    def target_map(self) -> np.ndarray:
+        return hedl_mlp_get_target_map(self.mlp)
+
+    def set_target_map(self, tmap) -> None:
+        hedl_mlp_set_target_map(self.mlp, tmap)
 
     def select(self, Y, k: int):
         """Indices (ascending) of the k best predictions (accuracy, then F1, then index)."""

@@ -88,6 +88,36 @@ def test_gradients_match_oracle(env):
         assert rel <= 2e-2, (name, rel)
 
 
+def test_target_map_fit_forward_and_gradients(env):
+    """The fitted map equals the oracle's; mapped predictions and the weighted loss's
+    gradients match the oracle's with the same map."""
+    torch, H, sg, kb = env
+    X, T = _xt(torch, kb, 1024, 9)
+    T = (T * np.array([0.3, 0.5], np.float32) + np.array([0.5, 0.2], np.float32)).astype(np.float32)
+    p = sg.init_params(10)
+    s = sg.Surrogate(p)
+    Xd = torch.from_numpy(X).to("cuda").to(torch.bfloat16)
+    Td = torch.from_numpy(T).to("cuda")
+    H.hedl_mlp_fit_target_map(s.mlp, Td, 3.0)
+    m = s.target_map()
+    ref_m = S.fit_target_map(T, 3.0)
+    assert np.allclose(m, ref_m, rtol=1e-5, atol=1e-6)
+    Y = s.predict(Xd).cpu().numpy()
+    ref_y, _ = S.forward(sg.split_params(p), X, rounding=True, tmap=m)
+    assert np.abs(Y - ref_y).max() <= 2e-2 * max(1.0, np.abs(ref_y).max())
+    loss = torch.zeros(1, device="cuda")
+    H.hedl_mlp_gradients(s.mlp, Xd, Td, s._workspace(1024), loss)
+    _, g, _ = H.hedl_mlp_get(s.mlp)
+    ref_loss, ref = S.backward(sg.split_params(p), X, T, rounding=True, tmap=m)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-3 * abs(ref_loss)
+    gd = sg.split_params(g)
+    for name in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        rel = np.linalg.norm(gd[name] - ref[name]) / max(np.linalg.norm(ref[name]), 1e-12)
+        assert rel <= 2e-2, (name, rel)
+    with pytest.raises(H.HedlError):
+        s.set_target_map([0, 0, 0.0, 1, 0])
+
+
 def test_train_step_matches_oracle_adam(env):
     torch, H, sg, kb = env
     X, T = _xt(torch, kb, 512, 7)

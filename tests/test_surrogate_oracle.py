@@ -92,6 +92,45 @@ def test_backward_matches_finite_differences():
             assert abs(fd - an) <= 1e-6 + 1e-5 * abs(fd), (name, i, fd, an)
 
 
+def test_mapped_weighted_loss_matches_finite_differences():
+    """With a target map the loss is taken on standardised targets with upper-tail row
+    weights, written out here directly (not through the oracle's helpers)."""
+    p = S.init_params(5)
+    rng = np.random.default_rng(6)
+    X = rng.normal(size=(7, 512)).astype(np.float32)
+    T = rng.uniform(size=(7, 2)).astype(np.float32)
+    tmap = (0.4, 0.3, 0.2, 0.25, 3.0)
+    p64 = {k: v.astype(np.float64) for k, v in p.items()}
+
+    def direct(pp):
+        u = S.forward(pp, X, rounding=False)[1]["u"]
+        t0 = (T[:, 0].astype(np.float64) - 0.4) / 0.2
+        t1 = (T[:, 1].astype(np.float64) - 0.3) / 0.25
+        w = 1.0 + 3.0 * np.maximum(t0, 0.0)
+        return float(np.sum(w * ((u[:, 0] - t0) ** 2 + (u[:, 1] - t1) ** 2)) / 7)
+    lval, g = S.backward(p64, X, T, rounding=False, tmap=tmap)
+    assert abs(lval - direct(p64)) <= 1e-9 * abs(lval)
+    eps = 1e-6
+    for name in ("w1", "b2", "w3", "b3"):
+        flat = p64[name].reshape(-1)
+        for i in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[i]
+            flat[i] = old + eps
+            lp = direct(p64)
+            flat[i] = old - eps
+            lm = direct(p64)
+            flat[i] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - g[name].reshape(-1)[i]) <= 1e-6 + 1e-5 * abs(fd), (name, i)
+    # predictions come back on the target scale
+    y = S.forward(p64, X, rounding=False, tmap=tmap)[0]
+    u = S.forward(p64, X, rounding=False)[0]
+    assert np.allclose(y, u * np.array([0.2, 0.25]) + np.array([0.4, 0.3]))
+    # the fitted map: column means and population standard deviations
+    m = S.fit_target_map(T, 2.0)
+    assert np.allclose(m[:2], T.mean(0)) and np.allclose(m[2:4], T.std(0)) and m[4] == 2.0
+
+
 def test_adam_first_step_closed_form():
     p = {"w": np.array([1.0, -2.0, 3.0], np.float32)}
     g = {"w": np.array([0.5, -0.25, 1e-3])}
