@@ -69,6 +69,43 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def mlp_forward_timing(s, X):
+    """CUDA-event time of the surrogate's forward over X on each GEMM engine, with the
+    tensor roofline of the dense layers (2 x B x (512*512*2 + 512*2) flops)."""
+    import torch
+    import paper_2412_00802_gb300 as H
+    B = X.shape[0]
+    Y = torch.empty((B, 2), dtype=torch.float32, device=X.device)
+    ws = s._workspace(B)
+    flops = 2.0 * B * (512 * 512 * 2 + 512 * 2)
+    peak, kind = measured_bf16_tflops()
+    out = {"rows": B, "flops": flops, "peak_tflops": peak, "peak_kind": f"{kind} bf16 (MEASURED_PEAKS.json bf16_tflops)"}
+    for name, eng in (("tcgen05", H.HEDL_GEMM_TCGEN05), ("mma_sync", H.HEDL_GEMM_MMA_SYNC)):
+        H.hedl_mlp_set_gemm(s.mlp, eng)
+        for _ in range(3):
+            H.hedl_mlp_forward(s.mlp, X, Y, ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(10):
+            H.hedl_mlp_forward(s.mlp, X, Y, ws)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        out[name] = {"ms": ms, "tflops": flops / ms / 1e9, "frac": flops / ms / 1e9 / peak}
+    H.hedl_mlp_set_gemm(s.mlp, H.HEDL_GEMM_TCGEN05)
+    H.hedl_mlp_status(s.mlp)
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -234,6 +271,7 @@ def surrogate_round(args, dev):
     Tsel = Tsel.cpu().numpy()
     sur_s = time.perf_counter() - t0
     found = bool(best in set(sel.tolist()))
+    fwd = mlp_forward_timing(s, s.encode(cflat, coffs))
     top_pred = np.argsort(-Y[:, 0].cpu().numpy(), kind="stable")[:100]
     return {"workload": ("planted KB with the single-hypothesis workload's distributions, N=" + f"{cfg.n:,}"
                          + f"; {n_train:,} engine-scored training hypotheses; 65,536 candidates, top 5 % scored"),
@@ -241,7 +279,7 @@ def surrogate_round(args, dev):
             "recall_at_100": OS.recall_at(100, order, sel), "recall_strict_top100": OS.recall_at(100, order, top_pred),
             "selected": k, "best_found": found, "best_acc": float(exact[best, 0]),
             "best_found_per_s": (1.0 / sur_s) if found else 0.0, "best_found_per_s_plain": 1.0 / plain_s,
-            "surrogate_round_s": sur_s, "plain_time_to_best_s": plain_s}
+            "surrogate_round_s": sur_s, "plain_time_to_best_s": plain_s, "mlp_forward": fwd}
 
 
 def search_run(args, dev):

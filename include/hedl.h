@@ -385,6 +385,19 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
                 const float *prior, uint16_t *X, hedl_stream s);
 
+/* Engine of the two 512-wide dense layers' forward GEMMs:
+ * HEDL_GEMM_TCGEN05 (default) runs them on the 5th-generation tensor cores
+ * (tcgen05.mma, accumulators in tensor memory); HEDL_GEMM_MMA_SYNC on the
+ * warp-level mma.sync path (the backward pass always uses mma.sync).  Both
+ * accumulate in FP32 and store bf16 activations. */
+#define HEDL_GEMM_TCGEN05  0u
+#define HEDL_GEMM_MMA_SYNC 1u
+int hedl_mlp_set_gemm(hedl_mlp *m, unsigned engine);
+
+/* SYNCHRONIZES the stream; HEDL_ERR_TIMEOUT if a tensor-core completion wait
+ * of an earlier call gave up (its outputs are then undefined), and clears it. */
+int hedl_mlp_status(hedl_mlp *m, hedl_stream s);
+
 /* Y (DEVICE float [B][2]) = the network applied to X (DEVICE bf16 [B][512]),
  * its raw output u mapped to the target scale: Y = u * scale + mean (the
  * target map; identity until one is set). */

@@ -49,7 +49,7 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
            "hedl_mlp_gradients", "hedl_mlp_train_step", "hedl_scores_from_counts", "hedl_select_workspace_size",
            "hedl_select_top", "hedl_canonical_batch", "hedl_mlp_fit_target_map", "hedl_mlp_set_target_map",
-           "hedl_mlp_get_target_map", "hedl_last_error")
+           "hedl_mlp_get_target_map", "hedl_mlp_set_gemm", "hedl_mlp_status", "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -132,6 +132,8 @@ def library(path: Optional[str] = None):
             "hedl_mlp_fit_target_map": (I, [P, P, U32, ctypes.c_float, P]),
             "hedl_mlp_set_target_map": (I, [P, P]),
             "hedl_mlp_get_target_map": (I, [P, P]),
+            "hedl_mlp_set_gemm": (I, [P, ctypes.c_uint]),
+            "hedl_mlp_status": (I, [P, P]),
             "hedl_select_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_select_top": (I, [P, U32, U32, P, P, ctypes.c_size_t, P]),
             "hedl_last_error": (ctypes.c_char_p, []),
@@ -460,6 +462,18 @@ def hedl_mlp_get_target_map(m: MLPHandle) -> np.ndarray:
     a = np.zeros(5, np.float32)
     _check(library().hedl_mlp_get_target_map(m.ptr, a.ctypes.data))
     return a
+
+
+HEDL_GEMM_TCGEN05 = 0
+HEDL_GEMM_MMA_SYNC = 1
+
+
+def hedl_mlp_set_gemm(m: MLPHandle, engine: int):
+    _check(library().hedl_mlp_set_gemm(m.ptr, engine))
+
+
+def hedl_mlp_status(m: MLPHandle, stream=None):
+    _check(library().hedl_mlp_status(m.ptr, _stream(stream)))
 
 
 def hedl_scores_from_counts(counts, scores, stream=None):

@@ -178,6 +178,22 @@ struct hedl_plan {
 namespace hedl {
 
 void set_error(const std::string &msg);
+// Surrogate dense layer on tcgen05 tensor cores (umma.cu): C[M][N] =
+// act(A[M][K] . B[N][K]^T + bias), A and B bf16 K-major, N % 256 == 0,
+// K % 64 == 0, 16-byte aligned rows; *err (device, may be null) gets bit 0
+// set if an MMA completion wait timed out.
+struct UmmaArgs {
+    const void *A;   // bf16 [M][lda]
+    const void *B;   // bf16 [N][ldb]
+    void *C;         // bf16 or float [M][ldc]
+    const float *bias;
+    int M, N, K, lda, ldb, ldc;
+    int relu, out_bf16;
+    uint32_t *err;
+};
+bool umma_shape_ok(const UmmaArgs &a);
+int umma_gemm(const UmmaArgs &a, void *stream);
+
 int fail(int code, const std::string &msg);
 int cuda_fail(int cuda_err, const char *what);
 

@@ -553,6 +553,8 @@ struct hedl_mlp {
     // FP32 master weights, Adam moments, gradients; BF16 copies for compute;
     // the target map (mean0, mean1, scale0, scale1, tail weight)
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *map = nullptr;
+    uint32_t *err = nullptr;                  // device: bit 0 = a tensor-core wait timed out
+    unsigned gemm = HEDL_GEMM_TCGEN05;        // engine of the dense layers' forward GEMMs
     __nv_bfloat16 *wb = nullptr;
     size_t n = 0;
     uint32_t step = 0;
@@ -590,23 +592,27 @@ MlpWs carve(void *ws, uint32_t B) {
 
 uint32_t grid1(size_t n) { return (uint32_t)std::min<size_t>((n + 255) / 256, 4096); }
 
+// One hidden layer, H = relu(A . W^T + b): on tcgen05 when selected (and the
+// shape allows it), else on the mma.sync GEMM.
+int dense_relu(hedl_mlp *mlp, const __nv_bfloat16 *A, const __nv_bfloat16 *W, const float *b, __nv_bfloat16 *H,
+               int M, int K, cudaStream_t s) {
+    UmmaArgs u{A, W, H, b, M, DH, K, K, K, DH, 1, 1, mlp->err};
+    if (mlp->gemm == HEDL_GEMM_TCGEN05 && umma_shape_ok(u)) return umma_gemm(u, s);
+    GemmArgs a{};
+    a.A = A;
+    a.B = W;
+    a.C = H;
+    a.bias = b;
+    a.M = M, a.N = DH, a.K = K, a.lda = K, a.ldb = K, a.ldc = DH;
+    a.relu = 1, a.out_bf16 = 1;
+    return gemm(a, false, false, 1, s);
+}
+
 int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs &w, cudaStream_t s,
                  bool mapped) {
-    GemmArgs a{};
-    a.A = X;
-    a.B = mlp->wb + OFF_W1;
-    a.C = w.h1;
-    a.bias = mlp->w + OFF_B1;
-    a.M = (int)B, a.N = DH, a.K = DI, a.lda = DI, a.ldb = DI, a.ldc = DH;
-    a.relu = 1, a.out_bf16 = 1;
-    int e = gemm(a, false, false, 1, s);
+    int e = dense_relu(mlp, X, mlp->wb + OFF_W1, mlp->w + OFF_B1, w.h1, (int)B, DI, s);
     if (e) return e;
-    a.A = w.h1;
-    a.B = mlp->wb + OFF_W2;
-    a.C = w.h2;
-    a.bias = mlp->w + OFF_B2;
-    a.K = DH, a.lda = DH, a.ldb = DH;
-    e = gemm(a, false, false, 1, s);
+    e = dense_relu(mlp, w.h1, mlp->wb + OFF_W2, mlp->w + OFF_B2, w.h2, (int)B, DH, s);
     if (e) return e;
     out_fwd_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B,
                                                         mapped ? mlp->map : nullptr);
@@ -670,6 +676,8 @@ int hedl_mlp_create(const float *params, hedl_mlp **out) {
     if (!e) e = cudaMalloc(&m->g, N_PARAMS * 4);
     if (!e) e = cudaMalloc(&m->wb, N_PARAMS * 2);
     if (!e) e = cudaMalloc(&m->map, 5 * 4);
+    if (!e) e = cudaMalloc(&m->err, 4);
+    if (!e) e = cudaMemset(m->err, 0, 4);
     if (!e) {
         const float ident[5] = {0.f, 0.f, 1.f, 1.f, 0.f};
         e = cudaMemcpy(m->map, ident, sizeof(ident), cudaMemcpyHostToDevice);
@@ -699,6 +707,7 @@ void hedl_mlp_free(hedl_mlp *m) {
     cudaFree(m->g);
     cudaFree(m->wb);
     cudaFree(m->map);
+    cudaFree(m->err);
     delete m;
 }
 
@@ -783,6 +792,28 @@ int hedl_mlp_set_target_map(hedl_mlp *m, const float *map) {
         return fail(HEDL_ERR_INVALID_ARG, "scales must be > 0 and the tail weight >= 0");
     cudaError_t e = cudaMemcpy(m->map, map, 5 * 4, cudaMemcpyHostToDevice);
     return e ? cuda_fail(e, "set map") : HEDL_OK;
+}
+
+int hedl_mlp_set_gemm(hedl_mlp *m, unsigned engine) {
+    if (!m) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    if (engine != HEDL_GEMM_TCGEN05 && engine != HEDL_GEMM_MMA_SYNC)
+        return fail(HEDL_ERR_INVALID_ARG, "engine must be HEDL_GEMM_TCGEN05 or HEDL_GEMM_MMA_SYNC");
+    m->gemm = engine;
+    return HEDL_OK;
+}
+
+int hedl_mlp_status(hedl_mlp *m, hedl_stream s) {
+    if (!m) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)s);
+    if (e) return cuda_fail(e, "stream synchronize");
+    uint32_t st = 0;
+    e = cudaMemcpy(&st, m->err, 4, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "status read");
+    if (st) {
+        cudaMemset(m->err, 0, 4);
+        return fail(HEDL_ERR_TIMEOUT, "a tensor-core completion wait gave up (timeout)");
+    }
+    return HEDL_OK;
 }
 
 int hedl_mlp_get_target_map(const hedl_mlp *m, float *map) {

@@ -70,6 +70,28 @@ def test_forward_matches_oracle(env):
     assert err.mean() <= 2e-3 * max(1.0, np.abs(ref).mean())
 
 
+@pytest.mark.parametrize("B", [1, 700, 8192])
+def test_tcgen05_forward_matches_mma_sync_and_oracle(env, B):
+    """The tcgen05 dense layers (accumulators in tensor memory) give the mma.sync path's
+    outputs up to FP32 summation order, and the oracle's within bf16 bounds."""
+    torch, H, sg, kb = env
+    X, _ = _xt(torch, kb, B, 11)
+    p = sg.init_params(12)
+    Xd = torch.from_numpy(X).to("cuda").to(torch.bfloat16)
+    s = sg.Surrogate(p)
+    y_tc = s.predict(Xd).cpu().numpy()
+    H.hedl_mlp_status(s.mlp)
+    H.hedl_mlp_set_gemm(s.mlp, H.HEDL_GEMM_MMA_SYNC)
+    y_ms = s.predict(Xd).cpu().numpy()
+    ref, _ = S.forward(sg.split_params(p), X, rounding=True)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(y_tc - y_ms).max() <= 2e-2 * scale
+    assert np.abs(y_tc - ref).max() <= 2e-2 * scale
+    assert np.abs(y_tc - ref).mean() <= 2e-3 * max(1.0, np.abs(ref).mean())
+    with pytest.raises(H.HedlError):
+        H.hedl_mlp_set_gemm(s.mlp, 7)
+
+
 def test_gradients_match_oracle(env):
     torch, H, sg, kb = env
     X, T = _xt(torch, kb, 1024, 4)
