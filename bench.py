@@ -431,6 +431,26 @@ def run_latency(args, local_rank):
         "clocks": clk.summary()}), flush=True)
 
 
+def run_mlp(args, local_rank):
+    """The surrogate's forward alone: 65,536 encoded random hypotheses (a 20,000-individual KB
+    of the surrogate workload's distributions) through both GEMM engines."""
+    import torch
+    from paper_2412_00802_gb300 import build
+    from paper_2412_00802_gb300 import surrogate as sg
+    from synth import hyps, kb as K, programs as P
+    torch.cuda.set_device(local_rank)
+    build.build()
+    kb = K.generate(K.CONFIGS["c4"].scaled(20_000))
+    progs = hyps.batch_hyps(kb, 77, 0, 65_536, gen=hyps.TreeGen(kb, 77, share=0.3))
+    s = sg.Surrogate(seed=1, device=f"cuda:{local_rank}", grid=sg.threshold_grid(kb.prop_vals))
+    X = s.encode(*P.pack_batch(progs))
+    fwd = mlp_forward_timing(s, X)
+    print(json.dumps({"metric": "surrogate forward TFLOP/s (tcgen05)", "value": fwd["tcgen05"]["tflops"],
+                      "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1, "dtype": "bf16",
+                      "data": "synthetic", "config": {"workload": "MLP 512-512-512-2 forward, 65,536 rows"},
+                      "mlp_forward": fwd}), flush=True)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle timed on the host cores, rank 0 only."""
     if rank != 0:
@@ -648,6 +668,7 @@ def main():
                     help="surrogate round at full size (10M individuals, 1M training hypotheses)")
     ap.add_argument("--latency", action="store_true",
                     help="the single-hypothesis latency workload (10M individuals) instead of the batched one")
+    ap.add_argument("--mlp", action="store_true", help="time the surrogate's forward alone (both GEMM engines)")
     ap.add_argument("--latency-n", type=int, default=0,
                     help="individuals of the latency workload's KB (default: its full 10,000,000)")
     ap.add_argument("--search-full", action="store_true",
@@ -672,6 +693,8 @@ def main():
         run_reference(args, rank, world)
     elif args.latency:
         run_latency(args, local_rank)
+    elif args.mlp:
+        run_mlp(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:
