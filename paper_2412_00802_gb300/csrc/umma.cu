@@ -2,12 +2,12 @@
 // C[M][N] = act(A[M][K] . B[N][K]^T + bias), A and B bf16 and K-major (rows
 // of K contiguous elements), FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 4 warps computes a 128 x 256 tile.  K runs in blocks of 64: the
-// CTA's threads copy a block of A (128 x 64) and B (256 x 64) into shared
+// One CTA of 4 warps computes a 128 x 256 tile.  K runs in blocks of 32: the
+// CTA's threads copy a block of A (128 x 32) and B (256 x 32) into shared
 // memory with 16-byte async copies, laid out as 8-row x 16-byte core
-// matrices (no swizzle); one thread issues four tcgen05.mma (M 128, N 256,
-// K 16 each) on it and commits them to an mbarrier, while the next block is
-// copied into the other of two stages.  The 128 x 256 FP32 accumulator lives
+// matrices (no swizzle), three blocks ahead in a ring of four stages; one
+// thread issues two tcgen05.mma (M 128, N 256, K 16 each) per block and
+// commits them to the stage's mbarrier, which frees the stage for reuse.  The 128 x 256 FP32 accumulator lives
 // in 256 TMEM columns; the epilogue reads it back with tcgen05.ld (each warp
 // its 32 rows), adds the bias, applies ReLU and stores bf16 or FP32 rows.
 //
@@ -22,12 +22,14 @@
 namespace hedl {
 namespace {
 
-constexpr int UM = 128, UN = 256, UK = 64;
-constexpr uint32_t A_BYTES = UM * UK * 2;            // 16 KB
-constexpr uint32_t B_BYTES = UN * UK * 2;            // 32 KB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
+constexpr int UM = 128, UN = 256, UK = 32, STAGES = 4;
+constexpr uint32_t KCH = UK / 8;                     // 16-byte K chunks per row and block
+constexpr uint32_t SBO = KCH * 128;                  // bytes between 8-row groups of a stage
+constexpr uint32_t A_BYTES = UM * UK * 2;            // 8 KB
+constexpr uint32_t B_BYTES = UN * UK * 2;            // 16 KB
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 24 KB
 constexpr uint32_t TMEM_COLS = UN;                   // FP32 accumulator columns
-constexpr size_t UMMA_SMEM = 2 * STAGE_BYTES + 1024 + 64;
+constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 128;
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bit 17,
@@ -37,11 +39,11 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >
 
 // Shared-memory matrix descriptor of a K-major operand without swizzle:
 // start address / 16, leading byte offset (next 8 K-elements: 128 B) / 16,
-// stride byte offset (next 8 rows: 1024 B) / 16, descriptor version 1.
+// stride byte offset (next 8 rows: SBO) / 16, descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)(SBO >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -80,33 +82,33 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // Stage one K block: A rows m0.. (zero past M), B rows n0.., 16 bytes a thread per copy.
 __device__ __forceinline__ void load_stage(const UmmaArgs &g, uint32_t sA, uint32_t sB, int m0, int n0, int k0) {
-    for (int c = threadIdx.x; c < UM * 8; c += blockDim.x) {
-        const int r = c >> 3, kc = c & 7;
+    for (int c = threadIdx.x; c < UM * (int)KCH; c += blockDim.x) {
+        const int r = c / (int)KCH, kc = c % (int)KCH;
         const bool ok = m0 + r < g.M;
         const __nv_bfloat16 *src =
             reinterpret_cast<const __nv_bfloat16 *>(g.A) + (size_t)(ok ? m0 + r : 0) * g.lda + k0 + kc * 8;
-        cp16(sA + (uint32_t)((r >> 3) * 1024 + kc * 128 + (r & 7) * 16), src, ok);
+        cp16(sA + (uint32_t)((r >> 3) * SBO + kc * 128 + (r & 7) * 16), src, ok);
     }
-    for (int c = threadIdx.x; c < UN * 8; c += blockDim.x) {
-        const int r = c >> 3, kc = c & 7;
+    for (int c = threadIdx.x; c < UN * (int)KCH; c += blockDim.x) {
+        const int r = c / (int)KCH, kc = c % (int)KCH;
         const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(g.B) + (size_t)(n0 + r) * g.ldb + k0 + kc * 8;
-        cp16(sB + (uint32_t)((r >> 3) * 1024 + kc * 128 + (r & 7) * 16), src, true);
+        cp16(sB + (uint32_t)((r >> 3) * SBO + kc * 128 + (r & 7) * 16), src, true);
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * STAGE_BYTES);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(base + 2 * STAGE_BYTES + 16);
-    uint32_t *okp = reinterpret_cast<uint32_t *>(base + 2 * STAGE_BYTES + 32);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);     // one per stage
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(base + STAGES * STAGE_BYTES + 64);
+    uint32_t *okp = reinterpret_cast<uint32_t *>(base + STAGES * STAGE_BYTES + 80);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const int n0 = blockIdx.x * UN, m0 = blockIdx.y * UM;
-    const uint32_t s0 = smem_u32(base), bar_a = smem_u32(bar);
+    const uint32_t s0 = smem_u32(base), bar0 = smem_u32(bar);
 
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        for (int i = 0; i < STAGES; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * i) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *okp = 1u;
     }
@@ -121,21 +123,17 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = *tslot;
 
+    // Block kb lives in stage kb % STAGES and its MMAs commit to that stage's
+    // barrier (the stage's (kb / STAGES)-th phase).  Copies run STAGES - 1
+    // blocks ahead; one async-copy group is committed per block (empty past K).
     const int nk = g.K / UK;
-    load_stage(g, s0, s0 + A_BYTES, m0, n0, 0);
+    for (int i = 0; i < STAGES - 1; ++i) {
+        if (i < nk) load_stage(g, s0 + i * STAGE_BYTES, s0 + i * STAGE_BYTES + A_BYTES, m0, n0, i * UK);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     for (int kb = 0; kb < nk; ++kb) {
-        const uint32_t st = s0 + (uint32_t)(kb & 1) * STAGE_BYTES;
-        if (kb + 1 < nk) {
-            // the other stage was last read by block kb-1's MMAs
-            if (kb >= 1 && threadIdx.x == 0 && !mbar_wait(bar_a, (uint32_t)(kb - 1) & 1u)) *okp = 0u;
-            __syncthreads();
-            if (!*okp) break;
-            const uint32_t nx = s0 + (uint32_t)((kb + 1) & 1) * STAGE_BYTES;
-            load_stage(g, nx, nx + A_BYTES, m0, n0, (kb + 1) * UK);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
+        const uint32_t st = s0 + (uint32_t)(kb % STAGES) * STAGE_BYTES;
+        asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
         // make this thread's copies visible to the tensor cores' (async) proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -152,12 +150,27 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
                     "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
                     : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8u * (uint32_t)(kb % STAGES))
                          : "memory");
         }
+        // refill the stage block kb-1 used with block kb + STAGES - 1, once its MMAs are done
+        const int nx = kb + STAGES - 1;
+        if (nx < nk) {
+            if (kb >= 1 && threadIdx.x == 0 &&
+                !mbar_wait(bar0 + 8u * (uint32_t)((kb - 1) % STAGES), (uint32_t)((kb - 1) / STAGES) & 1u))
+                *okp = 0u;
+            __syncthreads();
+            if (!*okp) break;
+            const uint32_t sx = s0 + (uint32_t)(nx % STAGES) * STAGE_BYTES;
+            load_stage(g, sx, sx + A_BYTES, m0, n0, nx * UK);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (threadIdx.x == 0 && *okp && !mbar_wait(bar_a, (uint32_t)(nk - 1) & 1u)) *okp = 0u;
+    if (threadIdx.x == 0 && *okp &&
+        !mbar_wait(bar0 + 8u * (uint32_t)((nk - 1) % STAGES), (uint32_t)((nk - 1) / STAGES) & 1u))
+        *okp = 0u;
     __syncthreads();
     const bool ok = *okp != 0u;
     if (!ok && threadIdx.x == 0 && g.err) atomicOr(g.err, 1u);
