@@ -27,7 +27,6 @@ struct ExecArgs {
     uint32_t *out_bits;   // [H][wp] or null
     uint32_t item_begin, item_end;
     uint32_t use_queue;   // 1: dynamic queue with dependency waits; 0: static striding, no waits
-    uint32_t claim;       // queue items a CTA takes per atomic (run in order)
 };
 
 template <int NW, int WPL>
@@ -364,23 +363,11 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(Ex
     const RGroup *rgroups = reinterpret_cast<const RGroup *>(A.ws + hd.off_rgroups);
 
     uint32_t stride_next = A.item_begin + blockIdx.x;
-    // Queue claims: `claim` consecutive items per atomic, run in increasing
-    // order.  Every dependency points to a lower item, and every CTA runs its
-    // items in increasing order, so the lowest unfinished item can always run.
-    uint32_t claim_next = 0, claim_end = 0;   // thread 0's current claim
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t it;
             if (A.use_queue) {
-                if (*(volatile uint32_t *)&ctr->abort) {
-                    it = A.item_end;
-                } else {
-                    if (claim_next == claim_end) {
-                        claim_next = A.item_begin + atomicAdd(&ctr->head, A.claim);
-                        claim_end = claim_next + A.claim;
-                    }
-                    it = claim_next++;
-                }
+                it = *(volatile uint32_t *)&ctr->abort ? A.item_end : A.item_begin + atomicAdd(&ctr->head, 1u);
             } else {
                 it = stride_next;
             }
@@ -498,7 +485,6 @@ int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t
     if (bps < 1) return cudaErrorInvalidConfiguration;
     if (t.ctas_per_sm && (int)t.ctas_per_sm < bps) bps = (int)t.ctas_per_sm;
     ExecArgs A{};
-    A.claim = t.warps <= 2 ? 4u : 1u;   // small CTAs take several items per queue atomic
     A.kb = kb->view();
     A.ws = (uint8_t *)ws;
     A.counts = counts;

@@ -673,9 +673,9 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         k = k2;
     }
     for (uint32_t l = 1; l <= n_levels; ++l) level_items[l] = std::max(level_items[l], level_items[l - 1]);
-    if (items >= (1ull << 31)) {   // the queue head must not wrap when CTAs claim past the end
+    if (items >= 0xFFFFFFFFull) {
         delete p;
-        return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^31 work items");
+        return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^32 work items");
     }
 
     // image: header, tables, counters; then the slots
