@@ -385,11 +385,12 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
                 const float *prior, uint16_t *X, hedl_stream s);
 
-/* Engine of the two 512-wide dense layers' forward GEMMs:
- * HEDL_GEMM_TCGEN05 (default) runs them on the 5th-generation tensor cores
- * (tcgen05.mma, accumulators in tensor memory); HEDL_GEMM_MMA_SYNC on the
- * warp-level mma.sync path (the backward pass always uses mma.sync).  Both
- * accumulate in FP32 and store bf16 activations. */
+/* Engine of the 512-wide dense layers' GEMMs: HEDL_GEMM_TCGEN05 (default)
+ * runs the forward layers, and the backward pass's weight and activation
+ * gradients when the batch is a multiple of 32, on the 5th-generation tensor
+ * cores (tcgen05.mma, accumulators in tensor memory); HEDL_GEMM_MMA_SYNC on
+ * the warp-level mma.sync path.  Both accumulate in FP32 and store bf16
+ * activations and activation gradients. */
 #define HEDL_GEMM_TCGEN05  0u
 #define HEDL_GEMM_MMA_SYNC 1u
 int hedl_mlp_set_gemm(hedl_mlp *m, unsigned engine);

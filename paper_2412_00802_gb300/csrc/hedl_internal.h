@@ -190,6 +190,7 @@ struct UmmaArgs {
     int M, N, K, lda, ldb, ldc;
     int relu, out_bf16;
     uint32_t *err;
+    const void *mask;   // bf16 [M][ldc] or null: outputs where mask <= 0 become 0
 };
 bool umma_shape_ok(const UmmaArgs &a);
 int umma_gemm(const UmmaArgs &a, void *stream);

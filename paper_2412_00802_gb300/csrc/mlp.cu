@@ -411,6 +411,25 @@ __global__ void colsum_kernel(const __nv_bfloat16 *dH, float *db, int B, int D) 
 }
 
 // Adam on FP32 master weights; refreshes the BF16 copy.
+// dst[c][r] = src[r][c] for an R x C bf16 matrix (32 x 32 tiles through shared memory).
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *src, int R, int C, int lds, __nv_bfloat16 *dst, int ldd) {
+    __shared__ __nv_bfloat16 t[32][34];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = src[(size_t)r * lds + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) dst[(size_t)c * ldd + r] = t[threadIdx.x][i];
+    }
+}
+
+void transpose_bf16(const __nv_bfloat16 *src, int R, int C, int lds, __nv_bfloat16 *dst, int ldd, cudaStream_t s) {
+    transpose_bf16_kernel<<<dim3((C + 31) / 32, (R + 31) / 32), dim3(32, 8), 0, s>>>(src, R, C, lds, dst, ldd);
+}
+
 __global__ void adam_kernel(float *w, float *m, float *v, const float *g, __nv_bfloat16 *wb, size_t n, float lr,
                             float b1, float b2, float eps, float c1, float c2) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -554,6 +573,7 @@ struct hedl_mlp {
     // the target map (mean0, mean1, scale0, scale1, tail weight)
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *map = nullptr;
     uint32_t *err = nullptr;                  // device: bit 0 = a tensor-core wait timed out
+    __nv_bfloat16 *w2t = nullptr;             // W2 transposed ([in][out], bf16) for the backward GEMM
     unsigned gemm = HEDL_GEMM_TCGEN05;        // engine of the dense layers' forward GEMMs
     __nv_bfloat16 *wb = nullptr;
     size_t n = 0;
@@ -568,9 +588,10 @@ constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (size_t)DH * DI, OFF_W2 = OFF_B1 
 struct MlpWs {
     __nv_bfloat16 *h1, *h2, *dh1, *dh2;
     float *y, *dy, *loss;
+    __nv_bfloat16 *t0, *t1;   // transposed operands ([512][B]) of the tensor-core weight gradients
 };
 
-size_t mlp_ws_bytes(uint32_t B) { return 4 * (size_t)B * DH * 2 + 2 * (size_t)B * DO * 4 + 256 + 5 * 256; }
+size_t mlp_ws_bytes(uint32_t B) { return 6 * (size_t)B * DH * 2 + 2 * (size_t)B * DO * 4 + 256 + 7 * 256; }
 
 MlpWs carve(void *ws, uint32_t B) {
     uint8_t *p = (uint8_t *)ws;
@@ -587,6 +608,8 @@ MlpWs carve(void *ws, uint32_t B) {
     w.y = (float *)take((size_t)B * DO * 4);
     w.dy = (float *)take((size_t)B * DO * 4);
     w.loss = (float *)take(4);
+    w.t0 = (__nv_bfloat16 *)take((size_t)B * DH * 2);
+    w.t1 = (__nv_bfloat16 *)take((size_t)B * DH * 2);
     return w;
 }
 
@@ -596,7 +619,7 @@ uint32_t grid1(size_t n) { return (uint32_t)std::min<size_t>((n + 255) / 256, 40
 // shape allows it), else on the mma.sync GEMM.
 int dense_relu(hedl_mlp *mlp, const __nv_bfloat16 *A, const __nv_bfloat16 *W, const float *b, __nv_bfloat16 *H,
                int M, int K, cudaStream_t s) {
-    UmmaArgs u{A, W, H, b, M, DH, K, K, K, DH, 1, 1, mlp->err};
+    UmmaArgs u{A, W, H, b, M, DH, K, K, K, DH, 1, 1, mlp->err, nullptr};
     if (mlp->gemm == HEDL_GEMM_TCGEN05 && umma_shape_ok(u)) return umma_gemm(u, s);
     GemmArgs a{};
     a.A = A;
@@ -630,6 +653,28 @@ int grads_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, const float *T, uint32_t B
     out_bwd_dw_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dy, w.h2, mlp->g + OFF_W3, mlp->g + OFF_B3, (int)B);
     out_bwd_dh_kernel<<<grid1((size_t)B * DH), 256, 0, s>>>(w.dy, mlp->wb + OFF_W3, w.h2, w.dh2, (int)B);
     colsum_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dh2, mlp->g + OFF_B2, (int)B, DH);
+    if (mlp->gemm == HEDL_GEMM_TCGEN05 && B % 32 == 0) {
+        // Weight gradients dW = dH^T . H on tcgen05 as K-major products over the
+        // batch: both operands are transposed to [512][B] first.
+        transpose_bf16(w.dh2, (int)B, DH, DH, w.t0, (int)B, s);
+        transpose_bf16(w.h1, (int)B, DH, DH, w.t1, (int)B, s);
+        UmmaArgs u{w.t0, w.t1, mlp->g + OFF_W2, nullptr, DH, DH, (int)B, (int)B, (int)B, DH, 0, 0, mlp->err,
+                   nullptr};
+        e = umma_gemm(u, s);
+        if (e) return e;
+        // dH1 = (dH2 . W2) * [H1 > 0], with W2 kept transposed ([in][out], K-major)
+        UmmaArgs d{w.dh2, mlp->w2t, w.dh1, nullptr, (int)B, DH, DH, DH, DH, DH, 0, 1, mlp->err, w.h1};
+        e = umma_gemm(d, s);
+        if (e) return e;
+        colsum_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dh1, mlp->g + OFF_B1, (int)B, DH);
+        transpose_bf16(w.dh1, (int)B, DH, DH, w.t0, (int)B, s);
+        transpose_bf16(X, (int)B, DI, DI, w.t1, (int)B, s);
+        UmmaArgs x{w.t0, w.t1, mlp->g + OFF_W1, nullptr, DH, DI, (int)B, (int)B, (int)B, DI, 0, 0, mlp->err,
+                   nullptr};
+        e = umma_gemm(x, s);
+        if (e) return e;
+        return cudaGetLastError();
+    }
     const int splits = std::max(1, std::min((int)(B / 256), 64));
     // dW2 = dH2^T H1   (M = out, N = in, K = batch): A stored [K][M], B stored [K][N]
     GemmArgs a{};
@@ -678,6 +723,7 @@ int hedl_mlp_create(const float *params, hedl_mlp **out) {
     if (!e) e = cudaMalloc(&m->map, 5 * 4);
     if (!e) e = cudaMalloc(&m->err, 4);
     if (!e) e = cudaMemset(m->err, 0, 4);
+    if (!e) e = cudaMalloc(&m->w2t, (size_t)DH * DH * 2);
     if (!e) {
         const float ident[5] = {0.f, 0.f, 1.f, 1.f, 0.f};
         e = cudaMemcpy(m->map, ident, sizeof(ident), cudaMemcpyHostToDevice);
@@ -687,6 +733,7 @@ int hedl_mlp_create(const float *params, hedl_mlp **out) {
     if (!e) e = cudaMemset(m->v, 0, N_PARAMS * 4);
     if (!e) {
         to_bf16_kernel<<<grid1(N_PARAMS), 256>>>(m->w, m->wb, N_PARAMS);
+        transpose_bf16(m->wb + OFF_W2, DH, DH, DH, m->w2t, DH, 0);
         e = cudaDeviceSynchronize();
     }
     if (e) {
@@ -708,6 +755,7 @@ void hedl_mlp_free(hedl_mlp *m) {
     cudaFree(m->wb);
     cudaFree(m->map);
     cudaFree(m->err);
+    cudaFree(m->w2t);
     delete m;
 }
 
@@ -773,6 +821,7 @@ int hedl_mlp_train_step(hedl_mlp *m, const uint16_t *X, const float *T, uint32_t
     const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
     adam_kernel<<<grid1(N_PARAMS), 256, 0, (cudaStream_t)s>>>(m->w, m->m, m->v, m->g, m->wb, N_PARAMS, lr, b1, b2,
                                                                 1e-8f, c1, c2);
+    transpose_bf16(m->wb + OFF_W2, DH, DH, DH, m->w2t, DH, (cudaStream_t)s);
     cudaError_t ce = cudaGetLastError();
     return ce ? cuda_fail(ce, "adam launch") : HEDL_OK;
 }

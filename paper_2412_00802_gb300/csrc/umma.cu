@@ -9,7 +9,8 @@
 // thread issues two tcgen05.mma (M 128, N 256, K 16 each) per block and
 // commits them to the stage's mbarrier, which frees the stage for reuse.  The 128 x 256 FP32 accumulator lives
 // in 256 TMEM columns; the epilogue reads it back with tcgen05.ld (each warp
-// its 32 rows), adds the bias, applies ReLU and stores bf16 or FP32 rows.
+// its 32 rows), adds the bias, applies ReLU or a mask (the backward pass's
+// ReLU derivative) and stores bf16 or FP32 rows.
 //
 // Every wait is bounded: if a stage's MMAs do not complete within 2 s, the
 // CTA records an error in *err, skips the rest of its work and still frees
@@ -201,6 +202,21 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
                     if (g.relu) x = fmaxf(x, 0.f);
                     v[j] = x;
                 }
+                if (g.mask) {   // keep where the mask (e.g. the forward activation) is positive
+                    const uint4 *mk = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(g.mask) +
+                                                                      (size_t)row * g.ldc + n0 + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 m4 = mk[q];
+                        const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&mw[e]);
+                            if (!(__low2float(h) > 0.f)) v[q * 8 + 2 * e] = 0.f;
+                            if (!(__high2float(h) > 0.f)) v[q * 8 + 2 * e + 1] = 0.f;
+                        }
+                    }
+                }
                 if (g.out_bf16) {
                     uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) +
                                                            (size_t)row * g.ldc + n0 + c0);
@@ -234,7 +250,7 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
 bool umma_shape_ok(const UmmaArgs &a) {
     return a.N % UN == 0 && a.K % UK == 0 && a.K > 0 && a.lda % 8 == 0 && a.ldb % 8 == 0 &&
            a.ldc % (a.out_bf16 ? 8 : 4) == 0 && ((uintptr_t)a.A & 15) == 0 && ((uintptr_t)a.B & 15) == 0 &&
-           ((uintptr_t)a.C & 15) == 0;
+           ((uintptr_t)a.C & 15) == 0 && (!a.mask || (a.ldc % 8 == 0 && ((uintptr_t)a.mask & 15) == 0));
 }
 
 int umma_gemm(const UmmaArgs &a, void *stream) {

@@ -92,15 +92,20 @@ def test_tcgen05_forward_matches_mma_sync_and_oracle(env, B):
         H.hedl_mlp_set_gemm(s.mlp, 7)
 
 
-def test_gradients_match_oracle(env):
+@pytest.mark.parametrize("engine,B", [("tcgen05", 1024), ("mma_sync", 1024), ("tcgen05", 736), ("tcgen05", 700)])
+def test_gradients_match_oracle(env, engine, B):
+    """Weight gradients on tcgen05 (batches that are multiples of 32; 700 falls back to
+    mma.sync) and on mma.sync, against the oracle's."""
     torch, H, sg, kb = env
-    X, T = _xt(torch, kb, 1024, 4)
+    X, T = _xt(torch, kb, B, 4)
     p = sg.init_params(6)
     s = sg.Surrogate(p)
+    H.hedl_mlp_set_gemm(s.mlp, H.HEDL_GEMM_TCGEN05 if engine == "tcgen05" else H.HEDL_GEMM_MMA_SYNC)
     Xd = torch.from_numpy(X).to("cuda").to(torch.bfloat16)
     Td = torch.from_numpy(T).to("cuda")
     loss = torch.zeros(1, device="cuda")
-    H.hedl_mlp_gradients(s.mlp, Xd, Td, s._workspace(1024), loss)
+    H.hedl_mlp_gradients(s.mlp, Xd, Td, s._workspace(B), loss)
+    H.hedl_mlp_status(s.mlp)
     _, g, _ = H.hedl_mlp_get(s.mlp)
     ref_loss, ref = S.backward(sg.split_params(p), X, T, rounding=True)
     assert abs(float(loss.item()) - ref_loss) <= 1e-3 * abs(ref_loss)
