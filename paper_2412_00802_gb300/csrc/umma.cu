@@ -2,15 +2,17 @@
 // C[M][N] = act(A[M][K] . B[N][K]^T + bias), A and B bf16 and K-major (rows
 // of K contiguous elements), FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 4 warps computes a 128 x 256 tile.  K runs in blocks of 32: the
-// CTA's threads copy a block of A (128 x 32) and B (256 x 32) into shared
+// One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 32: the
+// CTA's threads copy a block of A (256 x 32) and B (256 x 32) into shared
 // memory with 16-byte async copies, laid out as 8-row x 16-byte core
 // matrices (no swizzle), three blocks ahead in a ring of four stages; one
-// thread issues two tcgen05.mma (M 128, N 256, K 16 each) per block and
-// commits them to the stage's mbarrier, which frees the stage for reuse.  The 128 x 256 FP32 accumulator lives
-// in 256 TMEM columns; the epilogue reads it back with tcgen05.ld (each warp
-// its 32 rows), adds the bias, applies ReLU or a mask (the backward pass's
-// ReLU derivative) and stores bf16 or FP32 rows.
+// thread issues four tcgen05.mma (M 128, N 256, K 16 each: two K steps times
+// the two 128-row halves of A, which share the B block) per block and
+// commits them to the stage's mbarrier, which frees the stage for reuse.  The
+// two 128 x 256 FP32 accumulators fill the SM's 512 TMEM columns (one CTA
+// per SM); the epilogue reads them back with tcgen05.ld (each warp its 32
+// rows of each half), adds the bias, applies ReLU or a mask (the backward
+// pass's ReLU derivative) and stores bf16 or FP32 rows.
 //
 // Every wait is bounded: if a stage's MMAs do not complete within 2 s, the
 // CTA records an error in *err, skips the rest of its work and still frees
@@ -23,20 +25,20 @@
 namespace hedl {
 namespace {
 
-constexpr int UM = 128, UN = 256, UK = 32, STAGES = 4;
+constexpr int UM = 256, UN = 256, UK = 32, STAGES = 4;   // two 128-row MMA halves per tile
 constexpr uint32_t KCH = UK / 8;                     // 16-byte K chunks per row and block
 constexpr uint32_t SBO = KCH * 128;                  // bytes between 8-row groups of a stage
-constexpr uint32_t A_BYTES = UM * UK * 2;            // 8 KB
+constexpr uint32_t A_BYTES = UM * UK * 2;            // 16 KB
 constexpr uint32_t B_BYTES = UN * UK * 2;            // 16 KB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 24 KB
-constexpr uint32_t TMEM_COLS = UN;                   // FP32 accumulator columns
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 32 KB
+constexpr uint32_t TMEM_COLS = 2 * UN;               // FP32 accumulators of the two halves
 constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 128;
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bit 17,
 // M / 16 at bit 24.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) |
-                           ((uint32_t)(UM >> 4) << 24);
+                           ((uint32_t)(128 >> 4) << 24);
 
 // Shared-memory matrix descriptor of a K-major operand without swizzle:
 // start address / 16, leading byte offset (next 8 K-elements: 128 B) / 16,
@@ -142,14 +144,18 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int s = 0; s < UK / 16; ++s) {
-                const uint64_t ad = smem_desc(st + (uint32_t)s * 256u);
                 const uint64_t bd = smem_desc(st + A_BYTES + (uint32_t)s * 256u);
                 const uint32_t acc = (kb > 0 || s > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
-                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-                    : "memory");
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {   // rows 128h.. of the tile into accumulator columns 256h..
+                    const uint64_t ad = smem_desc(st + (uint32_t)h * (16u * SBO) + (uint32_t)s * 256u);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                            taddr + (uint32_t)h * UN),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        : "memory");
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              bar0 + 8u * (uint32_t)(kb % STAGES))
@@ -177,11 +183,11 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
     if (!ok && threadIdx.x == 0 && g.err) atomicOr(g.err, 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (ok) {
-        const int row = m0 + (int)(warp * 32 + lane);
+    for (int h = 0; ok && h < 2; ++h) {
+        const int row = m0 + h * 128 + (int)(warp * 32 + lane);
         for (int c0 = 0; c0 < UN; c0 += 32) {
             uint32_t r[32];
-            const uint32_t ta = taddr + ((warp * 32u) << 16) + (uint32_t)c0;
+            const uint32_t ta = taddr + ((warp * 32u) << 16) + (uint32_t)(h * UN + c0);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
