@@ -162,14 +162,14 @@ class ClockSampler:
 
 def traffic_for(workload_key: str, tuning: dict):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    kernel build with the same launch shape."""
+    interpreter sources with the same launch shape."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         from paper_2412_00802_gb300 import build
         with open(p) as f:
             d = json.load(f)
         e = d.get(workload_key)
-        if e and e.get("build_digest") == build._digest() and e.get("tuning") == tuning:
+        if e and e.get("interpreter_digest") == build.interpreter_digest() and e.get("tuning") == tuning:
             return e["dram_bytes_per_launch"]
     except Exception:
         pass

@@ -26,6 +26,21 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I", os.path.join(ROOT, "include")]
 
 
+# the files that define the batched interpreter (its kernels and the plans it runs)
+INTERPRETER = ["exec.cu", "device_common.cuh", "hedl_internal.h", "plan.cpp"]
+
+
+def interpreter_digest() -> str:
+    """Digest of the interpreter's sources and build flags (recorded ncu counters stay valid
+    while it is unchanged)."""
+    h = hashlib.sha256()
+    for f in INTERPRETER:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def _digest() -> str:
     h = hashlib.sha256()
     for f in SOURCES + HEADERS:

@@ -2,21 +2,25 @@
 // C[M][N] = act(A[M][K] . B[N][K]^T + bias), A and B bf16 and K-major (rows
 // of K contiguous elements), FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 32: the
-// CTA's threads copy a block of A (256 x 32) and B (256 x 32) into shared
-// memory with 16-byte async copies, laid out as 8-row x 16-byte core
-// matrices (no swizzle), three blocks ahead in a ring of four stages; one
-// thread issues four tcgen05.mma (M 128, N 256, K 16 each: two K steps times
-// the two 128-row halves of A, which share the B block) per block and
-// commits them to the stage's mbarrier, which frees the stage for reuse.  The
-// two 128 x 256 FP32 accumulators fill the SM's 512 TMEM columns (one CTA
-// per SM); the epilogue reads them back with tcgen05.ld (each warp its 32
-// rows of each half), adds the bias, applies ReLU or a mask (the backward
-// pass's ReLU derivative) and stores bf16 or FP32 rows.
+// One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 32
+// through a ring of six shared-memory stages.  Warp 0 is the producer: one of
+// its threads loads each block of A (256 x 32) and B (256 x 32) with TMA
+// (cp.async.bulk.tensor, one 8-column x 256-row box per 16-byte K chunk, so
+// shared memory receives 8-row x 16-byte core matrices, no swizzle) and
+// signals the stage's "full" mbarrier through the copies' byte count.  Warp
+// 1 is the MMA issuer: one thread waits for a full stage, issues four
+// tcgen05.mma (M 128, N 256, K 16 each: two K steps times the two 128-row
+// halves of A, which share the B block) and commits them to the stage's
+// "empty" mbarrier, which hands the stage back to the producer.  The two
+// 128 x 256 FP32 accumulators fill the SM's 512 TMEM columns (one CTA per
+// SM); the epilogue (all warps) reads them back with tcgen05.ld, each warp
+// its 32 rows of each half, adds the bias, applies ReLU or a mask (the
+// backward pass's ReLU derivative) and stores bf16 or FP32 rows.
 //
-// Every wait is bounded: if a stage's MMAs do not complete within 2 s, the
-// CTA records an error in *err, skips the rest of its work and still frees
-// its TMEM.
+// Every wait is bounded: a wait that does not complete within 2 s records an
+// error in *err; the CTA then skips the rest of its work and still frees its
+// TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -25,14 +29,14 @@
 namespace hedl {
 namespace {
 
-constexpr int UM = 256, UN = 256, UK = 32, STAGES = 4;   // two 128-row MMA halves per tile
+constexpr int UM = 256, UN = 256, UK = 32, STAGES = 6;
 constexpr uint32_t KCH = UK / 8;                     // 16-byte K chunks per row and block
-constexpr uint32_t SBO = KCH * 128;                  // bytes between 8-row groups of a stage
+constexpr uint32_t CHUNK = 256 * 16;                 // bytes of one chunk of 256 rows
 constexpr uint32_t A_BYTES = UM * UK * 2;            // 16 KB
 constexpr uint32_t B_BYTES = UN * UK * 2;            // 16 KB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 32 KB
 constexpr uint32_t TMEM_COLS = 2 * UN;               // FP32 accumulators of the two halves
-constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 128;
+constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bit 17,
@@ -40,23 +44,19 @@ constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 128;
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
 
-// Shared-memory matrix descriptor of a K-major operand without swizzle:
-// start address / 16, leading byte offset (next 8 K-elements: 128 B) / 16,
-// stride byte offset (next 8 rows: SBO) / 16, descriptor version 1.
+// Shared-memory matrix descriptor of a K-major operand without swizzle, in
+// the TMA layout above: start address / 16, leading byte offset (next 8
+// K-elements: one chunk, 4096 B) / 16, stride byte offset (next 8 rows:
+// 128 B) / 16, descriptor version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(SBO >> 4) << 32;
+    d |= (uint64_t)(CHUNK >> 4) << 16;
+    d |= (uint64_t)(128u >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-                 : "memory");
-}
 
 __device__ __forceinline__ uint64_t now_ns() {
     uint64_t t;
@@ -74,44 +74,44 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits (one thread) until the barrier's phase of this parity completed; false after 2 s.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits (one thread) until the barrier's phase of this parity completed, or
+// the CTA gave up (*okp cleared elsewhere); false after 2 s or on give-up.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t *okp) {
     const uint64_t t0 = now_ns();
     for (uint32_t i = 0;; ++i) {
         if (mbar_try(bar, parity)) return true;
-        if ((i & 255u) == 255u && now_ns() - t0 > 2000000000ull) return false;
+        if ((i & 255u) == 255u && (!*okp || now_ns() - t0 > 2000000000ull)) return false;
     }
 }
 
-// Stage one K block: A rows m0.. (zero past M), B rows n0.., 16 bytes a thread per copy.
-__device__ __forceinline__ void load_stage(const UmmaArgs &g, uint32_t sA, uint32_t sB, int m0, int n0, int k0) {
-    for (int c = threadIdx.x; c < UM * (int)KCH; c += blockDim.x) {
-        const int r = c / (int)KCH, kc = c % (int)KCH;
-        const bool ok = m0 + r < g.M;
-        const __nv_bfloat16 *src =
-            reinterpret_cast<const __nv_bfloat16 *>(g.A) + (size_t)(ok ? m0 + r : 0) * g.lda + k0 + kc * 8;
-        cp16(sA + (uint32_t)((r >> 3) * SBO + kc * 128 + (r & 7) * 16), src, ok);
-    }
-    for (int c = threadIdx.x; c < UN * (int)KCH; c += blockDim.x) {
-        const int r = c / (int)KCH, kc = c % (int)KCH;
-        const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(g.B) + (size_t)(n0 + r) * g.ldb + k0 + kc * 8;
-        cp16(sB + (uint32_t)((r >> 3) * SBO + kc * 128 + (r & 7) * 16), src, true);
-    }
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
-__global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
+__global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                   const __grid_constant__ CUtensorMap tmB, UmmaArgs g) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);     // one per stage
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(base + STAGES * STAGE_BYTES + 64);
-    uint32_t *okp = reinterpret_cast<uint32_t *>(base + STAGES * STAGE_BYTES + 80);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile uint32_t *okp = tslot + 1;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const int n0 = blockIdx.x * UN, m0 = blockIdx.y * UM;
-    const uint32_t s0 = smem_u32(base), bar0 = smem_u32(bar);
+    const uint32_t s0 = smem_u32(base);
+    const uint32_t full0 = smem_u32(full), empty0 = smem_u32(empty), done_a = smem_u32(done);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * i) : "memory");
+        for (int i = 0; i < STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * i) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8u * i) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_a) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *okp = 1u;
     }
@@ -125,30 +125,44 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = *tslot;
-
-    // Block kb lives in stage kb % STAGES and its MMAs commit to that stage's
-    // barrier (the stage's (kb / STAGES)-th phase).  Copies run STAGES - 1
-    // blocks ahead; one async-copy group is committed per block (empty past K).
     const int nk = g.K / UK;
-    for (int i = 0; i < STAGES - 1; ++i) {
-        if (i < nk) load_stage(g, s0 + i * STAGE_BYTES, s0 + i * STAGE_BYTES + A_BYTES, m0, n0, i * UK);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    for (int kb = 0; kb < nk; ++kb) {
-        const uint32_t st = s0 + (uint32_t)(kb % STAGES) * STAGE_BYTES;
-        asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
-        // make this thread's copies visible to the tensor cores' (async) proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
+
+    if (warp == 0 && lane == 0) {
+        // producer: block kb into stage kb % STAGES once the MMAs of block kb - STAGES released it
+        for (int kb = 0; kb < nk; ++kb) {
+            const int st = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(empty0 + 8u * st, (uint32_t)((kb - STAGES) / STAGES) & 1u, okp)) {
+                *okp = 0u;
+                break;
+            }
+            const uint32_t fb = full0 + 8u * st, sa = s0 + (uint32_t)st * STAGE_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES)
+                         : "memory");
+#pragma unroll
+            for (uint32_t kc = 0; kc < KCH; ++kc) {
+                tma_2d(sa + kc * CHUNK, &tmA, kb * UK + (int)kc * 8, m0, fb);
+                tma_2d(sa + A_BYTES + kc * CHUNK, &tmB, kb * UK + (int)kc * 8, n0, fb);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        bool good = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int st = kb % STAGES;
+            if (!mbar_wait(full0 + 8u * st, (uint32_t)(kb / STAGES) & 1u, okp)) {
+                *okp = 0u;
+                good = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = s0 + (uint32_t)st * STAGE_BYTES;
 #pragma unroll
             for (int s = 0; s < UK / 16; ++s) {
-                const uint64_t bd = smem_desc(st + A_BYTES + (uint32_t)s * 256u);
+                const uint64_t bd = smem_desc(sa + A_BYTES + (uint32_t)s * 2u * CHUNK);
                 const uint32_t acc = (kb > 0 || s > 0) ? 1u : 0u;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // rows 128h.. of the tile into accumulator columns 256h..
-                    const uint64_t ad = smem_desc(st + (uint32_t)h * (16u * SBO) + (uint32_t)s * 256u);
+                    const uint64_t ad = smem_desc(sa + (uint32_t)h * 128u * 16u + (uint32_t)s * 2u * CHUNK);
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -158,26 +172,15 @@ __global__ void __launch_bounds__(128) umma_kernel(UmmaArgs g) {
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             bar0 + 8u * (uint32_t)(kb % STAGES))
+                             empty0 + 8u * st)
                          : "memory");
         }
-        // refill the stage block kb-1 used with block kb + STAGES - 1, once its MMAs are done
-        const int nx = kb + STAGES - 1;
-        if (nx < nk) {
-            if (kb >= 1 && threadIdx.x == 0 &&
-                !mbar_wait(bar0 + 8u * (uint32_t)((kb - 1) % STAGES), (uint32_t)((kb - 1) / STAGES) & 1u))
-                *okp = 0u;
-            __syncthreads();
-            if (!*okp) break;
-            const uint32_t sx = s0 + (uint32_t)(nx % STAGES) * STAGE_BYTES;
-            load_stage(g, sx, sx + A_BYTES, m0, n0, nx * UK);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (good)   // every MMA issued so far completes before this arrives
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done_a)
+                         : "memory");
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (threadIdx.x == 0 && *okp &&
-        !mbar_wait(bar0 + 8u * (uint32_t)((nk - 1) % STAGES), (uint32_t)((nk - 1) / STAGES) & 1u))
-        *okp = 0u;
+    __syncwarp();
+    if (threadIdx.x == 0 && *okp && !mbar_wait(done_a, 0u, okp)) *okp = 0u;
     __syncthreads();
     const bool ok = *okp != 0u;
     if (!ok && threadIdx.x == 0 && g.err) atomicOr(g.err, 1u);
@@ -259,6 +262,41 @@ bool umma_shape_ok(const UmmaArgs &a) {
            ((uintptr_t)a.C & 15) == 0 && (!a.mask || (a.ldc % 8 == 0 && ((uintptr_t)a.mask & 15) == 0));
 }
 
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 8-column x 256-row
+// boxes, no swizzle, rows past the end read as zeros.
+bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld) {
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, 256};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 int umma_gemm(const UmmaArgs &a, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (!umma_shape_ok(a)) return (int)cudaErrorInvalidValue;
@@ -269,8 +307,11 @@ int umma_gemm(const UmmaArgs &a, void *stream) {
         if (e) return (int)e;
         attr = true;
     }
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, a.A, a.M, a.K, a.lda) || !make_map(&tb, a.B, a.N, a.K, a.ldb))
+        return (int)cudaErrorInvalidValue;
     dim3 grid((unsigned)(a.N / UN), (unsigned)((a.M + UM - 1) / UM));
-    umma_kernel<<<grid, 128, UMMA_SMEM, s>>>(a);
+    umma_kernel<<<grid, 128, UMMA_SMEM, s>>>(ta, tb, a);
     return (int)cudaGetLastError();
 }
 
