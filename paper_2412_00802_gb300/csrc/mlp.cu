@@ -289,27 +289,55 @@ int gemm(const GemmArgs &a0, bool a_km, bool b_kn, int splits, cudaStream_t s) {
 // raw output u is mapped back to the target scale: Y = u * scale + mean.
 __global__ void out_fwd_kernel(const __nv_bfloat16 *H2, const __nv_bfloat16 *W3, const float *b3, float *Y, int B,
                                const float *map) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= B) return;
-    float s0 = 0.f, s1 = 0.f;
-    for (int i = lane; i < DH; i += 32) {
-        const float h = __bfloat162float(H2[(size_t)warp * DH + i]);
-        s0 += h * __bfloat162float(W3[i]);
-        s1 += h * __bfloat162float(W3[DH + i]);
-    }
+    // warp per row (grid-stride); lane l holds columns 16l .. 16l+15 of both W3 rows
+    const int lane = threadIdx.x & 31;
+    float w0[16], w1[16];
+    {
+        const uint4 *p0 = reinterpret_cast<const uint4 *>(W3 + 16 * lane);
+        const uint4 *p1 = reinterpret_cast<const uint4 *>(W3 + DH + 16 * lane);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
-        s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-    }
-    if (lane == 0) {
-        float u0 = s0 + b3[0], u1 = s1 + b3[1];
-        if (map) {
-            u0 = u0 * map[2] + map[0];
-            u1 = u1 * map[3] + map[1];
+        for (int q = 0; q < 2; ++q) {
+            const uint4 a = p0[q], c = p1[q];
+            const uint32_t av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&av[e]);
+                const __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&cv[e]);
+                w0[q * 8 + 2 * e] = __low2float(x), w0[q * 8 + 2 * e + 1] = __high2float(x);
+                w1[q * 8 + 2 * e] = __low2float(y), w1[q * 8 + 2 * e + 1] = __high2float(y);
+            }
         }
-        Y[2 * warp] = u0;
-        Y[2 * warp + 1] = u1;
+    }
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < B; row += warps) {
+        const uint4 *h = reinterpret_cast<const uint4 *>(H2 + (size_t)row * DH + 16 * lane);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint4 a = h[q];
+            const uint32_t av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&av[e]);
+                const float lo = __low2float(x), hi = __high2float(x);
+                s0 += lo * w0[q * 8 + 2 * e] + hi * w0[q * 8 + 2 * e + 1];
+                s1 += lo * w1[q * 8 + 2 * e] + hi * w1[q * 8 + 2 * e + 1];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
+            s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+        }
+        if (lane == 0) {
+            float u0 = s0 + b3[0], u1 = s1 + b3[1];
+            if (map) {
+                u0 = u0 * map[2] + map[0];
+                u1 = u1 * map[3] + map[1];
+            }
+            Y[2 * row] = u0;
+            Y[2 * row + 1] = u1;
+        }
     }
 }
 
@@ -637,8 +665,8 @@ int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs 
     if (e) return e;
     e = dense_relu(mlp, w.h1, mlp->wb + OFF_W2, mlp->w + OFF_B2, w.h2, (int)B, DH, s);
     if (e) return e;
-    out_fwd_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B,
-                                                        mapped ? mlp->map : nullptr);
+    out_fwd_kernel<<<std::min<uint32_t>((B * 32 + 255) / 256, 148u * 8u), 256, 0, s>>>(
+        w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B, mapped ? mlp->map : nullptr);
     return cudaGetLastError();
 }
 

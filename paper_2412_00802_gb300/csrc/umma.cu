@@ -4,10 +4,11 @@
 //
 // One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 32
 // through a ring of six shared-memory stages.  Warp 0 is the producer: one of
-// its threads loads each block of A (256 x 32) and B (256 x 32) with TMA
-// (cp.async.bulk.tensor, one 8-column x 256-row box per 16-byte K chunk, so
-// shared memory receives 8-row x 16-byte core matrices, no swizzle) and
-// signals the stage's "full" mbarrier through the copies' byte count.  Warp
+// its threads loads each block of A (256 x 32) and B (256 x 32) with one TMA
+// copy each (cp.async.bulk.tensor, a 32-column x 256-row box: 64-byte rows
+// in the 64-byte swizzle pattern the tensor cores read as K-major
+// SWIZZLE_64B operands) and signals the stage's "full" mbarrier through the
+// copies' byte count.  Warp
 // 1 is the MMA issuer: one thread waits for a full stage, issues four
 // tcgen05.mma (M 128, N 256, K 16 each: two K steps times the two 128-row
 // halves of A, which share the B block) and commits them to the stage's
@@ -30,8 +31,7 @@ namespace hedl {
 namespace {
 
 constexpr int UM = 256, UN = 256, UK = 32, STAGES = 6;
-constexpr uint32_t KCH = UK / 8;                     // 16-byte K chunks per row and block
-constexpr uint32_t CHUNK = 256 * 16;                 // bytes of one chunk of 256 rows
+constexpr uint32_t ROW = UK * 2;                     // 64-byte rows of a block
 constexpr uint32_t A_BYTES = UM * UK * 2;            // 16 KB
 constexpr uint32_t B_BYTES = UN * UK * 2;            // 16 KB
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 32 KB
@@ -44,15 +44,17 @@ constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
 
-// Shared-memory matrix descriptor of a K-major operand without swizzle, in
-// the TMA layout above: start address / 16, leading byte offset (next 8
-// K-elements: one chunk, 4096 B) / 16, stride byte offset (next 8 rows:
-// 128 B) / 16, descriptor version 1.
+// Shared-memory matrix descriptor of a K-major SWIZZLE_64B operand (64-byte
+// rows as TMA wrote them): start address / 16 (a K step of 16 elements
+// advances it by 32 bytes inside the swizzle atom), leading byte offset
+// unused (1), stride byte offset (next 8 rows: 512 B) / 16, descriptor
+// version 1, layout type 4 (64-byte swizzle).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(CHUNK >> 4) << 16;
-    d |= (uint64_t)(128u >> 4) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((8u * ROW) >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
     return d;
 }
 
@@ -138,11 +140,8 @@ __global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUten
             const uint32_t fb = full0 + 8u * st, sa = s0 + (uint32_t)st * STAGE_BYTES;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES)
                          : "memory");
-#pragma unroll
-            for (uint32_t kc = 0; kc < KCH; ++kc) {
-                tma_2d(sa + kc * CHUNK, &tmA, kb * UK + (int)kc * 8, m0, fb);
-                tma_2d(sa + A_BYTES + kc * CHUNK, &tmB, kb * UK + (int)kc * 8, n0, fb);
-            }
+            tma_2d(sa, &tmA, kb * UK, m0, fb);
+            tma_2d(sa + A_BYTES, &tmB, kb * UK, n0, fb);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -158,11 +157,11 @@ __global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUten
             const uint32_t sa = s0 + (uint32_t)st * STAGE_BYTES;
 #pragma unroll
             for (int s = 0; s < UK / 16; ++s) {
-                const uint64_t bd = smem_desc(sa + A_BYTES + (uint32_t)s * 2u * CHUNK);
+                const uint64_t bd = smem_desc(sa + A_BYTES + (uint32_t)s * 32u);
                 const uint32_t acc = (kb > 0 || s > 0) ? 1u : 0u;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {   // rows 128h.. of the tile into accumulator columns 256h..
-                    const uint64_t ad = smem_desc(sa + (uint32_t)h * 128u * 16u + (uint32_t)s * 2u * CHUNK);
+                    const uint64_t ad = smem_desc(sa + (uint32_t)h * 128u * ROW + (uint32_t)s * 32u);
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -281,17 +280,17 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 8-column x 256-row
-// boxes, no swizzle, rows past the end read as zeros.
+// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 32-column x 256-row
+// boxes in the 64-byte swizzle, rows past the end read as zeros.
 bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld) {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {8, 256};
+    const cuuint32_t box[2] = {(cuuint32_t)UK, 256};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
