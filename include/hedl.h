@@ -387,7 +387,7 @@ int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const f
 
 /* Engine of the 512-wide dense layers' GEMMs: HEDL_GEMM_TCGEN05 (default)
  * runs the forward layers, and the backward pass's weight and activation
- * gradients when the batch is a multiple of 32, on the 5th-generation tensor
+ * gradients when the batch is a multiple of 64, on the 5th-generation tensor
  * cores (tcgen05.mma, accumulators in tensor memory); HEDL_GEMM_MMA_SYNC on
  * the warp-level mma.sync path.  Both accumulate in FP32 and store bf16
  * activations and activation gradients. */

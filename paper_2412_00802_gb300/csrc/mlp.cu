@@ -681,7 +681,7 @@ int grads_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, const float *T, uint32_t B
     out_bwd_dw_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dy, w.h2, mlp->g + OFF_W3, mlp->g + OFF_B3, (int)B);
     out_bwd_dh_kernel<<<grid1((size_t)B * DH), 256, 0, s>>>(w.dy, mlp->wb + OFF_W3, w.h2, w.dh2, (int)B);
     colsum_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dh2, mlp->g + OFF_B2, (int)B, DH);
-    if (mlp->gemm == HEDL_GEMM_TCGEN05 && B % 32 == 0) {
+    if (mlp->gemm == HEDL_GEMM_TCGEN05 && B % 64 == 0) {
         // Weight gradients dW = dH^T . H on tcgen05 as K-major products over the
         // batch: both operands are transposed to [512][B] first.
         transpose_bf16(w.dh2, (int)B, DH, DH, w.t0, (int)B, s);

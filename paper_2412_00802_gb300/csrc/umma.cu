@@ -2,15 +2,15 @@
 // C[M][N] = act(A[M][K] . B[N][K]^T + bias), A and B bf16 and K-major (rows
 // of K contiguous elements), FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 32
-// through a ring of six shared-memory stages.  Warp 0 is the producer: one of
-// its threads loads each block of A (256 x 32) and B (256 x 32) with one TMA
-// copy each (cp.async.bulk.tensor, a 32-column x 256-row box: 64-byte rows
-// in the 64-byte swizzle pattern the tensor cores read as K-major
-// SWIZZLE_64B operands) and signals the stage's "full" mbarrier through the
+// One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 64
+// through a ring of three shared-memory stages.  Warp 0 is the producer: one
+// of its threads loads each block of A (256 x 64) and B (256 x 64) with one
+// TMA copy each (cp.async.bulk.tensor, a 64-column x 256-row box: 128-byte
+// rows in the 128-byte swizzle pattern the tensor cores read as K-major
+// SWIZZLE_128B operands) and signals the stage's "full" mbarrier through the
 // copies' byte count.  Warp
-// 1 is the MMA issuer: one thread waits for a full stage, issues four
-// tcgen05.mma (M 128, N 256, K 16 each: two K steps times the two 128-row
+// 1 is the MMA issuer: one thread waits for a full stage, issues eight
+// tcgen05.mma (M 128, N 256, K 16 each: four K steps times the two 128-row
 // halves of A, which share the B block) and commits them to the stage's
 // "empty" mbarrier, which hands the stage back to the producer.  The two
 // 128 x 256 FP32 accumulators fill the SM's 512 TMEM columns (one CTA per
@@ -30,11 +30,11 @@
 namespace hedl {
 namespace {
 
-constexpr int UM = 256, UN = 256, UK = 32, STAGES = 6;
-constexpr uint32_t ROW = UK * 2;                     // 64-byte rows of a block
-constexpr uint32_t A_BYTES = UM * UK * 2;            // 16 KB
-constexpr uint32_t B_BYTES = UN * UK * 2;            // 16 KB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 32 KB
+constexpr int UM = 256, UN = 256, UK = 64, STAGES = 3;
+constexpr uint32_t ROW = UK * 2;                     // 128-byte rows of a block
+constexpr uint32_t A_BYTES = UM * UK * 2;            // 32 KB
+constexpr uint32_t B_BYTES = UN * UK * 2;            // 32 KB
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 64 KB
 constexpr uint32_t TMEM_COLS = 2 * UN;               // FP32 accumulators of the two halves
 constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 
@@ -44,17 +44,17 @@ constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
 
-// Shared-memory matrix descriptor of a K-major SWIZZLE_64B operand (64-byte
-// rows as TMA wrote them): start address / 16 (a K step of 16 elements
-// advances it by 32 bytes inside the swizzle atom), leading byte offset
-// unused (1), stride byte offset (next 8 rows: 512 B) / 16, descriptor
-// version 1, layout type 4 (64-byte swizzle).
+// Shared-memory matrix descriptor of a K-major SWIZZLE_128B operand
+// (128-byte rows as TMA wrote them): start address / 16 (a K step of 16
+// elements advances it by 32 bytes inside the swizzle atom), leading byte
+// offset unused (1), stride byte offset (next 8 rows: 1024 B) / 16,
+// descriptor version 1, layout type 2 (128-byte swizzle).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
     d |= (uint64_t)((8u * ROW) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -280,8 +280,8 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 32-column x 256-row
-// boxes in the 64-byte swizzle, rows past the end read as zeros.
+// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 64-column x 256-row
+// boxes in the 128-byte swizzle, rows past the end read as zeros.
 bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld) {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
@@ -290,7 +290,7 @@ bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld) {
     const cuuint32_t box[2] = {(cuuint32_t)UK, 256};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
