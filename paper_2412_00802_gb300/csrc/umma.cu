@@ -94,6 +94,63 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int
         : "memory");
 }
 
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta)
+        : "memory");
+}
+
+// Epilogue of 32 columns of one row: bias, ReLU or mask, bf16 or FP32 store.
+__device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, const uint32_t (&r)[32]) {
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        float x = __uint_as_float(r[j]);
+        if (g.bias) x += g.bias[col + j];
+        if (g.relu) x = fmaxf(x, 0.f);
+        v[j] = x;
+    }
+    if (g.mask) {   // keep where the mask (e.g. the forward activation) is positive
+        const uint4 *mk =
+            reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(g.mask) + (size_t)row * g.ldc + col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 m4 = mk[q];
+            const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&mw[e]);
+                if (!(__low2float(h) > 0.f)) v[q * 8 + 2 * e] = 0.f;
+                if (!(__high2float(h) > 0.f)) v[q * 8 + 2 * e + 1] = 0.f;
+            }
+        }
+    }
+    if (g.out_bf16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + (size_t)row * g.ldc + col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
+                w[e] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) + (size_t)row * g.ldc + col);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+}
+
 __global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUtensorMap tmA,
                                                    const __grid_constant__ CUtensorMap tmB, UmmaArgs g) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -187,63 +244,15 @@ __global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUten
 
     for (int h = 0; ok && h < 2; ++h) {
         const int row = m0 + h * 128 + (int)(warp * 32 + lane);
-        for (int c0 = 0; c0 < UN; c0 += 32) {
-            uint32_t r[32];
+        for (int c0 = 0; c0 < UN; c0 += 64) {   // two 32-column loads in flight per wait
+            uint32_t ra[32], rb[32];
             const uint32_t ta = taddr + ((warp * 32u) << 16) + (uint32_t)(h * UN + c0);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(ta)
-                : "memory");
+            tmem_ld32(ta, ra);
+            tmem_ld32(ta + 32u, rb);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (row < g.M) {
-                float v[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    float x = __uint_as_float(r[j]);
-                    if (g.bias) x += g.bias[n0 + c0 + j];
-                    if (g.relu) x = fmaxf(x, 0.f);
-                    v[j] = x;
-                }
-                if (g.mask) {   // keep where the mask (e.g. the forward activation) is positive
-                    const uint4 *mk = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(g.mask) +
-                                                                      (size_t)row * g.ldc + n0 + c0);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint4 m4 = mk[q];
-                        const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&mw[e]);
-                            if (!(__low2float(h) > 0.f)) v[q * 8 + 2 * e] = 0.f;
-                            if (!(__high2float(h) > 0.f)) v[q * 8 + 2 * e + 1] = 0.f;
-                        }
-                    }
-                }
-                if (g.out_bf16) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) +
-                                                           (size_t)row * g.ldc + n0 + c0);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const __nv_bfloat162 h = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
-                            w[e] = *reinterpret_cast<const uint32_t *>(&h);
-                        }
-                        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
-                } else {
-                    float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) + (size_t)row * g.ldc +
-                                                             n0 + c0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                }
+                emit32(g, row, n0 + c0, ra);
+                emit32(g, row, n0 + c0 + 32, rb);
             }
         }
     }
