@@ -232,6 +232,7 @@ def surrogate_round(args, dev):
     t0 = time.perf_counter()
     Xs, Ts = [], []
     s = sg.Surrogate(seed=4, device=str(dev), grid=sg.threshold_grid(kb.prop_vals))
+    s.fit_statistics(dkb, kb.n_concepts)      # the KB's per-symbol exact scores (an encoder input)
     for b in range(n_train // B):
         flat, offs = _pack(hyps.batch_hyps(kb, 404, b, B, gen=tg))
         _, T = sg.exact_scores(dkb, flat, offs)
@@ -305,6 +306,7 @@ def search_run(args, dev):
     steps = 20 if full else 10
     from paper_2412_00802_gb300.surrogate import threshold_grid
     sur = Surrogate(seed=5, device=str(dev), grid=threshold_grid(kb.prop_vals))
+    sur.fit_statistics(dkb, kb.n_concepts)
     tg = hyps.TreeGen(kb, 506, share=0.3)
     Xs, Ts = [], []
     for b in range(8):
@@ -326,6 +328,7 @@ def search_run(args, dev):
         if "online_epochs" in kw:     # each surrogate run starts from the same pre-trained network
             net = Surrogate(params=state, device=str(dev), grid=threshold_grid(kb.prop_vals))
             net.set_target_map(tmap)
+            net.stats, net.n_stat_concepts = sur.stats, sur.n_stat_concepts
             kw = dict(kw, surrogate=net)
         t0 = time.perf_counter()
         beam, logs = BeamSearch(dkb, refine, width=64, per_step=8192, batch=batch, **kw).run(start, steps)

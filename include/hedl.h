@@ -375,15 +375,25 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
  * 0..509 are integer counts scaled by 1/4: op histogram per depth, atomic
  * concepts, roles, restriction kinds per depth, cardinalities, >= / <=
  * restrictions by property and threshold bucket, role-over-atom pairs,
- * length, totals, a constant; concepts, thresholds and role-over-atom pairs
- * count -1 at odd polarity (under an odd number of NOT / ATMOST).  grid (DEVICE float [n_grid][15], or NULL)
- * holds each property's 15 increasing threshold boundaries: a threshold t of
- * property p lands in bucket #{g < t}.  prior (DEVICE float [H][2], or NULL
- * for zeros) gives features 510-511 per program, rounded to bf16 (the search
- * passes the exact accuracy and F1 of the hypothesis a candidate refines).
- * Instructions that are not op codes are ignored.  Asynchronous. */
+ * length, sums of the symbols' statistics, totals, a constant; concepts,
+ * thresholds, role-over-atom pairs and statistics count -1 at odd polarity
+ * (under an odd number of NOT / ATMOST).  grid (DEVICE float [n_grid][15],
+ * or NULL) holds each property's 15 increasing threshold boundaries: a
+ * threshold t of property p lands in bucket q = #{g < t}.  stats (DEVICE
+ * int32, or NULL for zeros) holds n_stat_concepts atom scores, then
+ * n_grid x 2 x 16 scores of (property, >= / <=, bucket), as written by
+ * hedl_stat_scores from the engine's exact scores of those symbols.  prior
+ * (DEVICE float [H][2], or NULL for zeros) gives features 510-511 per
+ * program, rounded to bf16 (the search passes the exact accuracy and F1 of
+ * the hypothesis a candidate refines).  Instructions that are not op codes
+ * are ignored.  Asynchronous. */
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
-                const float *prior, uint16_t *X, hedl_stream s);
+                const int32_t *stats, uint32_t n_stat_concepts, const float *prior, uint16_t *X, hedl_stream s);
+
+/* Statistics table entries (DEVICE int32 [n]) from exact scores (DEVICE
+ * float [n][2], accuracy first): round((accuracy - 1/2) * 32), computed in
+ * double, ties to even.  Asynchronous. */
+int hedl_stat_scores(const float *scores, uint32_t n, int32_t *out, hedl_stream s);
 
 /* Engine of the 512-wide dense layers' GEMMs: HEDL_GEMM_TCGEN05 (default)
  * runs the forward layers, and the backward pass's weight and activation

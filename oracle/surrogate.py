@@ -32,8 +32,14 @@ supplied with the programs; q = 0 without a grid or for NaN t).
   [244,284) role-restriction kind per depth: min(depth, 7)*5 + (op - EXISTS)
   [284,308) cardinality: (op - ATLEAST)*8 + min(n, 7)
   [308,436) >= and <= restrictions, signed: ((property id mod 16)*2 + (op - DGE))*4 + q // 4
-  [436,500) role restriction over an atom, signed: ((role*2 + inverse)*131 + concept) mod 64
-  [500,504) length bucket: min(len, 39) // 10
+  [436,493) role restriction over an atom, signed: ((role*2 + inverse)*131 + concept) mod 57
+  [493,497) length bucket: min(len, 39) // 10
+  [497,504) statistics, signed sums of the KB's own per-symbol scores (a table
+            the caller computes with the engine; 0 without one): atoms by
+            depth bucket min(depth // 2, 2) (497-499), >= / <= restrictions
+            by depth bucket (500-502) with the score of their (property,
+            compare, threshold bucket q), the atom fillers of role
+            restrictions (503)
   [504,508) counts of leaves, role restrictions, data restrictions, NOTs
   [508]     height - 1 (clamped to 7)
   [509]     constant 4 (a bias input; 4 * 1/4 = 1)
@@ -64,11 +70,13 @@ def _arity(op: int) -> int:
     return 0
 
 
-def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
+def encode(prog: Sequence[int], grid=None, prior=None, stats=None) -> np.ndarray:
     """Structural encoding of one postfix program (float32[512]).
 
     grid: per-property threshold boundaries, float32 [n_props][15], or None.
     prior: two floats (features 510, 511), or None.
+    stats: (atom_scores int[n_concepts], threshold_scores int[n_props][2][16])
+    or None; a symbol outside the tables scores 0.
     A program longer than 256 instructions is encoded by its last 256 (the
     root and the nodes nearest to it)."""
     prog = list(prog)[-256:]
@@ -88,6 +96,14 @@ def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
         child_pol = pl ^ 1 if op in (_NOT, _MAX) else pl
         for _ in range(_arity(op)):
             pending.append((d + 1, child_pol))
+    atoms_t, thr_t = (None, None) if stats is None else stats
+
+    def atom_score(c):
+        return int(atoms_t[c]) if atoms_t is not None and c < len(atoms_t) else 0
+
+    def thr_score(p, o, q):
+        return int(thr_t[p][o][q]) if thr_t is not None and p < len(thr_t) else 0
+
     f = np.zeros(D_IN, dtype=np.int64)
     leaves = roles = datas = nots = 0
     for k in range(L):
@@ -99,6 +115,7 @@ def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
             leaves += 1
         if op == _ATOM:
             f[84 + a % 96] += sign
+            f[497 + min(depth[k] // 2, 2)] += sign * atom_score(a)
         elif _EX <= op <= _EXACT:
             roles += 1
             f[180 + (a % 32) * 2 + inv] += 1
@@ -107,7 +124,9 @@ def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
                 f[284 + (op - _MIN) * 8 + min(b, 7)] += 1
             child = int(prog[k - 1])       # the filler ends right before its restriction
             if child & 0xFF == _ATOM:
-                f[436 + ((a * 2 + inv) * 131 + ((child >> 16) & 0xFFFF)) % 64] += sign
+                c = (child >> 16) & 0xFFFF
+                f[436 + ((a * 2 + inv) * 131 + c) % 57] += sign
+                f[503] += sign * atom_score(c)
         elif _GE <= op <= _EQ:
             datas += 1
             if op != _EQ:
@@ -116,9 +135,10 @@ def encode(prog: Sequence[int], grid=None, prior=None) -> np.ndarray:
                 if grid is not None and a < len(grid) and not np.isnan(t):
                     q = int(np.sum(np.asarray(grid[a], np.float32) < t))
                 f[308 + ((a % 16) * 2 + (op - _GE)) * 4 + q // 4] += sign
+                f[500 + min(depth[k] // 2, 2)] += sign * thr_score(a, op - _GE, q)
         elif op == _NOT:
             nots += 1
-    f[500 + min(L, 39) // 10] += 1
+    f[493 + min(L, 39) // 10] += 1
     f[504] += leaves
     f[505] += roles
     f[506] += datas
@@ -141,11 +161,17 @@ def threshold_grid(prop_vals: np.ndarray) -> np.ndarray:
     return out
 
 
-def encode_batch(progs: Sequence[Sequence[int]], grid=None, prior=None) -> np.ndarray:
-    """prior: float [H][2] or None."""
+def encode_batch(progs: Sequence[Sequence[int]], grid=None, prior=None, stats=None) -> np.ndarray:
+    """prior: float [H][2] or None; stats as for ``encode``."""
     if not len(progs):
         return np.zeros((0, D_IN), np.float32)
-    return np.stack([encode(p, grid, None if prior is None else prior[i]) for i, p in enumerate(progs)])
+    return np.stack([encode(p, grid, None if prior is None else prior[i], stats) for i, p in enumerate(progs)])
+
+
+def stat_score(acc: float) -> int:
+    """Table entry of a symbol whose exact accuracy on the examples is acc: round((acc - 1/2) * 32),
+    ties to even (float64)."""
+    return int(np.rint((np.float64(acc) - 0.5) * 32.0))
 
 
 # ---------------------------------------------------------------------------- bfloat16

@@ -49,7 +49,8 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
            "hedl_mlp_gradients", "hedl_mlp_train_step", "hedl_scores_from_counts", "hedl_select_workspace_size",
            "hedl_select_top", "hedl_canonical_batch", "hedl_mlp_fit_target_map", "hedl_mlp_set_target_map",
-           "hedl_mlp_get_target_map", "hedl_mlp_set_gemm", "hedl_mlp_status", "hedl_last_error")
+           "hedl_mlp_get_target_map", "hedl_mlp_set_gemm", "hedl_mlp_status", "hedl_stat_scores",
+           "hedl_last_error")
 
 
 class HedlError(RuntimeError):
@@ -124,7 +125,8 @@ def library(path: Optional[str] = None):
             "hedl_mlp_free": (None, [P]),
             "hedl_mlp_get": (I, [P, P, P, ctypes.POINTER(U32)]),
             "hedl_mlp_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
-            "hedl_encode": (I, [P, P, U32, P, U32, P, P, P]),
+            "hedl_encode": (I, [P, P, U32, P, U32, P, U32, P, P, P]),
+            "hedl_stat_scores": (I, [P, U32, P, P]),
             "hedl_mlp_forward": (I, [P, P, U32, P, P, ctypes.c_size_t, P]),
             "hedl_mlp_gradients": (I, [P, P, P, U32, P, P, ctypes.c_size_t, P]),
             "hedl_mlp_train_step": (I, [P, P, P, U32, ctypes.c_float, P, P, ctypes.c_size_t, P]),
@@ -426,12 +428,19 @@ def hedl_mlp_workspace_size(B: int) -> int:
     return out.value
 
 
-def hedl_encode(progs_dev, offs_dev, X, grid=None, prior=None, stream=None):
+def hedl_encode(progs_dev, offs_dev, X, grid=None, prior=None, stats=None, n_stat_concepts=0, stream=None):
     """progs_dev: CUDA int64 tensor of instructions; offs_dev: CUDA int32 [H+1]; X: CUDA bf16 [H][512];
-    grid: CUDA float32 [n_props][15] threshold boundaries or None; prior: CUDA float32 [H][2] or None."""
+    grid: CUDA float32 [n_props][15] threshold boundaries or None; prior: CUDA float32 [H][2] or None;
+    stats: CUDA int32 statistics table (n_stat_concepts atom scores, then n_props x 2 x 16) or None."""
     H = offs_dev.numel() - 1
     _check(library().hedl_encode(_dptr(progs_dev), _dptr(offs_dev), H, _dptr(grid),
-                                 0 if grid is None else grid.shape[0], _dptr(prior), _dptr(X), _stream(stream)))
+                                 0 if grid is None else grid.shape[0], _dptr(stats), n_stat_concepts, _dptr(prior),
+                                 _dptr(X), _stream(stream)))
+
+
+def hedl_stat_scores(scores, out, stream=None):
+    """out (CUDA int32 [n]) = round((scores[:, 0] - 1/2) * 32) for exact scores (CUDA float32 [n][2])."""
+    _check(library().hedl_stat_scores(_dptr(scores), scores.shape[0], _dptr(out), _stream(stream)))
 
 
 def hedl_mlp_forward(m: MLPHandle, X, Y, ws, stream=None):

@@ -42,12 +42,13 @@ constexpr int ENC_MAXLEN = 256;
 //   [  0, 84) op x min(depth, 5)          [ 84,180) concept mod 96, signed
 //   [180,244) role mod 32 x inverse       [244,284) restriction kind x depth
 //   [284,308) cardinality                 [308,436) property mod 16 x (>=, <=) x bucket / 4, signed
-//   [436,500) role-over-atom hash mod 64, signed
-//   [500,504) length / 10                 [504,510) totals, height, constant
-//   [510,512) prior
+//   [436,493) role-over-atom hash mod 57, signed
+//   [493,497) length / 10                 [497,504) statistics sums, signed
+//   [504,510) totals, height, constant    [510,512) prior
+// stats (or null): n_sc atom scores, then n_grid x 2 x 16 threshold scores.
 __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t *__restrict__ offs, uint32_t H,
-                              const float *__restrict__ grid, uint32_t n_grid, const float *__restrict__ prior,
-                              __nv_bfloat16 *__restrict__ X) {
+                              const float *__restrict__ grid, uint32_t n_grid, const int32_t *__restrict__ stats,
+                              uint32_t n_sc, const float *__restrict__ prior, __nv_bfloat16 *__restrict__ X) {
     constexpr int WARPS = 4;
     __shared__ int feat[WARPS][DI];
     __shared__ uint8_t depth[WARPS][ENC_MAXLEN];
@@ -95,6 +96,7 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             if (arity_of(op) == 0) atomicAdd(&feat[warp][504], 1);
             if (op == HEDL_OP_ATOM) {
                 atomicAdd(&feat[warp][84 + a % 96], sign);
+                if (stats && a < n_sc) atomicAdd(&feat[warp][497 + min(dk / 2, 2u)], sign * stats[a]);
             } else if (op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY) {
                 atomicAdd(&feat[warp][505], 1);
                 atomicAdd(&feat[warp][180 + (a % 32) * 2 + inv], 1);
@@ -102,8 +104,11 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
                 if (op >= HEDL_OP_ATLEAST) atomicAdd(&feat[warp][284 + (op - HEDL_OP_ATLEAST) * 8 + min(b, 7u)], 1);
                 if (k > 0) {   // the filler ends right before its restriction
                     const uint64_t c = progs[o0 + k - 1];
-                    if ((c & 0xFF) == HEDL_OP_ATOM)
-                        atomicAdd(&feat[warp][436 + ((a * 2 + inv) * 131 + (uint32_t)((c >> 16) & 0xFFFF)) % 64], sign);
+                    if ((c & 0xFF) == HEDL_OP_ATOM) {
+                        const uint32_t cc = (uint32_t)((c >> 16) & 0xFFFF);
+                        atomicAdd(&feat[warp][436 + ((a * 2 + inv) * 131 + cc) % 57], sign);
+                        if (stats && cc < n_sc) atomicAdd(&feat[warp][503], sign * stats[cc]);
+                    }
                 }
             } else if (op >= HEDL_OP_DGE) {
                 atomicAdd(&feat[warp][506], 1);
@@ -113,6 +118,9 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
                     if (grid && a < n_grid && !(t != t))
                         for (int g = 0; g < 15; ++g) q += grid[a * 15 + g] < t ? 1u : 0u;
                     atomicAdd(&feat[warp][308 + ((a % 16) * 2 + (op - HEDL_OP_DGE)) * 4 + q / 4], sign);
+                    if (stats && a < n_grid)
+                        atomicAdd(&feat[warp][500 + min(dk / 2, 2u)],
+                                  sign * stats[n_sc + (a * 2 + (op - HEDL_OP_DGE)) * 16 + q]);
                 }
             } else if (op == HEDL_OP_NOT) {
                 atomicAdd(&feat[warp][507], 1);
@@ -120,7 +128,7 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
         }
         __syncwarp();
         if (lane == 0) {
-            feat[warp][500 + min(L, 39u) / 10] += 1;
+            feat[warp][493 + min(L, 39u) / 10] += 1;
             feat[warp][508] += (int)min(height[warp], 8u) - 1;
             feat[warp][509] += 4;
         }
@@ -478,6 +486,12 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, size_t n) {
 }
 
 // accuracy = (TP + TN) / (|P| + |N|), F1 = 2TP / (2TP + FP + FN) (0 if the denominator is 0)
+// Statistics table entries from exact scores: round((accuracy - 1/2) * 32), in double.
+__global__ void stat_kernel(const float *scores, uint32_t n, int32_t *out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (int32_t)rint(((double)scores[2 * i] - 0.5) * 32.0);
+}
+
 __global__ void scores_kernel(const uint32_t *counts, uint32_t H, float *T) {
     for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < H; h += gridDim.x * blockDim.x) {
         const uint4 c = reinterpret_cast<const uint4 *>(counts)[h];
@@ -806,11 +820,12 @@ int hedl_mlp_workspace_size(uint32_t B, size_t *bytes) {
 }
 
 int hedl_encode(const uint64_t *progs, const uint32_t *offs, uint32_t H, const float *grid, uint32_t n_grid,
-                const float *prior, uint16_t *X, hedl_stream s) {
+                const int32_t *stats, uint32_t n_stat_concepts, const float *prior, uint16_t *X, hedl_stream s) {
     if (!progs || !offs || !X) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    if (stats && !grid && n_grid) return fail(HEDL_ERR_INVALID_ARG, "threshold statistics need the grid");
     if (H == 0) return HEDL_OK;
     encode_kernel<<<std::min<uint32_t>((H + 3) / 4, 8192), 128, 0, (cudaStream_t)s>>>(
-        progs, offs, H, grid, grid ? n_grid : 0u, prior, (__nv_bfloat16 *)X);
+        progs, offs, H, grid, grid ? n_grid : 0u, stats, stats ? n_stat_concepts : 0u, prior, (__nv_bfloat16 *)X);
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(e, "encode launch") : HEDL_OK;
 }
@@ -897,6 +912,14 @@ int hedl_mlp_get_target_map(const hedl_mlp *m, float *map) {
     if (!m || !map) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = cudaMemcpy(map, m->map, 5 * 4, cudaMemcpyDeviceToHost);
     return e ? cuda_fail(e, "get map") : HEDL_OK;
+}
+
+int hedl_stat_scores(const float *scores, uint32_t n, int32_t *out, hedl_stream s) {
+    if (!scores || !out) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return HEDL_OK;
+    stat_kernel<<<grid1(n), 256, 0, (cudaStream_t)s>>>(scores, n, out);
+    cudaError_t e = cudaGetLastError();
+    return e ? cuda_fail(e, "stat launch") : HEDL_OK;
 }
 
 int hedl_scores_from_counts(const uint32_t *counts, uint32_t H, float *scores, hedl_stream s) {

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import (DeviceKB, hedl_encode, hedl_mlp_create, hedl_mlp_fit_target_map, hedl_mlp_forward, hedl_mlp_get,
                hedl_mlp_get_target_map, hedl_mlp_param_count, hedl_mlp_set_target_map,
-               hedl_mlp_train_step, hedl_mlp_workspace_size, hedl_plan_batch, hedl_plan_execute,
+               hedl_mlp_train_step, hedl_mlp_workspace_size, hedl_plan_batch, hedl_plan_execute, hedl_stat_scores,
                hedl_plan_info_get, hedl_scores_from_counts, hedl_select_top, hedl_select_workspace_size,
                hedl_sync_status)
 
@@ -63,6 +63,9 @@ class Surrogate:
         self.device = torch.device(device)
         self.mlp = hedl_mlp_create(init_params(seed) if params is None else params)
         self.grid = None if grid is None else torch.from_numpy(np.ascontiguousarray(grid, np.float32)).to(self.device)
+        self._grid_host = None if grid is None else np.ascontiguousarray(grid, np.float32)
+        self.stats = None            # device int32 statistics table (see fit_statistics)
+        self.n_stat_concepts = 0
         self._ws = None
 
     def _workspace(self, B: int):
@@ -74,6 +77,31 @@ class Surrogate:
     def params(self) -> np.ndarray:
         return hedl_mlp_get(self.mlp)[0]
 
+    def statistic_programs(self, n_concepts: int) -> list:
+        """The symbols the statistics table scores: every atom, then every (property, >= / <=,
+        threshold bucket q) at the bucket's upper boundary (above the last boundary for q = 15)."""
+        from synth import programs as P
+        out = [np.array([P.insn(P.ATOM, 0, c)], np.uint64) for c in range(n_concepts)]
+        g = self._grid_host if self._grid_host is not None else np.zeros((0, 15), np.float32)
+        for p in range(g.shape[0]):
+            for op in (P.DGE, P.DLE):
+                for q in range(16):
+                    t = g[p][q] if q < 15 else np.nextafter(g[p][14], np.float32(np.inf))
+                    out.append(np.array([P.insn(op, 0, p, P.f32_bits(float(t)))], np.uint64))
+        return out
+
+    def fit_statistics(self, dkb: DeviceKB, n_concepts: int):
+        """Score the statistic programs exactly with the engine and keep their table entries."""
+        torch = self.torch
+        progs = self.statistic_programs(n_concepts)
+        flat = np.concatenate(progs)
+        offs = np.arange(len(progs) + 1, dtype=np.uint32)
+        _, T = exact_scores(dkb, flat, offs)
+        self.stats = torch.empty(len(progs), dtype=torch.int32, device=self.device)
+        hedl_stat_scores(T, self.stats)
+        self.n_stat_concepts = n_concepts
+        return self.stats
+
     def encode(self, progs: np.ndarray, offs: np.ndarray, prior: Optional[np.ndarray] = None):
         """bf16 [H][512] encodings of host programs (copied to the device first); prior: float
         [H][2] per-program inputs (features 510-511) or None."""
@@ -82,7 +110,7 @@ class Surrogate:
         o = torch.from_numpy(np.ascontiguousarray(offs, np.uint32).view(np.int32)).to(self.device)
         pr = None if prior is None else torch.from_numpy(np.ascontiguousarray(prior, np.float32)).to(self.device)
         X = torch.empty((len(offs) - 1, D_IN), dtype=torch.bfloat16, device=self.device)
-        hedl_encode(p, o, X, self.grid, pr)
+        hedl_encode(p, o, X, self.grid, pr, self.stats, self.n_stat_concepts)
         return X
 
     def predict(self, X, batch: int = 65536):

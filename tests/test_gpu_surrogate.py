@@ -46,6 +46,16 @@ def test_encoder_bit_exact(env):
     prior = np.random.default_rng(7).uniform(size=(len(progs), 2)).astype(np.float32)
     got = sg.Surrogate(grid=grid).encode(flat, offs, prior).float().cpu().numpy()
     assert np.array_equal(got, S.encode_batch(progs, grid, prior))
+    # with a statistics table (values large enough for bf16 rounding of the sums)
+    rng = np.random.default_rng(8)
+    atoms = rng.integers(-16, 17, size=kb.n_concepts)
+    thr = rng.integers(-16, 17, size=(kb.n_props, 2, 16))
+    s = sg.Surrogate(grid=grid)
+    s.stats = torch.from_numpy(np.concatenate([atoms, thr.reshape(-1)]).astype(np.int32)).to("cuda")
+    s.n_stat_concepts = kb.n_concepts
+    got = s.encode(flat, offs, prior).float().cpu().numpy()
+    assert np.array_equal(got, S.encode_batch(progs, grid, prior, (atoms, thr)))
+    assert np.abs(got[:, 497:504]).max() > 0
     assert np.array_equal(grid, sg.threshold_grid(kb.prop_vals))
 
 
@@ -164,6 +174,15 @@ def test_train_step_matches_oracle_adam(env):
         dr = ref_p[name] - sg.split_params(p)[name]
         agree = np.mean(np.sign(du) == np.sign(dr))
         assert agree >= 0.95, (name, agree)
+
+
+def test_stat_scores_exact(env):
+    torch, H, sg, kb = env
+    acc = np.concatenate([np.random.default_rng(3).uniform(size=997), [0.5, 0.515625, 0.484375, 0.0, 1.0]])
+    sc = np.stack([acc, acc], 1).astype(np.float32)
+    out = torch.empty(len(acc), dtype=torch.int32, device="cuda")
+    H.hedl_stat_scores(torch.from_numpy(sc).to("cuda"), out)
+    assert out.cpu().numpy().tolist() == [S.stat_score(a) for a in sc[:, 0]]
 
 
 def test_scores_from_counts_exact(env):

@@ -19,18 +19,18 @@ def test_encoding_hand_worked():
     # (and A1 (some r2- A3)), postfix A1 A3 EXISTS AND: AND depth 0; A1, EXISTS depth 1; A3 depth 2;
     # every node has polarity 0 (signed counts +1)
     f = S.encode(P.compile_text("(and A1 (some r2- A3))"))
-    assert ((2 * 2 + 1) * 131 + 3) % 64 == 18
+    assert ((2 * 2 + 1) * 131 + 3) % 57 == 31
     assert np.array_equal(f, _want({0 * 14 + 4: 1, 1 * 14 + 0: 1, 1 * 14 + 6: 1, 2 * 14 + 0: 1,   # op x depth
                                     84 + 1: 1, 84 + 3: 1,                 # concepts 1 and 3
                                     180 + 2 * 2 + 1: 1,                   # role 2 inverted
                                     244 + 1 * 5 + 0: 1,                   # EXISTS at depth 1
-                                    436 + 18: 1,                          # role 2^- over atom 3
-                                    500 + 4 // 10: 1,                     # length 4
+                                    436 + 31: 1,                          # role 2^- over atom 3
+                                    493 + 4 // 10: 1,                     # length 4
                                     504: 2, 505: 1, 508: 3 - 1, 509: 4}))  # leaves, roles, height, bias
     # (min 3 r0 (ge p9 1.0)): ATLEAST depth 0, DGE depth 1; property 9, >=, bucket 0 without a grid
     f = S.encode(P.compile_text("(min 3 r0 (ge p9 1.0))"))
     assert np.array_equal(f, _want({0 * 14 + 8: 1, 1 * 14 + 11: 1, 180 + 0: 1, 244 + 2: 1, 284 + 0 * 8 + 3: 1,
-                                    308 + (9 * 2 + 0) * 4 + 0: 1, 500: 1, 504: 1, 505: 1, 506: 1, 508: 1,
+                                    308 + (9 * 2 + 0) * 4 + 0: 1, 493: 1, 504: 1, 505: 1, 506: 1, 508: 1,
                                     509: 4}))
     # with a grid, 1.0 lies above 7 of property 9's 15 boundaries (0.3 .. 1.7 step 0.1, 1.0 excluded):
     # bucket 7, feature bucket 7 // 4 = 1
@@ -41,17 +41,31 @@ def test_encoding_hand_worked():
     assert g[308 + 18 * 4 + 1] == 0.25 and g[308 + 18 * 4] == 0.0
     # polarity: (not (and A1 (max 2 r1 A50))), postfix A1 A50 ATMOST AND NOT.  NOT puts the
     # conjunction and its operands at polarity 1 (count -1); ATMOST flips again, A50 is at 0.
-    assert ((1 * 2) * 131 + 50) % 64 == 56
+    assert ((1 * 2) * 131 + 50) % 57 == 27
     f = S.encode(P.compile_text("(not (and A1 (max 2 r1 A50)))"))
     assert np.array_equal(f, _want({0 * 14 + 3: 1, 1 * 14 + 4: 1, 2 * 14 + 0: 1, 2 * 14 + 9: 1, 3 * 14 + 0: 1,
                                     84 + 1: -1, 84 + 50: 1,
                                     180 + 1 * 2: 1, 244 + 2 * 5 + 3: 1, 284 + 1 * 8 + 2: 1,
-                                    436 + 56: -1,                          # the restriction sits at polarity 1
-                                    500 + 5 // 10: 1, 504: 2, 505: 1, 507: 1, 508: 4 - 1, 509: 4}))
+                                    436 + 27: -1,                          # the restriction sits at polarity 1
+                                    493 + 5 // 10: 1, 504: 2, 505: 1, 507: 1, 508: 4 - 1, 509: 4}))
     # seven nested NOTs over A0: depths 0..6 and 7, op x depth clamps depth at 5, A0 at polarity 1
     f = S.encode(P.compile_text("(not " * 7 + "A0" + ")" * 7))
     assert np.array_equal(f, _want({**{d * 14 + 3: 1 for d in range(5)}, 5 * 14 + 3: 2, 5 * 14 + 0: 1,
-                                    84 + 0: -1, 500: 1, 504: 1, 507: 7, 508: 7, 509: 4}))
+                                    84 + 0: -1, 493: 1, 504: 1, 507: 7, 508: 7, 509: 4}))
+    # statistics: atom scores summed by depth bucket with the polarity sign, threshold scores of
+    # (property, compare, bucket), the atom fillers of role restrictions
+    atoms = np.array([0, 7, 0, -3], np.int64)
+    thr = np.zeros((10, 2, 16), np.int64)
+    thr[9, 0, 7] = 5
+    st = (atoms, thr)
+    f = S.encode(P.compile_text("(and A1 (some r2- A3))"), None, None, st)
+    # A1 depth 1 -> bucket 0: +7; A3 depth 2 -> bucket 1: -3; role filler A3: -3
+    assert f[497] == 0.25 * 7 and f[498] == 0.25 * -3 and f[503] == 0.25 * -3 and f[499] == 0
+    g = S.encode(P.compile_text("(not (min 3 r0 (ge p9 1.0)))"), grid, None, st)
+    # the DGE sits at depth 2 (bucket 1) under one NOT: -5
+    assert g[501] == 0.25 * -5 and g[500] == 0 and g[502] == 0
+    assert np.array_equal(S.encode(P.compile_text("(ge p9 1.0)"), grid, None, None)[497:504], np.zeros(7))
+    assert S.stat_score(0.80095) == 10 and S.stat_score(0.5) == 0 and S.stat_score(0.0) == -16
     # a prior lands in features 510 and 511, rounded to bfloat16 and not scaled
     g = S.encode(P.compile_text("A0"), None, (0.8125, 0.3))
     assert g[510] == np.float32(0.8125) and g[511] == np.float32(0.30078125)
