@@ -178,7 +178,7 @@ def traffic_for(workload_key: str, tuning: dict):
 
 def make_workload(seed_kb: int = 3):
     from synth import kb as K
-    return K.generate(K.CONFIGS["c3"])
+    return K.generate(K.CONFIGS["batch"])
 
 
 def make_batch(kb, idx: int, gen=None, count: int = None):
@@ -221,7 +221,7 @@ def surrogate_round(args, dev):
     from oracle import surrogate as OS
     from synth import hyps, kb as K
     full = args.surrogate_full
-    cfg = K.CONFIGS["c4"] if full else K.CONFIGS["c4"].scaled(1_000_000)
+    cfg = K.CONFIGS["surrogate"] if full else K.CONFIGS["surrogate"].scaled(1_000_000)
     t0 = time.perf_counter()
     kb = K.generate(cfg)
     gen_s = time.perf_counter() - t0
@@ -293,7 +293,7 @@ def search_run(args, dev):
     from synth import hyps, kb as K, programs as P
     from synth.refine import Refiner
     full = args.search_full
-    cfg = K.CONFIGS["c5"] if full else K.CONFIGS["c5"].scaled(1_000_000)
+    cfg = K.CONFIGS["search"] if full else K.CONFIGS["search"].scaled(1_000_000)
     t0 = time.perf_counter()
     kb = K.generate(cfg)
     gen_s = time.perf_counter() - t0
@@ -368,7 +368,7 @@ def run_latency(args, local_rank):
     dev = torch.device("cuda", local_rank)
     build.build()
     t0 = time.perf_counter()
-    cfg = K.CONFIGS["c2"]
+    cfg = K.CONFIGS["large"]
     if args.latency_n:                       # smaller KB of the same distributions (profiling)
         cfg = cfg.scaled(args.latency_n)
     kb = K.generate(cfg)
@@ -443,7 +443,7 @@ def run_mlp(args, local_rank):
     from synth import hyps, kb as K, programs as P
     torch.cuda.set_device(local_rank)
     build.build()
-    kb = K.generate(K.CONFIGS["c4"].scaled(20_000))
+    kb = K.generate(K.CONFIGS["surrogate"].scaled(20_000))
     progs = hyps.batch_hyps(kb, 77, 0, 65_536, gen=hyps.TreeGen(kb, 77, share=0.3))
     s = sg.Surrogate(seed=1, device=f"cuda:{local_rank}", grid=sg.threshold_grid(kb.prop_vals))
     X = s.encode(*P.pack_batch(progs))
@@ -558,7 +558,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     model = [infos[i]["model_bytes"] for i in timed_ids]
     achieved = statistics.mean(m / (t / 1000.0) for m, t in zip(model, launch_ms)) / 1e9
-    traffic = traffic_for("c3_batch", H.hedl_tuning_get(dkb.handle))
+    traffic = traffic_for("batch", H.hedl_tuning_get(dkb.handle))
 
     # ---- end to end through the public C ABI from host programs: each step plans a batch
     # on the host (hedl_plan_batch), uploads and launches it (hedl_plan_execute) and copies

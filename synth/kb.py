@@ -108,19 +108,19 @@ class KBConfig:
 
 CONFIGS = {
     # plain single-hypothesis evaluation on a small KB
-    "c1": KBConfig("c1", 1, 10_000, 50, 0.02, 0.30, True, 8, ("poisson", 3.0), 4,
+    "small": KBConfig("small", 1, 10_000, 50, 0.02, 0.30, True, 8, ("poisson", 3.0), 4,
                    ("uniform", 0.0, 100.0), 0.20, 200, 200),
     # single large hypothesis latency
-    "c2": KBConfig("c2", 2, 10_000_000, 200, 0.01, 0.50, False, 32, ("zipf", 2.1, 8.0, 10_000), 16,
+    "large": KBConfig("large", 2, 10_000_000, 200, 0.01, 0.50, False, 32, ("zipf", 2.1, 8.0, 10_000), 16,
                    ("lognormal", 0.0, 1.0), 0.10, 100_000, 100_000),
     # batched exact evaluation
-    "c3": KBConfig("c3", 3, 1_000_000, 100, 0.01, 0.50, False, 16, ("poisson", 6.0), 8,
+    "batch": KBConfig("batch", 3, 1_000_000, 100, 0.01, 0.50, False, 16, ("poisson", 6.0), 8,
                    ("uniform", 0.0, 1000.0), 0.0, 10_000, 10_000),
     # refinement search
-    "c5": KBConfig("c5", 5, 4_000_000, 300, 0.01, 0.50, False, 64, ("zipf", 2.3, 10.0, 10_000), 32,
+    "search": KBConfig("search", 5, 4_000_000, 300, 0.01, 0.50, False, 64, ("zipf", 2.3, 10.0, 10_000), 32,
                    ("normal", 50.0, 15.0), 0.15, 50_000, 50_000, planted=True),
 }
-CONFIGS["c4"] = replace(CONFIGS["c2"], name="c4", seed=4, planted=True)
+CONFIGS["surrogate"] = replace(CONFIGS["large"], name="surrogate", seed=4, planted=True)
 
 # Planted structure (workloads that search or learn need a signal): a latent
 # class Z (a uniform 20 % of the individuals) supplies the positives, its

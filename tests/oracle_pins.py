@@ -101,7 +101,7 @@ def random_program(r: Rng, kb: K.KB, depth: int, role_free: bool = False) -> P.N
 
 
 def tiny_kbs():
-    base = K.CONFIGS["c1"]
+    base = K.CONFIGS["small"]
     out = []
     for seed, n, deg in ((101, 20, ("poisson", 2.0)), (102, 33, ("poisson", 3.0)), (103, 40, ("poisson", 4.0)),
                          (104, 17, ("zipf", 2.1, 3.0, 16))):
@@ -149,7 +149,7 @@ def _identities(x: str, y: str, r: str, n: int) -> List[tuple]:
 
 
 def identity_kb(n: int = 600):
-    cfg = K.CONFIGS["c1"].scaled(n, seed=31, n_concepts=8, n_roles=3)
+    cfg = K.CONFIGS["small"].scaled(n, seed=31, n_concepts=8, n_roles=3)
     return K.generate(cfg)
 
 
@@ -202,7 +202,7 @@ def pin_inverse_transpose(L, kb=None) -> List[str]:
 
 def pin_closed_forms(L) -> List[str]:
     bad = []
-    base = K.CONFIGS["c1"]
+    base = K.CONFIGS["small"]
     # unique subject: role r is a permutation pi (a -> pi(a))
     kb = K.generate(base.scaled(257, seed=41, n_concepts=4, n_roles=1, degree=("unique",)))
     okb = oracle.from_synth(kb)

@@ -33,7 +33,7 @@ def _check_sample(kb, dkb, progs, sample):
 
 def test_single_hypothesis_workload_full_size():
     import paper_2412_00802_gb300 as H
-    kb = K.generate(K.CONFIGS["c2"])
+    kb = K.generate(K.CONFIGS["large"])
     dkb = H.DeviceKB.from_synth(kb)
     progs = hyps.chain_hyps(kb, 2002, 64)
     _check_sample(kb, dkb, progs, [0, 13, 31, 63])
@@ -41,7 +41,7 @@ def test_single_hypothesis_workload_full_size():
 
 def test_search_workload_kb_full_size():
     import paper_2412_00802_gb300 as H
-    kb = K.generate(K.CONFIGS["c5"])
+    kb = K.generate(K.CONFIGS["search"])
     dkb = H.DeviceKB.from_synth(kb)
     progs = hyps.batch_hyps(kb, 5005, 0, 512, lmax=24, dmax=6)
     _check_sample(kb, dkb, progs, [0, 100, 333, 511])

@@ -40,52 +40,52 @@ def test_hand_worked_fixtures(name):
 
 
 @pytest.fixture(scope="module")
-def c1():
-    return K.generate(K.CONFIGS["c1"])
+def small():
+    return K.generate(K.CONFIGS["small"])
 
 
 @pytest.fixture(scope="module")
-def c1_dev(c1):
-    return device_kb(c1)
+def small_dev(small):
+    return device_kb(small)
 
 
 @pytest.fixture(scope="module")
-def c1_progs(c1):
-    return hyps.small_hyps(c1, 11, 1000)
+def small_progs(small):
+    return hyps.small_hyps(small, 11, 1000)
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
-def test_c1_all_hypotheses(c1, c1_dev, c1_progs, mode):
+def test_small_kb_all_hypotheses(small, small_dev, small_progs, mode):
     """Workload 1: 1,000 hypotheses of depth <= 4, every instance set and count."""
-    compare_batch(c1, c1_dev, c1_progs, MODES[mode])
+    compare_batch(small, small_dev, small_progs, MODES[mode])
 
 
 @pytest.mark.parametrize("flags", [0, H.HEDL_SLICE_ALL, H.HEDL_NO_SLICE])
-def test_repeated_execution_through_the_graph(c1, c1_dev, c1_progs, flags):
+def test_repeated_execution_through_the_graph(small, small_dev, small_progs, flags):
     """First execution launches directly, the second captures a CUDA graph, the third and
     a replay run the graph: every one matches the oracle."""
     import torch
-    flat, offs = P.pack_batch(c1_progs)
-    okb = oracle.from_synth(c1)
+    flat, offs = P.pack_batch(small_progs)
+    okb = oracle.from_synth(small)
     oc, osets, errs = oracle.eval_batch(okb, flat, offs, threads=4, keep_sets=True)
-    plan = H.hedl_plan_batch(c1_dev.handle, flat, offs, flags)
-    ws = c1_dev.workspace(H.hedl_plan_info_get(plan)["workspace_bytes"])
+    plan = H.hedl_plan_batch(small_dev.handle, flat, offs, flags)
+    ws = small_dev.workspace(H.hedl_plan_info_get(plan)["workspace_bytes"])
     for call in (H.hedl_plan_execute, H.hedl_plan_execute, H.hedl_plan_execute, H.hedl_plan_replay):
-        counts = torch.zeros((len(c1_progs), 4), dtype=torch.int32, device=c1_dev.device)
-        bits = torch.zeros((len(c1_progs), c1_dev.wp), dtype=torch.int32, device=c1_dev.device)
-        call(c1_dev.handle, plan, counts, bits, ws)
-        H.hedl_sync_status(c1_dev.handle)
+        counts = torch.zeros((len(small_progs), 4), dtype=torch.int32, device=small_dev.device)
+        bits = torch.zeros((len(small_progs), small_dev.wp), dtype=torch.int32, device=small_dev.device)
+        call(small_dev.handle, plan, counts, bits, ws)
+        H.hedl_sync_status(small_dev.handle)
         assert np.array_equal(counts.cpu().numpy().astype(np.int64), oc)
         bb = bits.cpu().numpy().view(np.uint32)
-        for h in range(len(c1_progs)):
-            assert np.array_equal(K.unpack_bits(bb[h], c1.n), osets[h].astype(bool)), (call, h)
+        for h in range(len(small_progs)):
+            assert np.array_equal(K.unpack_bits(bb[h], small.n), osets[h].astype(bool)), (call, h)
 
 
-def test_c1_batched_shapes(c1, c1_dev):
+def test_small_kb_batched_shapes(small, small_dev):
     """Uneven lengths 1..40, depths 1..8, shared sub-concepts."""
-    progs = hyps.batch_hyps(c1, 21, 0, 512)
-    compare_batch(c1, c1_dev, progs, 0)
-    compare_batch(c1, c1_dev, progs, H.HEDL_LEVELS)
+    progs = hyps.batch_hyps(small, 21, 0, 512)
+    compare_batch(small, small_dev, progs, 0)
+    compare_batch(small, small_dev, progs, H.HEDL_LEVELS)
 
 
 @pytest.mark.parametrize("tuning", [dict(warps_per_cta=4, words_per_lane=4, rounds=2),
@@ -99,27 +99,27 @@ def test_c1_batched_shapes(c1, c1_dev):
                                     dict(warps_per_cta=8, role_block=8, stage_fillers=0, full_occupancy=1, rounds=4),
                                     dict(warps_per_cta=1, role_block=8, rounds=1),
                                     dict(warps_per_cta=2, role_block=4, rounds=4, stage_fillers=1)])
-def test_launch_shapes(c1, tuning):
-    dkb = device_kb(c1)
+def test_launch_shapes(small, tuning):
+    dkb = device_kb(small)
     H.hedl_tuning_set(dkb.handle, **tuning)
-    compare_batch(c1, dkb, hyps.batch_hyps(c1, 22, 0, 300), 0)
+    compare_batch(small, dkb, hyps.batch_hyps(small, 22, 0, 300), 0)
 
 
-def test_autotune_picks_a_shape_and_stays_exact(c1, tmp_path):
-    dkb = device_kb(c1)
-    probe = P.pack_batch(hyps.batch_hyps(c1, 41, 0, 128))
+def test_autotune_picks_a_shape_and_stays_exact(small, tmp_path):
+    dkb = device_kb(small)
+    probe = P.pack_batch(hyps.batch_hyps(small, 41, 0, 128))
     cache = str(tmp_path / "tune.txt")
     chosen = dkb.autotune(*probe, cache_path=cache)
     assert H.hedl_tuning_get(dkb.handle) == chosen
     assert open(cache).read().count("\n") == 1
-    compare_batch(c1, dkb, hyps.batch_hyps(c1, 42, 0, 200), 0)
-    other = device_kb(c1)                      # the cached result is reused
+    compare_batch(small, dkb, hyps.batch_hyps(small, 42, 0, 200), 0)
+    other = device_kb(small)                      # the cached result is reused
     assert other.autotune(*probe, cache_path=cache) == chosen
     assert open(cache).read().count("\n") == 1
 
 
-def test_launch_shape_that_does_not_fit_is_rejected(c1):
-    dkb = device_kb(c1)
+def test_launch_shape_that_does_not_fit_is_rejected(small):
+    dkb = device_kb(small)
     with pytest.raises(H.HedlError) as e:
         H.hedl_tuning_set(dkb.handle, warps_per_cta=32, words_per_lane=4)
     assert e.value.code == -1
@@ -127,21 +127,21 @@ def test_launch_shape_that_does_not_fit_is_rejected(c1):
         H.hedl_tuning_set(dkb.handle, warps_per_cta=12)
 
 
-def test_eval_concept(c1, c1_dev):
-    okb = oracle.from_synth(c1)
+def test_eval_concept(small, small_dev):
+    okb = oracle.from_synth(small)
     r = Rng(9, 9)
     for i in range(40):
-        prog = pins.random_program(r, c1, r.randint(1, 6)).postfix()
+        prog = pins.random_program(r, small, r.randint(1, 6)).postfix()
         want = oracle.eval_program(okb, prog)
         for flags in (0, H.HEDL_SLICE_ALL):
-            got = K.unpack_bits(c1_dev.eval(np.array(prog, np.uint64), flags), c1.n)
+            got = K.unpack_bits(small_dev.eval(np.array(prog, np.uint64), flags), small.n)
             assert np.array_equal(got, want), (flags, P.to_text(P.from_postfix(prog)))
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 63, 64, 65, 100, 127, 129, 1000, 4097])
 def test_ragged_sizes_every_constructor(n):
     """Sizes around word and 128-bit boundaries, every constructor incl. TOP/BOT/EXACTLY/DEQ."""
-    cfg = K.CONFIGS["c1"].scaled(n, seed=1000 + n, n_concepts=6, n_roles=3, n_props=2,
+    cfg = K.CONFIGS["small"].scaled(n, seed=1000 + n, n_concepts=6, n_roles=3, n_props=2,
                                  degree=("poisson", min(3.0, max(n - 1, 0) / 2 + 0.5)),
                                  n_pos=max(1, n // 4), n_neg=max(1, n // 4) if n > 1 else 0)
     cfg = cfg if cfg.n_pos + cfg.n_neg <= n else cfg.scaled(n, n_pos=1, n_neg=0)
@@ -156,7 +156,7 @@ def test_ragged_sizes_every_constructor(n):
 def test_stress_shapes_single_and_unique_subject():
     """The paper's two assertion-set shapes: one subject holding every assertion (a 6,000-edge row)
     and one assertion per subject (a permutation)."""
-    base = K.CONFIGS["c1"]
+    base = K.CONFIGS["small"]
     for deg in (("single", 6000), ("unique",)):
         kb = K.generate(base.scaled(9000, seed=77, n_concepts=5, n_roles=2, degree=deg))
         dkb = device_kb(kb)
@@ -169,7 +169,7 @@ def test_stress_shapes_single_and_unique_subject():
 
 
 def test_zipf_heavy_rows():
-    kb = K.generate(K.CONFIGS["c2"].scaled(40_000, seed=55, n_concepts=12, n_roles=3, n_props=3))
+    kb = K.generate(K.CONFIGS["large"].scaled(40_000, seed=55, n_concepts=12, n_roles=3, n_props=3))
     dkb = device_kb(kb)
     progs = hyps.batch_hyps(kb, 5, 0, 300, lmax=30, dmax=7)
     compare_batch(kb, dkb, progs, 0)
@@ -177,7 +177,7 @@ def test_zipf_heavy_rows():
     compare_batch(kb, dkb, progs, H.HEDL_SLICE_ALL)
 
 
-def test_special_thresholds_and_counts(c1, c1_dev):
+def test_special_thresholds_and_counts(small, small_dev):
     texts = ["(ge p0 -0.0)", "(le p0 0.0)", "(eq p0 -0.0)", "(ge p1 inf)", "(le p1 -inf)", "(ge p2 nan)",
              "(not (le p3 nan))", "(min 0 r1 BOT)", "(max 4294967295 r2 TOP)", "(exactly 4294967295 r2 TOP)",
              "(min 4294967295 r2 TOP)", "(exactly 0 r3- A5)", "TOP", "BOT", "(not TOP)", "A0"]
@@ -186,10 +186,10 @@ def test_special_thresholds_and_counts(c1, c1_dev):
                     np.uint64)
     progs.append(deep)
     for mode in MODES.values():
-        compare_batch(c1, c1_dev, progs, mode)
+        compare_batch(small, small_dev, progs, mode)
 
 
-def test_role_groups_with_every_kind_and_many_slices(c1, c1_dev):
+def test_role_groups_with_every_kind_and_many_slices(small, small_dev):
     """More than 32 restrictions of one role in one level, every kind, n = 0..6 sliced and
     n = 7.. on the per-restriction walk, complemented fillers, heavy rows."""
     texts = []
@@ -201,75 +201,75 @@ def test_role_groups_with_every_kind_and_many_slices(c1, c1_dev):
     texts += [f"(and A{i} (some r2 (or A{i + 1} (min {i % 5} r2- A{i + 2}))))" for i in range(40)]
     progs = [P.compile_text(t) for t in texts]
     for mode in (0, H.HEDL_LEVELS, H.HEDL_NO_SLICE, H.HEDL_SLICE_ALL):
-        compare_batch(c1, c1_dev, progs, mode)
+        compare_batch(small, small_dev, progs, mode)
 
 
 def test_kb_without_roles_or_props():
-    kb = K.generate(K.CONFIGS["c1"].scaled(3000, seed=3, n_roles=0, n_props=0))
+    kb = K.generate(K.CONFIGS["small"].scaled(3000, seed=3, n_roles=0, n_props=0))
     dkb = device_kb(kb)
     progs = [P.compile_text(t) for t in ("(and A1 (not A2))", "(or A3 TOP)", "BOT")]
     compare_batch(kb, dkb, progs, 0)
 
 
-def test_examples_counts(c1, c1_dev):
-    assert H.hedl_examples_counts(c1_dev.handle) == (c1.pos_idx.size, c1.neg_idx.size)
+def test_examples_counts(small, small_dev):
+    assert H.hedl_examples_counts(small_dev.handle) == (small.pos_idx.size, small.neg_idx.size)
 
 
-def test_replay_and_workspace_checks(c1, c1_dev):
+def test_replay_and_workspace_checks(small, small_dev):
     import torch
-    progs = hyps.batch_hyps(c1, 31, 0, 200)
+    progs = hyps.batch_hyps(small, 31, 0, 200)
     flat, offs = P.pack_batch(progs)
-    plan = H.hedl_plan_batch(c1_dev.handle, flat, offs)
+    plan = H.hedl_plan_batch(small_dev.handle, flat, offs)
     info = H.hedl_plan_info_get(plan)
     ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device="cuda")
     counts = torch.zeros((200, 4), dtype=torch.int32, device="cuda")
-    H.hedl_plan_execute(c1_dev.handle, plan, counts, None, ws)
+    H.hedl_plan_execute(small_dev.handle, plan, counts, None, ws)
     first = counts.clone()
     for _ in range(3):
         counts.zero_()
-        H.hedl_plan_replay(c1_dev.handle, plan, counts, None, ws)
-        H.hedl_sync_status(c1_dev.handle)
+        H.hedl_plan_replay(small_dev.handle, plan, counts, None, ws)
+        H.hedl_sync_status(small_dev.handle)
         assert torch.equal(counts, first)
     small = torch.empty(info["workspace_bytes"] - 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(H.HedlError) as e:
-        H.hedl_plan_execute(c1_dev.handle, plan, counts, None, small)
+        H.hedl_plan_execute(small_dev.handle, plan, counts, None, small)
     assert e.value.code == -3
     big = torch.empty(info["workspace_bytes"] + 256, dtype=torch.uint8, device="cuda")
     with pytest.raises(H.HedlError) as e:   # large enough, but not 256-byte aligned
-        H.hedl_plan_execute(c1_dev.handle, plan, counts, None, big[1:])
+        H.hedl_plan_execute(small_dev.handle, plan, counts, None, big[1:])
     assert e.value.code == -1
 
 
-def test_score_batch_one_shot(c1, c1_dev):
+def test_score_batch_one_shot(small, small_dev):
     import torch
-    progs = hyps.batch_hyps(c1, 32, 0, 100)
+    progs = hyps.batch_hyps(small, 32, 0, 100)
     flat, offs = P.pack_batch(progs)
-    n = H.hedl_workspace_size(c1_dev.handle, flat, offs)
+    n = H.hedl_workspace_size(small_dev.handle, flat, offs)
     ws = torch.empty(n, dtype=torch.uint8, device="cuda")
     counts = torch.zeros((100, 4), dtype=torch.int32, device="cuda")
-    H.hedl_score_batch(c1_dev.handle, flat, offs, counts, ws)
-    H.hedl_sync_status(c1_dev.handle)
-    okb = oracle.from_synth(c1)
+    H.hedl_score_batch(small_dev.handle, flat, offs, counts, ws)
+    H.hedl_sync_status(small_dev.handle)
+    okb = oracle.from_synth(small)
     oc, _, _ = oracle.eval_batch(okb, flat, offs, threads=4)
     assert np.array_equal(counts.cpu().numpy().astype(np.int64), oc)
 
 
-def test_bounded_wait_reports_timeout(c1):
+def test_bounded_wait_reports_timeout(small):
     """A dependency nothing satisfies: the device wait gives up, the call reports
     HEDL_ERR_TIMEOUT, and the context stays usable."""
-    dkb = device_kb(c1)
+    dkb = device_kb(small)
     H.hedl_tuning_set(dkb.handle, wait_timeout_ms=100)
-    progs = hyps.batch_hyps(c1, 33, 0, 50)
+    progs = hyps.batch_hyps(small, 33, 0, 50)
     flat, offs = P.pack_batch(progs)
     with pytest.raises(H.HedlError) as e:
         dkb.score(flat, offs, H.HEDL_TEST_UNSAT_DEP | H.HEDL_NO_GRAPH)
     assert e.value.code == -5
-    compare_batch(c1, dkb, progs, 0)
+    compare_batch(small, dkb, progs, 0)
 
 
 def test_bad_kb_rejected():
     import torch
-    kb = K.generate(K.CONFIGS["c1"].scaled(500, seed=4, n_roles=2))
+    kb = K.generate(K.CONFIGS["small"].scaled(500, seed=4, n_roles=2))
     cases = {}
     col = kb.col[0].copy()
     k = int(np.nonzero(np.diff(kb.row_ptr[0].astype(np.int64)) >= 2)[0][0])
@@ -301,24 +301,24 @@ def test_bad_kb_rejected():
 
 
 @pytest.fixture(scope="module")
-def c3():
-    return K.generate(K.CONFIGS["c3"])
+def batch_kb():
+    return K.generate(K.CONFIGS["batch"])
 
 
 @pytest.mark.parametrize("stage,flags", [(1, 0), (0, 0), (1, 16)])
-def test_c3_full_size_batch_sampled(c3, stage, flags):
+def test_batch_full_size_sampled(batch_kb, stage, flags):
     """Workload 3 at full size (N = 1,000,000) in the bench's launch configuration: a whole
     4,096-hypothesis batch on the GPU; 48 sampled hypotheses checked bit-exactly (sets and
     counts) against the oracle, and the counts of all against the plain path."""
-    dkb = device_kb(c3)
+    dkb = device_kb(batch_kb)
     H.hedl_tuning_set(dkb.handle, stage_fillers=stage)
-    progs = hyps.batch_hyps(c3, 1003, 0, 4096, gen=hyps.TreeGen(c3, 1003, share=0.3))
+    progs = hyps.batch_hyps(batch_kb, 1003, 0, 4096, gen=hyps.TreeGen(batch_kb, 1003, share=0.3))
     sample = sorted(set(list(range(8)) + list(range(0, 4096, 97)) + [4095]))
-    counts, _ = compare_batch(c3, dkb, progs, flags, sample=sample, check_bits=False)
+    counts, _ = compare_batch(batch_kb, dkb, progs, flags, sample=sample, check_bits=False)
     # instance sets of the sampled hypotheses, through eval (bench-shaped plan for the counts above)
-    okb = oracle.from_synth(c3)
+    okb = oracle.from_synth(batch_kb)
     for h in sample[:12]:
-        got = K.unpack_bits(dkb.eval(progs[h]), c3.n)
+        got = K.unpack_bits(dkb.eval(progs[h]), batch_kb.n)
         assert np.array_equal(got, oracle.eval_program(okb, progs[h])), h
     if stage and not flags:
         plain = dkb.score(*P.pack_batch(progs), H.HEDL_PLAIN)

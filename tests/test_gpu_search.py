@@ -24,7 +24,7 @@ def env():
     from paper_2412_00802_gb300 import build
     build.build()
     import paper_2412_00802_gb300 as H
-    kb = K.generate(K.CONFIGS["c5"].scaled(20000, n_concepts=40, n_roles=8, n_props=6))
+    kb = K.generate(K.CONFIGS["search"].scaled(20000, n_concepts=40, n_roles=8, n_props=6))
     return H, kb, H.DeviceKB.from_synth(kb)
 
 

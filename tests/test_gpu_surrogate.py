@@ -19,7 +19,7 @@ def env():
     build.build()
     import paper_2412_00802_gb300 as H
     from paper_2412_00802_gb300 import surrogate as sg
-    kb = K.generate(K.CONFIGS["c1"])
+    kb = K.generate(K.CONFIGS["small"])
     return torch, H, sg, kb
 
 
@@ -221,7 +221,7 @@ def test_trained_surrogate_ranks_better_than_chance(env):
     """On a planted KB (the surrogate workload's shape, 20,000 individuals) the network, trained
     on exactly scored hypotheses, keeps most of the exact top 100 in its top 5 %."""
     torch, H, sg, _ = env
-    kb = K.generate(K.CONFIGS["c4"].scaled(20000, n_pos=500, n_neg=500, n_roles=8, n_props=4, n_concepts=50))
+    kb = K.generate(K.CONFIGS["surrogate"].scaled(20000, n_pos=500, n_neg=500, n_roles=8, n_props=4, n_concepts=50))
     dkb = H.DeviceKB.from_synth(kb)
     gen = hyps.TreeGen(kb, 51, share=0.3)
     train = hyps.batch_hyps(kb, 51, 0, 24576, lmax=20, dmax=6, gen=gen)

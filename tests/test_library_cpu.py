@@ -60,20 +60,20 @@ def test_row_words():
 
 
 @pytest.fixture(scope="module")
-def c1():
-    return K.generate(K.CONFIGS["c1"])
+def small():
+    return K.generate(K.CONFIGS["small"])
 
 
 def plan_kb(kb):
     return H.hedl_kb_plan_only(kb.n, kb.n_concepts, [kb.n_edges(r) for r in range(kb.n_roles)], kb.n_props)
 
 
-def test_validation_agrees_with_the_oracle(c1):
+def test_validation_agrees_with_the_oracle(small):
     """Accept / reject decisions match the oracle's on malformed programs."""
-    hk = plan_kb(c1)
-    okb = oracle.from_synth(c1)
+    hk = plan_kb(small)
+    okb = oracle.from_synth(small)
     r = np.random.default_rng(3)
-    good = hyps.small_hyps(c1, 5, 30)
+    good = hyps.small_hyps(small, 5, 30)
     cases = []
     for g in good:
         cases.append(g)
@@ -106,9 +106,9 @@ def test_validation_agrees_with_the_oracle(c1):
         assert got_ok == want_ok, P.to_text(P.from_postfix(c)) if want_ok else c
 
 
-def test_plan_batch_rejects_and_names_the_program(c1):
-    hk = plan_kb(c1)
-    progs = hyps.small_hyps(c1, 5, 10)
+def test_plan_batch_rejects_and_names_the_program(small):
+    hk = plan_kb(small)
+    progs = hyps.small_hyps(small, 5, 10)
     progs[7] = np.array([P.insn(P.AND)], np.uint64)
     flat, offs = P.pack_batch(progs)
     with pytest.raises(H.HedlError) as e:
@@ -116,8 +116,8 @@ def test_plan_batch_rejects_and_names_the_program(c1):
     assert "program 7" in str(e.value)
 
 
-def test_plan_sharing_and_levels(c1):
-    hk = plan_kb(c1)
+def test_plan_sharing_and_levels(small):
+    hk = plan_kb(small)
     x = "(and A1 (some r2 (min 2 r3- (or A4 (le p1 20)))))"
     progs = [P.compile_text(x)] * 10 + [P.compile_text(f"(or A{i} {x})") for i in range(5)]
     flat, offs = P.pack_batch(progs)
@@ -156,17 +156,17 @@ def test_plan_sharing_and_levels(c1):
     assert i["n_role_ops"] == 1
 
 
-def test_workspace_accounts_for_slots(c1):
-    hk = plan_kb(c1)
-    progs = hyps.batch_hyps(c1, 9, 0, 200)
+def test_workspace_accounts_for_slots(small):
+    hk = plan_kb(small)
+    progs = hyps.batch_hyps(small, 9, 0, 200)
     flat, offs = P.pack_batch(progs)
     info = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs))
-    assert info["workspace_bytes"] >= info["n_slots"] * 4 * c1.wp
-    assert info["n_items"] == info["n_segments"] * -(-c1.wp // info["tile_words"])
+    assert info["workspace_bytes"] >= info["n_slots"] * 4 * small.wp
+    assert info["n_items"] == info["n_segments"] * -(-small.wp // info["tile_words"])
 
 
-def test_planning_only_handle_refuses_launches(c1):
-    hk = plan_kb(c1)
+def test_planning_only_handle_refuses_launches(small):
+    hk = plan_kb(small)
     with pytest.raises(H.HedlError) as e:
         H.hedl_sync_status(hk, stream=0)
     assert e.value.code == -1
@@ -186,11 +186,11 @@ def test_narrow_tiles_for_single_hypotheses():
     assert paired["n_role_groups"] == 1 and paired["warp_words"] == 32
 
 
-def test_canonical_batch_agrees_with_the_search_oracle(c1):
+def test_canonical_batch_agrees_with_the_search_oracle(small):
     """The library's canonical form equals the independently written one of the search oracle."""
     from oracle import search as OS
     r = Rng(17, 4)
-    progs = [np.array(pins.random_program(r, c1, r.randint(1, 7)).postfix(), np.uint64) for _ in range(400)]
+    progs = [np.array(pins.random_program(r, small, r.randint(1, 7)).postfix(), np.uint64) for _ in range(400)]
     progs += [P.compile_text("(and (or A2 A1) (or A1 A2))"), P.compile_text("(and A1 A1)"), P.compile_text("TOP")]
     flat, offs = P.pack_batch(progs)
     got = H.hedl_canonical_batch(flat, offs)

@@ -29,7 +29,7 @@ def _worker(rank, world, port, out):
     ids = [None] * world
     td.all_gather_object(ids, warm + timed)
     # each rank scores its own shard (oracle as the stand-in evaluator)
-    kb = K.generate(K.CONFIGS["c1"].scaled(800, seed=5))
+    kb = K.generate(K.CONFIGS["small"].scaled(800, seed=5))
     okb = oracle.from_synth(kb)
     counts = []
     for b in timed:

@@ -17,52 +17,52 @@ def test_counter_rng_is_stateless():
 
 
 @pytest.fixture(scope="module")
-def c1():
-    return K.generate(K.CONFIGS["c1"])
+def small():
+    return K.generate(K.CONFIGS["small"])
 
 
-def test_deterministic(c1):
-    again = K.generate(K.CONFIGS["c1"])
-    assert np.array_equal(again.concept_bits, c1.concept_bits)
-    for r in range(c1.n_roles):
-        assert np.array_equal(again.col[r], c1.col[r])
-    assert np.array_equal(again.prop_vals, c1.prop_vals, equal_nan=True)
+def test_deterministic(small):
+    again = K.generate(K.CONFIGS["small"])
+    assert np.array_equal(again.concept_bits, small.concept_bits)
+    for r in range(small.n_roles):
+        assert np.array_equal(again.col[r], small.col[r])
+    assert np.array_equal(again.prop_vals, small.prop_vals, equal_nan=True)
 
 
-def test_csr_and_transpose(c1):
-    n = c1.n
-    for r in range(c1.n_roles):
-        rp, col = c1.row_ptr[r].astype(np.int64), c1.col[r].astype(np.int64)
+def test_csr_and_transpose(small):
+    n = small.n
+    for r in range(small.n_roles):
+        rp, col = small.row_ptr[r].astype(np.int64), small.col[r].astype(np.int64)
         assert rp[0] == 0 and rp[-1] == col.size and np.all(np.diff(rp) >= 0)
         assert col.max() < n
         rows = np.repeat(np.arange(n), np.diff(rp))
         key = rows * n + col
         assert np.all(np.diff(key) > 0), "rows sorted, no duplicate assertion"
-        ip, ic = c1.inv_row_ptr[r], c1.inv_col[r]
+        ip, ic = small.inv_row_ptr[r], small.inv_col[r]
         ikey = np.repeat(np.arange(n), np.diff(ip.astype(np.int64))) * n + ic.astype(np.int64)
         assert np.all(np.diff(ikey) > 0)
         # transpose of the transpose is the original
         rp2, col2 = K.transpose_csr(ip, ic, n)
-        assert np.array_equal(rp2, c1.row_ptr[r]) and np.array_equal(col2, c1.col[r])
+        assert np.array_equal(rp2, small.row_ptr[r]) and np.array_equal(col2, small.col[r])
 
 
-def test_tails_zero_and_dag_closed(c1):
-    w = c1.n // 32
-    tail = c1.n % 32
+def test_tails_zero_and_dag_closed(small):
+    w = small.n // 32
+    tail = small.n % 32
     if tail:
-        assert not (c1.concept_bits[:, w] >> np.uint32(tail)).any()
-    assert not c1.concept_bits[:, c1.w:].any()
-    parent = c1.meta["dag_parent"]
+        assert not (small.concept_bits[:, w] >> np.uint32(tail)).any()
+    assert not small.concept_bits[:, small.w:].any()
+    parent = small.meta["dag_parent"]
     for j, p in enumerate(parent):
         if p >= 0:
-            assert not (c1.concept_bits[j] & ~c1.concept_bits[p]).any(), "sub-concept members are in the parent"
+            assert not (small.concept_bits[j] & ~small.concept_bits[p]).any(), "sub-concept members are in the parent"
 
 
 def test_degree_laws():
-    cfg = K.CONFIGS["c3"].scaled(200_000, n_roles=1)
+    cfg = K.CONFIGS["batch"].scaled(200_000, n_roles=1)
     deg, _ = K.draw_degrees(cfg, 0, cfg.n)
     assert abs(deg.mean() - 6.0) < 0.05
-    cfg = K.CONFIGS["c2"].scaled(200_000, n_roles=1)
+    cfg = K.CONFIGS["large"].scaled(200_000, n_roles=1)
     deg, meta = K.draw_degrees(cfg, 0, cfg.n)
     assert abs(deg.mean() - 8.0) < 0.5 and deg.max() <= 10_000
     s = meta["zipf_shift"]
@@ -70,26 +70,26 @@ def test_degree_laws():
     assert abs((pmf * np.arange(10_001)).sum() - 8.0) < 1e-6
 
 
-def test_props_and_examples(c1):
-    v = c1.prop_vals
+def test_props_and_examples(small):
+    v = small.prop_vals
     miss = np.isnan(v).mean()
     assert 0.18 < miss < 0.22
     assert np.nanmin(v) >= 0 and np.nanmax(v) <= 100
-    assert c1.pos_idx.size == 200 and c1.neg_idx.size == 200
-    assert not np.intersect1d(c1.pos_idx, c1.neg_idx).size
+    assert small.pos_idx.size == 200 and small.neg_idx.size == 200
+    assert not np.intersect1d(small.pos_idx, small.neg_idx).size
 
 
-def test_hypothesis_shapes(c1):
-    g = Hy.TreeGen(c1, 5)
+def test_hypothesis_shapes(small):
+    g = Hy.TreeGen(small, 5)
     r = rng.Rng(5, 1)
     for _ in range(300):
         L, D = Hy.random_shape(r, 40, 1, 8)
         t = g._gen(r, L, D)
         assert t.size() == L and t.height() == D
         assert len(t.postfix()) == L
-    batch = Hy.batch_hyps(c1, 9, 0, 256)
+    batch = Hy.batch_hyps(small, 9, 0, 256)
     assert all(1 <= len(p) <= 40 for p in batch)
-    for p in Hy.chain_hyps(c1, 4, 8):
+    for p in Hy.chain_hyps(small, 4, 8):
         assert P.from_postfix(p).height() == 6
 
 
@@ -103,10 +103,10 @@ def test_text_roundtrip():
     assert P.fields(prog[-1]) == (P.ATLEAST, 1, 7, 3)
 
 
-@pytest.mark.parametrize("cfg", [K.CONFIGS["c1"].scaled(3001, seed=9),
-                                 K.CONFIGS["c2"].scaled(20_000, seed=8, n_roles=3, n_concepts=6),
-                                 K.CONFIGS["c4"].scaled(5_000, n_roles=2, n_concepts=6),
-                                 K.CONFIGS["c1"].scaled(300, seed=3, degree=("single", 250), n_roles=1)])
+@pytest.mark.parametrize("cfg", [K.CONFIGS["small"].scaled(3001, seed=9),
+                                 K.CONFIGS["large"].scaled(20_000, seed=8, n_roles=3, n_concepts=6),
+                                 K.CONFIGS["surrogate"].scaled(5_000, n_roles=2, n_concepts=6),
+                                 K.CONFIGS["small"].scaled(300, seed=3, degree=("single", 250), n_roles=1)])
 def test_c_helpers_match_numpy(cfg):
     """fastgen.c reproduces the numpy recipe array for array."""
     try:
@@ -127,9 +127,9 @@ def test_c_helpers_match_numpy(cfg):
 def test_refine_postfix_matches_the_python_generator():
     """The C refinement generator draws exactly the Python generator's candidates."""
     from synth.refine import Refiner
-    for cfg in (K.CONFIGS["c5"].scaled(3000, n_roles=6, n_props=4, n_concepts=20),
-                K.CONFIGS["c5"].scaled(2000, n_roles=0, n_props=3, n_concepts=9),
-                K.CONFIGS["c5"].scaled(2000, n_roles=4, n_props=0, n_concepts=7)):
+    for cfg in (K.CONFIGS["search"].scaled(3000, n_roles=6, n_props=4, n_concepts=20),
+                K.CONFIGS["search"].scaled(2000, n_roles=0, n_props=3, n_concepts=9),
+                K.CONFIGS["search"].scaled(2000, n_roles=4, n_props=0, n_concepts=7)):
         kb = K.generate(cfg)
         ref = Refiner(kb, 505)
         beam = [P.Node(P.TOP)]

@@ -22,7 +22,7 @@ def dkb():
     from paper_2412_00802_gb300 import build
     build.build()
     torch.cuda.set_device(0)
-    kb = K.generate(K.CONFIGS["c1"])
+    kb = K.generate(K.CONFIGS["small"])
     return kb, H.DeviceKB.from_synth(kb)
 
 
