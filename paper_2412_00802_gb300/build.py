@@ -37,7 +37,8 @@ def interpreter_digest() -> str:
     for f in INTERPRETER:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # flags without paths: the checkout's location must not change the digest
+    h.update(" ".join(a for a in ARCH + FLAGS if not os.path.isabs(a)).encode())
     return h.hexdigest()
 
 
