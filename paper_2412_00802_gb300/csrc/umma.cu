@@ -2,25 +2,30 @@
 // C[M][N] = act(A[M][K] . B[N][K]^T + bias), A and B bf16 and K-major (rows
 // of K contiguous elements), FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 4 warps computes a 256 x 256 tile.  K runs in blocks of 64
-// through a ring of three shared-memory stages.  Warp 0 is the producer: one
-// of its threads loads each block of A (256 x 64) and B (256 x 64) with one
-// TMA copy each (cp.async.bulk.tensor, a 64-column x 256-row box: 128-byte
-// rows in the 128-byte swizzle pattern the tensor cores read as K-major
-// SWIZZLE_128B operands) and signals the stage's "full" mbarrier through the
-// copies' byte count.  Warp
-// 1 is the MMA issuer: one thread waits for a full stage, issues eight
-// tcgen05.mma (M 128, N 256, K 16 each: four K steps times the two 128-row
-// halves of A, which share the B block) and commits them to the stage's
-// "empty" mbarrier, which hands the stage back to the producer.  The two
-// 128 x 256 FP32 accumulators fill the SM's 512 TMEM columns (one CTA per
-// SM); the epilogue (all warps) reads them back with tcgen05.ld, each warp
-// its 32 rows of each half, adds the bias, applies ReLU or a mask (the
-// backward pass's ReLU derivative) and stores bf16 or FP32 rows.
+// A persistent kernel: one CTA per SM walks the 128 x 256 output tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Its six warps have fixed roles:
+//   warp 0 (one thread): the TMA producer.  It loads each 64-wide K block of
+//     the tile's A (128 x 64) and B (256 x 64) with one TMA copy each
+//     (cp.async.bulk.tensor, 128-byte rows in the 128-byte swizzle the
+//     tensor cores read as K-major SWIZZLE_128B operands) into a ring of four
+//     48 KB stages, arming the stage's "full" mbarrier with the byte count;
+//   warp 1 (one thread): the MMA issuer.  Per K block it waits for a full
+//     stage, issues four tcgen05.mma (M 128, N 256, K 16) into one of two
+//     256-column TMEM accumulators and commits them to the stage's "empty"
+//     mbarrier; after a tile's last block it commits to the accumulator's
+//     "tmem full" mbarrier;
+//   warps 2-5: the epilogue.  Each reads its 32-lane quarter of a finished
+//     accumulator with tcgen05.ld, adds the bias, applies ReLU or a mask (the
+//     backward pass's ReLU derivative), stores bf16 or FP32 rows, and arrives
+//     on the accumulator's "tmem empty" mbarrier.
+// With two accumulators, the epilogue of one tile overlaps the loads and
+// MMAs of the next.
 //
 // Every wait is bounded: a wait that does not complete within 2 s records an
 // error in *err; the CTA then skips the rest of its work and still frees its
 // TMEM.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -30,12 +35,13 @@
 namespace hedl {
 namespace {
 
-constexpr int UM = 256, UN = 256, UK = 64, STAGES = 3;
+constexpr int UM = 128, UN = 256, UK = 64, STAGES = 4;
 constexpr uint32_t ROW = UK * 2;                     // 128-byte rows of a block
-constexpr uint32_t A_BYTES = UM * UK * 2;            // 32 KB
+constexpr uint32_t A_BYTES = UM * UK * 2;            // 16 KB
 constexpr uint32_t B_BYTES = UN * UK * 2;            // 32 KB
-constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 64 KB
-constexpr uint32_t TMEM_COLS = 2 * UN;               // FP32 accumulators of the two halves
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;  // 48 KB
+constexpr uint32_t TMEM_COLS = 2 * UN;               // two FP32 accumulators
+constexpr int THREADS = 192;                         // producer, MMA issuer, 4 epilogue warps
 constexpr size_t UMMA_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
@@ -151,26 +157,30 @@ __device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, cons
     }
 }
 
-__global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                   const __grid_constant__ CUtensorMap tmB, UmmaArgs g) {
+__global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB, UmmaArgs g) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(base + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *tfull = empty + STAGES;    // [2]: accumulator ready for the epilogue
+    uint64_t *tempty = tfull + 2;        // [2]: accumulator drained by the epilogue
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile uint32_t *okp = tslot + 1;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const int n0 = blockIdx.x * UN, m0 = blockIdx.y * UM;
     const uint32_t s0 = smem_u32(base);
-    const uint32_t full0 = smem_u32(full), empty0 = smem_u32(empty), done_a = smem_u32(done);
+    const uint32_t full0 = smem_u32(full), empty0 = smem_u32(empty), tfull0 = smem_u32(tfull),
+                   tempty0 = smem_u32(tempty);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * i) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8u * i) : "memory");
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done_a) : "memory");
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull0 + 8u * i) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tempty0 + 8u * i) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *okp = 1u;
     }
@@ -184,80 +194,107 @@ __global__ void __launch_bounds__(128) umma_kernel(const __grid_constant__ CUten
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = *tslot;
+
     const int nk = g.K / UK;
+    const int tiles_n = g.N / UN, tiles = ((g.M + UM - 1) / UM) * tiles_n;
 
     if (warp == 0 && lane == 0) {
-        // producer: block kb into stage kb % STAGES once the MMAs of block kb - STAGES released it
-        for (int kb = 0; kb < nk; ++kb) {
-            const int st = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(empty0 + 8u * st, (uint32_t)((kb - STAGES) / STAGES) & 1u, okp)) {
-                *okp = 0u;
-                break;
+        // producer: the running block count u uses stage u % STAGES
+        uint32_t u = 0;
+        for (int t = blockIdx.x; t < tiles && *okp; t += gridDim.x) {
+            const int m0 = (t / tiles_n) * UM, n0 = (t % tiles_n) * UN;
+            for (int kb = 0; kb < nk; ++kb, ++u) {
+                const uint32_t st = u % STAGES;
+                if (u >= STAGES && !mbar_wait(empty0 + 8u * st, ((u - STAGES) / STAGES) & 1u, okp)) {
+                    *okp = 0u;
+                    break;
+                }
+                const uint32_t fb = full0 + 8u * st, sa = s0 + st * STAGE_BYTES;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES)
+                             : "memory");
+                tma_2d(sa, &tmA, kb * UK, m0, fb);
+                tma_2d(sa + A_BYTES, &tmB, kb * UK, n0, fb);
             }
-            const uint32_t fb = full0 + 8u * st, sa = s0 + (uint32_t)st * STAGE_BYTES;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE_BYTES)
-                         : "memory");
-            tma_2d(sa, &tmA, kb * UK, m0, fb);
-            tma_2d(sa + A_BYTES, &tmB, kb * UK, n0, fb);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        bool good = true;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int st = kb % STAGES;
-            if (!mbar_wait(full0 + 8u * st, (uint32_t)(kb / STAGES) & 1u, okp)) {
+        // MMA issuer: the CTA's j-th tile accumulates into buffer j & 1
+        uint32_t u = 0, j = 0;
+        for (int t = blockIdx.x; t < tiles && *okp; t += gridDim.x, ++j) {
+            const uint32_t bf = j & 1u;
+            if (j >= 2 && !mbar_wait(tempty0 + 8u * bf, ((j >> 1) - 1u) & 1u, okp)) {
                 *okp = 0u;
-                good = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = s0 + (uint32_t)st * STAGE_BYTES;
+            const uint32_t acc_t = taddr + bf * UN;
+            bool good = true;
+            for (int kb = 0; kb < nk; ++kb, ++u) {
+                const uint32_t st = u % STAGES;
+                if (!mbar_wait(full0 + 8u * st, (u / STAGES) & 1u, okp)) {
+                    *okp = 0u;
+                    good = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = s0 + st * STAGE_BYTES;
 #pragma unroll
-            for (int s = 0; s < UK / 16; ++s) {
-                const uint64_t bd = smem_desc(sa + A_BYTES + (uint32_t)s * 32u);
-                const uint32_t acc = (kb > 0 || s > 0) ? 1u : 0u;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {   // rows 128h.. of the tile into accumulator columns 256h..
-                    const uint64_t ad = smem_desc(sa + (uint32_t)h * 128u * ROW + (uint32_t)s * 32u);
+                for (int s = 0; s < UK / 16; ++s) {
+                    const uint64_t ad = smem_desc(sa + (uint32_t)s * 32u);
+                    const uint64_t bd = smem_desc(sa + A_BYTES + (uint32_t)s * 32u);
+                    const uint32_t acc = (kb > 0 || s > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                            taddr + (uint32_t)h * UN),
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_t),
                         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
                         : "memory");
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 empty0 + 8u * st)
+                             : "memory");
             }
+            if (!good) break;
+            // every MMA issued so far completes before this arrives
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             empty0 + 8u * st)
+                             tfull0 + 8u * bf)
                          : "memory");
         }
-        if (good)   // every MMA issued so far completes before this arrives
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done_a)
-                         : "memory");
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, the tile rows of that quarter
+        const uint32_t q = warp & 3u;
+        uint32_t j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const uint32_t bf = j & 1u;
+            uint32_t ok = 1u;
+            if (lane == 0) ok = mbar_wait(tfull0 + 8u * bf, (j >> 1) & 1u, okp) ? 1u : 0u;
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            if (!ok) {
+                if (lane == 0) *okp = 0u;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t / tiles_n) * UM, n0 = (t % tiles_n) * UN;
+            const int row = m0 + (int)(q * 32 + lane);
+            for (int c0 = 0; c0 < UN; c0 += 64) {   // two 32-column loads in flight per wait
+                uint32_t ra[32], rb[32];
+                const uint32_t ta = taddr + ((q * 32u) << 16) + bf * UN + (uint32_t)c0;
+                tmem_ld32(ta, ra);
+                tmem_ld32(ta + 32u, rb);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < g.M) {
+                    emit32(g, row, n0 + c0, ra);
+                    emit32(g, row, n0 + c0 + 32, rb);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8u * bf) : "memory");
+        }
     }
     __syncwarp();
-    if (threadIdx.x == 0 && *okp && !mbar_wait(done_a, 0u, okp)) *okp = 0u;
     __syncthreads();
-    const bool ok = *okp != 0u;
-    if (!ok && threadIdx.x == 0 && g.err) atomicOr(g.err, 1u);
+    if (threadIdx.x == 0 && !*okp && g.err) atomicOr(g.err, 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-    for (int h = 0; ok && h < 2; ++h) {
-        const int row = m0 + h * 128 + (int)(warp * 32 + lane);
-        for (int c0 = 0; c0 < UN; c0 += 64) {   // two 32-column loads in flight per wait
-            uint32_t ra[32], rb[32];
-            const uint32_t ta = taddr + ((warp * 32u) << 16) + (uint32_t)(h * UN + c0);
-            tmem_ld32(ta, ra);
-            tmem_ld32(ta + 32u, rb);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < g.M) {
-                emit32(g, row, n0 + c0, ra);
-                emit32(g, row, n0 + c0 + 32, rb);
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
 }
@@ -289,14 +326,14 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 64-column x 256-row
+// Tensor map of a row-major bf16 matrix [rows][ld] (cols used): 64-column x box_rows
 // boxes in the 128-byte swizzle, rows past the end read as zeros.
-bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld) {
+bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int ld, int box_rows) {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)UK, 256};
+    const cuuint32_t box[2] = {(cuuint32_t)UK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -316,10 +353,16 @@ int umma_gemm(const UmmaArgs &a, void *stream) {
         attr = true;
     }
     CUtensorMap ta, tb;
-    if (!make_map(&ta, a.A, a.M, a.K, a.lda) || !make_map(&tb, a.B, a.N, a.K, a.ldb))
+    if (!make_map(&ta, a.A, a.M, a.K, a.lda, UM) || !make_map(&tb, a.B, a.N, a.K, a.ldb, UN))
         return (int)cudaErrorInvalidValue;
-    dim3 grid((unsigned)(a.N / UN), (unsigned)((a.M + UM - 1) / UM));
-    umma_kernel<<<grid, 128, UMMA_SMEM, s>>>(ta, tb, a);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || sms < 1) sms = 1;
+    }
+    const long tiles = (long)((a.M + UM - 1) / UM) * (a.N / UN);
+    umma_kernel<<<(unsigned)std::min<long>(tiles, sms), THREADS, UMMA_SMEM, s>>>(ta, tb, a);
     return (int)cudaGetLastError();
 }
 
