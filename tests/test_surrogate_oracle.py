@@ -162,3 +162,26 @@ def test_ranking_and_recall():
     assert order == [2, 1, 0, 3]                      # tie on (acc, F1): shorter program first
     assert S.recall_at(2, order, [1, 2, 3]) == 1.0
     assert S.recall_at(2, order, [0, 3]) == 0.0
+
+
+def test_statistic_programs_land_in_their_buckets():
+    """The statistics table scores, for each (property, compare, q), a threshold whose grid
+    bucket is q, so an encoded threshold finds its own table entry."""
+    torch = pytest.importorskip("torch")
+    from paper_2412_00802_gb300 import surrogate as sg
+    rng = np.random.default_rng(5)
+    vals = rng.lognormal(size=(3, 5000)).astype(np.float32)
+    grid = sg.threshold_grid(vals)
+    s = sg.Surrogate.__new__(sg.Surrogate)            # host-side helpers only, no device state
+    s._grid_host = grid
+    progs = s.statistic_programs(7)
+    assert len(progs) == 7 + 3 * 2 * 16
+    for i, p in enumerate(progs[:7]):
+        assert int(p[0]) & 0xFF == P.ATOM and (int(p[0]) >> 16) & 0xFFFF == i
+    for k, p in enumerate(progs[7:]):
+        prop, rest = divmod(k, 32)
+        o, q = divmod(rest, 16)
+        w = int(p[0])
+        assert w & 0xFF == (P.DGE, P.DLE)[o] and (w >> 16) & 0xFFFF == prop
+        t = np.float32(P.bits_f32(w >> 32))
+        assert int(np.sum(grid[prop] < t)) == q, (prop, o, q)
