@@ -191,11 +191,6 @@ struct UmmaArgs {
     int relu, out_bf16;
     uint32_t *err;
     const void *mask;   // bf16 [M][ldc] or null: outputs where mask <= 0 become 0
-    // Optional fold of a 2-output layer: with w_out (bf16 [2][N]) each tile adds
-    // its bf16-rounded outputs' dot products with both rows of w_out to
-    // out_part (float [M][N / 256][2], one slot per 256-column tile).
-    const void *w_out;
-    float *out_part;
 };
 bool umma_shape_ok(const UmmaArgs &a);
 int umma_gemm(const UmmaArgs &a, void *stream);

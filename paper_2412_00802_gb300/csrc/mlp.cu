@@ -349,27 +349,6 @@ __global__ void out_fwd_kernel(const __nv_bfloat16 *H2, const __nv_bfloat16 *W3,
     }
 }
 
-// Output layer from the per-tile partial dot products that layer 2's
-// epilogue left (tiles in column order): Y = b3 + sum of the tiles' parts,
-// mapped like out_fwd_kernel.
-__global__ void out_sum_kernel(const float *part, int tiles, const float *b3, float *Y, int B, const float *map) {
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < B; row += gridDim.x * blockDim.x) {
-        float u0 = b3[0], u1 = b3[1];
-        float s0 = 0.f, s1 = 0.f;
-        for (int t = 0; t < tiles; ++t) {
-            s0 += part[((size_t)row * tiles + t) * 2];
-            s1 += part[((size_t)row * tiles + t) * 2 + 1];
-        }
-        u0 += s0, u1 += s1;
-        if (map) {
-            u0 = u0 * map[2] + map[0];
-            u1 = u1 * map[3] + map[1];
-        }
-        Y[2 * row] = u0;
-        Y[2 * row + 1] = u1;
-    }
-}
-
 // Raw outputs U against mapped targets t' = (T - mean) / scale, row weight
 // w = 1 + tail * max(0, t'_0) (the upper tail of the first target counts
 // more): dU = 2 w (U - t') / B; loss += w (U - t')^2 / B.
@@ -652,12 +631,9 @@ struct MlpWs {
     __nv_bfloat16 *h1, *h2, *dh1, *dh2;
     float *y, *dy, *loss;
     __nv_bfloat16 *t0, *t1;   // transposed operands ([512][B]) of the tensor-core weight gradients
-    float *part;              // [B][2 tiles][2]: layer 2's folded output-layer partial sums
 };
 
-size_t mlp_ws_bytes(uint32_t B) {
-    return 6 * (size_t)B * DH * 2 + 2 * (size_t)B * DO * 4 + (size_t)B * (DH / 256) * DO * 4 + 256 + 8 * 256;
-}
+size_t mlp_ws_bytes(uint32_t B) { return 6 * (size_t)B * DH * 2 + 2 * (size_t)B * DO * 4 + 256 + 7 * 256; }
 
 MlpWs carve(void *ws, uint32_t B) {
     uint8_t *p = (uint8_t *)ws;
@@ -676,7 +652,6 @@ MlpWs carve(void *ws, uint32_t B) {
     w.loss = (float *)take(4);
     w.t0 = (__nv_bfloat16 *)take((size_t)B * DH * 2);
     w.t1 = (__nv_bfloat16 *)take((size_t)B * DH * 2);
-    w.part = (float *)take((size_t)B * (DH / 256) * DO * 4);
     return w;
 }
 
@@ -685,14 +660,9 @@ uint32_t grid1(size_t n) { return (uint32_t)std::min<size_t>((n + 255) / 256, 40
 // One hidden layer, H = relu(A . W^T + b): on tcgen05 when selected (and the
 // shape allows it), else on the mma.sync GEMM.
 int dense_relu(hedl_mlp *mlp, const __nv_bfloat16 *A, const __nv_bfloat16 *W, const float *b, __nv_bfloat16 *H,
-               int M, int K, cudaStream_t s, const __nv_bfloat16 *w_out = nullptr, float *out_part = nullptr,
-               bool *folded = nullptr) {
-    if (folded) *folded = false;
-    UmmaArgs u{A, W, H, b, M, DH, K, K, K, DH, 1, 1, mlp->err, nullptr, w_out, out_part};
-    if (mlp->gemm == HEDL_GEMM_TCGEN05 && umma_shape_ok(u)) {
-        if (folded) *folded = w_out != nullptr;
-        return umma_gemm(u, s);
-    }
+               int M, int K, cudaStream_t s) {
+    UmmaArgs u{A, W, H, b, M, DH, K, K, K, DH, 1, 1, mlp->err, nullptr};
+    if (mlp->gemm == HEDL_GEMM_TCGEN05 && umma_shape_ok(u)) return umma_gemm(u, s);
     GemmArgs a{};
     a.A = A;
     a.B = W;
@@ -707,17 +677,10 @@ int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs 
                  bool mapped) {
     int e = dense_relu(mlp, X, mlp->wb + OFF_W1, mlp->w + OFF_B1, w.h1, (int)B, DI, s);
     if (e) return e;
-    // layer 2 on tcgen05 folds the output layer's dot products into its epilogue
-    bool folded = false;
-    e = dense_relu(mlp, w.h1, mlp->wb + OFF_W2, mlp->w + OFF_B2, w.h2, (int)B, DH, s, mlp->wb + OFF_W3, w.part,
-                   &folded);
+    e = dense_relu(mlp, w.h1, mlp->wb + OFF_W2, mlp->w + OFF_B2, w.h2, (int)B, DH, s);
     if (e) return e;
-    if (folded)
-        out_sum_kernel<<<grid1(B), 256, 0, s>>>(w.part, DH / 256, mlp->w + OFF_B3, w.y, (int)B,
-                                                mapped ? mlp->map : nullptr);
-    else
-        out_fwd_kernel<<<std::min<uint32_t>((B * 32 + 255) / 256, 148u * 8u), 256, 0, s>>>(
-            w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B, mapped ? mlp->map : nullptr);
+    out_fwd_kernel<<<std::min<uint32_t>((B * 32 + 255) / 256, 148u * 8u), 256, 0, s>>>(
+        w.h2, mlp->wb + OFF_W3, mlp->w + OFF_B3, w.y, (int)B, mapped ? mlp->map : nullptr);
     return cudaGetLastError();
 }
 
@@ -738,19 +701,18 @@ int grads_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, const float *T, uint32_t B
         transpose_bf16(w.dh2, (int)B, DH, DH, w.t0, (int)B, s);
         transpose_bf16(w.h1, (int)B, DH, DH, w.t1, (int)B, s);
         UmmaArgs u{w.t0, w.t1, mlp->g + OFF_W2, nullptr, DH, DH, (int)B, (int)B, (int)B, DH, 0, 0, mlp->err,
-                   nullptr, nullptr, nullptr};
+                   nullptr};
         e = umma_gemm(u, s);
         if (e) return e;
         // dH1 = (dH2 . W2) * [H1 > 0], with W2 kept transposed ([in][out], K-major)
-        UmmaArgs d{w.dh2, mlp->w2t, w.dh1, nullptr, (int)B, DH, DH, DH, DH, DH, 0, 1, mlp->err, w.h1, nullptr,
-                   nullptr};
+        UmmaArgs d{w.dh2, mlp->w2t, w.dh1, nullptr, (int)B, DH, DH, DH, DH, DH, 0, 1, mlp->err, w.h1};
         e = umma_gemm(d, s);
         if (e) return e;
         colsum_kernel<<<(DH + 255) / 256, 256, 0, s>>>(w.dh1, mlp->g + OFF_B1, (int)B, DH);
         transpose_bf16(w.dh1, (int)B, DH, DH, w.t0, (int)B, s);
         transpose_bf16(X, (int)B, DI, DI, w.t1, (int)B, s);
         UmmaArgs x{w.t0, w.t1, mlp->g + OFF_W1, nullptr, DH, DI, (int)B, (int)B, (int)B, DI, 0, 0, mlp->err,
-                   nullptr, nullptr, nullptr};
+                   nullptr};
         e = umma_gemm(x, s);
         if (e) return e;
         return cudaGetLastError();

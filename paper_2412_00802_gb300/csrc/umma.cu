@@ -113,11 +113,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
         : "memory");
 }
 
-// Epilogue of 32 columns of one row: bias, ReLU or mask, bf16 or FP32 store;
-// with a folded 2-output layer, the stored (bf16) values' dot products with
-// w_out's two rows are added to p0, p1 in column order.
-__device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, const uint32_t (&r)[32], float &p0,
-                                       float &p1) {
+// Epilogue of 32 columns of one row: bias, ReLU or mask, bf16 or FP32 store.
+__device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, const uint32_t (&r)[32]) {
     float v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -143,7 +140,6 @@ __device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, cons
     }
     if (g.out_bf16) {
         uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + (size_t)row * g.ldc + col);
-        const __nv_bfloat16 *w0 = g.w_out ? reinterpret_cast<const __nv_bfloat16 *>(g.w_out) + col : nullptr;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t w[4];
@@ -151,12 +147,6 @@ __device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, cons
             for (int e = 0; e < 4; ++e) {
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
                 w[e] = *reinterpret_cast<const uint32_t *>(&h);
-                if (g.w_out) {
-                    const int c = q * 8 + 2 * e;
-                    p0 += __low2float(h) * __bfloat162float(w0[c]) + __high2float(h) * __bfloat162float(w0[c + 1]);
-                    p1 += __low2float(h) * __bfloat162float(w0[g.N + c]) +
-                          __high2float(h) * __bfloat162float(w0[g.N + c + 1]);
-                }
             }
             dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
         }
@@ -284,7 +274,6 @@ __global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant_
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = (t / tiles_n) * UM, n0 = (t % tiles_n) * UN;
             const int row = m0 + (int)(q * 32 + lane);
-            float p0 = 0.f, p1 = 0.f;
             for (int c0 = 0; c0 < UN; c0 += 64) {   // two 32-column loads in flight per wait
                 uint32_t ra[32], rb[32];
                 const uint32_t ta = taddr + ((q * 32u) << 16) + bf * UN + (uint32_t)c0;
@@ -292,14 +281,9 @@ __global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant_
                 tmem_ld32(ta + 32u, rb);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row < g.M) {
-                    emit32(g, row, n0 + c0, ra, p0, p1);
-                    emit32(g, row, n0 + c0 + 32, rb, p0, p1);
+                    emit32(g, row, n0 + c0, ra);
+                    emit32(g, row, n0 + c0 + 32, rb);
                 }
-            }
-            if (g.w_out && row < g.M) {
-                float *op = g.out_part + ((size_t)row * tiles_n + (size_t)(t % tiles_n)) * 2;
-                op[0] = p0;
-                op[1] = p1;
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -320,8 +304,7 @@ __global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant_
 bool umma_shape_ok(const UmmaArgs &a) {
     return a.N % UN == 0 && a.K % UK == 0 && a.K > 0 && a.lda % 8 == 0 && a.ldb % 8 == 0 &&
            a.ldc % (a.out_bf16 ? 8 : 4) == 0 && ((uintptr_t)a.A & 15) == 0 && ((uintptr_t)a.B & 15) == 0 &&
-           ((uintptr_t)a.C & 15) == 0 && (!a.mask || (a.ldc % 8 == 0 && ((uintptr_t)a.mask & 15) == 0)) &&
-           (!a.w_out || (a.out_bf16 && a.out_part));
+           ((uintptr_t)a.C & 15) == 0 && (!a.mask || (a.ldc % 8 == 0 && ((uintptr_t)a.mask & 15) == 0));
 }
 
 namespace {
