@@ -30,13 +30,36 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 INTERPRETER = ["exec.cu", "device_common.cuh", "hedl_internal.h", "plan.cpp"]
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and with whitespace runs collapsed (string literals kept)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':                                   # string literal, escapes included
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def interpreter_digest() -> str:
-    """Digest of the interpreter's sources and build flags (recorded ncu counters stay valid
-    while it is unchanged)."""
+    """Digest of the interpreter's code (comments and layout ignored) and build flags:
+    recorded ncu counters stay valid while it is unchanged."""
     h = hashlib.sha256()
     for f in INTERPRETER:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(CSRC, f), encoding="utf-8") as fh:
+            h.update(f.encode() + _code_only(fh.read()).encode())
     # flags without paths: the checkout's location must not change the digest
     h.update(" ".join(a for a in ARCH + FLAGS if not os.path.isabs(a)).encode())
     return h.hexdigest()

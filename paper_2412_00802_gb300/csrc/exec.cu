@@ -1,14 +1,17 @@
 // Batched evaluation: one persistent interpreter kernel over a work queue of
-// (segment, tile) items (see plan.cpp for how a batch becomes segments).
+// (task, tile) items (see plan.cpp for how a batch becomes tasks).
 //
-// Each CTA pops an item, waits (bounded) until every segment it reads is
-// complete, then its warps run the segment's program over the tile: a stack
-// machine whose values are bitset words (one register set per lane, deeper
-// stack entries in shared memory), whose leaves load concept rows / slots,
-// evaluate data ranges by ballot, or evaluate role restrictions by the
-// warp-cooperative CSR walk.  A segment's result is written to its slot, or,
-// for a hypothesis root, reduced against the example sets by popcount (the
-// paper's coverage count, Algorithm 15) with one atomic per warp.
+// Each CTA pops an item, waits (bounded) until every task it reads is
+// complete, then its warps run the task over the tile.  A segment task is a
+// stack machine whose values are bitset words (one register set per lane,
+// deeper stack entries in shared memory), whose leaves load concept rows /
+// slots, evaluate data ranges by ballot, or evaluate a lone role restriction
+// by the warp's edge-stream CSR walk (role_stream).  A segment's result is
+// written to its slot, or, for a hypothesis root, reduced against the example
+// sets by popcount (the paper's coverage count, Algorithm 15) with one atomic
+// per warp.  A role group (up to 32 restrictions sharing a role, direction
+// and level) runs as two tasks: a transpose of its fillers into one 32-bit
+// word per individual, and one bit-sliced walk that evaluates all of them.
 //
 // Waits never spin unbounded: each gives up after the plan's timeout, sets an
 // abort flag and an error bit, and every CTA then leaves the kernel.

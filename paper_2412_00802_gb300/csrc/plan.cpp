@@ -17,10 +17,15 @@
 //   3. every materialized node and every hypothesis root becomes a segment:
 //      a role-free boolean program whose leaves are atoms, data ranges,
 //      slots and role restrictions over slots or concept rows;
-//   4. segments get levels (1 + the deepest producer of a slot they read) and
+//   4. role restrictions that share a role, direction and nesting depth with
+//      another one become bit-sliced role groups (up to 32 per group, evaluated
+//      by one transposed-filler walk) instead of living inside a segment;
+//   5. tasks get levels (1 + the deepest producer of a slot they read) and
 //      are grouped by (level, first role read); each group's work items are
-//      (segment, tile) pairs in tile-major order so that segments sweeping the
-//      same role stream the same CSR rows at about the same time.
+//      (task, tile) pairs in tile-major order so that tasks sweeping the same
+//      role stream the same CSR rows at about the same time;
+//   6. the tile shape: 32 words per warp, or 16 / 8 / 4 with one round when a
+//      level that walks a role holds too few tasks to fill the GPU.
 #include <algorithm>
 #include <cstring>
 #include <unordered_map>
