@@ -198,3 +198,11 @@ def test_canonical_batch_agrees_with_the_search_oracle(small):
         assert got[offs[i]:offs[i + 1]].tobytes() == OS.canonical(p), i
     with pytest.raises(H.HedlError):
         H.hedl_canonical_batch(np.array([P.insn(P.AND)], np.uint64), np.array([0, 1], np.uint32))
+
+
+def test_interpreter_digest_ignores_comments_not_code():
+    from paper_2412_00802_gb300 import build
+    assert build._code_only('int a = 1; // note\n/* block\n comment */ int b = "x//y" [0];') == \
+        'int a = 1; int b = "x//y" [0];'
+    assert build._code_only("x  =\n\n y;") == "x = y;"
+    assert build._code_only("a = 1;") != build._code_only("a = 2;")
