@@ -6,7 +6,8 @@ no code with the GPU library (``paper_2412_00802_gb300``) and never imports
 it.
 
 ``hedl_oracle.c`` is the evaluator (byte-per-membership sets, role
-assertions as (subject, object) pairs, the paper's Section III layout);
+assertions as (subject, object) pairs and numeric concrete-role assertions as
+(subject, value) pairs, the paper's Section III layout);
 ``fo_brute`` is a second, first-order-semantics evaluator in pure Python for
 tiny inputs, used to pin the C one.  This wrapper only marshals arrays.
 """
@@ -50,7 +51,11 @@ class _KB(ctypes.Structure):
                 ("subj", ctypes.c_void_p),
                 ("obj", ctypes.c_void_p),
                 ("n_props", ctypes.c_int32),
-                ("prop", ctypes.c_void_p)]
+                ("prop", ctypes.c_void_p),
+                ("n_num_roles", ctypes.c_int32),
+                ("num_off", ctypes.c_void_p),
+                ("num_subj", ctypes.c_void_p),
+                ("num_val", ctypes.c_void_p)]
 
 
 def load(path: str):
@@ -92,14 +97,25 @@ class OracleKB:
     prop: np.ndarray          # float32 [P][n]
     pos: np.ndarray           # uint8 [n]
     neg: np.ndarray           # uint8 [n]
+    # numeric concrete roles (property ids n_props + q): (subject, value) assertions per role
+    num_off: np.ndarray = None    # int64 [Q+1]
+    num_subj: np.ndarray = None   # uint32 [M]
+    num_val: np.ndarray = None    # float32 [M]
 
     def __post_init__(self):
-        for name in ("member", "role_off", "subj", "obj", "prop", "pos", "neg"):
+        if self.num_off is None:
+            self.num_off = np.zeros(1, np.int64)
+            self.num_subj = np.zeros(0, np.uint32)
+            self.num_val = np.zeros(0, np.float32)
+        for name in ("member", "role_off", "subj", "obj", "prop", "pos", "neg", "num_off", "num_subj", "num_val"):
             setattr(self, name, np.ascontiguousarray(getattr(self, name)))
         self._c = _KB(self.n, self.member.shape[0], _ptr(self.member) if self.member.size else None,
                       self.role_off.size - 1, _ptr(self.role_off), _ptr(self.subj) if self.subj.size else None,
                       _ptr(self.obj) if self.obj.size else None, self.prop.shape[0],
-                      _ptr(self.prop) if self.prop.size else None)
+                      _ptr(self.prop) if self.prop.size else None,
+                      self.num_off.size - 1, _ptr(self.num_off),
+                      _ptr(self.num_subj) if self.num_subj.size else None,
+                      _ptr(self.num_val) if self.num_val.size else None)
 
     @property
     def cptr(self):
@@ -107,8 +123,10 @@ class OracleKB:
 
     @classmethod
     def from_parts(cls, n: int, member: np.ndarray, edges: Sequence[Tuple[np.ndarray, np.ndarray]],
-                   prop: np.ndarray, pos: np.ndarray, neg: np.ndarray) -> "OracleKB":
-        """edges: per role (subjects, objects); each pair must appear at most once."""
+                   prop: np.ndarray, pos: np.ndarray, neg: np.ndarray,
+                   num_roles: Sequence[Tuple[np.ndarray, np.ndarray]] = ()) -> "OracleKB":
+        """edges: per role (subjects, objects); each pair must appear at most once.
+        num_roles: per numeric concrete role (subjects, float values), any order."""
         offs = [0]
         subj, obj = [], []
         for s, o in edges:
@@ -125,11 +143,23 @@ class OracleKB:
             subj.append(s)
             obj.append(o)
             offs.append(offs[-1] + s.size)
-        cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0, np.uint32)
+        cat = lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt)
+        noff, nsubj, nval = [0], [], []
+        for s_, v_ in num_roles:
+            s_ = np.asarray(s_, dtype=np.uint32)
+            v_ = np.asarray(v_, dtype=np.float32)
+            if s_.size != v_.size:
+                raise ValueError("a numeric assertion needs one subject and one value")
+            if s_.size and int(s_.max()) >= n:
+                raise ValueError("numeric assertion names an individual >= n")
+            nsubj.append(s_)
+            nval.append(v_)
+            noff.append(noff[-1] + s_.size)
         return cls(n, np.asarray(member, np.uint8).reshape(-1, n) if n else np.zeros((len(member), 0), np.uint8),
-                   np.array(offs, dtype=np.int64), cat(subj), cat(obj),
+                   np.array(offs, dtype=np.int64), cat(subj, np.uint32), cat(obj, np.uint32),
                    np.asarray(prop, np.float32).reshape(-1, n) if n else np.zeros((len(prop), 0), np.float32),
-                   np.asarray(pos, np.uint8), np.asarray(neg, np.uint8))
+                   np.asarray(pos, np.uint8), np.asarray(neg, np.uint8),
+                   np.array(noff, dtype=np.int64), cat(nsubj, np.uint32), cat(nval, np.float32))
 
 
 def from_synth(kb) -> OracleKB:
@@ -151,7 +181,11 @@ def from_synth(kb) -> OracleKB:
     pos[kb.pos_idx] = 1
     neg = np.zeros(n, dtype=np.uint8)
     neg[kb.neg_idx] = 1
-    return OracleKB.from_parts(n, member, edges, kb.prop_vals, pos, neg)
+    nums = []
+    for q in range(kb.n_num_roles):
+        deg = np.diff(kb.num_row_ptr[q].astype(np.int64))
+        nums.append((np.repeat(np.arange(n, dtype=np.uint32), deg), kb.num_vals[q]))
+    return OracleKB.from_parts(n, member, edges, kb.prop_vals, pos, neg, nums)
 
 
 def validate(okb: OracleKB, prog, L=None) -> int:

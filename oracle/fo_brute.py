@@ -15,7 +15,9 @@ to pin it:
     (ge p t)       = { x | some v: p(x, v) and v >= t }   (float32 compare)
 
 under the closed-world reading (Section III-A of the paper): a fact not in
-the KB is false, so NOT is the complement within the domain.
+the KB is false, so NOT is the complement within the domain.  A property maps
+an individual to one value or to several (a numeric concrete role, Section
+III-B); either way the restriction asks for some value.
 """
 from __future__ import annotations
 
@@ -30,12 +32,14 @@ _GE, _LE, _EQ = 12, 13, 14
 
 class TinyKB:
     def __init__(self, n: int, concepts: Sequence[Set[int]], roles: Sequence[Set[Tuple[int, int]]],
-                 props: Sequence[Dict[int, float]]):
+                 props: Sequence[Dict[int, object]]):
+        """props[p][x]: a float or a sequence of floats (x's values of p)."""
         self.n = n
         self.domain = range(n)
         self.concepts = [set(c) for c in concepts]
         self.roles = [set(r) for r in roles]
-        self.props = [{int(k): np.float32(v) for k, v in p.items()} for p in props]
+        self.props = [{int(k): tuple(np.float32(u) for u in (v if isinstance(v, (list, tuple)) else [v]))
+                       for k, v in p.items()} for p in props]
 
     def rel(self, r: int, inverse: bool, x: int, y: int) -> bool:
         return ((y, x) if inverse else (x, y)) in self.roles[r]
@@ -80,10 +84,9 @@ def evaluate(kb: TinyKB, prog: Sequence[int]) -> Set[int]:
             vals = kb.props[a]
             out = set()
             for x in D:
-                if x in vals:
-                    v = vals[x]
-                    if (op == _GE and v >= t) or (op == _LE and v <= t) or (op == _EQ and v == t):
-                        out.add(x)
+                if any((op == _GE and v >= t) or (op == _LE and v <= t) or (op == _EQ and v == t)
+                       for v in vals.get(x, ())):
+                    out.add(x)
             stack.append(out)
         else:
             raise ValueError(f"bad op {op}")

@@ -10,7 +10,11 @@
  * (1 = member), a concept's memberships of all individuals contiguous (the
  * transposed concepts matrix); role assertions as a 2-column (subject, object)
  * matrix grouped per role through an offset table; a numeric data property as
- * one float per individual, NaN where the individual has no value.
+ * one float per individual, NaN where the individual has no value; a numeric
+ * concrete role (Section III-B: a subject may assert several values) as a
+ * 2-column (subject, value) matrix grouped per role through its own offset
+ * table.  Property ids below n_props name the one-value properties, ids
+ * n_props + q the numeric concrete role q.
  *
  * Semantics (closed world, Section III-A: anything not asserted is false):
  *   ATOM c         members of c
@@ -27,7 +31,9 @@
  *   DGE p t        { a : a has a value v of p and v >= t }
  *   DLE p t        { a : a has a value v of p and v <= t }
  *   DEQ p t        { a : a has a value v of p and v == t }     (Algorithms 9-10)
- *                  (float32 compares; a missing value satisfies nothing)
+ *                  (float32 compares; a missing value satisfies nothing; on a
+ *                  numeric concrete role "a value" ranges over every
+ *                  assertion of the subject: an existential restriction)
  * Coverage (Algorithm 15): TP = |R & P|, FP = |R & N|; FN = |P| - TP and
  * TN = |N| - FP complete the confusion matrix.
  *
@@ -85,6 +91,10 @@ typedef struct {
     const uint32_t *obj;
     int32_t n_props;
     const float *prop;               /* [n_props][n] */
+    int32_t n_num_roles;             /* numeric concrete roles (property ids n_props + q) */
+    const int64_t *num_off;          /* [n_num_roles + 1] */
+    const uint32_t *num_subj;        /* [total numeric assertions] */
+    const float *num_val;
 } oracle_kb;
 
 static unsigned op_of(uint64_t w) { return (unsigned)(w & 0xFF); }
@@ -118,7 +128,8 @@ int oracle_validate(const oracle_kb *kb, const uint64_t *prog, int64_t len) {
         if (ar < 0) return OE_BAD_OP;
         if (op == O_ATOM && (int32_t)a_of(prog[k]) >= kb->n_concepts) return OE_BAD_ID;
         if (ar == 1 && op != O_NOT && (int32_t)a_of(prog[k]) >= kb->n_roles) return OE_BAD_ID;
-        if ((op == O_DGE || op == O_DLE || op == O_DEQ) && (int32_t)a_of(prog[k]) >= kb->n_props)
+        if ((op == O_DGE || op == O_DLE || op == O_DEQ) &&
+            (int64_t)a_of(prog[k]) >= (int64_t)kb->n_props + kb->n_num_roles)
             return OE_BAD_ID;
         if (depth < ar) return OE_UNDERFLOW;
         depth = depth - ar + 1;
@@ -162,7 +173,25 @@ static void op_count(const oracle_kb *kb, unsigned op, unsigned r, int inverse, 
     }
 }
 
+static int compare(unsigned op, float v, float t) {
+    if (op == O_DGE) return v >= t;
+    if (op == O_DLE) return v <= t;
+    return v == t;
+}
+
+/* Existential restriction on a numeric concrete role (Algorithms 9-10): a
+ * subject belongs as soon as one of its assertions satisfies the compare. */
+static void op_numeric_role(const oracle_kb *kb, unsigned op, unsigned q, float t, uint8_t *out) {
+    memset(out, 0, (size_t)kb->n);
+    for (int64_t k = kb->num_off[q]; k < kb->num_off[q + 1]; ++k)
+        if (compare(op, kb->num_val[k], t)) out[kb->num_subj[k]] = 1;
+}
+
 static void op_data(const oracle_kb *kb, unsigned op, unsigned p, float t, uint8_t *out) {
+    if ((int32_t)p >= kb->n_props) {
+        op_numeric_role(kb, op, p - (unsigned)kb->n_props, t, out);
+        return;
+    }
     const float *v = kb->prop + (int64_t)p * kb->n;
     for (int64_t i = 0; i < kb->n; ++i) {
         if (isnan(v[i])) { out[i] = 0; continue; }

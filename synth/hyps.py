@@ -8,7 +8,10 @@ Internal constructors are drawn uniformly from the feasible members of the
 allowed set; a role restriction reads its role inverted with probability 1/2
 and draws n uniformly from 1..4; leaves are an atomic concept with probability
 0.8, otherwise a data-range restriction (>= or <=, equally likely) whose
-threshold is a present value of the property at a random individual.
+threshold is a present value of the property at a random individual.  On a KB
+with numeric concrete roles the restricted property is drawn over the
+one-value properties and the numeric roles together; a numeric role takes >=,
+<= or == equally likely, with a threshold drawn from its asserted values.
 
 Shared sub-concepts: a pool of 256 seeded subtrees of depth 2..4; whenever
 the generator is about to build a subtree of depth >= 2 whose exact
@@ -23,7 +26,7 @@ import numpy as np
 
 from . import rng
 from .kb import KB
-from .programs import (AND, ATLEAST, ATMOST, ATOM, DGE, DLE, EXISTS, FORALL, NOT, OR,
+from .programs import (AND, ATLEAST, ATMOST, ATOM, DEQ, DGE, DLE, EXISTS, FORALL, NOT, OR,
                        Node, f32_bits, pack_batch)
 
 S_HYP = 7 << 16
@@ -45,10 +48,12 @@ class TreeGen:
         self.n_roles = kb.n_roles
         self.n_props = kb.n_props
         self.props = kb.prop_vals
+        self.n_num = kb.n_num_roles
+        self.num_vals = kb.num_vals
         self.seed = seed
         self.unary = tuple(unary)
         self.binary = tuple(binary)
-        self.p_atom = p_atom if self.n_props > 0 else 1.0
+        self.p_atom = p_atom if self.n_props + self.n_num > 0 else 1.0
         self.share = share
         self.pool: Dict[Tuple[int, int], List[Node]] = {}
         if share > 0:
@@ -73,6 +78,14 @@ class TreeGen:
 
     def leaf(self, r: rng.Rng) -> Node:
         if self.n_concepts == 0 or r.random() >= self.p_atom:
+            if self.n_num:
+                p = r.randint(0, self.n_props + self.n_num - 1)
+                if p >= self.n_props:
+                    vals = self.num_vals[p - self.n_props]
+                    t = float(vals[r.randint(0, vals.size - 1)]) if vals.size else 0.0
+                    return Node((DGE, DLE, DEQ)[r.randint(0, 2)], p, f32_bits(t))
+                op = DGE if r.random() < 0.5 else DLE
+                return Node(op, p, f32_bits(self._threshold(r, p)))
             p = r.randint(0, self.n_props - 1)
             op = DGE if r.random() < 0.5 else DLE
             return Node(op, p, f32_bits(self._threshold(r, p)))

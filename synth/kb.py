@@ -9,6 +9,9 @@ A KB here is plain host data:
   duplicate-free rows, plus the inverse CSR (the transpose), whose rows come out
   sorted because it is built by a stable sort of the forward edges by object;
 * numeric data properties as float32[n], NaN where the value is missing;
+* numeric concrete roles (several values per individual, Section III-B) as a
+  CSR over individuals (``num_row_ptr`` uint32[n+1], ``num_vals`` float32[M]);
+  their property ids follow the one-value properties' (``n_props + q``);
 * positive and negative example sets (bitsets and index lists).
 
 Degree laws, value distributions and example counts follow the workload
@@ -23,7 +26,7 @@ import math
 import os
 import subprocess
 import threading
-from dataclasses import dataclass, replace
+from dataclasses import dataclass, field, replace
 from typing import List, Optional, Tuple
 
 import numpy as np
@@ -78,6 +81,8 @@ S_CONCEPT = 1 << 16
 S_ROLE_DEG = 2 << 16
 S_ROLE_TGT = 3 << 16
 S_PROP = 4 << 16
+S_NUM_DEG = 12 << 16
+S_NUM_VAL = 13 << 16
 
 
 @dataclass(frozen=True)
@@ -97,6 +102,8 @@ class KBConfig:
     n_pos: int
     n_neg: int
     planted: bool = False    # examples from a latent class that some concepts, role 0 and property 0 track
+    n_num_roles: int = 0     # numeric concrete roles (values from prop_dist)
+    num_degree: Tuple = ("poisson", 3.0)   # values per individual: ("poisson", lam) | ("single", m) | ("unique",)
 
     def scaled(self, n: int, **kw) -> "KBConfig":
         """Same distributions on ``n`` individuals (example counts scaled)."""
@@ -121,6 +128,11 @@ CONFIGS = {
                    ("normal", 50.0, 15.0), 0.15, 50_000, 50_000, planted=True),
 }
 CONFIGS["surrogate"] = replace(CONFIGS["large"], name="surrogate", seed=4, planted=True)
+# numeric concrete roles: 10^7 individuals, 8 roles with Poisson(4) values each
+# (4 * 10^7 assertions, 200 MB per role), values U[0, 1000]
+CONFIGS["numeric"] = KBConfig("numeric", 6, 10_000_000, 8, 0.01, 0.50, False, 0, ("poisson", 3.0), 0,
+                              ("uniform", 0.0, 1000.0), 0.0, 10_000, 10_000, n_num_roles=8,
+                              num_degree=("poisson", 4.0))
 
 # Planted structure (workloads that search or learn need a signal): a latent
 # class Z (a uniform 20 % of the individuals) supplies the positives, its
@@ -306,6 +318,8 @@ class KB:
     pos_bits: np.ndarray              # uint32 [wp]
     neg_bits: np.ndarray
     meta: dict
+    num_row_ptr: List[np.ndarray] = field(default_factory=list)   # per numeric role uint32 [n+1]
+    num_vals: List[np.ndarray] = field(default_factory=list)      # per numeric role float32 [M]
 
     @property
     def n_concepts(self) -> int:
@@ -319,6 +333,10 @@ class KB:
     def n_props(self) -> int:
         return self.prop_vals.shape[0]
 
+    @property
+    def n_num_roles(self) -> int:
+        return len(self.num_row_ptr)
+
     def n_edges(self, r: int) -> int:
         return int(self.col[r].size)
 
@@ -326,6 +344,8 @@ class KB:
         t = self.concept_bits.nbytes + self.prop_vals.nbytes + 2 * self.pos_bits.nbytes
         for r in range(self.n_roles):
             t += 2 * self.row_ptr[r].nbytes + 2 * self.col[r].nbytes
+        for q in range(self.n_num_roles):
+            t += self.num_row_ptr[q].nbytes + self.num_vals[q].nbytes
         return t
 
 
@@ -370,21 +390,24 @@ def gen_concepts(cfg: KBConfig, wp: int, meta: dict, z=None) -> np.ndarray:
     return bits
 
 
+def draw_values(cfg: KBConfig, stream: int, m: int) -> np.ndarray:
+    """m float64 draws from the configuration's value distribution."""
+    kind = cfg.prop_dist[0]
+    if kind == "uniform":
+        lo, hi = cfg.prop_dist[1], cfg.prop_dist[2]
+        return lo + (hi - lo) * rng.uniform_range(cfg.seed, stream, m)
+    if kind == "lognormal":
+        return np.exp(cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, stream, m))
+    if kind == "normal":
+        return cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, stream, m)
+    raise ValueError(kind)
+
+
 def gen_props(cfg: KBConfig, z=None) -> np.ndarray:
     n = cfg.n
     out = np.empty((cfg.n_props, n), dtype=np.float32)
-    kind = cfg.prop_dist[0]
     for p in range(cfg.n_props):
-        st = S_PROP + p
-        if kind == "uniform":
-            lo, hi = cfg.prop_dist[1], cfg.prop_dist[2]
-            v = lo + (hi - lo) * rng.uniform_range(cfg.seed, st, n)
-        elif kind == "lognormal":
-            v = np.exp(cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, st, n))
-        elif kind == "normal":
-            v = cfg.prop_dist[1] + cfg.prop_dist[2] * rng.normal(cfg.seed, st, n)
-        else:
-            raise ValueError(kind)
+        v = draw_values(cfg, S_PROP + p, n)
         if z is not None and p == 0:   # planted: property 0 shifted up inside the latent class
             lo, hi = np.nanmin(v), np.nanmax(v)
             v = np.where(z, v + 0.25 * (hi - lo), v)
@@ -394,6 +417,31 @@ def gen_props(cfg: KBConfig, z=None) -> np.ndarray:
             v[miss] = np.nan
         out[p] = v
     return out
+
+
+def gen_num_roles(cfg: KBConfig) -> Tuple[List[np.ndarray], List[np.ndarray]]:
+    """Numeric concrete roles as CSR over individuals: the number of values of
+    each individual from ``num_degree`` (the paper's "single subject" and
+    "unique subject" shapes included), the values from ``prop_dist``."""
+    n = cfg.n
+    rps, vals = [], []
+    for q in range(cfg.n_num_roles):
+        kind = cfg.num_degree[0]
+        if kind == "poisson":
+            cdf = poisson_cdf(cfg.num_degree[1], 200)
+            deg = np.searchsorted(cdf, rng.uniform_range(cfg.seed, S_NUM_DEG + q, n), side="right")
+        elif kind == "single":       # one individual holds every value
+            deg = np.zeros(n, dtype=np.int64)
+            deg[int(rng.randint(cfg.seed, S_NUM_DEG + q, np.array([0]), n)[0])] = int(cfg.num_degree[1])
+        elif kind == "unique":       # one value per individual
+            deg = np.ones(n, dtype=np.int64)
+        else:
+            raise ValueError(kind)
+        rp = np.zeros(n + 1, dtype=np.uint32)
+        np.cumsum(deg, out=rp[1:])
+        rps.append(rp)
+        vals.append(draw_values(cfg, S_NUM_VAL + q, int(rp[-1])).astype(np.float32))
+    return rps, vals
 
 
 def gen_examples(cfg: KBConfig, wp: int, z=None) -> Tuple[np.ndarray, np.ndarray]:
@@ -442,13 +490,16 @@ def generate(cfg: KBConfig, roles: Optional[int] = None) -> KB:
     mp[pos] = True
     mn = np.zeros(n, dtype=bool)
     mn[neg] = True
+    nrp, nv = gen_num_roles(cfg)
     return KB(cfg, n, w, wp, cb, rps, cols, irps, icols, props, pos, neg,
-              pack_bits(mp, wp), pack_bits(mn, wp), meta)
+              pack_bits(mp, wp), pack_bits(mn, wp), meta, nrp, nv)
 
 
 def from_arrays(n: int, concepts: List[List[int]], roles: List[List[Tuple[int, int]]],
-                props: List[List[float]], pos: List[int], neg: List[int]) -> KB:
-    """Small hand-written KB (fixtures): concepts as member lists, roles as edge lists."""
+                props: List[List[float]], pos: List[int], neg: List[int],
+                num_roles: Optional[List[List[Tuple[int, float]]]] = None) -> KB:
+    """Small hand-written KB (fixtures): concepts as member lists, roles as edge
+    lists, numeric concrete roles as (individual, value) lists in any order."""
     w, wp = words(n)
     cb = np.zeros((max(len(concepts), 0), wp), dtype=np.uint32)
     for j, mem in enumerate(concepts):
@@ -475,5 +526,13 @@ def from_arrays(n: int, concepts: List[List[int]], roles: List[List[Tuple[int, i
     mn[list(neg)] = True
     cfg = KBConfig("fixture", 0, n, len(concepts), 0, 0, False, len(roles), ("fixture",), len(props),
                    ("fixture",), 0.0, len(pos), len(neg))
+    nrp, nv = [], []
+    for assertions in num_roles or []:
+        order = sorted(range(len(assertions)), key=lambda k: int(assertions[k][0]))   # stable: keeps value order
+        rp = np.zeros(n + 1, dtype=np.uint32)
+        for a, _ in assertions:
+            rp[int(a) + 1] += 1
+        nrp.append(np.cumsum(rp).astype(np.uint32))
+        nv.append(np.array([assertions[k][1] for k in order], dtype=np.float32))
     return KB(cfg, n, w, wp, cb, rps, cols, irps, icols, pv, np.array(sorted(pos), dtype=np.int64),
-              np.array(sorted(neg), dtype=np.int64), pack_bits(mp, wp), pack_bits(mn, wp), {})
+              np.array(sorted(neg), dtype=np.int64), pack_bits(mp, wp), pack_bits(mn, wp), {}, nrp, nv)

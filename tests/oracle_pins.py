@@ -16,7 +16,13 @@ Sources of truth:
   subject": one subject holds every assertion; "unique subject": each
   subject one assertion, here a permutation) and on sorted data values;
 * the transposed assertion list: EXISTS r^- C on a KB equals EXISTS r C on
-  the KB whose role is the (numpy-built) transpose.
+  the KB whose role is the (numpy-built) transpose;
+* numeric concrete roles (several values per subject, Section III-B,
+  Algorithms 9-10): closed forms through per-subject maxima / minima / value
+  sets (>= t iff the largest value is >= t, and so on), a hand-worked KB with
+  NaN and signed zeros, the single- and unique-subject shapes (the latter
+  against a one-value property holding the same values) and the identities
+  (>= t) or (<= t) = "has a value", (== t) within both.
 """
 from __future__ import annotations
 
@@ -70,6 +76,10 @@ def to_tiny(kb: K.KB) -> fo_brute.TinyKB:
         rp, col = kb.row_ptr[r], kb.col[r]
         roles.append({(a, int(col[k])) for a in range(n) for k in range(int(rp[a]), int(rp[a + 1]))})
     props = [{i: float(v) for i, v in enumerate(kb.prop_vals[p]) if not math.isnan(v)} for p in range(kb.n_props)]
+    for q in range(kb.n_num_roles):
+        rp, vals = kb.num_row_ptr[q], kb.num_vals[q]
+        props.append({i: [float(vals[k]) for k in range(int(rp[i]), int(rp[i + 1]))]
+                      for i in range(n) if rp[i + 1] > rp[i]})
     return fo_brute.TinyKB(n, concepts, roles, props)
 
 
@@ -81,6 +91,11 @@ def random_program(r: Rng, kb: K.KB, depth: int, role_free: bool = False) -> P.N
             return P.Node(P.TOP)
         if k == 1:
             return P.Node(P.BOT)
+        if k <= 3 and kb.n_num_roles and r.random() < 0.5:
+            q = r.randint(0, kb.n_num_roles - 1)
+            vals = kb.num_vals[q]
+            t = float(vals[r.randint(0, vals.size - 1)]) if vals.size else 1.0
+            return P.Node((P.DGE, P.DLE, P.DEQ)[r.randint(0, 2)], kb.n_props + q, P.f32_bits(t))
         if k <= 3 and kb.n_props:
             p = r.randint(0, kb.n_props - 1)
             vals = kb.prop_vals[p]
@@ -106,6 +121,10 @@ def tiny_kbs():
     for seed, n, deg in ((101, 20, ("poisson", 2.0)), (102, 33, ("poisson", 3.0)), (103, 40, ("poisson", 4.0)),
                          (104, 17, ("zipf", 2.1, 3.0, 16))):
         cfg = base.scaled(n, seed=seed, n_concepts=5, n_roles=3, degree=deg, n_props=2, n_pos=4, n_neg=4)
+        out.append(K.generate(cfg))
+    for seed, n, nd in ((105, 24, ("poisson", 2.0)), (106, 37, ("poisson", 1.0))):
+        cfg = base.scaled(n, seed=seed, n_concepts=4, n_roles=2, degree=("poisson", 2.0), n_props=1, n_pos=4,
+                          n_neg=4, n_num_roles=2, num_degree=nd)
         out.append(K.generate(cfg))
     return out
 
@@ -260,6 +279,74 @@ def pin_closed_forms(L) -> List[str]:
     return bad
 
 
+def _per_subject(kb, q):
+    """(has a value, largest value, smallest value, subject of each value) of numeric role q."""
+    rp = kb.num_row_ptr[q].astype(np.int64)
+    vals = kb.num_vals[q].astype(np.float32)
+    subj = np.repeat(np.arange(kb.n), np.diff(rp))
+    present = ~np.isnan(vals)
+    has = np.zeros(kb.n, bool)
+    has[subj[present]] = True
+    mx = np.full(kb.n, -np.inf, np.float32)
+    np.maximum.at(mx, subj[present], vals[present])
+    mn = np.full(kb.n, np.inf, np.float32)
+    np.minimum.at(mn, subj[present], vals[present])
+    return has, mx, mn, subj, vals
+
+
+def pin_numeric_roles(L) -> List[str]:
+    bad = []
+    base = K.CONFIGS["small"]
+    ev = lambda okb, op, p, t: oracle.eval_program(okb, [P.insn(op, 0, p, P.f32_bits(t))], L=L)
+    # closed forms: some value >= t iff the largest is; <= t iff the smallest is; == t iff t is among them
+    for seed, n, nd in ((111, 300, ("poisson", 2.5)), (112, 97, ("single", 40)), (113, 200, ("unique",))):
+        kb = K.generate(base.scaled(n, seed=seed, n_concepts=2, n_roles=1, degree=("poisson", 2.0), n_props=1,
+                                    n_pos=10, n_neg=10, n_num_roles=3, num_degree=nd))
+        okb = oracle.from_synth(kb)
+        for q in range(kb.n_num_roles):
+            has, mx, mn, subj, vals = _per_subject(kb, q)
+            srt = np.sort(vals)
+            for t in (float(srt[0]), float(srt[len(srt) // 2]), float(srt[-1]), float(np.nextafter(srt[-1], 2e3)),
+                      -0.0, 0.0, 500.0, math.inf, -math.inf):
+                t32 = np.float32(t)
+                eq = np.zeros(kb.n, bool)
+                eq[subj[vals == t32]] = True
+                for op, want in ((P.DGE, has & (mx >= t32)), (P.DLE, has & (mn <= t32)), (P.DEQ, eq)):
+                    if not np.array_equal(ev(okb, op, kb.n_props + q, t), want):
+                        bad.append(f"numeric closed form {nd[0]} q={q} op={op} t={t}")
+                ge, le, eqs = (ev(okb, op, kb.n_props + q, t) for op in (P.DGE, P.DLE, P.DEQ))
+                if not np.array_equal(ge | le, has) or (eqs & ~(ge & le)).any():
+                    bad.append(f"numeric identities {nd[0]} q={q} t={t}")
+            if nd[0] == "single":
+                r = ev(okb, P.DGE, kb.n_props + q, float(srt[0]))
+                if int(r.sum()) != 1 or not r[subj[0]]:
+                    bad.append(f"single subject q={q}: {np.nonzero(r)[0].tolist()}")
+            if nd[0] == "unique":
+                # one value per subject: the same as a one-value property holding those values
+                col = np.full(kb.n, np.nan, np.float32)
+                col[subj] = vals
+                dense = oracle.OracleKB.from_parts(kb.n, np.zeros((0, kb.n), np.uint8), [], col[None, :],
+                                                   okb.pos, okb.neg)
+                for t in (float(srt[3]), float(srt[-5]), 0.0):
+                    for op in (P.DGE, P.DLE, P.DEQ):
+                        if not np.array_equal(ev(okb, op, kb.n_props + q, t), ev(dense, op, 0, t)):
+                            bad.append(f"unique subject q={q} op={op} t={t}")
+    # hand-worked: individual 0 holds {1.5, NaN}, 2 holds {-0.0}, 3 holds {NaN},
+    # 4 holds {7, 2, 9}, 5 holds {+0.0}; 1 holds nothing (a missing value)
+    nan = float("nan")
+    a = [(4, 7.0), (0, 1.5), (2, -0.0), (4, 2.0), (3, nan), (0, nan), (4, 9.0), (5, 0.0)]
+    okb = oracle.OracleKB.from_parts(6, np.zeros((0, 6), np.uint8), [], np.full((1, 6), np.nan, np.float32),
+                                     np.zeros(6, np.uint8), np.zeros(6, np.uint8),
+                                     [(np.array([s for s, _ in a]), np.array([v for _, v in a], np.float32))])
+    for op, t, want in ((P.DGE, 2.0, {4}), (P.DLE, 1.5, {0, 2, 5}), (P.DEQ, 0.0, {2, 5}), (P.DEQ, -0.0, {2, 5}),
+                        (P.DEQ, 2.0, {4}), (P.DEQ, nan, set()), (P.DGE, nan, set()), (P.DGE, -math.inf, {0, 2, 4, 5}),
+                        (P.DLE, math.inf, {0, 2, 4, 5}), (P.DGE, 9.5, set()), (P.DLE, -1.0, set())):
+        got = set(np.nonzero(ev(okb, op, 1, t))[0].tolist())
+        if got != want:
+            bad.append(f"hand-worked numeric role op={op} t={t}: {sorted(got)} != {sorted(want)}")
+    return bad
+
+
 def pin_validation(L) -> List[str]:
     fx = golden_io.load("family.txt")
     okb = tiny_from_fixture(fx)
@@ -283,7 +370,16 @@ def pin_validation(L) -> List[str]:
         got = oracle.validate(okb, np.array(prog, dtype=np.uint64), L=L)
         if got != want:
             bad.append(f"validate {prog[:3]}...: {got} != {want}")
+    # property ids: n_props one-value properties, then the numeric concrete roles
+    nkb = oracle.OracleKB.from_parts(3, np.zeros((0, 3), np.uint8), [], np.zeros((2, 3), np.float32),
+                                     np.zeros(3, np.uint8), np.zeros(3, np.uint8),
+                                     [(np.array([0]), np.array([1.0]))] * 2)
+    for p, want in ((1, 0), (2, 0), (3, 0), (4, -2)):
+        got = oracle.validate(nkb, np.array([P.insn(P.DGE, 0, p, 0)], dtype=np.uint64), L=L)
+        if got != want:
+            bad.append(f"validate property id {p}: {got} != {want}")
     return bad
 
 
-ALL_PINS = (pin_golden, pin_brute_force, pin_identities, pin_inverse_transpose, pin_closed_forms, pin_validation)
+ALL_PINS = (pin_golden, pin_brute_force, pin_identities, pin_inverse_transpose, pin_closed_forms,
+            pin_numeric_roles, pin_validation)
