@@ -85,6 +85,11 @@ typedef enum {
  *                 the inverse CSR
  *   DGE/DLE/DEQ   a whose value of property p is >= / <= / == t (float32
  *                 compares; a missing value, NaN, satisfies none) (Algs 9-10)
+ *                 Property ids below n_props name one-value properties (a
+ *                 float column); id n_props + q names numeric concrete role q
+ *                 (Section III-B: a subject may assert several values), on
+ *                 which the restriction is existential: a belongs as soon as
+ *                 one of its values passes the compare.
  */
 typedef enum {
     HEDL_OP_ATOM = 1, HEDL_OP_TOP = 2, HEDL_OP_BOT = 3, HEDL_OP_NOT = 4,
@@ -112,6 +117,17 @@ typedef struct {
     uint32_t n_edges;          /* < 2^31 */
 } hedl_csr;
 
+/* One numeric concrete role (Section III-B): the (subject, value) assertions
+ * grouped by subject as CSR.  Device arrays: row_ptr uint32[n_indiv+1] with
+ * row_ptr[0] = 0, non-decreasing, row_ptr[n_indiv] = n_vals; vals
+ * float32[n_vals], subject i's values at vals[row_ptr[i] .. row_ptr[i+1]) in
+ * any order (duplicates allowed; a NaN value satisfies no compare). */
+typedef struct {
+    const uint32_t *row_ptr;
+    const float *vals;
+    uint32_t n_vals;           /* < 2^31 */
+} hedl_numeric_role;
+
 typedef struct {
     uint32_t n_indiv;                  /* individuals, >= 1 */
     uint32_t n_concepts;
@@ -122,6 +138,8 @@ typedef struct {
     uint32_t n_props;
     const float *prop_vals;            /* device, [n_props][prop_stride], NaN = missing */
     uint64_t prop_stride;              /* floats between property rows, >= n_indiv */
+    uint32_t n_num_roles;              /* numeric concrete roles: property ids n_props + q */
+    const hedl_numeric_role *num_roles;/* HOST array [n_num_roles] of device CSRs */
 } hedl_kb_desc;
 
 typedef struct hedl_kb hedl_kb;
@@ -130,16 +148,19 @@ typedef struct hedl_kb hedl_kb;
 
 /* Register a knowledge base resident on the device (Section III-A).
  * Borrows every device array of d (see the conventions above); copies the
- * small host arrays roles / inv_roles.  Unless HEDL_KB_NO_VALIDATE, checks on
+ * small host arrays roles / inv_roles / num_roles.  n_props + n_num_roles is
+ * at most 65536 (16-bit property ids).  Unless HEDL_KB_NO_VALIDATE, checks on
  * the device that concept rows have zero tails, that each CSR is well formed
- * (monotone row_ptr, rows strictly increasing, ids < n) and that each inverse
- * CSR is exactly the transpose of its forward CSR; a failed check returns
- * HEDL_ERR_BAD_KB and no handle.  SYNCHRONIZES the stream.
+ * (monotone row_ptr, rows strictly increasing, ids < n), that each inverse
+ * CSR is exactly the transpose of its forward CSR and that each numeric
+ * role's row_ptr starts at 0, never decreases and ends at n_vals; a failed
+ * check returns HEDL_ERR_BAD_KB and no handle.  With HEDL_KB_NO_VALIDATE the
+ * caller guarantees all of that.  SYNCHRONIZES the stream.
  * *out receives the handle; release it with hedl_kb_free. */
 int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb **out);
 
-/* A planning-only handle: reads only the sizes in d (n_indiv, the counts and
- * each role's n_edges; pointers may be NULL) and makes no CUDA call, so it
+/* A planning-only handle: reads only the sizes in d (n_indiv, the counts,
+ * each role's n_edges and each numeric role's n_vals; pointers may be NULL) and makes no CUDA call, so it
  * works on a host without a GPU.  hedl_validate, hedl_plan_batch and
  * hedl_plan_info_get accept it (its plans are shaped for a 152-SM GB300);
  * every call that would launch work returns HEDL_ERR_INVALID_ARG.  Release

@@ -64,10 +64,15 @@ class hedl_csr(ctypes.Structure):
     _fields_ = [("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n_edges", ctypes.c_uint32)]
 
 
+class hedl_numeric_role(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("n_vals", ctypes.c_uint32)]
+
+
 class hedl_kb_desc(ctypes.Structure):
     _fields_ = [("n_indiv", ctypes.c_uint32), ("n_concepts", ctypes.c_uint32), ("concept_bits", ctypes.c_void_p),
                 ("n_roles", ctypes.c_uint32), ("roles", ctypes.c_void_p), ("inv_roles", ctypes.c_void_p),
-                ("n_props", ctypes.c_uint32), ("prop_vals", ctypes.c_void_p), ("prop_stride", ctypes.c_uint64)]
+                ("n_props", ctypes.c_uint32), ("prop_vals", ctypes.c_void_p), ("prop_stride", ctypes.c_uint64),
+                ("n_num_roles", ctypes.c_uint32), ("num_roles", ctypes.c_void_p)]
 
 
 class hedl_plan_info(ctypes.Structure):
@@ -208,9 +213,11 @@ class KBHandle:
 
 
 def hedl_kb_load(n_indiv: int, concept_bits, roles: Sequence[Tuple[object, object]],
-                 inv_roles: Sequence[Tuple[object, object]], prop_vals, flags: int = 0, stream=None) -> KBHandle:
+                 inv_roles: Sequence[Tuple[object, object]], prop_vals, flags: int = 0, stream=None,
+                 num_roles: Sequence[Tuple[object, object]] = ()) -> KBHandle:
     """concept_bits: CUDA [C, row_words] 32-bit tensor; roles / inv_roles: (row_ptr, col) CUDA int32 tensors;
-    prop_vals: CUDA float32 [P, stride] (or None)."""
+    prop_vals: CUDA float32 [P, stride] (or None); num_roles: (row_ptr int32, vals float32) CUDA tensors
+    of the numeric concrete roles (property ids P + q)."""
     n_roles = len(roles)
     csr = (hedl_csr * max(n_roles, 1))()
     icsr = (hedl_csr * max(n_roles, 1))()
@@ -221,25 +228,37 @@ def hedl_kb_load(n_indiv: int, concept_bits, roles: Sequence[Tuple[object, objec
         icsr[r] = hedl_csr(_dptr(rp), _dptr(col) if col.numel() else None, int(col.numel()))
     n_c = int(concept_bits.shape[0]) if concept_bits is not None else 0
     n_p = int(prop_vals.shape[0]) if prop_vals is not None else 0
+    Q = len(num_roles)
+    nums = (hedl_numeric_role * max(Q, 1))()
+    for q, (rp, vals) in enumerate(num_roles):
+        nums[q] = hedl_numeric_role(_dptr(rp), _dptr(vals) if vals.numel() else None, int(vals.numel()))
     d = hedl_kb_desc(n_indiv, n_c, _dptr(concept_bits) if n_c else None, n_roles,
                      ctypes.addressof(csr) if n_roles else None, ctypes.addressof(icsr) if n_roles else None,
-                     n_p, _dptr(prop_vals) if n_p else None, int(prop_vals.stride(0)) if n_p else 0)
+                     n_p, _dptr(prop_vals) if n_p else None, int(prop_vals.stride(0)) if n_p else 0,
+                     Q, ctypes.addressof(nums) if Q else None)
     out = ctypes.c_void_p()
     _check(library().hedl_kb_load(ctypes.byref(d), flags, _stream(stream), ctypes.byref(out)))
-    return KBHandle(out.value, [concept_bits, roles, inv_roles, prop_vals], n_indiv, hedl_row_words(n_indiv))
+    return KBHandle(out.value, [concept_bits, roles, inv_roles, prop_vals, num_roles], n_indiv,
+                    hedl_row_words(n_indiv))
 
 
-def hedl_kb_plan_only(n_indiv: int, n_concepts: int, role_edges: Sequence[int], n_props: int) -> KBHandle:
+def hedl_kb_plan_only(n_indiv: int, n_concepts: int, role_edges: Sequence[int], n_props: int,
+                      num_role_vals: Sequence[int] = ()) -> KBHandle:
     """Planning-only handle from sizes (no CUDA call; works without a GPU)."""
     R = len(role_edges)
     csr = (hedl_csr * max(R, 1))()
     for r, e in enumerate(role_edges):
         csr[r] = hedl_csr(None, None, int(e))
+    Q = len(num_role_vals)
+    nums = (hedl_numeric_role * max(Q, 1))()
+    for q, m in enumerate(num_role_vals):
+        nums[q] = hedl_numeric_role(None, None, int(m))
     d = hedl_kb_desc(n_indiv, n_concepts, None, R, ctypes.addressof(csr) if R else None,
-                     ctypes.addressof(csr) if R else None, n_props, None, n_indiv)
+                     ctypes.addressof(csr) if R else None, n_props, None, n_indiv,
+                     Q, ctypes.addressof(nums) if Q else None)
     out = ctypes.c_void_p()
     _check(library().hedl_kb_plan_only(ctypes.byref(d), ctypes.byref(out)))
-    return KBHandle(out.value, [csr], n_indiv, hedl_row_words(n_indiv))
+    return KBHandle(out.value, [csr, nums], n_indiv, hedl_row_words(n_indiv))
 
 
 def hedl_kb_free(kb: KBHandle):
@@ -507,7 +526,8 @@ class DeviceKB:
     def __init__(self, n: int, concept_bits: np.ndarray, row_ptr: List[np.ndarray], col: List[np.ndarray],
                  inv_row_ptr: List[np.ndarray], inv_col: List[np.ndarray], prop_vals: np.ndarray,
                  pos_bits: Optional[np.ndarray] = None, neg_bits: Optional[np.ndarray] = None,
-                 device: str = "cuda", flags: int = 0):
+                 device: str = "cuda", flags: int = 0, num_row_ptr: Sequence[np.ndarray] = (),
+                 num_vals: Sequence[np.ndarray] = ()):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -525,9 +545,11 @@ class DeviceKB:
         if P:
             pv[:, :n] = prop_vals
         self.props = torch.from_numpy(pv).to(self.device) if P else None
+        self.num_roles = [(t(rp, np.int32), t(np.asarray(v, np.float32), np.float32))
+                          for rp, v in zip(num_row_ptr, num_vals)]
         with torch.cuda.device(self.device):
             self.handle = hedl_kb_load(n, self.concepts if self.concepts.shape[0] else None, self.roles,
-                                       self.inv_roles, self.props, flags)
+                                       self.inv_roles, self.props, flags, num_roles=self.num_roles)
             if pos_bits is not None:
                 self.set_examples(pos_bits, neg_bits)
         self._ws = None
@@ -535,7 +557,8 @@ class DeviceKB:
     @classmethod
     def from_synth(cls, kb, device: str = "cuda", flags: int = 0) -> "DeviceKB":
         return cls(kb.n, kb.concept_bits, kb.row_ptr, kb.col, kb.inv_row_ptr, kb.inv_col, kb.prop_vals,
-                   kb.pos_bits, kb.neg_bits, device, flags)
+                   kb.pos_bits, kb.neg_bits, device, flags, getattr(kb, "num_row_ptr", ()),
+                   getattr(kb, "num_vals", ()))
 
     def set_examples(self, pos_bits: np.ndarray, neg_bits: np.ndarray):
         self.pos = self.torch.from_numpy(np.ascontiguousarray(pos_bits).view(np.int32)).to(self.device)

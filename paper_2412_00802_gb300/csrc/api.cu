@@ -35,6 +35,7 @@ hedl::KBView hedl_kb::view() const {
     KBView v{};
     v.concepts = concepts;
     v.csr = csr_dev;
+    v.num = num_dev;
     v.props = props;
     v.prop_stride = prop_stride;
     v.pos = pos;
@@ -66,6 +67,21 @@ void destroy_graph(PlanImpl *p) {
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// Host checks of the numeric concrete roles of a descriptor (arrays only when
+// the handle will read them).
+int check_num_roles(const hedl_kb_desc *d, bool arrays) {
+    if ((uint64_t)d->n_props + d->n_num_roles > 65536)
+        return fail(HEDL_ERR_INVALID_ARG, "at most 65536 properties and numeric roles together (16-bit ids)");
+    if (d->n_num_roles && !d->num_roles) return fail(HEDL_ERR_INVALID_ARG, "num_roles is NULL");
+    for (uint32_t q = 0; q < d->n_num_roles; ++q) {
+        const hedl_numeric_role &g = d->num_roles[q];
+        if (g.n_vals >= 0x80000000u) return fail(HEDL_ERR_INVALID_ARG, "a numeric role has 2^31 or more values");
+        if (arrays && (!g.row_ptr || (g.n_vals && !g.vals)))
+            return fail(HEDL_ERR_INVALID_ARG, "numeric role " + std::to_string(q) + ": NULL array");
+    }
+    return HEDL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -88,6 +104,7 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
     if (d->n_roles && (!d->roles || !d->inv_roles)) return fail(HEDL_ERR_INVALID_ARG, "roles / inv_roles is NULL");
     if (d->n_props && (!d->prop_vals || d->prop_stride < d->n_indiv))
         return fail(HEDL_ERR_INVALID_ARG, "prop_vals is NULL or prop_stride < n_indiv");
+    if (int e = check_num_roles(d, true)) return e;
     if (d->concept_bits && !aligned(d->concept_bits, 16))
         return fail(HEDL_ERR_INVALID_ARG, "concept_bits must be 16-byte aligned");
     for (uint32_t r = 0; r < d->n_roles; ++r) {
@@ -115,6 +132,9 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
         kb->csr_host[2 * r + 1] = DevCSR{d->inv_roles[r].row_ptr, d->inv_roles[r].col, d->inv_roles[r].n_edges, 0};
         kb->role_edges[r] = d->roles[r].n_edges;
     }
+    kb->n_num = d->n_num_roles;
+    for (uint32_t q = 0; q < d->n_num_roles; ++q)
+        kb->num_host.push_back(DevNum{d->num_roles[q].row_ptr, d->num_roles[q].vals, d->num_roles[q].n_vals, 0});
     cudaError_t e = cudaGetDevice(&kb->device);
     if (!e) e = cudaDeviceGetAttribute(&kb->n_sms, cudaDevAttrMultiProcessorCount, kb->device);
     int optin = 0;
@@ -126,6 +146,10 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
     if (!e && d->n_roles)
         e = cudaMemcpyAsync(kb->csr_dev, kb->csr_host.data(), sizeof(DevCSR) * kb->csr_host.size(),
                             cudaMemcpyHostToDevice, (cudaStream_t)s);
+    if (!e && kb->n_num) e = cudaMalloc(&kb->num_dev, sizeof(DevNum) * kb->n_num);
+    if (!e && kb->n_num)
+        e = cudaMemcpyAsync(kb->num_dev, kb->num_host.data(), sizeof(DevNum) * kb->n_num, cudaMemcpyHostToDevice,
+                            (cudaStream_t)s);
     if (!e) e = cudaStreamSynchronize((cudaStream_t)s);
     if (e) {
         int rc = cuda_fail(e, "hedl_kb_load");
@@ -157,6 +181,7 @@ int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out) {
     if (d->n_concepts > 65536 || d->n_roles > 65536 || d->n_props > 65536)
         return fail(HEDL_ERR_INVALID_ARG, "at most 65536 concepts, roles and properties (16-bit ids)");
     if (d->n_roles && (!d->roles || !d->inv_roles)) return fail(HEDL_ERR_INVALID_ARG, "roles / inv_roles is NULL");
+    if (int e = check_num_roles(d, false)) return e;
     auto *kb = new hedl_kb();
     kb->plan_only = true;
     kb->n = d->n_indiv;
@@ -173,6 +198,8 @@ int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out) {
         kb->csr_host[2 * r + 1] = DevCSR{nullptr, nullptr, d->inv_roles[r].n_edges, 0};
         kb->role_edges[r] = d->roles[r].n_edges;
     }
+    kb->n_num = d->n_num_roles;
+    for (uint32_t q = 0; q < d->n_num_roles; ++q) kb->num_host.push_back(DevNum{nullptr, nullptr, d->num_roles[q].n_vals, 0});
     *out = kb;
     return HEDL_OK;
 }
@@ -188,6 +215,7 @@ void hedl_kb_free(hedl_kb *kb) {
     drop_cached_plan(kb);
     if (kb->capture_stream) cudaStreamDestroy((cudaStream_t)kb->capture_stream);
     if (kb->csr_dev) cudaFree(kb->csr_dev);
+    if (kb->num_dev) cudaFree(kb->num_dev);
     if (kb->status_dev) cudaFree(kb->status_dev);
     delete kb;
 }

@@ -379,6 +379,56 @@ __device__ __forceinline__ void data_words(const float *__restrict__ vals, uint3
     }
 }
 
+__device__ __forceinline__ bool data_cmp(uint32_t cmp, float x, float t) {
+    return cmp == HEDL_OP_DGE ? (x >= t) : cmp == HEDL_OP_DLE ? (x <= t) : (x == t);
+}
+
+// Existential restriction on a numeric concrete role (Algorithms 9-10 with
+// several values per subject, Section III-B): individual i belongs iff one of
+// vals[rp[i] .. rp[i+1]) passes the compare.  The 32 individuals of a word own
+// one contiguous run of values; the warp reads it 64 values a step (two
+// coalesced loads), ballots the compares, and each lane tests the bits that
+// fall in its own sub-range.  The warp leaves the run once every individual
+// whose values reach past the step has found one (the paper's skip over a
+// subject already satisfied), so a heavy subject costs 1/32 of a lane walk.
+template <int WPL>
+__device__ __forceinline__ void num_words(const DevNum g, uint32_t cmp, float t, uint32_t n, uint32_t n_words,
+                                          uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
+    for (int j = 0; j < 32; ++j) {
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) {
+            const uint32_t w = wb + (uint32_t)j * WPL + s;
+            uint32_t word = 0;
+            if (w < n_words) {   // warp-uniform; then lane 0's individual 32w < n exists
+                const uint32_t i = w * 32u + lane;
+                uint32_t lo = 0, hi = 0;   // individuals >= n own no values
+                if (i < n) {
+                    lo = ld_stream(g.rp + i);
+                    hi = ld_stream(g.rp + i + 1);
+                }
+                const uint32_t base = __shfl_sync(FULL, lo, 0);
+                const uint32_t end = __reduce_max_sync(FULL, hi);
+                bool hit = false;
+                for (uint32_t c = base; c < end; c += 64u) {
+                    const uint32_t k0 = c + lane, k1 = c + 32u + lane;
+                    float x0 = 0.f, x1 = 0.f;
+                    if (k0 < end) x0 = __ldg(g.vals + k0);
+                    if (k1 < end) x1 = __ldg(g.vals + k1);
+                    const uint32_t m0 = __ballot_sync(FULL, k0 < end && data_cmp(cmp, x0, t));
+                    const uint32_t m1 = __ballot_sync(FULL, k1 < end && data_cmp(cmp, x1, t));
+                    const uint32_t a0 = lo > c ? min(lo - c, 32u) : 0u, b0 = hi > c ? min(hi - c, 32u) : 0u;
+                    const uint32_t c1 = c + 32u;
+                    const uint32_t a1 = lo > c1 ? min(lo - c1, 32u) : 0u, b1 = hi > c1 ? min(hi - c1, 32u) : 0u;
+                    hit = hit || (m0 & range_mask(a0, b0)) != 0u || (m1 & range_mask(a1, b1)) != 0u;
+                    if (__all_sync(FULL, hit || hi <= c + 64u)) break;
+                }
+                word = __ballot_sync(FULL, hit);
+            }
+            if (lane == (uint32_t)j) v[s] = word;
+        }
+    }
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

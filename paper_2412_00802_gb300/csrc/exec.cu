@@ -109,8 +109,12 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 for (int s = 0; s < WPL; ++s) top[s] = 0u;
                 break;
             case D_DATA:
-                data_words<WPL>(kb.props + (uint64_t)d.a * kb.prop_stride, (d.op >> 16) & 0xFFu,
-                                __uint_as_float(d.b), kb.n, lim_w, wb, lane, top);
+                if ((d.op >> 8) & 1u)
+                    num_words<WPL>(kb.num[d.a], (d.op >> 16) & 0xFFu, __uint_as_float(d.b), kb.n, lim_w, wb, lane,
+                                   top);
+                else
+                    data_words<WPL>(kb.props + (uint64_t)d.a * kb.prop_stride, (d.op >> 16) & 0xFFu,
+                                    __uint_as_float(d.b), kb.n, lim_w, wb, lane, top);
                 break;
             default: {  // D_ROLE
                 const uint32_t inv = (d.op >> 8) & 1u;

@@ -19,10 +19,19 @@ struct DevCSR {
     uint32_t pad;
 };
 
+// A numeric concrete role: CSR of values over subjects.
+struct DevNum {
+    const uint32_t *rp;    // [n+1]
+    const float *vals;     // [n_vals]
+    uint32_t n_vals;
+    uint32_t pad;
+};
+
 // Passed by value to every kernel.
 struct KBView {
     const uint32_t *concepts;    // [C][wp]
     const DevCSR *csr;           // device [2*R]: role r forward at 2r, inverse at 2r+1
+    const DevNum *num;           // device [Q]: the numeric concrete roles
     const float *props;          // [P][prop_stride]
     uint64_t prop_stride;
     const uint32_t *pos;         // [wp] or null
@@ -41,7 +50,8 @@ enum : uint32_t { ST_TIMEOUT = 1u, ST_DEVICE_CHECK = 2u };
 enum : uint32_t {
     D_ATOM = 1, D_TOP = 2, D_BOT = 3, D_NOT = 4, D_AND = 5, D_OR = 6,
     D_ROLE = 7,      // aux = kind (HEDL_OP_EXISTS..EXACTLY), a = role, flags bit0 = inverse, b = n
-    D_DATA = 12,     // aux = cmp (HEDL_OP_DGE/DLE/DEQ), a = property, b = float bits
+    D_DATA = 12,     // aux = cmp (HEDL_OP_DGE/DLE/DEQ), b = float bits; bit 8 of the op
+                     // word clear: a = one-value property, set: a = numeric role
     D_SLOT = 32      // a materialized bitset: ref = slot index
 };
 constexpr uint32_t REF_SLOT = 0x80000000u;   // filler ref: slot (low bits) vs concept id
@@ -147,13 +157,15 @@ struct PlanImpl;
 
 struct hedl_kb {
     uint32_t n = 0, w = 0, wp = 0;
-    uint32_t n_concepts = 0, n_roles = 0, n_props = 0;
+    uint32_t n_concepts = 0, n_roles = 0, n_props = 0, n_num = 0;
     const uint32_t *concepts = nullptr;
     const float *props = nullptr;
     uint64_t prop_stride = 0;
     std::vector<hedl::DevCSR> csr_host;     // [2R]
     std::vector<uint32_t> role_edges;       // [R] forward edge counts
     hedl::DevCSR *csr_dev = nullptr;
+    std::vector<hedl::DevNum> num_host;     // [Q] numeric concrete roles
+    hedl::DevNum *num_dev = nullptr;
     uint32_t *status_dev = nullptr;         // [4]: status, |P|, |N|, scratch
     const uint32_t *pos = nullptr, *neg = nullptr;
     uint32_t n_pos = 0, n_neg = 0;

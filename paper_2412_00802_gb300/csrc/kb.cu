@@ -1,4 +1,5 @@
-// Device-side checks run once when a knowledge base is registered, and the
+// Device-side checks run once when a knowledge base is registered (concept
+// tails, role CSRs and their transposes, numeric-role row pointers), and the
 // example-set popcounts.  Each check ORs a bit into a flag word; nothing traps.
 #include <cuda_runtime.h>
 
@@ -20,6 +21,7 @@ enum : uint32_t {
     F_NOT_TRANSPOSE = 1u << 5,
     F_EDGE_COUNT = 1u << 6,
     F_EXAMPLE_TAIL = 1u << 7,
+    F_NUM_RP = 1u << 8,
 };
 
 // Bits of individuals >= n and the padding words must be zero.
@@ -54,6 +56,16 @@ __global__ void csr_kernel(DevCSR g, uint32_t n, uint32_t *flag) {
             prev = c;
         }
     }
+}
+
+// A numeric role's row_ptr: starts at 0, ends at n_vals, never decreases
+// (the values themselves may be anything).
+__global__ void num_rp_kernel(DevNum g, uint32_t n, uint32_t *flag) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (g.rp[0] != 0 || g.rp[n] != g.n_vals) atomicOr(flag, F_NUM_RP);
+    }
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (g.rp[i + 1] < g.rp[i]) atomicOr(flag, F_NUM_RP);
 }
 
 // Every forward edge (a, b) appears as a in the inverse row of b.  With equal
@@ -121,6 +133,7 @@ std::string describe(uint32_t f) {
     add(F_NOT_TRANSPOSE, "an inverse CSR is not the transpose of its forward CSR");
     add(F_EDGE_COUNT, "an inverse CSR has a different edge count than its forward CSR");
     add(F_EXAMPLE_TAIL, "an example bitset has bits set beyond n or in its padding words");
+    add(F_NUM_RP, "a numeric role's row_ptr does not start at 0, decreases, or does not end at n_vals");
     return s;
 }
 
@@ -146,6 +159,8 @@ int kb_validate_device(const hedl_kb *kb, void *stream, std::string *why) {
         csr_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(t, kb->n, flag);
         transpose_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(f, t, kb->n, flag);
     }
+    for (uint32_t q = 0; q < kb->n_num; ++q)
+        num_rp_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(kb->num_host[q], kb->n, flag);
     e = cudaGetLastError();
     if (e) return e;
     uint32_t dev_flag = 0;

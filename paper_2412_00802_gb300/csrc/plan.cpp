@@ -60,6 +60,13 @@ struct KeyHash {
 
 inline bool is_role(uint32_t op) { return op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY; }
 inline bool is_data(uint32_t op) { return op >= HEDL_OP_DGE && op <= HEDL_OP_DEQ; }
+// Algorithmic bytes of a data restriction on property id a: a one-value
+// column (4N), or a numeric role's row pointers and values (4(N+1) + 4M).
+inline uint64_t data_bytes(const hedl_kb *kb, uint32_t a, uint64_t N) {
+    if (a < kb->n_props) return 4 * N;
+    return 4 * (N + 1) + 4ull * kb->num_host[a - kb->n_props].n_vals;
+}
+
 inline int arity(uint32_t op) {
     if (op == HEDL_OP_ATOM || op == HEDL_OP_TOP || op == HEDL_OP_BOT || is_data(op)) return 0;
     if (op == HEDL_OP_NOT || is_role(op)) return 1;
@@ -93,7 +100,7 @@ int validate_program(const hedl_kb *kb, const uint64_t *prog, uint32_t len, std:
             return HEDL_ERR_BAD_PROGRAM;
         }
         if ((op == HEDL_OP_ATOM && a >= kb->n_concepts) || (is_role(op) && a >= kb->n_roles) ||
-            (is_data(op) && a >= kb->n_props)) {
+            (is_data(op) && a >= kb->n_props + kb->n_num)) {
             snprintf(buf, sizeof buf, "instruction %u: %s names id %u, out of range", k, op_name(op), a);
             *why = buf;
             return HEDL_ERR_BAD_PROGRAM;
@@ -176,7 +183,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 d = d - arity(op) + 1;
                 maxd = std::max<uint32_t>(maxd, (uint32_t)d);
                 if (op == HEDL_OP_ATOM) mb += B, p->info.n_atom_loads++;
-                else if (is_data(op)) mb += 4 * N, p->info.n_data_ops++;
+                else if (is_data(op)) mb += data_bytes(kb, a, N), p->info.n_data_ops++;
                 else if (is_role(op)) mb += 4 * (N + 1) + 4ull * kb->role_edges[a] + 2 * B, p->info.n_role_ops++;
             }
             mb += 2 * B + 16;  // scoring
@@ -398,10 +405,11 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 } else if (n.op == HEDL_OP_TOP || n.op == HEDL_OP_BOT) {
                     d.op = n.op;
                 } else if (is_data(n.op)) {
-                    d.op = D_DATA | (n.op << 16);
-                    d.a = n.a;
+                    const bool num = n.a >= kb->n_props;   // a numeric concrete role
+                    d.op = D_DATA | (n.op << 16) | (num ? 1u << 8 : 0u);
+                    d.a = num ? n.a - kb->n_props : n.a;
                     d.b = n.b;
-                    model += 4 * N;
+                    model += data_bytes(kb, n.a, N);
                     p->info.n_data_ops++;
                 } else {  // role restriction
                     int32_t c = n.k0;

@@ -206,3 +206,32 @@ def test_interpreter_digest_ignores_comments_not_code():
         'int a = 1; int b = "x//y" [0];'
     assert build._code_only("x  =\n\n y;") == "x = y;"
     assert build._code_only("a = 1;") != build._code_only("a = 2;")
+
+
+def test_numeric_roles_on_a_planning_handle():
+    """Numeric concrete roles take the property ids after the one-value properties; a restriction
+    on one costs its row pointers and values in the byte model (4(N+1) + 4M, Algorithms 9-10)."""
+    n, M = 10_000, [30_000, 5]
+    hk = H.hedl_kb_plan_only(n, 3, [100], 2, num_role_vals=M)
+    insn = lambda p: np.array([P.insn(P.DGE, 0, p, P.f32_bits(1.5))], np.uint64)
+    for p in (0, 1, 2, 3):
+        H.hedl_validate(hk, insn(p))
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_validate(hk, insn(4))
+    assert e.value.code == -2   # HEDL_ERR_BAD_PROGRAM
+    B = 4 * H.hedl_row_words(n)
+    for flags in (0, H.HEDL_PLAIN):
+        for p, want in ((1, 4 * n), (2, 4 * (n + 1) + 4 * M[0]), (3, 4 * (n + 1) + 4 * M[1])):
+            info = H.hedl_plan_info_get(H.hedl_plan_batch(hk, insn(p), np.array([0, 1], np.uint32), flags))
+            assert info["n_data_ops"] == 1
+            assert info["model_bytes"] == want + 2 * B + 16, (flags, p)
+
+
+def test_numeric_role_limits():
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_kb_plan_only(100, 1, [], 65_000, num_role_vals=[1] * 537)
+    assert e.value.code == -1   # HEDL_ERR_INVALID_ARG
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_kb_plan_only(100, 1, [], 0, num_role_vals=[1 << 31])
+    assert e.value.code == -1   # HEDL_ERR_INVALID_ARG
+    H.hedl_kb_plan_only(100, 1, [], 65_000, num_role_vals=[1] * 536)
