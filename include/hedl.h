@@ -341,7 +341,9 @@ int hedl_autotune_workspace_size(hedl_kb *kb, const uint64_t *progs, const uint3
  * the paper.  Each candidate shape plans the probe batch (HOST progs / offs as
  * in hedl_plan_batch, scored against the handle's examples), runs it once,
  * then times three replays with CUDA events on s; the fastest becomes the
- * handle's tuning and is written to *chosen (may be NULL).  With cache_path
+ * handle's tuning and is written to *chosen (may be NULL), except that the
+ * handle's current shape is kept when it is within 2 % of the fastest (so
+ * timing noise between near-equal shapes does not flip the choice).  With cache_path
  * (may be NULL), a result stored earlier for the same KB shape and GPU is
  * reused without timing, and a new result is appended to that text file.
  * ws (>= hedl_autotune_workspace_size, 256-byte aligned) is scratch for the

@@ -14,6 +14,11 @@
 namespace hedl {
 namespace {
 
+bool same_shape(const Tuning &a, const Tuning &b) {
+    return a.warps == b.warps && a.wpl == b.wpl && a.rounds == b.rounds && a.stage == b.stage &&
+           a.role_block == b.role_block && a.full_occupancy == b.full_occupancy;
+}
+
 std::vector<Tuning> candidates(const Tuning &base) {
     std::vector<Tuning> out;
     for (uint32_t stage : {1u, 0u})
@@ -154,7 +159,8 @@ extern "C" int hedl_autotune(hedl_kb *kb, const uint64_t *progs, const uint32_t 
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
-        float best_ms = 1e30f;
+        float best_ms = 1e30f, saved_ms = -1.f;
+        Tuning saved_shape = saved;
         for (const Tuning &t : candidates(saved)) {
             if (!fits(kb, t)) continue;
             kb->tuning = t;
@@ -179,7 +185,14 @@ extern "C" int hedl_autotune(hedl_kb *kb, const uint64_t *progs, const uint32_t 
                 best_ms = ms;
                 best = t;
             }
+            if (same_shape(t, saved)) {
+                saved_ms = ms;
+                saved_shape = t;
+            }
         }
+        // the current shape stays unless another is at least 2 % faster: timing noise
+        // between near-equal shapes must not flip the choice from run to run
+        if (!e && saved_ms >= 0.f && saved_ms <= best_ms * 1.02f) best = saved_shape;
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         kb->tuning = saved;
