@@ -386,43 +386,88 @@ __device__ __forceinline__ bool data_cmp(uint32_t cmp, float x, float t) {
 // Existential restriction on a numeric concrete role (Algorithms 9-10 with
 // several values per subject, Section III-B): individual i belongs iff one of
 // vals[rp[i] .. rp[i+1]) passes the compare.  The 32 individuals of a word own
-// one contiguous run of values; the warp reads it 64 values a step (two
-// coalesced loads), ballots the compares, and each lane tests the bits that
-// fall in its own sub-range.  The warp leaves the run once every individual
-// whose values reach past the step has found one (the paper's skip over a
-// subject already satisfied), so a heavy subject costs 1/32 of a lane walk.
+// one contiguous run of values; the warp reads it NUM_STEP values a step
+// (four coalesced loads), ballots the compares, and each lane tests the bits
+// that fall in its own sub-range.  The words are software-pipelined: while
+// word w is tested, the row pointers of word w+2 and the first step of word
+// w+1 are in flight, so a word whose run fits one step costs one memory
+// latency, overlapped.  A longer run continues step by step and the warp
+// leaves it once every individual whose values reach past the step has found
+// one (the paper's skip over a subject already satisfied), so a heavy subject
+// costs 1/32 of a lane walk.
+constexpr uint32_t NUM_LOADS = 4;
+constexpr uint32_t NUM_STEP = 32u * NUM_LOADS;
+
+// this lane's row of word w (empty past the warp's words or past n)
+__device__ __forceinline__ void num_row(const DevNum &g, uint32_t w, uint32_t n_words, uint32_t n, uint32_t lane,
+                                        uint32_t &lo, uint32_t &hi) {
+    lo = hi = 0;
+    const uint32_t i = w * 32u + lane;
+    if (w < n_words && i < n) {
+        lo = ld_stream(g.rp + i);
+        hi = ld_stream(g.rp + i + 1);
+    }
+}
+
+// the values [c, c + NUM_STEP) of a run ending at end, one per lane and load
+__device__ __forceinline__ void num_fetch(const DevNum &g, uint32_t c, uint32_t end, uint32_t lane,
+                                          float (&x)[NUM_LOADS]) {
+#pragma unroll
+    for (uint32_t u = 0; u < NUM_LOADS; ++u) {
+        const uint32_t k = c + 32u * u + lane;
+        x[u] = k < end ? __ldg(g.vals + k) : 0.f;
+    }
+}
+
+// does a value in [c, c + NUM_STEP) of this lane's row [lo, hi) pass?
+__device__ __forceinline__ bool num_test(const float (&x)[NUM_LOADS], uint32_t c, uint32_t end, uint32_t lo,
+                                         uint32_t hi, uint32_t lane, uint32_t cmp, float t) {
+    bool hit = false;
+#pragma unroll
+    for (uint32_t u = 0; u < NUM_LOADS; ++u) {
+        const uint32_t cu = c + 32u * u;
+        const uint32_t m = __ballot_sync(FULL, cu + lane < end && data_cmp(cmp, x[u], t));
+        const uint32_t a = lo > cu ? min(lo - cu, 32u) : 0u, b = hi > cu ? min(hi - cu, 32u) : 0u;
+        hit = hit || (m & range_mask(a, b)) != 0u;
+    }
+    return hit;
+}
+
 template <int WPL>
 __device__ __forceinline__ void num_words(const DevNum g, uint32_t cmp, float t, uint32_t n, uint32_t n_words,
                                           uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
+    // word w: row [lo, hi), run [base, end), first step x; word w+1: row [lo1, hi1)
+    uint32_t lo, hi, lo1, hi1;
+    num_row(g, wb, n_words, n, lane, lo, hi);
+    uint32_t base = __shfl_sync(FULL, lo, 0), end = __reduce_max_sync(FULL, hi);
+    float x[NUM_LOADS];
+    num_fetch(g, base, end, lane, x);
+    num_row(g, wb + 1, n_words, n, lane, lo1, hi1);
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
         for (int s = 0; s < WPL; ++s) {
-            const uint32_t w = wb + (uint32_t)j * WPL + s;
+            const uint32_t w = wb + (uint32_t)j * WPL + s;   // the words go in order: w + 1 is the next
             uint32_t word = 0;
-            if (w < n_words) {   // warp-uniform; then lane 0's individual 32w < n exists
-                const uint32_t i = w * 32u + lane;
-                uint32_t lo = 0, hi = 0;   // individuals >= n own no values
-                if (i < n) {
-                    lo = ld_stream(g.rp + i);
-                    hi = ld_stream(g.rp + i + 1);
-                }
-                const uint32_t base = __shfl_sync(FULL, lo, 0);
-                const uint32_t end = __reduce_max_sync(FULL, hi);
-                bool hit = false;
-                for (uint32_t c = base; c < end; c += 64u) {
-                    const uint32_t k0 = c + lane, k1 = c + 32u + lane;
-                    float x0 = 0.f, x1 = 0.f;
-                    if (k0 < end) x0 = __ldg(g.vals + k0);
-                    if (k1 < end) x1 = __ldg(g.vals + k1);
-                    const uint32_t m0 = __ballot_sync(FULL, k0 < end && data_cmp(cmp, x0, t));
-                    const uint32_t m1 = __ballot_sync(FULL, k1 < end && data_cmp(cmp, x1, t));
-                    const uint32_t a0 = lo > c ? min(lo - c, 32u) : 0u, b0 = hi > c ? min(hi - c, 32u) : 0u;
-                    const uint32_t c1 = c + 32u;
-                    const uint32_t a1 = lo > c1 ? min(lo - c1, 32u) : 0u, b1 = hi > c1 ? min(hi - c1, 32u) : 0u;
-                    hit = hit || (m0 & range_mask(a0, b0)) != 0u || (m1 & range_mask(a1, b1)) != 0u;
-                    if (__all_sync(FULL, hit || hi <= c + 64u)) break;
+            if (w < n_words) {   // warp-uniform
+                // start word w+1's first step and word w+2's row pointers
+                const uint32_t base1 = __shfl_sync(FULL, lo1, 0), end1 = __reduce_max_sync(FULL, hi1);
+                float x1[NUM_LOADS];
+                num_fetch(g, base1, end1, lane, x1);
+                uint32_t lo2, hi2;
+                num_row(g, w + 2, n_words, n, lane, lo2, hi2);
+                // test word w
+                bool hit = num_test(x, base, end, lo, hi, lane, cmp, t);
+                for (uint32_t c = base + NUM_STEP; c < end; c += NUM_STEP) {
+                    if (__all_sync(FULL, hit || hi <= c)) break;
+                    float y[NUM_LOADS];
+                    num_fetch(g, c, end, lane, y);
+                    hit = num_test(y, c, end, lo, hi, lane, cmp, t) || hit;
                 }
                 word = __ballot_sync(FULL, hit);
+                lo = lo1, hi = hi1, base = base1, end = end1;
+                lo1 = lo2, hi1 = hi2;
+#pragma unroll
+                for (uint32_t u = 0; u < NUM_LOADS; ++u) x[u] = x1[u];
             }
             if (lane == (uint32_t)j) v[s] = word;
         }
