@@ -96,7 +96,8 @@ typedef enum {
     HEDL_OP_AND = 5, HEDL_OP_OR = 6,
     HEDL_OP_EXISTS = 7, HEDL_OP_FORALL = 8, HEDL_OP_ATLEAST = 9, HEDL_OP_ATMOST = 10,
     HEDL_OP_EXACTLY = 11,
-    HEDL_OP_DGE = 12, HEDL_OP_DLE = 13, HEDL_OP_DEQ = 14
+    HEDL_OP_DGE = 12, HEDL_OP_DLE = 13, HEDL_OP_DEQ = 14,
+    HEDL_OP_SEQ = 15, HEDL_OP_SCONTAINS = 16
 } hedl_op;
 
 #define HEDL_FLAG_INVERSE 1u

@@ -6,8 +6,9 @@ no code with the GPU library (``paper_2412_00802_gb300``) and never imports
 it.
 
 ``hedl_oracle.c`` is the evaluator (byte-per-membership sets, role
-assertions as (subject, object) pairs and numeric concrete-role assertions as
-(subject, value) pairs, the paper's Section III layout);
+assertions as (subject, object) pairs, numeric concrete-role assertions as
+(subject, value) pairs and string concrete-role assertions as (subject, bytes)
+pairs, the paper's Section III layout);
 ``fo_brute`` is a second, first-order-semantics evaluator in pure Python for
 tiny inputs, used to pin the C one.  This wrapper only marshals arrays.
 """
@@ -55,7 +56,27 @@ class _KB(ctypes.Structure):
                 ("n_num_roles", ctypes.c_int32),
                 ("num_off", ctypes.c_void_p),
                 ("num_subj", ctypes.c_void_p),
-                ("num_val", ctypes.c_void_p)]
+                ("num_val", ctypes.c_void_p),
+                ("n_str_roles", ctypes.c_int32),
+                ("str_off", ctypes.c_void_p),
+                ("str_subj", ctypes.c_void_p),
+                ("str_val_off", ctypes.c_void_p),
+                ("str_val", ctypes.c_void_p),
+                ("n_strings", ctypes.c_int64),
+                ("tbl_off", ctypes.c_void_p),
+                ("tbl", ctypes.c_void_p),
+                ("n_patterns", ctypes.c_int64),
+                ("pat_off", ctypes.c_void_p),
+                ("pat", ctypes.c_void_p)]
+
+
+def _byte_table(items) -> Tuple[np.ndarray, np.ndarray]:
+    """A list of byte strings as (int64 offsets [len+1], uint8 bytes)."""
+    items = [bytes(x) for x in items]
+    off = np.zeros(len(items) + 1, np.int64)
+    if items:
+        np.cumsum([len(x) for x in items], out=off[1:])
+    return off, np.frombuffer(b"".join(items), np.uint8).copy()
 
 
 def load(path: str):
@@ -101,21 +122,42 @@ class OracleKB:
     num_off: np.ndarray = None    # int64 [Q+1]
     num_subj: np.ndarray = None   # uint32 [M]
     num_val: np.ndarray = None    # float32 [M]
+    # string concrete roles: (subject, value bytes) assertions per role, the string table and the patterns
+    str_off: np.ndarray = None      # int64 [S_roles+1]
+    str_subj: np.ndarray = None     # uint32 [A]
+    str_val_off: np.ndarray = None  # int64 [A+1]
+    str_val: np.ndarray = None      # uint8
+    tbl_off: np.ndarray = None      # int64 [n_strings+1]
+    tbl: np.ndarray = None          # uint8
+    pat_off: np.ndarray = None      # int64 [n_patterns+1]
+    pat: np.ndarray = None          # uint8
 
     def __post_init__(self):
         if self.num_off is None:
             self.num_off = np.zeros(1, np.int64)
             self.num_subj = np.zeros(0, np.uint32)
             self.num_val = np.zeros(0, np.float32)
-        for name in ("member", "role_off", "subj", "obj", "prop", "pos", "neg", "num_off", "num_subj", "num_val"):
+        if self.str_off is None:
+            self.str_off = np.zeros(1, np.int64)
+            self.str_subj = np.zeros(0, np.uint32)
+            self.str_val_off, self.str_val = _byte_table([])
+            self.tbl_off, self.tbl = _byte_table([])
+            self.pat_off, self.pat = _byte_table([])
+        names = ("member", "role_off", "subj", "obj", "prop", "pos", "neg", "num_off", "num_subj", "num_val",
+                 "str_off", "str_subj", "str_val_off", "str_val", "tbl_off", "tbl", "pat_off", "pat")
+        for name in names:
             setattr(self, name, np.ascontiguousarray(getattr(self, name)))
+        opt = lambda a: _ptr(a) if a.size else None
         self._c = _KB(self.n, self.member.shape[0], _ptr(self.member) if self.member.size else None,
                       self.role_off.size - 1, _ptr(self.role_off), _ptr(self.subj) if self.subj.size else None,
                       _ptr(self.obj) if self.obj.size else None, self.prop.shape[0],
                       _ptr(self.prop) if self.prop.size else None,
                       self.num_off.size - 1, _ptr(self.num_off),
                       _ptr(self.num_subj) if self.num_subj.size else None,
-                      _ptr(self.num_val) if self.num_val.size else None)
+                      _ptr(self.num_val) if self.num_val.size else None,
+                      self.str_off.size - 1, _ptr(self.str_off), opt(self.str_subj), _ptr(self.str_val_off),
+                      opt(self.str_val), self.tbl_off.size - 1, _ptr(self.tbl_off), opt(self.tbl),
+                      self.pat_off.size - 1, _ptr(self.pat_off), opt(self.pat))
 
     @property
     def cptr(self):
@@ -124,9 +166,16 @@ class OracleKB:
     @classmethod
     def from_parts(cls, n: int, member: np.ndarray, edges: Sequence[Tuple[np.ndarray, np.ndarray]],
                    prop: np.ndarray, pos: np.ndarray, neg: np.ndarray,
-                   num_roles: Sequence[Tuple[np.ndarray, np.ndarray]] = ()) -> "OracleKB":
+                   num_roles: Sequence[Tuple[np.ndarray, np.ndarray]] = (),
+                   str_roles: Sequence[Tuple[np.ndarray, Sequence[bytes]]] = (),
+                   strings: Sequence[bytes] = (), patterns: Sequence[bytes] = (),
+                   str_arrays: Optional[Tuple[np.ndarray, ...]] = None) -> "OracleKB":
         """edges: per role (subjects, objects); each pair must appear at most once.
-        num_roles: per numeric concrete role (subjects, float values), any order."""
+        num_roles: per numeric concrete role (subjects, float values), any order.
+        str_roles: per string concrete role (subjects, value byte strings), any order;
+        strings: the table SEQ indexes; patterns: the substrings SCONTAINS indexes.
+        str_arrays: the string assertions already laid out (role offsets, subjects,
+        value offsets, value bytes), instead of str_roles."""
         offs = [0]
         subj, obj = [], []
         for s, o in edges:
@@ -155,11 +204,28 @@ class OracleKB:
             nsubj.append(s_)
             nval.append(v_)
             noff.append(noff[-1] + s_.size)
+        soff, ssubj, svals = [0], [], []
+        for s_, v_ in str_roles:
+            s_ = np.asarray(s_, dtype=np.uint32)
+            if s_.size != len(v_):
+                raise ValueError("a string assertion needs one subject and one value")
+            if s_.size and int(s_.max()) >= n:
+                raise ValueError("string assertion names an individual >= n")
+            ssubj.append(s_)
+            svals += list(v_)
+            soff.append(soff[-1] + s_.size)
+        sv_off, sv = _byte_table(svals)
+        if str_arrays is not None:
+            soff, ssubj, sv_off, sv = str_arrays
+            soff, ssubj = list(soff), [np.asarray(ssubj, np.uint32)]
+        t_off, t = _byte_table(strings)
+        p_off, pt = _byte_table(patterns)
         return cls(n, np.asarray(member, np.uint8).reshape(-1, n) if n else np.zeros((len(member), 0), np.uint8),
                    np.array(offs, dtype=np.int64), cat(subj, np.uint32), cat(obj, np.uint32),
                    np.asarray(prop, np.float32).reshape(-1, n) if n else np.zeros((len(prop), 0), np.float32),
                    np.asarray(pos, np.uint8), np.asarray(neg, np.uint8),
-                   np.array(noff, dtype=np.int64), cat(nsubj, np.uint32), cat(nval, np.float32))
+                   np.array(noff, dtype=np.int64), cat(nsubj, np.uint32), cat(nval, np.float32),
+                   np.array(soff, dtype=np.int64), cat(ssubj, np.uint32), sv_off, sv, t_off, t, p_off, pt)
 
 
 def from_synth(kb) -> OracleKB:
@@ -185,7 +251,26 @@ def from_synth(kb) -> OracleKB:
     for q in range(kb.n_num_roles):
         deg = np.diff(kb.num_row_ptr[q].astype(np.int64))
         nums.append((np.repeat(np.arange(n, dtype=np.uint32), deg), kb.num_vals[q]))
-    return OracleKB.from_parts(n, member, edges, kb.prop_vals, pos, neg, nums)
+    # string roles: each assertion gets its own copy of its value's bytes (the
+    # oracle compares bytes; the interned ids are not passed)
+    arrays = None
+    if kb.n_str_roles:
+        t_off, t = _byte_table(kb.strings)
+        t_len = np.diff(t_off)
+        soff, subj, ids = [0], [], []
+        for q in range(kb.n_str_roles):
+            deg = np.diff(kb.str_row_ptr[q].astype(np.int64))
+            subj.append(np.repeat(np.arange(n, dtype=np.uint32), deg))
+            ids.append(kb.str_ids[q].astype(np.int64))
+            soff.append(soff[-1] + int(deg.sum()))
+        ids = np.concatenate(ids)
+        lens = t_len[ids]
+        v_off = np.zeros(ids.size + 1, np.int64)
+        np.cumsum(lens, out=v_off[1:])
+        src = np.repeat(t_off[ids] - v_off[:-1], lens) + np.arange(int(v_off[-1]), dtype=np.int64)
+        arrays = (np.array(soff, np.int64), np.concatenate(subj), v_off, t[src])
+    return OracleKB.from_parts(n, member, edges, kb.prop_vals, pos, neg, nums, (), kb.strings, kb.patterns,
+                               arrays)
 
 
 def validate(okb: OracleKB, prog, L=None) -> int:

@@ -13,6 +13,8 @@ to pin it:
     (exactly n r C)= { x | #{ y | r(x, y) and C(y) } == n }
     r^-(x, y)      = r(y, x)
     (ge p t)       = { x | some v: p(x, v) and v >= t }   (float32 compare)
+    (seq s v)      = { x | some u: s(x, u) and u = strings[v] }
+    (contains s k) = { x | some u: s(x, u) and patterns[k] occurs in u }
 
 under the closed-world reading (Section III-A of the paper): a fact not in
 the KB is false, so NOT is the complement within the domain.  A property maps
@@ -28,18 +30,25 @@ import numpy as np
 _ATOM, _TOP, _BOT, _NOT, _AND, _OR = 1, 2, 3, 4, 5, 6
 _EX, _ALL, _MIN, _MAX, _EXACT = 7, 8, 9, 10, 11
 _GE, _LE, _EQ = 12, 13, 14
+_SEQ, _SCONTAINS = 15, 16
 
 
 class TinyKB:
     def __init__(self, n: int, concepts: Sequence[Set[int]], roles: Sequence[Set[Tuple[int, int]]],
-                 props: Sequence[Dict[int, object]]):
-        """props[p][x]: a float or a sequence of floats (x's values of p)."""
+                 props: Sequence[Dict[int, object]], str_roles: Sequence[Dict[int, Sequence[bytes]]] = (),
+                 strings: Sequence[bytes] = (), patterns: Sequence[bytes] = ()):
+        """props[p][x]: a float or a sequence of floats (x's values of p);
+        str_roles[s][x]: x's string values of string role s; strings: the table SEQ
+        names by index; patterns: the substrings SCONTAINS names by index."""
         self.n = n
         self.domain = range(n)
         self.concepts = [set(c) for c in concepts]
         self.roles = [set(r) for r in roles]
         self.props = [{int(k): tuple(np.float32(u) for u in (v if isinstance(v, (list, tuple)) else [v]))
                        for k, v in p.items()} for p in props]
+        self.str_roles = [{int(k): [bytes(u) for u in v] for k, v in r.items()} for r in str_roles]
+        self.strings = [bytes(x) for x in strings]
+        self.patterns = [bytes(x) for x in patterns]
 
     def rel(self, r: int, inverse: bool, x: int, y: int) -> bool:
         return ((y, x) if inverse else (x, y)) in self.roles[r]
@@ -88,6 +97,13 @@ def evaluate(kb: TinyKB, prog: Sequence[int]) -> Set[int]:
                        for v in vals.get(x, ())):
                     out.add(x)
             stack.append(out)
+        elif op == _SEQ:         # { x | some v: s(x, v) and v = strings[b] }
+            vals = kb.str_roles[a]
+            want = kb.strings[b] if b < len(kb.strings) else None
+            stack.append({x for x in D if want is not None and any(v == want for v in vals.get(x, ()))})
+        elif op == _SCONTAINS:   # { x | some v: s(x, v) and patterns[b] is a substring of v }
+            vals = kb.str_roles[a]
+            stack.append({x for x in D if any(kb.patterns[b] in v for v in vals.get(x, ()))})
         else:
             raise ValueError(f"bad op {op}")
     if len(stack) != 1:

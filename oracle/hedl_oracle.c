@@ -14,7 +14,10 @@
  * concrete role (Section III-B: a subject may assert several values) as a
  * 2-column (subject, value) matrix grouped per role through its own offset
  * table.  Property ids below n_props name the one-value properties, ids
- * n_props + q the numeric concrete role q.
+ * n_props + q the numeric concrete role q.  A string concrete role is a
+ * 2-column (subject, string value) matrix grouped per role, each assertion
+ * holding its own bytes; a string table (the strings SEQ names by index) and
+ * a pattern list (the substrings SCONTAINS names by index) complete it.
  *
  * Semantics (closed world, Section III-A: anything not asserted is false):
  *   ATOM c         members of c
@@ -34,6 +37,12 @@
  *                  (float32 compares; a missing value satisfies nothing; on a
  *                  numeric concrete role "a value" ranges over every
  *                  assertion of the subject: an existential restriction)
+ *   SEQ s v        { a : a has a value of string role s equal, byte for
+ *                  byte, to table string v }; empty when v is not in the
+ *                  table                                       (Algorithms 11-12)
+ *   SCONTAINS s k  { a : a has a value of string role s that contains
+ *                  pattern k as a substring; the empty pattern is contained
+ *                  in every string }                           (Algorithms 13-14)
  * Coverage (Algorithm 15): TP = |R & P|, FP = |R & N|; FN = |P| - TP and
  * TN = |N| - FP complete the confusion matrix.
  *
@@ -68,6 +77,8 @@
 #define O_DGE 12
 #define O_DLE 13
 #define O_DEQ 14
+#define O_SEQ 15
+#define O_SCONTAINS 16
 
 #define ORACLE_MAX_STACK 64
 
@@ -95,6 +106,17 @@ typedef struct {
     const int64_t *num_off;          /* [n_num_roles + 1] */
     const uint32_t *num_subj;        /* [total numeric assertions] */
     const float *num_val;
+    int32_t n_str_roles;             /* string concrete roles (ids of SEQ / SCONTAINS) */
+    const int64_t *str_off;          /* [n_str_roles + 1]: the assertions of each role */
+    const uint32_t *str_subj;        /* [total string assertions] */
+    const int64_t *str_val_off;      /* [total string assertions + 1]: each value's bytes */
+    const uint8_t *str_val;
+    int64_t n_strings;               /* the table SEQ's second field indexes */
+    const int64_t *tbl_off;          /* [n_strings + 1] */
+    const uint8_t *tbl;
+    int64_t n_patterns;              /* the patterns SCONTAINS's second field indexes */
+    const int64_t *pat_off;          /* [n_patterns + 1] */
+    const uint8_t *pat;
 } oracle_kb;
 
 static unsigned op_of(uint64_t w) { return (unsigned)(w & 0xFF); }
@@ -111,7 +133,8 @@ static float as_float(uint32_t bits) {
 /* Stack effect of each op: how many operands it pops (leaves pop 0). */
 static int arity(unsigned op) {
     switch (op) {
-    case O_ATOM: case O_TOP: case O_BOT: case O_DGE: case O_DLE: case O_DEQ: return 0;
+    case O_ATOM: case O_TOP: case O_BOT: case O_DGE: case O_DLE: case O_DEQ: case O_SEQ: case O_SCONTAINS:
+        return 0;
     case O_NOT: case O_EXISTS: case O_FORALL: case O_ATLEAST: case O_ATMOST: case O_EXACTLY: return 1;
     case O_AND: case O_OR: return 2;
     default: return -1;
@@ -131,6 +154,8 @@ int oracle_validate(const oracle_kb *kb, const uint64_t *prog, int64_t len) {
         if ((op == O_DGE || op == O_DLE || op == O_DEQ) &&
             (int64_t)a_of(prog[k]) >= (int64_t)kb->n_props + kb->n_num_roles)
             return OE_BAD_ID;
+        if ((op == O_SEQ || op == O_SCONTAINS) && (int32_t)a_of(prog[k]) >= kb->n_str_roles) return OE_BAD_ID;
+        if (op == O_SCONTAINS && (int64_t)b_of(prog[k]) >= kb->n_patterns) return OE_BAD_ID;
         if (depth < ar) return OE_UNDERFLOW;
         depth = depth - ar + 1;
         if (depth > ORACLE_MAX_STACK) return OE_OVERFLOW;
@@ -201,6 +226,43 @@ static void op_data(const oracle_kb *kb, unsigned op, unsigned p, float t, uint8
     }
 }
 
+static int bytes_equal(const uint8_t *x, int64_t lx, const uint8_t *y, int64_t ly) {
+    if (lx != ly) return 0;
+    for (int64_t i = 0; i < lx; ++i)
+        if (x[i] != y[i]) return 0;
+    return 1;
+}
+
+/* strContain of Algorithms 13-14: does x hold p at some position? */
+static int bytes_contain(const uint8_t *x, int64_t lx, const uint8_t *p, int64_t lp) {
+    for (int64_t i = 0; i + lp <= lx; ++i) {
+        int64_t j = 0;
+        while (j < lp && x[i + j] == p[j]) ++j;
+        if (j == lp) return 1;
+    }
+    return 0;
+}
+
+/* Existential restriction on a string concrete role (Algorithms 11-14). */
+static void op_string(const oracle_kb *kb, unsigned op, unsigned s, uint32_t b, uint8_t *out) {
+    memset(out, 0, (size_t)kb->n);
+    const uint8_t *y;
+    int64_t ly;
+    if (op == O_SEQ) {
+        if ((int64_t)b >= kb->n_strings) return;   /* not in the table: nothing equals it */
+        y = kb->tbl + kb->tbl_off[b];
+        ly = kb->tbl_off[b + 1] - kb->tbl_off[b];
+    } else {
+        y = kb->pat + kb->pat_off[b];
+        ly = kb->pat_off[b + 1] - kb->pat_off[b];
+    }
+    for (int64_t k = kb->str_off[s]; k < kb->str_off[s + 1]; ++k) {
+        const uint8_t *x = kb->str_val + kb->str_val_off[k];
+        const int64_t lx = kb->str_val_off[k + 1] - kb->str_val_off[k];
+        if (op == O_SEQ ? bytes_equal(x, lx, y, ly) : bytes_contain(x, lx, y, ly)) out[kb->str_subj[k]] = 1;
+    }
+}
+
 /* Evaluate one postfix program; out receives n bytes (0/1). */
 int oracle_eval(const oracle_kb *kb, const uint64_t *prog, int64_t len, uint8_t *out) {
     int err = oracle_validate(kb, prog, len);
@@ -224,6 +286,7 @@ int oracle_eval(const oracle_kb *kb, const uint64_t *prog, int64_t len, uint8_t 
             if (op == O_ATOM) memcpy(r, kb->concept_member + (int64_t)a * n, (size_t)n);
             else if (op == O_TOP) memset(r, 1, (size_t)n);
             else if (op == O_BOT) memset(r, 0, (size_t)n);
+            else if (op == O_SEQ || op == O_SCONTAINS) op_string(kb, op, a, b_of(prog[k]), r);
             else op_data(kb, op, a, as_float(b_of(prog[k])), r);
             sp += 1;
         } else if (op == O_NOT) {

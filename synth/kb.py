@@ -12,6 +12,9 @@ A KB here is plain host data:
 * numeric concrete roles (several values per individual, Section III-B) as a
   CSR over individuals (``num_row_ptr`` uint32[n+1], ``num_vals`` float32[M]);
   their property ids follow the one-value properties' (``n_props + q``);
+* string concrete roles as a CSR of interned string ids over individuals
+  (``str_row_ptr``, ``str_ids`` uint32[M]) into a table of distinct strings
+  (``strings``), with a list of substring patterns (``patterns``);
 * positive and negative example sets (bitsets and index lists).
 
 Degree laws, value distributions and example counts follow the workload
@@ -83,6 +86,10 @@ S_ROLE_TGT = 3 << 16
 S_PROP = 4 << 16
 S_NUM_DEG = 12 << 16
 S_NUM_VAL = 13 << 16
+S_STR_DEG = 14 << 16
+S_STR_ID = 15 << 16
+S_STR_TABLE = 16 << 16
+S_PATTERN = 17 << 16
 
 
 @dataclass(frozen=True)
@@ -104,6 +111,12 @@ class KBConfig:
     planted: bool = False    # examples from a latent class that some concepts, role 0 and property 0 track
     n_num_roles: int = 0     # numeric concrete roles (values from prop_dist)
     num_degree: Tuple = ("poisson", 3.0)   # values per individual: ("poisson", lam) | ("single", m) | ("unique",)
+    n_str_roles: int = 0     # string concrete roles
+    str_degree: Tuple = ("poisson", 2.0)   # values per individual, as num_degree
+    n_strings: int = 0       # distinct strings in the table (lengths str_len, letters of an alphabet)
+    str_len: Tuple = (3, 12)
+    alphabet: int = 6
+    n_patterns: int = 0      # substring patterns (the first is the empty string)
 
     def scaled(self, n: int, **kw) -> "KBConfig":
         """Same distributions on ``n`` individuals (example counts scaled)."""
@@ -320,6 +333,10 @@ class KB:
     meta: dict
     num_row_ptr: List[np.ndarray] = field(default_factory=list)   # per numeric role uint32 [n+1]
     num_vals: List[np.ndarray] = field(default_factory=list)      # per numeric role float32 [M]
+    str_row_ptr: List[np.ndarray] = field(default_factory=list)   # per string role uint32 [n+1]
+    str_ids: List[np.ndarray] = field(default_factory=list)       # per string role uint32 [M], ids into strings
+    strings: List[bytes] = field(default_factory=list)            # the table (distinct)
+    patterns: List[bytes] = field(default_factory=list)
 
     @property
     def n_concepts(self) -> int:
@@ -337,6 +354,14 @@ class KB:
     def n_num_roles(self) -> int:
         return len(self.num_row_ptr)
 
+    @property
+    def n_str_roles(self) -> int:
+        return len(self.str_row_ptr)
+
+    @property
+    def n_patterns(self) -> int:
+        return len(self.patterns)
+
     def n_edges(self, r: int) -> int:
         return int(self.col[r].size)
 
@@ -346,7 +371,9 @@ class KB:
             t += 2 * self.row_ptr[r].nbytes + 2 * self.col[r].nbytes
         for q in range(self.n_num_roles):
             t += self.num_row_ptr[q].nbytes + self.num_vals[q].nbytes
-        return t
+        for q in range(self.n_str_roles):
+            t += self.str_row_ptr[q].nbytes + self.str_ids[q].nbytes
+        return t + sum(len(x) for x in self.strings)
 
 
 def latent_class(cfg: KBConfig) -> np.ndarray:
@@ -417,6 +444,63 @@ def gen_props(cfg: KBConfig, z=None) -> np.ndarray:
             v[miss] = np.nan
         out[p] = v
     return out
+
+
+def _degrees(cfg: KBConfig, law: Tuple, stream: int) -> np.ndarray:
+    n = cfg.n
+    if law[0] == "poisson":
+        cdf = poisson_cdf(law[1], 200)
+        return np.searchsorted(cdf, rng.uniform_range(cfg.seed, stream, n), side="right")
+    if law[0] == "single":       # one individual holds every value
+        deg = np.zeros(n, dtype=np.int64)
+        deg[int(rng.randint(cfg.seed, stream, np.array([0]), n)[0])] = int(law[1])
+        return deg
+    if law[0] == "unique":       # one value per individual
+        return np.ones(n, dtype=np.int64)
+    raise ValueError(law[0])
+
+
+def gen_strings(cfg: KBConfig) -> Tuple[List[bytes], List[bytes]]:
+    """The string table (distinct strings of lengths str_len over the first
+    `alphabet` lowercase letters) and the patterns: the empty string, then
+    substrings of length 1-4 of table strings, then (the last) a string longer
+    than any in the table."""
+    table, seen = [], set()
+    r = rng.Rng(cfg.seed, S_STR_TABLE)
+    lo, hi = cfg.str_len
+    letters = b"abcdefghijklmnopqrstuvwxyz"[: cfg.alphabet]
+    while len(table) < cfg.n_strings:
+        k = r.randint(lo, hi)
+        x = bytes(letters[r.randint(0, len(letters) - 1)] for _ in range(k))
+        if x not in seen:
+            seen.add(x)
+            table.append(x)
+    pats = []
+    if cfg.n_patterns:
+        pr = rng.Rng(cfg.seed, S_PATTERN)
+        pats.append(b"")
+        while len(pats) < cfg.n_patterns - 1 and table:
+            x = table[pr.randint(0, len(table) - 1)]
+            k = pr.randint(1, min(4, len(x))) if x else 0
+            i = pr.randint(0, len(x) - k)
+            pats.append(x[i: i + k])
+        if len(pats) < cfg.n_patterns:
+            pats.append(letters[:1] * (hi + 1))
+    return table, pats
+
+
+def gen_str_roles(cfg: KBConfig, n_strings: int) -> Tuple[List[np.ndarray], List[np.ndarray]]:
+    """String concrete roles as CSR over individuals of uniform string ids."""
+    rps, ids = [], []
+    for q in range(cfg.n_str_roles):
+        deg = _degrees(cfg, cfg.str_degree, S_STR_DEG + q)
+        rp = np.zeros(cfg.n + 1, dtype=np.uint32)
+        np.cumsum(deg, out=rp[1:])
+        rps.append(rp)
+        m = int(rp[-1])
+        ids.append(rng.randint(cfg.seed, S_STR_ID + q, np.arange(m, dtype=np.uint64), max(n_strings, 1))
+                   .astype(np.uint32))
+    return rps, ids
 
 
 def gen_num_roles(cfg: KBConfig) -> Tuple[List[np.ndarray], List[np.ndarray]]:
@@ -491,15 +575,20 @@ def generate(cfg: KBConfig, roles: Optional[int] = None) -> KB:
     mn = np.zeros(n, dtype=bool)
     mn[neg] = True
     nrp, nv = gen_num_roles(cfg)
+    table, pats = gen_strings(cfg) if (cfg.n_str_roles or cfg.n_patterns) else ([], [])
+    srp, sid = gen_str_roles(cfg, len(table))
     return KB(cfg, n, w, wp, cb, rps, cols, irps, icols, props, pos, neg,
-              pack_bits(mp, wp), pack_bits(mn, wp), meta, nrp, nv)
+              pack_bits(mp, wp), pack_bits(mn, wp), meta, nrp, nv, srp, sid, table, pats)
 
 
 def from_arrays(n: int, concepts: List[List[int]], roles: List[List[Tuple[int, int]]],
                 props: List[List[float]], pos: List[int], neg: List[int],
-                num_roles: Optional[List[List[Tuple[int, float]]]] = None) -> KB:
+                num_roles: Optional[List[List[Tuple[int, float]]]] = None,
+                str_roles: Optional[List[List[Tuple[int, int]]]] = None, strings: Optional[List[bytes]] = None,
+                patterns: Optional[List[bytes]] = None) -> KB:
     """Small hand-written KB (fixtures): concepts as member lists, roles as edge
-    lists, numeric concrete roles as (individual, value) lists in any order."""
+    lists, numeric concrete roles as (individual, value) lists in any order,
+    string concrete roles as (individual, string id) lists into `strings`."""
     w, wp = words(n)
     cb = np.zeros((max(len(concepts), 0), wp), dtype=np.uint32)
     for j, mem in enumerate(concepts):
@@ -534,5 +623,14 @@ def from_arrays(n: int, concepts: List[List[int]], roles: List[List[Tuple[int, i
             rp[int(a) + 1] += 1
         nrp.append(np.cumsum(rp).astype(np.uint32))
         nv.append(np.array([assertions[k][1] for k in order], dtype=np.float32))
+    srp, sid = [], []
+    for assertions in str_roles or []:
+        order = sorted(range(len(assertions)), key=lambda k: int(assertions[k][0]))
+        rp = np.zeros(n + 1, dtype=np.uint32)
+        for a, _ in assertions:
+            rp[int(a) + 1] += 1
+        srp.append(np.cumsum(rp).astype(np.uint32))
+        sid.append(np.array([assertions[k][1] for k in order], dtype=np.uint32))
     return KB(cfg, n, w, wp, cb, rps, cols, irps, icols, pv, np.array(sorted(pos), dtype=np.int64),
-              np.array(sorted(neg), dtype=np.int64), pack_bits(mp, wp), pack_bits(mn, wp), {}, nrp, nv)
+              np.array(sorted(neg), dtype=np.int64), pack_bits(mp, wp), pack_bits(mn, wp), {}, nrp, nv,
+              srp, sid, list(strings or []), list(patterns or []))

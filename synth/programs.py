@@ -6,9 +6,9 @@ instructions, one uint64 each:
 
     bits  0..7   op
     bits  8..15  flags   (bit 0: the role is read inverted, r^-)
-    bits 16..31  a       (concept id, role id or data-property id)
-    bits 32..63  b       (n of a cardinality restriction, or the float32 bits
-                          of a data-range threshold)
+    bits 16..31  a       (concept id, role id, data-property id or string-role id)
+    bits 32..63  b       (n of a cardinality restriction, the float32 bits of a
+                          data-range threshold, a string id or a pattern id)
 
 Ops (binary AND/OR; NOT and the role restrictions are unary; the rest are
 leaves):
@@ -16,12 +16,14 @@ leaves):
     1 ATOM c   2 TOP   3 BOT   4 NOT   5 AND   6 OR
     7 EXISTS r   8 FORALL r   9 ATLEAST r n   10 ATMOST r n   11 EXACTLY r n
     12 DGE p t   13 DLE p t   14 DEQ p t
+    15 SEQ s v (a value of string role s is string v)
+    16 SCONTAINS s k (a value of string role s contains pattern k)
 
 The text syntax (for tests and fixtures) is prefix s-expressions:
 
     A3, TOP, BOT, (not X), (and X Y), (or X Y), (some r2 X), (some r2- X),
     (all r2 X), (min 2 r2 X), (max 2 r2 X), (exactly 2 r2 X),
-    (ge p1 0.5), (le p1 0.5), (eq p1 0.5)
+    (ge p1 0.5), (le p1 0.5), (eq p1 0.5), (seq s0 17), (contains s0 3)
 
 with r2- the inverse of role 2; ``(r-)-`` folds back to ``r`` (the suffix may
 repeat: r2-- is r2).
@@ -39,16 +41,18 @@ import numpy as np
 ATOM, TOP, BOT, NOT, AND, OR = 1, 2, 3, 4, 5, 6
 EXISTS, FORALL, ATLEAST, ATMOST, EXACTLY = 7, 8, 9, 10, 11
 DGE, DLE, DEQ = 12, 13, 14
+SEQ, SCONTAINS = 15, 16
 
 OP_NAMES = {
     ATOM: "ATOM", TOP: "TOP", BOT: "BOT", NOT: "NOT", AND: "AND", OR: "OR",
     EXISTS: "EXISTS", FORALL: "FORALL", ATLEAST: "ATLEAST", ATMOST: "ATMOST",
-    EXACTLY: "EXACTLY", DGE: "DGE", DLE: "DLE", DEQ: "DEQ",
+    EXACTLY: "EXACTLY", DGE: "DGE", DLE: "DLE", DEQ: "DEQ", SEQ: "SEQ", SCONTAINS: "SCONTAINS",
 }
 ROLE_OPS = (EXISTS, FORALL, ATLEAST, ATMOST, EXACTLY)
 COUNT_OPS = (ATLEAST, ATMOST, EXACTLY)
 DATA_OPS = (DGE, DLE, DEQ)
-LEAF_OPS = (ATOM, TOP, BOT) + DATA_OPS
+STRING_OPS = (SEQ, SCONTAINS)
+LEAF_OPS = (ATOM, TOP, BOT) + DATA_OPS + STRING_OPS
 FLAG_INVERSE = 1
 
 
@@ -74,8 +78,8 @@ def fields(w: int) -> Tuple[int, int, int, int]:
 class Node:
     """Expression tree node used by the generators and the text syntax."""
     op: int
-    a: int = 0            # concept / role / property id
-    b: int = 0            # n, or float32 bits of the threshold
+    a: int = 0            # concept / role / property / string-role id
+    b: int = 0            # n, float32 bits of the threshold, string id or pattern id
     inv: bool = False     # role read inverted
     kids: List["Node"] = field(default_factory=list)
 
@@ -98,7 +102,7 @@ def from_postfix(prog: Sequence[int]) -> Node:
     st: List[Node] = []
     for w in prog:
         op, fl, a, b = fields(w)
-        if op in (ATOM, TOP, BOT) or op in DATA_OPS:
+        if op in LEAF_OPS:
             st.append(Node(op, a, b))
         elif op in (NOT,) or op in ROLE_OPS:
             x = st.pop()
@@ -119,6 +123,8 @@ _ROLE_WORD = {EXISTS: "some", FORALL: "all", ATLEAST: "min", ATMOST: "max", EXAC
 _DATA_WORD = {DGE: "ge", DLE: "le", DEQ: "eq"}
 _WORD_ROLE = {v: k for k, v in _ROLE_WORD.items()}
 _WORD_DATA = {v: k for k, v in _DATA_WORD.items()}
+_STRING_WORD = {SEQ: "seq", SCONTAINS: "contains"}
+_WORD_STRING = {v: k for k, v in _STRING_WORD.items()}
 
 
 def to_text(n: Node) -> str:
@@ -139,6 +145,8 @@ def to_text(n: Node) -> str:
         return f"({_ROLE_WORD[n.op]} {r} {to_text(n.kids[0])})"
     if n.op in DATA_OPS:
         return f"({_DATA_WORD[n.op]} p{n.a} {str(np.float32(bits_f32(n.b)))})"  # shortest float32 text
+    if n.op in STRING_OPS:
+        return f"({_STRING_WORD[n.op]} s{n.a} {n.b})"
     raise ValueError(n.op)
 
 
@@ -194,6 +202,11 @@ def parse(text: str) -> Node:
             t = float(toks[pos + 1])
             pos += 2
             n = Node(_WORD_DATA[head], p, f32_bits(t))
+        elif head in _WORD_STRING:
+            if not toks[pos].startswith("s"):
+                raise ValueError(f"expected string role, got {toks[pos]}")
+            n = Node(_WORD_STRING[head], int(toks[pos][1:]), int(toks[pos + 1]))
+            pos += 2
         else:
             raise ValueError(f"bad head {head}")
         if toks[pos] != ")":

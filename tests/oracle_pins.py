@@ -22,7 +22,12 @@ Sources of truth:
   sets (>= t iff the largest value is >= t, and so on), a hand-worked KB with
   NaN and signed zeros, the single- and unique-subject shapes (the latter
   against a one-value property holding the same values) and the identities
-  (>= t) or (<= t) = "has a value", (== t) within both.
+  (>= t) or (<= t) = "has a value", (== t) within both;
+* string concrete roles (Algorithms 11-14): a hand-worked KB; closed forms
+  through the interned ids (the oracle compares bytes) and Python's own
+  substring search over the table; the empty pattern = "has a value"; a
+  string's equality restriction within the containment of any of its
+  substrings; the brute force over tiny KBs with string roles.
 """
 from __future__ import annotations
 
@@ -80,7 +85,12 @@ def to_tiny(kb: K.KB) -> fo_brute.TinyKB:
         rp, vals = kb.num_row_ptr[q], kb.num_vals[q]
         props.append({i: [float(vals[k]) for k in range(int(rp[i]), int(rp[i + 1]))]
                       for i in range(n) if rp[i + 1] > rp[i]})
-    return fo_brute.TinyKB(n, concepts, roles, props)
+    strs = []
+    for q in range(kb.n_str_roles):
+        rp, ids = kb.str_row_ptr[q], kb.str_ids[q]
+        strs.append({i: [kb.strings[int(ids[k])] for k in range(int(rp[i]), int(rp[i + 1]))]
+                     for i in range(n) if rp[i + 1] > rp[i]})
+    return fo_brute.TinyKB(n, concepts, roles, props, strs, kb.strings, kb.patterns)
 
 
 def random_program(r: Rng, kb: K.KB, depth: int, role_free: bool = False) -> P.Node:
@@ -91,6 +101,11 @@ def random_program(r: Rng, kb: K.KB, depth: int, role_free: bool = False) -> P.N
             return P.Node(P.TOP)
         if k == 1:
             return P.Node(P.BOT)
+        if k <= 3 and kb.n_str_roles and r.random() < 0.5:
+            q = r.randint(0, kb.n_str_roles - 1)
+            if r.random() < 0.5 and kb.n_patterns:
+                return P.Node(P.SCONTAINS, q, r.randint(0, kb.n_patterns - 1))
+            return P.Node(P.SEQ, q, r.randint(0, len(kb.strings)))    # the last id is not in the table
         if k <= 3 and kb.n_num_roles and r.random() < 0.5:
             q = r.randint(0, kb.n_num_roles - 1)
             vals = kb.num_vals[q]
@@ -125,6 +140,11 @@ def tiny_kbs():
     for seed, n, nd in ((105, 24, ("poisson", 2.0)), (106, 37, ("poisson", 1.0))):
         cfg = base.scaled(n, seed=seed, n_concepts=4, n_roles=2, degree=("poisson", 2.0), n_props=1, n_pos=4,
                           n_neg=4, n_num_roles=2, num_degree=nd)
+        out.append(K.generate(cfg))
+    for seed, n in ((107, 29), (108, 41)):
+        cfg = base.scaled(n, seed=seed, n_concepts=4, n_roles=2, degree=("poisson", 2.0), n_props=1, n_pos=4,
+                          n_neg=4, n_str_roles=2, str_degree=("poisson", 1.5), n_strings=12, str_len=(0, 5),
+                          alphabet=3, n_patterns=8)
         out.append(K.generate(cfg))
     return out
 
@@ -347,6 +367,61 @@ def pin_numeric_roles(L) -> List[str]:
     return bad
 
 
+def pin_string_roles(L) -> List[str]:
+    bad = []
+    ins = lambda op, s_, b: [P.insn(op, 0, s_, b)]
+    sets = lambda okb, op, s_, b: set(np.nonzero(oracle.eval_program(okb, ins(op, s_, b), L=L))[0].tolist())
+    # hand-worked: role 0 asserts 0:{catalog, dog} 1:{cat} 2:{""} 3:{at, dog} 5:{catalog}; role 1 asserts 4:{dog}
+    strings = [b"cat", b"catalog", b"dog", b"", b"at"]
+    patterns = [b"", b"cat", b"og", b"atalogue", b"t", b"a"]
+    r0 = [(5, b"catalog"), (0, b"dog"), (1, b"cat"), (2, b""), (3, b"at"), (0, b"catalog"), (3, b"dog")]
+    z = np.zeros(6, np.uint8)
+    okb = oracle.OracleKB.from_parts(6, np.zeros((0, 6), np.uint8), [], np.zeros((0, 6), np.float32), z, z,
+                                     str_roles=[(np.array([a for a, _ in r0]), [v for _, v in r0]),
+                                                (np.array([4]), [b"dog"])],
+                                     strings=strings, patterns=patterns)
+    cases = [(P.SEQ, 0, 0, {1}), (P.SEQ, 0, 1, {0, 5}), (P.SEQ, 0, 2, {0, 3}), (P.SEQ, 0, 3, {2}),
+             (P.SEQ, 0, 4, {3}), (P.SEQ, 0, 5, set()), (P.SEQ, 0, 0xFFFFFFFF, set()), (P.SEQ, 1, 2, {4}),
+             (P.SEQ, 1, 0, set()), (P.SCONTAINS, 0, 0, {0, 1, 2, 3, 5}), (P.SCONTAINS, 0, 1, {0, 1, 5}),
+             (P.SCONTAINS, 0, 2, {0, 3, 5}), (P.SCONTAINS, 0, 3, set()), (P.SCONTAINS, 0, 4, {0, 1, 3, 5}),
+             (P.SCONTAINS, 0, 5, {0, 1, 3, 5}), (P.SCONTAINS, 1, 2, {4}), (P.SCONTAINS, 1, 1, set())]
+    for op, s_, b, want in cases:
+        got = sets(okb, op, s_, b)
+        if got != want:
+            bad.append(f"hand-worked string role op={op} s={s_} b={b}: {sorted(got)} != {sorted(want)}")
+    # generated KBs: closed forms through the interned ids and Python's substring search
+    base = K.CONFIGS["small"]
+    for seed, n, sd in ((121, 400, ("poisson", 2.0)), (122, 150, ("single", 60)), (123, 300, ("unique",))):
+        kb = K.generate(base.scaled(n, seed=seed, n_concepts=2, n_roles=1, degree=("poisson", 2.0), n_props=1,
+                                    n_pos=10, n_neg=10, n_str_roles=2, str_degree=sd, n_strings=40,
+                                    str_len=(1, 7), alphabet=4, n_patterns=10))
+        okb = oracle.from_synth(kb)
+        contains = [[p_ in x for x in kb.strings] for p_ in kb.patterns]
+        for q in range(kb.n_str_roles):
+            ids = kb.str_ids[q].astype(np.int64)
+            subj = np.repeat(np.arange(kb.n), np.diff(kb.str_row_ptr[q].astype(np.int64)))
+            has = set(subj.tolist())
+            seq = {}
+            for b in list(range(len(kb.strings))) + [len(kb.strings), 0xFFFFFFFF]:
+                want = set(subj[ids == b].tolist())
+                seq[b] = sets(okb, P.SEQ, q, b)
+                if seq[b] != want:
+                    bad.append(f"string closed form SEQ {sd[0]} q={q} b={b}")
+            for k in range(len(kb.patterns)):
+                hit = np.array(contains[k], bool)
+                want = set(subj[hit[ids]].tolist()) if ids.size else set()
+                got = sets(okb, P.SCONTAINS, q, k)
+                if got != want:
+                    bad.append(f"string closed form SCONTAINS {sd[0]} q={q} k={k}")
+                if kb.patterns[k] == b"" and got != has:
+                    bad.append(f"empty pattern {sd[0]} q={q}")
+                for b, x in enumerate(kb.strings):      # equal to x implies containing any substring of x
+                    if kb.patterns[k] in x and not seq[b] <= got:
+                        bad.append(f"SEQ within SCONTAINS {sd[0]} q={q} b={b} k={k}")
+                        break
+    return bad
+
+
 def pin_validation(L) -> List[str]:
     fx = golden_io.load("family.txt")
     okb = tiny_from_fixture(fx)
@@ -354,7 +429,7 @@ def pin_validation(L) -> List[str]:
     cases = [
         ([], -6),
         ([P.insn(0)], -1),
-        ([P.insn(15)], -1),
+        ([P.insn(17)], -1),
         ([P.insn(255)], -1),
         ([A(4)], -2),
         ([A(0), P.insn(P.EXISTS, 0, 2)], -2),
@@ -378,8 +453,17 @@ def pin_validation(L) -> List[str]:
         got = oracle.validate(nkb, np.array([P.insn(P.DGE, 0, p, 0)], dtype=np.uint64), L=L)
         if got != want:
             bad.append(f"validate property id {p}: {got} != {want}")
+    # string roles: role ids below n_str_roles; pattern ids below n_patterns; any string id
+    z = np.zeros(3, np.uint8)
+    skb = oracle.OracleKB.from_parts(3, np.zeros((0, 3), np.uint8), [], np.zeros((0, 3), np.float32), z, z,
+                                     str_roles=[(np.array([0]), [b"x"])] * 2, strings=[b"x"], patterns=[b"", b"x"])
+    for op, a, b, want in ((P.SEQ, 1, 0, 0), (P.SEQ, 2, 0, -2), (P.SEQ, 0, 0xFFFFFFFF, 0), (P.SCONTAINS, 1, 1, 0),
+                           (P.SCONTAINS, 1, 2, -2), (P.SCONTAINS, 2, 0, -2)):
+        got = oracle.validate(skb, np.array([P.insn(op, 0, a, b)], dtype=np.uint64), L=L)
+        if got != want:
+            bad.append(f"validate string op={op} a={a} b={b}: {got} != {want}")
     return bad
 
 
 ALL_PINS = (pin_golden, pin_brute_force, pin_identities, pin_inverse_transpose, pin_closed_forms,
-            pin_numeric_roles, pin_validation)
+            pin_numeric_roles, pin_string_roles, pin_validation)

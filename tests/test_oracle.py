@@ -66,6 +66,12 @@ MUTANTS = {
     "numeric_le_strict": ("if (op == O_DLE) return v <= t;", "if (op == O_DLE) return v < t;"),
     "numeric_ids_rejected": ("(int64_t)a_of(prog[k]) >= (int64_t)kb->n_props + kb->n_num_roles",
                              "(int64_t)a_of(prog[k]) >= (int64_t)kb->n_props"),
+    "contain_misses_the_end": ("for (int64_t i = 0; i + lp <= lx; ++i) {", "for (int64_t i = 0; i + lp < lx; ++i) {"),
+    "contain_first_char_only": ("while (j < lp && x[i + j] == p[j]) ++j;", "while (j < lp && x[i + j] == p[0]) ++j;"),
+    "equal_as_prefix": ("    if (lx != ly) return 0;", "    if (lx < ly) return 0;"),
+    "seq_absent_is_first": ("if ((int64_t)b >= kb->n_strings) return;", "if ((int64_t)b >= kb->n_strings) b = 0;"),
+    "string_first_role_only": ("for (int64_t k = kb->str_off[s]; k < kb->str_off[s + 1]; ++k) {",
+                               "for (int64_t k = kb->str_off[0]; k < kb->str_off[1]; ++k) {"),
     "validate_depth_off_by_one": ("if (depth > ORACLE_MAX_STACK) return OE_OVERFLOW;",
                                   "if (depth >= ORACLE_MAX_STACK) return OE_OVERFLOW;"),
 }
