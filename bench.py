@@ -283,6 +283,39 @@ def surrogate_round(args, dev):
             "surrogate_round_s": sur_s, "plain_time_to_best_s": plain_s, "mlp_forward": fwd}
 
 
+def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7):
+    """One launch of a batch of restrictions, device-resident: median of `reps` CUDA-event timings on
+    the launching stream after warm-up (the graph is captured on the second execution)."""
+    import torch
+    import paper_2412_00802_gb300 as H
+    from synth import programs as P
+    stream = torch.cuda.current_stream(dev)
+    flat, offs = P.pack_batch(progs)
+    plan = H.hedl_plan_batch(dkb.handle, flat, offs, flags)
+    info = H.hedl_plan_info_get(plan)
+    ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device=dev)
+    counts = torch.zeros((len(progs), 4), dtype=torch.int32, device=dev)
+    run = (lambda: H.hedl_plan_execute(dkb.handle, plan, counts, None, ws)) if flags & H.HEDL_PLAIN else \
+        (lambda: H.hedl_plan_replay(dkb.handle, plan, counts, None, ws))
+    H.hedl_plan_execute(dkb.handle, plan, counts, None, ws)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    H.hedl_sync_status(dkb.handle)
+    t = statistics.median(ms) / 1000.0
+    return {"restrictions": len(progs), "ms": 1000 * t, "restrictions_per_s": len(progs) / t,
+            "model_bytes": info["model_bytes"], "achieved_gbs": info["model_bytes"] / t / 1e9,
+            "frac": info["model_bytes"] / t / 1e9 / peak}, counts.cpu()
+
+
 def numeric_run(args, dev):
     """Numeric concrete roles (several values per subject, Section III-B; existential compare,
     Algorithms 9-10) on their own KB: 10^7 individuals, 8 roles of ~4 * 10^7 values U[0, 1000]
@@ -297,48 +330,58 @@ def numeric_run(args, dev):
     kb = K.generate(K.CONFIGS["numeric"])
     gen_s = time.perf_counter() - t0
     dkb = H.DeviceKB.from_synth(kb, device=str(dev))
-    stream = torch.cuda.current_stream(dev)
     peak, kind = measured_peaks()
     thr = [float(v[(q * 7919) % v.size]) for q, v in enumerate(kb.num_vals)]
     one = [np.array([P.insn(P.DGE, 0, q, P.f32_bits(thr[q]))], np.uint64) for q in range(kb.n_num_roles)]
     three = [np.array([P.insn(op, 0, q, P.f32_bits(thr[q]))], np.uint64)
              for q in range(kb.n_num_roles) for op in (P.DGE, P.DLE, P.DEQ)]
-
-    def timed(progs, flags, reps=7):
-        flat, offs = P.pack_batch(progs)
-        plan = H.hedl_plan_batch(dkb.handle, flat, offs, flags)
-        info = H.hedl_plan_info_get(plan)
-        ws = torch.empty(info["workspace_bytes"], dtype=torch.uint8, device=dev)
-        counts = torch.zeros((len(progs), 4), dtype=torch.int32, device=dev)
-        run = (lambda: H.hedl_plan_execute(dkb.handle, plan, counts, None, ws)) if flags & H.HEDL_PLAIN else \
-            (lambda: H.hedl_plan_replay(dkb.handle, plan, counts, None, ws))
-        H.hedl_plan_execute(dkb.handle, plan, counts, None, ws)
-        for _ in range(3):                       # warm-up (the graph is captured on the second execution)
-            run()
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            run()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        H.hedl_sync_status(dkb.handle)
-        t = statistics.median(ms) / 1000.0
-        return {"restrictions": len(progs), "ms": 1000 * t, "restrictions_per_s": len(progs) / t,
-                "model_bytes": info["model_bytes"], "achieved_gbs": info["model_bytes"] / t / 1e9,
-                "frac": info["model_bytes"] / t / 1e9 / peak}, counts.cpu()
-
     with ClockSampler(dev.index or 0) as clk:
-        a, _ = timed(one, 0)
-        b, cb = timed(three, 0)
-        c, cp = timed(three, H.HEDL_PLAIN)
+        a, _ = _timed_restrictions(dkb, one, 0, dev, peak)
+        b, cb = _timed_restrictions(dkb, three, 0, dev, peak)
+        c, cp = _timed_restrictions(dkb, three, H.HEDL_PLAIN, dev, peak)
     return {"workload": "N=10,000,000 individuals, 8 numeric concrete roles, Poisson(4) values per individual "
                         "U[0,1000] (~4*10^7 values, 200 MB per role)", "kb_gen_s": gen_s,
-            "values": [int(v.size) for v in kb.num_vals], "kernel": "exec_kernel (num_words)",
+            "values": [int(v.size) for v in kb.num_vals], "kernel": "exec_kernel (exist_words)",
             "peak": peak, "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "one_per_role": a, "three_per_role": b, "plain_three_per_role": c,
+            "plain_counts_identical": bool(torch.equal(cb, cp)), "clocks": clk.summary()}
+
+
+def string_run(args, dev):
+    """String concrete roles (Section III-B; EQUAL, Algorithms 11-12, CONTAIN, Algorithms 13-14) on
+    their own KB: 10^7 individuals, 8 roles of ~2 * 10^7 interned ids (120 MB of row pointers and
+    ids each) into 100,000 distinct strings, 64 patterns.  Timed like the numeric roles: (a) one
+    EQUAL per role (no two read the same arrays: 0.96 GB > L2), (b) EQUAL and CONTAIN of two
+    patterns on every role (24 restrictions), (c) the 24 on the plain path.  Load time includes the
+    pattern-containment bitmap (64 x 100,000 strings)."""
+    import torch
+    import paper_2412_00802_gb300 as H
+    from synth import kb as K, programs as P
+    t0 = time.perf_counter()
+    kb = K.generate(K.CONFIGS["strings"])
+    gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dkb = H.DeviceKB.from_synth(kb, device=str(dev))
+    load_s = time.perf_counter() - t0
+    peak, kind = measured_peaks()
+    sid = [int(v[(q * 7919) % v.size]) for q, v in enumerate(kb.str_ids)]
+    one = [np.array([P.insn(P.SEQ, 0, q, sid[q])], np.uint64) for q in range(kb.n_str_roles)]
+    mixed = []
+    for q in range(kb.n_str_roles):
+        mixed += [np.array([P.insn(P.SEQ, 0, q, sid[q])], np.uint64),
+                  np.array([P.insn(P.SCONTAINS, 0, q, 1 + q)], np.uint64),
+                  np.array([P.insn(P.SCONTAINS, 0, q, 17 + q)], np.uint64)]
+    with ClockSampler(dev.index or 0) as clk:
+        a, _ = _timed_restrictions(dkb, one, 0, dev, peak)
+        b, cb = _timed_restrictions(dkb, mixed, 0, dev, peak)
+        c, cp = _timed_restrictions(dkb, mixed, H.HEDL_PLAIN, dev, peak)
+    return {"workload": "N=10,000,000 individuals, 8 string concrete roles, Poisson(2) values per individual "
+                        "(~2*10^7 ids, 120 MB per role) into 100,000 distinct strings of 3-12 letters; 64 "
+                        "patterns", "kb_gen_s": gen_s, "kb_load_s_with_bitmap": load_s,
+            "values": [int(v.size) for v in kb.str_ids], "kernel": "exec_kernel (exist_words)",
+            "peak": peak, "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "equal_one_per_role": a, "equal_and_contain": b, "plain_equal_and_contain": c,
             "plain_counts_identical": bool(torch.equal(cb, cp)), "clocks": clk.summary()}
 
 
@@ -688,6 +731,7 @@ def run_ours(args, rank, world, local_rank):
     surrogate = None if args.no_surrogate else surrogate_round(args, dev)
     search = None if args.no_search else search_run(args, dev)
     numeric = None if args.no_numeric else numeric_run(args, dev)
+    strings = None if args.no_strings else string_run(args, dev)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_ids),
         "warmup": len(warm_ids), "ms_per_step": 1000.0 * elapsed / len(timed_ids), "higher_is_better": True,
@@ -714,6 +758,7 @@ def run_ours(args, rank, world, local_rank):
         "surrogate": surrogate,
         "search": search,
         "numeric_roles": numeric,
+        "string_roles": strings,
     }
     print(json.dumps(out), flush=True)
 
@@ -731,6 +776,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-ranked round")
     ap.add_argument("--no-search", action="store_true", help="skip the beam-search comparison")
     ap.add_argument("--no-numeric", action="store_true", help="skip the numeric-concrete-role workload")
+    ap.add_argument("--no-strings", action="store_true", help="skip the string-concrete-role workload")
     ap.add_argument("--surrogate-train", type=int, default=0,
                     help="training hypotheses of the surrogate round (default 65,536; 1,000,000 with --surrogate-full)")
     ap.add_argument("--surrogate-full", action="store_true",

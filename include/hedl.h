@@ -62,9 +62,11 @@ typedef enum {
  * Program format: postfix, one uint64 per instruction.
  *   bits  0..7   op (hedl_op)
  *   bits  8..15  flags: bit 0 = read the role inverted (r^-); other bits ignored
- *   bits 16..31  a: concept id (ATOM), role id (role ops), property id (data ops)
+ *   bits 16..31  a: concept id (ATOM), role id (role ops), property id (data
+ *                ops), string-role id (SEQ / SCONTAINS)
  *   bits 32..63  b: n for ATLEAST / ATMOST / EXACTLY; the IEEE float32 bit
- *                pattern of the threshold for DGE / DLE / DEQ; ignored otherwise
+ *                pattern of the threshold for DGE / DLE / DEQ; a string id
+ *                for SEQ; a pattern id for SCONTAINS; ignored otherwise
  * AND and OR pop two operands, NOT and the role restrictions one, the rest are
  * leaves.  A valid program is non-empty, names existing ids, never pops an
  * empty stack, never holds more than HEDL_MAX_STACK operands, and leaves
@@ -90,6 +92,11 @@ typedef enum {
  *                 (Section III-B: a subject may assert several values), on
  *                 which the restriction is existential: a belongs as soon as
  *                 one of its values passes the compare.
+ *   SEQ s v       a with a value of string role s equal to table string v;
+ *                 a v outside the table matches nothing (the caller maps a
+ *                 string it does not find to such an id)       (Algs 11-12)
+ *   SCONTAINS s k a with a value of string role s that contains pattern k
+ *                 as a substring (the empty pattern: any value) (Algs 13-14)
  */
 typedef enum {
     HEDL_OP_ATOM = 1, HEDL_OP_TOP = 2, HEDL_OP_BOT = 3, HEDL_OP_NOT = 4,
@@ -129,6 +136,16 @@ typedef struct {
     uint32_t n_vals;           /* < 2^31 */
 } hedl_numeric_role;
 
+/* One string concrete role (Section III-B): the (subject, string) assertions
+ * grouped by subject as CSR of interned string ids.  Device arrays: row_ptr
+ * uint32[n_indiv+1] as for hedl_numeric_role; ids uint32[n_vals], each below
+ * the descriptor's n_strings. */
+typedef struct {
+    const uint32_t *row_ptr;
+    const uint32_t *ids;
+    uint32_t n_vals;           /* < 2^31 */
+} hedl_string_role;
+
 typedef struct {
     uint32_t n_indiv;                  /* individuals, >= 1 */
     uint32_t n_concepts;
@@ -141,6 +158,15 @@ typedef struct {
     uint64_t prop_stride;              /* floats between property rows, >= n_indiv */
     uint32_t n_num_roles;              /* numeric concrete roles: property ids n_props + q */
     const hedl_numeric_role *num_roles;/* HOST array [n_num_roles] of device CSRs */
+    uint32_t n_str_roles;              /* string concrete roles: ids of SEQ / SCONTAINS */
+    const hedl_string_role *str_roles; /* HOST array [n_str_roles] of device CSRs */
+    uint32_t n_strings;                /* the string table: DISTINCT strings (interned) */
+    const uint32_t *str_off;           /* device [n_strings+1]: string i is chars [off[i], off[i+1]) */
+    const uint8_t *str_chars;          /* device [n_str_chars] */
+    uint32_t n_str_chars;
+    uint32_t n_patterns;               /* substring patterns of SCONTAINS, fixed for the handle */
+    const uint32_t *pat_off;           /* HOST [n_patterns+1] */
+    const uint8_t *pat_chars;          /* HOST [pat_off[n_patterns]] */
 } hedl_kb_desc;
 
 typedef struct hedl_kb hedl_kb;
@@ -149,19 +175,25 @@ typedef struct hedl_kb hedl_kb;
 
 /* Register a knowledge base resident on the device (Section III-A).
  * Borrows every device array of d (see the conventions above); copies the
- * small host arrays roles / inv_roles / num_roles.  n_props + n_num_roles is
- * at most 65536 (16-bit property ids).  Unless HEDL_KB_NO_VALIDATE, checks on
- * the device that concept rows have zero tails, that each CSR is well formed
- * (monotone row_ptr, rows strictly increasing, ids < n), that each inverse
- * CSR is exactly the transpose of its forward CSR and that each numeric
- * role's row_ptr starts at 0, never decreases and ends at n_vals; a failed
- * check returns HEDL_ERR_BAD_KB and no handle.  With HEDL_KB_NO_VALIDATE the
- * caller guarantees all of that.  SYNCHRONIZES the stream.
+ * small host arrays roles / inv_roles / num_roles / str_roles and the
+ * patterns (to the device).  n_props + n_num_roles and n_str_roles are at most
+ * 65536 (16-bit ids).  Unless HEDL_KB_NO_VALIDATE, checks on the device that
+ * concept rows have zero tails, that each CSR is well formed (monotone
+ * row_ptr, rows strictly increasing, ids < n), that each inverse CSR is
+ * exactly the transpose of its forward CSR, that each numeric and string
+ * role's row_ptr starts at 0, never decreases and ends at n_vals, that string
+ * ids are below n_strings and that str_off starts at 0, never decreases and
+ * ends at n_str_chars; a failed check returns HEDL_ERR_BAD_KB and no handle.
+ * With HEDL_KB_NO_VALIDATE the caller guarantees all of that.  That the table
+ * holds distinct strings is never checked: SEQ compares ids.  Then computes,
+ * on the device, which table strings contain which pattern (a bitmap the
+ * handle owns; SCONTAINS reads it).  SYNCHRONIZES the stream.
  * *out receives the handle; release it with hedl_kb_free. */
 int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb **out);
 
 /* A planning-only handle: reads only the sizes in d (n_indiv, the counts,
- * each role's n_edges and each numeric role's n_vals; pointers may be NULL) and makes no CUDA call, so it
+ * each role's n_edges and each numeric and string role's n_vals; device
+ * pointers may be NULL; patterns are not read) and makes no CUDA call, so it
  * works on a host without a GPU.  hedl_validate, hedl_plan_batch and
  * hedl_plan_info_get accept it (its plans are shaped for a 152-SM GB300);
  * every call that would launch work returns HEDL_ERR_INVALID_ARG.  Release

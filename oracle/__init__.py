@@ -267,8 +267,13 @@ def from_synth(kb) -> OracleKB:
         lens = t_len[ids]
         v_off = np.zeros(ids.size + 1, np.int64)
         np.cumsum(lens, out=v_off[1:])
-        src = np.repeat(t_off[ids] - v_off[:-1], lens) + np.arange(int(v_off[-1]), dtype=np.int64)
-        arrays = (np.array(soff, np.int64), np.concatenate(subj), v_off, t[src])
+        vals = np.empty(int(v_off[-1]), np.uint8)
+        for c in range(0, ids.size, 1 << 22):    # gather each assertion's bytes, a chunk at a time
+            sl = slice(c, min(c + (1 << 22), ids.size))
+            b0, b1 = int(v_off[sl.start]), int(v_off[sl.stop])
+            src = np.repeat(t_off[ids[sl]] - v_off[sl], lens[sl]) + np.arange(b0, b1, dtype=np.int64)
+            vals[b0:b1] = t[src]
+        arrays = (np.array(soff, np.int64), np.concatenate(subj), v_off, vals)
     return OracleKB.from_parts(n, member, edges, kb.prop_vals, pos, neg, nums, (), kb.strings, kb.patterns,
                                arrays)
 

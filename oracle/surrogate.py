@@ -25,7 +25,9 @@ hypothesis grows (0) or shrinks (1) with its instance set.  A *signed* count
 adds +1 for an occurrence at polarity 0 and -1 at polarity 1.  A data
 threshold t of property p falls in bucket q = #{g in grid[p] : g < t} of a
 per-property grid of 15 increasing boundaries (the property's quantiles,
-supplied with the programs; q = 0 without a grid or for NaN t).
+supplied with the programs; q = 0 without a grid or for NaN t).  String
+restrictions (SEQ, SCONTAINS) have no features of their own: they count only
+in the length, depth and height features.
   [  0, 84) op histogram per depth: min(depth, 5)*14 + op-1
   [ 84,180) atomic concept, signed: concept id mod 96
   [180,244) role: (role id mod 32)*2 + inverse flag
@@ -110,6 +112,8 @@ def encode(prog: Sequence[int], grid=None, prior=None, stats=None) -> np.ndarray
         w = int(prog[k])
         op, inv, a, b = w & 0xFF, (w >> 8) & 1, (w >> 16) & 0xFFFF, (w >> 32) & 0xFFFFFFFF
         sign = 1 - 2 * pol[k]
+        if not 1 <= op <= 14:       # no feature: not an op, or a string restriction (ops 15-16)
+            continue
         f[min(depth[k], 5) * 14 + op - 1] += 1
         if _arity(op) == 0:
             leaves += 1

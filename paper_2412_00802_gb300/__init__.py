@@ -68,11 +68,28 @@ class hedl_numeric_role(ctypes.Structure):
     _fields_ = [("row_ptr", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("n_vals", ctypes.c_uint32)]
 
 
+class hedl_string_role(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("ids", ctypes.c_void_p), ("n_vals", ctypes.c_uint32)]
+
+
 class hedl_kb_desc(ctypes.Structure):
     _fields_ = [("n_indiv", ctypes.c_uint32), ("n_concepts", ctypes.c_uint32), ("concept_bits", ctypes.c_void_p),
                 ("n_roles", ctypes.c_uint32), ("roles", ctypes.c_void_p), ("inv_roles", ctypes.c_void_p),
                 ("n_props", ctypes.c_uint32), ("prop_vals", ctypes.c_void_p), ("prop_stride", ctypes.c_uint64),
-                ("n_num_roles", ctypes.c_uint32), ("num_roles", ctypes.c_void_p)]
+                ("n_num_roles", ctypes.c_uint32), ("num_roles", ctypes.c_void_p),
+                ("n_str_roles", ctypes.c_uint32), ("str_roles", ctypes.c_void_p),
+                ("n_strings", ctypes.c_uint32), ("str_off", ctypes.c_void_p), ("str_chars", ctypes.c_void_p),
+                ("n_str_chars", ctypes.c_uint32),
+                ("n_patterns", ctypes.c_uint32), ("pat_off", ctypes.c_void_p), ("pat_chars", ctypes.c_void_p)]
+
+
+def _byte_table(items) -> Tuple[np.ndarray, np.ndarray]:
+    """Byte strings as (uint32 offsets [len+1], uint8 bytes)."""
+    items = [bytes(x) for x in items]
+    off = np.zeros(len(items) + 1, np.uint32)
+    if items:
+        np.cumsum([len(x) for x in items], out=off[1:])
+    return off, np.frombuffer(b"".join(items) or b"\0", np.uint8).copy()
 
 
 class hedl_plan_info(ctypes.Structure):
@@ -214,10 +231,14 @@ class KBHandle:
 
 def hedl_kb_load(n_indiv: int, concept_bits, roles: Sequence[Tuple[object, object]],
                  inv_roles: Sequence[Tuple[object, object]], prop_vals, flags: int = 0, stream=None,
-                 num_roles: Sequence[Tuple[object, object]] = ()) -> KBHandle:
+                 num_roles: Sequence[Tuple[object, object]] = (), str_roles: Sequence[Tuple[object, object]] = (),
+                 str_table: Optional[Tuple[object, object, int, int]] = None,
+                 patterns: Sequence[bytes] = ()) -> KBHandle:
     """concept_bits: CUDA [C, row_words] 32-bit tensor; roles / inv_roles: (row_ptr, col) CUDA int32 tensors;
     prop_vals: CUDA float32 [P, stride] (or None); num_roles: (row_ptr int32, vals float32) CUDA tensors
-    of the numeric concrete roles (property ids P + q)."""
+    of the numeric concrete roles (property ids P + q); str_roles: (row_ptr, ids) CUDA int32 tensors of
+    the string concrete roles; str_table: (offsets int32 [S+1], chars uint8) CUDA tensors, S and the
+    number of chars; patterns: the substring patterns (host bytes)."""
     n_roles = len(roles)
     csr = (hedl_csr * max(n_roles, 1))()
     icsr = (hedl_csr * max(n_roles, 1))()
@@ -232,18 +253,28 @@ def hedl_kb_load(n_indiv: int, concept_bits, roles: Sequence[Tuple[object, objec
     nums = (hedl_numeric_role * max(Q, 1))()
     for q, (rp, vals) in enumerate(num_roles):
         nums[q] = hedl_numeric_role(_dptr(rp), _dptr(vals) if vals.numel() else None, int(vals.numel()))
+    SR = len(str_roles)
+    strs = (hedl_string_role * max(SR, 1))()
+    for q, (rp, ids) in enumerate(str_roles):
+        strs[q] = hedl_string_role(_dptr(rp), _dptr(ids) if ids.numel() else None, int(ids.numel()))
+    t_off, t_chars, n_str, n_chars = str_table if str_table is not None else (None, None, 0, 0)
+    p_off, p_chars = _byte_table(patterns)
     d = hedl_kb_desc(n_indiv, n_c, _dptr(concept_bits) if n_c else None, n_roles,
                      ctypes.addressof(csr) if n_roles else None, ctypes.addressof(icsr) if n_roles else None,
                      n_p, _dptr(prop_vals) if n_p else None, int(prop_vals.stride(0)) if n_p else 0,
-                     Q, ctypes.addressof(nums) if Q else None)
+                     Q, ctypes.addressof(nums) if Q else None,
+                     SR, ctypes.addressof(strs) if SR else None,
+                     n_str, _dptr(t_off) if n_str else None, _dptr(t_chars) if n_chars else None, n_chars,
+                     len(patterns), p_off.ctypes.data if patterns else None, p_chars.ctypes.data if patterns else None)
     out = ctypes.c_void_p()
     _check(library().hedl_kb_load(ctypes.byref(d), flags, _stream(stream), ctypes.byref(out)))
-    return KBHandle(out.value, [concept_bits, roles, inv_roles, prop_vals, num_roles], n_indiv,
-                    hedl_row_words(n_indiv))
+    return KBHandle(out.value, [concept_bits, roles, inv_roles, prop_vals, num_roles, str_roles, str_table],
+                    n_indiv, hedl_row_words(n_indiv))
 
 
 def hedl_kb_plan_only(n_indiv: int, n_concepts: int, role_edges: Sequence[int], n_props: int,
-                      num_role_vals: Sequence[int] = ()) -> KBHandle:
+                      num_role_vals: Sequence[int] = (), str_role_vals: Sequence[int] = (), n_strings: int = 0,
+                      n_patterns: int = 0) -> KBHandle:
     """Planning-only handle from sizes (no CUDA call; works without a GPU)."""
     R = len(role_edges)
     csr = (hedl_csr * max(R, 1))()
@@ -253,12 +284,17 @@ def hedl_kb_plan_only(n_indiv: int, n_concepts: int, role_edges: Sequence[int], 
     nums = (hedl_numeric_role * max(Q, 1))()
     for q, m in enumerate(num_role_vals):
         nums[q] = hedl_numeric_role(None, None, int(m))
+    SR = len(str_role_vals)
+    strs = (hedl_string_role * max(SR, 1))()
+    for q, m in enumerate(str_role_vals):
+        strs[q] = hedl_string_role(None, None, int(m))
     d = hedl_kb_desc(n_indiv, n_concepts, None, R, ctypes.addressof(csr) if R else None,
                      ctypes.addressof(csr) if R else None, n_props, None, n_indiv,
-                     Q, ctypes.addressof(nums) if Q else None)
+                     Q, ctypes.addressof(nums) if Q else None, SR, ctypes.addressof(strs) if SR else None,
+                     n_strings, None, None, 0, n_patterns, None, None)
     out = ctypes.c_void_p()
     _check(library().hedl_kb_plan_only(ctypes.byref(d), ctypes.byref(out)))
-    return KBHandle(out.value, [csr, nums], n_indiv, hedl_row_words(n_indiv))
+    return KBHandle(out.value, [csr, nums, strs], n_indiv, hedl_row_words(n_indiv))
 
 
 def hedl_kb_free(kb: KBHandle):
@@ -527,7 +563,9 @@ class DeviceKB:
                  inv_row_ptr: List[np.ndarray], inv_col: List[np.ndarray], prop_vals: np.ndarray,
                  pos_bits: Optional[np.ndarray] = None, neg_bits: Optional[np.ndarray] = None,
                  device: str = "cuda", flags: int = 0, num_row_ptr: Sequence[np.ndarray] = (),
-                 num_vals: Sequence[np.ndarray] = ()):
+                 num_vals: Sequence[np.ndarray] = (), str_row_ptr: Sequence[np.ndarray] = (),
+                 str_ids: Sequence[np.ndarray] = (), strings: Sequence[bytes] = (),
+                 patterns: Sequence[bytes] = ()):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -547,9 +585,16 @@ class DeviceKB:
         self.props = torch.from_numpy(pv).to(self.device) if P else None
         self.num_roles = [(t(rp, np.int32), t(np.asarray(v, np.float32), np.float32))
                           for rp, v in zip(num_row_ptr, num_vals)]
+        self.str_roles = [(t(rp, np.int32), t(np.asarray(ids, np.uint32), np.int32))
+                          for rp, ids in zip(str_row_ptr, str_ids)]
+        table = None
+        if len(strings):
+            off, chars = _byte_table(strings)
+            table = (t(off, np.int32), torch.from_numpy(chars).to(self.device), len(strings), int(off[-1]))
         with torch.cuda.device(self.device):
             self.handle = hedl_kb_load(n, self.concepts if self.concepts.shape[0] else None, self.roles,
-                                       self.inv_roles, self.props, flags, num_roles=self.num_roles)
+                                       self.inv_roles, self.props, flags, num_roles=self.num_roles,
+                                       str_roles=self.str_roles, str_table=table, patterns=list(patterns))
             if pos_bits is not None:
                 self.set_examples(pos_bits, neg_bits)
         self._ws = None
@@ -558,7 +603,8 @@ class DeviceKB:
     def from_synth(cls, kb, device: str = "cuda", flags: int = 0) -> "DeviceKB":
         return cls(kb.n, kb.concept_bits, kb.row_ptr, kb.col, kb.inv_row_ptr, kb.inv_col, kb.prop_vals,
                    kb.pos_bits, kb.neg_bits, device, flags, getattr(kb, "num_row_ptr", ()),
-                   getattr(kb, "num_vals", ()))
+                   getattr(kb, "num_vals", ()), getattr(kb, "str_row_ptr", ()), getattr(kb, "str_ids", ()),
+                   getattr(kb, "strings", ()), getattr(kb, "patterns", ()))
 
     def set_examples(self, pos_bits: np.ndarray, neg_bits: np.ndarray):
         self.pos = self.torch.from_numpy(np.ascontiguousarray(pos_bits).view(np.int32)).to(self.device)

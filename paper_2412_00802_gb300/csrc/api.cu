@@ -36,6 +36,9 @@ hedl::KBView hedl_kb::view() const {
     v.concepts = concepts;
     v.csr = csr_dev;
     v.num = num_dev;
+    v.str = str_dev;
+    v.contain = contain_dev;
+    v.contain_words = contain_words;
     v.props = props;
     v.prop_stride = prop_stride;
     v.pos = pos;
@@ -66,6 +69,45 @@ void destroy_graph(PlanImpl *p) {
 }
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Host checks of the string concrete roles, the table and the patterns.
+int check_str_roles(const hedl_kb_desc *d, bool arrays) {
+    if (d->n_str_roles > 65536) return fail(HEDL_ERR_INVALID_ARG, "at most 65536 string roles (16-bit ids)");
+    if (d->n_str_roles && !d->str_roles) return fail(HEDL_ERR_INVALID_ARG, "str_roles is NULL");
+    for (uint32_t q = 0; q < d->n_str_roles; ++q) {
+        const hedl_string_role &g = d->str_roles[q];
+        if (g.n_vals >= 0x80000000u) return fail(HEDL_ERR_INVALID_ARG, "a string role has 2^31 or more values");
+        if (arrays && (!g.row_ptr || (g.n_vals && !g.ids)))
+            return fail(HEDL_ERR_INVALID_ARG, "string role " + std::to_string(q) + ": NULL array");
+        if (g.n_vals && d->n_strings == 0)
+            return fail(HEDL_ERR_INVALID_ARG, "a string role has values but the string table is empty");
+    }
+    if (arrays && d->n_strings && (!d->str_off || (d->n_str_chars && !d->str_chars)))
+        return fail(HEDL_ERR_INVALID_ARG, "str_off / str_chars is NULL");
+    if (arrays && d->n_patterns) {
+        if (!d->pat_off || d->pat_off[0] != 0 || (d->pat_off[d->n_patterns] && !d->pat_chars))
+            return fail(HEDL_ERR_INVALID_ARG, "pat_off is NULL or does not start at 0, or pat_chars is NULL");
+        for (uint32_t k = 0; k < d->n_patterns; ++k)
+            if (d->pat_off[k + 1] < d->pat_off[k]) return fail(HEDL_ERR_INVALID_ARG, "pat_off decreases");
+    }
+    return HEDL_OK;
+}
+
+// Sizes (and, for a loadable handle, the device arrays) of the string roles.
+void take_str_sizes(hedl_kb *kb, const hedl_kb_desc *d, bool arrays) {
+    kb->n_str = d->n_str_roles;
+    for (uint32_t q = 0; q < d->n_str_roles; ++q)
+        kb->str_host.push_back(DevStr{arrays ? d->str_roles[q].row_ptr : nullptr,
+                                      arrays ? d->str_roles[q].ids : nullptr, d->str_roles[q].n_vals, 0});
+    kb->n_strings = d->n_strings;
+    kb->n_str_chars = d->n_str_chars;
+    kb->n_patterns = d->n_patterns;
+    kb->contain_words = ((uint64_t)d->n_strings + 31) / 32;
+    if (arrays) {
+        kb->str_off = d->str_off;
+        kb->str_chars = d->str_chars;
+    }
+}
 
 // Host checks of the numeric concrete roles of a descriptor (arrays only when
 // the handle will read them).
@@ -105,6 +147,7 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
     if (d->n_props && (!d->prop_vals || d->prop_stride < d->n_indiv))
         return fail(HEDL_ERR_INVALID_ARG, "prop_vals is NULL or prop_stride < n_indiv");
     if (int e = check_num_roles(d, true)) return e;
+    if (int e = check_str_roles(d, true)) return e;
     if (d->concept_bits && !aligned(d->concept_bits, 16))
         return fail(HEDL_ERR_INVALID_ARG, "concept_bits must be 16-byte aligned");
     for (uint32_t r = 0; r < d->n_roles; ++r) {
@@ -135,6 +178,7 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
     kb->n_num = d->n_num_roles;
     for (uint32_t q = 0; q < d->n_num_roles; ++q)
         kb->num_host.push_back(DevNum{d->num_roles[q].row_ptr, d->num_roles[q].vals, d->num_roles[q].n_vals, 0});
+    take_str_sizes(kb, d, true);
     cudaError_t e = cudaGetDevice(&kb->device);
     if (!e) e = cudaDeviceGetAttribute(&kb->n_sms, cudaDevAttrMultiProcessorCount, kb->device);
     int optin = 0;
@@ -150,6 +194,21 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
     if (!e && kb->n_num)
         e = cudaMemcpyAsync(kb->num_dev, kb->num_host.data(), sizeof(DevNum) * kb->n_num, cudaMemcpyHostToDevice,
                             (cudaStream_t)s);
+    if (!e && kb->n_str) e = cudaMalloc(&kb->str_dev, sizeof(DevStr) * kb->n_str);
+    if (!e && kb->n_str)
+        e = cudaMemcpyAsync(kb->str_dev, kb->str_host.data(), sizeof(DevStr) * kb->n_str, cudaMemcpyHostToDevice,
+                            (cudaStream_t)s);
+    if (!e && kb->n_patterns) {
+        const size_t pbytes = d->pat_off[kb->n_patterns];
+        e = cudaMalloc(&kb->pat_off_dev, 4ull * (kb->n_patterns + 1));
+        if (!e) e = cudaMalloc(&kb->pat_chars_dev, pbytes ? pbytes : 1);
+        if (!e)
+            e = cudaMemcpyAsync(kb->pat_off_dev, d->pat_off, 4ull * (kb->n_patterns + 1), cudaMemcpyHostToDevice,
+                                (cudaStream_t)s);
+        if (!e && pbytes)
+            e = cudaMemcpyAsync(kb->pat_chars_dev, d->pat_chars, pbytes, cudaMemcpyHostToDevice, (cudaStream_t)s);
+        if (!e && kb->contain_words) e = cudaMalloc(&kb->contain_dev, 4ull * kb->contain_words * kb->n_patterns);
+    }
     if (!e) e = cudaStreamSynchronize((cudaStream_t)s);
     if (e) {
         int rc = cuda_fail(e, "hedl_kb_load");
@@ -169,6 +228,14 @@ int hedl_kb_load(const hedl_kb_desc *d, unsigned flags, hedl_stream s, hedl_kb *
             return fail(HEDL_ERR_BAD_KB, why);
         }
     }
+    if (kb->n_patterns) {   // which table strings contain which pattern (the table is valid here)
+        int ce = contain_bitmap_device(kb, s);
+        if (ce) {
+            int rc = cuda_fail(ce, "hedl_kb_load pattern bitmap");
+            hedl_kb_free(kb);
+            return rc;
+        }
+    }
     *out = kb;
     return HEDL_OK;
 }
@@ -182,6 +249,7 @@ int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out) {
         return fail(HEDL_ERR_INVALID_ARG, "at most 65536 concepts, roles and properties (16-bit ids)");
     if (d->n_roles && (!d->roles || !d->inv_roles)) return fail(HEDL_ERR_INVALID_ARG, "roles / inv_roles is NULL");
     if (int e = check_num_roles(d, false)) return e;
+    if (int e = check_str_roles(d, false)) return e;
     auto *kb = new hedl_kb();
     kb->plan_only = true;
     kb->n = d->n_indiv;
@@ -200,6 +268,7 @@ int hedl_kb_plan_only(const hedl_kb_desc *d, hedl_kb **out) {
     }
     kb->n_num = d->n_num_roles;
     for (uint32_t q = 0; q < d->n_num_roles; ++q) kb->num_host.push_back(DevNum{nullptr, nullptr, d->num_roles[q].n_vals, 0});
+    take_str_sizes(kb, d, false);
     *out = kb;
     return HEDL_OK;
 }
@@ -216,6 +285,10 @@ void hedl_kb_free(hedl_kb *kb) {
     if (kb->capture_stream) cudaStreamDestroy((cudaStream_t)kb->capture_stream);
     if (kb->csr_dev) cudaFree(kb->csr_dev);
     if (kb->num_dev) cudaFree(kb->num_dev);
+    if (kb->str_dev) cudaFree(kb->str_dev);
+    if (kb->pat_off_dev) cudaFree(kb->pat_off_dev);
+    if (kb->pat_chars_dev) cudaFree(kb->pat_chars_dev);
+    if (kb->contain_dev) cudaFree(kb->contain_dev);
     if (kb->status_dev) cudaFree(kb->status_dev);
     delete kb;
 }

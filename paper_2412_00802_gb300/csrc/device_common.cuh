@@ -383,50 +383,67 @@ __device__ __forceinline__ bool data_cmp(uint32_t cmp, float x, float t) {
     return cmp == HEDL_OP_DGE ? (x >= t) : cmp == HEDL_OP_DLE ? (x <= t) : (x == t);
 }
 
-// Existential restriction on a numeric concrete role (Algorithms 9-10 with
-// several values per subject, Section III-B): individual i belongs iff one of
-// vals[rp[i] .. rp[i+1]) passes the compare.  The 32 individuals of a word own
-// one contiguous run of values; the warp reads it NUM_STEP values a step
-// (four coalesced loads), ballots the compares, and each lane tests the bits
-// that fall in its own sub-range.  The words are software-pipelined: while
-// word w is tested, the row pointers of word w+2 and the first step of word
-// w+1 are in flight, so a word whose run fits one step costs one memory
-// latency, overlapped.  A longer run continues step by step and the warp
-// leaves it once every individual whose values reach past the step has found
-// one (the paper's skip over a subject already satisfied), so a heavy subject
-// costs 1/32 of a lane walk.
-constexpr uint32_t NUM_LOADS = 4;
-constexpr uint32_t NUM_STEP = 32u * NUM_LOADS;
+// The test a concrete-role restriction applies to each asserted value (the
+// 32-bit word of a float value or of a string id): a float compare (numeric
+// roles, Algorithms 9-10), id equality (string EQUAL, Algorithms 11-12) or a
+// bit of the pattern's containment row (string CONTAIN, Algorithms 13-14).
+struct ValueTest {
+    enum : uint32_t { FLOAT_CMP = 0, ID_EQ = 1, ID_BIT = 2 };
+    uint32_t mode;
+    uint32_t cmp;           // FLOAT_CMP: HEDL_OP_DGE / DLE / DEQ
+    uint32_t arg;           // FLOAT_CMP: the threshold's bits; ID_EQ: the string id
+    const uint32_t *bits;   // ID_BIT: the containment row
+    __device__ __forceinline__ bool operator()(uint32_t x) const {
+        if (mode == FLOAT_CMP) return data_cmp(cmp, __uint_as_float(x), __uint_as_float(arg));
+        if (mode == ID_EQ) return x == arg;
+        return (__ldg(bits + (x >> 5)) >> (x & 31u)) & 1u;
+    }
+};
+
+// Existential restriction on a concrete role with several values per
+// subject (Section III-B): individual i belongs iff one of its values
+// vals[rp[i] .. rp[i+1]) passes the test.  The 32 individuals of a word own
+// one contiguous run of values; the warp reads it EX_STEP values a step (four
+// coalesced loads), ballots the tests, and each lane tests the bits that fall
+// in its own sub-range.  The words are software-pipelined: while word w is
+// tested, the row pointers of word w+2 and the first step of word w+1 are in
+// flight, so a word whose run fits one step costs one memory latency,
+// overlapped.  A longer run continues step by step and the warp leaves it
+// once every individual whose values reach past the step has found one (the
+// paper's skip over a subject already satisfied), so a heavy subject costs
+// 1/32 of a lane walk.
+constexpr uint32_t EX_LOADS = 4;
+constexpr uint32_t EX_STEP = 32u * EX_LOADS;
 
 // this lane's row of word w (empty past the warp's words or past n)
-__device__ __forceinline__ void num_row(const DevNum &g, uint32_t w, uint32_t n_words, uint32_t n, uint32_t lane,
-                                        uint32_t &lo, uint32_t &hi) {
+__device__ __forceinline__ void ex_row(const uint32_t *rp, uint32_t w, uint32_t n_words, uint32_t n, uint32_t lane,
+                                       uint32_t &lo, uint32_t &hi) {
     lo = hi = 0;
     const uint32_t i = w * 32u + lane;
     if (w < n_words && i < n) {
-        lo = ld_stream(g.rp + i);
-        hi = ld_stream(g.rp + i + 1);
+        lo = ld_stream(rp + i);
+        hi = ld_stream(rp + i + 1);
     }
 }
 
-// the values [c, c + NUM_STEP) of a run ending at end, one per lane and load
-__device__ __forceinline__ void num_fetch(const DevNum &g, uint32_t c, uint32_t end, uint32_t lane,
-                                          float (&x)[NUM_LOADS]) {
+// the values [c, c + EX_STEP) of a run ending at end, one per lane and load
+__device__ __forceinline__ void ex_fetch(const uint32_t *vals, uint32_t c, uint32_t end, uint32_t lane,
+                                         uint32_t (&x)[EX_LOADS]) {
 #pragma unroll
-    for (uint32_t u = 0; u < NUM_LOADS; ++u) {
+    for (uint32_t u = 0; u < EX_LOADS; ++u) {
         const uint32_t k = c + 32u * u + lane;
-        x[u] = k < end ? __ldg(g.vals + k) : 0.f;
+        x[u] = k < end ? __ldg(vals + k) : 0u;
     }
 }
 
-// does a value in [c, c + NUM_STEP) of this lane's row [lo, hi) pass?
-__device__ __forceinline__ bool num_test(const float (&x)[NUM_LOADS], uint32_t c, uint32_t end, uint32_t lo,
-                                         uint32_t hi, uint32_t lane, uint32_t cmp, float t) {
+// does a value in [c, c + EX_STEP) of this lane's row [lo, hi) pass?
+__device__ __forceinline__ bool ex_test(const uint32_t (&x)[EX_LOADS], uint32_t c, uint32_t end, uint32_t lo,
+                                        uint32_t hi, uint32_t lane, const ValueTest &test) {
     bool hit = false;
 #pragma unroll
-    for (uint32_t u = 0; u < NUM_LOADS; ++u) {
+    for (uint32_t u = 0; u < EX_LOADS; ++u) {
         const uint32_t cu = c + 32u * u;
-        const uint32_t m = __ballot_sync(FULL, cu + lane < end && data_cmp(cmp, x[u], t));
+        const uint32_t m = __ballot_sync(FULL, cu + lane < end && test(x[u]));
         const uint32_t a = lo > cu ? min(lo - cu, 32u) : 0u, b = hi > cu ? min(hi - cu, 32u) : 0u;
         hit = hit || (m & range_mask(a, b)) != 0u;
     }
@@ -434,44 +451,54 @@ __device__ __forceinline__ bool num_test(const float (&x)[NUM_LOADS], uint32_t c
 }
 
 template <int WPL>
-__device__ __forceinline__ void num_words(const DevNum g, uint32_t cmp, float t, uint32_t n, uint32_t n_words,
-                                          uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
+__device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const ValueTest test,
+                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
+                                            uint32_t (&v)[WPL]) {
     // word w: row [lo, hi), run [base, end), first step x; word w+1: row [lo1, hi1)
     uint32_t lo, hi, lo1, hi1;
-    num_row(g, wb, n_words, n, lane, lo, hi);
+    ex_row(rp, wb, n_words, n, lane, lo, hi);
     uint32_t base = __shfl_sync(FULL, lo, 0), end = __reduce_max_sync(FULL, hi);
-    float x[NUM_LOADS];
-    num_fetch(g, base, end, lane, x);
-    num_row(g, wb + 1, n_words, n, lane, lo1, hi1);
+    uint32_t x[EX_LOADS];
+    ex_fetch(vals, base, end, lane, x);
+    ex_row(rp, wb + 1, n_words, n, lane, lo1, hi1);
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
         for (int s = 0; s < WPL; ++s) {
             const uint32_t w = wb + (uint32_t)j * WPL + s;   // the words go in order: w + 1 is the next
             uint32_t word = 0;
-            if (w < n_words) {   // warp-uniform
+            if (w < n_words) {   // warp-uniform; then lane 0's individual 32w < n exists
                 // start word w+1's first step and word w+2's row pointers
                 const uint32_t base1 = __shfl_sync(FULL, lo1, 0), end1 = __reduce_max_sync(FULL, hi1);
-                float x1[NUM_LOADS];
-                num_fetch(g, base1, end1, lane, x1);
+                uint32_t x1[EX_LOADS];
+                ex_fetch(vals, base1, end1, lane, x1);
                 uint32_t lo2, hi2;
-                num_row(g, w + 2, n_words, n, lane, lo2, hi2);
+                ex_row(rp, w + 2, n_words, n, lane, lo2, hi2);
                 // test word w
-                bool hit = num_test(x, base, end, lo, hi, lane, cmp, t);
-                for (uint32_t c = base + NUM_STEP; c < end; c += NUM_STEP) {
+                bool hit = ex_test(x, base, end, lo, hi, lane, test);
+                for (uint32_t c = base + EX_STEP; c < end; c += EX_STEP) {
                     if (__all_sync(FULL, hit || hi <= c)) break;
-                    float y[NUM_LOADS];
-                    num_fetch(g, c, end, lane, y);
-                    hit = num_test(y, c, end, lo, hi, lane, cmp, t) || hit;
+                    uint32_t y[EX_LOADS];
+                    ex_fetch(vals, c, end, lane, y);
+                    hit = ex_test(y, c, end, lo, hi, lane, test) || hit;
                 }
                 word = __ballot_sync(FULL, hit);
                 lo = lo1, hi = hi1, base = base1, end = end1;
                 lo1 = lo2, hi1 = hi2;
 #pragma unroll
-                for (uint32_t u = 0; u < NUM_LOADS; ++u) x[u] = x1[u];
+                for (uint32_t u = 0; u < EX_LOADS; ++u) x[u] = x1[u];
             }
             if (lane == (uint32_t)j) v[s] = word;
         }
     }
+}
+
+// The test of a D_DATA instruction on a numeric or string role (op word bit 8
+// or 9; aux = the op; b = threshold bits, string id or pattern id).
+__host__ __device__ __forceinline__ ValueTest value_test(const KBView &kb, uint32_t op_word, uint32_t b) {
+    const uint32_t op = (op_word >> 16) & 0xFFu;
+    if (op == HEDL_OP_SEQ) return ValueTest{ValueTest::ID_EQ, 0u, b, nullptr};
+    if (op == HEDL_OP_SCONTAINS) return ValueTest{ValueTest::ID_BIT, 0u, 0u, kb.contain + (uint64_t)b * kb.contain_words};
+    return ValueTest{ValueTest::FLOAT_CMP, op, b, nullptr};
 }
 
 __device__ __forceinline__ uint64_t global_ns() {

@@ -109,10 +109,12 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 for (int s = 0; s < WPL; ++s) top[s] = 0u;
                 break;
             case D_DATA:
-                if ((d.op >> 8) & 1u)
-                    num_words<WPL>(kb.num[d.a], (d.op >> 16) & 0xFFu, __uint_as_float(d.b), kb.n, lim_w, wb, lane,
-                                   top);
-                else
+                if ((d.op >> 8) & 3u) {   // a numeric (bit 8) or string (bit 9) concrete role
+                    const bool str = (d.op >> 9) & 1u;
+                    const uint32_t *rp = str ? kb.str[d.a].rp : kb.num[d.a].rp;
+                    const uint32_t *vals = str ? kb.str[d.a].ids : reinterpret_cast<const uint32_t *>(kb.num[d.a].vals);
+                    exist_words<WPL>(rp, vals, value_test(kb, d.op, d.b), kb.n, lim_w, wb, lane, top);
+                } else
                     data_words<WPL>(kb.props + (uint64_t)d.a * kb.prop_stride, (d.op >> 16) & 0xFFu,
                                     __uint_as_float(d.b), kb.n, lim_w, wb, lane, top);
                 break;

@@ -27,11 +27,22 @@ struct DevNum {
     uint32_t pad;
 };
 
+// A string concrete role: CSR of interned string ids over subjects.
+struct DevStr {
+    const uint32_t *rp;    // [n+1]
+    const uint32_t *ids;   // [n_vals], each < n_strings
+    uint32_t n_vals;
+    uint32_t pad;
+};
+
 // Passed by value to every kernel.
 struct KBView {
     const uint32_t *concepts;    // [C][wp]
     const DevCSR *csr;           // device [2*R]: role r forward at 2r, inverse at 2r+1
     const DevNum *num;           // device [Q]: the numeric concrete roles
+    const DevStr *str;           // device [S]: the string concrete roles
+    const uint32_t *contain;     // [n_patterns][contain_words]: bit i of row k = string i contains pattern k
+    uint64_t contain_words;
     const float *props;          // [P][prop_stride]
     uint64_t prop_stride;
     const uint32_t *pos;         // [wp] or null
@@ -50,8 +61,9 @@ enum : uint32_t { ST_TIMEOUT = 1u, ST_DEVICE_CHECK = 2u };
 enum : uint32_t {
     D_ATOM = 1, D_TOP = 2, D_BOT = 3, D_NOT = 4, D_AND = 5, D_OR = 6,
     D_ROLE = 7,      // aux = kind (HEDL_OP_EXISTS..EXACTLY), a = role, flags bit0 = inverse, b = n
-    D_DATA = 12,     // aux = cmp (HEDL_OP_DGE/DLE/DEQ), b = float bits; bit 8 of the op
-                     // word clear: a = one-value property, set: a = numeric role
+    D_DATA = 12,     // aux = the op (HEDL_OP_DGE/DLE/DEQ/SEQ/SCONTAINS); bits 8/9 of the op
+                     // word clear: a = one-value property, b = float bits; bit 8: a = numeric
+                     // role, b = float bits; bit 9: a = string role, b = string / pattern id
     D_SLOT = 32      // a materialized bitset: ref = slot index
 };
 constexpr uint32_t REF_SLOT = 0x80000000u;   // filler ref: slot (low bits) vs concept id
@@ -166,6 +178,15 @@ struct hedl_kb {
     hedl::DevCSR *csr_dev = nullptr;
     std::vector<hedl::DevNum> num_host;     // [Q] numeric concrete roles
     hedl::DevNum *num_dev = nullptr;
+    uint32_t n_str = 0, n_strings = 0, n_str_chars = 0, n_patterns = 0;
+    std::vector<hedl::DevStr> str_host;     // [S] string concrete roles
+    hedl::DevStr *str_dev = nullptr;
+    const uint32_t *str_off = nullptr;      // borrowed string table
+    const uint8_t *str_chars = nullptr;
+    uint32_t *pat_off_dev = nullptr;        // owned: pattern offsets [P+1]
+    uint8_t *pat_chars_dev = nullptr;       // owned: pattern bytes
+    uint32_t *contain_dev = nullptr;        // owned: [P][contain_words]
+    uint64_t contain_words = 0;
     uint32_t *status_dev = nullptr;         // [4]: status, |P|, |N|, scratch
     const uint32_t *pos = nullptr, *neg = nullptr;
     uint32_t n_pos = 0, n_neg = 0;
@@ -264,6 +285,7 @@ int launch_plain(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_
                  void *stream);
 int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm);
 int kb_validate_device(const hedl_kb *kb, void *stream, std::string *why);
+int contain_bitmap_device(const hedl_kb *kb, void *stream);
 int examples_count_device(const hedl_kb *kb, void *stream, uint32_t *np, uint32_t *nn);
 size_t exec_smem_bytes(const Tuning &t);
 

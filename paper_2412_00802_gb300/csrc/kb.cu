@@ -1,6 +1,7 @@
 // Device-side checks run once when a knowledge base is registered (concept
-// tails, role CSRs and their transposes, numeric-role row pointers), and the
-// example-set popcounts.  Each check ORs a bit into a flag word; nothing traps.
+// tails, role CSRs and their transposes, numeric- and string-role row
+// pointers, string ids, the string table's offsets), the pattern-containment
+// bitmap of the string table, and the example-set popcounts.  Each check ORs a bit into a flag word; nothing traps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +23,9 @@ enum : uint32_t {
     F_EDGE_COUNT = 1u << 6,
     F_EXAMPLE_TAIL = 1u << 7,
     F_NUM_RP = 1u << 8,
+    F_STR_RP = 1u << 9,
+    F_STR_ID = 1u << 10,
+    F_STR_TABLE = 1u << 11,
 };
 
 // Bits of individuals >= n and the padding words must be zero.
@@ -58,14 +62,45 @@ __global__ void csr_kernel(DevCSR g, uint32_t n, uint32_t *flag) {
     }
 }
 
-// A numeric role's row_ptr: starts at 0, ends at n_vals, never decreases
-// (the values themselves may be anything).
-__global__ void num_rp_kernel(DevNum g, uint32_t n, uint32_t *flag) {
+// Offsets over n rows into m entries (a numeric or string role's row_ptr, the
+// string table's offsets): start at 0, end at m, never decrease.
+__global__ void offsets_kernel(const uint32_t *rp, uint32_t m, uint32_t n, uint32_t *flag, uint32_t bit) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (g.rp[0] != 0 || g.rp[n] != g.n_vals) atomicOr(flag, F_NUM_RP);
+        if (rp[0] != 0 || rp[n] != m) atomicOr(flag, bit);
     }
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        if (g.rp[i + 1] < g.rp[i]) atomicOr(flag, F_NUM_RP);
+        if (rp[i + 1] < rp[i]) atomicOr(flag, bit);
+}
+
+// Every string id of a string role names a table string.
+__global__ void str_ids_kernel(const uint32_t *ids, uint32_t m, uint32_t n_strings, uint32_t *flag) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+        if (ids[k] >= n_strings) atomicOr(flag, F_STR_ID);
+}
+
+// Bit i of row k: table string i contains pattern k (strContain of
+// Algorithms 13-14, a naive scan; the empty pattern is in every string).  One
+// warp per (pattern, 32 strings), a lane per string.
+__global__ void contain_kernel(const uint32_t *off, const uint8_t *chars, uint32_t n_strings, const uint32_t *poff,
+                               const uint8_t *pchars, uint32_t n_patterns, uint64_t words, uint32_t *out) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < (uint64_t)n_patterns * words;
+         t += warps) {
+        const uint32_t k = (uint32_t)(t / words);
+        const uint64_t w = t % words, i = w * 32u + lane;
+        bool hit = false;
+        if (i < n_strings) {
+            const uint32_t s0 = off[i], ls = off[i + 1] - s0, p0 = poff[k], lp = poff[k + 1] - p0;
+            for (uint32_t a = 0; a + lp <= ls && !hit; ++a) {
+                uint32_t j = 0;
+                while (j < lp && chars[s0 + a + j] == pchars[p0 + j]) ++j;
+                hit = j == lp;
+            }
+        }
+        const uint32_t word = __ballot_sync(FULL, hit);
+        if (lane == 0) out[(uint64_t)k * words + w] = word;
+    }
 }
 
 // Every forward edge (a, b) appears as a in the inverse row of b.  With equal
@@ -134,6 +169,9 @@ std::string describe(uint32_t f) {
     add(F_EDGE_COUNT, "an inverse CSR has a different edge count than its forward CSR");
     add(F_EXAMPLE_TAIL, "an example bitset has bits set beyond n or in its padding words");
     add(F_NUM_RP, "a numeric role's row_ptr does not start at 0, decreases, or does not end at n_vals");
+    add(F_STR_RP, "a string role's row_ptr does not start at 0, decreases, or does not end at n_vals");
+    add(F_STR_ID, "a string role holds an id >= n_strings");
+    add(F_STR_TABLE, "str_off does not start at 0, decreases, or does not end at n_str_chars");
     return s;
 }
 
@@ -160,7 +198,17 @@ int kb_validate_device(const hedl_kb *kb, void *stream, std::string *why) {
         transpose_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(f, t, kb->n, flag);
     }
     for (uint32_t q = 0; q < kb->n_num; ++q)
-        num_rp_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(kb->num_host[q], kb->n, flag);
+        offsets_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(kb->num_host[q].rp, kb->num_host[q].n_vals,
+                                                                     kb->n, flag, F_NUM_RP);
+    if (kb->n_strings)
+        offsets_kernel<<<blocks_for(kb->n_strings, kb->n_sms), 256, 0, s>>>(kb->str_off, kb->n_str_chars,
+                                                                             kb->n_strings, flag, F_STR_TABLE);
+    for (uint32_t q = 0; q < kb->n_str; ++q) {
+        const DevStr &g = kb->str_host[q];
+        offsets_kernel<<<blocks_for(kb->n, kb->n_sms), 256, 0, s>>>(g.rp, g.n_vals, kb->n, flag, F_STR_RP);
+        if (g.n_vals)
+            str_ids_kernel<<<blocks_for(g.n_vals, kb->n_sms), 256, 0, s>>>(g.ids, g.n_vals, kb->n_strings, flag);
+    }
     e = cudaGetLastError();
     if (e) return e;
     uint32_t dev_flag = 0;
@@ -170,6 +218,19 @@ int kb_validate_device(const hedl_kb *kb, void *stream, std::string *why) {
     if (e) return e;
     *why = describe(dev_flag | host_flag);
     return 0;
+}
+
+int contain_bitmap_device(const hedl_kb *kb, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!kb->contain_words || !kb->n_patterns) return 0;
+    const uint64_t warps = (uint64_t)kb->n_patterns * kb->contain_words;
+    contain_kernel<<<blocks_for(warps * 32u, kb->n_sms), 256, 0, s>>>(kb->str_off, kb->str_chars, kb->n_strings,
+                                                                      kb->pat_off_dev, kb->pat_chars_dev,
+                                                                      kb->n_patterns, kb->contain_words,
+                                                                      kb->contain_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    return cudaStreamSynchronize(s);
 }
 
 int examples_count_device(const hedl_kb *kb, void *stream, uint32_t *np, uint32_t *nn) {

@@ -89,7 +89,7 @@ __global__ void encode_kernel(const uint64_t *__restrict__ progs, const uint32_t
             const uint64_t w = progs[o0 + k];
             const uint32_t op = (uint32_t)(w & 0xFF), inv = (uint32_t)((w >> 8) & 1);
             const uint32_t a = (uint32_t)((w >> 16) & 0xFFFF), b = (uint32_t)(w >> 32);
-            if (op < HEDL_OP_ATOM || op > HEDL_OP_DEQ) continue;   // not an op code: ignored
+            if (op < HEDL_OP_ATOM || op > HEDL_OP_DEQ) continue;   // no feature: not an op, or a string restriction
             const uint32_t dk = depth[warp][k];
             const int sign = pol[warp][k] ? -1 : 1;
             atomicAdd(&feat[warp][min(dk, 5u) * 14 + op - 1], 1);

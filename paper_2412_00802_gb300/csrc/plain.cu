@@ -53,13 +53,15 @@ __global__ void role_kernel(DevCSR g, const uint32_t *filler, uint32_t kind, uin
     }
 }
 
-__global__ void num_kernel(DevNum g, uint32_t cmp, float t, uint32_t *out, uint32_t n, uint32_t n_words,
-                           uint32_t wp) {
+// A numeric or string concrete-role restriction (existential over each
+// subject's values).
+__global__ void exist_kernel(const uint32_t *rp, const uint32_t *vals, ValueTest test, uint32_t *out, uint32_t n,
+                             uint32_t n_words, uint32_t wp) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wg * 32u < wp; wg += warps) {
         uint32_t v[1];
-        num_words<1>(g, cmp, t, n, n_words, wg * 32u, lane, v);
+        exist_words<1>(rp, vals, test, n, n_words, wg * 32u, lane, v);
         if (wg * 32u + lane < wp) out[wg * 32u + lane] = v[0];
     }
 }
@@ -162,14 +164,20 @@ int launch_plain(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_
                 bool_kernel<<<g_quad, PT, 0, s>>>(op, x.ptr, y.ptr, out, wp, v.w, v.n);
                 give(x);
                 give(y);
+            } else if (op == HEDL_OP_SEQ || op == HEDL_OP_SCONTAINS) {   // a string concrete role
+                exist_kernel<<<g_warp, PT, 0, s>>>(kb->str_host[a].rp, kb->str_host[a].ids,
+                                                   value_test(v, op << 16, b), out, v.n, v.w, wp);
             } else if (op >= HEDL_OP_DGE) {
                 float t;
                 memcpy(&t, &b, sizeof t);
-                if (a >= kb->n_props)   // a numeric concrete role
-                    num_kernel<<<g_warp, PT, 0, s>>>(kb->num_host[a - kb->n_props], op, t, out, v.n, v.w, wp);
-                else
+                if (a >= kb->n_props) {   // a numeric concrete role
+                    const DevNum &g = kb->num_host[a - kb->n_props];
+                    exist_kernel<<<g_warp, PT, 0, s>>>(g.rp, reinterpret_cast<const uint32_t *>(g.vals),
+                                                       value_test(v, op << 16, b), out, v.n, v.w, wp);
+                } else {
                     data_kernel<<<g_warp, PT, 0, s>>>(kb->props + (uint64_t)a * kb->prop_stride, op, t, out, v.n,
                                                       v.w, wp);
+                }
             } else {  // role restriction
                 Val x = st.back();
                 st.pop_back();

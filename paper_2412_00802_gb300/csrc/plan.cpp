@@ -60,15 +60,21 @@ struct KeyHash {
 
 inline bool is_role(uint32_t op) { return op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY; }
 inline bool is_data(uint32_t op) { return op >= HEDL_OP_DGE && op <= HEDL_OP_DEQ; }
+inline bool is_str(uint32_t op) { return op == HEDL_OP_SEQ || op == HEDL_OP_SCONTAINS; }
 // Algorithmic bytes of a data restriction on property id a: a one-value
 // column (4N), or a numeric role's row pointers and values (4(N+1) + 4M).
 inline uint64_t data_bytes(const hedl_kb *kb, uint32_t a, uint64_t N) {
     if (a < kb->n_props) return 4 * N;
     return 4 * (N + 1) + 4ull * kb->num_host[a - kb->n_props].n_vals;
 }
+// ... and of a string restriction: the role's row pointers and ids, plus
+// SCONTAINS's row of the containment bitmap.
+inline uint64_t str_bytes(const hedl_kb *kb, uint32_t op, uint32_t a, uint64_t N) {
+    return 4 * (N + 1) + 4ull * kb->str_host[a].n_vals + (op == HEDL_OP_SCONTAINS ? 4 * kb->contain_words : 0);
+}
 
 inline int arity(uint32_t op) {
-    if (op == HEDL_OP_ATOM || op == HEDL_OP_TOP || op == HEDL_OP_BOT || is_data(op)) return 0;
+    if (op == HEDL_OP_ATOM || op == HEDL_OP_TOP || op == HEDL_OP_BOT || is_data(op) || is_str(op)) return 0;
     if (op == HEDL_OP_NOT || is_role(op)) return 1;
     if (op == HEDL_OP_AND || op == HEDL_OP_OR) return 2;
     return -1;
@@ -76,8 +82,8 @@ inline int arity(uint32_t op) {
 
 const char *op_name(uint32_t op) {
     static const char *names[] = {"?", "ATOM", "TOP", "BOT", "NOT", "AND", "OR", "EXISTS", "FORALL",
-                                  "ATLEAST", "ATMOST", "EXACTLY", "DGE", "DLE", "DEQ"};
-    return op < 15 ? names[op] : "?";
+                                  "ATLEAST", "ATMOST", "EXACTLY", "DGE", "DLE", "DEQ", "SEQ", "SCONTAINS"};
+    return op < 17 ? names[op] : "?";
 }
 
 }  // namespace
@@ -100,8 +106,14 @@ int validate_program(const hedl_kb *kb, const uint64_t *prog, uint32_t len, std:
             return HEDL_ERR_BAD_PROGRAM;
         }
         if ((op == HEDL_OP_ATOM && a >= kb->n_concepts) || (is_role(op) && a >= kb->n_roles) ||
-            (is_data(op) && a >= kb->n_props + kb->n_num)) {
+            (is_data(op) && a >= kb->n_props + kb->n_num) || (is_str(op) && a >= kb->n_str)) {
             snprintf(buf, sizeof buf, "instruction %u: %s names id %u, out of range", k, op_name(op), a);
+            *why = buf;
+            return HEDL_ERR_BAD_PROGRAM;
+        }
+        if (op == HEDL_OP_SCONTAINS && (uint32_t)(w >> 32) >= kb->n_patterns) {
+            snprintf(buf, sizeof buf, "instruction %u: SCONTAINS names pattern %u, out of range", k,
+                     (uint32_t)(w >> 32));
             *why = buf;
             return HEDL_ERR_BAD_PROGRAM;
         }
@@ -184,6 +196,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 maxd = std::max<uint32_t>(maxd, (uint32_t)d);
                 if (op == HEDL_OP_ATOM) mb += B, p->info.n_atom_loads++;
                 else if (is_data(op)) mb += data_bytes(kb, a, N), p->info.n_data_ops++;
+                else if (is_str(op)) mb += str_bytes(kb, op, a, N), p->info.n_data_ops++;
                 else if (is_role(op)) mb += 4 * (N + 1) + 4ull * kb->role_edges[a] + 2 * B, p->info.n_role_ops++;
             }
             mb += 2 * B + 16;  // scoring
@@ -208,8 +221,10 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     auto make = [&](PNode n) -> int32_t {
         // canonical form: ignored fields zeroed, commutative operands ordered
         if (!is_role(n.op)) n.inv = 0;
-        if (!(n.op == HEDL_OP_ATOM || is_role(n.op) || is_data(n.op))) n.a = 0;
-        if (!(n.op == HEDL_OP_ATLEAST || n.op == HEDL_OP_ATMOST || n.op == HEDL_OP_EXACTLY || is_data(n.op))) n.b = 0;
+        if (!(n.op == HEDL_OP_ATOM || is_role(n.op) || is_data(n.op) || is_str(n.op))) n.a = 0;
+        if (!(n.op == HEDL_OP_ATLEAST || n.op == HEDL_OP_ATMOST || n.op == HEDL_OP_EXACTLY || is_data(n.op) ||
+              is_str(n.op)))
+            n.b = 0;
         if (cse) {
             if ((n.op == HEDL_OP_AND || n.op == HEDL_OP_OR) && n.k0 > n.k1) std::swap(n.k0, n.k1);
             if (n.op == HEDL_OP_NOT && nodes[n.k0].op == HEDL_OP_NOT) return nodes[n.k0].k0;
@@ -410,6 +425,12 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                     d.a = num ? n.a - kb->n_props : n.a;
                     d.b = n.b;
                     model += data_bytes(kb, n.a, N);
+                    p->info.n_data_ops++;
+                } else if (is_str(n.op)) {   // a string concrete role
+                    d.op = D_DATA | (n.op << 16) | (1u << 9);
+                    d.a = n.a;
+                    d.b = n.b;
+                    model += str_bytes(kb, n.op, n.a, N);
                     p->info.n_data_ops++;
                 } else {  // role restriction
                     int32_t c = n.k0;

@@ -15,7 +15,7 @@ namespace {
 int arity(uint32_t op) {
     if (op == HEDL_OP_NOT || (op >= HEDL_OP_EXISTS && op <= HEDL_OP_EXACTLY)) return 1;
     if (op == HEDL_OP_AND || op == HEDL_OP_OR) return 2;
-    if (op >= HEDL_OP_ATOM && op <= HEDL_OP_DEQ) return 0;
+    if (op >= HEDL_OP_ATOM && op <= HEDL_OP_SCONTAINS) return 0;
     return -1;
 }
 

@@ -11,7 +11,10 @@ and draws n uniformly from 1..4; leaves are an atomic concept with probability
 threshold is a present value of the property at a random individual.  On a KB
 with numeric concrete roles the restricted property is drawn over the
 one-value properties and the numeric roles together; a numeric role takes >=,
-<= or == equally likely, with a threshold drawn from its asserted values.
+<= or == equally likely, with a threshold drawn from its asserted values.  On
+a KB with string concrete roles, half of the data leaves (all, without other
+data) restrict a string role: equality with a uniform table string or
+containment of a uniform pattern, equally likely.
 
 Shared sub-concepts: a pool of 256 seeded subtrees of depth 2..4; whenever
 the generator is about to build a subtree of depth >= 2 whose exact
@@ -26,7 +29,7 @@ import numpy as np
 
 from . import rng
 from .kb import KB
-from .programs import (AND, ATLEAST, ATMOST, ATOM, DEQ, DGE, DLE, EXISTS, FORALL, NOT, OR,
+from .programs import (AND, ATLEAST, ATMOST, ATOM, DEQ, DGE, DLE, EXISTS, FORALL, NOT, OR, SCONTAINS, SEQ,
                        Node, f32_bits, pack_batch)
 
 S_HYP = 7 << 16
@@ -50,10 +53,13 @@ class TreeGen:
         self.props = kb.prop_vals
         self.n_num = kb.n_num_roles
         self.num_vals = kb.num_vals
+        self.n_str = kb.n_str_roles
+        self.n_strings = len(kb.strings)
+        self.n_patterns = kb.n_patterns
         self.seed = seed
         self.unary = tuple(unary)
         self.binary = tuple(binary)
-        self.p_atom = p_atom if self.n_props + self.n_num > 0 else 1.0
+        self.p_atom = p_atom if self.n_props + self.n_num + self.n_str > 0 else 1.0
         self.share = share
         self.pool: Dict[Tuple[int, int], List[Node]] = {}
         if share > 0:
@@ -78,6 +84,11 @@ class TreeGen:
 
     def leaf(self, r: rng.Rng) -> Node:
         if self.n_concepts == 0 or r.random() >= self.p_atom:
+            if self.n_str and (self.n_props + self.n_num == 0 or r.random() < 0.5):
+                q = r.randint(0, self.n_str - 1)
+                if self.n_patterns and r.random() < 0.5:
+                    return Node(SCONTAINS, q, r.randint(0, self.n_patterns - 1))
+                return Node(SEQ, q, r.randint(0, max(self.n_strings - 1, 0)))
             if self.n_num:
                 p = r.randint(0, self.n_props + self.n_num - 1)
                 if p >= self.n_props:

@@ -146,6 +146,13 @@ CONFIGS["surrogate"] = replace(CONFIGS["large"], name="surrogate", seed=4, plant
 CONFIGS["numeric"] = KBConfig("numeric", 6, 10_000_000, 8, 0.01, 0.50, False, 0, ("poisson", 3.0), 0,
                               ("uniform", 0.0, 1000.0), 0.0, 10_000, 10_000, n_num_roles=8,
                               num_degree=("poisson", 4.0))
+# string concrete roles: 10^7 individuals, 8 roles with Poisson(2) values each
+# (2 * 10^7 ids, 120 MB of row pointers and ids per role) into a table of
+# 100,000 distinct strings of 3-12 letters over a 6-letter alphabet; 64 patterns
+CONFIGS["strings"] = KBConfig("strings", 7, 10_000_000, 8, 0.01, 0.50, False, 0, ("poisson", 3.0), 0,
+                              ("uniform", 0.0, 1.0), 0.0, 10_000, 10_000, n_str_roles=8,
+                              str_degree=("poisson", 2.0), n_strings=100_000, str_len=(3, 12), alphabet=6,
+                              n_patterns=64)
 
 # Planted structure (workloads that search or learn need a signal): a latent
 # class Z (a uniform 20 % of the individuals) supplies the positives, its

@@ -235,3 +235,36 @@ def test_numeric_role_limits():
         H.hedl_kb_plan_only(100, 1, [], 0, num_role_vals=[1 << 31])
     assert e.value.code == -1   # HEDL_ERR_INVALID_ARG
     H.hedl_kb_plan_only(100, 1, [], 65_000, num_role_vals=[1] * 536)
+
+
+def test_string_roles_on_a_planning_handle():
+    """String restrictions name a string role below n_str_roles; SCONTAINS a pattern below
+    n_patterns; SEQ any string id.  Byte model: 4(N+1) + 4M, plus the pattern's bitmap row."""
+    n, M, S = 10_000, [20_000, 7], 1000
+    hk = H.hedl_kb_plan_only(n, 3, [100], 1, str_role_vals=M, n_strings=S, n_patterns=4)
+    one = lambda op, a, b: np.array([P.insn(op, 0, a, b)], np.uint64)
+    for op, a, b in ((P.SEQ, 0, 5), (P.SEQ, 1, 0xFFFFFFFF), (P.SCONTAINS, 1, 3)):
+        H.hedl_validate(hk, one(op, a, b))
+    for op, a, b in ((P.SEQ, 2, 0), (P.SCONTAINS, 0, 4), (P.SCONTAINS, 2, 0)):
+        with pytest.raises(H.HedlError) as e:
+            H.hedl_validate(hk, one(op, a, b))
+        assert e.value.code == -2, (op, a, b)
+    B = 4 * H.hedl_row_words(n)
+    for flags in (0, H.HEDL_PLAIN):
+        for op, a, want in ((P.SEQ, 0, 4 * (n + 1) + 4 * M[0]), (P.SCONTAINS, 1, 4 * (n + 1) + 4 * M[1] + 4 * 32)):
+            info = H.hedl_plan_info_get(H.hedl_plan_batch(hk, one(op, a, 1), np.array([0, 1], np.uint32), flags))
+            assert info["n_data_ops"] == 1
+            assert info["model_bytes"] == want + 2 * B + 16, (flags, op)
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_kb_plan_only(100, 1, [], 0, str_role_vals=[1] * 65537, n_strings=1)
+    assert e.value.code == -1
+    with pytest.raises(H.HedlError) as e:     # values but no table
+        H.hedl_kb_plan_only(100, 1, [], 0, str_role_vals=[3], n_strings=0)
+    assert e.value.code == -1
+
+
+def test_canonical_form_keeps_string_leaves():
+    progs = [P.compile_text("(or (contains s1 2) (seq s0 7))"), P.compile_text("(or (seq s0 7) (contains s1 2))")]
+    flat, offs = P.pack_batch(progs)
+    got = H.hedl_canonical_batch(flat, offs)
+    assert got[offs[0]:offs[1]].tobytes() == got[offs[1]:offs[2]].tobytes()
