@@ -139,3 +139,31 @@ def test_refine_postfix_matches_the_python_generator():
             got = [flat[offs[i]:offs[i + 1]] for i in range(700)]
             assert all(np.array_equal(a, b) for a, b in zip(want, got)), step
             beam = [P.from_postfix(w) for w in want[::23]]      # a varied beam for the next step
+
+
+def test_concrete_roles():
+    """Numeric and string concrete roles: CSR over individuals with the stated shapes; the string
+    table holds distinct strings (ids are interned); patterns start with the empty string and end
+    with one no table string holds; the generator's leaves restrict both kinds."""
+    base = K.CONFIGS["small"]
+    kb = K.generate(base.scaled(4000, seed=31, n_num_roles=2, num_degree=("poisson", 3.0), n_str_roles=2,
+                                str_degree=("poisson", 2.0), n_strings=300, str_len=(2, 6), alphabet=5,
+                                n_patterns=10))
+    for rp, vals in zip(kb.num_row_ptr, kb.num_vals):
+        assert rp[0] == 0 and rp[-1] == vals.size and np.all(np.diff(rp.astype(np.int64)) >= 0)
+        assert abs(vals.size / kb.n - 3.0) < 0.2 and not np.isnan(vals).any()
+    assert len(set(kb.strings)) == len(kb.strings) == 300
+    assert all(2 <= len(x) <= 6 and set(x) <= set(b"abcde") for x in kb.strings)
+    assert kb.patterns[0] == b"" and len(kb.patterns) == 10
+    assert not any(kb.patterns[-1] in x for x in kb.strings)
+    assert all(any(p in x for x in kb.strings) for p in kb.patterns[1:-1])
+    for rp, ids in zip(kb.str_row_ptr, kb.str_ids):
+        assert rp[-1] == ids.size and int(ids.max()) < len(kb.strings)
+    for nd, want in ((("single", 50), [50]), (("unique",), [1])):
+        k2 = K.generate(base.scaled(300, seed=32, n_num_roles=1, num_degree=nd, n_str_roles=1, str_degree=nd,
+                                    n_strings=20, n_patterns=3))
+        for rp in (k2.num_row_ptr[0], k2.str_row_ptr[0]):
+            deg = np.diff(rp.astype(np.int64))
+            assert sorted(set(deg.tolist()) - {0}) == want
+    leaves = [P.fields(int(w))[0] for p in Hy.small_hyps(kb, 3, 200) for w in p]
+    assert P.SEQ in leaves and P.SCONTAINS in leaves and P.DEQ in leaves
