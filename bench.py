@@ -186,23 +186,30 @@ def make_batch(kb, idx: int, gen=None, count: int = None):
     return hyps.batch_hyps(kb, 1003, idx, count or BATCH, gen=gen)
 
 
-def cpu_baseline(kb, progs, budget_s: float = 12.0):
-    """The oracle (as it stands) on all host cores over a bounded sample of the batch."""
+def cpu_baseline(kb, progs, budget_s: float = 12.0, single_budget_s: float = 4.0):
+    """The oracle (as it stands) on all host cores over a bounded sample of the batch (the paper's
+    multi-threaded CPU evaluator's analog), and on one thread (its single-threaded baseline's)."""
     import oracle
     from synth import programs as P
     okb = oracle.from_synth(kb)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    done, t0 = 0, time.perf_counter()
-    chunk = max(cores, 16)
-    while done < len(progs) and time.perf_counter() - t0 < budget_s:
-        sub = progs[done:done + chunk]
-        flat, offs = P.pack_batch(sub)
-        oracle.eval_batch(okb, flat, offs, threads=cores)
-        done += len(sub)
-    dt = time.perf_counter() - t0
+
+    def run(threads, chunk, budget):
+        done, t0 = 0, time.perf_counter()
+        while done < len(progs) and time.perf_counter() - t0 < budget:
+            sub = progs[done:done + chunk]
+            flat, offs = P.pack_batch(sub)
+            oracle.eval_batch(okb, flat, offs, threads=threads)
+            done += len(sub)
+        return done, time.perf_counter() - t0
+
+    done, dt = run(cores, max(cores, 16), budget_s)
+    done1, dt1 = run(1, 1, single_budget_s)
     return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {done} hypotheses of a 4,096-hypothesis batch of this workload, "
-                      f"hypothesis-parallel on {cores} host threads ({dt:.1f} s)"}
+                      f"hypothesis-parallel on {cores} host threads ({dt:.1f} s)",
+            "single_thread": {"value": done1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {done1} hypotheses of the same batch on one thread ({dt1:.1f} s)"}}
 
 
 def _pack(progs):
