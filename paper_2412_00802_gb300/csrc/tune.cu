@@ -87,6 +87,14 @@ std::string cache_key(const hedl_kb *kb) {
     mix(kb->n_roles);
     mix(kb->n_props);
     for (uint32_t e : kb->role_edges) mix(e);
+    if (kb->n_num || kb->n_str) {   // concrete roles (absent: the key of a KB without them is unchanged)
+        mix(kb->n_num);
+        for (const DevNum &g : kb->num_host) mix(g.n_vals);
+        mix(kb->n_str);
+        for (const DevStr &g : kb->str_host) mix(g.n_vals);
+        mix(kb->n_strings);
+        mix(kb->n_patterns);
+    }
     for (const char *c = prop.name; *c; ++c) mix((uint8_t)*c);
     mix((uint64_t)prop.multiProcessorCount);
     char buf[64];
