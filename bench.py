@@ -290,6 +290,17 @@ def surrogate_round(args, dev):
             "surrogate_round_s": sur_s, "plain_time_to_best_s": plain_s, "mlp_forward": fwd}
 
 
+def _section(fn, *a):
+    """A secondary workload of the JSON line; a Python-level failure in it is reported in its
+    object (with the traceback on stderr) instead of losing the headline line."""
+    try:
+        return fn(*a)
+    except Exception as e:                     # noqa: BLE001 (reported, not hidden)
+        import traceback
+        traceback.print_exc()
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7):
     """One launch of a batch of restrictions, device-resident: median of `reps` CUDA-event timings on
     the launching stream after warm-up (the graph is captured on the second execution)."""
@@ -735,10 +746,10 @@ def run_ours(args, rank, world, local_rank):
         return
     cpu = None if args.no_cpu else cpu_baseline(kb, make_batch(kb, timed_ids[0], gen))
     clocks = clk.summary()
-    surrogate = None if args.no_surrogate else surrogate_round(args, dev)
-    search = None if args.no_search else search_run(args, dev)
-    numeric = None if args.no_numeric else numeric_run(args, dev)
-    strings = None if args.no_strings else string_run(args, dev)
+    surrogate = None if args.no_surrogate else _section(surrogate_round, args, dev)
+    search = None if args.no_search else _section(search_run, args, dev)
+    numeric = None if args.no_numeric else _section(numeric_run, args, dev)
+    strings = None if args.no_strings else _section(string_run, args, dev)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_ids),
         "warmup": len(warm_ids), "ms_per_step": 1000.0 * elapsed / len(timed_ids), "higher_is_better": True,
