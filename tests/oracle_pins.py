@@ -351,6 +351,21 @@ def pin_numeric_roles(L) -> List[str]:
                     for op in (P.DGE, P.DLE, P.DEQ):
                         if not np.array_equal(ev(okb, op, kb.n_props + q, t), ev(dense, op, 0, t)):
                             bad.append(f"unique subject q={q} op={op} t={t}")
+    # an existential restriction ignores how often a value is asserted: the KB with every numeric
+    # assertion doubled (in another order) gives the same sets
+    kb = K.generate(base.scaled(250, seed=114, n_concepts=2, n_roles=1, degree=("poisson", 2.0), n_props=1,
+                                n_pos=10, n_neg=10, n_num_roles=2, num_degree=("poisson", 2.0)))
+    okb = oracle.from_synth(kb)
+    pairs = []
+    for q in range(kb.n_num_roles):
+        _, _, _, subj, vals = _per_subject(kb, q)
+        pairs.append((np.concatenate([subj[::-1], subj]), np.concatenate([vals[::-1], vals])))
+    dup = oracle.OracleKB.from_parts(kb.n, okb.member, [], okb.prop, okb.pos, okb.neg, pairs)
+    for q in range(kb.n_num_roles):
+        for t in (float(np.median(kb.num_vals[q])), 0.0):
+            for op in (P.DGE, P.DLE, P.DEQ):
+                if not np.array_equal(ev(okb, op, kb.n_props + q, t), ev(dup, op, kb.n_props + q, t)):
+                    bad.append(f"numeric duplicates q={q} op={op} t={t}")
     # hand-worked: individual 0 holds {1.5, NaN}, 2 holds {-0.0}, 3 holds {NaN},
     # 4 holds {7, 2, 9}, 5 holds {+0.0}; 1 holds nothing (a missing value)
     nan = float("nan")
