@@ -114,6 +114,13 @@ def test_plan_batch_rejects_and_names_the_program(small):
     with pytest.raises(H.HedlError) as e:
         H.hedl_plan_batch(hk, flat, offs)
     assert "program 7" in str(e.value)
+    # a string restriction naming a pattern the handle does not hold
+    sk = H.hedl_kb_plan_only(small.n, small.n_concepts, [small.n_edges(r) for r in range(small.n_roles)],
+                             small.n_props, str_role_vals=[10], n_strings=5, n_patterns=2)
+    progs = [P.compile_text("(contains s0 1)"), P.compile_text("(and A0 (contains s0 2))")]
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_plan_batch(sk, *P.pack_batch(progs))
+    assert "program 1" in str(e.value) and "pattern 2" in str(e.value)
 
 
 def test_plan_sharing_and_levels(small):

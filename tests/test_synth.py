@@ -95,8 +95,9 @@ def test_hypothesis_shapes(small):
 
 def test_text_roundtrip():
     for s in ["(and A1 (not (some r2- (min 3 r0 (ge p1 2.5)))))", "(or TOP BOT)", "(exactly 2 r1 (le p0 -0.0))",
-              "(all r3 (eq p2 1e+30))"]:
+              "(all r3 (eq p2 1e+30))", "(and (seq s0 17) (not (contains s3 0)))", "(some r1 (seq s2 4294967295))"]:
         assert P.to_text(P.parse(s)) == s
+    assert P.fields(P.compile_text("(contains s5 9)")[-1]) == (P.SCONTAINS, 0, 5, 9)
     assert P.to_text(P.parse("(some r2-- A0)")) == "(some r2 A0)"
     assert P.to_text(P.parse("(some r2--- A0)")) == "(some r2- A0)"
     prog = P.compile_text("(min 3 r7- A9)")
