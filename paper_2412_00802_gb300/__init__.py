@@ -9,9 +9,10 @@ and importing a function that needs the library fails loudly if it has not
 been built (``paper_2412_00802_gb300.build.build()``).
 
 ``DeviceKB`` is a convenience owner: it copies host (numpy) arrays of a
-knowledge base into torch device tensors, registers them and keeps them
-alive, and offers ``score`` / ``eval`` that allocate outputs and workspaces
-with torch.
+knowledge base into torch device tensors (concept bitsets, role CSRs, property
+columns, numeric and string concrete roles, the string table; the patterns
+go to the library as host bytes), registers them and keeps them alive, and
+offers ``score`` / ``eval`` that allocate outputs and workspaces with torch.
 """
 from __future__ import annotations
 
