@@ -275,3 +275,20 @@ def test_canonical_form_keeps_string_leaves():
     flat, offs = P.pack_batch(progs)
     got = H.hedl_canonical_batch(flat, offs)
     assert got[offs[0]:offs[1]].tobytes() == got[offs[1]:offs[2]].tobytes()
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hedl.h compiles as C99 with every warning on, and a C program links against the
+    library through it (no torch or C++ types in the boundary)."""
+    src = tmp_path / "use.c"
+    src.write_text('#include "hedl.h"\n#include <stdio.h>\n'
+                   "int main(void) { hedl_kb_desc d = {0}; hedl_kb *kb = 0; d.n_indiv = 1000;\n"
+                   "  int rc = hedl_kb_plan_only(&d, &kb); printf(\"%d %u\\n\", rc, hedl_row_words(1000));\n"
+                   "  hedl_kb_free(kb); return rc; }\n")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(H.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lhedl",
+                           f"-Wl,-rpath,{libdir}"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.split() == ["0", "32"], out
