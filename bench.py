@@ -28,6 +28,7 @@ import subprocess
 import sys
 import threading
 import time
+from dataclasses import replace as dc_replace
 
 import numpy as np
 
@@ -301,6 +302,23 @@ def _section(fn, *a):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
+def _oracle_rate(kb, progs, budget_s: float = 6.0):
+    """The oracle (as it stands) on the same restrictions, hypothesis-parallel on the host cores,
+    for about budget_s seconds; the KB's conversion to the oracle's layout is not timed."""
+    import oracle
+    from synth import programs as P
+    okb = oracle.from_synth(kb)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    done, t0 = 0, time.perf_counter()
+    while done < len(progs) and time.perf_counter() - t0 < budget_s:
+        sub = progs[done:done + cores]
+        oracle.eval_batch(okb, *P.pack_batch(sub), threads=cores)
+        done += len(sub)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "restrictions/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {done} of these restrictions on {cores} host threads ({dt:.1f} s)"}
+
+
 def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7):
     """One launch of a batch of restrictions, device-resident: median of `reps` CUDA-event timings on
     the launching stream after warm-up (the graph is captured on the second execution)."""
@@ -357,8 +375,10 @@ def numeric_run(args, dev):
         a, _ = _timed_restrictions(dkb, one, 0, dev, peak)
         b, cb = _timed_restrictions(dkb, three, 0, dev, peak)
         c, cp = _timed_restrictions(dkb, three, H.HEDL_PLAIN, dev, peak)
+    # the oracle on roles 0 and 1 (their 6 restrictions), converted alone to keep the run short
+    cpu = _oracle_rate(dc_replace(kb, num_row_ptr=kb.num_row_ptr[:2], num_vals=kb.num_vals[:2]), three[:6])
     return {"workload": "N=10,000,000 individuals, 8 numeric concrete roles, Poisson(4) values per individual "
-                        "U[0,1000] (~4*10^7 values, 200 MB per role)", "kb_gen_s": gen_s,
+                        "U[0,1000] (~4*10^7 values, 200 MB per role)", "kb_gen_s": gen_s, "cpu_baseline": cpu,
             "values": [int(v.size) for v in kb.num_vals], "kernel": "exec_kernel (exist_words)",
             "peak": peak, "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "one_per_role": a, "three_per_role": b, "plain_three_per_role": c,
@@ -394,9 +414,10 @@ def string_run(args, dev):
         a, _ = _timed_restrictions(dkb, one, 0, dev, peak)
         b, cb = _timed_restrictions(dkb, mixed, 0, dev, peak)
         c, cp = _timed_restrictions(dkb, mixed, H.HEDL_PLAIN, dev, peak)
+    cpu = _oracle_rate(dc_replace(kb, str_row_ptr=kb.str_row_ptr[:2], str_ids=kb.str_ids[:2]), mixed[:6])
     return {"workload": "N=10,000,000 individuals, 8 string concrete roles, Poisson(2) values per individual "
                         "(~2*10^7 ids, 120 MB per role) into 100,000 distinct strings of 3-12 letters; 64 "
-                        "patterns", "kb_gen_s": gen_s, "kb_load_s_with_bitmap": load_s,
+                        "patterns", "kb_gen_s": gen_s, "kb_load_s_with_bitmap": load_s, "cpu_baseline": cpu,
             "values": [int(v.size) for v in kb.str_ids], "kernel": "exec_kernel (exist_words)",
             "peak": peak, "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "equal_one_per_role": a, "equal_and_contain": b, "plain_equal_and_contain": c,
