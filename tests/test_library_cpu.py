@@ -292,3 +292,31 @@ def test_header_is_plain_c(tmp_path):
                            f"-Wl,-rpath,{libdir}"])
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.split() == ["0", "32"], out
+
+
+def test_planner_accepts_every_construct_in_every_mode():
+    """Random batches over every constructor (numeric and string roles included), plus a
+    600-instruction chain and a 64-leaf balanced tree, plan in every mode: the planner keeps each
+    segment within the device stack by materialising, never fails on a valid program."""
+    kb = K.generate(K.CONFIGS["small"].scaled(3000, seed=5, n_num_roles=2, n_str_roles=2, n_strings=50,
+                                              n_patterns=6))
+    hk = H.hedl_kb_plan_only(kb.n, kb.n_concepts, [kb.n_edges(r) for r in range(kb.n_roles)], kb.n_props,
+                             num_role_vals=[v.size for v in kb.num_vals],
+                             str_role_vals=[v.size for v in kb.str_ids], n_strings=len(kb.strings),
+                             n_patterns=kb.n_patterns)
+    r = Rng(77, 1)
+    modes = [0, H.HEDL_NO_CSE, H.HEDL_NO_SLICE, H.HEDL_SLICE_ALL, H.HEDL_PLAIN, H.HEDL_LEVELS,
+             H.HEDL_NO_CSE | H.HEDL_NO_SLICE]
+    for it in range(40):
+        progs = [np.array(pins.random_program(r, kb, r.randint(1, 9)).postfix(), np.uint64)
+                 for _ in range(r.randint(1, 60))]
+        if it % 10 == 0:
+            d = 300
+            progs.append(np.array([P.insn(P.ATOM, 0, 0)] + [x for i in range(d) for x in (
+                P.insn(P.ATOM, 0, i % kb.n_concepts), P.insn(P.AND if i % 2 else P.OR))], np.uint64))
+            progs.append(np.array([P.insn(P.ATOM, 0, i % kb.n_concepts) for i in range(64)] + [P.insn(P.AND)] * 63,
+                                  np.uint64))
+        flat, offs = P.pack_batch(progs)
+        for f in modes:
+            info = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, f))
+            assert info["n_hyps"] == len(progs)
