@@ -274,6 +274,14 @@ int hedl_plan_batch(const hedl_kb *kb, const uint64_t *progs, const uint32_t *of
 int hedl_plan_info_get(const hedl_plan *p, hedl_plan_info *info);
 void hedl_plan_free(hedl_plan *p);
 
+/* Copy a plan's image (the work queue the interpreter reads: header, task and
+ * group tables, dependency lists, segment code, zeroed counters; image_bytes
+ * of hedl_plan_info) into the HOST buffer out of cap bytes, and its size into
+ * *bytes.  For inspection and tests; the layout is the library's own and may
+ * change with it.  A HEDL_PLAIN plan has no image (size 0).  Returns
+ * HEDL_ERR_INVALID_ARG if cap is smaller than the image (with *bytes set). */
+int hedl_plan_image(const hedl_plan *p, void *out, size_t cap, size_t *bytes);
+
 /* Execute a plan.  counts: device uint32[H][4] receiving (TP, FP, FN, TN) per
  * program (Algorithm 15 and its complements), or NULL; out_bits: device
  * uint32[H][hedl_row_words(n)] receiving each instance set, or NULL (not both

@@ -43,7 +43,8 @@ HEDL_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 # exported symbols (one per declaration in include/hedl.h)
 SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free", "hedl_examples_set", "hedl_examples_counts",
-           "hedl_validate", "hedl_plan_batch", "hedl_plan_info_get", "hedl_plan_free", "hedl_plan_execute",
+           "hedl_validate", "hedl_plan_batch", "hedl_plan_info_get", "hedl_plan_image", "hedl_plan_free",
+           "hedl_plan_execute",
            "hedl_plan_replay", "hedl_workspace_size", "hedl_score_batch", "hedl_eval_concept",
            "hedl_eval_concept_noalloc", "hedl_sync_status", "hedl_tuning_get", "hedl_tuning_set",
            "hedl_autotune_workspace_size", "hedl_autotune", "hedl_mlp_param_count", "hedl_mlp_create",
@@ -131,6 +132,7 @@ def library(path: Optional[str] = None):
             "hedl_canonical_batch": (I, [P, P, U32, P]),
             "hedl_plan_batch": (I, [P, P, P, U32, ctypes.c_uint, ctypes.POINTER(P)]),
             "hedl_plan_info_get": (I, [P, ctypes.POINTER(hedl_plan_info)]),
+            "hedl_plan_image": (I, [P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_plan_free": (None, [P]),
             "hedl_plan_execute": (I, [P, P, P, P, P, ctypes.c_size_t, P]),
             "hedl_plan_replay": (I, [P, P, P, P, P, ctypes.c_size_t, P]),
@@ -354,6 +356,19 @@ def hedl_plan_info_get(plan: Plan) -> Dict[str, int]:
     info = hedl_plan_info()
     _check(library().hedl_plan_info_get(plan.ptr, ctypes.byref(info)))
     return {k: int(getattr(info, k)) for k, _ in hedl_plan_info._fields_}
+
+
+def hedl_plan_image(plan: Plan) -> np.ndarray:
+    """The plan's image (uint8, host copy): the work queue the interpreter reads."""
+    lib = library()
+    n = ctypes.c_size_t(0)
+    rc = lib.hedl_plan_image(plan.ptr, None, 0, ctypes.byref(n))   # sizes it (fails only on a NULL plan)
+    if rc != 0 and n.value == 0:
+        _check(rc)
+    out = np.zeros(n.value, np.uint8)
+    if n.value:
+        _check(lib.hedl_plan_image(plan.ptr, out.ctypes.data, out.size, ctypes.byref(n)))
+    return out
 
 
 def hedl_plan_free(plan: Plan):

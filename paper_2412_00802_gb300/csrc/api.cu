@@ -354,6 +354,18 @@ int hedl_plan_info_get(const hedl_plan *p, hedl_plan_info *info) {
     return HEDL_OK;
 }
 
+int hedl_plan_image(const hedl_plan *p, void *out, size_t cap, size_t *bytes) {
+    if (!p || !bytes) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    const std::vector<uint8_t> &img = p->impl->image;
+    *bytes = img.size();
+    if (img.empty()) return HEDL_OK;
+    if (!out || cap < img.size())
+        return fail(HEDL_ERR_INVALID_ARG, "image of " + std::to_string(img.size()) + " bytes, buffer of " +
+                                              std::to_string(cap));
+    memcpy(out, img.data(), img.size());
+    return HEDL_OK;
+}
+
 void hedl_plan_free(hedl_plan *p) {
     if (!p) return;
     if (p->impl) {

@@ -320,3 +320,42 @@ def test_planner_accepts_every_construct_in_every_mode():
         for f in modes:
             info = H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, f))
             assert info["n_hyps"] == len(progs)
+
+
+@pytest.mark.parametrize("n", [3000, 1_000_000])
+def test_no_sharing_plans_have_a_data_parallel_formulation(n):
+    """The plan image of a batch planned without sharing or bit slicing equals, byte for byte, the
+    one written by a formulation whose steps are independent per hypothesis or prefix sums, a stable
+    sort and a reduction (tests/plan_model.py): the shape of a device-side planner.  Workspace size
+    and algorithmic bytes agree too.  Random batches over every construct, deep chains that force
+    materialisation, narrow and full-width tiles."""
+    from tests import plan_model as M
+    kb = K.generate(K.CONFIGS["small"].scaled(3000, seed=5, n_num_roles=2, n_str_roles=2, n_strings=50,
+                                              n_patterns=6))
+    w = (n + 31) // 32
+    sizes = dict(n=n, wp=(w + 3) // 4 * 4, n_props=kb.n_props, num_vals=[v.size for v in kb.num_vals],
+                 str_vals=[v.size for v in kb.str_ids], contain_words=(len(kb.strings) + 31) // 32,
+                 role_edges=[kb.n_edges(r) for r in range(kb.n_roles)])
+    hk = H.hedl_kb_plan_only(n, kb.n_concepts, sizes["role_edges"], kb.n_props, num_role_vals=sizes["num_vals"],
+                             str_role_vals=sizes["str_vals"], n_strings=len(kb.strings), n_patterns=kb.n_patterns)
+    F = H.HEDL_NO_CSE | H.HEDL_NO_SLICE
+    r = Rng(99, 3)
+    for it in range(60):
+        progs = [np.array(pins.random_program(r, kb, r.randint(1, 9)).postfix(), np.uint64)
+                 for _ in range(r.randint(1, 80))]
+        if it % 7 == 0:
+            progs.append(np.array([P.insn(P.ATOM, 0, 0)] + [x for i in range(200) for x in (
+                P.insn(P.ATOM, 0, i % kb.n_concepts), P.insn(P.AND if i % 2 else P.OR))], np.uint64))
+        if it % 5 == 0:
+            progs += hyps.small_hyps(kb, it, 50)
+        flat, offs = P.pack_batch(progs)
+        pl = H.hedl_plan_batch(hk, flat, offs, F)
+        info = H.hedl_plan_info_get(pl)
+        img, ws, model = M.plan_image(progs, sizes, F)
+        assert np.array_equal(H.hedl_plan_image(pl), img), it
+        assert (ws, model) == (info["workspace_bytes"], info["model_bytes"]), it
+    import ctypes
+    size = ctypes.c_size_t(0)
+    buf = np.zeros(16, np.uint8)   # a buffer too small is refused, with the size reported
+    assert H.library().hedl_plan_image(pl.ptr, buf.ctypes.data, buf.size, ctypes.byref(size)) == -1
+    assert size.value == info["image_bytes"]
