@@ -274,6 +274,19 @@ int hedl_plan_batch(const hedl_kb *kb, const uint64_t *progs, const uint32_t *of
 int hedl_plan_info_get(const hedl_plan *p, hedl_plan_info *info);
 void hedl_plan_free(hedl_plan *p);
 
+/* The same plan as hedl_plan_batch with HEDL_NO_CSE | HEDL_NO_SLICE (no
+ * sharing of sub-concepts, no bit slicing), built one hypothesis at a time on
+ * n_threads host threads (0 = one per hardware thread): the paper plans the
+ * hypotheses of a batch in parallel on the CPU (Section V).  Every
+ * per-hypothesis step is independent and every global one a prefix sum, a
+ * reduction or a stable sort, the form a device-side planner takes.  The
+ * image equals hedl_plan_batch's for those flags, byte for byte.  flags may
+ * add HEDL_NO_GRAPH or HEDL_LEVELS; HEDL_PLAIN and HEDL_SLICE_ALL are refused
+ * (HEDL_ERR_INVALID_ARG), and so is a handle whose tuning stages role fillers.
+ * Host-only; HOST progs / offs as in hedl_plan_batch. */
+int hedl_plan_batch_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+                             unsigned flags, uint32_t n_threads, hedl_plan **out);
+
 /* Copy a plan's image (the work queue the interpreter reads: header, task and
  * group tables, dependency lists, segment code, zeroed counters; image_bytes
  * of hedl_plan_info) into the HOST buffer out of cap bytes, and its size into

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhedl.so")
-SOURCES = ["api.cu", "exec.cu", "plain.cu", "kb.cu", "noalloc.cu", "tune.cu", "mlp.cu", "umma.cu", "plan.cpp", "search.cpp"]
+SOURCES = ["api.cu", "exec.cu", "plain.cu", "kb.cu", "noalloc.cu", "tune.cu", "mlp.cu", "umma.cu", "plan.cpp",
+           "devplan.cu", "search.cpp"]
 HEADERS = ["hedl_internal.h", "device_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

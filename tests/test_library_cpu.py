@@ -359,3 +359,40 @@ def test_no_sharing_plans_have_a_data_parallel_formulation(n):
     buf = np.zeros(16, np.uint8)   # a buffer too small is refused, with the size reported
     assert H.library().hedl_plan_image(pl.ptr, buf.ctypes.data, buf.size, ctypes.byref(size)) == -1
     assert size.value == info["image_bytes"]
+
+
+@pytest.mark.parametrize("n", [3000, 1_000_000])
+def test_parallel_planner_equals_the_host_planner(n):
+    """hedl_plan_batch_parallel (per-hypothesis steps on host threads, the paper's parallel plan
+    generation) gives the same plan as hedl_plan_batch with HEDL_NO_CSE | HEDL_NO_SLICE: image byte
+    for byte and every field of the plan info, with and without HEDL_LEVELS, on 1 to 4 threads."""
+    kb = K.generate(K.CONFIGS["small"].scaled(3000, seed=5, n_num_roles=2, n_str_roles=2, n_strings=50,
+                                              n_patterns=6))
+    hk = H.hedl_kb_plan_only(n, kb.n_concepts, [kb.n_edges(r) for r in range(kb.n_roles)], kb.n_props,
+                             num_role_vals=[v.size for v in kb.num_vals], str_role_vals=[v.size for v in kb.str_ids],
+                             n_strings=len(kb.strings), n_patterns=kb.n_patterns)
+    F = H.HEDL_NO_CSE | H.HEDL_NO_SLICE
+    r = Rng(5, 9)
+    for it in range(40):
+        progs = [np.array(pins.random_program(r, kb, r.randint(1, 9)).postfix(), np.uint64)
+                 for _ in range(r.randint(1, 80))]
+        if it % 7 == 0:
+            progs.append(np.array([P.insn(P.ATOM, 0, 0)] + [x for i in range(250) for x in (
+                P.insn(P.ATOM, 0, i % kb.n_concepts), P.insn(P.AND if i % 2 else P.OR))], np.uint64))
+        if it % 5 == 0:
+            progs += hyps.small_hyps(kb, it, 50)
+        flat, offs = P.pack_batch(progs)
+        for extra in (0, H.HEDL_LEVELS):
+            a = H.hedl_plan_batch(hk, flat, offs, F | extra)
+            b = H.hedl_plan_batch_parallel(hk, flat, offs, F | extra, n_threads=1 + it % 4)
+            assert np.array_equal(H.hedl_plan_image(a), H.hedl_plan_image(b)), (it, extra)
+            assert H.hedl_plan_info_get(a) == H.hedl_plan_info_get(b), (it, extra)
+    progs = hyps.small_hyps(kb, 1, 10)
+    progs[6] = np.array([P.insn(P.OR)], np.uint64)
+    with pytest.raises(H.HedlError) as e:
+        H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs), n_threads=3)
+    assert e.value.code == -2 and "program 6" in str(e.value)
+    for bad_flags in (H.HEDL_PLAIN, H.HEDL_SLICE_ALL):
+        with pytest.raises(H.HedlError) as e:
+            H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs[:3]), bad_flags)
+        assert e.value.code == -1
