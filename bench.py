@@ -291,6 +291,25 @@ def surrogate_round(args, dev):
             "surrogate_round_s": sur_s, "plain_time_to_best_s": plain_s, "mlp_forward": fwd}
 
 
+def _planner_times(H, handle, batch, reps: int = 5):
+    """Host time to plan one batch without sharing or bit slicing: the host planner, and the
+    per-hypothesis planner on 1 and on all host threads (best of `reps`; the plans are equal)."""
+    F = H.HEDL_NO_CSE | H.HEDL_NO_SLICE
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+    def best(fn):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return 1000 * min(ts)
+
+    return {"host": best(lambda: H.hedl_plan_batch(handle, *batch, F)),
+            "parallel_1": best(lambda: H.hedl_plan_batch_parallel(handle, *batch, F, 1)),
+            f"parallel_{cores}": best(lambda: H.hedl_plan_batch_parallel(handle, *batch, F, cores))}
+
+
 def _section(fn, *a):
     """A secondary workload of the JSON line; a Python-level failure in it is reported in its
     object (with the traceback on stderr) instead of losing the headline line."""
@@ -762,6 +781,7 @@ def run_ours(args, rank, world, local_rank):
         plain["counts_identical"] = bool(torch.equal(pcounts, counts))
     info0 = infos[timed_ids[0]]
     ncse = H.hedl_plan_info_get(H.hedl_plan_batch(dkb.handle, *batches[timed_ids[0]], H.HEDL_NO_CSE))
+    planners = _section(_planner_times, H, dkb.handle, batches[timed_ids[0]])
 
     if rank != 0:
         return
@@ -792,7 +812,8 @@ def run_ours(args, rank, world, local_rank):
         "plan": {"host_ms_per_batch": 1000 * statistics.mean(plan_s), "segments": info0["n_segments"],
                  "slots": info0["n_slots"], "levels": info0["n_levels"], "items": info0["n_items"],
                  "role_ops": info0["n_role_ops"], "role_ops_without_sharing": ncse["n_role_ops"],
-                 "model_bytes": info0["model_bytes"], "model_bytes_without_sharing": ncse["model_bytes"]},
+                 "model_bytes": info0["model_bytes"], "model_bytes_without_sharing": ncse["model_bytes"],
+                 "no_sharing_planners_ms": planners},
         "effective_frac_unshared": value / world * (ncse["model_bytes"] / BATCH) / 1e9 / peak,
         "surrogate": surrogate,
         "search": search,
