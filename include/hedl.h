@@ -282,8 +282,7 @@ void hedl_plan_free(hedl_plan *p);
  * reduction or a stable sort, the form a device-side planner takes.  The
  * image equals hedl_plan_batch's for those flags, byte for byte.  flags may
  * add HEDL_NO_GRAPH or HEDL_LEVELS; HEDL_PLAIN and HEDL_SLICE_ALL are refused
- * (HEDL_ERR_INVALID_ARG), and so is a handle whose tuning stages role fillers.
- * Host-only; HOST progs / offs as in hedl_plan_batch. */
+ * (HEDL_ERR_INVALID_ARG).  Host-only; HOST progs / offs as in hedl_plan_batch. */
 int hedl_plan_batch_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
                              unsigned flags, uint32_t n_threads, hedl_plan **out);
 

@@ -1,7 +1,7 @@
 // Plans without sharing or bit slicing, built one hypothesis at a time.
 //
 // These are the host planner's steps (plan.cpp) for HEDL_NO_CSE | HEDL_NO_SLICE
-// with role fillers not staged, written so that every per-hypothesis step is a
+// (role fillers staged or not), written so that every per-hypothesis step is a
 // __host__ __device__ function over that hypothesis's instructions and its own
 // stretch of scratch, and every global step is a prefix sum, a reduction or a
 // stable sort:
@@ -71,7 +71,11 @@ struct Scratch {
 };
 
 // Step 1.  Returns the root's position.  The program is valid (validated).
-__host__ __device__ inline uint32_t analyze(const uint64_t *progs, uint32_t o0, uint32_t o1, const Scratch &sc) {
+// staged: role fillers are staged in shared memory, one role restriction per
+// segment, so every further role restriction met in a segment's inline
+// expansion (depth-first, first operand first) is materialised as well.
+__host__ __device__ inline uint32_t analyze(const uint64_t *progs, uint32_t o0, uint32_t o1, const Scratch &sc,
+                                            bool staged) {
     uint32_t sp = 0;
     for (uint32_t k = o0; k < o1; ++k) {
         const int ar = arity(op_of(progs[k]));
@@ -106,6 +110,27 @@ __host__ __device__ inline uint32_t analyze(const uint64_t *progs, uint32_t o0, 
                 v = a == b ? a + 1 : (a > b ? a : b);
             }
             sc.need[k] = v;
+        }
+    }
+    if (staged) {
+        for (uint32_t q = o0; q <= o1; ++q) {   // segment roots: materialised nodes, then the root
+            const uint32_t r = q < o1 ? q : root;
+            if (q < o1 && !sc.mat[r]) continue;
+            if (q == o1 && sc.mat[r]) continue;
+            bool kept = false;
+            uint32_t sp2 = 0;
+            sc.stk[o0 + sp2++] = r;
+            while (sp2) {
+                const uint32_t i = sc.stk[o0 + --sp2];
+                if (i != r && sc.mat[i]) continue;
+                if (is_role(op_of(progs[i]))) {
+                    if (kept && i != r) sc.mat[i] = 1;
+                    kept = true;
+                    continue;   // its filler is a slot or a concept row, not inline
+                }
+                if (sc.k1[i] >= 0) sc.stk[o0 + sp2++] = (uint32_t)sc.k1[i];
+                if (sc.k0[i] >= 0) sc.stk[o0 + sp2++] = (uint32_t)sc.k0[i];
+            }
         }
     }
     return root;
@@ -262,11 +287,10 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
     if (H == 0) return fail(HEDL_ERR_INVALID_ARG, "empty batch (H = 0)");
     if (flags & (HEDL_PLAIN | HEDL_TEST_UNSAT_DEP | HEDL_SLICE_ALL))
         return fail(HEDL_ERR_INVALID_ARG, "the parallel planner takes neither HEDL_PLAIN, HEDL_SLICE_ALL nor test flags");
-    if (use_staging(kb, kb->tuning))
-        return fail(HEDL_ERR_INVALID_ARG, "the parallel planner does not stage role fillers (set stage_fillers 0)");
     for (uint32_t h = 0; h < H; ++h)
         if (offs[h + 1] < offs[h]) return fail(HEDL_ERR_INVALID_ARG, "offs must be non-decreasing");
     flags |= HEDL_NO_CSE | HEDL_NO_SLICE;
+    const bool staged = use_staging(kb, kb->tuning);
     if (!n_threads) n_threads = std::max(1u, std::thread::hardware_concurrency());
     {   // validation per hypothesis, in parallel; the first bad program is reported
         std::vector<int> err(H, 0);
@@ -298,7 +322,7 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
     parallel_for(H, n_threads, [&](uint32_t h) {
         const uint32_t o0 = offs[h], o1 = offs[h + 1];
         Count &c = cnt[h];
-        c.root = dp::analyze(progs, o0, o1, sc);
+        c.root = dp::analyze(progs, o0, o1, sc, staged);
         for (uint32_t k = o0; k < o1; ++k)
             if (mat[k]) {
                 slot[k] = c.n_mat++;
@@ -383,6 +407,7 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
     p->flags = flags;
     p->n_hyps = H;
     p->tuning = kb->tuning;
+    p->staged = staged;
     p->info.n_hyps = H;
     p->info.total_insns = NI;
     p->info.n_nodes = NI;

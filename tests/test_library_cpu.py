@@ -361,16 +361,18 @@ def test_no_sharing_plans_have_a_data_parallel_formulation(n):
     assert size.value == info["image_bytes"]
 
 
-@pytest.mark.parametrize("n", [3000, 1_000_000])
-def test_parallel_planner_equals_the_host_planner(n):
+@pytest.mark.parametrize("n,stage", [(3000, 0), (1_000_000, 0), (3000, 1), (1_000_000, 1)])
+def test_parallel_planner_equals_the_host_planner(n, stage):
     """hedl_plan_batch_parallel (per-hypothesis steps on host threads, the paper's parallel plan
     generation) gives the same plan as hedl_plan_batch with HEDL_NO_CSE | HEDL_NO_SLICE: image byte
-    for byte and every field of the plan info, with and without HEDL_LEVELS, on 1 to 4 threads."""
+    for byte and every field of the plan info, with and without HEDL_LEVELS, on 1 to 4 threads, with
+    role fillers staged in shared memory (one role restriction per segment) or not."""
     kb = K.generate(K.CONFIGS["small"].scaled(3000, seed=5, n_num_roles=2, n_str_roles=2, n_strings=50,
                                               n_patterns=6))
     hk = H.hedl_kb_plan_only(n, kb.n_concepts, [kb.n_edges(r) for r in range(kb.n_roles)], kb.n_props,
                              num_role_vals=[v.size for v in kb.num_vals], str_role_vals=[v.size for v in kb.str_ids],
                              n_strings=len(kb.strings), n_patterns=kb.n_patterns)
+    H.hedl_tuning_set(hk, stage_fillers=stage)
     F = H.HEDL_NO_CSE | H.HEDL_NO_SLICE
     r = Rng(5, 9)
     for it in range(40):
@@ -396,3 +398,10 @@ def test_parallel_planner_equals_the_host_planner(n):
         with pytest.raises(H.HedlError) as e:
             H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs[:3]), bad_flags)
         assert e.value.code == -1
+    if stage:   # staging split restrictions into more segments than without
+        r2 = Rng(6, 1)
+        progs = [np.array(pins.random_program(r2, kb, 6).postfix(), np.uint64) for _ in range(200)]
+        staged = H.hedl_plan_info_get(H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs), F))
+        H.hedl_tuning_set(hk, stage_fillers=0)
+        plain = H.hedl_plan_info_get(H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs), F))
+        assert staged["n_segments"] > plain["n_segments"]
