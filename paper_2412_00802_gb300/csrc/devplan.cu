@@ -17,15 +17,18 @@
 //      offsets;
 //   4. a reduction (segments per level that walk a role) fixes the tile shape
 //      and a stable sort by (level, role key) orders the work queue.
-// The host driver runs steps 1-2 on several threads (the paper plans
-// hypotheses in parallel on the CPU, Section V); the same functions are the
-// body of a device-side planner (the paper's future work, Section VII).  The
-// image equals the host planner's for the same flags, byte for byte.
+// The host driver runs the per-hypothesis steps on several threads (the paper
+// plans hypotheses in parallel on the CPU, Section V) and the others in turn;
+// every step is a __host__ __device__ function of one index, so the same code
+// is the body of a device-side planner (the paper's future work, Section VII).
+// The image equals the host planner's for the same flags, byte for byte.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <string>
+#include <type_traits>
 #include <thread>
 #include <vector>
 
@@ -247,21 +250,327 @@ __host__ __device__ inline SegInfo emit(const uint64_t *progs, uint32_t o0, cons
     return s;
 }
 
+// ---------------------------------------------------------------- the steps
+// The whole pipeline as functions of one index (a hypothesis, a segment, a
+// sort position) or of none (the sequential steps), over one context of plain
+// pointers: the host driver below runs them in loops (the per-hypothesis ones
+// on threads), a device driver runs them as grid-stride kernels.
+
+struct HypCount {           // per hypothesis; scanned in place into offsets
+    uint32_t root, n_mat, mat_code, mat_reads, root_code, root_reads, err;
+    uint32_t n_role, n_data, n_atom, max_depth;
+    uint64_t model;
+};
+
+struct Totals {
+    uint64_t n_slots, code_n, deps_n, NS, n_levels, WW, TW, n_tiles, n_groups, items;
+    uint64_t off_segs, off_deps, off_code, off_ctr, ctr_words;   // set by finish_step
+    uint32_t err_hyp, err_code;
+};
+
+// Offsets of the image's tables, as the host planner lays them out (each
+// table 256-byte aligned after the header).
+struct Layout {
+    uint64_t off_segs, off_groups, off_gsegs, off_deps, off_code, off_li, off_ctr, off_slots, off_ft, ctr_words;
+};
+
+__host__ __device__ inline uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+__host__ __device__ inline Layout layout(uint64_t NS, uint64_t G, uint64_t D, uint64_t C, uint64_t L, uint64_t H,
+                                         uint64_t n_slots, uint64_t B) {
+    Layout o{};
+    o.off_segs = align256(sizeof(PlanHeader));
+    o.off_groups = align256(o.off_segs + NS * sizeof(Seg));
+    o.off_gsegs = align256(o.off_groups + G * sizeof(Group));
+    o.off_deps = align256(o.off_gsegs + NS * 4);
+    o.off_code = align256(o.off_deps + D * 4);
+    o.off_li = align256(o.off_code + C * sizeof(DInsn));
+    o.off_ctr = align256(o.off_li + (L + 1) * 4);
+    o.ctr_words = 4 + (NS + 1) + 2 * H;
+    o.off_slots = align256(o.off_ctr + o.ctr_words * 4);   // the (empty) role-group table starts here too
+    o.off_ft = align256(o.off_slots + n_slots * B);
+    return o;
+}
+
+struct Ctx {
+    const uint64_t *progs;
+    const uint32_t *offs;
+    uint32_t H;
+    uint32_t n_concepts, n_roles, n_data, n_str, n_patterns;   // id limits (validation)
+    bool staged;
+    bool validated;            // programs already validated (skip it in count_step)
+    Sizes z;
+    Scratch sc;
+    HypCount *cnt;
+    Totals *tot;
+    Seg *segs;                 // per segment, in segment order
+    DInsn *code;
+    uint32_t *deps;
+    uint32_t *seg_level, *seg_key;
+    uint8_t *seg_walks;
+    uint64_t *keys;            // (level, role key, segment), padded with ~0
+    uint8_t *starts;           // sorted position starts a group
+    uint32_t *segs_at, *walks_at;   // per level
+    uint32_t warps, wpl, rounds, timeout_ms, wp, n_sms;
+    unsigned flags;
+    uint8_t *img;              // the image (zero-filled beforehand)
+    uint32_t *level_items;     // [n_levels + 1]
+};
+
+// A program's validity as the host planner decides it: HEDL_OK or a negative status.
+__host__ __device__ inline int validate(const Ctx &c, uint32_t o0, uint32_t o1) {
+    if (o1 <= o0) return HEDL_ERR_BAD_PROGRAM;
+    int depth = 0;
+    for (uint32_t k = o0; k < o1; ++k) {
+        const uint64_t w = c.progs[k];
+        const uint32_t op = op_of(w), a = a_of(w);
+        if (op < HEDL_OP_ATOM || op > HEDL_OP_SCONTAINS) return HEDL_ERR_BAD_PROGRAM;
+        if ((op == HEDL_OP_ATOM && a >= c.n_concepts) || (is_role(op) && a >= c.n_roles) ||
+            (is_data(op) && a >= c.n_data) || (is_str(op) && a >= c.n_str) ||
+            (op == HEDL_OP_SCONTAINS && b_of(w) >= c.n_patterns))
+            return HEDL_ERR_BAD_PROGRAM;
+        const int ar = arity(op);
+        if (depth < ar) return HEDL_ERR_BAD_PROGRAM;
+        depth = depth - ar + 1;
+        if (depth > HEDL_MAX_STACK) return HEDL_ERR_BAD_PROGRAM;
+    }
+    return depth == 1 ? HEDL_OK : HEDL_ERR_BAD_PROGRAM;
+}
+
+// Per hypothesis: validate, analyze, count its segments' code and reads.
+__host__ __device__ inline void count_step(const Ctx &c, uint32_t h) {
+    const uint32_t o0 = c.offs[h], o1 = c.offs[h + 1];
+    HypCount &n = c.cnt[h];
+    n = HypCount{};
+    const int e = o1 < o0 ? HEDL_ERR_INVALID_ARG : (c.validated ? HEDL_OK : validate(c, o0, o1));
+    n.err = (uint32_t)-e;
+    if (e) return;
+    n.root = analyze(c.progs, o0, o1, c.sc, c.staged);
+    for (uint32_t k = o0; k < o1; ++k)
+        if (c.sc.mat[k]) {
+            c.sc.slot[k] = n.n_mat++;
+            const SegInfo s = emit(c.progs, o0, c.sc, k, c.z, 0, nullptr, nullptr);
+            c.sc.level[k] = s.level;   // operand segments come first: node order
+            n.mat_code += s.code_len;
+            n.mat_reads += s.n_reads;
+        }
+    const SegInfo r = emit(c.progs, o0, c.sc, n.root, c.z, 0, nullptr, nullptr);
+    n.root_code = r.code_len;
+    n.root_reads = r.n_reads;
+}
+
+// Sequential: offsets in place (materialised segments of every hypothesis
+// first, then the roots), the totals and the first failing hypothesis.
+__host__ __device__ inline void scan_step(const Ctx &c) {
+    uint64_t slots = 0, code = 0, deps = 0;
+    uint32_t err_h = 0xFFFFFFFFu, err_c = 0;
+    for (uint32_t h = 0; h < c.H; ++h) {
+        HypCount &n = c.cnt[h];
+        if (n.err && err_h == 0xFFFFFFFFu) err_h = h, err_c = n.err;
+        const uint32_t m = n.n_mat, mc = n.mat_code, md = n.mat_reads;
+        n.n_mat = (uint32_t)slots;
+        n.mat_code = (uint32_t)code;
+        n.mat_reads = (uint32_t)deps;
+        slots += m;
+        code += mc;
+        deps += md;
+    }
+    for (uint32_t h = 0; h < c.H; ++h) {
+        HypCount &n = c.cnt[h];
+        const uint32_t rc = n.root_code, rd = n.root_reads;
+        n.root_code = (uint32_t)code;
+        n.root_reads = (uint32_t)deps;
+        code += rc;
+        deps += rd;
+    }
+    Totals &t = *c.tot;
+    t = Totals{};
+    t.n_slots = slots;
+    t.code_n = code;
+    t.deps_n = deps;
+    t.NS = slots + c.H;
+    t.err_hyp = err_h;
+    t.err_code = err_c;
+}
+
+// Per hypothesis: emit its segments at their offsets.
+__host__ __device__ inline void write_step(const Ctx &c, uint32_t h) {
+    if (c.tot->err_hyp != 0xFFFFFFFFu) return;
+    const uint32_t o0 = c.offs[h], o1 = c.offs[h + 1];
+    HypCount &n = c.cnt[h];
+    const uint32_t slot_base = n.n_mat;
+    uint32_t c_at = n.mat_code, d_at = n.mat_reads;
+    auto record = [&](uint32_t sidx, const SegInfo &s, uint32_t c0, uint32_t d0, uint32_t out_slot, uint32_t hyp) {
+        Seg g{};
+        g.code_off = c0;
+        g.code_len = s.code_len;
+        g.out_slot = out_slot;
+        g.hyp = hyp;
+        g.dep_off = d0;
+        g.dep_cnt = s.n_reads;
+        g.filler = s.filler;
+        g.kind = TASK_SEGMENT;
+        c.segs[sidx] = g;
+        c.seg_level[sidx] = s.level;
+        c.seg_key[sidx] = s.key;
+        c.seg_walks[sidx] = s.key != NO_FILLER;
+        n.model += s.model;
+        n.n_role += s.n_role;
+        n.n_data += s.n_data;
+        n.n_atom += s.n_atom;
+        if (s.max_depth > n.max_depth) n.max_depth = s.max_depth;
+    };
+    for (uint32_t k = o0; k < o1; ++k)
+        if (c.sc.mat[k]) {
+            const SegInfo s = emit(c.progs, o0, c.sc, k, c.z, slot_base, c.code + c_at, c.deps + d_at);
+            c.sc.level[k] = s.level;
+            record(slot_base + c.sc.slot[k], s, c_at, d_at, slot_base + c.sc.slot[k], NO_HYP);
+            c_at += s.code_len;
+            d_at += s.n_reads;
+        }
+    const SegInfo r = emit(c.progs, o0, c.sc, n.root, c.z, slot_base, c.code + n.root_code, c.deps + n.root_reads);
+    record((uint32_t)c.tot->n_slots + h, r, n.root_code, n.root_reads, NO_SLOT, h);
+    n.model += 2 * c.z.B + 16;   // the hypothesis's score
+}
+
+// Sequential: levels, and the tile shape by the host planner's rule (a warp
+// covers fewer words when a level that walks a role has few segments).
+__host__ __device__ inline void shape_step(const Ctx &c) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    uint32_t n_levels = 0;
+    for (uint64_t s = 0; s < t.NS; ++s) n_levels = c.seg_level[s] + 1 > n_levels ? c.seg_level[s] + 1 : n_levels;
+    for (uint32_t L = 0; L < n_levels; ++L) c.segs_at[L] = c.walks_at[L] = 0;
+    for (uint64_t s = 0; s < t.NS; ++s) {
+        c.segs_at[c.seg_level[s]]++;
+        c.walks_at[c.seg_level[s]] |= c.seg_walks[s];
+    }
+    uint64_t smin = ~0ull;
+    for (uint32_t L = 0; L < n_levels; ++L)
+        if (c.walks_at[L] && c.segs_at[L] < smin) smin = c.segs_at[L];
+    uint32_t WW = 32, rounds = c.rounds;
+    if (c.n_sms > 0) {
+        const uint64_t resident = 32ull * c.n_sms;
+        if (smin != ~0ull)
+            while (WW > 4 && smin * c.wp < 4ull * resident * WW * c.wpl) WW >>= 1;
+        if (WW < 32) rounds = 1;
+    }
+    t.n_levels = n_levels;
+    t.WW = WW;
+    t.TW = (uint64_t)c.warps * WW * c.wpl * rounds;
+    t.n_tiles = (c.wp + t.TW - 1) / t.TW;
+}
+
+// Per sort position: the key of segment i (unique, so any sort is the stable one).
+__host__ __device__ inline void key_step(const Ctx &c, uint64_t i) {
+    if (i < c.tot->NS) {
+        const uint64_t key = c.seg_key[i] == NO_FILLER ? (1ull << 17) : (uint64_t)c.seg_key[i];   // role keys < 2^17
+        c.keys[i] = ((uint64_t)c.seg_level[i] << 50) | (key << 32) | i;
+    } else {
+        c.keys[i] = ~0ull;
+    }
+}
+
+// Per sort position: one compare-exchange of a bitonic step (n2 a power of two).
+__host__ __device__ inline void bitonic_step(uint64_t *keys, uint64_t i, uint64_t j, uint64_t k) {
+    const uint64_t l = i ^ j;
+    if (l > i) {
+        const uint64_t a = keys[i], b = keys[l];
+        if ((a > b) == ((i & k) == 0)) {
+            keys[i] = b;
+            keys[l] = a;
+        }
+    }
+}
+
+// Per sorted position: does it start a group (a new (level, role key))?
+__host__ __device__ inline void start_step(const Ctx &c, uint64_t i) {
+    if (i < c.tot->NS) c.starts[i] = i == 0 || (c.keys[i] >> 32) != (c.keys[i - 1] >> 32);
+}
+
+// Sequential: groups, gsegs, level_items and the header.
+__host__ __device__ inline void finish_step(const Ctx &c) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    const uint64_t NS = t.NS, n_tiles = t.n_tiles, L = t.n_levels;
+    uint64_t G = 0;
+    for (uint64_t i = 0; i < NS; ++i) G += c.starts[i];
+    const Layout o = layout(NS, G, t.deps_n, t.code_n, L, c.H, t.n_slots, c.z.B);
+    Group *groups = reinterpret_cast<Group *>(c.img + o.off_groups);
+    uint32_t *gsegs = reinterpret_cast<uint32_t *>(c.img + o.off_gsegs);
+    uint32_t *li = reinterpret_cast<uint32_t *>(c.img + o.off_li);
+    for (uint64_t l = 0; l <= L; ++l) li[l] = 0;
+    uint64_t g = 0, begin = 0;
+    for (uint64_t i = 0; i < NS; ++i) {
+        gsegs[i] = (uint32_t)(c.keys[i] & 0xFFFFFFFFull);
+        if (c.starts[i]) begin = i;
+        if (i + 1 == NS || c.starts[i + 1]) {   // the group [begin, i] ends here
+            const uint32_t lvl = c.seg_level[gsegs[begin]];
+            groups[g++] = Group{(uint32_t)(begin * n_tiles), (uint32_t)begin, (uint32_t)(i + 1 - begin), lvl};
+            li[lvl + 1] = (uint32_t)((i + 1) * n_tiles);
+        }
+    }
+    for (uint64_t l = 1; l <= L; ++l) li[l] = li[l] > li[l - 1] ? li[l] : li[l - 1];
+    for (uint64_t l = 0; l <= L; ++l) c.level_items[l] = li[l];
+    PlanHeader hd{};
+    hd.n_items = (uint32_t)(NS * n_tiles);
+    hd.n_segs = (uint32_t)NS;
+    hd.n_groups = (uint32_t)G;
+    hd.n_hyps = c.H;
+    hd.n_tiles = (uint32_t)n_tiles;
+    hd.tile_words = (uint32_t)t.TW;
+    hd.n_slots = (uint32_t)t.n_slots;
+    hd.flags = c.flags;
+    hd.n_levels = (uint32_t)L;
+    hd.n_deps = (uint32_t)t.deps_n;
+    hd.n_rgroups = 0;
+    hd.warp_words = (uint32_t)t.WW;
+    hd.off_segs = o.off_segs;
+    hd.off_groups = o.off_groups;
+    hd.off_gsegs = o.off_gsegs;
+    hd.off_deps = o.off_deps;
+    hd.off_code = o.off_code;
+    hd.off_level_items = o.off_li;
+    hd.off_ctr = o.off_ctr;
+    hd.off_slots = o.off_slots;
+    hd.off_rgroups = o.off_slots;
+    hd.off_ft = o.off_ft;
+    hd.timeout_ns = (uint64_t)c.timeout_ms * 1000000ull;
+    *reinterpret_cast<PlanHeader *>(c.img) = hd;
+    t.n_groups = G;
+    t.items = NS * n_tiles;
+    t.off_segs = o.off_segs;
+    t.off_deps = o.off_deps;
+    t.off_code = o.off_code;
+    t.off_ctr = o.off_ctr;
+    t.ctr_words = o.ctr_words;
+}
+
+// Per index: copy segment i, dependency i and code word i into the image; zero counter i.
+__host__ __device__ inline void assemble_step(const Ctx &c, uint64_t i) {
+    const Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    if (i < t.NS) reinterpret_cast<Seg *>(c.img + t.off_segs)[i] = c.segs[i];
+    if (i < t.deps_n) reinterpret_cast<uint32_t *>(c.img + t.off_deps)[i] = c.deps[i];
+    if (i < t.code_n) reinterpret_cast<DInsn *>(c.img + t.off_code)[i] = c.code[i];
+    if (i < t.ctr_words) reinterpret_cast<uint32_t *>(c.img + t.off_ctr)[i] = 0;
+}
+
+// Upper bounds from the instruction count NI and H, known before planning.
+struct Bounds {
+    uint64_t NS, code, deps, levels, slots;
+};
+__host__ __device__ inline Bounds bounds(uint64_t NI, uint64_t H) { return Bounds{NI + H, 2 * NI, NI, NI + 1, NI}; }
+
+__host__ __device__ inline uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
 }  // namespace dp
 
 namespace {
-
-uint64_t put_bytes(std::vector<uint8_t> &img, const void *data, size_t n) {
-    const uint64_t off = (img.size() + 255) & ~uint64_t(255);
-    img.resize(off + n);
-    if (n) memcpy(img.data() + off, data, n);
-    return off;
-}
-
-template <typename T>
-uint64_t put_vec(std::vector<uint8_t> &img, const std::vector<T> &v) {
-    return put_bytes(img, v.data(), v.size() * sizeof(T));
-}
 
 // Run f(h) for h in [0, H) on n threads (contiguous shares).
 template <typename F>
@@ -290,9 +599,8 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
     for (uint32_t h = 0; h < H; ++h)
         if (offs[h + 1] < offs[h]) return fail(HEDL_ERR_INVALID_ARG, "offs must be non-decreasing");
     flags |= HEDL_NO_CSE | HEDL_NO_SLICE;
-    const bool staged = use_staging(kb, kb->tuning);
     if (!n_threads) n_threads = std::max(1u, std::thread::hardware_concurrency());
-    {   // validation per hypothesis, in parallel; the first bad program is reported
+    {   // validation with messages, per hypothesis in parallel; the first bad program is reported
         std::vector<int> err(H, 0);
         std::vector<std::string> why(H);
         parallel_for(H, n_threads, [&](uint32_t h) {
@@ -301,224 +609,125 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
         for (uint32_t h = 0; h < H; ++h)
             if (err[h]) return fail(err[h], "program " + std::to_string(h) + ": " + why[h]);
     }
-    const uint32_t NI = offs[H];
+    const uint64_t NI = offs[H];
+    const dp::Bounds b = dp::bounds(NI, H);
     std::vector<uint32_t> num_vals, str_vals, csr_edges;
     for (const DevNum &g : kb->num_host) num_vals.push_back(g.n_vals);
     for (const DevStr &g : kb->str_host) str_vals.push_back(g.n_vals);
     for (const DevCSR &g : kb->csr_host) csr_edges.push_back(g.n_edges);
-    const dp::Sizes z{kb->n, 4ull * kb->wp, kb->n_props, num_vals.data(), str_vals.data(), csr_edges.data(),
-                      kb->contain_words};
-    std::vector<int32_t> k0(NI), k1(NI);
-    std::vector<uint32_t> need(NI), slot(NI), level(NI), stk(NI);
-    std::vector<uint8_t> mat(NI), state(NI);
-    const dp::Scratch sc{k0.data(), k1.data(), need.data(), mat.data(), slot.data(), level.data(), stk.data(),
-                         state.data()};
+    // scratch: every entry is written before it is read, so it is left uninitialised
+    auto buf = [](uint64_t n, auto *tag) { return std::unique_ptr<std::remove_pointer_t<decltype(tag)>[]>(
+                                               new std::remove_pointer_t<decltype(tag)>[n ? n : 1]); };
+    auto k0 = buf(NI, (int32_t *)nullptr), k1 = buf(NI, (int32_t *)nullptr);
+    auto need = buf(NI, (uint32_t *)nullptr), slot = buf(NI, (uint32_t *)nullptr);
+    auto level = buf(NI, (uint32_t *)nullptr), stk = buf(NI, (uint32_t *)nullptr);
+    auto mat = buf(NI, (uint8_t *)nullptr), state = buf(NI, (uint8_t *)nullptr);
+    std::vector<dp::HypCount> cnt(H);
+    dp::Totals tot{};
+    auto segs = buf(b.NS, (Seg *)nullptr);
+    auto code = buf(b.code, (DInsn *)nullptr);
+    auto deps = buf(b.deps, (uint32_t *)nullptr);
+    auto seg_level = buf(b.NS, (uint32_t *)nullptr), seg_key = buf(b.NS, (uint32_t *)nullptr);
+    auto seg_walks = buf(b.NS, (uint8_t *)nullptr), starts = buf(b.NS, (uint8_t *)nullptr);
+    auto keys = buf(b.NS, (uint64_t *)nullptr);
+    std::vector<uint32_t> segs_at(b.levels), walks_at(b.levels), level_items(b.levels + 1);
+    std::vector<uint8_t> img;   // sized once the groups are known
 
-    // steps 1-2 (count): per hypothesis
-    struct Count {
-        uint32_t root = 0, n_mat = 0, mat_code = 0, mat_reads = 0, root_code = 0, root_reads = 0;
-    };
-    std::vector<Count> cnt(H);
-    parallel_for(H, n_threads, [&](uint32_t h) {
-        const uint32_t o0 = offs[h], o1 = offs[h + 1];
-        Count &c = cnt[h];
-        c.root = dp::analyze(progs, o0, o1, sc, staged);
-        for (uint32_t k = o0; k < o1; ++k)
-            if (mat[k]) {
-                slot[k] = c.n_mat++;
-                const dp::SegInfo s = dp::emit(progs, o0, sc, k, z, 0, nullptr, nullptr);
-                level[k] = s.level;   // levels of earlier (operand) segments are set: node order
-                c.mat_code += s.code_len;
-                c.mat_reads += s.n_reads;
-            }
-        const dp::SegInfo r = dp::emit(progs, o0, sc, c.root, z, 0, nullptr, nullptr);
-        c.root_code = r.code_len;
-        c.root_reads = r.n_reads;
-    });
+    dp::Ctx c{};
+    c.progs = progs;
+    c.offs = offs;
+    c.H = H;
+    c.n_concepts = kb->n_concepts;
+    c.n_roles = kb->n_roles;
+    c.n_data = kb->n_props + kb->n_num;
+    c.n_str = kb->n_str;
+    c.n_patterns = kb->n_patterns;
+    c.staged = use_staging(kb, kb->tuning);
+    c.validated = true;
+    c.z = dp::Sizes{kb->n, 4ull * kb->wp, kb->n_props, num_vals.data(), str_vals.data(), csr_edges.data(),
+                    kb->contain_words};
+    c.sc = dp::Scratch{k0.get(), k1.get(), need.get(), mat.get(), slot.get(), level.get(), stk.get(), state.get()};
+    c.cnt = cnt.data();
+    c.tot = &tot;
+    c.segs = segs.get();
+    c.code = code.get();
+    c.deps = deps.get();
+    c.seg_level = seg_level.get();
+    c.seg_key = seg_key.get();
+    c.seg_walks = seg_walks.get();
+    c.keys = keys.get();
+    c.starts = starts.get();
+    c.segs_at = segs_at.data();
+    c.walks_at = walks_at.data();
+    const Tuning &tu = kb->tuning;
+    c.warps = tu.warps;
+    c.wpl = tu.wpl;
+    c.rounds = tu.rounds;
+    c.timeout_ms = tu.timeout_ms;
+    c.wp = kb->wp;
+    c.n_sms = (uint32_t)std::max(kb->n_sms, 0);
+    c.flags = flags;
+    c.level_items = level_items.data();
 
-    // step 3: prefix sums (materialised segments of every hypothesis first, then the roots)
-    std::vector<uint32_t> slot_base(H), mcode(H), mdeps(H), rcode(H), rdeps(H);
-    uint64_t n_slots = 0, code_n = 0, deps_n = 0;
-    for (uint32_t h = 0; h < H; ++h) {
-        slot_base[h] = (uint32_t)n_slots;
-        mcode[h] = (uint32_t)code_n;
-        mdeps[h] = (uint32_t)deps_n;
-        n_slots += cnt[h].n_mat;
-        code_n += cnt[h].mat_code;
-        deps_n += cnt[h].mat_reads;
+    // the steps: per hypothesis on threads, the sequential ones in turn; the
+    // sort of unique keys is std::sort here (a bitonic network on the device)
+    parallel_for(H, n_threads, [&](uint32_t h) { dp::count_step(c, h); });
+    dp::scan_step(c);
+    if (tot.err_hyp != 0xFFFFFFFFu)
+        return fail(-(int)tot.err_code, "program " + std::to_string(tot.err_hyp) + " is not valid");
+    if (tot.n_slots > REF_ID) return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^30 materialized intermediate sets");
+    parallel_for(H, n_threads, [&](uint32_t h) { dp::write_step(c, h); });
+    dp::shape_step(c);
+    for (uint64_t i = 0; i < tot.NS; ++i) dp::key_step(c, i);
+    std::sort(keys.get(), keys.get() + tot.NS);
+    uint64_t G = 0;
+    for (uint64_t i = 0; i < tot.NS; ++i) {
+        dp::start_step(c, i);
+        G += starts[i];
     }
-    for (uint32_t h = 0; h < H; ++h) {
-        rcode[h] = (uint32_t)code_n;
-        rdeps[h] = (uint32_t)deps_n;
-        code_n += cnt[h].root_code;
-        deps_n += cnt[h].root_reads;
-    }
-    if (n_slots > REF_ID) return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^30 materialized intermediate sets");
-    const uint32_t NS = (uint32_t)n_slots + H;
-    std::vector<Seg> segs(NS);
-    std::vector<DInsn> code(code_n);
-    std::vector<uint32_t> deps(deps_n), seg_level(NS), seg_key(NS);
-    std::vector<uint8_t> seg_walks(NS);
-    struct Tally {
-        uint64_t model = 0;
-        uint32_t n_role = 0, n_data = 0, n_atom = 0, max_depth = 0;
-    };
-    std::vector<Tally> tally(H);
+    img.assign(dp::layout(tot.NS, G, tot.deps_n, tot.code_n, tot.n_levels, H, tot.n_slots, 4ull * kb->wp).off_slots, 0);
+    c.img = img.data();
+    dp::finish_step(c);
+    const uint64_t span = std::max<uint64_t>(std::max<uint64_t>(tot.NS, tot.code_n), std::max<uint64_t>(tot.deps_n, 4 + tot.NS + 1 + 2ull * H));
+    for (uint64_t i = 0; i < span; ++i) dp::assemble_step(c, i);
+    if (tot.items >= 0xFFFFFFFFull) return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^32 work items");
 
-    // step 2 (write): per hypothesis, into its own ranges
-    parallel_for(H, n_threads, [&](uint32_t h) {
-        const uint32_t o0 = offs[h], o1 = offs[h + 1];
-        uint32_t c_at = mcode[h], d_at = mdeps[h];
-        Tally &t = tally[h];
-        auto record = [&](uint32_t sidx, const dp::SegInfo &s, uint32_t c0, uint32_t d0, uint32_t out_slot,
-                          uint32_t hyp) {
-            Seg &g = segs[sidx];
-            g.code_off = c0;
-            g.code_len = s.code_len;
-            g.out_slot = out_slot;
-            g.hyp = hyp;
-            g.dep_off = d0;
-            g.dep_cnt = s.n_reads;
-            g.filler = s.filler;
-            g.kind = TASK_SEGMENT;
-            seg_level[sidx] = s.level;
-            seg_key[sidx] = s.key;
-            seg_walks[sidx] = s.key != NO_FILLER;
-            t.model += s.model;
-            t.n_role += s.n_role;
-            t.n_data += s.n_data;
-            t.n_atom += s.n_atom;
-            t.max_depth = std::max(t.max_depth, s.max_depth);
-        };
-        for (uint32_t k = o0; k < o1; ++k)
-            if (mat[k]) {
-                const dp::SegInfo s = dp::emit(progs, o0, sc, k, z, slot_base[h], code.data() + c_at, deps.data() + d_at);
-                level[k] = s.level;
-                record(slot_base[h] + slot[k], s, c_at, d_at, slot_base[h] + slot[k], NO_HYP);
-                c_at += s.code_len;
-                d_at += s.n_reads;
-            }
-        const dp::SegInfo r = dp::emit(progs, o0, sc, cnt[h].root, z, slot_base[h], code.data() + rcode[h],
-                                       deps.data() + rdeps[h]);
-        record((uint32_t)n_slots + h, r, rcode[h], rdeps[h], NO_SLOT, h);
-        t.model += 2 * z.B + 16;
-    });
-    PlanImpl *p = new PlanImpl();
+    PlanHeader hd;
+    memcpy(&hd, img.data(), sizeof hd);
+    auto *p = new PlanImpl();
     p->flags = flags;
     p->n_hyps = H;
     p->tuning = kb->tuning;
-    p->staged = staged;
+    p->staged = c.staged;
     p->info.n_hyps = H;
     p->info.total_insns = NI;
     p->info.n_nodes = NI;
     uint64_t model = 0;
-    for (const Tally &t : tally) {
-        model += t.model;
-        p->info.n_role_ops += t.n_role;
-        p->info.n_data_ops += t.n_data;
-        p->info.n_atom_loads += t.n_atom;
-        p->max_stack = std::max(p->max_stack, t.max_depth);
+    for (const dp::HypCount &n : cnt) {
+        model += n.model;
+        p->info.n_role_ops += n.n_role;
+        p->info.n_data_ops += n.n_data;
+        p->info.n_atom_loads += n.n_atom;
+        p->max_stack = std::max(p->max_stack, n.max_depth);
     }
     if (p->max_stack > (uint32_t)STACK_MAX) {
         delete p;
         return fail(HEDL_ERR_BAD_PROGRAM, "internal: segment stack exceeds the device limit");
     }
-
-    // step 4: tile shape (a reduction over levels), work queue (a stable sort)
-    uint32_t n_levels = 0;
-    for (uint32_t s = 0; s < NS; ++s) n_levels = std::max(n_levels, seg_level[s] + 1);
-    const Tuning &t = p->tuning;
-    uint32_t WW = 32, rounds = t.rounds;
-    if (kb->n_sms > 0) {
-        std::vector<uint32_t> segs_at(n_levels, 0);
-        std::vector<uint8_t> walks_at(n_levels, 0);
-        for (uint32_t s = 0; s < NS; ++s) {
-            segs_at[seg_level[s]]++;
-            walks_at[seg_level[s]] |= seg_walks[s];
-        }
-        uint64_t smin = UINT64_MAX;
-        for (uint32_t L = 0; L < n_levels; ++L)
-            if (walks_at[L]) smin = std::min<uint64_t>(smin, segs_at[L]);
-        const uint64_t resident = 32ull * (uint64_t)kb->n_sms;
-        if (smin != UINT64_MAX)
-            while (WW > 4 && smin * kb->wp < 4ull * resident * WW * t.wpl) WW >>= 1;
-        if (WW < 32) rounds = 1;
-    }
-    const uint32_t TW = t.warps * WW * t.wpl * rounds;
-    const uint32_t n_tiles = (kb->wp + TW - 1) / TW;
-    std::vector<uint32_t> order(NS);
-    for (uint32_t s = 0; s < NS; ++s) order[s] = s;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-        if (seg_level[x] != seg_level[y]) return seg_level[x] < seg_level[y];
-        return seg_key[x] < seg_key[y];
-    });
-    std::vector<Group> groups;
-    std::vector<uint32_t> gsegs;
-    std::vector<uint32_t> level_items(n_levels + 1, 0);
-    uint64_t items = 0;
-    for (uint32_t k = 0; k < NS;) {
-        const uint32_t s0 = order[k];
-        Group g{};
-        g.item_begin = (uint32_t)items;
-        g.seg_begin = (uint32_t)gsegs.size();
-        g.level = seg_level[s0];
-        uint32_t k2 = k;
-        while (k2 < NS && seg_level[order[k2]] == g.level && seg_key[order[k2]] == seg_key[s0]) gsegs.push_back(order[k2++]);
-        g.n_segs = k2 - k;
-        items += (uint64_t)g.n_segs * n_tiles;
-        groups.push_back(g);
-        level_items[g.level + 1] = (uint32_t)items;
-        k = k2;
-    }
-    for (uint32_t l = 1; l <= n_levels; ++l) level_items[l] = std::max(level_items[l], level_items[l - 1]);
-    if (items >= 0xFFFFFFFFull) {
-        delete p;
-        return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^32 work items");
-    }
-
-    // the image, laid out as the host planner lays it out
-    std::vector<uint8_t> &img = p->image;
-    img.resize(sizeof(PlanHeader));
-    PlanHeader hd{};
-    hd.n_items = (uint32_t)items;
-    hd.n_segs = NS;
-    hd.n_groups = (uint32_t)groups.size();
-    hd.n_hyps = H;
-    hd.n_tiles = n_tiles;
-    hd.tile_words = TW;
-    hd.warp_words = WW;
-    hd.n_slots = (uint32_t)n_slots;
-    hd.flags = flags;
-    hd.n_levels = n_levels;
-    hd.n_deps = (uint32_t)deps.size();
-    hd.off_segs = put_vec(img, segs);
-    hd.off_groups = put_vec(img, groups);
-    hd.off_gsegs = put_vec(img, gsegs);
-    hd.off_deps = put_vec(img, deps);
-    hd.off_code = put_vec(img, code);
-    hd.off_level_items = put_vec(img, level_items);
-    hd.n_rgroups = 0;
-    std::vector<uint32_t> zeros(4 + (NS + 1) + 2ull * H, 0);
-    hd.off_ctr = put_vec(img, zeros);
+    p->image = std::move(img);
+    p->image_bytes = hd.off_slots;
     p->ctr_off = hd.off_ctr;
-    p->ctr_bytes = zeros.size() * 4;
-    hd.off_rgroups = put_bytes(img, nullptr, 0);
-    img.resize((img.size() + 255) & ~size_t(255));
-    hd.off_slots = img.size();
-    hd.off_ft = (hd.off_slots + n_slots * 4ull * kb->wp + 255) & ~uint64_t(255);
-    hd.timeout_ns = (uint64_t)t.timeout_ms * 1000000ull;
-    memcpy(img.data(), &hd, sizeof hd);
-    p->image_bytes = img.size();
+    p->ctr_bytes = (4 + (uint64_t)(tot.NS + 1) + 2ull * H) * 4;
     p->slots_off = hd.off_slots;
     p->ws_bytes = hd.off_ft;
     p->n_rgroups = 0;
-    p->level_items = level_items;
-    p->info.n_segments = NS;
-    p->info.n_slots = (uint32_t)n_slots;
-    p->info.n_levels = n_levels;
-    p->info.n_items = (uint32_t)items;
-    p->info.tile_words = TW;
-    p->info.warp_words = WW;
+    p->level_items.assign(level_items.begin(), level_items.begin() + tot.n_levels + 1);
+    p->info.n_segments = hd.n_segs;
+    p->info.n_slots = hd.n_slots;
+    p->info.n_levels = hd.n_levels;
+    p->info.n_items = hd.n_items;
+    p->info.tile_words = hd.tile_words;
+    p->info.warp_words = hd.warp_words;
     p->info.workspace_bytes = p->ws_bytes;
     p->info.image_bytes = p->image_bytes;
     p->info.model_bytes = model;
