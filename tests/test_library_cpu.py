@@ -405,3 +405,30 @@ def test_parallel_planner_equals_the_host_planner(n, stage):
         H.hedl_tuning_set(hk, stage_fillers=0)
         plain = H.hedl_plan_info_get(H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs), F))
         assert staged["n_segments"] > plain["n_segments"]
+
+
+def test_bitonic_step_sorts_on_the_host(tmp_path):
+    """The device planner's sort is a bitonic network over the padded unique keys (the host driver
+    uses std::sort): run the network's compare-exchange step on the host and check it sorts."""
+    src = tmp_path / "bitonic.cu"
+    src.write_text('#include "devplan.cu"\n#include <algorithm>\n#include <cstdio>\n#include <random>\n'
+                   "int main() {\n"
+                   "  std::mt19937_64 g(7);\n"
+                   "  for (uint64_t n : {1ull, 2ull, 3ull, 5ull, 100ull, 1000ull, 4099ull}) {\n"
+                   "    const uint64_t n2 = hedl::dp::pow2_at_least(n);\n"
+                   "    std::vector<uint64_t> k(n2, ~0ull), ref(n);\n"
+                   "    for (uint64_t i = 0; i < n; ++i) ref[i] = k[i] = (g() >> 8) << 8 | (i & 255);\n"
+                   "    for (uint64_t kk = 2; kk <= n2; kk <<= 1)\n"
+                   "      for (uint64_t j = kk >> 1; j > 0; j >>= 1)\n"
+                   "        for (uint64_t i = 0; i < n2; ++i) hedl::dp::bitonic_step(k.data(), i, j, kk);\n"
+                   "    std::sort(ref.begin(), ref.end());\n"
+                   "    for (uint64_t i = 0; i < n; ++i) if (k[i] != ref[i]) { printf(\"bad %llu\\n\", (unsigned long long)n); return 1; }\n"
+                   "  }\n  printf(\"ok\\n\");\n  return 0;\n}\n")
+    exe = tmp_path / "bitonic"
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    libdir = os.path.dirname(H.LIB_PATH)
+    subprocess.check_call([nvcc, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"), "-I",
+                           os.path.join(ROOT, "paper_2412_00802_gb300", "csrc"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lhedl", "-Xlinker", f"-rpath={libdir}"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out
