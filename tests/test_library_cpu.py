@@ -432,3 +432,44 @@ def test_bitonic_step_sorts_on_the_host(tmp_path):
                            "-L", libdir, "-lhedl", "-Xlinker", f"-rpath={libdir}"])
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out
+
+
+def test_device_validation_agrees_with_the_host(tmp_path):
+    """The device planner validates programs with dp::validate (codes, no messages); on random and
+    malformed programs it decides as hedl_validate does (run on the host through the library)."""
+    src = tmp_path / "validate.cu"
+    src.write_text('#include "devplan.cu"\n#include <cstdio>\n#include <random>\n'
+                   "int main() {\n"
+                   "  hedl_csr roles[3] = {{0, 0, 10}, {0, 0, 10}, {0, 0, 10}};\n"
+                   "  hedl_numeric_role nums[2] = {{0, 0, 5}, {0, 0, 5}};\n"
+                   "  hedl_string_role strs[2] = {{0, 0, 5}, {0, 0, 5}};\n"
+                   "  hedl_kb_desc d = {0};\n"
+                   "  d.n_indiv = 1000; d.n_concepts = 7; d.n_roles = 3; d.roles = roles; d.inv_roles = roles;\n"
+                   "  d.n_props = 2; d.n_num_roles = 2; d.num_roles = nums; d.n_str_roles = 2; d.str_roles = strs;\n"
+                   "  d.n_strings = 9; d.n_patterns = 4;\n"
+                   "  hedl_kb *kb = 0; if (hedl_kb_plan_only(&d, &kb)) return 2;\n"
+                   "  std::mt19937_64 g(11); int agree = 0, bad = 0;\n"
+                   "  for (int it = 0; it < 20000; ++it) {\n"
+                   "    std::vector<uint64_t> p(1 + g() % 12);\n"
+                   "    for (auto &w : p) {\n"
+                   "      const uint64_t op = 1 + g() % 17, a = g() % 9, b = g() % 6;\n"
+                   "      w = op | ((g() % 2) << 8) | (a << 16) | (b << 32);\n"
+                   "    }\n"
+                   "    const uint32_t offs[2] = {0, (uint32_t)p.size()};\n"
+                   "    hedl::dp::Ctx c{}; c.progs = p.data(); c.offs = offs; c.H = 1;\n"
+                   "    c.n_concepts = 7; c.n_roles = 3; c.n_data = 4; c.n_str = 2; c.n_patterns = 4;\n"
+                   "    const bool dev = hedl::dp::validate(c, 0, (uint32_t)p.size()) == 0;\n"
+                   "    const bool host = hedl_validate(kb, p.data(), (uint32_t)p.size()) == 0;\n"
+                   "    if (dev != host) { if (++bad < 4) printf(\"disagree at %d\\n\", it); } else agree += dev;\n"
+                   "  }\n"
+                   "  hedl_kb_free(kb);\n"
+                   "  printf(bad ? \"bad\\n\" : \"ok %d\\n\", agree);\n  return bad ? 1 : 0;\n}\n")
+    exe = tmp_path / "validate"
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    libdir = os.path.dirname(H.LIB_PATH)
+    subprocess.check_call([nvcc, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"), "-I",
+                           os.path.join(ROOT, "paper_2412_00802_gb300", "csrc"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lhedl", "-Xlinker", f"-rpath={libdir}"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.startswith("ok"), out
+    assert int(out.stdout.split()[1]) > 100   # some random programs are valid, so both branches are seen
