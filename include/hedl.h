@@ -282,7 +282,10 @@ void hedl_plan_free(hedl_plan *p);
  * reduction or a stable sort, the form a device-side planner takes.  The
  * image equals hedl_plan_batch's for those flags, byte for byte.  flags may
  * add HEDL_NO_GRAPH or HEDL_LEVELS; HEDL_PLAIN and HEDL_SLICE_ALL are refused
- * (HEDL_ERR_INVALID_ARG).  Host-only; HOST progs / offs as in hedl_plan_batch. */
+ * (HEDL_ERR_INVALID_ARG), and so is a batch whose plan would have more than
+ * 16,384 dependency levels (a chain of that many nested role restrictions),
+ * which hedl_plan_batch still plans.  Host-only; HOST progs / offs as in
+ * hedl_plan_batch. */
 int hedl_plan_batch_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
                              unsigned flags, uint32_t n_threads, hedl_plan **out);
 
@@ -344,8 +347,10 @@ int hedl_eval_concept(hedl_kb *kb, const uint64_t *prog, uint32_t len, uint32_t 
  *     and flags HEDL_NO_GRAPH tells) is rejected with
  *     HEDL_ERR_WORKSPACE_TOO_SMALL before anything is launched.
  *   - Set-up: the first call on each device (that device current) looks up
- *     the array's device address; make that first call before any stream
- *     capture.
+ *     the array's device address and remembers it with the device's current
+ *     context; after cudaDeviceReset the next call looks it up again.  Make
+ *     the first call on a device, and the first after a reset, before any
+ *     stream capture.
  *   - Sharing: every call uses the same array and brings its own zeroed
  *     counters, so nothing carries over between calls; calls whose GPU work
  *     overlaps race on the array and must be ordered by the caller.

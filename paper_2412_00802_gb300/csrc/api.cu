@@ -470,8 +470,11 @@ int cached_plan(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32
     if (H == 0) return fail(HEDL_ERR_INVALID_ARG, "empty batch (H = 0)");
     uint64_t h = hash_programs(progs, offs, H);
     if (kb->cached && kb->cached_hash == h && kb->cached_flags == flags) {
+        // the hash only selects a candidate: the programs themselves must be the cached ones
         const PlanImpl *c = kb->cached->impl;
-        if (c->info.n_hyps == H && c->info.total_insns == offs[H]) {
+        if (c->info.n_hyps == H && c->info.total_insns == offs[H] && kb->cached_offs.size() == (size_t)H + 1 &&
+            memcmp(kb->cached_offs.data(), offs, 4ull * (H + 1)) == 0 &&
+            (offs[H] == 0 || memcmp(kb->cached_progs.data(), progs, 8ull * offs[H]) == 0)) {
             *out = c;
             return HEDL_OK;
         }
@@ -483,6 +486,8 @@ int cached_plan(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32
     kb->cached = np;
     kb->cached_hash = h;
     kb->cached_flags = flags;
+    kb->cached_offs.assign(offs, offs + H + 1);
+    kb->cached_progs.assign(progs, progs + offs[H]);
     *out = np->impl;
     return HEDL_OK;
 }

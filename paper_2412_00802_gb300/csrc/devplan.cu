@@ -265,8 +265,15 @@ struct HypCount {           // per hypothesis; scanned in place into offsets
 struct Totals {
     uint64_t n_slots, code_n, deps_n, NS, n_levels, WW, TW, n_tiles, n_groups, items;
     uint64_t off_segs, off_deps, off_code, off_ctr, ctr_words;   // set by finish_step
-    uint32_t err_hyp, err_code;
+    uint32_t err_hyp, err_code;   // first failing hypothesis (or ERR_BATCH) and its positive error code
 };
+
+// err_hyp of a failure of the batch as a whole rather than of one program.
+constexpr uint32_t ERR_BATCH = 0xFFFFFFFEu;
+// A sort key packs (level, role key, segment) into 14 + 18 + 32 bits, so a
+// plan may have at most 2^14 dependency levels (a chain of 16,384 nested role
+// restrictions); a deeper batch is refused rather than mis-sorted.
+constexpr uint64_t MAX_KEY_LEVELS = 1ull << 14;
 
 // Offsets of the image's tables, as the host planner lays them out (each
 // table 256-byte aligned after the header).
@@ -440,6 +447,11 @@ __host__ __device__ inline void shape_step(const Ctx &c) {
     if (t.err_hyp != 0xFFFFFFFFu) return;
     uint32_t n_levels = 0;
     for (uint64_t s = 0; s < t.NS; ++s) n_levels = c.seg_level[s] + 1 > n_levels ? c.seg_level[s] + 1 : n_levels;
+    if (n_levels > MAX_KEY_LEVELS) {
+        t.err_hyp = ERR_BATCH;
+        t.err_code = (uint32_t)-HEDL_ERR_INVALID_ARG;
+        return;
+    }
     for (uint32_t L = 0; L < n_levels; ++L) c.segs_at[L] = c.walks_at[L] = 0;
     for (uint64_t s = 0; s < t.NS; ++s) {
         c.segs_at[c.seg_level[s]]++;
@@ -678,6 +690,9 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
     if (tot.n_slots > REF_ID) return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^30 materialized intermediate sets");
     parallel_for(H, n_threads, [&](uint32_t h) { dp::write_step(c, h); });
     dp::shape_step(c);
+    if (tot.err_hyp == dp::ERR_BATCH)
+        return fail(HEDL_ERR_INVALID_ARG, "batch too deep for the per-hypothesis planner: more than 16,384 dependency "
+                                          "levels (nested role restrictions); plan it with hedl_plan_batch");
     for (uint64_t i = 0; i < tot.NS; ++i) dp::key_step(c, i);
     std::sort(keys.get(), keys.get() + tot.NS);
     uint64_t G = 0;

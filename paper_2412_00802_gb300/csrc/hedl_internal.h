@@ -201,6 +201,8 @@ struct hedl_kb {
     hedl_plan *cached = nullptr;
     uint64_t cached_hash = 0;
     unsigned cached_flags = 0;
+    std::vector<uint64_t> cached_progs;     // the cached plan's programs, compared on a hash match
+    std::vector<uint32_t> cached_offs;
     hedl::KBView view() const;
 };
 

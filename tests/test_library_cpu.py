@@ -398,6 +398,22 @@ def test_parallel_planner_equals_the_host_planner(n, stage):
         with pytest.raises(H.HedlError) as e:
             H.hedl_plan_batch_parallel(hk, *P.pack_batch(progs[:3]), bad_flags)
         assert e.value.code == -1
+    if n == 3000 and not stage:
+        # A chain of nested restrictions makes one dependency level per link.  The sort key holds
+        # 14 bits of level: 16,000 links still plan identically, 17,000 are refused by the
+        # per-hypothesis planner (not mis-sorted) and still planned by the host planner.
+        for links, ok in ((16_000, True), (17_000, False)):
+            chain = [P.insn(P.ATOM, 0, 1)] + [P.insn(P.EXISTS, 0, 0)] * links
+            batch = P.pack_batch([np.array(chain, np.uint64)] + progs[:3])
+            a = H.hedl_plan_batch(hk, *batch, F)
+            assert H.hedl_plan_info_get(a)["n_levels"] >= links
+            if ok:
+                b = H.hedl_plan_batch_parallel(hk, *batch, F, n_threads=2)
+                assert np.array_equal(H.hedl_plan_image(a), H.hedl_plan_image(b))
+            else:
+                with pytest.raises(H.HedlError) as e:
+                    H.hedl_plan_batch_parallel(hk, *batch, F, n_threads=2)
+                assert e.value.code == -1 and "16,384 dependency levels" in str(e.value)
     if stage:   # staging split restrictions into more segments than without
         r2 = Rng(6, 1)
         progs = [np.array(pins.random_program(r2, kb, 6).postfix(), np.uint64) for _ in range(200)]
@@ -461,6 +477,18 @@ def test_device_validation_agrees_with_the_host(tmp_path):
                    "    const bool dev = hedl::dp::validate(c, 0, (uint32_t)p.size()) == 0;\n"
                    "    const bool host = hedl_validate(kb, p.data(), (uint32_t)p.size()) == 0;\n"
                    "    if (dev != host) { if (++bad < 4) printf(\"disagree at %d\\n\", it); } else agree += dev;\n"
+                   "  }\n"
+                   "  // the stack limit's edge: 64 operands on the stack are legal, 65 are not, both ways\n"
+                   "  for (int depth = 63; depth <= 66; ++depth) {\n"
+                   "    std::vector<uint64_t> p;\n"
+                   "    for (int i = 0; i < depth; ++i) p.push_back(1 | (uint64_t)(i % 7) << 16);\n"
+                   "    for (int i = 1; i < depth; ++i) p.push_back(5);\n"
+                   "    const uint32_t offs[2] = {0, (uint32_t)p.size()};\n"
+                   "    hedl::dp::Ctx c{}; c.progs = p.data(); c.offs = offs; c.H = 1;\n"
+                   "    c.n_concepts = 7; c.n_roles = 3; c.n_data = 4; c.n_str = 2; c.n_patterns = 4;\n"
+                   "    const bool dev = hedl::dp::validate(c, 0, (uint32_t)p.size()) == 0;\n"
+                   "    const bool host = hedl_validate(kb, p.data(), (uint32_t)p.size()) == 0;\n"
+                   "    if (dev != host || dev != (depth <= 64)) { ++bad; printf(\"depth %d: dev %d host %d\\n\", depth, dev, host); }\n"
                    "  }\n"
                    "  hedl_kb_free(kb);\n"
                    "  printf(bad ? \"bad\\n\" : \"ok %d\\n\", agree);\n  return bad ? 1 : 0;\n}\n")
