@@ -89,8 +89,12 @@ def load(path: str):
     L.oracle_eval.restype = ctypes.c_int
     L.oracle_score.argtypes = [ctypes.c_int64, P, P, P, P]
     L.oracle_score.restype = None
-    L.oracle_eval_batch.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int32, P, P, P]
+    L.oracle_eval_batch.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int32, P, P, P, P]
     L.oracle_eval_batch.restype = ctypes.c_int64
+    L.oracle_eval_bytes.argtypes = [P, P, ctypes.c_int64, P, P]
+    L.oracle_eval_bytes.restype = ctypes.c_int
+    L.oracle_score_bytes.argtypes = [ctypes.c_int64]
+    L.oracle_score_bytes.restype = ctypes.c_int64
     return L
 
 
@@ -302,18 +306,36 @@ def score(okb: OracleKB, r: np.ndarray, L=None) -> np.ndarray:
 
 
 def eval_batch(okb: OracleKB, progs: np.ndarray, offs: np.ndarray, threads: int = 1,
-               keep_sets: bool = False, L=None) -> Tuple[np.ndarray, Optional[np.ndarray], np.ndarray]:
-    """Evaluate and score a batch: returns counts int64[H][4], sets uint8[H][n] or None, errs."""
+               keep_sets: bool = False, L=None, bytes_out: Optional[np.ndarray] = None
+               ) -> Tuple[np.ndarray, Optional[np.ndarray], np.ndarray]:
+    """Evaluate and score a batch: returns counts int64[H][4], sets uint8[H][n] or None, errs.
+    bytes_out (int64[H], optional) receives each program's algorithmic bytes, score included."""
     progs = np.ascontiguousarray(progs, dtype=np.uint64)
     offs64 = np.ascontiguousarray(offs, dtype=np.int64)
     H = offs64.size - 1
     counts = np.zeros((H, 4), dtype=np.int64)
     errs = np.zeros(H, dtype=np.int32)
     sets = np.zeros((H, okb.n), dtype=np.uint8) if keep_sets else None
+    if bytes_out is not None:
+        assert bytes_out.dtype == np.int64 and bytes_out.shape == (H,) and bytes_out.flags.c_contiguous
     (L or lib()).oracle_eval_batch(okb.cptr, _ptr(progs) if progs.size else None, _ptr(offs64), H,
                             _ptr(okb.pos), _ptr(okb.neg), threads, _ptr(counts),
-                            _ptr(sets) if sets is not None else None, _ptr(errs))
+                            _ptr(sets) if sets is not None else None, _ptr(errs),
+                            _ptr(bytes_out) if bytes_out is not None else None)
     return counts, sets, errs
+
+
+def model_bytes(okb: OracleKB, prog, L=None) -> int:
+    """Algorithmic bytes of one program (its operations as the evaluator runs them, plus its
+    score): the plain method's per-operation byte model, counted while evaluating."""
+    p = np.ascontiguousarray(prog, dtype=np.uint64)
+    out = np.zeros(max(okb.n, 1), dtype=np.uint8)
+    b = ctypes.c_int64(0)
+    lb = L or lib()
+    e = lb.oracle_eval_bytes(okb.cptr, _ptr(p) if p.size else None, p.size, _ptr(out), ctypes.byref(b))
+    if e:
+        raise ValueError(ERRORS.get(e, str(e)))
+    return int(b.value) + int(lb.oracle_score_bytes(okb.n))
 
 
 def accuracy_f1(counts: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:

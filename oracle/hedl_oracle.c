@@ -263,8 +263,57 @@ static void op_string(const oracle_kb *kb, unsigned op, unsigned s, uint32_t b, 
     }
 }
 
-/* Evaluate one postfix program; out receives n bytes (0/1). */
+/* ------------------------------------------------------ byte model */
+/* The algorithmic bytes of the plain method, per operation as it is
+ * evaluated (no credit for sharing or caches).  A set is a row of 32-bit
+ * words, W = ceil(n / 32) of them, padded to Wp = a multiple of 4, so one
+ * set is B = 4 Wp bytes.  Per operation:
+ *   ATOM                 B      (its row is read)
+ *   TOP BOT NOT AND OR   0      (operands are counted at their leaves)
+ *   role restriction     4(n+1) + 4 E_r + 2B   (row pointers, the E_r
+ *                        assertions of the role, the filler written and
+ *                        read; either direction)
+ *   DGE DLE DEQ          4n on a one-value property; 4(n+1) + 4M on a
+ *                        numeric concrete role with M assertions
+ *   SEQ                  4(n+1) + 4M on a string role with M assertions
+ *   SCONTAINS            the same + 4 ceil(S / 32) (the pattern's row of
+ *                        the containment bitmap over the S table strings)
+ *   score (per program)  2B + 16 (the example sets, four counts) */
+static int64_t set_bytes(int64_t n) {
+    int64_t w = (n + 31) / 32;
+    int64_t wp = (w + 3) / 4 * 4;
+    return 4 * wp;
+}
+
+static int64_t op_bytes(const oracle_kb *kb, uint64_t insn) {
+    const unsigned op = op_of(insn), a = a_of(insn);
+    const int64_t n = kb->n, B = set_bytes(n);
+    switch (op) {
+    case O_ATOM: return B;
+    case O_TOP: case O_BOT: case O_NOT: case O_AND: case O_OR: return 0;
+    case O_EXISTS: case O_FORALL: case O_ATLEAST: case O_ATMOST: case O_EXACTLY:
+        return 4 * (n + 1) + 4 * (kb->role_off[a + 1] - kb->role_off[a]) + 2 * B;
+    case O_DGE: case O_DLE: case O_DEQ:
+        if ((int32_t)a < kb->n_props) return 4 * n;
+        return 4 * (n + 1) + 4 * (kb->num_off[a - kb->n_props + 1] - kb->num_off[a - kb->n_props]);
+    case O_SEQ: return 4 * (n + 1) + 4 * (kb->str_off[a + 1] - kb->str_off[a]);
+    case O_SCONTAINS:
+        return 4 * (n + 1) + 4 * (kb->str_off[a + 1] - kb->str_off[a]) + 4 * ((kb->n_strings + 31) / 32);
+    default: return 0;
+    }
+}
+
+int64_t oracle_score_bytes(int64_t n) { return 2 * set_bytes(n) + 16; }
+
+/* Evaluate one postfix program; out receives n bytes (0/1).  With bytes != NULL
+ * the algorithmic bytes of its operations are added to *bytes as they run. */
+int oracle_eval_bytes(const oracle_kb *kb, const uint64_t *prog, int64_t len, uint8_t *out, int64_t *bytes);
+
 int oracle_eval(const oracle_kb *kb, const uint64_t *prog, int64_t len, uint8_t *out) {
+    return oracle_eval_bytes(kb, prog, len, out, NULL);
+}
+
+int oracle_eval_bytes(const oracle_kb *kb, const uint64_t *prog, int64_t len, uint8_t *out, int64_t *bytes) {
     int err = oracle_validate(kb, prog, len);
     if (err) return err;
     const int64_t n = kb->n;
@@ -279,6 +328,7 @@ int oracle_eval(const oracle_kb *kb, const uint64_t *prog, int64_t len, uint8_t 
         unsigned a = a_of(prog[k]);
         int inverse = (flags_of(prog[k]) & 1) != 0;
         int ar = arity(op);
+        if (bytes) *bytes += op_bytes(kb, prog[k]);
         if (ar == 0) {
             if (!stack[sp]) stack[sp] = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
             if (!stack[sp]) { err = OE_NOMEM; break; }
@@ -341,6 +391,7 @@ typedef struct {
     int64_t *counts;      /* [H][4] */
     uint8_t *sets;        /* [H][n] or NULL */
     int32_t *errs;        /* [H] */
+    int64_t *bytes;       /* [H] or NULL: algorithmic bytes, score included */
 } batch_job;
 
 static void *batch_worker(void *arg) {
@@ -349,10 +400,12 @@ static void *batch_worker(void *arg) {
     uint8_t *r = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     for (int64_t h = j->h_begin; h < j->h_end; ++h) {
         uint8_t *dst = j->sets ? j->sets + h * n : r;
-        int e = r ? oracle_eval(j->kb, j->progs + j->offs[h], j->offs[h + 1] - j->offs[h], dst) : OE_NOMEM;
+        int64_t b = 0;
+        int e = r ? oracle_eval_bytes(j->kb, j->progs + j->offs[h], j->offs[h + 1] - j->offs[h], dst, &b) : OE_NOMEM;
         j->errs[h] = e;
         if (e == OE_OK) oracle_score(n, dst, j->pos, j->neg, j->counts + 4 * h);
         else memset(j->counts + 4 * h, 0, 4 * sizeof(int64_t));
+        if (j->bytes) j->bytes[h] = e == OE_OK ? b + oracle_score_bytes(n) : 0;
     }
     free(r);
     return NULL;
@@ -360,17 +413,18 @@ static void *batch_worker(void *arg) {
 
 /* Evaluate and score H programs on n_threads host threads (hypotheses split
  * into equal contiguous shares).  Returns the number of programs that failed
- * validation; their error codes are in errs. */
+ * validation; their error codes are in errs.  bytes (NULL or [H]) receives
+ * each program's algorithmic bytes, its score included. */
 int64_t oracle_eval_batch(const oracle_kb *kb, const uint64_t *progs, const int64_t *offs, int64_t H,
                           const uint8_t *pos, const uint8_t *neg, int32_t n_threads,
-                          int64_t *counts, uint8_t *sets, int32_t *errs) {
+                          int64_t *counts, uint8_t *sets, int32_t *errs, int64_t *bytes) {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > H) n_threads = H > 0 ? (int32_t)H : 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
     batch_job *jobs = (batch_job *)malloc(sizeof(batch_job) * (size_t)n_threads);
     for (int32_t t = 0; t < n_threads; ++t) {
         jobs[t] = (batch_job){kb, progs, offs, H * t / n_threads, H * (t + 1) / n_threads, pos, neg,
-                              counts, sets, errs};
+                              counts, sets, errs, bytes};
         if (n_threads == 1) batch_worker(&jobs[t]);
         else pthread_create(&th[t], NULL, batch_worker, &jobs[t]);
     }

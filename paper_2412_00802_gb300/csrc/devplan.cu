@@ -194,8 +194,9 @@ __host__ __device__ inline SegInfo emit(const uint64_t *progs, uint32_t o0, cons
                 s.n_data++;
             } else {   // role restriction
                 const uint32_t c = (uint32_t)sc.k0[i], inv = inv_of(w), a = a_of(w);
-                const uint32_t ref = (op_of(progs[c]) == HEDL_OP_ATOM && !sc.mat[c]) ? a_of(progs[c])
-                                                                                      : (REF_SLOT | read(c));
+                const bool atom = op_of(progs[c]) == HEDL_OP_ATOM && !sc.mat[c];
+                const uint32_t ref = atom ? a_of(progs[c]) : (REF_SLOT | read(c));
+                if (atom) s.model += z.B;   // the filler concept's row
                 put(D_ROLE | (inv << 8) | (op << 16), a, is_count(op) ? b_of(w) : 0u, ref);
                 if (s.key == NO_FILLER) s.key = a * 2 + inv;
                 if (s.filler == NO_FILLER) s.filler = ref | (op == HEDL_OP_FORALL ? REF_NEG : 0u);

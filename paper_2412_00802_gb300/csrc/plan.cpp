@@ -381,10 +381,10 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     std::vector<uint32_t> seg_of_slot(n_slots, 0);
     std::vector<uint32_t> role_key;  // first role read, for grouping
     // Algorithmic bytes, the per-operation model (no credit for sharing a CSR
-    // walk or for caches): an atom read B, a data range 4N, a role
-    // restriction 4(N+1) + 4E + 2B (row pointers, columns, filler written and
-    // read), a hypothesis score 2B + 16, over the operations left after
-    // common sub-concepts are shared.
+    // walk or for caches): an atom read B (a role restriction's filler concept
+    // included), a data range 4N, a role restriction 4(N+1) + 4E + 2B (row
+    // pointers, columns, filler written and read), a hypothesis score
+    // 2B + 16, over the operations left after common sub-concepts are shared.
     uint64_t model = 0;
 
     std::vector<int32_t> work;
@@ -437,8 +437,10 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                     d.op = D_ROLE | ((uint32_t)n.inv << 8) | ((uint32_t)n.op << 16);
                     d.a = n.a;
                     d.b = n.b;
-                    if (nodes[c].op == HEDL_OP_ATOM && !mat[c]) d.ref = nodes[c].a;
-                    else {
+                    if (nodes[c].op == HEDL_OP_ATOM && !mat[c]) {
+                        d.ref = nodes[c].a;
+                        model += B;   // the filler concept's row: an atom leaf of the plain method
+                    } else {
                         d.ref = REF_SLOT | slot_of[c];
                         reads.push_back(slot_of[c]);
                     }
@@ -579,6 +581,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                 const uint32_t s_ = (uint32_t)(q - k);
                 if (nodes[f].op == HEDL_OP_ATOM && !mat[f]) {
                     g.filler[s_] = nodes[f].a;
+                    model += B;   // the filler concept's row
                 } else {
                     g.filler[s_] = REF_SLOT | slot_of[f];
                     reads.push_back(slot_of[f]);

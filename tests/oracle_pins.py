@@ -480,5 +480,75 @@ def pin_validation(L) -> List[str]:
     return bad
 
 
+def _bytes_kb(n: int):
+    """A hand-built KB for the byte model: 2 concepts, role 0 with 7 assertions and role 1 with 3,
+    one one-value property, numeric role 0 with 5 values, string role 0 with 4 values, a table of
+    40 strings and 2 patterns."""
+    z = np.zeros(n, np.uint8)
+    r0 = (np.array([0, 0, 1, 2, 3, 5, 9]) % n, np.array([1, 2, 0, 4, 4, 6, 8]) % n)
+    r1 = (np.array([0, 2, 7]) % n, np.array([3, 3, 7]) % n)
+    if n < 10:   # keep the pairs a set on tiny KBs
+        r0 = (np.array([0, 0, 1, 2, 3, 4, 5])[:7] % n, np.array([1, 2, 0, 4, 4, 6, 8])[:7] % n)
+        keys = sorted(set(zip(r0[0].tolist(), r0[1].tolist())))
+        r0 = (np.array([a for a, _ in keys]), np.array([b for _, b in keys]))
+        keys = sorted(set(zip(r1[0].tolist(), r1[1].tolist())))
+        r1 = (np.array([a for a, _ in keys]), np.array([b for _, b in keys]))
+    strings = [bytes([97 + i % 26, 98 + i // 26]) for i in range(40)]
+    return oracle.OracleKB.from_parts(
+        n, np.zeros((2, n), np.uint8), [r0, r1], np.zeros((1, n), np.float32), z, z,
+        num_roles=[(np.arange(5) % n, np.arange(5, dtype=np.float32))],
+        str_roles=[(np.arange(4) % n, [b"ab", b"cb", b"xx", b""])], strings=strings, patterns=[b"a", b"b"])
+
+
+def pin_byte_model(L) -> List[str]:
+    """The algorithmic-byte model of the plain method (per operation, no sharing credit), counted
+    by the oracle while it evaluates.  Pinned to values worked by hand from the per-operation table
+    (a set is B = 4 Wp bytes, Wp = ceil(n / 32) rounded up to a multiple of 4; a role restriction
+    reads 4(n+1) row-pointer bytes and 4 bytes per assertion of its role and writes and reads its
+    filler, 2B; a one-value data restriction reads 4n; a concrete-role restriction 4(n+1) + 4M,
+    SCONTAINS also its bitmap row of 4 ceil(S / 32); the score 2B + 16), and to its invariants:
+    Boolean operators cost nothing beyond their operands, an inverse costs what its forward role
+    does, and B steps at multiples of 128 individuals."""
+    bad = []
+    t = P.f32_bits(1.0)
+    # n = 100: W = 4, Wp = 4, B = 16; score 48; role 0: 404 + 28 + 32 = 464; role 1: 404 + 12 + 32 = 448
+    okb = _bytes_kb(100)
+    hand = [("A0", 64), ("(some r0 A0)", 528), ("(some r0- A0)", 528), ("(all r1 A1)", 512),
+            ("(not (and A0 A1))", 80), ("(or A0 (not A0))", 80), ("TOP", 48), ("(not BOT)", 48),
+            ("(min 2 r0 (some r1 A1))", 976), ("(max 1 r1- (exactly 3 r0 A1))", 976)]
+    for text, want in hand:
+        got = oracle.model_bytes(okb, P.compile_text(text), L=L)
+        if got != want:
+            bad.append(f"byte model n=100 {text}: {got} != {want}")
+    leaves = [([P.insn(P.DGE, 0, 0, t)], 448),                 # 4n + 48
+              ([P.insn(P.DLE, 0, 1, t)], 472),                 # numeric role: 404 + 20 + 48
+              ([P.insn(P.SEQ, 0, 0, 1)], 468),                 # 404 + 16 + 48
+              ([P.insn(P.SCONTAINS, 0, 0, 1)], 476)]           # 404 + 16 + 4 * 2 + 48
+    for prog, want in leaves:
+        got = oracle.model_bytes(okb, prog, L=L)
+        if got != want:
+            bad.append(f"byte model n=100 leaf {P.fields(prog[0])}: {got} != {want}")
+    # B = 16 up to 128 individuals, 32 from 129 (W = 5 words pad to 8): an atom costs B, its score 2B + 16
+    for n, want in ((1, 64), (128, 64), (129, 112), (513, 256)):
+        got = oracle.model_bytes(_bytes_kb(n), P.compile_text("A0"), L=L)
+        if got != want:
+            bad.append(f"byte model n={n} A0: {got} != {want}")
+    # invariants on a generated KB: Boolean operators add nothing, inverse = forward, the role
+    # term differs between roles by 4 bytes per assertion
+    kb = K.generate(K.CONFIGS["small"].scaled(3000, seed=47, n_concepts=6, n_roles=3))
+    okb = oracle.from_synth(kb)
+    mb = lambda x: oracle.model_bytes(okb, P.compile_text(x), L=L)
+    score = mb("TOP")
+    for x, y in (("A1", "(some r0 A2)"), ("(min 2 r1 A3)", "(all r2- (or A0 A4))")):
+        if mb(f"(and {x} {y})") != mb(x) + mb(y) - score or mb(f"(or {x} (not {y}))") != mb(x) + mb(y) - score:
+            bad.append(f"byte model: Boolean operators over {x}, {y} are not free")
+    for r in range(kb.n_roles):
+        if mb(f"(some r{r}- A0)") != mb(f"(some r{r} A0)"):
+            bad.append(f"byte model: inverse of r{r} differs")
+    if mb("(some r1 A0)") - mb("(some r0 A0)") != 4 * (kb.n_edges(1) - kb.n_edges(0)):
+        bad.append("byte model: role terms do not differ by 4 bytes per assertion")
+    return bad
+
+
 ALL_PINS = (pin_golden, pin_brute_force, pin_identities, pin_inverse_transpose, pin_closed_forms,
-            pin_numeric_roles, pin_string_roles, pin_validation)
+            pin_numeric_roles, pin_string_roles, pin_validation, pin_byte_model)

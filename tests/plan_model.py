@@ -136,6 +136,7 @@ class Hyp:
                 c = k0
                 if nodes[c][0] == P.ATOM and not mat[c]:
                     ref = nodes[c][2]
+                    model += B                      # the filler concept's row
                 else:
                     ref = ("slot", self.slot_of[c])
                     reads.append(self.slot_of[c])

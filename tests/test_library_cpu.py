@@ -501,3 +501,37 @@ def test_device_validation_agrees_with_the_host(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.startswith("ok"), out
     assert int(out.stdout.split()[1]) > 100   # some random programs are valid, so both branches are seen
+
+@pytest.mark.parametrize("n", [3000, 641])
+def test_plan_byte_model_equals_the_oracles_count(n):
+    """The algorithmic bytes a plan reports (plan.cpp, devplan.cu) are the oracle's per-operation
+    count, taken while it evaluates (oracle/hedl_oracle.c): equal, program by program summed,
+    whenever nothing is shared (HEDL_NO_CSE, with or without bit slicing, per-level launches, the
+    plain path, the per-hypothesis planner); with sharing the plan counts each common sub-concept
+    once, so never more.  The plan-only handle has the sizes of the KB the oracle evaluates on."""
+    import oracle
+    kb = K.generate(K.CONFIGS["small"].scaled(n, seed=5, n_num_roles=2, n_str_roles=2,
+                                              n_strings=50, n_patterns=6))
+    okb = oracle.from_synth(kb)
+    hk = H.hedl_kb_plan_only(kb.n, kb.n_concepts, [kb.n_edges(r) for r in range(kb.n_roles)], kb.n_props,
+                             num_role_vals=[v.size for v in kb.num_vals], str_role_vals=[v.size for v in kb.str_ids],
+                             n_strings=len(kb.strings), n_patterns=kb.n_patterns)
+    r = Rng(31, n % 97)
+    exact = [H.HEDL_NO_CSE, H.HEDL_NO_CSE | H.HEDL_NO_SLICE, H.HEDL_NO_CSE | H.HEDL_SLICE_ALL,
+             H.HEDL_NO_CSE | H.HEDL_LEVELS, H.HEDL_PLAIN]
+    for it in range(12):
+        progs = [np.array(pins.random_program(r, kb, r.randint(1, 8)).postfix(), np.uint64)
+                 for _ in range(r.randint(1, 60))]
+        if it % 4 == 0:
+            progs += hyps.small_hyps(kb, it, 30)
+        flat, offs = P.pack_batch(progs)
+        per = np.zeros(len(progs), np.int64)
+        _, _, errs = oracle.eval_batch(okb, flat, offs, threads=4, bytes_out=per)
+        assert not errs.any()
+        want = int(per.sum())
+        for f in exact:
+            assert H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, f))["model_bytes"] == want, (it, f)
+        par = H.hedl_plan_batch_parallel(hk, flat, offs, H.HEDL_NO_CSE | H.HEDL_NO_SLICE, n_threads=2)
+        assert H.hedl_plan_info_get(par)["model_bytes"] == want
+        for f in (0, H.HEDL_NO_SLICE, H.HEDL_SLICE_ALL):
+            assert H.hedl_plan_info_get(H.hedl_plan_batch(hk, flat, offs, f))["model_bytes"] <= want, (it, f)

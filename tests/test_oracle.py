@@ -74,6 +74,19 @@ MUTANTS = {
                                "for (int64_t k = kb->str_off[0]; k < kb->str_off[1]; ++k) {"),
     "validate_depth_off_by_one": ("if (depth > ORACLE_MAX_STACK) return OE_OVERFLOW;",
                                   "if (depth >= ORACLE_MAX_STACK) return OE_OVERFLOW;"),
+    # the byte model (the per-operation table of algorithmic bytes)
+    "bytes_filler_read_only": ("+ 4 * (kb->role_off[a + 1] - kb->role_off[a]) + 2 * B;",
+                               "+ 4 * (kb->role_off[a + 1] - kb->role_off[a]) + B;"),
+    "bytes_first_role_edges": ("+ 4 * (kb->role_off[a + 1] - kb->role_off[a]) + 2 * B;",
+                               "+ 4 * (kb->role_off[1] - kb->role_off[0]) + 2 * B;"),
+    "bytes_row_pointers_n": ("return 4 * (n + 1) + 4 * (kb->role_off[a + 1]", "return 4 * n + 4 * (kb->role_off[a + 1]"),
+    "bytes_atom_free": ("case O_ATOM: return B;", "case O_ATOM: return 0;"),
+    "bytes_unpadded_rows": ("int64_t wp = (w + 3) / 4 * 4;", "int64_t wp = w;"),
+    "bytes_score_one_set": ("return 2 * set_bytes(n) + 16;", "return set_bytes(n) + 16;"),
+    "bytes_column_plus_one": ("if ((int32_t)a < kb->n_props) return 4 * n;", "if ((int32_t)a < kb->n_props) return 4 * (n + 1);"),
+    "bytes_contain_no_bitmap": ("+ 4 * ((kb->n_strings + 31) / 32);", ";"),
+    "bytes_not_counts_a_set": ("case O_TOP: case O_BOT: case O_NOT: case O_AND: case O_OR: return 0;",
+                               "case O_NOT: return B;\n    case O_TOP: case O_BOT: case O_AND: case O_OR: return 0;"),
 }
 
 
