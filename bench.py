@@ -89,19 +89,23 @@ def mlp_forward_timing(s, X):
     flops = 2.0 * B * (512 * 512 * 2 + 512 * 2)
     peak, kind = measured_bf16_tflops()
     out = {"rows": B, "flops": flops, "peak_tflops": peak, "peak_kind": f"{kind} bf16 (MEASURED_PEAKS.json bf16_tflops)"}
-    for name, eng in (("tcgen05", H.HEDL_GEMM_TCGEN05), ("mma_sync", H.HEDL_GEMM_MMA_SYNC)):
+    stream = torch.cuda.current_stream(X.device)
+    for name, eng, reps in (("tcgen05", H.HEDL_GEMM_TCGEN05, 60), ("mma_sync", H.HEDL_GEMM_MMA_SYNC, 10)):
         H.hedl_mlp_set_gemm(s.mlp, eng)
-        for _ in range(3):
+        for _ in range(5):
             H.hedl_mlp_forward(s.mlp, X, Y, ws)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         torch.cuda.synchronize()
-        a.record()
-        for _ in range(10):
-            H.hedl_mlp_forward(s.mlp, X, Y, ws)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 10
-        out[name] = {"ms": ms, "tflops": flops / ms / 1e9, "frac": flops / ms / 1e9 / peak}
+        with ClockSampler(X.device.index or 0) as clk:
+            for a, b in ev:              # one forward per event pair; the median is reported
+                a.record(stream)
+                H.hedl_mlp_forward(s.mlp, X, Y, ws)
+                b.record(stream)
+            torch.cuda.synchronize()
+        t = sorted(a.elapsed_time(b) for a, b in ev)
+        ms = statistics.median(t)
+        out[name] = {"ms": ms, "tflops": flops / ms / 1e9, "frac": flops / ms / 1e9 / peak, "forwards": reps,
+                     "ms_min": t[0], "ms_max": t[-1], "clocks": clk.summary()}
     H.hedl_mlp_set_gemm(s.mlp, H.HEDL_GEMM_TCGEN05)
     H.hedl_mlp_status(s.mlp)
     return out
@@ -162,8 +166,9 @@ class ClockSampler:
 
 
 def traffic_for(workload_key: str, tuning: dict):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    interpreter sources with the same launch shape."""
+    """The committed ncu figures of the interpreter launch (profiles/traffic.json: DRAM bytes per
+    launch, and the L2 throughput share if captured), if they were taken on the current
+    interpreter sources with the same launch shape; else None (stale counters are not reused)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         from paper_2412_00802_gb300 import build
@@ -171,10 +176,19 @@ def traffic_for(workload_key: str, tuning: dict):
             d = json.load(f)
         e = d.get(workload_key)
         if e and e.get("interpreter_digest") == build.interpreter_digest() and e.get("tuning") == tuning:
-            return e["dram_bytes_per_launch"]
+            return e
     except Exception:
         pass
     return None
+
+
+def _r(x, nd: int = 4):
+    """A number rounded to nd significant digits (None stays None) for the compact summary."""
+    if x is None or isinstance(x, bool):
+        return x
+    if isinstance(x, int):
+        return x
+    return float(f"{x:.{nd}g}")
 
 
 def make_workload(seed_kb: int = 3):
@@ -284,6 +298,7 @@ def surrogate_round(args, dev):
     top_pred = np.argsort(-Y[:, 0].cpu().numpy(), kind="stable")[:100]
     return {"workload": ("planted KB with the single-hypothesis workload's distributions, N=" + f"{cfg.n:,}"
                          + f"; {n_train:,} engine-scored training hypotheses; 65,536 candidates, top 5 % scored"),
+            "n": cfg.n, "n_train": n_train,
             "kb_gen_s": gen_s, "train_scoring_s": score_s, "train_s": train_s, "train_loss": [losses[0], losses[-1]],
             "recall_at_100": OS.recall_at(100, order, sel), "recall_strict_top100": OS.recall_at(100, order, top_pred),
             "selected": k, "best_found": found, "best_acc": float(exact[best, 0]),
@@ -476,7 +491,8 @@ def search_run(args, dev):
         Ts.append(T)
     sur.train(torch.cat(Xs), torch.cat(Ts), epochs=40, batch=4096, lr=2e-3)
     out = {"workload": f"planted KB with the search workload's distributions, N={cfg.n:,}, {kb.n_roles} roles; "
-                       f"beam 64, 8,192 refinements per step, {steps} steps", "kb_gen_s": gen_s}
+                       f"beam 64, 8,192 refinements per step, {steps} steps", "kb_gen_s": gen_s,
+           "n": cfg.n, "steps": steps}
     res = {}
     state, tmap = sur.params().copy(), sur.target_map()
     online = {"online_epochs": 2, "online_window": 16384}
@@ -515,18 +531,14 @@ def search_run(args, dev):
     return out
 
 
-def run_latency(args, local_rank):
+def latency_measure(args, dev, tune: bool = True):
     """Single large hypothesis latency: the 10,000,000-individual KB (32 Zipf(2.1) roles,
     ~2.6 G assertions), 64 depth-6 hypotheses with chains of 3 nested EXISTS / ATLEAST,
     each evaluated alone through hedl_eval_concept (plan + upload + launch) and timed with
     CUDA events; algorithmic bytes per hypothesis from its plan."""
     import torch
     import paper_2412_00802_gb300 as H
-    from paper_2412_00802_gb300 import build
     from synth import hyps, kb as K, programs as P
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    build.build()
     t0 = time.perf_counter()
     cfg = K.CONFIGS["large"]
     if args.latency_n:                       # smaller KB of the same distributions (profiling)
@@ -536,7 +548,7 @@ def run_latency(args, local_rank):
     dkb = H.DeviceKB.from_synth(kb, device=str(dev))
     progs = hyps.chain_hyps(kb, 2002, 64)
     tune_s = None
-    if not args.no_tune:
+    if tune:
         # launch shape picked on another hypothesis of the same shape, evaluated alone
         t0 = time.perf_counter()
         dkb.autotune(*P.pack_batch(hyps.chain_hyps(kb, 2003, 1)))
@@ -547,7 +559,7 @@ def run_latency(args, local_rank):
         dkb.eval(p, args.flags)
     lat, model, host, replay, levels = [], [], [], [], []
     offs = lambda p: np.array([0, len(p)], np.uint32)
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(dev.index or 0) as clk:
         for p in progs:
             nbytes = H.hedl_workspace_size(dkb.handle, p, offs(p), args.flags)
             ws = dkb.workspace(nbytes)
@@ -576,22 +588,44 @@ def run_latency(args, local_rank):
     H.hedl_sync_status(dkb.handle)
     peak, kind = measured_peaks()
     gbs = [m / t / 1e9 for m, t in zip(model, lat)]
-    print(json.dumps({
-        "metric": "single-hypothesis latency", "value": 1000 * statistics.median(lat), "unit": "ms",
-        "higher_is_better": False, "n_gpus": 1, "steps": len(progs), "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "N=10,000,000 individuals, 200 concepts, 32 roles Zipf(2.1) mean 8 cap 10^4 + "
-                               "inverses, 16 props lognormal(0,1) 10% missing, 100k/100k examples; 64 depth-6 "
-                               "hypotheses with 3-chains of EXISTS/ATLEAST, one at a time", "kb_gen_s": gen_s,
-                   "n": kb.n, "flags": args.flags, "tuning": H.hedl_tuning_get(dkb.handle), "autotune_s": tune_s},
+    res = {
+        "workload": "N=10,000,000 individuals, 200 concepts, 32 roles Zipf(2.1) mean 8 cap 10^4 + inverses, "
+                    "16 props lognormal(0,1) 10% missing, 100k/100k examples; 64 depth-6 hypotheses with "
+                    "3-chains of EXISTS/ATLEAST, one at a time",
+        "n": kb.n, "kb_gen_s": gen_s, "flags": args.flags, "tuning": H.hedl_tuning_get(dkb.handle),
+        "autotune_s": tune_s,
         "latency_ms": {"median": 1000 * statistics.median(lat), "min": 1000 * min(lat), "max": 1000 * max(lat),
                        "host_call_median": 1000 * statistics.median(host),
                        "resident_replay_median": 1000 * statistics.median(replay)},
         "levels_median": statistics.median(levels),
-        "roofline": {"bound": "hbm", "achieved": statistics.median(gbs), "peak": peak, "unit": "GB/s",
-                     "frac": statistics.median(gbs) / peak, "traffic": None,
-                     "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "model_bytes_median": statistics.median(model)},
-        "clocks": clk.summary()}), flush=True)
+        "model": {"achieved_gbs": statistics.median(gbs), "peak": peak, "frac": statistics.median(gbs) / peak,
+                  "peak_kind": f"{kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                  "model_bytes_median": statistics.median(model)},
+        "clocks": clk.summary()}
+    del dkb
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_latency(args, local_rank):
+    """The single-hypothesis latency workload alone (one JSON line, time-like metric)."""
+    import torch
+    from paper_2412_00802_gb300 import build
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    build.build()
+    r = latency_measure(args, dev, tune=not args.no_tune)
+    print(json.dumps({
+        "metric": "single-hypothesis latency", "value": r["latency_ms"]["median"], "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": 64, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": r["workload"], "kb_gen_s": r["kb_gen_s"], "n": r["n"], "flags": r["flags"],
+                   "tuning": r["tuning"], "autotune_s": r["autotune_s"]},
+        "latency_ms": r["latency_ms"], "levels_median": r["levels_median"],
+        "roofline": {"bound": "hbm", "achieved": r["model"]["achieved_gbs"], "peak": r["model"]["peak"],
+                     "unit": "GB/s", "frac": r["model"]["frac"], "traffic": None,
+                     "peak_kind": r["model"]["peak_kind"], "model_bytes_median": r["model"]["model_bytes_median"],
+                     "note": "algorithmic bytes of the plan (byte model) / CUDA-event latency"},
+        "clocks": r["clocks"]}), flush=True)
 
 
 def run_mlp(args, local_rank):
@@ -659,7 +693,11 @@ def run_ours(args, rank, world, local_rank):
     gen = hyps.TreeGen(kb, 1003, share=0.3)
     warm_ids, timed_ids = shard_batches(rank, world, args.warmup, args.steps)
     ids = warm_ids + timed_ids
-    batches = {i: P.pack_batch(make_batch(kb, i, gen)) for i in ids}
+    if args.one_batch:            # profiling: every step replays the first timed batch on one workspace
+        one = P.pack_batch(make_batch(kb, timed_ids[0], gen))
+        batches = {i: one for i in ids}
+    else:
+        batches = {i: P.pack_batch(make_batch(kb, i, gen)) for i in ids}
     tune_s = None
     if not args.no_tune:
         # launch shape picked by the autotuner on a probe batch (not a timed one)
@@ -673,13 +711,16 @@ def run_ours(args, rank, world, local_rank):
     plans, infos, wss = {}, {}, {}
     plan_s = []
     for i in ids:
+        if args.one_batch and i != ids[0]:
+            plans[i], infos[i], wss[i] = plans[ids[0]], infos[ids[0]], wss[ids[0]]
+            continue
         t0 = time.perf_counter()
         plans[i] = H.hedl_plan_batch(dkb.handle, *batches[i], args.flags)
         plan_s.append(time.perf_counter() - t0)
         infos[i] = H.hedl_plan_info_get(plans[i])
         wss[i] = torch.empty(infos[i]["workspace_bytes"], dtype=torch.uint8, device=dev)
     counts = torch.zeros((BATCH, 4), dtype=torch.int32, device=dev)
-    for i in ids:
+    for i in (ids[:1] if args.one_batch else ids):
         H.hedl_plan_execute(dkb.handle, plans[i], counts, None, wss[i])
     H.hedl_sync_status(dkb.handle)
     for i in timed_ids:          # second execution: the plan's CUDA graph is captured here
@@ -714,11 +755,21 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     value = world * len(timed_ids) * BATCH / elapsed
 
-    # ---- roofline of the interpreter launch
+    # ---- roofline of the interpreter launch.  The kernel is timed by CUDA events on its stream;
+    # its DRAM bytes per launch come from the committed ncu capture of the same interpreter code
+    # and launch shape (profiles/traffic.json), so `achieved` is measured HBM traffic / time.  The
+    # plan's algorithmic bytes (the per-operation byte model, what the plain method would move)
+    # over the same time are the "effective" figure: far above the peak, since bit-sliced walks and
+    # L2 reuse read each role's arrays once for many restrictions.
     peak, peak_kind = measured_peaks()
     model = [infos[i]["model_bytes"] for i in timed_ids]
-    achieved = statistics.mean(m / (t / 1000.0) for m, t in zip(model, launch_ms)) / 1e9
-    traffic = traffic_for("batch", H.hedl_tuning_get(dkb.handle))
+    launch_s = statistics.mean(launch_ms) / 1000.0
+    effective = statistics.mean(m / (t / 1000.0) for m, t in zip(model, launch_ms)) / 1e9
+    tuning_now = H.hedl_tuning_get(dkb.handle)
+    prof = traffic_for("batch", tuning_now)
+    traffic = prof["dram_bytes_per_launch"] if prof else None
+    achieved = traffic / launch_s / 1e9 if traffic else None
+    l2_frac = prof.get("lts_throughput_pct", None) if prof else None
 
     # ---- end to end through the public C ABI from host programs: each step plans a batch
     # on the host (hedl_plan_batch), uploads and launches it (hedl_plan_execute) and copies
@@ -752,11 +803,12 @@ def run_ours(args, rank, world, local_rank):
     if dist:                                              # whole job: every rank's batches, slowest rank
         e2e_s = max_over_ranks(e2e_s, dev)
     H.hedl_sync_status(dkb.handle)
-    same = bool(torch.equal(pinned[(len(e2e_ids) - 1) & 1].to(dev), counts)) if e2e_ids[-1] == timed_ids[-1] else None
     e2e = {"value": world * len(e2e_ids) * BATCH / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(statistics.mean(h2d)), "d2h_bytes_per_step": BATCH * 16,
            "note": "host programs -> hedl_plan_batch -> hedl_plan_execute (plan upload + launch) -> counts to "
                    "pinned host memory, wall clock; the next batch is planned while the GPU runs the current one"}
+    del e2e_ws
+    torch.cuda.empty_cache()
 
     # ---- plain path (one launch per operation) on the first timed batch, and sharing off
     plain = None
@@ -773,7 +825,6 @@ def run_ours(args, rank, world, local_rank):
         b.record(stream)
         torch.cuda.synchronize()
         H.hedl_sync_status(dkb.handle)
-        same = bool(torch.equal(pcounts, counts)) if i == e2e_ids[-1] else None
         plain = {"value": BATCH / (a.elapsed_time(b) / 1000.0), "unit": UNIT}
         # verify the batched counts of that batch against the plain path
         H.hedl_plan_replay(dkb.handle, plans[i], counts, None, wss[i])
@@ -787,40 +838,88 @@ def run_ours(args, rank, world, local_rank):
         return
     cpu = None if args.no_cpu else cpu_baseline(kb, make_batch(kb, timed_ids[0], gen))
     clocks = clk.summary()
+    # the secondary workloads run on KBs of their own: free this one's device memory first
+    del wss, dkb
+    torch.cuda.empty_cache()
+    latency = None if args.no_latency else _section(latency_measure, args, dev, not args.no_tune)
     surrogate = None if args.no_surrogate else _section(surrogate_round, args, dev)
     search = None if args.no_search else _section(search_run, args, dev)
     numeric = None if args.no_numeric else _section(numeric_run, args, dev)
     strings = None if args.no_strings else _section(string_run, args, dev)
+    plan_info = {"host_ms_per_batch": 1000 * statistics.mean(plan_s), "segments": info0["n_segments"],
+                 "slots": info0["n_slots"], "levels": info0["n_levels"], "items": info0["n_items"],
+                 "role_ops": info0["n_role_ops"], "role_groups": info0["n_role_groups"],
+                 "role_ops_without_sharing": ncse["n_role_ops"],
+                 "model_bytes": info0["model_bytes"], "model_bytes_without_sharing": ncse["model_bytes"],
+                 "no_sharing_planners_ms": planners}
+    details = {"plain": plain, "plan": plan_info, "latency": latency, "surrogate": surrogate, "search": search,
+               "numeric_roles": numeric, "string_roles": strings,
+               "cpu_single_thread": cpu.get("single_thread") if cpu else None}
+    # every secondary workload in full, on one stderr line (the stdout line stays short)
+    print(json.dumps({"details": details}), file=sys.stderr, flush=True)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed_ids),
         "warmup": len(warm_ids), "ms_per_step": 1000.0 * elapsed / len(timed_ids), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": BATCH, "l2": "inputs larger than L2 (KB ~0.95 GB + workspaces)",
-                   "parallelism": f"replicas{world}", "flags": args.flags,
-                   "tuning": H.hedl_tuning_get(dkb.handle), "autotune_s": tune_s},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                   "parallelism": f"replicas{world}", "flags": args.flags, "one_batch": bool(args.one_batch),
+                   "tuning": tuning_now, "autotune_s": tune_s},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
+                     "l2_frac": l2_frac,
+                     "effective_gbs": effective, "effective_frac": effective / peak,
+                     "algorithmic_bytes_per_launch": statistics.mean(model),
+                     "launch_ms": statistics.mean(launch_ms),
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "kernel": "exec_kernel (persistent segment interpreter)",
-                     "model_bytes_per_launch": statistics.mean(model),
-                     "launch_ms": statistics.mean(launch_ms)},
-        "cpu_baseline": cpu,
+                     "note": "achieved = ncu DRAM bytes per launch (traffic) / CUDA-event launch time; "
+                             "effective = the plan's algorithmic bytes / the same time"},
+        "cpu_baseline": {k: v for k, v in cpu.items() if k != "single_thread"} if cpu else None,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": 2 * len(timed_ids),
-        "plain": plain,
-        "batched_vs_plain": (value / world / plain["value"]) if plain else None,
-        "plan": {"host_ms_per_batch": 1000 * statistics.mean(plan_s), "segments": info0["n_segments"],
-                 "slots": info0["n_slots"], "levels": info0["n_levels"], "items": info0["n_items"],
-                 "role_ops": info0["n_role_ops"], "role_ops_without_sharing": ncse["n_role_ops"],
-                 "model_bytes": info0["model_bytes"], "model_bytes_without_sharing": ncse["model_bytes"],
-                 "no_sharing_planners_ms": planners},
-        "effective_frac_unshared": value / world * (ncse["model_bytes"] / BATCH) / 1e9 / peak,
-        "surrogate": surrogate,
-        "search": search,
-        "numeric_roles": numeric,
-        "string_roles": strings,
+        "secondary": _summary(value / world, plain, plan_info, ncse, peak, latency, surrogate, search, numeric,
+                              strings, cpu),
     }
     print(json.dumps(out), flush=True)
+
+
+def _summary(value, plain, plan_info, ncse, peak, latency, surrogate, search, numeric, strings, cpu):
+    """The secondary figures, rounded, flat enough to survive a truncated stdout tail."""
+    def ok(x):
+        return x if isinstance(x, dict) and "error" not in x else None
+    out = {"batched_vs_plain": _r(value / plain["value"]) if plain else None,
+           "plain_hyp_s": _r(plain["value"]) if plain else None,
+           "plain_counts_identical": plain["counts_identical"] if plain else None,
+           "effective_frac_unshared": _r(value * (ncse["model_bytes"] / BATCH) / 1e9 / peak),
+           "plan_ms": _r(plan_info["host_ms_per_batch"]), "role_ops": plan_info["role_ops"],
+           "role_groups": plan_info["role_groups"],
+           "cpu_1thread_hyp_s": _r(cpu["single_thread"]["value"]) if cpu else None}
+    if ok(latency):
+        out["latency"] = {"n": latency["n"], "median_ms": _r(latency["latency_ms"]["median"]),
+                          "replay_ms": _r(latency["latency_ms"]["resident_replay_median"]),
+                          "model_gbs": _r(latency["model"]["achieved_gbs"]), "model_frac": _r(latency["model"]["frac"])}
+    if ok(surrogate):
+        f = surrogate["mlp_forward"]
+        out["surrogate"] = {"n": surrogate["n"], "train": surrogate["n_train"],
+                            "recall_at_100": surrogate["recall_at_100"],
+                            "recall_strict": surrogate["recall_strict_top100"], "best_found": surrogate["best_found"],
+                            "bfps": _r(surrogate["best_found_per_s"]),
+                            "bfps_plain": _r(surrogate["best_found_per_s_plain"]),
+                            "mlp_tflops": _r(f["tcgen05"]["tflops"]), "mlp_frac": _r(f["tcgen05"]["frac"]),
+                            "mlp_ms_median": _r(f["tcgen05"]["ms"]),
+                            "mma_sync_tflops": _r(f["mma_sync"]["tflops"])}
+    if ok(search):
+        out["search"] = {"n": search["n"], "steps": search["steps"], "best_acc": search["best_acc"]}
+        for k in ("exhaustive", "surrogate_pruned", "surrogate_adaptive"):
+            if k in search:
+                out["search"][k] = {"bfps": _r(search[k]["best_found_per_s"]), "s": _r(search[k]["seconds"]),
+                                    "same_beam": search[k]["same_final_beam"]}
+    if ok(numeric):
+        out["numeric_frac"] = [_r(numeric["one_per_role"]["frac"]), _r(numeric["three_per_role"]["frac"])]
+    if ok(strings):
+        out["string_frac"] = [_r(strings["equal_one_per_role"]["frac"]), _r(strings["equal_and_contain"]["frac"])]
+    return out
 
 
 def main():
@@ -848,6 +947,9 @@ def main():
                     help="individuals of the latency workload's KB (default: its full 10,000,000)")
     ap.add_argument("--search-full", action="store_true",
                     help="search at full size (4M individuals, 64 roles, 20 steps)")
+    ap.add_argument("--no-latency", action="store_true", help="skip the single-hypothesis latency section")
+    ap.add_argument("--one-batch", action="store_true",
+                    help="every step replays one batch on one workspace (small device footprint, for ncu)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="hypotheses per step (smaller only for profiling captures)")
     args = ap.parse_args()

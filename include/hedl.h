@@ -447,6 +447,13 @@ void hedl_mlp_free(hedl_mlp *m);
  * SYNCHRONIZES the device. */
 int hedl_mlp_get(const hedl_mlp *m, float *params, float *grads, uint32_t *step);
 
+/* Copy the Adam moments (HOST float [hedl_mlp_param_count()] each, either may
+ * be NULL): the first moment m and the second moment v of Adam's definition
+ * (Kingma and Ba, 2015), as left by the last hedl_mlp_train_step, zero before
+ * the first.  The paper has no learned component: for checking the optimiser.
+ * SYNCHRONIZES the device. */
+int hedl_mlp_get_moments(const hedl_mlp *m, float *first, float *second);
+
 /* Workspace bytes for a batch of B rows (activations and their gradients). */
 int hedl_mlp_workspace_size(uint32_t B, size_t *bytes);
 

@@ -52,7 +52,7 @@ in the length, depth and height features.
 from __future__ import annotations
 
 import math
-from typing import Dict, List, Sequence, Tuple
+from typing import Optional, Dict, List, Sequence, Tuple
 
 import numpy as np
 
@@ -249,13 +249,16 @@ def fit_target_map(T: np.ndarray, tail: float) -> np.ndarray:
 
 
 def backward(p: Dict[str, np.ndarray], X: np.ndarray, T: np.ndarray, rounding: bool = True,
-             tmap=None) -> Tuple[float, dict]:
+             tmap=None, operands: Optional[dict] = None) -> Tuple[float, dict]:
     """Gradients of the (weighted) loss by the chain rule (relu'(0) = 0), float64:
     mean_b w_b sum_j (u_bj - t_bj)^2 on the raw output u and the mapped targets
     (``mapped_targets``); without a map, the plain ``loss`` of Y against T.
 
     With rounding, the gradients flowing into the hidden layers are rounded to
-    bfloat16 where the GPU stores them."""
+    bfloat16 where the GPU stores them.  With a dict ``operands``, it receives the
+    two factors of each weight gradient (g[w] = A^T C over the batch; a bias
+    gradient is the column sum of its A): w3 <- (dy, h2), w2 <- (dh2, h1),
+    w1 <- (dh1, x)."""
     r = bf16 if rounding else (lambda v: np.asarray(v, np.float64))
     _, c = forward(p, X, rounding)
     u = c["u"]
@@ -272,6 +275,8 @@ def backward(p: Dict[str, np.ndarray], X: np.ndarray, T: np.ndarray, rounding: b
     dh1 = np.asarray(r(dh1), np.float64)
     g["w1"] = dh1.T @ c["x"]
     g["b1"] = dh1.sum(0)
+    if operands is not None:
+        operands.update({"w3": (dy, c["h2"]), "w2": (dh2, c["h1"]), "w1": (dh1, c["x"])})
     return lval, g
 
 

@@ -49,7 +49,7 @@ SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free"
            "hedl_plan_replay", "hedl_workspace_size", "hedl_score_batch", "hedl_eval_concept",
            "hedl_eval_concept_noalloc", "hedl_sync_status", "hedl_tuning_get", "hedl_tuning_set",
            "hedl_autotune_workspace_size", "hedl_autotune", "hedl_mlp_param_count", "hedl_mlp_create",
-           "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
+           "hedl_mlp_free", "hedl_mlp_get", "hedl_mlp_get_moments", "hedl_mlp_workspace_size", "hedl_encode", "hedl_mlp_forward",
            "hedl_mlp_gradients", "hedl_mlp_train_step", "hedl_scores_from_counts", "hedl_select_workspace_size",
            "hedl_select_top", "hedl_canonical_batch", "hedl_mlp_fit_target_map", "hedl_mlp_set_target_map",
            "hedl_mlp_get_target_map", "hedl_mlp_set_gemm", "hedl_mlp_status", "hedl_stat_scores",
@@ -151,6 +151,7 @@ def library(path: Optional[str] = None):
             "hedl_mlp_create": (I, [P, ctypes.POINTER(P)]),
             "hedl_mlp_free": (None, [P]),
             "hedl_mlp_get": (I, [P, P, P, ctypes.POINTER(U32)]),
+            "hedl_mlp_get_moments": (I, [P, P, P]),
             "hedl_mlp_workspace_size": (I, [U32, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_encode": (I, [P, P, U32, P, U32, P, U32, P, P, P]),
             "hedl_stat_scores": (I, [P, U32, P, P]),
@@ -502,6 +503,15 @@ def hedl_mlp_get(m: MLPHandle):
     step = ctypes.c_uint32()
     _check(library().hedl_mlp_get(m.ptr, p.ctypes.data, g.ctypes.data, ctypes.byref(step)))
     return p, g, step.value
+
+
+def hedl_mlp_get_moments(m: MLPHandle):
+    """Adam's first and second moments (float32 arrays of hedl_mlp_param_count() values)."""
+    n = hedl_mlp_param_count()
+    first = np.zeros(n, np.float32)
+    second = np.zeros(n, np.float32)
+    _check(library().hedl_mlp_get_moments(m.ptr, first.ctypes.data, second.ctypes.data))
+    return first, second
 
 
 def hedl_mlp_workspace_size(B: int) -> int:

@@ -813,6 +813,14 @@ int hedl_mlp_get(const hedl_mlp *m, float *params, float *grads, uint32_t *step)
     return HEDL_OK;
 }
 
+int hedl_mlp_get_moments(const hedl_mlp *m, float *first, float *second) {
+    if (!m) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (!e && first) e = cudaMemcpy(first, m->m, N_PARAMS * 4, cudaMemcpyDeviceToHost);
+    if (!e && second) e = cudaMemcpy(second, m->v, N_PARAMS * 4, cudaMemcpyDeviceToHost);
+    return e ? cuda_fail(e, "hedl_mlp_get_moments") : HEDL_OK;
+}
+
 int hedl_mlp_workspace_size(uint32_t B, size_t *bytes) {
     if (!bytes) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     *bytes = mlp_ws_bytes(B);

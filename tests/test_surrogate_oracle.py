@@ -185,3 +185,84 @@ def test_statistic_programs_land_in_their_buckets():
         assert w & 0xFF == (P.DGE, P.DLE)[o] and (w >> 16) & 0xFFFF == prop
         t = np.float32(P.bits_f32(w >> 32))
         assert int(np.sum(grid[prop] < t)) == q, (prop, o, q)
+
+
+def _grad_case(B=4096, seed=4, tmap=None):
+    from synth import hyps, kb as K
+    kb = K.generate(K.CONFIGS["small"])
+    X = S.encode_batch(hyps.batch_hyps(kb, seed, 0, B))
+    T = np.random.default_rng(seed).uniform(size=(B, 2)).astype(np.float32)
+    p = S.init_params(6)
+    ops = {}
+    _, ref = S.backward(p, X, T, rounding=True, tmap=tmap, operands=ops)
+    return p, X, T, ref, ops
+
+
+@pytest.mark.parametrize("mapped", [False, True])
+def test_gradient_bound_accepts_fp32_and_rejects_planted_mistakes(mapped):
+    """The element-wise gradient tolerance (tests/surrogate_bounds.py) holds a float32 emulation of
+    the GPU's arithmetic at a training-size batch, and rejects perturbed copies of the oracle's own
+    gradient (host arrays only): one 128 x 256 tile of dW1 summed without its last 64 batch rows,
+    one tile of dW2 holding its neighbour's values, one ReLU-mask row of h1 flipped."""
+    from tests import surrogate_bounds as SB
+    tmap = np.array([0.5, 0.2, 0.3, 0.5, 3.0]) if mapped else None
+    p, X, T, ref, ops = _grad_case(tmap=tmap)
+    tol = SB.gradient_tolerances(ops)
+    emu = SB.fp32_emulation(p, X, T, S.bf16, tmap=tmap)
+    assert not SB.gradient_violations(emu, ref, tol)
+    # a tile of dW1 missing its last K block (64 batch rows)
+    dh1, x = ops["w1"]
+    bad = {k: v.copy() for k, v in ref.items()}
+    bad["w1"][:128, :256] -= dh1[-64:, :128].T @ x[-64:, :256]
+    assert any(v.startswith("w1") for v in SB.gradient_violations(bad, ref, tol))
+    # a tile of dW2 holding the values of the tile beside it
+    bad = {k: v.copy() for k, v in ref.items()}
+    bad["w2"][128:256, 0:256] = ref["w2"][128:256, 256:512]
+    assert any(v.startswith("w2") for v in SB.gradient_violations(bad, ref, tol))
+    # one batch row's ReLU mask of h1 inverted in the backward pass
+    dh2, h1 = ops["w2"]
+    b = 17
+    pre = dh2[b] @ S.bf16(p["w2"]).astype(np.float64)
+    row = S.bf16((pre * (h1[b] <= 0)).astype(np.float32)).astype(np.float64)
+    bad = {k: v.copy() for k, v in ref.items()}
+    bad["w1"] += np.outer(row - dh1[b], x[b])
+    bad["b1"] += row - dh1[b]
+    v = SB.gradient_violations(bad, ref, tol)
+    assert any(s.startswith("w1") for s in v) and any(s.startswith("b1") for s in v), v
+
+
+def test_adam_bound_accepts_fp32_and_rejects_wrong_steps():
+    """The element-wise Adam tolerance holds a float32 step with the GPU kernel's arithmetic, against
+    the oracle's float64 step (oracle.surrogate.adam, with the float32 decay rates), over two
+    steps; it rejects a step without bias correction, with the moments' decay rates swapped, or
+    with the first step's moments lost."""
+    from tests import surrogate_bounds as SB
+    f = np.float32
+    B1, B2 = f(0.9), f(0.999)
+    rng = np.random.default_rng(3)
+    n = 20000
+    w = rng.normal(0, 0.05, n).astype(np.float32)
+    g1 = (rng.normal(0, 1e-2, n) * rng.choice([1e-4, 1.0], n)).astype(np.float32)
+    g2 = rng.normal(0, 1e-2, n).astype(np.float32)
+
+    def step32(w, m, v, g, t, lr, b1=B1, b2=B2, correct=True):
+        m = b1 * m + (f(1) - b1) * g
+        v = b2 * v + (f(1) - b2) * g * g
+        c1 = f(1) - b1 ** f(t) if correct else f(1)
+        c2 = f(1) - b2 ** f(t) if correct else f(1)
+        return (w - f(lr) * (m / c1) / (np.sqrt(v / c2) + f(1e-8))).astype(np.float32), m, v
+
+    def ref(w, m, v, g, t, lr):
+        p, mm, vv = {"x": w.astype(np.float64)}, {"x": m.astype(np.float64)}, {"x": v.astype(np.float64)}
+        S.adam(p, {"x": g.astype(np.float64)}, mm, vv, step=t, lr=lr, b1=float(B1), b2=float(B2))
+        return (p["x"], mm["x"], vv["x"]) + SB.adam_tolerances(w, m, v, g, t, lr, float(B1), float(B2))
+
+    ok = lambda got, r: all(np.all(np.abs(np.float64(a) - b) <= t) for a, b, t in zip(got, r[:3], r[3:]))
+    z = np.zeros(n, np.float32)
+    w1, m1, v1 = step32(w, z, z, g1, 1, 1e-3)
+    assert ok((w1, m1, v1), ref(w, z, z, g1, 1, 1e-3))
+    r2 = ref(w1, m1, v1, g2, 2, 1e-3)
+    assert ok(step32(w1, m1, v1, g2, 2, 1e-3), r2)
+    assert not ok(step32(w1, m1, v1, g2, 2, 1e-3, correct=False), r2)
+    assert not ok(step32(w1, m1, v1, g2, 2, 1e-3, b1=B2, b2=B1), r2)
+    assert not ok(step32(w1, z, z, g2, 2, 1e-3), r2)
