@@ -307,8 +307,10 @@ def surrogate_round(args, dev):
 
 
 def _planner_times(H, handle, batch, reps: int = 5):
-    """Host time to plan one batch without sharing or bit slicing: the host planner, and the
-    per-hypothesis planner on 1 and on all host threads (best of `reps`; the plans are equal)."""
+    """Time to plan one batch without sharing or bit slicing: the host planner, the
+    per-hypothesis planner on 1 and on all host threads, and the device planner from programs
+    already in device memory (wall clock including its two synchronisations; best of `reps`;
+    the plans are equal, the device image is compared with the host's)."""
     F = H.HEDL_NO_CSE | H.HEDL_NO_SLICE
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
@@ -320,9 +322,18 @@ def _planner_times(H, handle, batch, reps: int = 5):
             ts.append(time.perf_counter() - t0)
         return 1000 * min(ts)
 
+    import torch
+    flat, offs = batch
+    pd = torch.from_numpy(np.ascontiguousarray(flat).view(np.int64)).cuda()
+    od = torch.from_numpy(np.ascontiguousarray(offs, np.uint32).view(np.int32)).cuda()
+    host = H.hedl_plan_batch(handle, *batch, F)
+    dev = H.hedl_plan_batch_device(handle, pd, od, int(offs[-1]))
+    same = bool(np.array_equal(H.hedl_plan_image(host), H.hedl_plan_image(dev)))
     return {"host": best(lambda: H.hedl_plan_batch(handle, *batch, F)),
             "parallel_1": best(lambda: H.hedl_plan_batch_parallel(handle, *batch, F, 1)),
-            f"parallel_{cores}": best(lambda: H.hedl_plan_batch_parallel(handle, *batch, F, cores))}
+            f"parallel_{cores}": best(lambda: H.hedl_plan_batch_parallel(handle, *batch, F, cores)),
+            "device": best(lambda: H.hedl_plan_batch_device(handle, pd, od, int(offs[-1]))),
+            "device_image_equals_host": same}
 
 
 def _section(fn, *a):
@@ -893,6 +904,9 @@ def _summary(value, plain, plan_info, ncse, peak, latency, surrogate, search, nu
            "plain_counts_identical": plain["counts_identical"] if plain else None,
            "effective_frac_unshared": _r(value * (ncse["model_bytes"] / BATCH) / 1e9 / peak),
            "plan_ms": _r(plan_info["host_ms_per_batch"]), "role_ops": plan_info["role_ops"],
+           "plan_no_sharing_ms": {k: (_r(v) if not isinstance(v, bool) else v)
+                                  for k, v in (plan_info["no_sharing_planners_ms"] or {}).items()
+                                  if k != "error"},
            "role_groups": plan_info["role_groups"],
            "cpu_1thread_hyp_s": _r(cpu["single_thread"]["value"]) if cpu else None}
     if ok(latency):

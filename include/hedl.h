@@ -289,6 +289,23 @@ void hedl_plan_free(hedl_plan *p);
 int hedl_plan_batch_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
                              unsigned flags, uint32_t n_threads, hedl_plan **out);
 
+/* The same plan built on the device (the paper's future work, Section VII:
+ * the GPU generates its own evaluation plans): the per-hypothesis steps of
+ * hedl_plan_batch_parallel run as grid-stride kernels over DEVICE programs
+ * (progs uint64[n_insns], offs uint32[H+1], offs[0] = 0, offs[H] = n_insns),
+ * the prefix sums as block-wide scans, the work-queue order as a bitonic
+ * sort.  Validation runs on the device too (HEDL_ERR_BAD_PROGRAM names the
+ * first bad program; offsets outside [0, n_insns] or decreasing give
+ * HEDL_ERR_INVALID_ARG).  The image (byte for byte hedl_plan_batch's with
+ * HEDL_NO_CSE | HEDL_NO_SLICE) stays in device memory owned by the plan;
+ * hedl_plan_execute copies it into the workspace within the device, and
+ * hedl_plan_image copies it to the host.  The library allocates the planner's
+ * scratch (about 80 bytes per instruction) for the call and the image for the
+ * plan's lifetime.  Flags and the depth limit as hedl_plan_batch_parallel.
+ * Synchronizes s twice (the totals size the image; the header comes back). */
+int hedl_plan_batch_device(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, uint64_t n_insns,
+                           unsigned flags, hedl_stream s, hedl_plan **out);
+
 /* Copy a plan's image (the work queue the interpreter reads: header, task and
  * group tables, dependency lists, segment code, zeroed counters; image_bytes
  * of hedl_plan_info) into the HOST buffer out of cap bytes, and its size into

@@ -43,7 +43,7 @@ HEDL_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 # exported symbols (one per declaration in include/hedl.h)
 SYMBOLS = ("hedl_row_words", "hedl_kb_load", "hedl_kb_plan_only", "hedl_kb_free", "hedl_examples_set", "hedl_examples_counts",
-           "hedl_validate", "hedl_plan_batch", "hedl_plan_batch_parallel", "hedl_plan_info_get", "hedl_plan_image",
+           "hedl_validate", "hedl_plan_batch", "hedl_plan_batch_parallel", "hedl_plan_batch_device", "hedl_plan_info_get", "hedl_plan_image",
            "hedl_plan_free",
            "hedl_plan_execute",
            "hedl_plan_replay", "hedl_workspace_size", "hedl_score_batch", "hedl_eval_concept",
@@ -133,6 +133,7 @@ def library(path: Optional[str] = None):
             "hedl_canonical_batch": (I, [P, P, U32, P]),
             "hedl_plan_batch": (I, [P, P, P, U32, ctypes.c_uint, ctypes.POINTER(P)]),
             "hedl_plan_batch_parallel": (I, [P, P, P, U32, ctypes.c_uint, U32, ctypes.POINTER(P)]),
+            "hedl_plan_batch_device": (I, [P, P, P, U32, U64, ctypes.c_uint, P, ctypes.POINTER(P)]),
             "hedl_plan_info_get": (I, [P, ctypes.POINTER(hedl_plan_info)]),
             "hedl_plan_image": (I, [P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
             "hedl_plan_free": (None, [P]),
@@ -361,6 +362,15 @@ def hedl_plan_batch_parallel(kb: KBHandle, progs, offs, flags: int = 0, n_thread
     out = ctypes.c_void_p()
     _check(library().hedl_plan_batch_parallel(kb.ptr, p.ctypes.data if p.size else None, o.ctypes.data, o.size - 1,
                                               flags, n_threads, ctypes.byref(out)))
+    return Plan(out.value)
+
+
+def hedl_plan_batch_device(kb: KBHandle, progs_dev, offs_dev, n_insns: int, flags: int = 0, stream=None) -> Plan:
+    """The no-sharing, no-slicing plan of the batch built on the device from DEVICE programs
+    (progs_dev: int64/uint64 tensor of n_insns instructions, offs_dev: int32 tensor [H+1])."""
+    out = ctypes.c_void_p()
+    _check(library().hedl_plan_batch_device(kb.ptr, _dptr(progs_dev), _dptr(offs_dev), offs_dev.numel() - 1,
+                                            n_insns, flags, _stream(stream), ctypes.byref(out)))
     return Plan(out.value)
 
 

@@ -356,6 +356,14 @@ int hedl_plan_info_get(const hedl_plan *p, hedl_plan_info *info) {
 
 int hedl_plan_image(const hedl_plan *p, void *out, size_t cap, size_t *bytes) {
     if (!p || !bytes) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    if (p->impl->dev_image) {   // a device-built plan
+        *bytes = p->impl->image_bytes;
+        if (!out || cap < *bytes)
+            return fail(HEDL_ERR_INVALID_ARG, "image of " + std::to_string(*bytes) + " bytes, buffer of " +
+                                                  std::to_string(cap));
+        cudaError_t e = cudaMemcpy(out, p->impl->dev_image, *bytes, cudaMemcpyDeviceToHost);
+        return e ? cuda_fail(e, "plan image copy") : HEDL_OK;
+    }
     const std::vector<uint8_t> &img = p->impl->image;
     *bytes = img.size();
     if (img.empty()) return HEDL_OK;
@@ -370,6 +378,7 @@ void hedl_plan_free(hedl_plan *p) {
     if (!p) return;
     if (p->impl) {
         destroy_graph(p->impl);
+        if (p->impl->dev_image) cudaFree(p->impl->dev_image);
         delete p->impl;
     }
     delete p;
@@ -402,7 +411,11 @@ int execute(hedl_kb *kb, const PlanImpl *pc, uint32_t *counts, uint32_t *out_bit
         p->bps = bps;
     }
     cudaError_t e;
-    if (upload) {
+    if (upload && p->dev_image) {
+        // a device-built plan: its image is copied within the device
+        e = cudaMemcpyAsync(ws, p->dev_image, p->image_bytes, cudaMemcpyDeviceToDevice, st);
+        if (e) return cuda_fail(e, "plan copy");
+    } else if (upload) {
         // pageable source: the copy is complete (staged) when the call returns,
         // so the host image may be reused at once
         e = cudaMemcpyAsync(ws, p->image.data(), p->image_bytes, cudaMemcpyHostToDevice, st);

@@ -501,30 +501,12 @@ __host__ __device__ inline void start_step(const Ctx &c, uint64_t i) {
     if (i < c.tot->NS) c.starts[i] = i == 0 || (c.keys[i] >> 32) != (c.keys[i - 1] >> 32);
 }
 
-// Sequential: groups, gsegs, level_items and the header.
-__host__ __device__ inline void finish_step(const Ctx &c) {
+// The header and the totals of a plan with G groups, once the groups, gsegs
+// and level items are in the image (both drivers).
+__host__ __device__ inline void header_step(const Ctx &c, uint64_t G) {
     Totals &t = *c.tot;
-    if (t.err_hyp != 0xFFFFFFFFu) return;
     const uint64_t NS = t.NS, n_tiles = t.n_tiles, L = t.n_levels;
-    uint64_t G = 0;
-    for (uint64_t i = 0; i < NS; ++i) G += c.starts[i];
     const Layout o = layout(NS, G, t.deps_n, t.code_n, L, c.H, t.n_slots, c.z.B);
-    Group *groups = reinterpret_cast<Group *>(c.img + o.off_groups);
-    uint32_t *gsegs = reinterpret_cast<uint32_t *>(c.img + o.off_gsegs);
-    uint32_t *li = reinterpret_cast<uint32_t *>(c.img + o.off_li);
-    for (uint64_t l = 0; l <= L; ++l) li[l] = 0;
-    uint64_t g = 0, begin = 0;
-    for (uint64_t i = 0; i < NS; ++i) {
-        gsegs[i] = (uint32_t)(c.keys[i] & 0xFFFFFFFFull);
-        if (c.starts[i]) begin = i;
-        if (i + 1 == NS || c.starts[i + 1]) {   // the group [begin, i] ends here
-            const uint32_t lvl = c.seg_level[gsegs[begin]];
-            groups[g++] = Group{(uint32_t)(begin * n_tiles), (uint32_t)begin, (uint32_t)(i + 1 - begin), lvl};
-            li[lvl + 1] = (uint32_t)((i + 1) * n_tiles);
-        }
-    }
-    for (uint64_t l = 1; l <= L; ++l) li[l] = li[l] > li[l - 1] ? li[l] : li[l - 1];
-    for (uint64_t l = 0; l <= L; ++l) c.level_items[l] = li[l];
     PlanHeader hd{};
     hd.n_items = (uint32_t)(NS * n_tiles);
     hd.n_segs = (uint32_t)NS;
@@ -559,6 +541,33 @@ __host__ __device__ inline void finish_step(const Ctx &c) {
     t.ctr_words = o.ctr_words;
 }
 
+// Sequential: groups, gsegs, level_items and the header.
+__host__ __device__ inline void finish_step(const Ctx &c) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    const uint64_t NS = t.NS, n_tiles = t.n_tiles, L = t.n_levels;
+    uint64_t G = 0;
+    for (uint64_t i = 0; i < NS; ++i) G += c.starts[i];
+    const Layout o = layout(NS, G, t.deps_n, t.code_n, L, c.H, t.n_slots, c.z.B);
+    Group *groups = reinterpret_cast<Group *>(c.img + o.off_groups);
+    uint32_t *gsegs = reinterpret_cast<uint32_t *>(c.img + o.off_gsegs);
+    uint32_t *li = reinterpret_cast<uint32_t *>(c.img + o.off_li);
+    for (uint64_t l = 0; l <= L; ++l) li[l] = 0;
+    uint64_t g = 0, begin = 0;
+    for (uint64_t i = 0; i < NS; ++i) {
+        gsegs[i] = (uint32_t)(c.keys[i] & 0xFFFFFFFFull);
+        if (c.starts[i]) begin = i;
+        if (i + 1 == NS || c.starts[i + 1]) {   // the group [begin, i] ends here
+            const uint32_t lvl = c.seg_level[gsegs[begin]];
+            groups[g++] = Group{(uint32_t)(begin * n_tiles), (uint32_t)begin, (uint32_t)(i + 1 - begin), lvl};
+            li[lvl + 1] = (uint32_t)((i + 1) * n_tiles);
+        }
+    }
+    for (uint64_t l = 1; l <= L; ++l) li[l] = li[l] > li[l - 1] ? li[l] : li[l - 1];
+    for (uint64_t l = 0; l <= L; ++l) c.level_items[l] = li[l];
+    header_step(c, G);
+}
+
 // Per index: copy segment i, dependency i and code word i into the image; zero counter i.
 __host__ __device__ inline void assemble_step(const Ctx &c, uint64_t i) {
     const Totals &t = *c.tot;
@@ -579,6 +588,277 @@ __host__ __device__ inline uint64_t pow2_at_least(uint64_t x) {
     uint64_t p = 1;
     while (p < x) p <<= 1;
     return p;
+}
+
+// ---------------------------------------------------------------- the device driver's kernels
+// The per-index steps above as grid-stride kernels; the sequential steps as
+// one-block kernels built on block-wide scans and reductions.
+
+constexpr int SCAN_THREADS = 1024;
+
+__device__ inline uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
+__device__ inline uint64_t gindex() { return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+
+// Inclusive scan of one value per thread over a block of SCAN_THREADS threads.
+__device__ inline uint64_t block_inclusive_scan(uint64_t x, uint64_t *sh) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < (blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= (uint32_t)o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t r = x + (warp ? sh[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// Per hypothesis: offsets bounds first (a program outside [0, n_insns) is
+// refused before any scratch is touched), then count_step.
+__global__ void count_kernel(Ctx c, uint64_t n_insns) {
+    for (uint64_t h = gindex(); h < c.H; h += gstride()) {
+        const uint32_t o0 = c.offs[h], o1 = c.offs[h + 1];
+        if ((h == 0 && o0 != 0) || o1 < o0 || o1 > n_insns || (h + 1 == c.H && o1 != n_insns)) {
+            c.cnt[h] = HypCount{};
+            c.cnt[h].err = (uint32_t)-HEDL_ERR_INVALID_ARG;
+            continue;
+        }
+        count_step(c, (uint32_t)h);
+    }
+}
+
+// scan_step's offsets and totals by block-wide scans (one block of SCAN_THREADS):
+// each thread sums a contiguous stretch of hypotheses, the block scans the
+// stretch sums, and each thread writes its stretch's offsets.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(Ctx c) {
+    __shared__ uint64_t sh[32];
+    __shared__ uint64_t tot_mat_code, tot_mat_reads;
+    __shared__ uint32_t first_err;
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    const uint32_t per = (c.H + T - 1) / T;
+    const uint32_t h0 = min(c.H, t * per), h1 = min(c.H, h0 + per);
+    if (t == 0) first_err = 0xFFFFFFFFu;
+    __syncthreads();
+    uint64_t slots = 0, code = 0, deps = 0, rcode = 0, rdeps = 0;
+    for (uint32_t h = h0; h < h1; ++h) {
+        const HypCount &n = c.cnt[h];
+        if (n.err) atomicMin(&first_err, h);
+        slots += n.n_mat;
+        code += n.mat_code;
+        deps += n.mat_reads;
+        rcode += n.root_code;
+        rdeps += n.root_reads;
+    }
+    const uint64_t i_slots = block_inclusive_scan(slots, sh), i_code = block_inclusive_scan(code, sh);
+    const uint64_t i_deps = block_inclusive_scan(deps, sh), i_rcode = block_inclusive_scan(rcode, sh);
+    const uint64_t i_rdeps = block_inclusive_scan(rdeps, sh);
+    if (t == T - 1) {
+        tot_mat_code = i_code;
+        tot_mat_reads = i_deps;
+    }
+    __syncthreads();
+    uint64_t a_slots = i_slots - slots, a_code = i_code - code, a_deps = i_deps - deps;
+    uint64_t a_rcode = tot_mat_code + i_rcode - rcode, a_rdeps = tot_mat_reads + i_rdeps - rdeps;
+    for (uint32_t h = h0; h < h1; ++h) {
+        HypCount &n = c.cnt[h];
+        const uint32_t m = n.n_mat, mc = n.mat_code, md = n.mat_reads, rc = n.root_code, rd = n.root_reads;
+        n.n_mat = (uint32_t)a_slots;
+        n.mat_code = (uint32_t)a_code;
+        n.mat_reads = (uint32_t)a_deps;
+        n.root_code = (uint32_t)a_rcode;
+        n.root_reads = (uint32_t)a_rdeps;
+        a_slots += m;
+        a_code += mc;
+        a_deps += md;
+        a_rcode += rc;
+        a_rdeps += rd;
+    }
+    if (t == T - 1) {
+        Totals &tt = *c.tot;
+        tt = Totals{};
+        tt.n_slots = i_slots;
+        tt.code_n = tot_mat_code + i_rcode;
+        tt.deps_n = tot_mat_reads + i_rdeps;
+        tt.NS = i_slots + c.H;
+        tt.err_hyp = first_err;
+        tt.err_code = first_err == 0xFFFFFFFFu ? 0u : c.cnt[first_err].err;
+    }
+}
+
+__global__ void write_kernel(Ctx c) {
+    for (uint64_t h = gindex(); h < c.H; h += gstride()) write_step(c, (uint32_t)h);
+}
+
+// shape_step by block-wide reductions (one block): the level count, the
+// segments (and role-walking segments) per level, the narrowest level, then
+// the tile shape by thread 0.
+__global__ void __launch_bounds__(SCAN_THREADS) shape_kernel(Ctx c) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    __shared__ uint32_t n_levels;
+    __shared__ unsigned long long smin;
+    if (threadIdx.x == 0) {
+        n_levels = 0;
+        smin = ~0ull;
+    }
+    __syncthreads();
+    for (uint64_t s = threadIdx.x; s < t.NS; s += blockDim.x) atomicMax(&n_levels, c.seg_level[s] + 1);
+    __syncthreads();
+    const uint32_t L = n_levels;
+    if ((uint64_t)L > MAX_KEY_LEVELS) {
+        if (threadIdx.x == 0) {
+            t.err_hyp = ERR_BATCH;
+            t.err_code = (uint32_t)-HEDL_ERR_INVALID_ARG;
+        }
+        return;
+    }
+    for (uint32_t l = threadIdx.x; l < L; l += blockDim.x) c.segs_at[l] = c.walks_at[l] = 0;
+    __syncthreads();
+    for (uint64_t s = threadIdx.x; s < t.NS; s += blockDim.x) {
+        atomicAdd(&c.segs_at[c.seg_level[s]], 1u);
+        if (c.seg_walks[s]) atomicOr(&c.walks_at[c.seg_level[s]], 1u);
+    }
+    __threadfence_block();
+    __syncthreads();
+    for (uint32_t l = threadIdx.x; l < L; l += blockDim.x)
+        if (__ldcg(c.walks_at + l)) atomicMin(&smin, (unsigned long long)__ldcg(c.segs_at + l));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t WW = 32, rounds = c.rounds;
+        if (c.n_sms > 0) {
+            const uint64_t resident = 32ull * c.n_sms;
+            if (smin != ~0ull)
+                while (WW > 4 && smin * c.wp < 4ull * resident * WW * c.wpl) WW >>= 1;
+            if (WW < 32) rounds = 1;
+        }
+        t.n_levels = L;
+        t.WW = WW;
+        t.TW = (uint64_t)c.warps * WW * c.wpl * rounds;
+        t.n_tiles = (c.wp + t.TW - 1) / t.TW;
+    }
+}
+
+__global__ void key_kernel(Ctx c, uint64_t n2) {
+    if (c.tot->err_hyp != 0xFFFFFFFFu) return;
+    for (uint64_t i = gindex(); i < n2; i += gstride()) key_step(c, i);
+}
+
+// One compare-exchange step (j, k) of the bitonic network over all n2 keys.
+__global__ void bitonic_global_kernel(uint64_t *keys, uint64_t n2, uint64_t j, uint64_t k) {
+    for (uint64_t i = gindex(); i < n2; i += gstride()) bitonic_step(keys, i, j, k);
+}
+
+constexpr uint32_t BITONIC_TILE = 2048;   // keys a block sorts in shared memory (16 KB)
+
+// The steps of the network whose partners lie within one tile of BITONIC_TILE
+// keys: every k from k_from to k_to (powers of two), each with j from
+// min(j_from, k / 2) down to 1; a block holds one tile in shared memory.
+__global__ void __launch_bounds__(1024) bitonic_tile_kernel(uint64_t *keys, uint64_t n2, uint64_t k_from,
+                                                            uint64_t k_to, uint64_t j_from) {
+    __shared__ uint64_t sk[BITONIC_TILE];
+    const uint64_t base = (uint64_t)blockIdx.x * BITONIC_TILE;
+    const uint32_t span = (uint32_t)(n2 - base < BITONIC_TILE ? n2 - base : (uint64_t)BITONIC_TILE);
+    for (uint32_t q = threadIdx.x; q < span; q += blockDim.x) sk[q] = keys[base + q];
+    __syncthreads();
+    for (uint64_t k = k_from; k <= k_to; k <<= 1) {
+        for (uint64_t j = (j_from < (k >> 1) ? j_from : (k >> 1)); j > 0; j >>= 1) {
+            for (uint32_t q = threadIdx.x; q < span; q += blockDim.x) {
+                const uint64_t i = base + q, l = i ^ j;   // l stays inside the tile: j < BITONIC_TILE
+                if (l > i) {
+                    const uint64_t a = sk[q], b = sk[l - base];
+                    if ((a > b) == ((i & k) == 0)) {
+                        sk[q] = b;
+                        sk[l - base] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t q = threadIdx.x; q < span; q += blockDim.x) keys[base + q] = sk[q];
+}
+
+__global__ void start_kernel(Ctx c) {
+    if (c.tot->err_hyp != 0xFFFFFFFFu) return;
+    for (uint64_t i = gindex(); i < c.tot->NS; i += gstride()) start_step(c, i);
+}
+
+// Group index of every sorted position (exclusive scan of the starts, one
+// block), the group count, and the zeroed level items.
+__global__ void __launch_bounds__(SCAN_THREADS) group_scan_kernel(Ctx c, uint32_t *gidx, uint64_t *G_out) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    __shared__ uint64_t sh[32];
+    const uint64_t NS = t.NS, T = blockDim.x, per = (NS + T - 1) / T;
+    const uint64_t i0 = min(NS, threadIdx.x * per), i1 = min(NS, i0 + per);
+    uint64_t cnt = 0;
+    for (uint64_t i = i0; i < i1; ++i) cnt += c.starts[i];
+    const uint64_t incl = block_inclusive_scan(cnt, sh);
+    uint64_t g = incl - cnt;
+    for (uint64_t i = i0; i < i1; ++i) {
+        g += c.starts[i];
+        gidx[i] = (uint32_t)(g - 1);   // the group position i belongs to
+    }
+    if (threadIdx.x == T - 1) *G_out = incl;
+}
+
+// Per sorted position: gsegs, and the group that ends there (with its first
+// position found by the group's start), and its level's item bound.
+__global__ void group_kernel(Ctx c, const uint32_t *gidx, const uint64_t *G_in, uint64_t *gbegin) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    const uint64_t NS = t.NS, n_tiles = t.n_tiles;
+    const Layout o = layout(NS, *G_in, t.deps_n, t.code_n, t.n_levels, c.H, t.n_slots, c.z.B);
+    uint32_t *gsegs = reinterpret_cast<uint32_t *>(c.img + o.off_gsegs);
+    for (uint64_t i = gindex(); i < NS; i += gstride()) {
+        gsegs[i] = (uint32_t)(c.keys[i] & 0xFFFFFFFFull);
+        if (c.starts[i]) gbegin[gidx[i]] = i;
+    }
+}
+
+__global__ void group_end_kernel(Ctx c, const uint32_t *gidx, const uint64_t *G_in, const uint64_t *gbegin) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    const uint64_t NS = t.NS, n_tiles = t.n_tiles;
+    const Layout o = layout(NS, *G_in, t.deps_n, t.code_n, t.n_levels, c.H, t.n_slots, c.z.B);
+    Group *groups = reinterpret_cast<Group *>(c.img + o.off_groups);
+    uint32_t *li = reinterpret_cast<uint32_t *>(c.img + o.off_li);
+    for (uint64_t i = gindex(); i < NS; i += gstride()) {
+        if (i + 1 == NS || c.starts[i + 1]) {
+            const uint64_t g = gidx[i], begin = gbegin[g];
+            const uint32_t lvl = c.seg_level[(uint32_t)(c.keys[begin] & 0xFFFFFFFFull)];
+            groups[g] = Group{(uint32_t)(begin * n_tiles), (uint32_t)begin, (uint32_t)(i + 1 - begin), lvl};
+            atomicMax(li + lvl + 1, (uint32_t)((i + 1) * n_tiles));
+        }
+    }
+}
+
+// The level items' running maximum (levels in order), then the header.
+__global__ void header_kernel(Ctx c, const uint64_t *G_in) {
+    Totals &t = *c.tot;
+    if (t.err_hyp != 0xFFFFFFFFu) return;
+    const uint64_t L = t.n_levels;
+    const Layout o = layout(t.NS, *G_in, t.deps_n, t.code_n, L, c.H, t.n_slots, c.z.B);
+    uint32_t *li = reinterpret_cast<uint32_t *>(c.img + o.off_li);
+    for (uint64_t l = 1; l <= L; ++l) li[l] = li[l] > li[l - 1] ? li[l] : li[l - 1];
+    for (uint64_t l = 0; l <= L; ++l) c.level_items[l] = li[l];
+    header_step(c, *G_in);
+}
+
+__global__ void assemble_kernel(Ctx c, uint64_t span) {
+    if (c.tot->err_hyp != 0xFFFFFFFFu) return;
+    for (uint64_t i = gindex(); i < span; i += gstride()) assemble_step(c, i);
 }
 
 }  // namespace dp
@@ -751,9 +1031,228 @@ int build_plan_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t
     return HEDL_OK;
 }
 
+namespace {
+
+// One device allocation carved into 256-byte aligned pieces.
+struct Carve {
+    uint8_t *base = nullptr;
+    uint64_t at = 0;
+    template <typename T>
+    T *take(uint64_t n) {
+        T *p = reinterpret_cast<T *>(base + at);
+        at = (at + sizeof(T) * (n ? n : 1) + 255) & ~uint64_t(255);
+        return p;
+    }
+};
+
+uint32_t grid_for(uint64_t n, uint32_t threads) {
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((n + threads - 1) / threads, 4096));
+}
+
+}  // namespace
+
+// The device-side planner: the same steps as build_plan_parallel, launched as
+// kernels over device programs.  Two host synchronisations: after the scan
+// (the totals size the image) and at the end (the header, level items and
+// per-hypothesis counts come back for the plan's info).
+int build_plan_device(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H, uint64_t NI,
+                      unsigned flags, cudaStream_t st, PlanImpl **out) {
+    *out = nullptr;
+    if (H == 0) return fail(HEDL_ERR_INVALID_ARG, "empty batch (H = 0)");
+    if (kb->plan_only) return fail(HEDL_ERR_INVALID_ARG, "planning-only handle: the device planner needs a GPU");
+    if (NI == 0 || NI >= 0xFFFFFFFFull) return fail(HEDL_ERR_INVALID_ARG, "n_insns must be in [1, 2^32 - 1)");
+    if (flags & (HEDL_PLAIN | HEDL_TEST_UNSAT_DEP | HEDL_SLICE_ALL))
+        return fail(HEDL_ERR_INVALID_ARG, "the device planner takes neither HEDL_PLAIN, HEDL_SLICE_ALL nor test flags");
+    flags |= HEDL_NO_CSE | HEDL_NO_SLICE;
+    const dp::Bounds b = dp::bounds(NI, H);
+    const uint64_t n2max = dp::pow2_at_least(b.NS);
+    std::vector<uint32_t> num_vals, str_vals, csr_edges;
+    for (const DevNum &g : kb->num_host) num_vals.push_back(g.n_vals);
+    for (const DevStr &g : kb->str_host) str_vals.push_back(g.n_vals);
+    for (const DevCSR &g : kb->csr_host) csr_edges.push_back(g.n_edges);
+    // the scratch, carved once the sizes are summed
+    auto carve_all = [&](Carve &cv, dp::Ctx &c, uint32_t **gidx, uint64_t **gbegin, uint64_t **G,
+                         uint32_t **dnum, uint32_t **dstr, uint32_t **dcsr) {
+        c.sc.k0 = cv.take<int32_t>(NI);
+        c.sc.k1 = cv.take<int32_t>(NI);
+        c.sc.need = cv.take<uint32_t>(NI);
+        c.sc.slot = cv.take<uint32_t>(NI);
+        c.sc.level = cv.take<uint32_t>(NI);
+        c.sc.stk = cv.take<uint32_t>(NI);
+        c.sc.mat = cv.take<uint8_t>(NI);
+        c.sc.state = cv.take<uint8_t>(NI);
+        c.cnt = cv.take<dp::HypCount>(H);
+        c.tot = cv.take<dp::Totals>(1);
+        c.segs = cv.take<Seg>(b.NS);
+        c.code = cv.take<DInsn>(b.code);
+        c.deps = cv.take<uint32_t>(b.deps);
+        c.seg_level = cv.take<uint32_t>(b.NS);
+        c.seg_key = cv.take<uint32_t>(b.NS);
+        c.seg_walks = cv.take<uint8_t>(b.NS);
+        c.starts = cv.take<uint8_t>(b.NS);
+        c.keys = cv.take<uint64_t>(n2max);
+        c.segs_at = cv.take<uint32_t>(b.levels);
+        c.walks_at = cv.take<uint32_t>(b.levels);
+        c.level_items = cv.take<uint32_t>(b.levels + 1);
+        *gidx = cv.take<uint32_t>(b.NS);
+        *gbegin = cv.take<uint64_t>(b.NS);
+        *G = cv.take<uint64_t>(1);
+        *dnum = cv.take<uint32_t>(num_vals.size());
+        *dstr = cv.take<uint32_t>(str_vals.size());
+        *dcsr = cv.take<uint32_t>(csr_edges.size());
+    };
+    dp::Ctx c{};
+    uint32_t *gidx, *dnum, *dstr, *dcsr;
+    uint64_t *gbegin, *Gd;
+    Carve sizing;
+    carve_all(sizing, c, &gidx, &gbegin, &Gd, &dnum, &dstr, &dcsr);
+    void *scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, sizing.at);
+    if (e) return cuda_fail(e, "device planner scratch");
+    std::unique_ptr<void, void (*)(void *)> scratch_guard(scratch, [](void *q) { cudaFree(q); });
+    Carve cv;
+    cv.base = (uint8_t *)scratch;
+    carve_all(cv, c, &gidx, &gbegin, &Gd, &dnum, &dstr, &dcsr);
+    if (!num_vals.empty()) e = cudaMemcpyAsync(dnum, num_vals.data(), 4 * num_vals.size(), cudaMemcpyHostToDevice, st);
+    if (!e && !str_vals.empty()) e = cudaMemcpyAsync(dstr, str_vals.data(), 4 * str_vals.size(), cudaMemcpyHostToDevice, st);
+    if (!e && !csr_edges.empty()) e = cudaMemcpyAsync(dcsr, csr_edges.data(), 4 * csr_edges.size(), cudaMemcpyHostToDevice, st);
+    if (e) return cuda_fail(e, "device planner sizes");
+    c.progs = progs;
+    c.offs = offs;
+    c.H = H;
+    c.n_concepts = kb->n_concepts;
+    c.n_roles = kb->n_roles;
+    c.n_data = kb->n_props + kb->n_num;
+    c.n_str = kb->n_str;
+    c.n_patterns = kb->n_patterns;
+    c.staged = use_staging(kb, kb->tuning);
+    c.validated = false;
+    c.z = dp::Sizes{kb->n, 4ull * kb->wp, kb->n_props, dnum, dstr, dcsr, kb->contain_words};
+    const Tuning &tu = kb->tuning;
+    c.warps = tu.warps;
+    c.wpl = tu.wpl;
+    c.rounds = tu.rounds;
+    c.timeout_ms = tu.timeout_ms;
+    c.wp = kb->wp;
+    c.n_sms = (uint32_t)std::max(kb->n_sms, 0);
+    c.flags = flags;
+
+    // phase 1: validate, analyse and count per hypothesis; scan
+    dp::count_kernel<<<grid_for(H, 128), 128, 0, st>>>(c, NI);
+    dp::scan_kernel<<<1, dp::SCAN_THREADS, 0, st>>>(c);
+    dp::Totals tot{};
+    e = cudaGetLastError();
+    if (!e) e = cudaMemcpyAsync(&tot, c.tot, sizeof tot, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cuda_fail(e, "device planner (count, scan)");
+    if (tot.err_hyp != 0xFFFFFFFFu)
+        return fail(-(int)tot.err_code, "program " + std::to_string(tot.err_hyp) + " is not valid");
+    if (tot.n_slots > REF_ID) return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^30 materialized intermediate sets");
+
+    // phase 2: the image, laid out for at most NS groups and levels, zeroed, then filled
+    const dp::Layout ub = dp::layout(tot.NS, tot.NS, tot.deps_n, tot.code_n, tot.NS, H, tot.n_slots, 4ull * kb->wp);
+    void *img = nullptr;
+    e = cudaMalloc(&img, ub.off_slots);
+    if (e) return cuda_fail(e, "device plan image");
+    std::unique_ptr<void, void (*)(void *)> img_guard(img, [](void *q) { cudaFree(q); });
+    c.img = (uint8_t *)img;
+    e = cudaMemsetAsync(img, 0, ub.off_slots, st);
+    if (e) return cuda_fail(e, "device plan image");
+    const uint64_t NS = tot.NS, n2 = dp::pow2_at_least(NS);
+    dp::write_kernel<<<grid_for(H, 128), 128, 0, st>>>(c);
+    dp::shape_kernel<<<1, dp::SCAN_THREADS, 0, st>>>(c);
+    dp::key_kernel<<<grid_for(n2, 256), 256, 0, st>>>(c, n2);
+    const uint64_t T = dp::BITONIC_TILE;
+    const uint32_t tiles = (uint32_t)((n2 + T - 1) / T);
+    dp::bitonic_tile_kernel<<<tiles, 1024, 0, st>>>(c.keys, n2, 2, std::min<uint64_t>(n2, T), T);
+    for (uint64_t k = 2 * T; k <= n2; k <<= 1) {
+        for (uint64_t j = k >> 1; j >= T; j >>= 1)
+            dp::bitonic_global_kernel<<<grid_for(n2, 256), 256, 0, st>>>(c.keys, n2, j, k);
+        dp::bitonic_tile_kernel<<<tiles, 1024, 0, st>>>(c.keys, n2, k, k, T >> 1);
+    }
+    dp::start_kernel<<<grid_for(NS, 256), 256, 0, st>>>(c);
+    dp::group_scan_kernel<<<1, dp::SCAN_THREADS, 0, st>>>(c, gidx, Gd);
+    dp::group_kernel<<<grid_for(NS, 256), 256, 0, st>>>(c, gidx, Gd, gbegin);
+    dp::group_end_kernel<<<grid_for(NS, 256), 256, 0, st>>>(c, gidx, Gd, gbegin);
+    dp::header_kernel<<<1, 1, 0, st>>>(c, Gd);
+    const uint64_t span = std::max<uint64_t>(std::max<uint64_t>(NS, tot.code_n),
+                                             std::max<uint64_t>(tot.deps_n, 4 + NS + 1 + 2ull * H));
+    dp::assemble_kernel<<<grid_for(span, 256), 256, 0, st>>>(c, span);
+    e = cudaGetLastError();
+    PlanHeader hd{};
+    std::vector<dp::HypCount> cnt(H);
+    if (!e) e = cudaMemcpyAsync(&tot, c.tot, sizeof tot, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(&hd, img, sizeof hd, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(cnt.data(), c.cnt, sizeof(dp::HypCount) * H, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cuda_fail(e, "device planner (write, sort, assemble)");
+    if (tot.err_hyp == dp::ERR_BATCH)
+        return fail(HEDL_ERR_INVALID_ARG, "batch too deep for the per-hypothesis planner: more than 16,384 dependency "
+                                          "levels (nested role restrictions); plan it with hedl_plan_batch");
+    if (tot.err_hyp != 0xFFFFFFFFu) return fail(HEDL_ERR_INVALID_ARG, "device planner: unexpected failure");
+    if (tot.items >= 0xFFFFFFFFull) return fail(HEDL_ERR_INVALID_ARG, "batch too large: more than 2^32 work items");
+    std::vector<uint32_t> level_items(tot.n_levels + 1);
+    e = cudaMemcpy(level_items.data(), c.level_items, 4 * level_items.size(), cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "device planner (level items)");
+
+    auto *p = new PlanImpl();
+    p->flags = flags;
+    p->n_hyps = H;
+    p->tuning = kb->tuning;
+    p->staged = c.staged;
+    p->info.n_hyps = H;
+    p->info.total_insns = NI;
+    p->info.n_nodes = NI;
+    uint64_t model = 0;
+    for (const dp::HypCount &n : cnt) {
+        model += n.model;
+        p->info.n_role_ops += n.n_role;
+        p->info.n_data_ops += n.n_data;
+        p->info.n_atom_loads += n.n_atom;
+        p->max_stack = std::max(p->max_stack, n.max_depth);
+    }
+    if (p->max_stack > (uint32_t)STACK_MAX) {
+        delete p;
+        return fail(HEDL_ERR_BAD_PROGRAM, "internal: segment stack exceeds the device limit");
+    }
+    p->dev_image = img_guard.release();
+    p->image_bytes = hd.off_slots;
+    p->ctr_off = hd.off_ctr;
+    p->ctr_bytes = (4 + (uint64_t)(tot.NS + 1) + 2ull * H) * 4;
+    p->slots_off = hd.off_slots;
+    p->ws_bytes = hd.off_ft;
+    p->n_rgroups = 0;
+    p->level_items = std::move(level_items);
+    p->info.n_segments = hd.n_segs;
+    p->info.n_slots = hd.n_slots;
+    p->info.n_levels = hd.n_levels;
+    p->info.n_items = hd.n_items;
+    p->info.tile_words = hd.tile_words;
+    p->info.warp_words = hd.warp_words;
+    p->info.workspace_bytes = p->ws_bytes;
+    p->info.image_bytes = p->image_bytes;
+    p->info.model_bytes = model;
+    *out = p;
+    return HEDL_OK;
+}
+
 }  // namespace hedl
 
 using namespace hedl;
+
+extern "C" int hedl_plan_batch_device(hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
+                                      uint64_t n_insns, unsigned flags, hedl_stream s, hedl_plan **out) {
+    if (!out) return fail(HEDL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!kb || !offs || !progs) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
+    PlanImpl *impl = nullptr;
+    const int e = build_plan_device(kb, progs, offs, H, n_insns, flags, (cudaStream_t)s, &impl);
+    if (e) return e;
+    auto *p = new hedl_plan();
+    p->impl = impl;
+    *out = p;
+    return HEDL_OK;
+}
 
 extern "C" int hedl_plan_batch_parallel(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, uint32_t H,
                                         unsigned flags, uint32_t n_threads, hedl_plan **out) {

@@ -239,6 +239,7 @@ struct PlanImpl {
     uint32_t n_hyps = 0;
     hedl_plan_info info{};
     std::vector<uint8_t> image;          // header + tables + zeroed counters
+    void *dev_image = nullptr;           // or: the image in device memory (device-built plans), owned
     uint64_t image_bytes = 0;            // bytes to upload (aligned)
     uint64_t ctr_off = 0, ctr_bytes = 0; // counters region inside the image
     uint64_t slots_off = 0;              // slots region (after the image)
