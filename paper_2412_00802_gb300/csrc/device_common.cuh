@@ -353,29 +353,41 @@ __device__ __forceinline__ void role_stream(const DevCSR g, const uint32_t *fill
     }
 }
 
+__device__ __forceinline__ bool data_cmp(uint32_t cmp, float x, float t);
+
 // Numeric data-range restriction (Algorithms 9-10): one float compare per
-// individual, a ballot packs 32 of them into a word.  NaN (missing) compares
-// false.
+// individual.  Lane l builds its own words wb + l*WPL + s from the 32
+// contiguous values of each (eight 16-byte loads, all in flight at once, when
+// the row is 16-byte aligned and the word is whole; scalar loads otherwise).
+// NaN (missing) compares false.
 template <int WPL>
 __device__ __forceinline__ void data_words(const float *__restrict__ vals, uint32_t cmp, float t, uint32_t n,
                                            uint32_t n_words, uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
+    const bool vec = (reinterpret_cast<uintptr_t>(vals) & 15u) == 0;
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) {
-            const uint32_t w = wb + (uint32_t)j * WPL + s;
-            uint32_t word = 0;
-            if (w < n_words) {
-                const uint32_t i = w * 32u + lane;
-                bool p = false;
-                if (i < n) {
-                    const float x = __ldg(vals + i);
-                    p = cmp == HEDL_OP_DGE ? (x >= t) : cmp == HEDL_OP_DLE ? (x <= t) : (x == t);
+    for (int s = 0; s < WPL; ++s) {
+        const uint32_t w = wb + lane * WPL + s;
+        uint32_t word = 0;
+        if (w < n_words) {
+            const uint32_t i0 = w * 32u;
+            if (vec && i0 + 32u <= n) {
+                float4 q[8];
+                const float4 *p4 = reinterpret_cast<const float4 *>(vals + i0);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) q[k] = __ldg(p4 + k);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    word |= (uint32_t)data_cmp(cmp, q[k].x, t) << (4 * k);
+                    word |= (uint32_t)data_cmp(cmp, q[k].y, t) << (4 * k + 1);
+                    word |= (uint32_t)data_cmp(cmp, q[k].z, t) << (4 * k + 2);
+                    word |= (uint32_t)data_cmp(cmp, q[k].w, t) << (4 * k + 3);
                 }
-                word = __ballot_sync(FULL, p);
+            } else {
+                for (uint32_t k = 0; k < 32u && i0 + k < n; ++k)
+                    word |= (uint32_t)data_cmp(cmp, __ldg(vals + i0 + k), t) << k;
             }
-            if (lane == (uint32_t)j) v[s] = word;
         }
+        v[s] = word;
     }
 }
 
@@ -387,17 +399,27 @@ __device__ __forceinline__ bool data_cmp(uint32_t cmp, float x, float t) {
 // 32-bit word of a float value or of a string id): a float compare (numeric
 // roles, Algorithms 9-10), id equality (string EQUAL, Algorithms 11-12) or a
 // bit of the pattern's containment row (string CONTAIN, Algorithms 13-14).
+// ValueTest carries the kind at run time; exist_words is compiled once per
+// kind (FloatTest, IdEqTest, IdBitTest) and dispatched once per restriction.
 struct ValueTest {
     enum : uint32_t { FLOAT_CMP = 0, ID_EQ = 1, ID_BIT = 2 };
     uint32_t mode;
     uint32_t cmp;           // FLOAT_CMP: HEDL_OP_DGE / DLE / DEQ
     uint32_t arg;           // FLOAT_CMP: the threshold's bits; ID_EQ: the string id
     const uint32_t *bits;   // ID_BIT: the containment row
-    __device__ __forceinline__ bool operator()(uint32_t x) const {
-        if (mode == FLOAT_CMP) return data_cmp(cmp, __uint_as_float(x), __uint_as_float(arg));
-        if (mode == ID_EQ) return x == arg;
-        return (__ldg(bits + (x >> 5)) >> (x & 31u)) & 1u;
-    }
+};
+struct FloatTest {
+    uint32_t cmp;
+    float t;
+    __device__ __forceinline__ bool operator()(uint32_t x) const { return data_cmp(cmp, __uint_as_float(x), t); }
+};
+struct IdEqTest {
+    uint32_t id;
+    __device__ __forceinline__ bool operator()(uint32_t x) const { return x == id; }
+};
+struct IdBitTest {
+    const uint32_t *bits;
+    __device__ __forceinline__ bool operator()(uint32_t x) const { return (__ldg(bits + (x >> 5)) >> (x & 31u)) & 1u; }
 };
 
 // Existential restriction on a concrete role with several values per
@@ -405,13 +427,13 @@ struct ValueTest {
 // vals[rp[i] .. rp[i+1]) passes the test.  The 32 individuals of a word own
 // one contiguous run of values; the warp reads it EX_STEP values a step (four
 // coalesced loads), ballots the tests, and each lane tests the bits that fall
-// in its own sub-range.  The words are software-pipelined: while word w is
-// tested, the row pointers of word w+2 and the first step of word w+1 are in
-// flight, so a word whose run fits one step costs one memory latency,
-// overlapped.  A longer run continues step by step and the warp leaves it
-// once every individual whose values reach past the step has found one (the
-// paper's skip over a subject already satisfied), so a heavy subject costs
-// 1/32 of a lane walk.
+// in its own sub-range.  The words are software-pipelined two deep: while
+// word w is tested, the first steps of words w+1 and w+2 and the row pointers
+// of word w+3 are in flight, so a word whose run fits one step costs a third
+// of a memory latency.  A longer run continues step by step and the warp
+// leaves it once every individual whose values reach past the step has found
+// one (the paper's skip over a subject already satisfied), so a heavy subject
+// costs 1/32 of a lane walk.
 constexpr uint32_t EX_LOADS = 4;
 constexpr uint32_t EX_STEP = 32u * EX_LOADS;
 
@@ -437,8 +459,9 @@ __device__ __forceinline__ void ex_fetch(const uint32_t *vals, uint32_t c, uint3
 }
 
 // does a value in [c, c + EX_STEP) of this lane's row [lo, hi) pass?
+template <class Test>
 __device__ __forceinline__ bool ex_test(const uint32_t (&x)[EX_LOADS], uint32_t c, uint32_t end, uint32_t lo,
-                                        uint32_t hi, uint32_t lane, const ValueTest &test) {
+                                        uint32_t hi, uint32_t lane, const Test &test) {
     bool hit = false;
 #pragma unroll
     for (uint32_t u = 0; u < EX_LOADS; ++u) {
@@ -450,46 +473,67 @@ __device__ __forceinline__ bool ex_test(const uint32_t (&x)[EX_LOADS], uint32_t 
     return hit;
 }
 
-template <int WPL>
-__device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const ValueTest test,
-                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
-                                            uint32_t (&v)[WPL]) {
-    // word w: row [lo, hi), run [base, end), first step x; word w+1: row [lo1, hi1)
-    uint32_t lo, hi, lo1, hi1;
-    ex_row(rp, wb, n_words, n, lane, lo, hi);
-    uint32_t base = __shfl_sync(FULL, lo, 0), end = __reduce_max_sync(FULL, hi);
-    uint32_t x[EX_LOADS];
-    ex_fetch(vals, base, end, lane, x);
+template <int WPL, class Test>
+__device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const Test test, uint32_t n,
+                                            uint32_t n_words, uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
+    // word w: row [lo0, hi0), run [b0, e0), first step x0; word w+1: the same with 1;
+    // word w+2: with 2; word w+3: row [lo3, hi3)
+    uint32_t lo0, hi0, lo1, hi1, lo2, hi2;
+    ex_row(rp, wb, n_words, n, lane, lo0, hi0);
     ex_row(rp, wb + 1, n_words, n, lane, lo1, hi1);
+    ex_row(rp, wb + 2, n_words, n, lane, lo2, hi2);
+    uint32_t b0 = __shfl_sync(FULL, lo0, 0), e0 = __reduce_max_sync(FULL, hi0);
+    uint32_t b1 = __shfl_sync(FULL, lo1, 0), e1 = __reduce_max_sync(FULL, hi1);
+    uint32_t x0[EX_LOADS], x1[EX_LOADS];
+    ex_fetch(vals, b0, e0, lane, x0);
+    ex_fetch(vals, b1, e1, lane, x1);
     for (int j = 0; j < 32; ++j) {
 #pragma unroll
         for (int s = 0; s < WPL; ++s) {
             const uint32_t w = wb + (uint32_t)j * WPL + s;   // the words go in order: w + 1 is the next
             uint32_t word = 0;
             if (w < n_words) {   // warp-uniform; then lane 0's individual 32w < n exists
-                // start word w+1's first step and word w+2's row pointers
-                const uint32_t base1 = __shfl_sync(FULL, lo1, 0), end1 = __reduce_max_sync(FULL, hi1);
-                uint32_t x1[EX_LOADS];
-                ex_fetch(vals, base1, end1, lane, x1);
-                uint32_t lo2, hi2;
-                ex_row(rp, w + 2, n_words, n, lane, lo2, hi2);
+                // start word w+2's first step and word w+3's row pointers
+                const uint32_t b2 = __shfl_sync(FULL, lo2, 0), e2 = __reduce_max_sync(FULL, hi2);
+                uint32_t x2[EX_LOADS];
+                ex_fetch(vals, b2, e2, lane, x2);
+                uint32_t lo3, hi3;
+                ex_row(rp, w + 3, n_words, n, lane, lo3, hi3);
                 // test word w
-                bool hit = ex_test(x, base, end, lo, hi, lane, test);
-                for (uint32_t c = base + EX_STEP; c < end; c += EX_STEP) {
-                    if (__all_sync(FULL, hit || hi <= c)) break;
+                bool hit = ex_test(x0, b0, e0, lo0, hi0, lane, test);
+                for (uint32_t c = b0 + EX_STEP; c < e0; c += EX_STEP) {
+                    if (__all_sync(FULL, hit || hi0 <= c)) break;
                     uint32_t y[EX_LOADS];
-                    ex_fetch(vals, c, end, lane, y);
-                    hit = ex_test(y, c, end, lo, hi, lane, test) || hit;
+                    ex_fetch(vals, c, e0, lane, y);
+                    hit = ex_test(y, c, e0, lo0, hi0, lane, test) || hit;
                 }
                 word = __ballot_sync(FULL, hit);
-                lo = lo1, hi = hi1, base = base1, end = end1;
-                lo1 = lo2, hi1 = hi2;
+                lo0 = lo1, hi0 = hi1, b0 = b1, e0 = e1;
+                lo1 = lo2, hi1 = hi2, b1 = b2, e1 = e2;
+                lo2 = lo3, hi2 = hi3;
 #pragma unroll
-                for (uint32_t u = 0; u < EX_LOADS; ++u) x[u] = x1[u];
+                for (uint32_t u = 0; u < EX_LOADS; ++u) {
+                    x0[u] = x1[u];
+                    x1[u] = x2[u];
+                }
             }
             if (lane == (uint32_t)j) v[s] = word;
         }
     }
+}
+
+// exist_words with the test's kind resolved at compile time (one dispatch per
+// restriction, warp-uniform).
+template <int WPL>
+__device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const ValueTest &test,
+                                            uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
+                                            uint32_t (&v)[WPL]) {
+    if (test.mode == ValueTest::FLOAT_CMP)
+        exist_words<WPL>(rp, vals, FloatTest{test.cmp, __uint_as_float(test.arg)}, n, n_words, wb, lane, v);
+    else if (test.mode == ValueTest::ID_EQ)
+        exist_words<WPL>(rp, vals, IdEqTest{test.arg}, n, n_words, wb, lane, v);
+    else
+        exist_words<WPL>(rp, vals, IdBitTest{test.bits}, n, n_words, wb, lane, v);
 }
 
 // The test of a D_DATA instruction on a numeric or string role (op word bit 8

@@ -35,6 +35,7 @@ struct ExecArgs {
 template <int NW, int WPL>
 struct Smem {
     uint32_t stk[NW][STACK_MAX][WPL][32];
+    uint64_t leaf[NW][PF_SLOTS];   // per warp: the segment's first leaf rows (bit 0 set: a slot)
     uint32_t item;
     uint32_t ok;
     uint32_t pad[2];
@@ -61,12 +62,59 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
     // words of no one: every load, store and walk stops at the warp's limit
     const uint32_t ww = hd.warp_words;
     const uint32_t rounds = hd.tile_words / (NW * ww * WPL);
+    // The segment's first PF concept-row and slot leaves, in code order: each
+    // round loads them all at once (their latencies overlap), and the stack
+    // machine takes the k-th such leaf from pf[k] instead of loading it where
+    // it stands.  The warp builds the table with one ballot per 32
+    // instructions.
+    constexpr int PF = WPL == 1 ? PF_SLOTS : 2;
+    uint32_t n_pf = 0;
+    for (uint32_t b0 = 0; b0 < seg.code_len && n_pf < (uint32_t)PF; b0 += 32) {
+        const uint32_t pc = b0 + lane;
+        uint64_t addr = 0;
+        bool leaf = false;
+        if (pc < seg.code_len) {
+            const DInsn d = code[pc];
+            const uint32_t op = d.op & 0xFFu;
+            if (op == D_ATOM) {
+                leaf = true;
+                addr = reinterpret_cast<uint64_t>(kb.concepts + (uint64_t)d.a * kb.wp);
+            } else if (op == D_SLOT) {
+                leaf = true;
+                addr = reinterpret_cast<uint64_t>(slots + (uint64_t)d.ref * kb.wp) | 1ull;
+            }
+        }
+        const uint32_t m = __ballot_sync(FULL, leaf);
+        const uint32_t rank = n_pf + __popc(m & ((1u << lane) - 1u));
+        if (leaf && rank < (uint32_t)PF) sm.leaf[warp][rank] = addr;
+        n_pf = min((uint32_t)PF, n_pf + (uint32_t)__popc(m));
+    }
+    __syncwarp();
+    const bool score = seg.hyp != NO_HYP && A.counts;
     uint32_t tp = 0, fp = 0;
     for (uint32_t r = 0; r < rounds; ++r) {
         const uint32_t wb = tile * hd.tile_words + (r * NW + warp) * ww * WPL;
         if (wb >= kb.wp) break;
         const uint32_t lim_p = min(kb.wp, wb + ww * WPL);   // padded row words
         const uint32_t lim_w = min(kb.w, wb + ww * WPL);    // words holding individuals
+        uint32_t pf[PF][WPL];
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            if ((uint32_t)k < n_pf) {
+                const uint64_t a = sm.leaf[warp][k];
+                if (a & 1ull) load_row_rw<WPL>(reinterpret_cast<const uint32_t *>(a & ~1ull), wb, lane, lim_p, pf[k]);
+                else load_row_ro<WPL>(reinterpret_cast<const uint32_t *>(a), wb, lane, lim_p, pf[k]);
+            } else {
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) pf[k][s] = 0u;
+            }
+        }
+        uint32_t pv[WPL], nv[WPL];
+        if (score) {
+            load_row_ro<WPL>(kb.pos, wb, lane, lim_p, pv);
+            load_row_ro<WPL>(kb.neg, wb, lane, lim_p, nv);
+        }
+        uint32_t n_used = 0;   // concept-row and slot leaves met so far this round
         uint32_t top[WPL];
         uint32_t sp = 0;  // values on the stack, top included
         for (uint32_t pc = 0; pc < seg.code_len; ++pc) {
@@ -95,10 +143,22 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
             sp += 1;
             switch (op) {
             case D_ATOM:
-                load_row_ro<WPL>(kb.concepts + (uint64_t)d.a * kb.wp, wb, lane, lim_p, top);
-                break;
             case D_SLOT:
-                load_row_rw<WPL>(slots + (uint64_t)d.ref * kb.wp, wb, lane, lim_p, top);
+                if (n_used < n_pf) {   // loaded at the start of the round
+#pragma unroll
+                    for (int s = 0; s < WPL; ++s) {
+                        uint32_t x = pf[0][s];
+#pragma unroll
+                        for (int k = 1; k < PF; ++k)
+                            if ((uint32_t)k == n_used) x = pf[k][s];
+                        top[s] = x;
+                    }
+                } else if (op == D_ATOM) {
+                    load_row_ro<WPL>(kb.concepts + (uint64_t)d.a * kb.wp, wb, lane, lim_p, top);
+                } else {
+                    load_row_rw<WPL>(slots + (uint64_t)d.ref * kb.wp, wb, lane, lim_p, top);
+                }
+                ++n_used;
                 break;
             case D_TOP:
 #pragma unroll
@@ -136,10 +196,7 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
         if (seg.out_slot != NO_SLOT) store_row<WPL>(slots + (uint64_t)seg.out_slot * kb.wp, wb, lane, lim_p, top);
         if (seg.hyp != NO_HYP) {
             if (A.out_bits) store_row<WPL>(A.out_bits + (uint64_t)seg.hyp * kb.wp, wb, lane, lim_p, top);
-            if (A.counts) {
-                uint32_t pv[WPL], nv[WPL];
-                load_row_ro<WPL>(kb.pos, wb, lane, lim_p, pv);
-                load_row_ro<WPL>(kb.neg, wb, lane, lim_p, nv);
+            if (score) {
 #pragma unroll
                 for (int s = 0; s < WPL; ++s) {
                     tp += __popc(top[s] & pv[s]);
@@ -224,94 +281,128 @@ __device__ __forceinline__ void sat_add3(uint32_t &a0, uint32_t &a1, uint32_t &a
 }
 
 constexpr uint32_t HEAVY_ROW = 64;   // longer rows are walked by the whole warp
-constexpr uint32_t WALK_STEP = 8;    // edges a lane loads per step (predicated)
+constexpr uint32_t WALK_LOADS = 8;   // edges a lane gathers per window
+constexpr uint32_t WALK_WIN = 32u * WALK_LOADS;   // edges per window
 
 // Walk task: for each individual, the saturating per-slice count of its
 // successors' FT words, mapped through the group's truth table, transposed
 // back into the 32 output slots (four words per lane per 16-byte store).
-// A lane walks its own row WALK_STEP edges at a time, all loads of a step
-// issued together; rows longer than HEAVY_ROW are walked by the whole warp,
-// 32 edges at a time, and their counts reduced across lanes.
+// The warp takes its words four at a time (128 individuals, whose rows form
+// one contiguous edge range) and streams that range in windows of WALK_WIN
+// edges: lane e loads edges e, e + 32, ... of the window (coalesced), gathers
+// their FT words and puts them in a per-warp shared-memory buffer; then each
+// lane adds the buffer entries of its own rows.  The next window's edges are
+// loaded while the current window's FT words are gathered, and windows that
+// hold no light row's edge are skipped.  Rows longer than HEAVY_ROW are
+// walked by the whole warp, 32 edges at a time, and their counts reduced
+// across lanes.
 template <int NW>
 __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *gp, uint32_t tile,
-                         uint32_t *slots) {
+                         uint32_t *slots, uint32_t *buf) {
     const KBView &kb = A.kb;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const DevCSR g = kb.csr[gp->role2];
     const uint32_t *__restrict__ rp = g.rp;
     const uint32_t *__restrict__ col = g.col;
     const uint32_t *ft = reinterpret_cast<const uint32_t *>(A.ws + gp->ft_off);
-    uint32_t want[8];
-#pragma unroll
-    for (int v = 0; v < 8; ++v) want[v] = gp->want[v];
     const uint32_t n = gp->n;
     uint32_t *my_row = slots + (uint64_t)(lane < n ? gp->out[lane] : 0u) * kb.wp;
     const uint32_t passes = hd.tile_words / (NW * 32u);
     for (uint32_t p = 0; p < passes; ++p) {
         const uint32_t wb = tile * hd.tile_words + (p * NW + warp) * 32u;
         if (wb >= kb.wp) break;
-        uint32_t nlo = 0, nhi = 0;   // row pointers of the next word, fetched ahead
-        if (wb < kb.w && wb * 32u + lane < kb.n) {
-            nlo = ld_stream(rp + wb * 32u + lane);
-            nhi = ld_stream(rp + wb * 32u + lane + 1);
-        }
         for (uint32_t jj = 0; jj < 32u; jj += 4) {
-          if (wb + jj >= kb.wp) break;   // wp and wb are multiples of 4: whole groups of four words
-          uint32_t outw[4];
+            if (wb + jj >= kb.wp) break;   // wp and wb are multiples of 4: whole groups of four words
+            uint32_t lo[4], hi[4];
+            bool light[4], heavy[4];
 #pragma unroll
-          for (uint32_t q = 0; q < 4; ++q) {
-            const uint32_t w = wb + jj + q;
-            const uint32_t i = w * 32u + lane;
-            const bool valid = w < kb.w && i < kb.n;
-            const uint32_t lo = nlo, hi = nhi;
-            if (w + 1 < kb.w && i + 32u < kb.n) {
-                nlo = ld_stream(rp + i + 32u);
-                nhi = ld_stream(rp + i + 33u);
-            }
-            uint32_t c0 = 0, c1 = 0, c2 = 0;
-            const bool heavy = hi - lo > HEAVY_ROW;
-            if (!heavy) {
-                for (uint32_t k0 = lo; k0 < hi; k0 += WALK_STEP) {
-                    uint32_t b[WALK_STEP];
-#pragma unroll
-                    for (uint32_t u = 0; u < WALK_STEP; ++u) b[u] = k0 + u < hi ? ld_stream(col + k0 + u) : 0u;
-                    uint32_t x[WALK_STEP];
-#pragma unroll
-                    for (uint32_t u = 0; u < WALK_STEP; ++u) x[u] = k0 + u < hi ? ft[b[u]] : 0u;
-#pragma unroll
-                    for (uint32_t u = 0; u < WALK_STEP; ++u) sat_add1(c0, c1, c2, x[u]);
+            for (uint32_t q = 0; q < 4; ++q) {
+                const uint32_t w = wb + jj + q, i = w * 32u + lane;
+                lo[q] = hi[q] = 0;
+                if (w < kb.w && i < kb.n) {
+                    lo[q] = ld_stream(rp + i);
+                    hi[q] = ld_stream(rp + i + 1);
                 }
+                heavy[q] = hi[q] - lo[q] > HEAVY_ROW;
+                light[q] = !heavy[q] && hi[q] > lo[q];
             }
-            uint32_t hm = __ballot_sync(FULL, heavy);
-            while (hm) {
-                const uint32_t h = __ffs(hm) - 1;
-                hm &= hm - 1;
-                const uint32_t hlo = __shfl_sync(FULL, lo, h), hhi = __shfl_sync(FULL, hi, h);
-                uint32_t d0 = 0, d1 = 0, d2 = 0;
-                for (uint32_t k = hlo + lane; k < hhi; k += 32u) sat_add1(d0, d1, d2, ft[ld_stream(col + k)]);
+            // the chunk's edge range ends at its last individual's row end
+            const uint32_t E1 = __reduce_max_sync(FULL, max(max(hi[0], hi[1]), max(hi[2], hi[3])));
+            // first edge at or after `at` that some light row of the chunk holds (E1 if none)
+            auto next_light = [&](uint32_t at) {
+                uint32_t m = E1;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const uint32_t e0 = __shfl_xor_sync(FULL, d0, o), e1 = __shfl_xor_sync(FULL, d1, o);
-                    const uint32_t e2 = __shfl_xor_sync(FULL, d2, o);
-                    sat_add3(d0, d1, d2, e0, e1, e2);
-                }
-                if (lane == h) {
-                    c0 = d0;
-                    c1 = d1;
-                    c2 = d2;
-                }
-            }
-            uint32_t r = 0;
+                for (uint32_t q = 0; q < 4; ++q)
+                    if (light[q] && hi[q] > at) m = min(m, max(lo[q], at));
+                return __reduce_min_sync(FULL, m);
+            };
+            uint32_t c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
+            uint32_t base = next_light(0);
+            uint32_t cn[WALK_LOADS];
+            auto fetch = [&](uint32_t at) {
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const uint32_t m = ((v & 4) ? c2 : ~c2) & ((v & 2) ? c1 : ~c1) & ((v & 1) ? c0 : ~c0);
-                r |= m & want[v];
+                for (uint32_t u = 0; u < WALK_LOADS; ++u) {
+                    const uint32_t e = at + 32u * u + lane;
+                    cn[u] = e < E1 ? ld_stream(col + e) : 0u;
+                }
+            };
+            if (base < E1) fetch(base);
+            while (base < E1) {   // warp-uniform
+                uint32_t x[WALK_LOADS];
+#pragma unroll
+                for (uint32_t u = 0; u < WALK_LOADS; ++u) x[u] = cn[u];
+                const uint32_t nb = base + WALK_WIN, next = next_light(nb);
+                if (next < E1) fetch(next);
+#pragma unroll
+                for (uint32_t u = 0; u < WALK_LOADS; ++u) x[u] = base + 32u * u + lane < E1 ? ft[x[u]] : 0u;
+#pragma unroll
+                for (uint32_t u = 0; u < WALK_LOADS; ++u) buf[32u * u + lane] = x[u];
+                __syncwarp();
+#pragma unroll
+                for (uint32_t q = 0; q < 4; ++q) {
+                    if (!light[q]) continue;
+                    const uint32_t k1 = min(hi[q], nb);
+                    for (uint32_t k = max(lo[q], base); k < k1; ++k) sat_add1(c0[q], c1[q], c2[q], buf[k - base]);
+                }
+                __syncwarp();
+                base = next;
             }
-            r = valid ? r : 0u;
-            outw[q] = transpose32(r, lane);   // lane s: slice s's word w
-          }
-          if (lane < n)   // 16-byte aligned: wb + jj is a multiple of 4
-              *reinterpret_cast<uint4 *>(my_row + wb + jj) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+            uint32_t outw[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                uint32_t hm = __ballot_sync(FULL, heavy[q]);
+                while (hm) {
+                    const uint32_t h = __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    const uint32_t hlo = __shfl_sync(FULL, lo[q], h), hhi = __shfl_sync(FULL, hi[q], h);
+                    uint32_t d0 = 0, d1 = 0, d2 = 0;
+                    for (uint32_t k = hlo + lane; k < hhi; k += 32u) sat_add1(d0, d1, d2, ft[ld_stream(col + k)]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const uint32_t e0 = __shfl_xor_sync(FULL, d0, o), e1 = __shfl_xor_sync(FULL, d1, o);
+                        const uint32_t e2 = __shfl_xor_sync(FULL, d2, o);
+                        sat_add3(d0, d1, d2, e0, e1, e2);
+                    }
+                    if (lane == h) {
+                        c0[q] = d0;
+                        c1[q] = d1;
+                        c2[q] = d2;
+                    }
+                }
+                const uint32_t w = wb + jj + q;
+                const bool valid = w < kb.w && w * 32u + lane < kb.n;
+                uint32_t r = 0;
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const uint32_t m = ((v & 4) ? c2[q] : ~c2[q]) & ((v & 2) ? c1[q] : ~c1[q]) &
+                                       ((v & 1) ? c0[q] : ~c0[q]);
+                    r |= m & gp->want[v];   // the group's truth table (cached, read per word)
+                }
+                r = valid ? r : 0u;
+                outw[q] = transpose32(r, lane);   // lane s: slice s's word w
+            }
+            if (lane < n)   // 16-byte aligned: wb + jj is a multiple of 4
+                *reinterpret_cast<uint4 *>(my_row + wb + jj) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
         }
     }
 }
@@ -371,17 +462,15 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(Ex
     uint32_t *slots = reinterpret_cast<uint32_t *>(A.ws + hd.off_slots);
     const RGroup *rgroups = reinterpret_cast<const RGroup *>(A.ws + hd.off_rgroups);
 
+    // Thread 0 claims the next item as soon as the current one may start (its
+    // dependencies are done), so the claim's round trip overlaps the work.
+    // Items are claimed in queue order and a CTA holds at most two, the one it
+    // runs and the next; every dependency points to an earlier item, so the
+    // earliest unfinished item is always running and the queue drains.
     uint32_t stride_next = A.item_begin + blockIdx.x;
+    uint32_t nxt = A.item_end;   // thread 0: the item claimed while the current one runs
+    if (threadIdx.x == 0) sm.item = A.use_queue ? A.item_begin + atomicAdd(&ctr->head, 1u) : stride_next;
     for (;;) {
-        if (threadIdx.x == 0) {
-            uint32_t it;
-            if (A.use_queue) {
-                it = *(volatile uint32_t *)&ctr->abort ? A.item_end : A.item_begin + atomicAdd(&ctr->head, 1u);
-            } else {
-                it = stride_next;
-            }
-            sm.item = it;
-        }
         __syncthreads();
         const uint32_t item = sm.item;
         stride_next += gridDim.x;
@@ -393,14 +482,19 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(Ex
         const uint32_t sidx = gsegs[grp.seg_begin + local % grp.n_segs];
         const Seg seg = segs[sidx];
         if (A.use_queue) {
-            if (threadIdx.x == 0) sm.ok = wait_deps(hd, deps, seg, done, ctr) ? 1u : 0u;
+            if (threadIdx.x == 0) {
+                const bool ok = wait_deps(hd, deps, seg, done, ctr);
+                sm.ok = ok ? 1u : 0u;
+                if (ok) nxt = A.item_begin + atomicAdd(&ctr->head, 1u);
+            }
             __syncthreads();
             if (!sm.ok) break;
         }
         if (seg.kind == TASK_TRANSPOSE) {
             run_transpose<NW>(A, hd, rgroups + seg.code_off, tile, slots);
         } else if (seg.kind == TASK_WALK) {
-            run_walk<NW>(A, hd, rgroups + seg.code_off, tile, slots);
+            // the warp's stack (unused by a walk) holds its window of gathered FT words
+            run_walk<NW>(A, hd, rgroups + seg.code_off, tile, slots, &sm.stk[threadIdx.x >> 5][0][0][0]);
         } else {
             if constexpr (STAGE) {
                 if (seg.filler != NO_FILLER) {
@@ -411,9 +505,14 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(Ex
             run_tile<NW, WPL, STAGE, BLK>(A, hd, seg, tile, sm, slots, acc);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && A.use_queue) {
-            __threadfence();
-            atomicAdd(done + sidx, 1u);
+        if (threadIdx.x == 0) {
+            if (A.use_queue) {
+                __threadfence();
+                atomicAdd(done + sidx, 1u);
+                sm.item = *(volatile uint32_t *)&ctr->abort ? A.item_end : nxt;
+            } else {
+                sm.item = stride_next;
+            }
         }
     }
 }
@@ -461,7 +560,7 @@ KernelFn pick(const Tuning &t, bool stage) {
 }
 
 size_t smem_bytes(const hedl_kb *kb, const Tuning &t, bool stage) {
-    size_t b = stack_smem_bytes(t) + 16;
+    size_t b = stack_smem_bytes(t) + 16;   // stacks, leaf tables, then item / ok / pad
     if (stage) b += 4ull * kb->wp;
     return b;
 }

@@ -160,8 +160,14 @@ struct Tuning {
 constexpr size_t SMEM_OPTIN_DEFAULT = 232448;   // bytes of shared memory a CTA may opt into
 constexpr int PLAN_ONLY_SMS = 152;               // planning-only handles plan for a 152-SM GB300
 
-// Shared-memory bytes of the interpreter's stack (per CTA).
-inline size_t stack_smem_bytes(const Tuning &t) { return sizeof(uint32_t) * (size_t)t.warps * STACK_MAX * t.wpl * 32; }
+// Leaf rows (concept rows and slots) a warp loads ahead at the start of each
+// round of a segment, in code order.
+constexpr int PF_SLOTS = 8;
+
+// Shared-memory bytes of the interpreter's stacks and leaf tables (per CTA).
+inline size_t stack_smem_bytes(const Tuning &t) {
+    return sizeof(uint32_t) * (size_t)t.warps * STACK_MAX * t.wpl * 32 + sizeof(uint64_t) * (size_t)t.warps * PF_SLOTS;
+}
 
 struct PlanImpl;
 
