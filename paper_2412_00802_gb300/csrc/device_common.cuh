@@ -427,10 +427,11 @@ struct IdBitTest {
 // vals[rp[i] .. rp[i+1]) passes the test.  The 32 individuals of a word own
 // one contiguous run of values; the warp reads it EX_STEP values a step (four
 // coalesced loads), ballots the tests, and each lane tests the bits that fall
-// in its own sub-range.  The words are software-pipelined two deep: while
-// word w is tested, the first steps of words w+1 and w+2 and the row pointers
-// of word w+3 are in flight, so a word whose run fits one step costs a third
-// of a memory latency.  A longer run continues step by step and the warp
+// in its own sub-range.  The words are software-pipelined: while word w is
+// tested, the first steps of words w+1 and w+2 and the row pointers of words
+// w+3 and w+4 are in flight (a word's first step is fetched two words after
+// its row pointers), so a word whose run fits one step costs a fraction of a
+// memory latency.  A longer run continues step by step and the warp
 // leaves it once every individual whose values reach past the step has found
 // one (the paper's skip over a subject already satisfied), so a heavy subject
 // costs 1/32 of a lane walk.
@@ -476,12 +477,12 @@ __device__ __forceinline__ bool ex_test(const uint32_t (&x)[EX_LOADS], uint32_t 
 template <int WPL, class Test>
 __device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const Test test, uint32_t n,
                                             uint32_t n_words, uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
-    // word w: row [lo0, hi0), run [b0, e0), first step x0; word w+1: the same with 1;
-    // word w+2: with 2; word w+3: row [lo3, hi3)
-    uint32_t lo0, hi0, lo1, hi1, lo2, hi2;
+    // rows [loK, hiK) of words w .. w+3; runs [bK, eK) and first steps xK of words w, w+1
+    uint32_t lo0, hi0, lo1, hi1, lo2, hi2, lo3, hi3;
     ex_row(rp, wb, n_words, n, lane, lo0, hi0);
     ex_row(rp, wb + 1, n_words, n, lane, lo1, hi1);
     ex_row(rp, wb + 2, n_words, n, lane, lo2, hi2);
+    ex_row(rp, wb + 3, n_words, n, lane, lo3, hi3);
     uint32_t b0 = __shfl_sync(FULL, lo0, 0), e0 = __reduce_max_sync(FULL, hi0);
     uint32_t b1 = __shfl_sync(FULL, lo1, 0), e1 = __reduce_max_sync(FULL, hi1);
     uint32_t x0[EX_LOADS], x1[EX_LOADS];
@@ -493,12 +494,12 @@ __device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *
             const uint32_t w = wb + (uint32_t)j * WPL + s;   // the words go in order: w + 1 is the next
             uint32_t word = 0;
             if (w < n_words) {   // warp-uniform; then lane 0's individual 32w < n exists
-                // start word w+2's first step and word w+3's row pointers
+                // start word w+2's first step (its rows came two words ago) and word w+4's rows
                 const uint32_t b2 = __shfl_sync(FULL, lo2, 0), e2 = __reduce_max_sync(FULL, hi2);
                 uint32_t x2[EX_LOADS];
                 ex_fetch(vals, b2, e2, lane, x2);
-                uint32_t lo3, hi3;
-                ex_row(rp, w + 3, n_words, n, lane, lo3, hi3);
+                uint32_t lo4, hi4;
+                ex_row(rp, w + 4, n_words, n, lane, lo4, hi4);
                 // test word w
                 bool hit = ex_test(x0, b0, e0, lo0, hi0, lane, test);
                 for (uint32_t c = b0 + EX_STEP; c < e0; c += EX_STEP) {
@@ -511,6 +512,7 @@ __device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *
                 lo0 = lo1, hi0 = hi1, b0 = b1, e0 = e1;
                 lo1 = lo2, hi1 = hi2, b1 = b2, e1 = e2;
                 lo2 = lo3, hi2 = hi3;
+                lo3 = lo4, hi3 = hi4;
 #pragma unroll
                 for (uint32_t u = 0; u < EX_LOADS; ++u) {
                     x0[u] = x1[u];

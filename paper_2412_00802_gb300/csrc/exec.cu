@@ -42,8 +42,17 @@ struct Smem {
     uint32_t filler[1];   // staged plans: the segment's filler row (wp words) from here on
 };
 
-__device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_groups, uint32_t item) {
-    uint32_t lo = 0, hi = n_groups;  // last group with item_begin <= item
+// The last group with item_begin <= item.  A CTA's items only grow (the queue
+// hands them out in order; static striding steps forward), so the search
+// starts at the CTA's previous group: a few steps forward, else a binary
+// search over the groups after it.
+__device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_groups, uint32_t item, uint32_t from) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (from + 1 >= n_groups || groups[from + 1].item_begin > item) return from;
+        ++from;
+    }
+    uint32_t lo = from, hi = n_groups;
     while (hi - lo > 1) {
         uint32_t mid = (lo + hi) >> 1;
         if (groups[mid].item_begin <= item) lo = mid;
@@ -92,12 +101,9 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
     __syncwarp();
     const bool score = seg.hyp != NO_HYP && A.counts;
     uint32_t tp = 0, fp = 0;
-    for (uint32_t r = 0; r < rounds; ++r) {
-        const uint32_t wb = tile * hd.tile_words + (r * NW + warp) * ww * WPL;
-        if (wb >= kb.wp) break;
+    // the leaf rows (and example rows) of one round, loaded together
+    auto prefetch = [&](uint32_t wb, uint32_t (&pf)[PF][WPL], uint32_t (&pv)[WPL], uint32_t (&nv)[WPL]) {
         const uint32_t lim_p = min(kb.wp, wb + ww * WPL);   // padded row words
-        const uint32_t lim_w = min(kb.w, wb + ww * WPL);    // words holding individuals
-        uint32_t pf[PF][WPL];
 #pragma unroll
         for (int k = 0; k < PF; ++k) {
             if ((uint32_t)k < n_pf) {
@@ -109,11 +115,19 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 for (int s = 0; s < WPL; ++s) pf[k][s] = 0u;
             }
         }
-        uint32_t pv[WPL], nv[WPL];
         if (score) {
             load_row_ro<WPL>(kb.pos, wb, lane, lim_p, pv);
             load_row_ro<WPL>(kb.neg, wb, lane, lim_p, nv);
+        } else {
+#pragma unroll
+            for (int s = 0; s < WPL; ++s) pv[s] = nv[s] = 0u;
         }
+    };
+    // the stack machine over one round's words
+    auto evaluate = [&](uint32_t wb, const uint32_t (&pf)[PF][WPL], const uint32_t (&pv)[WPL],
+                        const uint32_t (&nv)[WPL]) {
+        const uint32_t lim_p = min(kb.wp, wb + ww * WPL);   // padded row words
+        const uint32_t lim_w = min(kb.w, wb + ww * WPL);    // words holding individuals
         uint32_t n_used = 0;   // concept-row and slot leaves met so far this round
         uint32_t top[WPL];
         uint32_t sp = 0;  // values on the stack, top included
@@ -204,6 +218,31 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 }
             }
         }
+    };
+    // rounds in pairs: both rounds' rows are requested before either is evaluated
+    for (uint32_t r = 0; r < rounds; r += 2) {
+        const uint32_t wb0 = tile * hd.tile_words + (r * NW + warp) * ww * WPL;
+        if (wb0 >= kb.wp) break;
+        const uint32_t wb1 = wb0 + NW * ww * WPL;
+        const bool two = r + 1 < rounds && wb1 < kb.wp;
+        uint32_t pf0[PF][WPL], pv0[WPL], nv0[WPL], pf1[PF][WPL], pv1[WPL], nv1[WPL];
+        prefetch(wb0, pf0, pv0, nv0);
+        if (two) prefetch(wb1, pf1, pv1, nv1);
+        uint32_t wb = wb0;
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {   // one copy of the stack machine: round 1's rows move into round 0's
+            if (q == 1) {
+                if (!two) break;
+#pragma unroll
+                for (int k = 0; k < PF; ++k)
+#pragma unroll
+                    for (int s = 0; s < WPL; ++s) pf0[k][s] = pf1[k][s];
+#pragma unroll
+                for (int s = 0; s < WPL; ++s) pv0[s] = pv1[s], nv0[s] = nv1[s];
+                wb = wb1;
+            }
+            evaluate(wb, pf0, pv0, nv0);
+        }
     }
     if (seg.hyp != NO_HYP && A.counts) {
 #pragma unroll
@@ -233,18 +272,27 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
     return x;
 }
 
-// Transpose task: FT[i] bit s = slice s's filler at individual i (its
-// complement for REF_NEG slices), one 32-word pass per warp at a time.
-template <int NW>
+// Transpose task: word p of FT[i], bit s = slice 32p + s's filler at
+// individual i (its complement for REF_NEG slices), one 32-word pass per warp
+// at a time; lane s reads slice 32p + s's row.
+template <int NW, int P>
 __device__ void run_transpose(const ExecArgs &A, const PlanHeader &hd, const RGroup *gp, uint32_t tile,
                               const uint32_t *slots) {
     const KBView &kb = A.kb;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t n = gp->n;
-    const uint32_t ref = lane < n ? gp->filler[lane] : 0u;
-    const uint32_t id = ref & REF_ID;
-    const uint32_t *src = (ref & REF_SLOT) ? slots + (uint64_t)id * kb.wp : kb.concepts + (uint64_t)id * kb.wp;
-    const uint32_t x = (ref & REF_NEG) ? FULL : 0u;
+    const uint32_t *src[P];
+    uint32_t x[P];
+    bool on[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const uint32_t s = 32u * q + lane;
+        on[q] = s < n;
+        const uint32_t ref = on[q] ? gp->filler[s] : 0u;
+        const uint32_t id = ref & REF_ID;
+        src[q] = (ref & REF_SLOT) ? slots + (uint64_t)id * kb.wp : kb.concepts + (uint64_t)id * kb.wp;
+        x[q] = (ref & REF_NEG) ? FULL : 0u;
+    }
     uint32_t *ft = reinterpret_cast<uint32_t *>(A.ws + gp->ft_off);
     const uint32_t passes = hd.tile_words / (NW * 32u);
     for (uint32_t p = 0; p < passes; ++p) {
@@ -253,8 +301,11 @@ __device__ void run_transpose(const ExecArgs &A, const PlanHeader &hd, const RGr
         for (uint32_t j = 0; j < 32u; ++j) {
             const uint32_t w = wb + j;
             if (w >= kb.w) break;
-            const uint32_t v = lane < n ? (src[w] ^ x) : 0u;
-            ft[32ull * w + lane] = transpose32(v, lane);
+            uint32_t t[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) t[q] = transpose32(on[q] ? (src[q][w] ^ x[q]) : 0u, lane);
+            if constexpr (P == 1) ft[32ull * w + lane] = t[0];
+            else reinterpret_cast<uint2 *>(ft)[32ull * w + lane] = make_uint2(t[0], t[1]);
         }
     }
 }
@@ -281,24 +332,25 @@ __device__ __forceinline__ void sat_add3(uint32_t &a0, uint32_t &a1, uint32_t &a
 }
 
 constexpr uint32_t HEAVY_ROW = 64;   // longer rows are walked by the whole warp
-constexpr uint32_t WALK_LOADS = 8;   // edges a lane gathers per window
-constexpr uint32_t WALK_WIN = 32u * WALK_LOADS;   // edges per window
+constexpr uint32_t WALK_BUF = 256;   // 32-bit words of a warp's window buffer
 
 // Walk task: for each individual, the saturating per-slice count of its
-// successors' FT words, mapped through the group's truth table, transposed
-// back into the 32 output slots (four words per lane per 16-byte store).
-// The warp takes its words four at a time (128 individuals, whose rows form
-// one contiguous edge range) and streams that range in windows of WALK_WIN
-// edges: lane e loads edges e, e + 32, ... of the window (coalesced), gathers
-// their FT words and puts them in a per-warp shared-memory buffer; then each
-// lane adds the buffer entries of its own rows.  The next window's edges are
-// loaded while the current window's FT words are gathered, and windows that
-// hold no light row's edge are skipped.  Rows longer than HEAVY_ROW are
-// walked by the whole warp, 32 edges at a time, and their counts reduced
-// across lanes.
-template <int NW>
+// successors' FT words (P words each: 32 P slices), mapped through the
+// group's truth tables, transposed back into the output slots (four words per
+// lane per 16-byte store).  The warp takes its words four at a time (128
+// individuals, whose rows form one contiguous edge range) and streams that
+// range in windows of WALK_BUF / P edges: lane e loads edges e, e + 32, ...
+// of the window (coalesced), gathers their FT words and puts them in a
+// per-warp shared-memory buffer; then each lane adds the buffer entries of its
+// own rows.  The next window's edges are loaded while the current window's FT
+// words are gathered, and windows that hold no light row's edge are skipped.
+// Rows longer than HEAVY_ROW are walked by the whole warp, 32 edges at a time,
+// and their counts reduced across lanes.
+template <int NW, int P>
 __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *gp, uint32_t tile,
                          uint32_t *slots, uint32_t *buf) {
+    constexpr uint32_t LOADS = WALK_BUF / (32u * P);   // edges a lane gathers per window
+    constexpr uint32_t WIN = 32u * LOADS;
     const KBView &kb = A.kb;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const DevCSR g = kb.csr[gp->role2];
@@ -306,7 +358,16 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
     const uint32_t *__restrict__ col = g.col;
     const uint32_t *ft = reinterpret_cast<const uint32_t *>(A.ws + gp->ft_off);
     const uint32_t n = gp->n;
-    uint32_t *my_row = slots + (uint64_t)(lane < n ? gp->out[lane] : 0u) * kb.wp;
+    // one FT entry (P words) of individual b
+    auto ft_at = [&](uint32_t b, uint32_t (&o)[P]) {
+        if constexpr (P == 1) {
+            o[0] = ft[b];
+        } else {
+            const uint2 q = reinterpret_cast<const uint2 *>(ft)[b];
+            o[0] = q.x;
+            o[1] = q.y;
+        }
+    };
     const uint32_t passes = hd.tile_words / (NW * 32u);
     for (uint32_t p = 0; p < passes; ++p) {
         const uint32_t wb = tile * hd.tile_words + (p * NW + warp) * 32u;
@@ -336,38 +397,61 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                     if (light[q] && hi[q] > at) m = min(m, max(lo[q], at));
                 return __reduce_min_sync(FULL, m);
             };
-            uint32_t c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
+            uint32_t c0[4][P], c1[4][P], c2[4][P];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q)
+#pragma unroll
+                for (int k = 0; k < P; ++k) c0[q][k] = c1[q][k] = c2[q][k] = 0;
             uint32_t base = next_light(0);
-            uint32_t cn[WALK_LOADS];
+            uint32_t cn[LOADS];
             auto fetch = [&](uint32_t at) {
 #pragma unroll
-                for (uint32_t u = 0; u < WALK_LOADS; ++u) {
+                for (uint32_t u = 0; u < LOADS; ++u) {
                     const uint32_t e = at + 32u * u + lane;
                     cn[u] = e < E1 ? ld_stream(col + e) : 0u;
                 }
             };
             if (base < E1) fetch(base);
             while (base < E1) {   // warp-uniform
-                uint32_t x[WALK_LOADS];
+                uint32_t b[LOADS];
 #pragma unroll
-                for (uint32_t u = 0; u < WALK_LOADS; ++u) x[u] = cn[u];
-                const uint32_t nb = base + WALK_WIN, next = next_light(nb);
+                for (uint32_t u = 0; u < LOADS; ++u) b[u] = cn[u];
+                const uint32_t nb = base + WIN, next = next_light(nb);
                 if (next < E1) fetch(next);
+                uint32_t x[LOADS][P];
 #pragma unroll
-                for (uint32_t u = 0; u < WALK_LOADS; ++u) x[u] = base + 32u * u + lane < E1 ? ft[x[u]] : 0u;
+                for (uint32_t u = 0; u < LOADS; ++u) {
+                    if (base + 32u * u + lane < E1) {
+                        ft_at(b[u], x[u]);
+                    } else {
 #pragma unroll
-                for (uint32_t u = 0; u < WALK_LOADS; ++u) buf[32u * u + lane] = x[u];
+                        for (int k = 0; k < P; ++k) x[u][k] = 0u;
+                    }
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < LOADS; ++u) {   // one P-word store per lane: no bank conflicts
+                    if constexpr (P == 1) buf[32u * u + lane] = x[u][0];
+                    else reinterpret_cast<uint2 *>(buf)[32u * u + lane] = make_uint2(x[u][0], x[u][1]);
+                }
                 __syncwarp();
 #pragma unroll
                 for (uint32_t q = 0; q < 4; ++q) {
                     if (!light[q]) continue;
                     const uint32_t k1 = min(hi[q], nb);
-                    for (uint32_t k = max(lo[q], base); k < k1; ++k) sat_add1(c0[q], c1[q], c2[q], buf[k - base]);
+                    for (uint32_t e = max(lo[q], base); e < k1; ++e) {
+                        if constexpr (P == 1) {
+                            sat_add1(c0[q][0], c1[q][0], c2[q][0], buf[e - base]);
+                        } else {
+                            const uint2 y = reinterpret_cast<const uint2 *>(buf)[e - base];
+                            sat_add1(c0[q][0], c1[q][0], c2[q][0], y.x);
+                            sat_add1(c0[q][1], c1[q][1], c2[q][1], y.y);
+                        }
+                    }
                 }
                 __syncwarp();
                 base = next;
             }
-            uint32_t outw[4];
+            uint32_t outw[P][4];
 #pragma unroll
             for (uint32_t q = 0; q < 4; ++q) {
                 uint32_t hm = __ballot_sync(FULL, heavy[q]);
@@ -375,34 +459,52 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                     const uint32_t h = __ffs(hm) - 1;
                     hm &= hm - 1;
                     const uint32_t hlo = __shfl_sync(FULL, lo[q], h), hhi = __shfl_sync(FULL, hi[q], h);
-                    uint32_t d0 = 0, d1 = 0, d2 = 0;
-                    for (uint32_t k = hlo + lane; k < hhi; k += 32u) sat_add1(d0, d1, d2, ft[ld_stream(col + k)]);
+                    uint32_t d0[P], d1[P], d2[P];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const uint32_t e0 = __shfl_xor_sync(FULL, d0, o), e1 = __shfl_xor_sync(FULL, d1, o);
-                        const uint32_t e2 = __shfl_xor_sync(FULL, d2, o);
-                        sat_add3(d0, d1, d2, e0, e1, e2);
+                    for (int k = 0; k < P; ++k) d0[k] = d1[k] = d2[k] = 0;
+                    for (uint32_t e = hlo + lane; e < hhi; e += 32u) {
+                        uint32_t y[P];
+                        ft_at(ld_stream(col + e), y);
+#pragma unroll
+                        for (int k = 0; k < P; ++k) sat_add1(d0[k], d1[k], d2[k], y[k]);
                     }
-                    if (lane == h) {
-                        c0[q] = d0;
-                        c1[q] = d1;
-                        c2[q] = d2;
+#pragma unroll
+                    for (int k = 0; k < P; ++k) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const uint32_t e0 = __shfl_xor_sync(FULL, d0[k], o), e1 = __shfl_xor_sync(FULL, d1[k], o);
+                            const uint32_t e2 = __shfl_xor_sync(FULL, d2[k], o);
+                            sat_add3(d0[k], d1[k], d2[k], e0, e1, e2);
+                        }
+                        if (lane == h) {
+                            c0[q][k] = d0[k];
+                            c1[q][k] = d1[k];
+                            c2[q][k] = d2[k];
+                        }
                     }
                 }
                 const uint32_t w = wb + jj + q;
                 const bool valid = w < kb.w && w * 32u + lane < kb.n;
-                uint32_t r = 0;
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const uint32_t m = ((v & 4) ? c2[q] : ~c2[q]) & ((v & 2) ? c1[q] : ~c1[q]) &
-                                       ((v & 1) ? c0[q] : ~c0[q]);
-                    r |= m & gp->want[v];   // the group's truth table (cached, read per word)
+                for (int k = 0; k < P; ++k) {
+                    uint32_t r = 0;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const uint32_t m = ((v & 4) ? c2[q][k] : ~c2[q][k]) & ((v & 2) ? c1[q][k] : ~c1[q][k]) &
+                                           ((v & 1) ? c0[q][k] : ~c0[q][k]);
+                        r |= m & gp->want[k][v];   // the group's truth table (cached, read per word)
+                    }
+                    r = valid ? r : 0u;
+                    outw[k][q] = transpose32(r, lane);   // lane s: slice 32k + s's word w
                 }
-                r = valid ? r : 0u;
-                outw[q] = transpose32(r, lane);   // lane s: slice s's word w
             }
-            if (lane < n)   // 16-byte aligned: wb + jj is a multiple of 4
-                *reinterpret_cast<uint4 *>(my_row + wb + jj) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const uint32_t s = 32u * k + lane;
+                if (s < n)   // 16-byte aligned: wb + jj is a multiple of 4
+                    *reinterpret_cast<uint4 *>(slots + (uint64_t)gp->out[s] * kb.wp + wb + jj) =
+                        make_uint4(outw[k][0], outw[k][1], outw[k][2], outw[k][3]);
+            }
         }
     }
 }
@@ -444,11 +546,12 @@ __device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *s
     }
 }
 
-// Register budget: every shape is compiled for 1,024 resident threads per SM
-// (64 registers a thread, half occupancy); FULL ones for 2,048 (32 registers,
-// full occupancy, at the price of spills).
+// Register budget: every shape is compiled for 768 resident threads per SM
+// (80 registers a thread; the prefetching stack machine and the windowed walks
+// spill heavily at 64); FULL ones for 2,048 (32 registers, full occupancy, at
+// the price of spills).
 template <int NW, int WPL, bool STAGE, int BLK, bool FULL = false>
-__global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(ExecArgs A) {
+__global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 24) / NW) exec_kernel(ExecArgs A) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
     const PlanHeader hd = *reinterpret_cast<const PlanHeader *>(A.ws);
@@ -469,13 +572,14 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(Ex
     // earliest unfinished item is always running and the queue drains.
     uint32_t stride_next = A.item_begin + blockIdx.x;
     uint32_t nxt = A.item_end;   // thread 0: the item claimed while the current one runs
+    uint32_t g = 0;              // the current item's group
     if (threadIdx.x == 0) sm.item = A.use_queue ? A.item_begin + atomicAdd(&ctr->head, 1u) : stride_next;
     for (;;) {
         __syncthreads();
         const uint32_t item = sm.item;
         stride_next += gridDim.x;
         if (item >= A.item_end) break;
-        const uint32_t g = find_group(groups, hd.n_groups, item);
+        g = find_group(groups, hd.n_groups, item, g);
         const Group grp = groups[g];
         const uint32_t local = item - grp.item_begin;
         const uint32_t tile = local / grp.n_segs;
@@ -491,10 +595,15 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 32) / NW) exec_kernel(Ex
             if (!sm.ok) break;
         }
         if (seg.kind == TASK_TRANSPOSE) {
-            run_transpose<NW>(A, hd, rgroups + seg.code_off, tile, slots);
+            const RGroup *gp = rgroups + seg.code_off;
+            if (gp->parts == 1) run_transpose<NW, 1>(A, hd, gp, tile, slots);
+            else run_transpose<NW, MAX_PARTS>(A, hd, gp, tile, slots);
         } else if (seg.kind == TASK_WALK) {
             // the warp's stack (unused by a walk) holds its window of gathered FT words
-            run_walk<NW>(A, hd, rgroups + seg.code_off, tile, slots, &sm.stk[threadIdx.x >> 5][0][0][0]);
+            const RGroup *gp = rgroups + seg.code_off;
+            uint32_t *buf = &sm.stk[threadIdx.x >> 5][0][0][0];
+            if (gp->parts == 1) run_walk<NW, 1>(A, hd, gp, tile, slots, buf);
+            else run_walk<NW, MAX_PARTS>(A, hd, gp, tile, slots, buf);
         } else {
             if constexpr (STAGE) {
                 if (seg.filler != NO_FILLER) {

@@ -98,21 +98,24 @@ struct Seg {
     uint32_t kind;       // TASK_*
 };
 
-// Up to 32 role restrictions of one role and direction, evaluated together:
-// the transpose turns the fillers into one word per individual (bit s =
-// slice s's filler), the walk adds those words over each individual's
-// successors in bit-sliced 3-bit saturating counters and maps the counts
-// through a truth table.
-constexpr uint32_t SLICES = 32;
+// Up to 64 role restrictions of one role, direction and role depth,
+// evaluated together: the transpose turns the fillers into `parts` words per
+// individual (bit s of word p = slice 32p + s's filler), the walk adds those
+// words over each individual's successors in bit-sliced 3-bit saturating
+// counters and maps the counts through a truth table per word.
+constexpr uint32_t SLICES = 32;      // slices per FT word
+constexpr uint32_t MAX_PARTS = 2;    // FT words per individual
 constexpr uint32_t SLICE_MAX_N = 6;  // counting restrictions with n <= 6 can be sliced
 
 struct RGroup {
     uint32_t role2;             // 2 * role + inverse
     uint32_t n;                 // slices in use
-    uint64_t ft_off;            // byte offset of the transposed fillers (uint32 per individual)
-    uint32_t want[8];           // bit s of want[v]: slice s holds at count v (v = 7: seven or more)
-    uint32_t filler[SLICES];    // filler refs (REF_NEG: count successors outside the filler)
-    uint32_t out[SLICES];       // output slots
+    uint64_t ft_off;            // byte offset of the transposed fillers (`parts` uint32 per individual)
+    uint32_t parts;             // FT words per individual: 1, or MAX_PARTS when n > SLICES
+    uint32_t pad;
+    uint32_t want[MAX_PARTS][8];   // bit s of want[p][v]: slice 32p + s holds at count v (v = 7: 7 or more)
+    uint32_t filler[SLICES * MAX_PARTS];   // filler refs (REF_NEG: count successors outside the filler)
+    uint32_t out[SLICES * MAX_PARTS];      // output slots
 };
 
 struct Group {

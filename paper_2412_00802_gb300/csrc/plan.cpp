@@ -288,11 +288,11 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     // itself included), the depth standing in for the level it becomes ready at.
     const bool sliced = !(flags & HEDL_NO_SLICE);
     std::vector<uint8_t> sl(NN, 0);
+    std::vector<uint32_t> rdepth(NN, 0);
     if (sliced) {
         auto eligible = [&](const PNode &n) {
             return is_role(n.op) && (n.op == HEDL_OP_EXISTS || n.op == HEDL_OP_FORALL || n.b <= SLICE_MAX_N);
         };
-        std::vector<uint32_t> rdepth(NN, 0);
         std::unordered_map<uint64_t, uint32_t> same;
         for (uint32_t i = 0; i < NN; ++i) {
             const PNode &n = nodes[i];
@@ -526,39 +526,76 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
         return fail(HEDL_ERR_BAD_PROGRAM, "internal: segment stack exceeds the device limit");
     }
     const uint32_t NSEG = (uint32_t)segs.size();
-    const uint64_t FT_BYTES = 4ull * 32ull * kb->wp;   // transposed fillers of one role group (>= 4 N)
+    const uint64_t FT_PART = 4ull * 32ull * kb->wp;   // one FT word per individual (>= 4 N bytes)
+
+    // Sliced restrictions are grouped by (role depth, role, direction): one
+    // group key per distinct triple, in a dense numbering.
+    std::vector<uint32_t> key_of(NN, 0xFFFFFFFFu);
+    std::vector<uint64_t> key_val;
+    uint32_t max_rd = 0;
+    {
+        std::unordered_map<uint64_t, uint32_t> ids;
+        for (uint32_t i = 0; i < NN; ++i) {
+            if (!sl[i]) continue;
+            const uint64_t k = ((uint64_t)rdepth[i] << 32) | (nodes[i].a * 2u + nodes[i].inv);
+            auto it = ids.find(k);
+            if (it == ids.end()) {
+                it = ids.emplace(k, (uint32_t)key_val.size()).first;
+                key_val.push_back(k);
+            }
+            key_of[i] = it->second;
+            max_rd = std::max(max_rd, rdepth[i]);
+        }
+    }
 
     // Production level of every slot and level of every segment, in node order
     // (children first).  A segment reading nothing is at level 0 and one level
-    // above the slots it reads; a sliced role restriction's transpose runs one
-    // level above its filler's producer (level 0 for a concept row) and its
-    // walk, which produces its slot, one level above that.
+    // above the slots it reads.  A sliced role restriction is ready one level
+    // above its filler's transpose, which runs one level above the filler's
+    // producer (level 0 for a concept row); all restrictions of a group key
+    // walk together, at the level of the group's last-ready one.  A filler
+    // holds only restrictions of smaller role depth, so the levels of depth d
+    // are final once those of depths below d are: one pass per depth fixes
+    // them in turn, and a last pass sets every level.
     std::vector<uint32_t> slot_level(n_slots, 0), seg_level(NSEG, 0);
+    std::vector<uint32_t> group_level(key_val.size(), 0);
     auto seg_lvl = [&](uint32_t sidx) {
         uint32_t lvl = 0;
         for (uint32_t sl2 : seg_slots_read[sidx]) lvl = std::max(lvl, slot_level[sl2] + 1);
         return lvl;
     };
-    for (uint32_t i = 0; i < NN; ++i) {
-        if (!mat[i]) continue;
-        if (sl[i]) {
-            const int32_t f = nodes[i].k0;
-            const bool concept_filler = nodes[f].op == HEDL_OP_ATOM && !mat[f];
-            slot_level[slot_of[i]] = concept_filler ? 1u : slot_level[slot_of[f]] + 2u;
-        } else {
-            const uint32_t sidx = seg_of_slot[slot_of[i]];
-            seg_level[sidx] = seg_lvl(sidx);
-            slot_level[slot_of[i]] = seg_level[sidx];
+    for (uint32_t d = 1; d <= max_rd + 1; ++d) {
+        std::vector<uint32_t> ready(key_val.size(), 0);
+        for (uint32_t i = 0; i < NN; ++i) {
+            if (!mat[i]) continue;
+            if (sl[i]) {
+                const int32_t f = nodes[i].k0;
+                const bool concept_filler = nodes[f].op == HEDL_OP_ATOM && !mat[f];
+                const uint32_t own = concept_filler ? 1u : slot_level[slot_of[f]] + 2u;
+                uint32_t lvl = own;
+                if (rdepth[i] < d) lvl = group_level[key_of[i]];
+                else if (rdepth[i] == d) ready[key_of[i]] = std::max(ready[key_of[i]], own);
+                slot_level[slot_of[i]] = lvl;
+            } else {
+                const uint32_t sidx = seg_of_slot[slot_of[i]];
+                seg_level[sidx] = seg_lvl(sidx);
+                slot_level[slot_of[i]] = seg_level[sidx];
+            }
         }
+        for (size_t k = 0; k < key_val.size(); ++k)
+            if ((key_val[k] >> 32) == d) group_level[k] = ready[k];
+        if (!sliced) break;
     }
     for (uint32_t sidx = 0; sidx < NSEG; ++sidx)
         if (segs[sidx].hyp != NO_HYP) seg_level[sidx] = seg_lvl(sidx);
 
-    // role groups: sliced restrictions keyed by (walk level, role, direction), 32 at a time
+    // role groups: sliced restrictions keyed by (role depth, role, direction), up to
+    // SLICES * MAX_PARTS at a time (one FT word per 32 of them)
     std::vector<RGroup> rgroups;
     std::vector<uint32_t> task_level(seg_level);
     std::vector<uint32_t> task_key(role_key);
     std::vector<std::vector<uint32_t>> task_reads(seg_slots_read);
+    uint64_t ft_bytes = 0;
     {
         std::vector<std::pair<uint64_t, uint32_t>> keyed;   // ((level << 32) | role2, node)
         for (uint32_t i = 0; i < NN; ++i)
@@ -569,10 +606,11 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                          });
         for (size_t k = 0; k < keyed.size();) {
             size_t k2 = k;
-            while (k2 < keyed.size() && keyed[k2].first == keyed[k].first && k2 - k < SLICES) ++k2;
+            while (k2 < keyed.size() && keyed[k2].first == keyed[k].first && k2 - k < SLICES * MAX_PARTS) ++k2;
             RGroup g{};
             g.role2 = (uint32_t)(keyed[k].first & 0xFFFFFFFFu);
             g.n = (uint32_t)(k2 - k);
+            g.parts = g.n > SLICES ? MAX_PARTS : 1u;
             std::vector<uint32_t> reads;
             for (size_t q = k; q < k2; ++q) {
                 const uint32_t i = keyed[q].second;
@@ -597,7 +635,7 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
                     case HEDL_OP_ATMOST: holds = v <= n.b; break;
                     default: holds = v == n.b; break;
                     }
-                    if (holds) g.want[v] |= 1u << s_;
+                    if (holds) g.want[s_ / SLICES][v] |= 1u << (s_ % SLICES);
                 }
                 p->info.n_role_ops++;
             }
@@ -626,6 +664,8 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
             for (uint32_t s_ = 0; s_ < g.n; ++s_) seg_of_slot[g.out[s_]] = walk_task;
             const DevCSR &csr = kb->csr_host[g.role2];
             model += (uint64_t)g.n * (4 * (N + 1) + 4ull * csr.n_edges + 2 * B);
+            g.ft_off = ft_bytes;   // relative to the FT region until the slots are placed
+            ft_bytes += g.parts * FT_PART;
             rgroups.push_back(g);
             k = k2;
         }
@@ -746,13 +786,13 @@ int build_plan(const hedl_kb *kb, const uint64_t *progs, const uint32_t *offs, u
     img.resize((img.size() + 255) & ~size_t(255));
     hd.off_slots = img.size();
     hd.off_ft = (hd.off_slots + (uint64_t)n_slots * B + 255) & ~uint64_t(255);
-    for (size_t g = 0; g < rgroups.size(); ++g) rgroups[g].ft_off = hd.off_ft + g * FT_BYTES;
+    for (size_t g = 0; g < rgroups.size(); ++g) rgroups[g].ft_off += hd.off_ft;
     if (!rgroups.empty()) memcpy(img.data() + hd.off_rgroups, rgroups.data(), rgroups.size() * sizeof(RGroup));
     hd.timeout_ns = (uint64_t)t.timeout_ms * 1000000ull;
     memcpy(img.data(), &hd, sizeof hd);
     p->image_bytes = img.size();
     p->slots_off = hd.off_slots;
-    p->ws_bytes = hd.off_ft + (uint64_t)rgroups.size() * FT_BYTES;
+    p->ws_bytes = hd.off_ft + ft_bytes;
     p->n_rgroups = (uint32_t)rgroups.size();
     p->info.n_role_groups = (uint32_t)rgroups.size();
     p->level_items = level_items;
