@@ -405,7 +405,7 @@ int execute(hedl_kb *kb, const PlanImpl *pc, uint32_t *counts, uint32_t *out_bit
     }
     if (p->bps == 0) {  // launch shape, resolved outside any stream capture
         int bps = 0;
-        int oe = exec_occupancy(kb, p->tuning, &bps);
+        int oe = exec_occupancy(kb, p->tuning, p->n_rgroups > 0, &bps);
         if (oe) return cuda_fail(oe, "occupancy query");
         if (bps < 1) return fail(HEDL_ERR_CUDA, "the interpreter kernel does not fit on an SM");
         p->bps = bps;

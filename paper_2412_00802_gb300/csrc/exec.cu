@@ -9,13 +9,16 @@
 // by the warp's edge-stream CSR walk (role_stream).  A segment's result is
 // written to its slot, or, for a hypothesis root, reduced against the example
 // sets by popcount (the paper's coverage count, Algorithm 15) with one atomic
-// per warp.  A role group (up to 32 restrictions sharing a role, direction
-// and level) runs as two tasks: a transpose of its fillers into one 32-bit
-// word per individual, and one bit-sliced walk that evaluates all of them.
+// per warp.  A role group (up to 64 restrictions sharing a role, direction
+// and role depth) runs as two tasks: a transpose of its fillers into one or
+// two 32-bit words per individual, and one bit-sliced walk that evaluates all
+// of them.
 //
 // Waits never spin unbounded: each gives up after the plan's timeout, sets an
 // abort flag and an error bit, and every CTA then leaves the kernel.
 #include <cuda_runtime.h>
+
+#include <cstddef>
 
 #include "device_common.cuh"
 
@@ -549,9 +552,17 @@ __device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *s
 // Register budget: every shape is compiled for 768 resident threads per SM
 // (80 registers a thread; the prefetching stack machine and the windowed walks
 // spill heavily at 64); FULL ones for 2,048 (32 registers, full occupancy, at
-// the price of spills).
-template <int NW, int WPL, bool STAGE, int BLK, bool FULL = false>
-__global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 24) / NW) exec_kernel(ExecArgs A) {
+// the price of spills).  GROUPS = false leaves the role groups' transposes and
+// walks out (for plans without role groups: a lone hypothesis, concrete-role
+// restrictions); the rest fits 64 registers, so that build keeps 1,024
+// threads per SM for the latency-bound lone walks and value streams.
+template <int NW, int WPL, bool STAGE, int BLK, bool FULL = false, bool GROUPS = true>
+__global__ void __launch_bounds__(NW * 32, (FULL ? 64 : (GROUPS ? 24 : 32)) / NW) exec_kernel(ExecArgs A) {
+    // the host sizes the dynamic shared memory as stack_smem_bytes + 16 (+ a staged filler)
+    using SmemT = Smem<NW, WPL>;
+    static_assert(offsetof(SmemT, filler) ==
+                      sizeof(uint32_t) * NW * STACK_MAX * WPL * 32 + sizeof(uint64_t) * NW * PF_SLOTS + 16,
+                  "the shared-memory layout and its host-side size disagree");
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem<NW, WPL> &sm = *reinterpret_cast<Smem<NW, WPL> *>(smem_raw);
     const PlanHeader hd = *reinterpret_cast<const PlanHeader *>(A.ws);
@@ -594,16 +605,26 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : 24) / NW) exec_kernel(Ex
             __syncthreads();
             if (!sm.ok) break;
         }
-        if (seg.kind == TASK_TRANSPOSE) {
-            const RGroup *gp = rgroups + seg.code_off;
-            if (gp->parts == 1) run_transpose<NW, 1>(A, hd, gp, tile, slots);
-            else run_transpose<NW, MAX_PARTS>(A, hd, gp, tile, slots);
+        if (seg.kind != TASK_SEGMENT && !GROUPS) {
+            // a build without role groups was given a plan with them (the host never does this)
+            if (threadIdx.x == 0) {
+                atomicOr(&ctr->err, ST_DEVICE_CHECK);
+                atomicExch(&ctr->abort, 1u);
+            }
+        } else if (seg.kind == TASK_TRANSPOSE) {
+            if constexpr (GROUPS) {
+                const RGroup *gp = rgroups + seg.code_off;
+                if (gp->parts == 1) run_transpose<NW, 1>(A, hd, gp, tile, slots);
+                else run_transpose<NW, MAX_PARTS>(A, hd, gp, tile, slots);
+            }
         } else if (seg.kind == TASK_WALK) {
-            // the warp's stack (unused by a walk) holds its window of gathered FT words
-            const RGroup *gp = rgroups + seg.code_off;
-            uint32_t *buf = &sm.stk[threadIdx.x >> 5][0][0][0];
-            if (gp->parts == 1) run_walk<NW, 1>(A, hd, gp, tile, slots, buf);
-            else run_walk<NW, MAX_PARTS>(A, hd, gp, tile, slots, buf);
+            if constexpr (GROUPS) {
+                // the warp's stack (unused by a walk) holds its window of gathered FT words
+                const RGroup *gp = rgroups + seg.code_off;
+                uint32_t *buf = &sm.stk[threadIdx.x >> 5][0][0][0];
+                if (gp->parts == 1) run_walk<NW, 1>(A, hd, gp, tile, slots, buf);
+                else run_walk<NW, MAX_PARTS>(A, hd, gp, tile, slots, buf);
+            }
         } else {
             if constexpr (STAGE) {
                 if (seg.filler != NO_FILLER) {
@@ -661,7 +682,9 @@ KernelFn pick_t(uint32_t warps, uint32_t wpl) {
     return exec_kernel<8, 1, STAGE, BLK>;
 }
 
-KernelFn pick(const Tuning &t, bool stage) {
+KernelFn pick(const Tuning &t, bool stage, bool groups) {
+    if (!groups && !t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage)   // no role groups: 64 registers
+        return t.role_block == 4 ? exec_kernel<8, 1, false, 4, false, false> : exec_kernel<8, 1, false, 8, false, false>;
     if (t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage)
         return t.role_block == 4 ? exec_kernel<8, 1, false, 4, true> : exec_kernel<8, 1, false, 8, true>;
     if (t.role_block == 4) return stage ? pick_t<true, 4>(t.warps, t.wpl) : pick_t<false, 4>(t.warps, t.wpl);
@@ -682,9 +705,9 @@ bool use_staging(const hedl_kb *kb, const Tuning &t) {
 
 size_t exec_smem_bytes(const Tuning &t) { return stack_smem_bytes(t) + 16; }
 
-int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm) {
+int exec_occupancy(const hedl_kb *kb, const Tuning &t, bool groups, int *blocks_per_sm) {
     const bool stage = use_staging(kb, t);
-    KernelFn fn = pick(t, stage);
+    KernelFn fn = pick(t, stage, groups);
     size_t smem = smem_bytes(kb, t, stage);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -696,7 +719,7 @@ int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t
                 void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Tuning &t = p->tuning;
-    KernelFn fn = pick(t, p->staged);
+    KernelFn fn = pick(t, p->staged, p->n_rgroups > 0);
     size_t smem = smem_bytes(kb, t, p->staged);
     int bps = p->bps;
     if (bps < 1) return cudaErrorInvalidConfiguration;

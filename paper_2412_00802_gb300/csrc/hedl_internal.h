@@ -235,6 +235,13 @@ struct UmmaArgs {
     int relu, out_bf16;
     uint32_t *err;
     const void *mask;   // bf16 [M][ldc] or null: outputs where mask <= 0 become 0
+    // Optional fused output layer (the surrogate's N = 2 head): with w3 (bf16
+    // [2][N]) set, each row's bf16-rounded outputs are also dotted with both
+    // rows of w3 and the two partial sums added atomically to y (float
+    // [M][2], zeroed by the caller); store = 0 then skips writing C.
+    const void *w3 = nullptr;
+    float *y = nullptr;
+    int store = 1;
 };
 bool umma_shape_ok(const UmmaArgs &a);
 int umma_gemm(const UmmaArgs &a, void *stream);
@@ -295,7 +302,7 @@ int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t
 bool use_staging(const hedl_kb *kb, const Tuning &t);
 int launch_plain(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t *out_bits, void *ws,
                  void *stream);
-int exec_occupancy(const hedl_kb *kb, const Tuning &t, int *blocks_per_sm);
+int exec_occupancy(const hedl_kb *kb, const Tuning &t, bool groups, int *blocks_per_sm);
 int kb_validate_device(const hedl_kb *kb, void *stream, std::string *why);
 int contain_bitmap_device(const hedl_kb *kb, void *stream);
 int examples_count_device(const hedl_kb *kb, void *stream, uint32_t *np, uint32_t *nn);

@@ -295,6 +295,20 @@ int gemm(const GemmArgs &a0, bool a_km, bool b_kn, int splits, cudaStream_t s) {
 // Y[b][j] = sum_i H2[b][i] W3[j][i] + b3[j]: one warp per row.
 // With map (DEVICE float[5]: mean0, mean1, scale0, scale1, tail weight), the
 // raw output u is mapped back to the target scale: Y = u * scale + mean.
+// y = (u + b3), mapped back to the target scale when map is set, from the
+// fused output layer's sums u (the unfused path's out_fwd_kernel semantics).
+__global__ void out_map_kernel(const float *u, const float *b3, float *Y, int B, const float *map) {
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < B; row += gridDim.x * blockDim.x) {
+        float u0 = u[2 * row] + b3[0], u1 = u[2 * row + 1] + b3[1];
+        if (map) {
+            u0 = u0 * map[2] + map[0];
+            u1 = u1 * map[3] + map[1];
+        }
+        Y[2 * row] = u0;
+        Y[2 * row + 1] = u1;
+    }
+}
+
 __global__ void out_fwd_kernel(const __nv_bfloat16 *H2, const __nv_bfloat16 *W3, const float *b3, float *Y, int B,
                                const float *map) {
     // warp per row (grid-stride); lane l holds columns 16l .. 16l+15 of both W3 rows
@@ -674,9 +688,25 @@ int dense_relu(hedl_mlp *mlp, const __nv_bfloat16 *A, const __nv_bfloat16 *W, co
 }
 
 int forward_impl(hedl_mlp *mlp, const __nv_bfloat16 *X, uint32_t B, const MlpWs &w, cudaStream_t s,
-                 bool mapped) {
+                 bool mapped, bool need_h2 = true) {
     int e = dense_relu(mlp, X, mlp->wb + OFF_W1, mlp->w + OFF_B1, w.h1, (int)B, DI, s);
     if (e) return e;
+    if (!need_h2 && mlp->gemm == HEDL_GEMM_TCGEN05) {
+        // inference: the second layer's epilogue computes the output layer (h2 is never written)
+        UmmaArgs u{w.h1, mlp->wb + OFF_W2, w.h2, mlp->w + OFF_B2, (int)B, DH, DH, DH, DH, DH, 1, 1, mlp->err, nullptr};
+        u.w3 = mlp->wb + OFF_W3;
+        u.y = w.dy;   // [B][2] sums, zeroed first
+        u.store = 0;
+        if (umma_shape_ok(u)) {
+            e = cudaMemsetAsync(w.dy, 0, (size_t)B * DO * 4, s);
+            if (e) return e;
+            e = umma_gemm(u, s);
+            if (e) return e;
+            out_map_kernel<<<std::min<uint32_t>((B + 255) / 256, 148u * 8u), 256, 0, s>>>(
+                w.dy, mlp->w + OFF_B3, w.y, (int)B, mapped ? mlp->map : nullptr);
+            return cudaGetLastError();
+        }
+    }
     e = dense_relu(mlp, w.h1, mlp->wb + OFF_W2, mlp->w + OFF_B2, w.h2, (int)B, DH, s);
     if (e) return e;
     out_fwd_kernel<<<std::min<uint32_t>((B * 32 + 255) / 256, 148u * 8u), 256, 0, s>>>(
@@ -843,7 +873,7 @@ int hedl_mlp_forward(hedl_mlp *m, const uint16_t *X, uint32_t B, float *Y, void 
     if (!m || !X || !Y) return fail(HEDL_ERR_INVALID_ARG, "NULL argument");
     if (!ws || ws_bytes < mlp_ws_bytes(B)) return fail(HEDL_ERR_WORKSPACE_TOO_SMALL, "MLP workspace too small");
     MlpWs w = carve(ws, B);
-    int e = forward_impl(m, (const __nv_bfloat16 *)X, B, w, (cudaStream_t)s, true);
+    int e = forward_impl(m, (const __nv_bfloat16 *)X, B, w, (cudaStream_t)s, true, false);
     if (e) return cuda_fail(e, "mlp forward");
     e = cudaMemcpyAsync(Y, w.y, (size_t)B * DO * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)s);
     return e ? cuda_fail(e, "mlp forward copy") : HEDL_OK;

@@ -113,8 +113,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
         : "memory");
 }
 
-// Epilogue of 32 columns of one row: bias, ReLU or mask, bf16 or FP32 store.
-__device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, const uint32_t (&r)[32]) {
+// Fused output layer on 32 columns of one row: the bf16-rounded activations
+// (what the unfused path stores and reads back) dotted with both rows of w3.
+__device__ __forceinline__ void head32(const UmmaArgs &g, int col, const float (&v)[32], float &a0, float &a1) {
+    const uint4 *w0 = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(g.w3) + col);
+    const uint4 *w1 = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(g.w3) + g.N + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 x = __ldg(w0 + q), y = __ldg(w1 + q);
+        const uint32_t xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 wx = *reinterpret_cast<const __nv_bfloat162 *>(&xv[e]);
+            const __nv_bfloat162 wy = *reinterpret_cast<const __nv_bfloat162 *>(&yv[e]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
+            const float hl = __low2float(h), hh = __high2float(h);
+            a0 += hl * __low2float(wx) + hh * __high2float(wx);
+            a1 += hl * __low2float(wy) + hh * __high2float(wy);
+        }
+    }
+}
+
+// Epilogue of 32 columns of one row: bias, ReLU or mask, bf16 or FP32 store
+// (and the fused output layer's partial sums).
+__device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, const uint32_t (&r)[32], float &a0,
+                                       float &a1) {
     float v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -138,6 +161,8 @@ __device__ __forceinline__ void emit32(const UmmaArgs &g, int row, int col, cons
             }
         }
     }
+    if (g.w3) head32(g, col, v, a0, a1);
+    if (!g.store) return;
     if (g.out_bf16) {
         uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + (size_t)row * g.ldc + col);
 #pragma unroll
@@ -274,6 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant_
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = (t / tiles_n) * UM, n0 = (t % tiles_n) * UN;
             const int row = m0 + (int)(q * 32 + lane);
+            float a0 = 0.f, a1 = 0.f;   // the fused output layer's partial sums over this tile's columns
             for (int c0 = 0; c0 < UN; c0 += 64) {   // two 32-column loads in flight per wait
                 uint32_t ra[32], rb[32];
                 const uint32_t ta = taddr + ((q * 32u) << 16) + bf * UN + (uint32_t)c0;
@@ -281,9 +307,13 @@ __global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant_
                 tmem_ld32(ta + 32u, rb);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row < g.M) {
-                    emit32(g, row, n0 + c0, ra);
-                    emit32(g, row, n0 + c0 + 32, rb);
+                    emit32(g, row, n0 + c0, ra, a0, a1);
+                    emit32(g, row, n0 + c0 + 32, rb, a0, a1);
                 }
+            }
+            if (g.w3 && row < g.M) {
+                atomicAdd(g.y + 2 * (size_t)row, a0);
+                atomicAdd(g.y + 2 * (size_t)row + 1, a1);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -304,7 +334,8 @@ __global__ void __launch_bounds__(THREADS, 1) umma_kernel(const __grid_constant_
 bool umma_shape_ok(const UmmaArgs &a) {
     return a.N % UN == 0 && a.K % UK == 0 && a.K > 0 && a.lda % 8 == 0 && a.ldb % 8 == 0 &&
            a.ldc % (a.out_bf16 ? 8 : 4) == 0 && ((uintptr_t)a.A & 15) == 0 && ((uintptr_t)a.B & 15) == 0 &&
-           ((uintptr_t)a.C & 15) == 0 && (!a.mask || (a.ldc % 8 == 0 && ((uintptr_t)a.mask & 15) == 0));
+           ((uintptr_t)a.C & 15) == 0 && (!a.mask || (a.ldc % 8 == 0 && ((uintptr_t)a.mask & 15) == 0)) &&
+           (!a.w3 || (a.y && ((uintptr_t)a.w3 & 15) == 0 && a.N % 8 == 0));
 }
 
 namespace {
