@@ -247,7 +247,7 @@ def surrogate_round(args, dev):
     from paper_2412_00802_gb300 import surrogate as sg
     from oracle import surrogate as OS
     from synth import hyps, kb as K
-    full = args.surrogate_full
+    full = not args.surrogate_small
     cfg = K.CONFIGS["surrogate"] if full else K.CONFIGS["surrogate"].scaled(1_000_000)
     t0 = time.perf_counter()
     kb = K.generate(cfg)
@@ -483,7 +483,7 @@ def search_run(args, dev):
     from paper_2412_00802_gb300.surrogate import Surrogate, exact_scores
     from synth import hyps, kb as K, programs as P
     from synth.refine import Refiner
-    full = args.search_full
+    full = not args.search_small
     cfg = K.CONFIGS["search"] if full else K.CONFIGS["search"].scaled(1_000_000)
     t0 = time.perf_counter()
     kb = K.generate(cfg)
@@ -1055,16 +1055,19 @@ def main():
     ap.add_argument("--no-numeric", action="store_true", help="skip the numeric-concrete-role workload")
     ap.add_argument("--no-strings", action="store_true", help="skip the string-concrete-role workload")
     ap.add_argument("--surrogate-train", type=int, default=0,
-                    help="training hypotheses of the surrogate round (default 65,536; 1,000,000 with --surrogate-full)")
-    ap.add_argument("--surrogate-full", action="store_true",
-                    help="surrogate round at full size (10M individuals, 1M training hypotheses)")
+                    help="training hypotheses of the surrogate round (default 1,000,000; 65,536 with "
+                         "--surrogate-small)")
+    ap.add_argument("--surrogate-small", action="store_true",
+                    help="surrogate round on a 1M-individual KB of its distributions (the full size is 10M "
+                         "individuals and 1M training hypotheses, the default)")
     ap.add_argument("--latency", action="store_true",
                     help="the single-hypothesis latency workload (10M individuals) instead of the batched one")
     ap.add_argument("--mlp", action="store_true", help="time the surrogate's forward alone (both GEMM engines)")
     ap.add_argument("--latency-n", type=int, default=0,
                     help="individuals of the latency workload's KB (default: its full 10,000,000)")
-    ap.add_argument("--search-full", action="store_true",
-                    help="search at full size (4M individuals, 64 roles, 20 steps)")
+    ap.add_argument("--search-small", action="store_true",
+                    help="search on a 1M-individual KB for 10 steps (the full size, 4M individuals and 20 steps, "
+                         "is the default)")
     ap.add_argument("--no-latency", action="store_true", help="skip the single-hypothesis latency section")
     ap.add_argument("--schedule", default="replicas", choices=["replicas", "static", "dynamic"],
                     help="replicas: each rank its own batches (default); static: every global batch split by "

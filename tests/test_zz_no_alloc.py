@@ -32,8 +32,12 @@ def test_no_alloc_matches_eval_concept_on_two_calls(dkb):
     r = Rng(12, 12)
     progs = [np.array(pins.random_program(r, kb, r.randint(1, 6)).postfix(), np.uint64) for _ in range(24)]
     progs += hyps.batch_hyps(kb, 13, 0, 8)
+    import oracle
+    okb = oracle.from_synth(kb)
     for prog in progs:
         want = d.eval(prog)                                  # the existing entry point, caller workspace
+        # and the instance set itself, from the independent CPU evaluator
+        assert np.array_equal(K.unpack_bits(want, kb.n), oracle.eval_program(okb, prog))
         for call in range(2):                                # two calls in a row on the shared scratch
             out = torch.full((d.wp,), -1, dtype=torch.int32, device="cuda")
             H.hedl_eval_concept_noalloc(d.handle, prog, out)
