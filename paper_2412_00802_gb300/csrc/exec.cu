@@ -222,30 +222,15 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
             }
         }
     };
-    // rounds in pairs: both rounds' rows are requested before either is evaluated
-    for (uint32_t r = 0; r < rounds; r += 2) {
-        const uint32_t wb0 = tile * hd.tile_words + (r * NW + warp) * ww * WPL;
-        if (wb0 >= kb.wp) break;
-        const uint32_t wb1 = wb0 + NW * ww * WPL;
-        const bool two = r + 1 < rounds && wb1 < kb.wp;
-        uint32_t pf0[PF][WPL], pv0[WPL], nv0[WPL], pf1[PF][WPL], pv1[WPL], nv1[WPL];
-        prefetch(wb0, pf0, pv0, nv0);
-        if (two) prefetch(wb1, pf1, pv1, nv1);
-        uint32_t wb = wb0;
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {   // one copy of the stack machine: round 1's rows move into round 0's
-            if (q == 1) {
-                if (!two) break;
-#pragma unroll
-                for (int k = 0; k < PF; ++k)
-#pragma unroll
-                    for (int s = 0; s < WPL; ++s) pf0[k][s] = pf1[k][s];
-#pragma unroll
-                for (int s = 0; s < WPL; ++s) pv0[s] = pv1[s], nv0[s] = nv1[s];
-                wb = wb1;
-            }
-            evaluate(wb, pf0, pv0, nv0);
-        }
+    // one round at a time: the round's leaf rows are all requested before the
+    // first instruction runs (requesting the next round's as well was slower:
+    // twice the prefetch registers, more spills)
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t wb = tile * hd.tile_words + (r * NW + warp) * ww * WPL;
+        if (wb >= kb.wp) break;
+        uint32_t pf[PF][WPL], pv[WPL], nv[WPL];
+        prefetch(wb, pf, pv, nv);
+        evaluate(wb, pf, pv, nv);
     }
     if (seg.hyp != NO_HYP && A.counts) {
 #pragma unroll
@@ -339,10 +324,10 @@ constexpr uint32_t WALK_BUF = 256;   // 32-bit words of a warp's window buffer
 
 // Walk task: for each individual, the saturating per-slice count of its
 // successors' FT words (P words each: 32 P slices), mapped through the
-// group's truth tables, transposed back into the output slots (four words per
-// lane per 16-byte store).  The warp takes its words four at a time (128
-// individuals, whose rows form one contiguous edge range) and streams that
-// range in windows of WALK_BUF / P edges: lane e loads edges e, e + 32, ...
+// group's truth tables, transposed back into the output slots (4 / P words
+// per lane per store).  The warp takes its words 4 / P at a time (their
+// individuals' rows form one contiguous edge range) and streams that range in
+// windows of WALK_BUF / P edges: lane e loads edges e, e + 32, ...
 // of the window (coalesced), gathers their FT words and puts them in a
 // per-warp shared-memory buffer; then each lane adds the buffer entries of its
 // own rows.  The next window's edges are loaded while the current window's FT
@@ -354,6 +339,7 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                          uint32_t *slots, uint32_t *buf) {
     constexpr uint32_t LOADS = WALK_BUF / (32u * P);   // edges a lane gathers per window
     constexpr uint32_t WIN = 32u * LOADS;
+    constexpr uint32_t CW = 4u / P;                    // words per chunk: 4 x 3 x P counters a lane
     const KBView &kb = A.kb;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const DevCSR g = kb.csr[gp->role2];
@@ -375,12 +361,12 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
     for (uint32_t p = 0; p < passes; ++p) {
         const uint32_t wb = tile * hd.tile_words + (p * NW + warp) * 32u;
         if (wb >= kb.wp) break;
-        for (uint32_t jj = 0; jj < 32u; jj += 4) {
-            if (wb + jj >= kb.wp) break;   // wp and wb are multiples of 4: whole groups of four words
-            uint32_t lo[4], hi[4];
-            bool light[4], heavy[4];
+        for (uint32_t jj = 0; jj < 32u; jj += CW) {
+            if (wb + jj >= kb.wp) break;   // wp and wb are multiples of 4: whole chunks
+            uint32_t lo[CW], hi[CW];
+            bool light[CW], heavy[CW];
 #pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
+            for (uint32_t q = 0; q < CW; ++q) {
                 const uint32_t w = wb + jj + q, i = w * 32u + lane;
                 lo[q] = hi[q] = 0;
                 if (w < kb.w && i < kb.n) {
@@ -391,18 +377,21 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                 light[q] = !heavy[q] && hi[q] > lo[q];
             }
             // the chunk's edge range ends at its last individual's row end
-            const uint32_t E1 = __reduce_max_sync(FULL, max(max(hi[0], hi[1]), max(hi[2], hi[3])));
+            uint32_t hmax = hi[0];
+#pragma unroll
+            for (uint32_t q = 1; q < CW; ++q) hmax = max(hmax, hi[q]);
+            const uint32_t E1 = __reduce_max_sync(FULL, hmax);
             // first edge at or after `at` that some light row of the chunk holds (E1 if none)
             auto next_light = [&](uint32_t at) {
                 uint32_t m = E1;
 #pragma unroll
-                for (uint32_t q = 0; q < 4; ++q)
+                for (uint32_t q = 0; q < CW; ++q)
                     if (light[q] && hi[q] > at) m = min(m, max(lo[q], at));
                 return __reduce_min_sync(FULL, m);
             };
-            uint32_t c0[4][P], c1[4][P], c2[4][P];
+            uint32_t c0[CW][P], c1[CW][P], c2[CW][P];
 #pragma unroll
-            for (uint32_t q = 0; q < 4; ++q)
+            for (uint32_t q = 0; q < CW; ++q)
 #pragma unroll
                 for (int k = 0; k < P; ++k) c0[q][k] = c1[q][k] = c2[q][k] = 0;
             uint32_t base = next_light(0);
@@ -438,7 +427,7 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                 }
                 __syncwarp();
 #pragma unroll
-                for (uint32_t q = 0; q < 4; ++q) {
+                for (uint32_t q = 0; q < CW; ++q) {
                     if (!light[q]) continue;
                     const uint32_t k1 = min(hi[q], nb);
                     for (uint32_t e = max(lo[q], base); e < k1; ++e) {
@@ -454,9 +443,9 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
                 __syncwarp();
                 base = next;
             }
-            uint32_t outw[P][4];
+            uint32_t outw[P][CW];
 #pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
+            for (uint32_t q = 0; q < CW; ++q) {
                 uint32_t hm = __ballot_sync(FULL, heavy[q]);
                 while (hm) {
                     const uint32_t h = __ffs(hm) - 1;
@@ -504,9 +493,13 @@ __device__ void run_walk(const ExecArgs &A, const PlanHeader &hd, const RGroup *
 #pragma unroll
             for (int k = 0; k < P; ++k) {
                 const uint32_t s = 32u * k + lane;
-                if (s < n)   // 16-byte aligned: wb + jj is a multiple of 4
-                    *reinterpret_cast<uint4 *>(slots + (uint64_t)gp->out[s] * kb.wp + wb + jj) =
-                        make_uint4(outw[k][0], outw[k][1], outw[k][2], outw[k][3]);
+                if (s < n) {   // aligned: wb + jj is a multiple of CW
+                    uint32_t *dst = slots + (uint64_t)gp->out[s] * kb.wp + wb + jj;
+                    if constexpr (CW == 4)
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(outw[k][0], outw[k][1], outw[k][2], outw[k][3]);
+                    else
+                        *reinterpret_cast<uint2 *>(dst) = make_uint2(outw[k][0], outw[k][1]);
+                }
             }
         }
     }
