@@ -369,9 +369,10 @@ def _oracle_rate(kb, progs, budget_s: float = 6.0):
             "sample": f"the first {done} of these restrictions on {cores} host threads ({dt:.1f} s)"}
 
 
-def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7):
+def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7, label=None):
     """One launch of a batch of restrictions, device-resident: median of `reps` CUDA-event timings on
-    the launching stream after warm-up (the graph is captured on the second execution)."""
+    the launching stream after warm-up (the graph is captured on the second execution).  The timed
+    launches sit in the NVTX range `label`, if given, so a profiler can capture only those."""
     import torch
     import paper_2412_00802_gb300 as H
     from synth import programs as P
@@ -388,6 +389,8 @@ def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7):
         run()
     torch.cuda.synchronize()
     ms = []
+    if label:
+        torch.cuda.nvtx.range_push(label)
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -395,6 +398,8 @@ def _timed_restrictions(dkb, progs, flags, dev, peak, reps=7):
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+    if label:
+        torch.cuda.nvtx.range_pop()
     H.hedl_sync_status(dkb.handle)
     t = statistics.median(ms) / 1000.0
     return {"restrictions": len(progs), "ms": 1000 * t, "restrictions_per_s": len(progs) / t,
@@ -422,9 +427,9 @@ def numeric_run(args, dev):
     three = [np.array([P.insn(op, 0, q, P.f32_bits(thr[q]))], np.uint64)
              for q in range(kb.n_num_roles) for op in (P.DGE, P.DLE, P.DEQ)]
     with ClockSampler(dev.index or 0) as clk:
-        a, _ = _timed_restrictions(dkb, one, 0, dev, peak)
-        b, cb = _timed_restrictions(dkb, three, 0, dev, peak)
-        c, cp = _timed_restrictions(dkb, three, H.HEDL_PLAIN, dev, peak)
+        a, _ = _timed_restrictions(dkb, one, 0, dev, peak, label="numeric_one")
+        b, cb = _timed_restrictions(dkb, three, 0, dev, peak, label="numeric_three")
+        c, cp = _timed_restrictions(dkb, three, H.HEDL_PLAIN, dev, peak, label="numeric_three_plain")
     # the oracle on roles 0 and 1 (their 6 restrictions), converted alone to keep the run short
     cpu = _oracle_rate(dc_replace(kb, num_row_ptr=kb.num_row_ptr[:2], num_vals=kb.num_vals[:2]), three[:6])
     return {"workload": "N=10,000,000 individuals, 8 numeric concrete roles, Poisson(4) values per individual "
@@ -461,9 +466,9 @@ def string_run(args, dev):
                   np.array([P.insn(P.SCONTAINS, 0, q, 1 + q)], np.uint64),
                   np.array([P.insn(P.SCONTAINS, 0, q, 17 + q)], np.uint64)]
     with ClockSampler(dev.index or 0) as clk:
-        a, _ = _timed_restrictions(dkb, one, 0, dev, peak)
-        b, cb = _timed_restrictions(dkb, mixed, 0, dev, peak)
-        c, cp = _timed_restrictions(dkb, mixed, H.HEDL_PLAIN, dev, peak)
+        a, _ = _timed_restrictions(dkb, one, 0, dev, peak, label="strings_one")
+        b, cb = _timed_restrictions(dkb, mixed, 0, dev, peak, label="strings_mixed")
+        c, cp = _timed_restrictions(dkb, mixed, H.HEDL_PLAIN, dev, peak, label="strings_mixed_plain")
     cpu = _oracle_rate(dc_replace(kb, str_row_ptr=kb.str_row_ptr[:2], str_ids=kb.str_ids[:2]), mixed[:6])
     return {"workload": "N=10,000,000 individuals, 8 string concrete roles, Poisson(2) values per individual "
                         "(~2*10^7 ids, 120 MB per role) into 100,000 distinct strings of 3-12 letters; 64 "

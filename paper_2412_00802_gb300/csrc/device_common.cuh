@@ -108,6 +108,15 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
     return v;
 }
 
+// the same for four consecutive words (p 16-byte aligned)
+__device__ __forceinline__ uint4 ld_stream4(const uint32_t *p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
 
 // Role restriction over the warp's 32*WPL words (Algorithms 3-8 of the
 // paper, recast).  For each word (32 individuals) the warp walks the word's
@@ -400,7 +409,8 @@ __device__ __forceinline__ bool data_cmp(uint32_t cmp, float x, float t) {
 // roles, Algorithms 9-10), id equality (string EQUAL, Algorithms 11-12) or a
 // bit of the pattern's containment row (string CONTAIN, Algorithms 13-14).
 // ValueTest carries the kind at run time; exist_words is compiled once per
-// kind (FloatTest, IdEqTest, IdBitTest) and dispatched once per restriction.
+// kind (each float compare, IdEqTest, IdBitTest) and dispatched once per
+// restriction.
 struct ValueTest {
     enum : uint32_t { FLOAT_CMP = 0, ID_EQ = 1, ID_BIT = 2 };
     uint32_t mode;
@@ -408,10 +418,13 @@ struct ValueTest {
     uint32_t arg;           // FLOAT_CMP: the threshold's bits; ID_EQ: the string id
     const uint32_t *bits;   // ID_BIT: the containment row
 };
+template <uint32_t CMP>
 struct FloatTest {
-    uint32_t cmp;
     float t;
-    __device__ __forceinline__ bool operator()(uint32_t x) const { return data_cmp(cmp, __uint_as_float(x), t); }
+    __device__ __forceinline__ bool operator()(uint32_t x) const {
+        const float f = __uint_as_float(x);
+        return CMP == HEDL_OP_DGE ? (f >= t) : CMP == HEDL_OP_DLE ? (f <= t) : (f == t);
+    }
 };
 struct IdEqTest {
     uint32_t id;
@@ -424,103 +437,153 @@ struct IdBitTest {
 
 // Existential restriction on a concrete role with several values per
 // subject (Section III-B): individual i belongs iff one of its values
-// vals[rp[i] .. rp[i+1]) passes the test.  The 32 individuals of a word own
-// one contiguous run of values; the warp reads it EX_STEP values a step (four
-// coalesced loads), ballots the tests, and each lane tests the bits that fall
-// in its own sub-range.  The words are software-pipelined: while word w is
-// tested, the first steps of words w+1 and w+2 and the row pointers of words
-// w+3 and w+4 are in flight (a word's first step is fetched two words after
-// its row pointers), so a word whose run fits one step costs a fraction of a
-// memory latency.  A longer run continues step by step and the warp
-// leaves it once every individual whose values reach past the step has found
-// one (the paper's skip over a subject already satisfied), so a heavy subject
-// costs 1/32 of a lane walk.
-constexpr uint32_t EX_LOADS = 4;
-constexpr uint32_t EX_STEP = 32u * EX_LOADS;
+// vals[rp[i] .. rp[i+1]) passes the test.  The warp's 32*WPL words are
+// 1024*WPL consecutive individuals, so their values form one contiguous run,
+// and the warp streams that run once, in windows of EX_WIN values.  Each lane
+// loads four 16-byte vectors of a window (each load coalesced over 512
+// bytes), and the warp turns the tests into the window's 512-bit pass mask:
+// lane k < 16 keeps mask word k and the position of the first pass in the
+// words after it.  The row pointers come four words at a time (lane l loads
+// rp[32w + l] of each, the next four in flight), and each lane finds the
+// first pass at or after its row's start with two shuffles and compares it
+// with the row's end.  The next window's values are in flight while the
+// current one is looked up.  A window is loaded only while a row that has
+// not passed yet reaches into it, and the stream jumps straight to the first
+// such row, so a subject already satisfied is skipped (the paper's early
+// exit): a heavy subject costs its values up to the window of its first
+// pass.  Value counts stay below 2^31 (the KB loader's limit), so positions
+// relative to a window fit signed 32-bit arithmetic.
+constexpr uint32_t EX_LOADS = 4;               // 16-byte loads per lane per window
+constexpr uint32_t EX_WIN = 128u * EX_LOADS;   // values per window
+constexpr uint32_t EX_NONE = 0x7FFFFFFFu;      // no pass
 
-// this lane's row of word w (empty past the warp's words or past n)
-__device__ __forceinline__ void ex_row(const uint32_t *rp, uint32_t w, uint32_t n_words, uint32_t n, uint32_t lane,
-                                       uint32_t &lo, uint32_t &hi) {
-    lo = hi = 0;
-    const uint32_t i = w * 32u + lane;
-    if (w < n_words && i < n) {
-        lo = ld_stream(rp + i);
-        hi = ld_stream(rp + i + 1);
+// The row pointers of words w0 .. w0+3: r[q] = rp[32(w0 + q) + lane],
+// tail = rp[32 w0 + 128], zero past n (a zero end makes a row empty).
+struct ExRows {
+    uint32_t r[4];
+    uint32_t tail;
+};
+__device__ __forceinline__ void ex_rows(ExRows &b, const uint32_t *rp, uint32_t w0, uint32_t w_end, uint32_t n,
+                                        uint32_t lane) {
+    if (w0 >= w_end) return;   // warp-uniform; nothing reads this batch
+#pragma unroll
+    for (uint32_t q = 0; q < 4u; ++q) {
+        const uint32_t i = 32u * (w0 + q) + lane;
+        b.r[q] = i <= n ? ld_stream(rp + i) : 0u;
     }
+    const uint32_t t = 32u * w0 + 128u;
+    b.tail = t <= n ? ld_stream(rp + t) : 0u;
 }
 
-// the values [c, c + EX_STEP) of a run ending at end, one per lane and load
-__device__ __forceinline__ void ex_fetch(const uint32_t *vals, uint32_t c, uint32_t end, uint32_t lane,
-                                         uint32_t (&x)[EX_LOADS]) {
+// the window [c, c + EX_WIN) of a run ending at end (c a multiple of 128):
+// lane l's vector u holds values c + 128u + 4l .. + 3 (zero at and past end)
+__device__ __forceinline__ void ex_fetch(const uint32_t *vals, uint32_t c, uint32_t end, bool vec, uint32_t lane,
+                                         uint4 (&x)[EX_LOADS]) {
 #pragma unroll
     for (uint32_t u = 0; u < EX_LOADS; ++u) {
-        const uint32_t k = c + 32u * u + lane;
-        x[u] = k < end ? __ldg(vals + k) : 0u;
+        const uint32_t k = c + 128u * u + 4u * lane;
+        if (vec && k + 4u <= end) {
+            x[u] = ld_stream4(vals + k);
+        } else {
+            x[u].x = k < end ? ld_stream(vals + k) : 0u;
+            x[u].y = k + 1u < end ? ld_stream(vals + k + 1u) : 0u;
+            x[u].z = k + 2u < end ? ld_stream(vals + k + 2u) : 0u;
+            x[u].w = k + 3u < end ? ld_stream(vals + k + 3u) : 0u;
+        }
     }
 }
 
-// does a value in [c, c + EX_STEP) of this lane's row [lo, hi) pass?
+// The window's pass mask: word k (values c + 32k .. c + 32k + 31) to lane k
+// < 16, zero to lanes 16..31, and in fn the position of the first pass in
+// words k+1 .. 15 (EX_NONE if none).  Lane l's four values of vector u are
+// bits 4(l mod 8) .. +3 of word 4u + l/8; an OR over each group of eight
+// lanes assembles the word, lane k fetches word k from its group, and a
+// suffix minimum over the lanes gives fn.
 template <class Test>
-__device__ __forceinline__ bool ex_test(const uint32_t (&x)[EX_LOADS], uint32_t c, uint32_t end, uint32_t lo,
-                                        uint32_t hi, uint32_t lane, const Test &test) {
-    bool hit = false;
+__device__ __forceinline__ uint32_t ex_bits(const uint4 (&x)[EX_LOADS], uint32_t lane, const Test &test,
+                                            uint32_t &fn) {
+    uint32_t wu[EX_LOADS];
 #pragma unroll
     for (uint32_t u = 0; u < EX_LOADS; ++u) {
-        const uint32_t cu = c + 32u * u;
-        const uint32_t m = __ballot_sync(FULL, cu + lane < end && test(x[u]));
-        const uint32_t a = lo > cu ? min(lo - cu, 32u) : 0u, b = hi > cu ? min(hi - cu, 32u) : 0u;
-        hit = hit || (m & range_mask(a, b)) != 0u;
+        uint32_t q = (uint32_t)test(x[u].x) | (uint32_t)test(x[u].y) << 1 | (uint32_t)test(x[u].z) << 2 |
+                     (uint32_t)test(x[u].w) << 3;
+        q <<= 4u * (lane & 7u);
+        q |= __shfl_xor_sync(FULL, q, 1);
+        q |= __shfl_xor_sync(FULL, q, 2);
+        q |= __shfl_xor_sync(FULL, q, 4);
+        wu[u] = q;
     }
-    return hit;
+    uint32_t bm = 0;
+#pragma unroll
+    for (uint32_t u = 0; u < EX_LOADS; ++u) {
+        const uint32_t t = __shfl_sync(FULL, wu[u], 8u * (lane & 3u));
+        if ((lane >> 2) == u) bm = t;
+    }
+    uint32_t f = bm ? 32u * lane + (uint32_t)__ffs(bm) - 1u : EX_NONE;
+#pragma unroll
+    for (uint32_t o = 1; o < 16u; o <<= 1) f = min(f, __shfl_down_sync(FULL, f, o));
+    fn = __shfl_down_sync(FULL, f, 1);   // lane 31 keeps its own EX_NONE
+    return bm;
 }
 
 template <int WPL, class Test>
 __device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const Test test, uint32_t n,
                                             uint32_t n_words, uint32_t wb, uint32_t lane, uint32_t (&v)[WPL]) {
-    // rows [loK, hiK) of words w .. w+3; runs [bK, eK) and first steps xK of words w, w+1
-    uint32_t lo0, hi0, lo1, hi1, lo2, hi2, lo3, hi3;
-    ex_row(rp, wb, n_words, n, lane, lo0, hi0);
-    ex_row(rp, wb + 1, n_words, n, lane, lo1, hi1);
-    ex_row(rp, wb + 2, n_words, n, lane, lo2, hi2);
-    ex_row(rp, wb + 3, n_words, n, lane, lo3, hi3);
-    uint32_t b0 = __shfl_sync(FULL, lo0, 0), e0 = __reduce_max_sync(FULL, hi0);
-    uint32_t b1 = __shfl_sync(FULL, lo1, 0), e1 = __reduce_max_sync(FULL, hi1);
-    uint32_t x0[EX_LOADS], x1[EX_LOADS];
-    ex_fetch(vals, b0, e0, lane, x0);
-    ex_fetch(vals, b1, e1, lane, x1);
-    for (int j = 0; j < 32; ++j) {
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) {
-            const uint32_t w = wb + (uint32_t)j * WPL + s;   // the words go in order: w + 1 is the next
-            uint32_t word = 0;
-            if (w < n_words) {   // warp-uniform; then lane 0's individual 32w < n exists
-                // start word w+2's first step (its rows came two words ago) and word w+4's rows
-                const uint32_t b2 = __shfl_sync(FULL, lo2, 0), e2 = __reduce_max_sync(FULL, hi2);
-                uint32_t x2[EX_LOADS];
-                ex_fetch(vals, b2, e2, lane, x2);
-                uint32_t lo4, hi4;
-                ex_row(rp, w + 4, n_words, n, lane, lo4, hi4);
-                // test word w
-                bool hit = ex_test(x0, b0, e0, lo0, hi0, lane, test);
-                for (uint32_t c = b0 + EX_STEP; c < e0; c += EX_STEP) {
-                    if (__all_sync(FULL, hit || hi0 <= c)) break;
-                    uint32_t y[EX_LOADS];
-                    ex_fetch(vals, c, e0, lane, y);
-                    hit = ex_test(y, c, e0, lo0, hi0, lane, test) || hit;
-                }
-                word = __ballot_sync(FULL, hit);
-                lo0 = lo1, hi0 = hi1, b0 = b1, e0 = e1;
-                lo1 = lo2, hi1 = hi2, b1 = b2, e1 = e2;
-                lo2 = lo3, hi2 = hi3;
-                lo3 = lo4, hi3 = hi4;
-#pragma unroll
-                for (uint32_t u = 0; u < EX_LOADS; ++u) {
-                    x0[u] = x1[u];
-                    x1[u] = x2[u];
-                }
+    for (int s = 0; s < WPL; ++s) v[s] = 0u;
+    const uint32_t w_end = min(wb + 32u * WPL, n_words);   // the warp's words [wb, w_end)
+    if (wb >= w_end) return;
+    const bool vec = (reinterpret_cast<uintptr_t>(vals) & 15u) == 0;
+    const uint32_t end = ld_stream(rp + min(32u * w_end, n));   // the end of the warp's run
+    uint32_t c = ld_stream(rp + 32u * wb) & ~127u;               // the window
+    uint4 x[EX_LOADS];
+    ex_fetch(vals, c, end, vec, lane, x);
+    uint32_t fn;
+    uint32_t bm = ex_bits(x, lane, test, fn);
+    ex_fetch(vals, c + EX_WIN, end, vec, lane, x);               // the next window, in flight
+    // row batches alternate between two registers, so a pending load is never copied
+    ExRows ra, rb;
+    ex_rows(ra, rp, wb, w_end, n, lane);
+    ex_rows(rb, rp, wb + 4u, w_end, n, lane);
+    auto batch = [&](uint32_t w0, const ExRows &rows) {
+#pragma unroll 1
+        for (uint32_t j = 0; j < 4u && w0 + j < w_end; ++j) {   // warp-uniform
+            // this lane's row [lo, hi): lane 31's end is the next word's first row pointer
+            const uint32_t lo = j == 0u ? rows.r[0] : j == 1u ? rows.r[1] : j == 2u ? rows.r[2] : rows.r[3];
+            const uint32_t ln = j == 0u ? rows.r[1] : j == 1u ? rows.r[2] : j == 2u ? rows.r[3] : rows.tail;
+            const uint32_t dn = __shfl_down_sync(FULL, lo, 1), up = __shfl_sync(FULL, ln, 0);
+            const uint32_t hi = lane == 31u ? up : dn;
+            bool hit = false;
+            for (;;) {
+                const int rl = (int)(lo - c), rh = (int)(hi - c);   // the row relative to the window
+                const int a = max(rl, 0), b = min(rh, (int)EX_WIN);
+                const uint32_t wa = (uint32_t)a >> 5;
+                const uint32_t ma = __shfl_sync(FULL, bm, wa), fa = __shfl_sync(FULL, fn, wa);
+                const uint32_t m = ma & (FULL << (a & 31));
+                const int first = m ? (int)(32u * wa + (uint32_t)__ffs(m) - 1u) : (int)fa;   // first pass >= a
+                hit = hit || (a < b && first < b);
+                // the first value, past the window, of a row that has not passed yet
+                const bool more = !hit && rh > (int)EX_WIN && rl < rh;
+                const uint32_t nxt = __reduce_min_sync(FULL, more ? (uint32_t)max(rl, (int)EX_WIN) : 0xFFFFFFFFu);
+                if (nxt == 0xFFFFFFFFu) break;
+                const uint32_t cn = c + (nxt & ~127u);
+                if (cn != c + EX_WIN) ex_fetch(vals, cn, end, vec, lane, x);   // a jump: not the window in flight
+                c = cn;
+                bm = ex_bits(x, lane, test, fn);
+                ex_fetch(vals, c + EX_WIN, end, vec, lane, x);
             }
-            if (lane == (uint32_t)j) v[s] = word;
+            const uint32_t word = __ballot_sync(FULL, hit), k = w0 + j - wb;
+#pragma unroll
+            for (int s = 0; s < WPL; ++s)
+                if (lane == k / WPL && k % WPL == (uint32_t)s) v[s] = word;
         }
+    };
+    for (uint32_t w0 = wb; w0 < w_end; w0 += 8u) {
+        batch(w0, ra);
+        ex_rows(ra, rp, w0 + 8u, w_end, n, lane);
+        if (w0 + 4u >= w_end) break;
+        batch(w0 + 4u, rb);
+        ex_rows(rb, rp, w0 + 12u, w_end, n, lane);
     }
 }
 
@@ -530,9 +593,15 @@ template <int WPL>
 __device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *vals, const ValueTest &test,
                                             uint32_t n, uint32_t n_words, uint32_t wb, uint32_t lane,
                                             uint32_t (&v)[WPL]) {
-    if (test.mode == ValueTest::FLOAT_CMP)
-        exist_words<WPL>(rp, vals, FloatTest{test.cmp, __uint_as_float(test.arg)}, n, n_words, wb, lane, v);
-    else if (test.mode == ValueTest::ID_EQ)
+    if (test.mode == ValueTest::FLOAT_CMP) {
+        const float t = __uint_as_float(test.arg);
+        if (test.cmp == HEDL_OP_DGE)
+            exist_words<WPL>(rp, vals, FloatTest<HEDL_OP_DGE>{t}, n, n_words, wb, lane, v);
+        else if (test.cmp == HEDL_OP_DLE)
+            exist_words<WPL>(rp, vals, FloatTest<HEDL_OP_DLE>{t}, n, n_words, wb, lane, v);
+        else
+            exist_words<WPL>(rp, vals, FloatTest<HEDL_OP_DEQ>{t}, n, n_words, wb, lane, v);
+    } else if (test.mode == ValueTest::ID_EQ)
         exist_words<WPL>(rp, vals, IdEqTest{test.arg}, n, n_words, wb, lane, v);
     else
         exist_words<WPL>(rp, vals, IdBitTest{test.bits}, n, n_words, wb, lane, v);

@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t find_group(const Group *groups, uint32_t n_g
     return lo;
 }
 
-template <int NW, int WPL, bool STAGE, int BLK>
+template <int NW, int WPL, bool STAGE, int BLK, bool CONCRETE>
 __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg, uint32_t tile,
                          Smem<NW, WPL> &sm, uint32_t *slots, uint32_t *acc) {
     const KBView &kb = A.kb;
@@ -187,10 +187,13 @@ __device__ void run_tile(const ExecArgs &A, const PlanHeader &hd, const Seg &seg
                 break;
             case D_DATA:
                 if ((d.op >> 8) & 3u) {   // a numeric (bit 8) or string (bit 9) concrete role
-                    const bool str = (d.op >> 9) & 1u;
-                    const uint32_t *rp = str ? kb.str[d.a].rp : kb.num[d.a].rp;
-                    const uint32_t *vals = str ? kb.str[d.a].ids : reinterpret_cast<const uint32_t *>(kb.num[d.a].vals);
-                    exist_words<WPL>(rp, vals, value_test(kb, d.op, d.b), kb.n, lim_w, wb, lane, top);
+                    if constexpr (CONCRETE) {
+                        const bool str = (d.op >> 9) & 1u;
+                        const uint32_t *rp = str ? kb.str[d.a].rp : kb.num[d.a].rp;
+                        const uint32_t *vals =
+                            str ? kb.str[d.a].ids : reinterpret_cast<const uint32_t *>(kb.num[d.a].vals);
+                        exist_words<WPL>(rp, vals, value_test(kb, d.op, d.b), kb.n, lim_w, wb, lane, top);
+                    }
                 } else
                     data_words<WPL>(kb.props + (uint64_t)d.a * kb.prop_stride, (d.op >> 16) & 0xFFu,
                                     __uint_as_float(d.b), kb.n, lim_w, wb, lane, top);
@@ -549,7 +552,10 @@ __device__ __forceinline__ void stage_filler(const KBView &kb, const uint32_t *s
 // walks out (for plans without role groups: a lone hypothesis, concrete-role
 // restrictions); the rest fits 64 registers, so that build keeps 1,024
 // threads per SM for the latency-bound lone walks and value streams.
-template <int NW, int WPL, bool STAGE, int BLK, bool FULL = false, bool GROUPS = true>
+// CONCRETE = false leaves the concrete-role value walk out, for KBs that have
+// no concrete roles: its registers would otherwise raise the spills of the
+// whole stack machine.
+template <int NW, int WPL, bool STAGE, int BLK, bool FULL = false, bool GROUPS = true, bool CONCRETE = true>
 __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : (GROUPS ? 24 : 32)) / NW) exec_kernel(ExecArgs A) {
     // the host sizes the dynamic shared memory as stack_smem_bytes + 16 (+ a staged filler)
     using SmemT = Smem<NW, WPL>;
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(NW * 32, (FULL ? 64 : (GROUPS ? 24 : 32)) / NW
                     __syncthreads();
                 }
             }
-            run_tile<NW, WPL, STAGE, BLK>(A, hd, seg, tile, sm, slots, acc);
+            run_tile<NW, WPL, STAGE, BLK, CONCRETE>(A, hd, seg, tile, sm, slots, acc);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -675,7 +681,14 @@ KernelFn pick_t(uint32_t warps, uint32_t wpl) {
     return exec_kernel<8, 1, STAGE, BLK>;
 }
 
-KernelFn pick(const Tuning &t, bool stage, bool groups) {
+KernelFn pick(const Tuning &t, bool stage, bool groups, bool concrete) {
+    if (!concrete && !t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage) {   // the common shapes
+        if (!groups)
+            return t.role_block == 4 ? exec_kernel<8, 1, false, 4, false, false, false>
+                                     : exec_kernel<8, 1, false, 8, false, false, false>;
+        return t.role_block == 4 ? exec_kernel<8, 1, false, 4, false, true, false>
+                                 : exec_kernel<8, 1, false, 8, false, true, false>;
+    }
     if (!groups && !t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage)   // no role groups: 64 registers
         return t.role_block == 4 ? exec_kernel<8, 1, false, 4, false, false> : exec_kernel<8, 1, false, 8, false, false>;
     if (t.full_occupancy && t.warps == 8 && t.wpl == 1 && !stage)
@@ -700,7 +713,7 @@ size_t exec_smem_bytes(const Tuning &t) { return stack_smem_bytes(t) + 16; }
 
 int exec_occupancy(const hedl_kb *kb, const Tuning &t, bool groups, int *blocks_per_sm) {
     const bool stage = use_staging(kb, t);
-    KernelFn fn = pick(t, stage, groups);
+    KernelFn fn = pick(t, stage, groups, kb->has_concrete());
     size_t smem = smem_bytes(kb, t, stage);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -712,7 +725,7 @@ int launch_exec(const hedl_kb *kb, const PlanImpl *p, uint32_t *counts, uint32_t
                 void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Tuning &t = p->tuning;
-    KernelFn fn = pick(t, p->staged, p->n_rgroups > 0);
+    KernelFn fn = pick(t, p->staged, p->n_rgroups > 0, kb->has_concrete());
     size_t smem = smem_bytes(kb, t, p->staged);
     int bps = p->bps;
     if (bps < 1) return cudaErrorInvalidConfiguration;

@@ -213,6 +213,8 @@ struct hedl_kb {
     std::vector<uint64_t> cached_progs;     // the cached plan's programs, compared on a hash match
     std::vector<uint32_t> cached_offs;
     hedl::KBView view() const;
+    // a plan can name a concrete role only if the KB has one
+    bool has_concrete() const { return !num_host.empty() || !str_host.empty(); }
 };
 
 struct hedl_plan {
