@@ -108,6 +108,22 @@ __device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
     return v;
 }
 
+// A hint to bring bytes [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16, the range inside one allocation); no register waits on it.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of a[lo, hi) by lane 0 (a 16-byte aligned): the start is
+// rounded down and the size down to whole 16-byte units, so the hint stays
+// inside [0, hi).
+__device__ __forceinline__ void prefetch_range(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t lane) {
+    if (lane != 0u || lo >= hi) return;
+    lo &= ~3u;
+    const uint32_t bytes = ((hi - lo) * 4u) & ~15u;
+    if (bytes) prefetch_l2(a + lo, bytes);
+}
+
 // the same for four consecutive words (p 16-byte aligned)
 __device__ __forceinline__ uint4 ld_stream4(const uint32_t *p) {
     uint4 v;
@@ -225,7 +241,8 @@ __device__ __forceinline__ void role_words(const DevCSR g, const uint32_t *fille
 // walk).  The words wb .. wb+K-1 are consecutive individuals, so their CSR
 // rows form one contiguous edge range [E0, E1).  The warp reads that range in
 // blocks of BLK 32-edge chunks, always loading the next block while it tests
-// the current one (the gather's DRAM latency overlaps the filler lookups),
+// the current one (the gather's DRAM latency overlaps the filler lookups) and
+// asking L2 for the blocks after it (prefetch hints that hold no registers),
 // and attributes each block's hits to the words whose rows it covers: lane i
 // of word k counts the hits inside its row with two rank lookups, as in
 // role_words, and a word is emitted (ballot) once its last edge has passed.
@@ -292,8 +309,16 @@ __device__ __forceinline__ void role_stream(const DevCSR g, const uint32_t *fill
 #pragma unroll
         for (int u = 0; u < BLK; ++u) pf[u] = ld_stream(col + min(at + 32u * u + lane, E1 - 1u));
     };
+    // L2 hints (no registers held): the warp's row pointers, and the edge
+    // blocks two to four ahead of the one loading into registers
+    const bool cvec = (reinterpret_cast<uintptr_t>(col) & 15u) == 0;
+    if ((reinterpret_cast<uintptr_t>(rp) & 15u) == 0) prefetch_range(rp, wb * 32u, min(n, (wb + K) * 32u) + 1u, lane);
+    auto ahead = [&](uint32_t from, uint32_t blocks) {
+        if (cvec && from < E1) prefetch_range(col, from, min(E1, from + blocks * BE), lane);
+    };
     uint32_t base = E0;
     if (base < E1) fetch(base);
+    ahead(E0 + BE, 3u);
 #pragma unroll 1
     while (base < E1) {
         uint32_t hit[BLK];
@@ -301,6 +326,7 @@ __device__ __forceinline__ void role_stream(const DevCSR g, const uint32_t *fill
         for (int u = 0; u < BLK; ++u) hit[u] = pf[u];
         const uint32_t nb = base + BE;
         if (nb < E1) fetch(nb);
+        ahead(base + 4u * BE, 1u);
         // Positions past E1 reloaded edge E1-1; they lie beyond every row, so no rank counts them.
 #pragma unroll
         for (int u = 0; u < BLK; ++u) hit[u] = (__funnelshift_r(filler[hit[u] >> 5], 0u, hit[u]) & 1u) ^ neg;
@@ -349,7 +375,10 @@ __device__ __forceinline__ void role_stream(const DevCSR g, const uint32_t *fill
             if (++k == K) return;
             const uint32_t nxt = ew1;                  // the next word's first edge
             next_word();
-            if (nxt != nb && nxt < E1) fetch(nxt);
+            if (nxt != nb && nxt < E1) {
+                fetch(nxt);
+                ahead(nxt + BE, 3u);
+            }
             base = nxt;
         } else {
             base = nb;
@@ -447,7 +476,10 @@ struct IdBitTest {
 // rp[32w + l] of each, the next four in flight), and each lane finds the
 // first pass at or after its row's start with two shuffles and compares it
 // with the row's end.  The next window's values are in flight while the
-// current one is looked up.  A window is loaded only while a row that has
+// current one is looked up, and the warp's row pointers are requested into L2
+// when it starts (a bulk prefetch hint, which holds no registers).  Hinting
+// the values too was slower where several restrictions read one role's
+// values at once.  A window is loaded only while a row that has
 // not passed yet reaches into it, and the stream jumps straight to the first
 // such row, so a subject already satisfied is skipped (the paper's early
 // exit): a heavy subject costs its values up to the window of its first
@@ -536,6 +568,9 @@ __device__ __forceinline__ void exist_words(const uint32_t *rp, const uint32_t *
     const bool vec = (reinterpret_cast<uintptr_t>(vals) & 15u) == 0;
     const uint32_t end = ld_stream(rp + min(32u * w_end, n));   // the end of the warp's run
     uint32_t c = ld_stream(rp + 32u * wb) & ~127u;               // the window
+    // the warp's row pointers go to L2 ahead of their loads (a hint that
+    // holds no registers)
+    if ((reinterpret_cast<uintptr_t>(rp) & 15u) == 0) prefetch_range(rp, 32u * wb, min(32u * w_end, n) + 1u, lane);
     uint4 x[EX_LOADS];
     ex_fetch(vals, c, end, vec, lane, x);
     uint32_t fn;
