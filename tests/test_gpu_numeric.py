@@ -105,6 +105,34 @@ def test_stress_shapes(nd):
         compare_batch(kb, dkb, progs, mode)
 
 
+@pytest.mark.parametrize("nd", [("poisson", 3.0), ("single", 20_000)])
+def test_value_arrays_not_16_byte_aligned(nd):
+    """The value walk reads 16-byte vectors and hints row pointers into L2 only from 16-byte
+    aligned arrays; row pointers and values that start 4 bytes past a boundary take the scalar
+    loads and must give the same sets (a ragged size, and a run spanning many windows)."""
+    import torch
+    kb = numeric_kb(4099, 410, nd=nd, n_num=2)
+    dkb = device_kb(kb)
+
+    def shifted(x):
+        big = torch.zeros(x.numel() + 1, dtype=x.dtype, device=x.device)
+        big[1:] = x
+        return big[1:]
+    dkb.num_roles = [(shifted(rp), shifted(v)) for rp, v in dkb.num_roles]
+    assert all(rp.data_ptr() % 16 and v.data_ptr() % 16 for rp, v in dkb.num_roles)
+    with torch.cuda.device(dkb.device):
+        dkb.handle = H.hedl_kb_load(kb.n, dkb.concepts, dkb.roles, dkb.inv_roles, dkb.props,
+                                    num_roles=dkb.num_roles)
+        dkb.set_examples(kb.pos_bits, kb.neg_bits)
+    progs = []
+    for q in range(kb.n_num_roles):
+        progs += restrictions(kb, q, (500.0,))
+    r = Rng(411, 1)
+    progs += [np.array(pins.random_program(r, kb, r.randint(1, 4)).postfix(), np.uint64) for _ in range(60)]
+    for mode in (0, H.HEDL_PLAIN):
+        compare_batch(kb, dkb, progs, mode)
+
+
 def test_hand_worked_nan_and_signed_zero():
     """Individual 0 holds {1.5, NaN}, 2 holds {-0.0}, 3 holds {NaN}, 4 holds {7, 2, 9},
     5 holds {+0.0}; 1 has no value.  Expected sets worked out by hand."""
